@@ -1,0 +1,130 @@
+"""Seeded synthetic workloads shared by the tests, the smoke check and the benchmark.
+
+Parameters only: patch layouts, motion laws, pulse parameters, time steps
+and random arrays.  None of the method's arithmetic lives here; both the CUDA
+library and the CPU oracle receive these numbers and evaluate everything
+themselves.  Seeds are ``numpy.random.default_rng(20020088 + index)`` with a
+fixed draw order, so every workload is reproducible bit for bit.
+
+The paper evaluates on no public dataset: its tests use closed-form plane
+waves (Sec. 3).  The throughput workloads here follow the same recipe with
+Gaussian-pulse closed forms:
+
+* ``static_gauss``   -- global 48^3 on [-1,1]^3 plus one static local 32^3 at
+  2x resolution centred on the origin, one Gaussian pulse (A = 1, width 0.1,
+  centre uniform in [-0.2,0.2]^3), 5-point Lagrange, CFL 0.25, 100 steps.
+* ``orbiting_gauss`` -- global 256^3 on [-1,1]^3 plus four local 128^3 patches
+  (half-width 0.25, 2x resolution) on circular orbits of radius 0.4 and
+  angular speed 2 pi in the planes z = +-0.3 (pairs opposite in phase, pair
+  phases seeded), eight Gaussians (amplitudes N(0,1), widths U[0.05,0.2],
+  centres U[-1,1]^3), 6-point Lagrange, CFL 0.25, 200 steps.
+"""
+from dataclasses import dataclass, field
+from typing import List, Tuple
+
+import numpy as np
+
+SEED_BASE = 20020088
+
+GLOBAL, LOCAL = 0, 1
+BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
+STATIC, LINEAR, CIRCULAR = 0, 1, 2
+GAUSS_SUM, PLANE_SUM, HARMONIC_POLY = 0, 1, 2
+
+
+@dataclass
+class PatchSpec:
+    kind: int
+    n: Tuple[int, int, int]
+    lo: Tuple[float, float, float]
+    hi: Tuple[float, float, float]
+    outer_bc: int
+    motion: int = STATIC
+    motion_params: Tuple[float, ...] = ()
+
+
+@dataclass
+class Workload:
+    name: str
+    patches: List[PatchSpec]
+    analytic_kind: int
+    analytic_params: np.ndarray
+    analytic_count: int
+    interp_points: int
+    ko_eps: float
+    dt: float
+    steps: int
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def interior_points(self):
+        return sum(int(np.prod(p.n)) for p in self.patches)
+
+
+def rng(index):
+    return np.random.default_rng(SEED_BASE + index)
+
+
+def static_gauss(scale=1, steps=100, interp_points=5, seed_index=0):
+    """Static global + one local patch; ``scale`` multiplies both resolutions."""
+    r = rng(seed_index)
+    centre = r.uniform(-0.2, 0.2, 3)
+    ng, nl = 48 * scale, 32 * scale
+    third = 1.0 / 3.0
+    patches = [
+        PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC),
+        PatchSpec(LOCAL, (nl, nl, nl), (-third, -third, -third), (third, third, third), BC_INTERPATCH),
+    ]
+    h_min = (2.0 * third) / nl
+    params = np.array([1.0, 0.1, centre[0], centre[1], centre[2]])
+    return Workload(f"static_gauss_{ng}+{nl}", patches, GAUSS_SUM, params, 1, interp_points, 0.005,
+                    0.25 * h_min, steps, {"centre": centre})
+
+
+def orbiting_gauss(scale=1, steps=200, interp_points=6, seed_index=1, radius=0.4, omega=2.0 * np.pi,
+                   plane_z=0.3, half_width=0.25):
+    """Global 256^3/scale + four orbiting local 128^3/scale patches."""
+    r = rng(seed_index)
+    pair_phase = r.uniform(0.0, 2.0 * np.pi, 2)
+    amps = r.normal(0.0, 1.0, 8)
+    widths = r.uniform(0.05, 0.2, 8)
+    centres = r.uniform(-1.0, 1.0, (8, 3))
+    ng, nl = 256 // scale, 128 // scale
+    patches = [PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC)]
+    for pair, z in enumerate((plane_z, -plane_z)):
+        for member in range(2):
+            phase = pair_phase[pair] + member * np.pi
+            patches.append(PatchSpec(LOCAL, (nl, nl, nl), (-half_width,) * 3, (half_width,) * 3, BC_INTERPATCH,
+                                     CIRCULAR, (0.0, 0.0, z, radius, omega, phase)))
+    params = np.column_stack([amps, widths, centres]).ravel()
+    h_min = 2.0 * half_width / nl
+    return Workload(f"orbiting_gauss_{ng}+4x{nl}", patches, GAUSS_SUM, params, 8, interp_points, 0.005,
+                    0.25 * h_min, steps)
+
+
+def translating_plane(scale=1, steps=16, interp_points=6, velocity=(0.4, 0.3, 0.0), start=(-0.05, -0.02, 0.0)):
+    """Sec. 3.2-style convergence layout at reduced size: global cube [-1,1]^3
+    and a 2:1 local cube [-0.5,0.5]^3 translating with constant velocity,
+    evolving the two-wave superposition of Sec. 3.4.2 scaled to the box
+    (wavelengths L1 = L2 = 2, offset 3)."""
+    ng, nl = 32 * scale, 32 * scale
+    patches = [
+        PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC),
+        PatchSpec(LOCAL, (nl, nl, nl), (-0.5, -0.5, -0.5), (0.5, 0.5, 0.5), BC_INTERPATCH, LINEAR,
+                  tuple(start) + tuple(velocity)),
+    ]
+    k = 2.0 * np.pi / 2.0
+    params = np.array([3.0, 1.0, k, 0.0, 0.0, 0.0, 1.0, k, -k, k, 0.5 * np.pi])
+    h_min = 1.0 / nl
+    return Workload(f"translating_plane_{ng}+{nl}", patches, PLANE_SUM, params, 2, interp_points, 0.005,
+                    0.25 * h_min, steps * scale)
+
+
+def random_fields(shape, seed_index, scale=1.0):
+    """Two independent standard-normal arrays of the given shape."""
+    r = rng(100 + seed_index)
+    return scale * r.standard_normal(shape), scale * r.standard_normal(shape)
+
+
+def random_offsets(count, seed_index, low, high):
+    return rng(200 + seed_index).uniform(low, high, (count, 3))
