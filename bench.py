@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Throughput of the multipatch scalar-wave hot path on GB300.
+
+Metric: grid-point RK4 stage-updates/s = (live points summed over patches) x 4
+substages x steps / device time, ghost fills and cover flags included.
+Workload: global 256^3 on [-1,1]^3 plus four orbiting local 128^3 patches,
+eight Gaussian pulses, 6-point Lagrange, FP64 (paper_2002_00088_gb300.workloads
+.orbiting_gauss).  The state (~1.8 GB) is far larger than L2, so no flush is
+needed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With --gpus N > 1 (under torch.distributed.run) every rank advances an
+independent replica on its own GPU ("replicas only": the method needs no
+exchange between instances); value is the sum over ranks.  --impl reference
+times the plain FP64 CPU oracle on the host cores on a bounded sample of the
+same workload (the paper publishes no timings to compare with).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-point RK4 stage-updates/s"
+UNIT = "stage-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+# algorithmic bytes of one live point in one fused RHS+stage launch, averaged
+# over the four substages: S1 48 B, S2 80 B, S3 80 B, S4 48 B (FP64)
+BYTES_PER_POINT_STAGE = 64.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--scale", type=int, default=1, help="divide the workload resolution (testing only)")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-sample-scale", type=int, default=2)
+    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_info():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        try:
+            with open(path) as f:
+                d = json.load(f)
+            for k in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if k in d:
+                    return float(d[k]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        rows = []
+        with open(self.out.name) as f:
+            for ln in f:
+                parts = [p.strip() for p in ln.split(",")]
+                if len(parts) == 7:
+                    rows.append(parts)
+        os.unlink(self.out.name)
+        if not rows:
+            return None
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[3 + i].lower().startswith("active")})
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2002_00088_gb300", "csrc"))):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(ROOT, "paper_2002_00088_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per launch of the RHS kernel from the committed ncu summary,
+    if it was taken on the current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "rhs_stage_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        d = json.load(f)
+    if d.get("kernel_source_hash") != kernel_source_hash():
+        return None
+    return d.get("traffic_bytes_per_launch")
+
+
+def cpu_baseline(args, threads):
+    """The oracle as it stands, on the host cores, on a bounded sample."""
+    from oracle import pyoracle as po
+    from paper_2002_00088_gb300 import workloads as wl
+    w = wl.orbiting_gauss(scale=args.cpu_sample_scale)
+    o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
+    for p in w.patches:
+        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+    o.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
+    o.fill_analytic(0.0)
+    o.step(w.dt, 1)  # first step: flags from scratch, allocation warm-up
+    live = o.live_points()
+    t0 = time.perf_counter()
+    o.step(w.dt, args.cpu_sample_steps)
+    el = time.perf_counter() - t0
+    return {"value": live * 4 * args.cpu_sample_steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{args.cpu_sample_steps} step(s) of {w.name} (the workload at 1/{args.cpu_sample_scale} "
+                      f"resolution per axis), {live} live points, {el:.2f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_info()
+    if rank != 0:
+        return 0
+    from oracle import pyoracle as po
+    from paper_2002_00088_gb300 import workloads as wl
+    threads = os.cpu_count() or 1
+    full = wl.orbiting_gauss(scale=args.scale)
+    w = wl.orbiting_gauss(scale=max(args.scale, args.cpu_sample_scale))
+    o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
+    for p in w.patches:
+        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+    o.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
+    o.fill_analytic(0.0)
+    o.step(w.dt, args.warmup)
+    live = o.live_points()
+    t0 = time.perf_counter()
+    o.step(w.dt, args.steps)
+    el = time.perf_counter() - t0
+    value = live * 4 * args.steps / el
+    sample = (f"each step: one oracle step of {w.name} (the workload at 1/{max(args.scale, args.cpu_sample_scale)}"
+              f" resolution per axis), {live} live points")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded closed-form Gaussian pulses)",
+            "config": {"workload": full.name, "sample": w.name},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    rank, world, local = dist_info()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    from paper_2002_00088_gb300.build import build_library
+    build_library()
+    from paper_2002_00088_gb300 import mpw
+    from paper_2002_00088_gb300 import workloads as wl
+
+    w = wl.orbiting_gauss(scale=args.scale)
+    stream = torch.cuda.current_stream(local)
+    sim = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream)
+    for p in w.patches:
+        sim.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+    sim.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
+    sim.fill_analytic(0.0)  # inputs generated in HBM
+    sim.step(w.dt, args.warmup)
+    live = sim.live_points()
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    # ---- device-timed region: exactly K steps, inputs resident in HBM
+    sampler = ClockSampler(local)
+    sampler.start()
+    sim.profile(True)
+    sim.profile_read()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    start.record(stream)
+    sim.step(w.dt, args.steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = start.elapsed_time(end)
+    prof = sim.profile_read()
+    sim.profile(False)
+    clocks = sampler.stop()
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = live * 4 * args.steps * world / (ms * 1e-3)
+
+    # ---- end-to-end through the C ABI with host buffers: every step copies the
+    # state in from pinned host memory and the result back out
+    shapes = [(p.n[2], p.n[1], p.n[0]) for p in w.patches]
+    host = [(torch.empty(s, dtype=torch.float64, pin_memory=True).numpy(),
+             torch.empty(s, dtype=torch.float64, pin_memory=True).numpy()) for s in shapes]
+    for q in range(len(shapes)):
+        sim.get_fields(q)  # warm the staging path
+    hq = [sim.get_fields(q) for q in range(len(shapes))]
+    for q in range(len(shapes)):
+        host[q][0][...] = np.nan_to_num(hq[q][0])
+        host[q][1][...] = np.nan_to_num(hq[q][1])
+    bytes_in = sum(2 * 8 * int(np.prod(s)) for s in shapes)
+    barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        for q in range(len(shapes)):
+            sim.set_fields(q, host[q][0], host[q][1])
+        sim.step(w.dt, 1)
+        for q in range(len(shapes)):
+            mpw.check(mpw.lib.mpw_get_fields(sim.h, q, host[q][0].ctypes.data, host[q][1].ctypes.data, 0))
+    torch.cuda.synchronize()
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_value = live * 4 * args.e2e_steps * world / e2e_s
+
+    if rank != 0:
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return 0
+
+    rhs_ms, rhs_n = prof["rhs"]
+    fill_ms, fill_n = prof["fill"]
+    flags_ms, flags_n = prof["flags"]
+    rhs_avg_ms = rhs_ms / max(rhs_n, 1)
+    peak, peak_kind = measured_peaks()
+    achieved = live * BYTES_PER_POINT_STAGE / (rhs_avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded closed-form Gaussian pulses)",
+        "config": {"workload": w.name, "live_points": live, "interp_points": w.interp_points,
+                   "dt": w.dt, "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "state of %.2f GB, larger than L2; no flush" % (
+                       sum(8 * 8 * (p.n[0] + 6) * (p.n[1] + 6) * (p.n[2] + 6) for p in w.patches) / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "rhs_stage (fused RHS + RK4 stage)", "achieved": achieved,
+                     "peak": peak, "peak_source": f"{peak_kind} HBM GB/s", "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": traffic,
+                     "avg_launch_ms": rhs_avg_ms,
+                     "algorithmic_bytes_per_launch": live * BYTES_PER_POINT_STAGE},
+        "kernel_time_share": {"rhs_stage": rhs_ms / ms, "ghost_fill": fill_ms / ms, "cover_flags": flags_ms / ms},
+        "gpu_launches": int(rhs_n + fill_n + flags_n),
+        "clocks": clocks,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_in,
+                "steps": args.e2e_steps},
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(args, os.cpu_count() or 1)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,186 @@
+/*
+ * mpw.h -- C ABI of libmpw, a single-GPU (sm_103a) implementation of the
+ * data-parallel hot path of the multipatch scalar-wave method of
+ * "PatchworkWave" (arXiv:2002.00088): 4th-order method-of-lines evolution of
+ * the fields psi and Pi = d(psi)/dt on one global patch plus moving local
+ * patches, with ghost zones refilled at every RK4 substage by tensor-product
+ * Lagrange interpolation through the time-dependent patch maps and a buffer of
+ * live global cells under each local patch edge (one-way data flow).
+ *
+ * Conventions shared by every entry point
+ *  - Every call returns mpw_status; MPW_OK is 0.  On error a message is kept
+ *    per thread and returned by mpw_last_error().
+ *  - Floating point is IEEE binary64 throughout (psi, Pi, time, maps).
+ *  - Field arrays exchanged with the library are dense interior boxes
+ *    [k][j][i], i fastest, n[0]*n[1]*n[2] doubles.  A pointer flagged
+ *    on_device = 1 is a CUDA device pointer on the context's device; 0 means
+ *    host memory (pinned or pageable).  The library never keeps or frees a
+ *    caller pointer.
+ *  - Patch geometry: patch j has numeric coordinates X'_j; the live box is
+ *    [lo, hi] per axis holding n cells of width h = (hi - lo)/n, nodes
+ *    cell-centred at lo + (i + 1/2) h.  The background Cartesian frame of
+ *    Sec. 2.4.1 is X_B = X'_j + X0_j(t) (rigid translation; the global patch,
+ *    id 0, is the background frame itself).  Every patch carries NG = 3
+ *    ghost cells per side.
+ *  - All work is enqueued on the stream given in mpw_config (NULL = the legacy
+ *    default stream).  mpw_step(), mpw_get_fields() and mpw_get_flags()
+ *    synchronise that stream before returning.
+ */
+#ifndef MPW_H
+#define MPW_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mpw_ctx mpw_ctx;
+
+typedef enum {
+  MPW_OK = 0,
+  MPW_ERR_ARG = 1,            /* invalid argument or configuration */
+  MPW_ERR_OVERLAP = 2,        /* local patches closer than the separation rule */
+  MPW_ERR_CFL = 3,            /* dt beyond the RK4 stability estimate */
+  MPW_ERR_TRAVERSAL = 4,      /* a patch would cross more than one global cell in a step */
+  MPW_ERR_OUTSIDE = 5,        /* a local patch (with ghosts and stencils) leaves the global interior */
+  MPW_ERR_GHOST_UNFILLED = 6, /* a ghost point could not be interpolated (Sec. 2.4.1 "skip") */
+  MPW_ERR_BOUNDS = 7,         /* a device-side index check failed */
+  MPW_ERR_TIMEOUT = 8,        /* reserved for bounded device waits */
+  MPW_ERR_CUDA = 9,           /* a CUDA runtime call failed */
+  MPW_ERR_STATE = 10          /* call not valid in the current state */
+} mpw_status;
+
+enum { MPW_PATCH_GLOBAL = 0, MPW_PATCH_LOCAL = 1 };
+enum { MPW_BC_ANALYTIC = 0, MPW_BC_PERIODIC = 1, MPW_BC_INTERPATCH = 2 };
+enum { MPW_MOTION_STATIC = 0, MPW_MOTION_LINEAR = 1, MPW_MOTION_CIRCULAR = 2 };
+enum { MPW_ANALYTIC_GAUSS_SUM = 0, MPW_ANALYTIC_PLANE_SUM = 1, MPW_ANALYTIC_HARMONIC_POLY = 2 };
+/* Cover-flag byte of a global interior cell: state | (owning local patch id << 2). */
+enum { MPW_FLAG_LIVE = 0, MPW_FLAG_GHOST = 1, MPW_FLAG_DEAD = 2, MPW_FLAG_REVIVED = 3 };
+
+/* Device allocator hook.  alloc returns device memory of at least `bytes`
+ * bytes (256-byte aligned) or NULL; free releases it.  NULL hooks mean
+ * cudaMalloc / cudaFree. */
+typedef void* (*mpw_alloc_fn)(size_t bytes, void* user);
+typedef void (*mpw_free_fn)(void* ptr, void* user);
+
+typedef struct {
+  int precision;      /* 64 (IEEE binary64); no other value is accepted */
+  int ghost;          /* NG, must be 3 (the reach of the KO stencil, Sec. 2.4.2) */
+  int interp_points;  /* Lagrange window P: 6 (the paper's i_c-2..i_c+3) or 5 (i_c-2..i_c+2) */
+  double ko_eps;      /* Kreiss-Oliger strength epsilon (Sec. 2.3; the paper uses 0.005) */
+  int buffer;         /* live global cells under a local edge; 0 selects NG+1 (Sec. 2.4.2) */
+  int device;         /* CUDA device ordinal */
+  void* stream;       /* cudaStream_t to enqueue on, or NULL */
+  mpw_alloc_fn alloc; /* optional device allocator hook */
+  mpw_free_fn free;
+  void* alloc_user;
+  int arith;          /* stencil arithmetic: 0 = library default, 1 = native FP64 */
+} mpw_config;
+
+typedef struct {
+  int kind;                 /* MPW_PATCH_GLOBAL (must be created first, id 0) or MPW_PATCH_LOCAL */
+  int n[3];                 /* interior cells per axis, >= 6 */
+  double lo[3], hi[3];      /* live box in the patch's numeric coordinates */
+  int outer_bc;             /* global: ANALYTIC or PERIODIC; local: INTERPATCH */
+  int motion;               /* MPW_MOTION_*; the global patch must be STATIC at the origin
+                               when local patches exist */
+  double motion_params[16]; /* STATIC   : X0 = (p0,p1,p2)
+                               LINEAR   : X0 = (p0,p1,p2) + t (p3,p4,p5)
+                               CIRCULAR : X0 = (p0,p1,p2) + p3 (cos(p4 t + p5), sin(p4 t + p5), 0) */
+} mpw_patch_desc;
+
+/* Create a context on cfg->device.  cfg is copied.  Errors: MPW_ERR_ARG for
+ * unsupported precision/ghost/interp_points, MPW_ERR_CUDA. */
+mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out);
+
+/* Add a patch (Sec. 2.4.1: one global patch id 0, local patches 1..N-1) and
+ * allocate its device storage (4 padded state buffers x 2 fields).  Returns
+ * its id in *patch_id.  Errors: MPW_ERR_ARG, MPW_ERR_STATE (global patch not
+ * first / already stepped), MPW_ERR_CUDA (allocation). */
+mpw_status mpw_create_patch(mpw_ctx* ctx, const mpw_patch_desc* desc, int* patch_id);
+
+/* Closed-form solution used by the analytic outer BC and mpw_fill_analytic
+ * (Sec. 3: analytic BCs at the physical edges of the global domain).
+ *   GAUSS_SUM     count pulses, params 5 per pulse (A, width, cx, cy, cz):
+ *                 psi = sum [g(t+r) - g(t-r)]/(2r), g(s) = A s exp(-s^2/width^2)
+ *   PLANE_SUM     params (C, then 5 per wave: A, kx, ky, kz, phase):
+ *                 psi = C + sum A sin(k.x - |k| t + phase)   (Sec. 3, Eq. wave_solution)
+ *   HARMONIC_POLY count <= 14 coefficients of the static harmonic basis
+ *                 1, x, y, z, xy, yz, zx, x^2-y^2, y^2-z^2, xyz, x^3-3xy^2,
+ *                 y^3-3yz^2, z^3-3zx^2, x^4-6x^2y^2+y^4 (Pi = 0).
+ * params is host memory and is copied.  Errors: MPW_ERR_ARG. */
+mpw_status mpw_set_analytic(mpw_ctx* ctx, int kind, const double* params, int count);
+
+/* Set every patch's interior to the closed form at time t and the context time
+ * to t.  Errors: MPW_ERR_STATE (no analytic function), MPW_ERR_CUDA. */
+mpw_status mpw_fill_analytic(mpw_ctx* ctx, double t);
+
+/* Copy the interior of both fields of `patch` in (psi, Pi dense [k][j][i]).
+ * The cover flags are left as they are (a restart restores them with
+ * mpw_set_flags). */
+mpw_status mpw_set_fields(mpw_ctx* ctx, int patch, const double* psi, const double* pi, int on_device);
+
+/* Copy the interior of both fields out.  Global cells that are not live
+ * (effective ghost or deactivated, Sec. 2.4.2) read as NaN. */
+mpw_status mpw_get_fields(mpw_ctx* ctx, int patch, double* psi, double* pi, int on_device);
+
+/* Copy the whole padded box of the state u (ghost zones included) out, dense
+ * [k][j][i] over (n+6)^3, index (i+3) + (n0+6)((j+3) + (n1+6)(k+3)).  Ghost
+ * values are those of the last boundary fill of substage 1 (or of
+ * mpw_fill_ghosts).  For tests of the ghost-zone fill.  Host or device. */
+mpw_status mpw_get_padded(mpw_ctx* ctx, int patch, double* psi, double* pi, int on_device);
+
+/* Time of the state. */
+mpw_status mpw_set_time(mpw_ctx* ctx, double t);
+double mpw_time(const mpw_ctx* ctx);
+
+/* Recompute the cover flags at the current time (Sec. 2.4.2), poisoning
+ * deactivated cells with NaN and reviving cells that became live. */
+mpw_status mpw_compute_flags(mpw_ctx* ctx);
+
+/* Read / restore the global cover flags (n0*n1*n2 bytes, host memory).  A
+ * checkpoint is fields + flags + time. */
+mpw_status mpw_get_flags(mpw_ctx* ctx, uint8_t* flags);
+mpw_status mpw_set_flags(mpw_ctx* ctx, const uint8_t* flags);
+
+/* Fill every ghost zone of the state u at time t (maps at t): physical BC,
+ * Local-to-Global, Global-to-Local (Sec. 2.4).  Flags are computed first if
+ * invalid. */
+mpw_status mpw_fill_ghosts(mpw_ctx* ctx, double t);
+
+/* Advance nsteps RK4 steps of size dt (Sec. 2.3, Table 1).  Validates CFL,
+ * traversal, separation and containment before launching; reads the device
+ * error word once at the end.  On a device-side error the call returns
+ * MPW_ERR_GHOST_UNFILLED or MPW_ERR_BOUNDS. */
+mpw_status mpw_step(mpw_ctx* ctx, double dt, int nsteps);
+
+/* Number of live points summed over patches (the unit of the throughput
+ * metric: one live point advanced through one RK4 substage). */
+mpw_status mpw_live_points(mpw_ctx* ctx, long long* count);
+
+/* Kernel families reported by mpw_profile_read. */
+enum { MPW_KERNEL_RHS = 0, MPW_KERNEL_FILL = 1, MPW_KERNEL_FLAGS = 2, MPW_KERNEL_FAMILIES = 3 };
+
+/* Measurement support (no counterpart in the paper, which reports no
+ * timings).  While enabled (enable = 1) every kernel launch of the context is
+ * bracketed by a pair of CUDA events on the context's stream.  Launch counts
+ * are kept whether or not timing is enabled. */
+mpw_status mpw_profile_enable(mpw_ctx* ctx, int enable);
+
+/* Synchronise the stream, write for families 0..n-1 the device milliseconds
+ * accumulated by timed launches (ms, may be NULL) and the number of launches
+ * (launches, may be NULL) since the last read, then reset both. */
+mpw_status mpw_profile_read(mpw_ctx* ctx, double* ms, long long* launches, int n);
+
+/* Thread-local message of the last failing call on this thread. */
+const char* mpw_last_error(void);
+
+/* Free all device storage of the context. */
+void mpw_destroy(mpw_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,748 @@
+// mpw_api.cu -- host side of libmpw: the C ABI of include/mpw.h, patch
+// storage, motion laws, validation and the per-step launch schedule.
+//
+// Per step (Sec. 2.3-2.4): cover flags from the maps at t_n (recomputed every
+// step while any local patch moves, once for static layouts), then for each
+// RK4 substage l = 1..4 at t_l = t_n + c_l dt one ghost-fill launch (outer
+// BC, Local-to-Global, Global-to-Local with the maps at t_l) and one fused
+// RHS + stage launch covering every patch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/mpw.h"
+#include "mpw_internal.cuh"
+
+using namespace mpw;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+mpw_status set_err(mpw_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CUDA_TRY(call)                                                                              \
+  do {                                                                                              \
+    cudaError_t e_ = (call);                                                                        \
+    if (e_ != cudaSuccess) return set_err(MPW_ERR_CUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+// Classic RK4 (Table 1): c_l.
+const double RK_C[4] = {0.0, 0.5, 0.5, 1.0};
+
+struct PatchState {
+  mpw_patch_desc d;
+  Geom g;
+  double* base = nullptr;  // 4 buffers x 2 fields x vol doubles
+  double* buf(int b) const { return base + (size_t)b * 2 * (size_t)g.vol; }
+};
+
+}  // namespace
+
+struct mpw_ctx {
+  mpw_config cfg{};
+  cudaStream_t stream = nullptr;
+  int P = 6, buffer = NG + 1;
+  std::vector<PatchState> p;
+  int akind = -1, acount = 0;
+  std::vector<double> aparams;
+  double* d_aparams = nullptr;
+  uint8_t* d_flags = nullptr;
+  bool flags_valid = false;
+  std::vector<Box> boxes;  // covered boxes at the last flag computation
+  int* d_err = nullptr;
+  int* h_err = nullptr;
+  double* d_stage = nullptr;
+  size_t stage_bytes = 0;
+  double t = 0.0;
+  bool stepped = false;
+  // measurement: per kernel family, a pool of event pairs and a launch count
+  bool prof = false;
+  std::vector<cudaEvent_t> ev[MPW_KERNEL_FAMILIES];
+  size_t ev_used[MPW_KERNEL_FAMILIES] = {0, 0, 0};
+  long long launches[MPW_KERNEL_FAMILIES] = {0, 0, 0};
+
+  // Record the start event of a launch of family f (when timing is on).
+  void launch_begin(int f) {
+    ++launches[f];
+    if (!prof) return;
+    if (ev[f].size() < 2 * (ev_used[f] + 1)) {
+      cudaEvent_t a, b;
+      cudaEventCreate(&a);
+      cudaEventCreate(&b);
+      ev[f].push_back(a);
+      ev[f].push_back(b);
+    }
+    cudaEventRecord(ev[f][2 * ev_used[f]], stream);
+  }
+  void launch_end(int f) {
+    if (!prof) return;
+    cudaEventRecord(ev[f][2 * ev_used[f] + 1], stream);
+    ++ev_used[f];
+  }
+
+  void* dalloc(size_t bytes) {
+    if (cfg.alloc) return cfg.alloc(bytes, cfg.alloc_user);
+    void* ptr = nullptr;
+    return cudaMalloc(&ptr, bytes) == cudaSuccess ? ptr : nullptr;
+  }
+  void dfree(void* ptr) {
+    if (!ptr) return;
+    if (cfg.free)
+      cfg.free(ptr, cfg.alloc_user);
+    else
+      cudaFree(ptr);
+  }
+};
+
+namespace {
+
+// Rigid translation of a patch: X_B = X' + X0(t); w = dX0/dt.  The rounding
+// order is fixed (no contraction) because the cover flags depend on it.
+void motion(const mpw_patch_desc& d, double t, double X0[3], double w[3]) {
+  const double* mp = d.motion_params;
+  if (d.motion == MPW_MOTION_LINEAR) {
+    for (int a = 0; a < 3; ++a) {
+      X0[a] = mp[a] + t * mp[3 + a];
+      w[a] = mp[3 + a];
+    }
+  } else if (d.motion == MPW_MOTION_CIRCULAR) {
+    const double ph = mp[4] * t + mp[5];
+    const double c = std::cos(ph), s = std::sin(ph);
+    X0[0] = mp[0] + mp[3] * c;
+    X0[1] = mp[1] + mp[3] * s;
+    X0[2] = mp[2];
+    w[0] = -(mp[3] * mp[4]) * s;
+    w[1] = (mp[3] * mp[4]) * c;
+    w[2] = 0.0;
+  } else {
+    for (int a = 0; a < 3; ++a) {
+      X0[a] = mp[a];
+      w[a] = 0.0;
+    }
+  }
+}
+
+// Largest |w_a| the motion law can reach.
+void max_speed(const mpw_patch_desc& d, double v[3]) {
+  const double* mp = d.motion_params;
+  for (int a = 0; a < 3; ++a) v[a] = 0.0;
+  if (d.motion == MPW_MOTION_LINEAR)
+    for (int a = 0; a < 3; ++a) v[a] = std::fabs(mp[3 + a]);
+  if (d.motion == MPW_MOTION_CIRCULAR) v[0] = v[1] = std::fabs(mp[3] * mp[4]);
+}
+
+bool is_moving(const mpw_patch_desc& d) {
+  double v[3];
+  max_speed(d, v);
+  return v[0] != 0.0 || v[1] != 0.0 || v[2] != 0.0;
+}
+
+Geom make_geom(const mpw_patch_desc& d) {
+  Geom g{};
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = d.n[a];
+    g.lo[a] = d.lo[a];
+    g.h[a] = (d.hi[a] - d.lo[a]) / d.n[a];
+  }
+  g.px = ((d.n[0] + XOFF + NG + 1) + 15) / 16 * 16;
+  g.py = d.n[1] + 2 * NG;
+  g.plane = (long long)g.px * g.py;
+  g.vol = g.plane * (d.n[2] + 2 * NG);
+  return g;
+}
+
+// Covered box of local patch l on the global grid at time t (Sec. 2.4.2,
+// "Find Covered Zones"): global cell centres inside the closed live box of l,
+// tested in l's numeric coordinates.  Under translation the covered set is a
+// product of one index interval per axis.
+Box covered_box(const PatchState& g, const PatchState& l, double t) {
+  double X0[3], w[3];
+  motion(l.d, t, X0, w);
+  Box b;
+  for (int a = 0; a < 3; ++a) {
+    b.lo[a] = 1 << 30;
+    b.hi[a] = -1;
+    const double h = (g.d.hi[a] - g.d.lo[a]) / g.d.n[a];
+    for (int i = 0; i < g.d.n[a]; ++i) {
+      const double x = g.d.lo[a] + (i + 0.5) * h;
+      const double xl = x - X0[a];
+      if (l.d.lo[a] <= xl && xl <= l.d.hi[a]) {
+        b.lo[a] = std::min(b.lo[a], i);
+        b.hi[a] = std::max(b.hi[a], i);
+      }
+    }
+  }
+  return b;
+}
+
+bool box_empty(const Box& b) { return b.lo[0] > b.hi[0] || b.lo[1] > b.hi[1] || b.lo[2] > b.hi[2]; }
+
+mpw_status check_ctx(const mpw_ctx* c) {
+  if (!c) return set_err(MPW_ERR_ARG, "null context");
+  return MPW_OK;
+}
+
+mpw_status use_device(mpw_ctx* c) {
+  CUDA_TRY(cudaSetDevice(c->cfg.device));
+  return MPW_OK;
+}
+
+mpw_status ensure_stage(mpw_ctx* c, size_t bytes) {
+  if (c->stage_bytes >= bytes) return MPW_OK;
+  c->dfree(c->d_stage);
+  c->d_stage = (double*)c->dalloc(bytes);
+  c->stage_bytes = c->d_stage ? bytes : 0;
+  if (!c->d_stage) return set_err(MPW_ERR_CUDA, "staging allocation of %zu bytes failed", bytes);
+  return MPW_OK;
+}
+
+// Validation of a step of size dt from time t (the checks the paper leaves to
+// the user, Sec. 2.4.2, plus the RK4 stability estimate).
+mpw_status validate_step(mpw_ctx* c, double dt, double t) {
+  if (!(dt > 0.0) || !std::isfinite(dt)) return set_err(MPW_ERR_ARG, "dt must be positive and finite");
+  const PatchState& g = c->p[0];
+  const double h0 = std::min(g.g.h[0], std::min(g.g.h[1], g.g.h[2]));
+  for (size_t q = 0; q < c->p.size(); ++q) {
+    const PatchState& P = c->p[q];
+    double v[3];
+    max_speed(P.d, v);
+    // RK4 stays stable on the imaginary axis up to 2 sqrt(2); the 4th-order
+    // Laplacian reaches 16/(3 h^2) per axis, the 4th-order first derivative
+    // 1.372/h.
+    double lap = 0.0, adv = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      lap += 16.0 / (3.0 * P.g.h[a] * P.g.h[a]);
+      adv += 1.372 * v[a] / P.g.h[a];
+    }
+    if (dt * (std::sqrt(lap) + adv) > 2.8)
+      return set_err(MPW_ERR_CFL, "patch %zu: dt = %g exceeds the RK4 stability estimate", q, dt);
+    if (q == 0) continue;
+    // the buffer of B live cells lets a patch cross B - NG global cells per step
+    for (int a = 0; a < 3; ++a)
+      if (v[a] * dt > (c->buffer - NG) * g.g.h[a])
+        return set_err(MPW_ERR_TRAVERSAL, "patch %zu crosses more than %d global cell(s) per step", q,
+                       c->buffer - NG);
+  }
+  const double ts[3] = {t, t + 0.5 * dt, t + dt};
+  for (double tt : ts) {
+    for (size_t q = 1; q < c->p.size(); ++q) {
+      const PatchState& P = c->p[q];
+      double X0[3], w[3];
+      motion(P.d, tt, X0, w);
+      for (int a = 0; a < 3; ++a) {
+        const double margin = NG * P.g.h[a] + (NG + 2) * g.g.h[a];
+        if (P.d.lo[a] + X0[a] - margin < g.d.lo[a] || P.d.hi[a] + X0[a] + margin > g.d.hi[a])
+          return set_err(MPW_ERR_OUTSIDE, "patch %zu leaves the global interior at t = %g", q, tt);
+      }
+      for (size_t r = q + 1; r < c->p.size(); ++r) {
+        const PatchState& R = c->p[r];
+        double Y0[3], w2[3];
+        motion(R.d, tt, Y0, w2);
+        double gap = -1e300;
+        for (int a = 0; a < 3; ++a) {
+          const double g1 = (R.d.lo[a] + Y0[a]) - (P.d.hi[a] + X0[a]);
+          const double g2 = (P.d.lo[a] + X0[a]) - (R.d.hi[a] + Y0[a]);
+          gap = std::max(gap, std::max(g1, g2));
+        }
+        if (gap < 2.0 * h0)
+          return set_err(MPW_ERR_OVERLAP, "patches %zu and %zu are closer than 2 global cells at t = %g", q, r, tt);
+      }
+    }
+  }
+  return MPW_OK;
+}
+
+// Cover flags at time t; revival uses the previous flags when valid.
+mpw_status run_flags(mpw_ctx* c, double t) {
+  const PatchState& g = c->p[0];
+  FlagArgs a{};
+  a.flags = c->d_flags;
+  for (int k = 0; k < 3; ++k) a.n[k] = g.d.n[k];
+  a.nloc = (int)c->p.size() - 1;
+  c->boxes.assign(a.nloc, Box{});
+  for (int q = 0; q < a.nloc; ++q) {
+    const PatchState& L = c->p[q + 1];
+    c->boxes[q] = covered_box(g, L, t);
+    a.box[q] = c->boxes[q];
+    a.Uloc[q] = L.buf(BUF_U);
+    a.gl[q] = L.g;
+    double w[3];
+    motion(L.d, t, a.X0[q], w);
+  }
+  a.buffer = c->buffer;
+  a.old_valid = c->flags_valid ? 1 : 0;
+  a.Ug = g.buf(BUF_U);
+  a.gg = g.g;
+  a.P = c->P;
+  a.err = c->d_err;
+  c->launch_begin(MPW_KERNEL_FLAGS);
+  launch_flags(a, c->stream);
+  c->launch_end(MPW_KERNEL_FLAGS);
+  CUDA_TRY(cudaGetLastError());
+  c->flags_valid = true;
+  return MPW_OK;
+}
+
+// Ghost fill of the stage buffer `b` at time t.
+mpw_status run_fill(mpw_ctx* c, int b, double t) {
+  const PatchState& g = c->p[0];
+  FillArgs a{};
+  a.Yg = g.buf(b);
+  a.gg = g.g;
+  a.outer_bc = g.d.outer_bc == MPW_BC_PERIODIC ? 1 : 0;
+  if (a.outer_bc == 0 && c->akind < 0) return set_err(MPW_ERR_STATE, "analytic outer BC without mpw_set_analytic");
+  a.akind = c->akind;
+  a.acount = c->acount;
+  a.aparams = c->d_aparams;
+  a.t = t;
+  a.outer_count = (long long)(g.d.n[0] + 2 * NG) * (g.d.n[1] + 2 * NG) * (g.d.n[2] + 2 * NG) -
+                  (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
+  a.nloc = (int)c->p.size() - 1;
+  long long pos = a.outer_count;
+  for (int q = 0; q < a.nloc; ++q) {
+    FillLocal& L = a.loc[q];
+    const Box& bx = c->boxes[q];
+    L.l2g_begin = pos;
+    L.l2g_count = 0;
+    if (!box_empty(bx)) {
+      long long outer = 1, inner = 1;
+      bool any = true;
+      for (int k = 0; k < 3; ++k) {
+        L.shell_lo[k] = bx.lo[k] + c->buffer;
+        L.shell_dim[k] = bx.hi[k] - bx.lo[k] + 1 - 2 * c->buffer;
+        if (L.shell_dim[k] <= 0) any = false;
+        outer *= std::max(L.shell_dim[k], 0);
+        inner *= std::max(L.shell_dim[k] - 2 * NG, 0);
+      }
+      if (any) L.l2g_count = outer - inner;
+    }
+    pos += L.l2g_count;
+  }
+  for (int q = 0; q < a.nloc; ++q) {
+    FillLocal& L = a.loc[q];
+    const PatchState& P = c->p[q + 1];
+    L.Y = P.buf(b);
+    L.g = P.g;
+    double w[3];
+    motion(P.d, t, L.X0, w);
+    L.g2l_begin = pos;
+    L.g2l_count = (long long)(P.d.n[0] + 2 * NG) * (P.d.n[1] + 2 * NG) * (P.d.n[2] + 2 * NG) -
+                  (long long)P.d.n[0] * P.d.n[1] * P.d.n[2];
+    pos += L.g2l_count;
+  }
+  a.total = pos;
+  a.flags = c->d_flags;
+  a.P = c->P;
+  a.buffer = c->buffer;
+  a.err = c->d_err;
+  if (a.total <= 0) return MPW_OK;
+  c->launch_begin(MPW_KERNEL_FILL);
+  launch_fill(a, c->stream);
+  c->launch_end(MPW_KERNEL_FILL);
+  CUDA_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+// One fused RHS + RK4 stage launch over every patch (substage l at t).
+mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
+  static const int in_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
+  static const int out_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
+  RhsArgs a{};
+  a.np = (int)c->p.size();
+  a.stage = l;
+  // OUT = U + alpha K (l < 3) or ACC + alpha K (l = 3); ACC = base + beta K
+  const double alpha[4] = {0.5 * dt, 0.5 * dt, dt, dt / 6.0};
+  const double beta[4] = {dt / 6.0, dt / 3.0, dt / 3.0, 0.0};
+  a.alpha = alpha[l];
+  a.beta = beta[l];
+  a.flags = c->d_flags;
+  a.nbox = (int)c->boxes.size();
+  for (int q = 0; q < a.nbox; ++q) a.box[q] = c->boxes[q];
+  int blocks = 0;
+  for (int q = 0; q < a.np; ++q) {
+    const PatchState& P = c->p[q];
+    RhsPatch& R = a.p[q];
+    R.Y = P.buf(in_buf[l]);
+    R.U = P.buf(BUF_U);
+    R.ACC = P.buf(BUF_ACC);
+    R.OUT = P.buf(out_buf[l]);
+    R.g = P.g;
+    double X0[3], w[3];
+    motion(P.d, t, X0, w);
+    R.moving = 0;
+    for (int k = 0; k < 3; ++k) {
+      const double h = P.g.h[k];
+      R.c1[k] = w[k] / (12.0 * h);
+      R.c2[k] = 1.0 / (12.0 * h * h);
+      R.cko[k] = c->cfg.ko_eps / (64.0 * h);
+      if (w[k] != 0.0) R.moving = 1;
+    }
+    R.is_global = q == 0 && c->flags_valid && !c->boxes.empty();
+    R.tiles_x = (P.d.n[0] + RHS_TX - 1) / RHS_TX;
+    R.tiles_y = (P.d.n[1] + RHS_TY - 1) / RHS_TY;
+    R.zc = P.d.n[2] >= 128 ? 32 : 8;
+    R.zchunks = (P.d.n[2] + R.zc - 1) / R.zc;
+    R.block0 = blocks;
+    blocks += R.tiles_x * R.tiles_y * R.zchunks;
+  }
+  c->launch_begin(MPW_KERNEL_RHS);
+  launch_rhs_fp64(a, blocks, c->stream);
+  c->launch_end(MPW_KERNEL_RHS);
+  CUDA_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+mpw_status read_error_word(mpw_ctx* c) {
+  CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  const int e = *c->h_err;
+  if (e) {
+    CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    if (e & ERR_UNFILLED) return set_err(MPW_ERR_GHOST_UNFILLED, "a ghost point could not be interpolated");
+    return set_err(MPW_ERR_BOUNDS, "device index check failed (error word 0x%x)", e);
+  }
+  return MPW_OK;
+}
+
+}  // namespace
+
+// ============================================================================ C ABI
+
+extern "C" {
+
+const char* mpw_last_error(void) { return g_last_error.c_str(); }
+
+mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out) {
+  if (!cfg || !out) return set_err(MPW_ERR_ARG, "null argument");
+  *out = nullptr;
+  if (cfg->precision != 64) return set_err(MPW_ERR_ARG, "precision must be 64");
+  if (cfg->ghost != NG) return set_err(MPW_ERR_ARG, "ghost must be %d", NG);
+  if (cfg->interp_points != 5 && cfg->interp_points != 6) return set_err(MPW_ERR_ARG, "interp_points must be 5 or 6");
+  if (!(cfg->ko_eps >= 0.0)) return set_err(MPW_ERR_ARG, "ko_eps must be >= 0");
+  const int buffer = cfg->buffer > 0 ? cfg->buffer : NG + 1;
+  if (buffer < NG + 1) return set_err(MPW_ERR_ARG, "buffer must be at least NG + 1 = %d", NG + 1);
+  if ((cfg->alloc == nullptr) != (cfg->free == nullptr)) return set_err(MPW_ERR_ARG, "alloc and free go together");
+  mpw_ctx* c = new mpw_ctx();
+  c->cfg = *cfg;
+  c->P = cfg->interp_points;
+  c->buffer = buffer;
+  c->stream = (cudaStream_t)cfg->stream;
+  mpw_status st = use_device(c);
+  if (st != MPW_OK) {
+    delete c;
+    return st;
+  }
+  c->d_err = (int*)c->dalloc(256);
+  c->d_aparams = (double*)c->dalloc(sizeof(double) * MAX_APARAMS);
+  if (!c->d_err || !c->d_aparams || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+    mpw_destroy(c);
+    return set_err(MPW_ERR_CUDA, "context allocation failed");
+  }
+  if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess) {
+    mpw_destroy(c);
+    return set_err(MPW_ERR_CUDA, "memset failed");
+  }
+  *out = c;
+  return MPW_OK;
+}
+
+void mpw_destroy(mpw_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  cudaStreamSynchronize(c->stream);
+  for (auto& P : c->p) c->dfree(P.base);
+  c->dfree(c->d_flags);
+  c->dfree(c->d_err);
+  c->dfree(c->d_aparams);
+  c->dfree(c->d_stage);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  for (auto& v : c->ev)
+    for (cudaEvent_t e : v) cudaEventDestroy(e);
+  delete c;
+}
+
+mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (!d || !patch_id) return set_err(MPW_ERR_ARG, "null argument");
+  if (c->stepped) return set_err(MPW_ERR_STATE, "patches must be created before the first step");
+  if ((c->p.empty()) != (d->kind == MPW_PATCH_GLOBAL))
+    return set_err(MPW_ERR_STATE, "the global patch must be created first, and only once");
+  if ((int)c->p.size() >= MAX_PATCHES) return set_err(MPW_ERR_ARG, "at most %d patches", MAX_PATCHES);
+  for (int a = 0; a < 3; ++a) {
+    if (d->n[a] < 2 * NG) return set_err(MPW_ERR_ARG, "n[%d] must be >= %d", a, 2 * NG);
+    if (!(d->hi[a] > d->lo[a])) return set_err(MPW_ERR_ARG, "hi must exceed lo");
+  }
+  if (d->motion < MPW_MOTION_STATIC || d->motion > MPW_MOTION_CIRCULAR) return set_err(MPW_ERR_ARG, "bad motion law");
+  if (d->kind == MPW_PATCH_GLOBAL) {
+    if (d->outer_bc != MPW_BC_ANALYTIC && d->outer_bc != MPW_BC_PERIODIC)
+      return set_err(MPW_ERR_ARG, "global outer_bc must be ANALYTIC or PERIODIC");
+  } else {
+    if (d->outer_bc != MPW_BC_INTERPATCH) return set_err(MPW_ERR_ARG, "local outer_bc must be INTERPATCH");
+    const mpw_patch_desc& g = c->p[0].d;
+    if (g.motion != MPW_MOTION_STATIC || g.motion_params[0] != 0.0 || g.motion_params[1] != 0.0 ||
+        g.motion_params[2] != 0.0)
+      return set_err(MPW_ERR_ARG, "with local patches the global patch must be static at the origin");
+    const Geom gg = make_geom(g);
+    for (int a = 0; a < 3; ++a)
+      if ((d->hi[a] - d->lo[a]) / d->n[a] > gg.h[a] * (1.0 + 1e-12))
+        return set_err(MPW_ERR_ARG, "a local patch must not be coarser than the global patch");
+  }
+  if (use_device(c)) return MPW_ERR_CUDA;
+  PatchState P;
+  P.d = *d;
+  P.g = make_geom(*d);
+  const size_t bytes = sizeof(double) * 8 * (size_t)P.g.vol;
+  P.base = (double*)c->dalloc(bytes);
+  if (!P.base) return set_err(MPW_ERR_CUDA, "allocation of %zu bytes failed", bytes);
+  CUDA_TRY(cudaMemsetAsync(P.base, 0, bytes, c->stream));
+  if (d->kind == MPW_PATCH_GLOBAL) {
+    const size_t nb = (size_t)d->n[0] * d->n[1] * d->n[2];
+    c->d_flags = (uint8_t*)c->dalloc(nb);
+    if (!c->d_flags) return set_err(MPW_ERR_CUDA, "flag allocation failed");
+    CUDA_TRY(cudaMemsetAsync(c->d_flags, 0, nb, c->stream));
+  }
+  c->p.push_back(P);
+  c->flags_valid = false;
+  *patch_id = (int)c->p.size() - 1;
+  return MPW_OK;
+}
+
+mpw_status mpw_set_analytic(mpw_ctx* c, int kind, const double* params, int count) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  int need = 0;
+  if (kind == MPW_ANALYTIC_GAUSS_SUM)
+    need = 5 * count;
+  else if (kind == MPW_ANALYTIC_PLANE_SUM)
+    need = 1 + 5 * count;
+  else if (kind == MPW_ANALYTIC_HARMONIC_POLY)
+    need = count;
+  else
+    return set_err(MPW_ERR_ARG, "unknown analytic kind %d", kind);
+  if (count < 0 || need > MAX_APARAMS || (kind == MPW_ANALYTIC_HARMONIC_POLY && count > 14) || (need && !params))
+    return set_err(MPW_ERR_ARG, "bad analytic parameter count");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  c->akind = kind;
+  c->acount = count;
+  c->aparams.assign(params, params + need);
+  if (need) CUDA_TRY(cudaMemcpyAsync(c->d_aparams, c->aparams.data(), sizeof(double) * need, cudaMemcpyHostToDevice,
+                                     c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MPW_OK;
+}
+
+mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (c->akind < 0) return set_err(MPW_ERR_STATE, "no analytic function set");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  for (auto& P : c->p) {
+    double X0[3], w[3];
+    motion(P.d, t, X0, w);
+    launch_analytic(P.buf(BUF_U), P.g, X0[0], X0[1], X0[2], c->akind, c->acount, c->d_aparams, t, c->stream);
+    CUDA_TRY(cudaGetLastError());
+  }
+  c->t = t;
+  return MPW_OK;
+}
+
+static mpw_status get_patch(mpw_ctx* c, int patch, PatchState** out) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (patch < 0 || patch >= (int)c->p.size()) return set_err(MPW_ERR_ARG, "bad patch id %d", patch);
+  *out = &c->p[patch];
+  return use_device(c);
+}
+
+mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double* pi, int on_device) {
+  PatchState* P;
+  mpw_status st = get_patch(c, patch, &P);
+  if (st) return st;
+  if (!psi || !pi) return set_err(MPW_ERR_ARG, "null field pointer");
+  const size_t n = (size_t)P->d.n[0] * P->d.n[1] * P->d.n[2];
+  const double *s0 = psi, *s1 = pi;
+  if (!on_device) {
+    if ((st = ensure_stage(c, 2 * n * sizeof(double)))) return st;
+    CUDA_TRY(cudaMemcpyAsync(c->d_stage, psi, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(c->d_stage + n, pi, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    s0 = c->d_stage;
+    s1 = c->d_stage + n;
+  }
+  launch_unpack(P->buf(BUF_U), P->g, s0, s1, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MPW_OK;
+}
+
+static mpw_status get_impl(mpw_ctx* c, int patch, double* psi, double* pi, int on_device, int padded) {
+  PatchState* P;
+  mpw_status st = get_patch(c, patch, &P);
+  if (st) return st;
+  if (!psi || !pi) return set_err(MPW_ERR_ARG, "null field pointer");
+  const int e = padded ? 2 * NG : 0;
+  const size_t n = (size_t)(P->d.n[0] + e) * (P->d.n[1] + e) * (P->d.n[2] + e);
+  const uint8_t* flags = (patch == 0 && c->flags_valid) ? c->d_flags : nullptr;
+  if (on_device) {
+    launch_pack(P->buf(BUF_U), P->g, psi, pi, padded, flags, c->stream);
+    CUDA_TRY(cudaGetLastError());
+  } else {
+    if ((st = ensure_stage(c, 2 * n * sizeof(double)))) return st;
+    launch_pack(P->buf(BUF_U), P->g, c->d_stage, c->d_stage + n, padded, flags, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(psi, c->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaMemcpyAsync(pi, c->d_stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  }
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MPW_OK;
+}
+
+mpw_status mpw_get_fields(mpw_ctx* c, int patch, double* psi, double* pi, int on_device) {
+  return get_impl(c, patch, psi, pi, on_device, 0);
+}
+
+mpw_status mpw_get_padded(mpw_ctx* c, int patch, double* psi, double* pi, int on_device) {
+  return get_impl(c, patch, psi, pi, on_device, 1);
+}
+
+mpw_status mpw_set_time(mpw_ctx* c, double t) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  c->t = t;
+  return MPW_OK;
+}
+
+double mpw_time(const mpw_ctx* c) { return c ? c->t : NAN; }
+
+mpw_status mpw_compute_flags(mpw_ctx* c) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  if ((st = run_flags(c, c->t))) return st;
+  return read_error_word(c);
+}
+
+mpw_status mpw_get_flags(mpw_ctx* c, uint8_t* flags) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (c->p.empty() || !flags) return set_err(MPW_ERR_ARG, "no global patch or null pointer");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  const size_t nb = (size_t)c->p[0].d.n[0] * c->p[0].d.n[1] * c->p[0].d.n[2];
+  CUDA_TRY(cudaMemcpyAsync(flags, c->d_flags, nb, cudaMemcpyDeviceToHost, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  return MPW_OK;
+}
+
+mpw_status mpw_set_flags(mpw_ctx* c, const uint8_t* flags) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (c->p.empty() || !flags) return set_err(MPW_ERR_ARG, "no global patch or null pointer");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  const PatchState& g = c->p[0];
+  const size_t nb = (size_t)g.d.n[0] * g.d.n[1] * g.d.n[2];
+  CUDA_TRY(cudaMemcpyAsync(c->d_flags, flags, nb, cudaMemcpyHostToDevice, c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->boxes.assign(c->p.size() - 1, Box{});
+  for (size_t q = 1; q < c->p.size(); ++q) c->boxes[q - 1] = covered_box(g, c->p[q], c->t);
+  c->flags_valid = true;
+  return MPW_OK;
+}
+
+mpw_status mpw_fill_ghosts(mpw_ctx* c, double t) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  if (!c->flags_valid && (st = run_flags(c, c->t))) return st;
+  if ((st = run_fill(c, BUF_U, t))) return st;
+  return read_error_word(c);
+}
+
+mpw_status mpw_step(mpw_ctx* c, double dt, int nsteps) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
+  if (nsteps < 0) return set_err(MPW_ERR_ARG, "nsteps must be >= 0");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  bool moving = false;
+  for (size_t q = 1; q < c->p.size(); ++q) moving = moving || is_moving(c->p[q].d);
+  for (int s = 0; s < nsteps; ++s) {
+    const double tn = c->t;
+    if ((st = validate_step(c, dt, tn))) return st;
+    if (moving || !c->flags_valid)
+      if ((st = run_flags(c, tn))) return st;
+    static const int fill_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
+    for (int l = 0; l < 4; ++l) {
+      const double tl = tn + RK_C[l] * dt;
+      if ((st = run_fill(c, fill_buf[l], tl))) return st;
+      if ((st = run_rhs(c, l, tl, dt))) return st;
+    }
+    c->t = tn + dt;
+    c->stepped = true;
+  }
+  return read_error_word(c);
+}
+
+mpw_status mpw_live_points(mpw_ctx* c, long long* count) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (c->p.empty() || !count) return set_err(MPW_ERR_ARG, "no global patch or null pointer");
+  long long n = 0;
+  for (const auto& P : c->p) n += (long long)P.d.n[0] * P.d.n[1] * P.d.n[2];
+  for (size_t q = 1; q < c->p.size(); ++q) {
+    const Box b = c->flags_valid && q - 1 < c->boxes.size() ? c->boxes[q - 1] : covered_box(c->p[0], c->p[q], c->t);
+    long long inner = 1;
+    for (int a = 0; a < 3; ++a) inner *= std::max(b.hi[a] - b.lo[a] + 1 - 2 * c->buffer, 0);
+    if (!box_empty(b)) n -= inner;
+  }
+  *count = n;
+  return MPW_OK;
+}
+
+mpw_status mpw_profile_enable(mpw_ctx* c, int enable) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  c->prof = enable != 0;
+  return MPW_OK;
+}
+
+mpw_status mpw_profile_read(mpw_ctx* c, double* ms, long long* launches, int n) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (n < 0 || n > MPW_KERNEL_FAMILIES) return set_err(MPW_ERR_ARG, "n must be in [0, %d]", MPW_KERNEL_FAMILIES);
+  if (use_device(c)) return MPW_ERR_CUDA;
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  for (int f = 0; f < MPW_KERNEL_FAMILIES; ++f) {
+    double total = 0.0;
+    for (size_t i = 0; i < c->ev_used[f]; ++i) {
+      float m = 0.0f;
+      CUDA_TRY(cudaEventElapsedTime(&m, c->ev[f][2 * i], c->ev[f][2 * i + 1]));
+      total += m;
+    }
+    if (f < n) {
+      if (ms) ms[f] = total;
+      if (launches) launches[f] = c->launches[f];
+    }
+    c->ev_used[f] = 0;
+    c->launches[f] = 0;
+  }
+  return MPW_OK;
+}
+
+}  // extern "C"

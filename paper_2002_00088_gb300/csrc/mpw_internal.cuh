@@ -1,0 +1,121 @@
+// mpw_internal.cuh -- device data layout and kernel interfaces of libmpw.
+//
+// Layout in HBM.  Every patch owns one allocation of 8 field arrays
+// (state u, accumulator, two stage buffers; x 2 fields psi, Pi).  A field
+// array is a padded box of (n+6) planes x (n+6) rows with a row pitch px that
+// is a multiple of 16 doubles (128 B); the interior cell i = 0 sits at column
+// XOFF = 4 (32 B aligned), the ghost cells i = -3..-1 at columns 1..3.
+#pragma once
+#include <cstdint>
+
+namespace mpw {
+
+constexpr int NG = 3;
+constexpr int XOFF = 4;
+constexpr int MAX_PATCHES = 16;
+constexpr int MAX_APARAMS = 1024;
+
+enum { BUF_U = 0, BUF_ACC = 1, BUF_YA = 2, BUF_YB = 3 };
+enum { FLAG_LIVE = 0, FLAG_GHOST = 1, FLAG_DEAD = 2, FLAG_REVIVED = 3 };
+enum { ERR_UNFILLED = 1, ERR_BOUNDS = 2, ERR_NONFINITE = 4 };
+
+struct Geom {
+  int n[3];
+  int px, py;
+  long long plane, vol;
+  double lo[3], h[3];
+  __host__ __device__ __forceinline__ long long at(int i, int j, int k) const {
+    return (long long)(k + NG) * plane + (long long)(j + NG) * px + (i + XOFF);
+  }
+};
+
+// Covered box of one local patch in global index space (inclusive bounds);
+// empty when lo > hi on any axis.
+struct Box {
+  int lo[3], hi[3];
+};
+
+// ---------------------------------------------------------------- K1
+struct RhsPatch {
+  const double* Y;   // stencil input (psi; Pi at +vol)
+  const double* U;   // u_n
+  double* ACC;       // accumulator
+  double* OUT;       // next stage state (or u_{n+1} at the last substage)
+  Geom g;
+  double c1[3];      // w_a / (12 h_a)
+  double c2[3];      // 1 / (12 h_a^2)
+  double cko[3];     // eps / (64 h_a)
+  int tiles_x, tiles_y, zchunks, zc;
+  int block0;
+  int moving;        // any w_a != 0
+  int is_global;
+};
+
+struct RhsArgs {
+  RhsPatch p[MAX_PATCHES];
+  int np;
+  int stage;            // 0..3
+  double alpha, beta;   // OUT = base + alpha K ; ACC = base' + beta K
+  const uint8_t* flags; // global cover flags
+  int nbox;
+  Box box[MAX_PATCHES];
+};
+
+// ---------------------------------------------------------------- fill
+struct FillLocal {
+  double* Y;          // this patch's stage buffer (psi; Pi at +vol)
+  Geom g;
+  double X0[3];       // map at the substage time
+  long long g2l_begin, g2l_count;   // its ghost shell
+  long long l2g_begin, l2g_count;   // global effective-ghost shell under it
+  int shell_lo[3], shell_dim[3];    // outer box of that shell (global indices) and extents
+};
+
+struct FillArgs {
+  double* Yg;          // global stage buffer
+  Geom gg;
+  int outer_bc;        // 0 analytic, 1 periodic
+  int akind, acount;
+  const double* aparams;
+  double t;
+  long long outer_count;
+  int nloc;
+  FillLocal loc[MAX_PATCHES];
+  const uint8_t* flags;
+  int P;
+  int buffer;
+  long long total;
+  int* err;
+};
+
+// ---------------------------------------------------------------- flags
+struct FlagArgs {
+  uint8_t* flags;
+  int n[3];
+  int nloc;
+  Box box[MAX_PATCHES];
+  int buffer;
+  int old_valid;
+  double* Ug;          // global u (psi; Pi at +vol)
+  Geom gg;
+  const double* Uloc[MAX_PATCHES];
+  Geom gl[MAX_PATCHES];
+  double X0[MAX_PATCHES][3];
+  int P;
+  int* err;
+};
+
+// ---------------------------------------------------------------- host entry points of the kernels
+void launch_rhs_fp64(const RhsArgs& a, int blocks, void* stream);
+void launch_fill(const FillArgs& a, void* stream);
+void launch_flags(const FlagArgs& a, void* stream);
+void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
+                     const double* aparams, double t, void* stream);
+void launch_pack(const double* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags,
+                 void* stream);
+void launch_unpack(double* buf, const Geom& g, const double* d0, const double* d1, void* stream);
+
+constexpr int RHS_TX = 32;
+constexpr int RHS_TY = 8;
+
+}  // namespace mpw

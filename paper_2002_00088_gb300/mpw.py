@@ -1,0 +1,238 @@
+"""Thin ctypes binding of libmpw (include/mpw.h).
+
+Argument marshalling only: every step of the method runs in the CUDA kernels
+of libmpw.so.  PyTorch supplies device memory (through the allocator hook
+bound to its caching allocator), the stream and, for the tests and the
+benchmark, device tensors.  There is no CPU fallback: if libmpw.so is missing
+or cannot be loaded, importing this module raises.
+"""
+import ctypes as C
+import os
+
+import numpy as np
+
+from .build import LIB_PATH
+
+# enums of include/mpw.h
+MPW_OK = 0
+STATUS_NAMES = {0: "MPW_OK", 1: "MPW_ERR_ARG", 2: "MPW_ERR_OVERLAP", 3: "MPW_ERR_CFL", 4: "MPW_ERR_TRAVERSAL",
+                5: "MPW_ERR_OUTSIDE", 6: "MPW_ERR_GHOST_UNFILLED", 7: "MPW_ERR_BOUNDS", 8: "MPW_ERR_TIMEOUT",
+                9: "MPW_ERR_CUDA", 10: "MPW_ERR_STATE"}
+PATCH_GLOBAL, PATCH_LOCAL = 0, 1
+BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
+MOTION_STATIC, MOTION_LINEAR, MOTION_CIRCULAR = 0, 1, 2
+ANALYTIC_GAUSS_SUM, ANALYTIC_PLANE_SUM, ANALYTIC_HARMONIC_POLY = 0, 1, 2
+FLAG_LIVE, FLAG_GHOST, FLAG_DEAD, FLAG_REVIVED = 0, 1, 2, 3
+NG = 3
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class mpw_config(C.Structure):
+    _fields_ = [("precision", C.c_int), ("ghost", C.c_int), ("interp_points", C.c_int), ("ko_eps", C.c_double),
+                ("buffer", C.c_int), ("device", C.c_int), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
+                ("free", FREE_FN), ("alloc_user", C.c_void_p), ("arith", C.c_int)]
+
+
+class mpw_patch_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
+                ("outer_bc", C.c_int), ("motion", C.c_int), ("motion_params", C.c_double * 16)]
+
+
+# Every symbol that include/mpw.h declares, with its ctypes signature.
+_dp = C.POINTER(C.c_double)
+_vp = C.c_void_p
+SIGNATURES = {
+    "mpw_create": (C.c_int, [C.POINTER(mpw_config), C.POINTER(C.c_void_p)]),
+    "mpw_create_patch": (C.c_int, [_vp, C.POINTER(mpw_patch_desc), C.POINTER(C.c_int)]),
+    "mpw_set_analytic": (C.c_int, [_vp, C.c_int, _dp, C.c_int]),
+    "mpw_fill_analytic": (C.c_int, [_vp, C.c_double]),
+    "mpw_set_fields": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int]),
+    "mpw_get_fields": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int]),
+    "mpw_get_padded": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int]),
+    "mpw_set_time": (C.c_int, [_vp, C.c_double]),
+    "mpw_time": (C.c_double, [_vp]),
+    "mpw_compute_flags": (C.c_int, [_vp]),
+    "mpw_get_flags": (C.c_int, [_vp, _vp]),
+    "mpw_set_flags": (C.c_int, [_vp, _vp]),
+    "mpw_fill_ghosts": (C.c_int, [_vp, C.c_double]),
+    "mpw_step": (C.c_int, [_vp, C.c_double, C.c_int]),
+    "mpw_live_points": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
+    "mpw_profile_enable": (C.c_int, [_vp, C.c_int]),
+    "mpw_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
+    "mpw_last_error": (C.c_char_p, []),
+    "mpw_destroy": (None, [_vp]),
+}
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: run paper_2002_00088_gb300.build.build_library() "
+                          "(or __graft_entry__.build()) first; there is no fallback path")
+    L = C.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    return L
+
+
+lib = _load()
+
+
+class MpwError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def check(status):
+    if status != MPW_OK:
+        raise MpwError(status, lib.mpw_last_error().decode())
+    return status
+
+
+def _torch():
+    import torch
+    return torch
+
+
+class Multipatch:
+    """One multipatch simulation on one GPU (owns an mpw_ctx).
+
+    Device storage comes from PyTorch's caching allocator through the
+    mpw_config allocator hook; work is enqueued on the current torch stream.
+    """
+
+    def __init__(self, interp_points=6, ko_eps=0.005, buffer=0, device=0, stream=None, arith=0):
+        torch = _torch()
+        self.device = device
+        self._torch = torch
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        self.stream = stream
+
+        def _alloc(nbytes, user):
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, self.stream)
+
+        def _free(ptr, user):
+            torch.cuda.caching_allocator_delete(ptr)
+
+        self._alloc_cb = ALLOC_FN(_alloc)
+        self._free_cb = FREE_FN(_free)
+        cfg = mpw_config(precision=64, ghost=NG, interp_points=interp_points, ko_eps=ko_eps, buffer=buffer,
+                         device=device, stream=C.c_void_p(stream.cuda_stream), alloc=self._alloc_cb,
+                         free=self._free_cb, alloc_user=None, arith=arith)
+        self.h = C.c_void_p()
+        check(lib.mpw_create(C.byref(cfg), C.byref(self.h)))
+        self.shapes = []
+
+    def close(self):
+        if self.h:
+            lib.mpw_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- setup --------------------------------------------------------------
+    def create_patch(self, kind, n, lo, hi, outer_bc, motion=MOTION_STATIC, motion_params=()):
+        d = mpw_patch_desc()
+        d.kind = kind
+        for a in range(3):
+            d.n[a] = int(n[a])
+            d.lo[a] = float(lo[a])
+            d.hi[a] = float(hi[a])
+        d.outer_bc = outer_bc
+        d.motion = motion
+        for i, v in enumerate(motion_params):
+            d.motion_params[i] = float(v)
+        pid = C.c_int()
+        check(lib.mpw_create_patch(self.h, C.byref(d), C.byref(pid)))
+        self.shapes.append((int(n[2]), int(n[1]), int(n[0])))
+        return pid.value
+
+    def set_analytic(self, kind, params, count):
+        p = np.ascontiguousarray(params, dtype=np.float64)
+        check(lib.mpw_set_analytic(self.h, kind, p.ctypes.data_as(_dp), count))
+
+    def fill_analytic(self, t):
+        check(lib.mpw_fill_analytic(self.h, float(t)))
+
+    # -- fields -------------------------------------------------------------
+    def set_fields(self, pid, psi, pi):
+        """psi, pi: numpy arrays (host) or torch CUDA tensors, shape (n2, n1, n0) float64."""
+        torch = self._torch
+        if isinstance(psi, torch.Tensor) and psi.is_cuda:
+            psi = psi.contiguous()
+            pi = pi.contiguous()
+            assert psi.dtype == torch.float64 and pi.dtype == torch.float64
+            check(lib.mpw_set_fields(self.h, pid, C.c_void_p(psi.data_ptr()), C.c_void_p(pi.data_ptr()), 1))
+        else:
+            psi = np.ascontiguousarray(psi, dtype=np.float64)
+            pi = np.ascontiguousarray(pi, dtype=np.float64)
+            check(lib.mpw_set_fields(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp), 0))
+
+    def get_fields(self, pid, out=None):
+        """Returns host numpy arrays, or fills the given pair of CUDA tensors."""
+        if out is not None:
+            psi, pi = out
+            check(lib.mpw_get_fields(self.h, pid, C.c_void_p(psi.data_ptr()), C.c_void_p(pi.data_ptr()), 1))
+            return psi, pi
+        psi = np.empty(self.shapes[pid])
+        pi = np.empty(self.shapes[pid])
+        check(lib.mpw_get_fields(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp), 0))
+        return psi, pi
+
+    def get_padded(self, pid):
+        s = tuple(v + 2 * NG for v in self.shapes[pid])
+        psi = np.empty(s)
+        pi = np.empty(s)
+        check(lib.mpw_get_padded(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp), 0))
+        return psi, pi
+
+    # -- time, flags, stepping ----------------------------------------------
+    @property
+    def time(self):
+        return lib.mpw_time(self.h)
+
+    @time.setter
+    def time(self, t):
+        check(lib.mpw_set_time(self.h, float(t)))
+
+    def compute_flags(self):
+        check(lib.mpw_compute_flags(self.h))
+
+    def get_flags(self):
+        f = np.empty(self.shapes[0], dtype=np.uint8)
+        check(lib.mpw_get_flags(self.h, f.ctypes.data_as(_vp)))
+        return f
+
+    def set_flags(self, flags):
+        f = np.ascontiguousarray(flags, dtype=np.uint8)
+        check(lib.mpw_set_flags(self.h, f.ctypes.data_as(_vp)))
+
+    def fill_ghosts(self, t):
+        check(lib.mpw_fill_ghosts(self.h, float(t)))
+
+    def step(self, dt, nsteps=1):
+        check(lib.mpw_step(self.h, float(dt), int(nsteps)))
+
+    def profile(self, enable=True):
+        check(lib.mpw_profile_enable(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{family: (device ms, launches)} since the last read; families rhs, fill, flags."""
+        ms = (C.c_double * 3)()
+        n = (C.c_longlong * 3)()
+        check(lib.mpw_profile_read(self.h, ms, n, 3))
+        return {name: (ms[i], n[i]) for i, name in enumerate(("rhs", "fill", "flags"))}
+
+    def live_points(self):
+        n = C.c_longlong()
+        check(lib.mpw_live_points(self.h, C.byref(n)))
+        return n.value

@@ -49,7 +49,7 @@ def test_harmonic_polynomial_is_a_fixed_point(P):
 
 
 def test_no_nan_reaches_live_data():
-    w = wl.orbiting_gauss(scale=8, steps=3)
+    w = wl.orbiting_gauss(scale=4, steps=3)
     o = oracle_from(w)
     o.fill_analytic(0.0)
     o.step(w.dt, 3)
@@ -73,7 +73,7 @@ def test_planted_narrow_buffer_is_caught():
 
 
 def test_l2g_g2l_order_is_irrelevant():
-    w = wl.orbiting_gauss(scale=8, steps=2)
+    w = wl.orbiting_gauss(scale=4, steps=2)
     res = []
     for first in (True, False):
         o = oracle_from(w)
