@@ -76,7 +76,8 @@ typedef struct {
   mpw_alloc_fn alloc; /* optional device allocator hook */
   mpw_free_fn free;
   void* alloc_user;
-  int arith;          /* stencil arithmetic: 0 = library default, 1 = native FP64 */
+  int arith;          /* RHS arithmetic: 0 = exact int64 fixed-point stencil sums with FP64
+                         stage updates (default), 1 = native FP64 throughout */
 } mpw_config;
 
 typedef struct {

@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/mpw.h"
+#include "mpw_fixed.cuh"
 #include "mpw_internal.cuh"
 
 using namespace mpw;
@@ -47,7 +48,8 @@ const double RK_C[4] = {0.0, 0.5, 0.5, 1.0};
 struct PatchState {
   mpw_patch_desc d;
   Geom g;
-  double* base = nullptr;  // 4 buffers x 2 fields x vol doubles
+  bool u_expo_valid = false;  // exponent slots of u track its live values
+  double* base = nullptr;     // 4 buffers x 2 fields x vol doubles
   double* buf(int b) const { return base + (size_t)b * 2 * (size_t)g.vol; }
 };
 
@@ -66,6 +68,7 @@ struct mpw_ctx {
   std::vector<Box> boxes;  // covered boxes at the last flag computation
   int* d_err = nullptr;
   int* h_err = nullptr;
+  int* d_expo = nullptr;  // [patch][buffer][field] maximum biased exponent
   double* d_stage = nullptr;
   size_t stage_bytes = 0;
   double t = 0.0;
@@ -290,6 +293,7 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   a.gg = g.g;
   a.P = c->P;
   a.err = c->d_err;
+  a.expo = c->d_expo;
   c->launch_begin(MPW_KERNEL_FLAGS);
   launch_flags(a, c->stream);
   c->launch_end(MPW_KERNEL_FLAGS);
@@ -298,8 +302,9 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   return MPW_OK;
 }
 
-// Ghost fill of the stage buffer `b` at time t.
-mpw_status run_fill(mpw_ctx* c, int b, double t) {
+// Ghost fill of the stage buffer `b` at time t; clears the exponent slots of
+// buffer reset_buf (the output of the following RHS launch), if >= 0.
+mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   const PatchState& g = c->p[0];
   FillArgs a{};
   a.Yg = g.buf(b);
@@ -350,7 +355,11 @@ mpw_status run_fill(mpw_ctx* c, int b, double t) {
   a.P = c->P;
   a.buffer = c->buffer;
   a.err = c->d_err;
-  if (a.total <= 0) return MPW_OK;
+  a.expo = c->d_expo;
+  a.y_buf = b;
+  a.reset_buf = reset_buf;
+  a.np = (int)c->p.size();
+  if (a.total <= 0) return set_err(MPW_ERR_STATE, "empty ghost fill");
   c->launch_begin(MPW_KERNEL_FILL);
   launch_fill(a, c->stream);
   c->launch_end(MPW_KERNEL_FILL);
@@ -373,6 +382,7 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
   a.flags = c->d_flags;
   a.nbox = (int)c->boxes.size();
   for (int q = 0; q < a.nbox; ++q) a.box[q] = c->boxes[q];
+  a.expo = c->d_expo;
   int blocks = 0;
   for (int q = 0; q < a.np; ++q) {
     const PatchState& P = c->p[q];
@@ -393,6 +403,9 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
       if (w[k] != 0.0) R.moving = 1;
     }
     R.is_global = q == 0 && c->flags_valid && !c->boxes.empty();
+    R.iso = P.g.h[0] == P.g.h[1] && P.g.h[1] == P.g.h[2];
+    R.in_buf = in_buf[l];
+    R.out_buf = out_buf[l];
     R.tiles_x = (P.d.n[0] + RHS_TX - 1) / RHS_TX;
     R.tiles_y = (P.d.n[1] + RHS_TY - 1) / RHS_TY;
     R.zc = P.d.n[2] >= 128 ? 32 : 8;
@@ -401,9 +414,24 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
     blocks += R.tiles_x * R.tiles_y * R.zchunks;
   }
   c->launch_begin(MPW_KERNEL_RHS);
-  launch_rhs_fp64(a, blocks, c->stream);
+  launch_rhs(a, blocks, c->cfg.arith != 1, c->stream);
   c->launch_end(MPW_KERNEL_RHS);
   CUDA_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+// Recompute the exponent slots of u for patches whose u was written from
+// outside a step (creation, set_fields, fill_analytic).
+mpw_status ensure_u_exponents(mpw_ctx* c) {
+  for (size_t q = 0; q < c->p.size(); ++q) {
+    PatchState& P = c->p[q];
+    if (P.u_expo_valid) continue;
+    int* slot2 = c->d_expo + q * EXP_SLOTS_PER_PATCH + BUF_U * 2;
+    CUDA_TRY(cudaMemsetAsync(slot2, 0, 2 * sizeof(int), c->stream));
+    launch_expo_scan(P.buf(BUF_U), P.g, (q == 0 && c->flags_valid) ? c->d_flags : nullptr, slot2, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    P.u_expo_valid = true;
+  }
   return MPW_OK;
 }
 
@@ -449,11 +477,13 @@ mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out) {
   }
   c->d_err = (int*)c->dalloc(256);
   c->d_aparams = (double*)c->dalloc(sizeof(double) * MAX_APARAMS);
-  if (!c->d_err || !c->d_aparams || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+  c->d_expo = (int*)c->dalloc(sizeof(int) * MAX_PATCHES * EXP_SLOTS_PER_PATCH);
+  if (!c->d_err || !c->d_aparams || !c->d_expo || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
     mpw_destroy(c);
     return set_err(MPW_ERR_CUDA, "context allocation failed");
   }
-  if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess) {
+  if (cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->d_expo, 0, sizeof(int) * MAX_PATCHES * EXP_SLOTS_PER_PATCH, c->stream) != cudaSuccess) {
     mpw_destroy(c);
     return set_err(MPW_ERR_CUDA, "memset failed");
   }
@@ -469,6 +499,7 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_flags);
   c->dfree(c->d_err);
   c->dfree(c->d_aparams);
+  c->dfree(c->d_expo);
   c->dfree(c->d_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& v : c->ev)
@@ -557,6 +588,7 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
     motion(P.d, t, X0, w);
     launch_analytic(P.buf(BUF_U), P.g, X0[0], X0[1], X0[2], c->akind, c->acount, c->d_aparams, t, c->stream);
     CUDA_TRY(cudaGetLastError());
+    P.u_expo_valid = false;
   }
   c->t = t;
   return MPW_OK;
@@ -586,6 +618,7 @@ mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double
   }
   launch_unpack(P->buf(BUF_U), P->g, s0, s1, c->stream);
   CUDA_TRY(cudaGetLastError());
+  P->u_expo_valid = false;
   if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
   return MPW_OK;
 }
@@ -670,7 +703,8 @@ mpw_status mpw_fill_ghosts(mpw_ctx* c, double t) {
   if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
   if (use_device(c)) return MPW_ERR_CUDA;
   if (!c->flags_valid && (st = run_flags(c, c->t))) return st;
-  if ((st = run_fill(c, BUF_U, t))) return st;
+  if ((st = ensure_u_exponents(c))) return st;
+  if ((st = run_fill(c, BUF_U, t, -1))) return st;
   return read_error_word(c);
 }
 
@@ -687,10 +721,12 @@ mpw_status mpw_step(mpw_ctx* c, double dt, int nsteps) {
     if ((st = validate_step(c, dt, tn))) return st;
     if (moving || !c->flags_valid)
       if ((st = run_flags(c, tn))) return st;
+    if ((st = ensure_u_exponents(c))) return st;
     static const int fill_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
+    static const int next_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
     for (int l = 0; l < 4; ++l) {
       const double tl = tn + RK_C[l] * dt;
-      if ((st = run_fill(c, fill_buf[l], tl))) return st;
+      if ((st = run_fill(c, fill_buf[l], tl, next_buf[l]))) return st;
       if ((st = run_rhs(c, l, tl, dt))) return st;
     }
     c->t = tn + dt;

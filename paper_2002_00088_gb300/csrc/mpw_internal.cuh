@@ -49,6 +49,8 @@ struct RhsPatch {
   int block0;
   int moving;        // any w_a != 0
   int is_global;
+  int iso;           // equal spacing on all axes (D2 and KO sums aggregated)
+  int in_buf, out_buf;
 };
 
 struct RhsArgs {
@@ -59,6 +61,7 @@ struct RhsArgs {
   const uint8_t* flags; // global cover flags
   int nbox;
   Box box[MAX_PATCHES];
+  int* expo;            // tracked maximum biased exponents, [patch][buffer][field]
 };
 
 // ---------------------------------------------------------------- fill
@@ -86,6 +89,10 @@ struct FillArgs {
   int buffer;
   long long total;
   int* err;
+  int* expo;
+  int y_buf;           // buffer being filled (its exponent slots receive the ghost values)
+  int reset_buf;       // buffer whose exponent slots are cleared (the next stage's output), or -1
+  int np;
 };
 
 // ---------------------------------------------------------------- flags
@@ -103,10 +110,12 @@ struct FlagArgs {
   double X0[MAX_PATCHES][3];
   int P;
   int* err;
+  int* expo;
 };
 
 // ---------------------------------------------------------------- host entry points of the kernels
-void launch_rhs_fp64(const RhsArgs& a, int blocks, void* stream);
+void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
+void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);
 void launch_fill(const FillArgs& a, void* stream);
 void launch_flags(const FlagArgs& a, void* stream);
 void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 
+#include "mpw_fixed.cuh"
 #include "mpw_internal.cuh"
 
 namespace mpw {
@@ -194,73 +195,114 @@ __device__ __forceinline__ int wrap_index(int i, int n) { return ((i % n) + n) %
 // Global-to-Local into every local ghost shell.  The three target sets are
 // disjoint and each reads only data the others do not write (the buffer makes
 // every interpolation donor a live cell), so they run as one launch.
+// Warp-aggregated atomicMax of the exponents written by each lane into the
+// exponent slots of the patch it wrote (patch < 0: nothing written).
+__device__ __forceinline__ void report_exponents(int* expo, int buf, int patch, double v0, double v1) {
+  const unsigned mask = __activemask();
+  const unsigned peers = __match_any_sync(mask, patch);
+  const int e0 = __reduce_max_sync(peers, patch >= 0 ? biased_exponent(v0) : 0);
+  const int e1 = __reduce_max_sync(peers, patch >= 0 ? biased_exponent(v1) : 0);
+  if (patch >= 0 && (threadIdx.x & 31) == __ffs(peers) - 1) {
+    atomicMax(&expo[patch * EXP_SLOTS_PER_PATCH + buf * 2], e0);
+    atomicMax(&expo[patch * EXP_SLOTS_PER_PATCH + buf * 2 + 1], e1);
+  }
+}
+
+// Global outer ghost shell point idx: analytic closed form or periodic wrap.
+__device__ __forceinline__ void fill_outer(const FillArgs& A, long long idx, double& w0, double& w1) {
+  const int O[3] = {A.gg.n[0] + 2 * NG, A.gg.n[1] + 2 * NG, A.gg.n[2] + 2 * NG};
+  int x, y, z;
+  shell_point(idx, O, NG, x, y, z);
+  const int i = x - NG, j = y - NG, k = z - NG;
+  const long long c = A.gg.at(i, j, k);
+  if (A.outer_bc == 1) {
+    const long long s = A.gg.at(wrap_index(i, A.gg.n[0]), wrap_index(j, A.gg.n[1]), wrap_index(k, A.gg.n[2]));
+    w0 = A.Yg[s];
+    w1 = A.Yg[s + A.gg.vol];
+  } else {
+    closed_form(A.akind, A.aparams, A.acount, A.t, A.gg.lo[0] + (i + 0.5) * A.gg.h[0],
+                A.gg.lo[1] + (j + 0.5) * A.gg.h[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2], w0, w1);
+  }
+  A.Yg[c] = w0;
+  A.Yg[c + A.gg.vol] = w1;
+}
+
+// Local-to-Global (Sec. 2.4.2): effective ghost cell number r of the shell
+// under local patch q, interpolated from q at the substage time.
+template <int P>
+__device__ __forceinline__ bool fill_l2g(const FillArgs& A, int q, long long r, double& w0, double& w1) {
+  const FillLocal& L = A.loc[q];
+  int x, y, z;
+  shell_point(r, L.shell_dim, NG, x, y, z);
+  const int i = L.shell_lo[0] + x, j = L.shell_lo[1] + y, k = L.shell_lo[2] + z;
+  const uint8_t f = A.flags[((long long)k * A.gg.n[1] + j) * A.gg.n[0] + i];
+  if ((f & 3) != FLAG_GHOST || (f >> 2) != q + 1) {
+    atomicOr(A.err, ERR_BOUNDS);
+    return false;
+  }
+  if (!interp<P>(L.Y, L.g, A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - L.X0[0],
+                 A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - L.X0[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - L.X0[2], w0,
+                 w1)) {
+    atomicOr(A.err, ERR_UNFILLED);
+    return false;
+  }
+  const long long c = A.gg.at(i, j, k);
+  A.Yg[c] = w0;
+  A.Yg[c + A.gg.vol] = w1;
+  return true;
+}
+
+// Global-to-Local (Sec. 2.4.1): ghost point number r of local patch q,
+// interpolated from the global patch at the substage time.
+template <int P>
+__device__ __forceinline__ bool fill_g2l(const FillArgs& A, int q, long long r, double& w0, double& w1) {
+  const FillLocal& L = A.loc[q];
+  const int O[3] = {L.g.n[0] + 2 * NG, L.g.n[1] + 2 * NG, L.g.n[2] + 2 * NG};
+  int x, y, z;
+  shell_point(r, O, NG, x, y, z);
+  const int i = x - NG, j = y - NG, k = z - NG;
+  if (!interp<P>(A.Yg, A.gg, L.g.lo[0] + (i + 0.5) * L.g.h[0] + L.X0[0], L.g.lo[1] + (j + 0.5) * L.g.h[1] + L.X0[1],
+                 L.g.lo[2] + (k + 0.5) * L.g.h[2] + L.X0[2], w0, w1)) {
+    atomicOr(A.err, ERR_UNFILLED);
+    return false;
+  }
+  const long long c = L.g.at(i, j, k);
+  L.Y[c] = w0;
+  L.Y[c + L.g.vol] = w1;
+  return true;
+}
+
+// Ghost-zone fill of one substage (Sec. 2.4): global outer shell, then the
+// Local-to-Global segments, then the Global-to-Local segments, as consecutive
+// ranges of one index space.  The target sets are disjoint and each reads only
+// data the others do not write (the buffer makes every interpolation donor a
+// live cell), so one launch serves them all.  Block 0 also clears the
+// exponent slots of the buffer the next RHS launch will write.
 template <int P>
 __global__ void __launch_bounds__(256) k_fill(const __grid_constant__ FillArgs A) {
+  if (A.reset_buf >= 0 && blockIdx.x == 0 && threadIdx.x < 2 * A.np)
+    A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < A.total; idx += stride) {
+    int wrote = -1;
+    double w0 = 0.0, w1 = 0.0;
     if (idx < A.outer_count) {
-      const int O[3] = {A.gg.n[0] + 2 * NG, A.gg.n[1] + 2 * NG, A.gg.n[2] + 2 * NG};
-      int x, y, z;
-      shell_point(idx, O, NG, x, y, z);
-      const int i = x - NG, j = y - NG, k = z - NG;
-      const long long c = A.gg.at(i, j, k);
-      if (A.outer_bc == 1) {
-        const long long s =
-            A.gg.at(wrap_index(i, A.gg.n[0]), wrap_index(j, A.gg.n[1]), wrap_index(k, A.gg.n[2]));
-        A.Yg[c] = A.Yg[s];
-        A.Yg[c + A.gg.vol] = A.Yg[s + A.gg.vol];
-      } else {
-        double ps, pv;
-        closed_form(A.akind, A.aparams, A.acount, A.t, A.gg.lo[0] + (i + 0.5) * A.gg.h[0],
-                    A.gg.lo[1] + (j + 0.5) * A.gg.h[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2], ps, pv);
-        A.Yg[c] = ps;
-        A.Yg[c + A.gg.vol] = pv;
-      }
-      continue;
-    }
-    for (int q = 0; q < A.nloc; ++q) {
-      const FillLocal& L = A.loc[q];
-      if (idx >= L.l2g_begin && idx < L.l2g_begin + L.l2g_count) {
-        int x, y, z;
-        shell_point(idx - L.l2g_begin, L.shell_dim, NG, x, y, z);
-        const int i = L.shell_lo[0] + x, j = L.shell_lo[1] + y, k = L.shell_lo[2] + z;
-        const uint8_t f = A.flags[((long long)k * A.gg.n[1] + j) * A.gg.n[0] + i];
-        if ((f & 3) != FLAG_GHOST || (f >> 2) != q + 1) {
-          atomicOr(A.err, ERR_BOUNDS);
+      fill_outer(A, idx, w0, w1);
+      wrote = 0;
+    } else {
+      for (int q = 0; q < A.nloc; ++q) {
+        const FillLocal& L = A.loc[q];
+        if (idx >= L.l2g_begin && idx < L.l2g_begin + L.l2g_count) {
+          if (fill_l2g<P>(A, q, idx - L.l2g_begin, w0, w1)) wrote = 0;
           break;
         }
-        double v0, v1;
-        const bool ok = interp<P>(L.Y, L.g, A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - L.X0[0],
-                                  A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - L.X0[1],
-                                  A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - L.X0[2], v0, v1);
-        if (!ok) {
-          atomicOr(A.err, ERR_UNFILLED);
+        if (idx >= L.g2l_begin && idx < L.g2l_begin + L.g2l_count) {
+          if (fill_g2l<P>(A, q, idx - L.g2l_begin, w0, w1)) wrote = q + 1;
           break;
         }
-        const long long c = A.gg.at(i, j, k);
-        A.Yg[c] = v0;
-        A.Yg[c + A.gg.vol] = v1;
-        break;
-      }
-      if (idx >= L.g2l_begin && idx < L.g2l_begin + L.g2l_count) {
-        const int O[3] = {L.g.n[0] + 2 * NG, L.g.n[1] + 2 * NG, L.g.n[2] + 2 * NG};
-        int x, y, z;
-        shell_point(idx - L.g2l_begin, O, NG, x, y, z);
-        const int i = x - NG, j = y - NG, k = z - NG;
-        double v0, v1;
-        const bool ok = interp<P>(A.Yg, A.gg, L.g.lo[0] + (i + 0.5) * L.g.h[0] + L.X0[0],
-                                  L.g.lo[1] + (j + 0.5) * L.g.h[1] + L.X0[1],
-                                  L.g.lo[2] + (k + 0.5) * L.g.h[2] + L.X0[2], v0, v1);
-        if (!ok) {
-          atomicOr(A.err, ERR_UNFILLED);
-          break;
-        }
-        const long long c = L.g.at(i, j, k);
-        L.Y[c] = v0;
-        L.Y[c + L.g.vol] = v1;
-        break;
       }
     }
+    report_exponents(A.expo, A.y_buf, wrote, w0, w1);
   }
 }
 
@@ -321,6 +363,8 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
     }
     A.Ug[c] = v0;
     A.Ug[c + A.gg.vol] = v1;
+    atomicMax(&A.expo[BUF_U * 2], biased_exponent(v0));
+    atomicMax(&A.expo[BUF_U * 2 + 1], biased_exponent(v1));
   }
 }
 
@@ -331,147 +375,6 @@ void launch_flags(const FlagArgs& a, void* stream) {
     k_flags<6><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
   else
     k_flags<5><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
-}
-
-// ---------------------------------------------------------------------------
-// Native FP64 fused RHS + RK4 stage (reference GPU path; Sec. 2.2-2.3).
-// One CTA owns a TX x TY column tile and marches a chunk of zc planes: the z
-// neighbours of its own column sit in a 7-deep register queue, the x/y
-// neighbours of the current plane in shared memory (halo 3, star stencil).
-template <int TX, int TY>
-__global__ void __launch_bounds__(TX* TY) k_rhs_fp64(const __grid_constant__ RhsArgs A) {
-  __shared__ double sm[2][TY + 6][TX + 6];
-  const int b = blockIdx.x;
-  int p = 0;
-  while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
-  const RhsPatch& Pt = A.p[p];
-  const Geom& g = Pt.g;
-  int lb = b - Pt.block0;
-  const int tx = lb % Pt.tiles_x;
-  lb /= Pt.tiles_x;
-  const int ty = lb % Pt.tiles_y;
-  const int tz = lb / Pt.tiles_y;
-  const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
-  const int i0 = tx * TX, j0 = ty * TY;
-  const int i = i0 + li, j = j0 + lj;
-  const int z0 = tz * Pt.zc, z1 = min(z0 + Pt.zc, g.n[2]);
-  const bool in_box = (i < g.n[0] + NG) && (j < g.n[1] + NG);
-  const bool in_xy = (i < g.n[0]) && (j < g.n[1]);
-  bool check_flags = false;
-  if (Pt.is_global) {
-    for (int q = 0; q < A.nbox; ++q) {
-      const Box& bx = A.box[q];
-      if (bx.lo[0] <= i0 + TX - 1 && bx.hi[0] >= i0 && bx.lo[1] <= j0 + TY - 1 && bx.hi[1] >= j0 &&
-          bx.lo[2] <= z1 - 1 && bx.hi[2] >= z0)
-        check_flags = true;
-    }
-  }
-  const double* Ys = Pt.Y;
-  const double* Yp = Pt.Y + g.vol;
-  double qs[7], qp[7];
-#pragma unroll
-  for (int o = 0; o < 6; ++o) {
-    qs[o] = 0.0;
-    qp[o] = 0.0;
-    if (in_box) {
-      const long long c = g.at(i, j, z0 - NG + o);
-      qs[o] = Ys[c];
-      qp[o] = Yp[c];
-    }
-  }
-  // halo assignment: threads [0, 6 TX) load the y halo, [6 TX, 6 TX + 6 TY) the x halo
-  const int t = threadIdx.x;
-  int hi_ = -100, hj = -100, hsi = 0, hsj = 0;
-  if (t < 6 * TX) {
-    const int rr = t / TX, cc = t % TX;
-    hsj = rr < 3 ? rr : TY + rr;
-    hsi = cc + 3;
-    hi_ = i0 + cc;
-    hj = j0 + (rr < 3 ? rr - 3 : TY + rr - 3);
-  } else if (t < 6 * TX + 6 * TY) {
-    const int u = t - 6 * TX, rr = u / 6, cc = u % 6;
-    hsj = rr + 3;
-    hsi = cc < 3 ? cc : TX + cc;
-    hj = j0 + rr;
-    hi_ = i0 + (cc < 3 ? cc - 3 : TX + cc - 3);
-  }
-  const bool h_ok = hi_ >= -NG && hi_ < g.n[0] + NG && hj >= -NG && hj < g.n[1] + NG;
-  const double c2x = Pt.c2[0], c2y = Pt.c2[1], c2z = Pt.c2[2];
-  const double kx = Pt.cko[0], ky = Pt.cko[1], kz = Pt.cko[2];
-  const double c1x = Pt.c1[0], c1y = Pt.c1[1], c1z = Pt.c1[2];
-  constexpr int SY = TX + 6;
-  for (int z = z0; z < z1; ++z) {
-    if (in_box) {
-      const long long c = g.at(i, j, z + NG);
-      qs[6] = Ys[c];
-      qp[6] = Yp[c];
-    }
-    __syncthreads();
-    sm[0][lj + 3][li + 3] = qs[3];
-    sm[1][lj + 3][li + 3] = qp[3];
-    if (h_ok) {
-      const long long c = g.at(hi_, hj, z);
-      sm[0][hsj][hsi] = Ys[c];
-      sm[1][hsj][hsi] = Yp[c];
-    }
-    __syncthreads();
-    bool live = in_xy;
-    if (live && check_flags) {
-      const int f = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
-      live = (f == FLAG_LIVE) || (f == FLAG_REVIVED);
-    }
-    if (live) {
-      const double* rs = &sm[0][lj + 3][li + 3];
-      const double* rp = &sm[1][lj + 3][li + 3];
-      const double u0 = qs[3], v0 = qp[3];
-      const double xs1 = rs[-1] + rs[1], xs2 = rs[-2] + rs[2], xs3 = rs[-3] + rs[3];
-      const double ys1 = rs[-SY] + rs[SY], ys2 = rs[-2 * SY] + rs[2 * SY], ys3 = rs[-3 * SY] + rs[3 * SY];
-      const double zs1 = qs[2] + qs[4], zs2 = qs[1] + qs[5], zs3 = qs[0] + qs[6];
-      const double xp1 = rp[-1] + rp[1], xp2 = rp[-2] + rp[2], xp3 = rp[-3] + rp[3];
-      const double yp1 = rp[-SY] + rp[SY], yp2 = rp[-2 * SY] + rp[2 * SY], yp3 = rp[-3 * SY] + rp[3 * SY];
-      const double zp1 = qp[2] + qp[4], zp2 = qp[1] + qp[5], zp3 = qp[0] + qp[6];
-      const double d2 = c2x * (16.0 * xs1 - xs2 - 30.0 * u0) + c2y * (16.0 * ys1 - ys2 - 30.0 * u0) +
-                        c2z * (16.0 * zs1 - zs2 - 30.0 * u0);
-      const double kos = kx * (xs3 - 6.0 * xs2 + 15.0 * xs1 - 20.0 * u0) +
-                         ky * (ys3 - 6.0 * ys2 + 15.0 * ys1 - 20.0 * u0) +
-                         kz * (zs3 - 6.0 * zs2 + 15.0 * zs1 - 20.0 * u0);
-      const double kop = kx * (xp3 - 6.0 * xp2 + 15.0 * xp1 - 20.0 * v0) +
-                         ky * (yp3 - 6.0 * yp2 + 15.0 * yp1 - 20.0 * v0) +
-                         kz * (zp3 - 6.0 * zp2 + 15.0 * zp1 - 20.0 * v0);
-      double Ks = v0 + kos, Kp = d2 + kop;
-      if (Pt.moving) {
-        Ks += c1x * (8.0 * (rs[1] - rs[-1]) - (rs[2] - rs[-2])) +
-              c1y * (8.0 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY])) +
-              c1z * (8.0 * (qs[4] - qs[2]) - (qs[5] - qs[1]));
-        Kp += c1x * (8.0 * (rp[1] - rp[-1]) - (rp[2] - rp[-2])) +
-              c1y * (8.0 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY])) +
-              c1z * (8.0 * (qp[4] - qp[2]) - (qp[5] - qp[1]));
-      }
-      const long long c = g.at(i, j, z);
-      if (A.stage == 3) {
-        Pt.OUT[c] = fma(A.alpha, Ks, Pt.ACC[c]);
-        Pt.OUT[c + g.vol] = fma(A.alpha, Kp, Pt.ACC[c + g.vol]);
-      } else {
-        const double us = A.stage == 0 ? u0 : Pt.U[c];
-        const double up = A.stage == 0 ? v0 : Pt.U[c + g.vol];
-        const double as = A.stage == 0 ? u0 : Pt.ACC[c];
-        const double ap = A.stage == 0 ? v0 : Pt.ACC[c + g.vol];
-        Pt.OUT[c] = fma(A.alpha, Ks, us);
-        Pt.OUT[c + g.vol] = fma(A.alpha, Kp, up);
-        Pt.ACC[c] = fma(A.beta, Ks, as);
-        Pt.ACC[c + g.vol] = fma(A.beta, Kp, ap);
-      }
-    }
-#pragma unroll
-    for (int o = 0; o < 6; ++o) {
-      qs[o] = qs[o + 1];
-      qp[o] = qp[o + 1];
-    }
-  }
-}
-
-void launch_rhs_fp64(const RhsArgs& a, int blocks, void* stream) {
-  k_rhs_fp64<RHS_TX, RHS_TY><<<blocks, RHS_TX * RHS_TY, 0, (cudaStream_t)stream>>>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -547,6 +450,46 @@ __global__ void k_unpack(double* buf, const Geom g, const double* __restrict__ d
 void launch_unpack(double* buf, const Geom& g, const double* d0, const double* d1, void* stream) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   k_unpack<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)stream>>>(buf, g, d0, d1);
+}
+
+}  // namespace mpw
+
+namespace mpw {
+
+// Largest biased exponent of the live interior values of a buffer (both
+// fields), for buffers written from outside the step (set_fields,
+// fill_analytic).  slot2 points at the two slots of the buffer.
+__global__ void k_expo_scan(const double* __restrict__ buf, const Geom g, const uint8_t* __restrict__ flags,
+                            int* slot2) {
+  const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+  int e0 = 0, e1 = 0;
+  for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < N;
+       idx += (long long)gridDim.x * blockDim.x) {
+    if (flags) {
+      const int f = flags[idx] & 3;
+      if (f == FLAG_GHOST || f == FLAG_DEAD) continue;
+    }
+    const int i = (int)(idx % g.n[0]);
+    const long long r = idx / g.n[0];
+    const int j = (int)(r % g.n[1]);
+    const int k = (int)(r / g.n[1]);
+    const long long c = g.at(i, j, k);
+    e0 = max(e0, biased_exponent(buf[c]));
+    e1 = max(e1, biased_exponent(buf[c + g.vol]));
+  }
+  e0 = __reduce_max_sync(0xffffffffu, e0);
+  e1 = __reduce_max_sync(0xffffffffu, e1);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&slot2[0], e0);
+    atomicMax(&slot2[1], e1);
+  }
+}
+
+void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream) {
+  const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
+  long long blocks = (N + 255) / 256;
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  k_expo_scan<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(buf, g, flags, slot2);
 }
 
 }  // namespace mpw

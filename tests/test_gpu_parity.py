@@ -29,28 +29,40 @@ def seed_both(o, g, npatch):
 
 
 def compare_fields(o, g, npatch, tol):
+    """max |gpu - oracle| of each field over every patch, relative to the
+    largest |value| of that field over the whole domain (all patches)."""
+    got = [g.get_fields(q) for q in range(npatch)]
+    want = [o.get_fields(q) for q in range(npatch)]
     worst = 0.0
-    for q in range(npatch):
-        a_ps, a_pi = g.get_fields(q)
-        b_ps, b_pi = o.get_fields(q)
-        np.testing.assert_array_equal(np.isnan(a_ps), np.isnan(b_ps))
-        e = max(rel_err(a_ps, b_ps), rel_err(a_pi, b_pi))
-        worst = max(worst, e)
-        assert e <= tol, f"patch {q}: relative error {e:.3e} > {tol:.1e}"
+    for f in range(2):
+        scale = max(np.nanmax(np.abs(w[f])) for w in want)
+        for q in range(npatch):
+            a, b = got[q][f], want[q][f]
+            np.testing.assert_array_equal(np.isnan(a), np.isnan(b))
+            m = np.isfinite(b)
+            e = float(np.abs(a[m] - b[m]).max() / scale)
+            worst = max(worst, e)
+            assert e <= tol, f"patch {q} field {f}: relative error {e:.3e} > {tol:.1e}"
     return worst
 
 
+ARITH = [pytest.param(0, id="fixed"), pytest.param(1, id="fp64")]
+
+
+@pytest.mark.parametrize("arith", ARITH)
 @pytest.mark.parametrize("w", [(0.0, 0.0, 0.0), (0.7, -0.4, 1.3)])
-@pytest.mark.parametrize("n", [(40, 24, 20), (67, 29, 33)])
-def test_periodic_patch_random_fields(mpw_lib, w, n):
+@pytest.mark.parametrize("n,lo,hi", [((40, 24, 20), (-0.5, -0.3, -0.2), (0.5, 0.4, 0.3)),
+                                     ((67, 29, 33), (-0.5, -0.3, -0.2), (0.5, 0.4, 0.3)),
+                                     ((48, 48, 48), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0))])
+def test_periodic_patch_random_fields(mpw_lib, w, n, lo, hi, arith):
     """Fused RHS + RK4 stage kernel alone: one periodic patch (several tiles and
-    ragged tails), random data, with and without frame velocity."""
-    lo, hi = (-0.5, -0.3, -0.2), (0.5, 0.4, 0.3)
+    ragged tails, anisotropic and isotropic spacing), random data, with and
+    without frame velocity, in both arithmetic modes."""
     motion = po.LINEAR if any(w) else po.STATIC
     mp = (0.0, 0.0, 0.0) + tuple(w)
     o = po.Oracle(6, 0.005, threads=THREADS)
     o.add_patch(po.GLOBAL, n, lo, hi, po.BC_PERIODIC, motion, mp)
-    g = mpw_lib.Multipatch(6, 0.005)
+    g = mpw_lib.Multipatch(6, 0.005, arith=arith)
     g.create_patch(mpw_lib.PATCH_GLOBAL, n, lo, hi, mpw_lib.BC_PERIODIC, motion, mp)
     ps, pi = wl.random_fields((n[2], n[1], n[0]), 3)
     o.set_fields(0, ps, pi)
@@ -64,6 +76,28 @@ def test_periodic_patch_random_fields(mpw_lib, w, n):
     g.step(dt, 4)
     compare_fields(o, g, 1, 5e-12)
     assert g.time == o.time
+
+
+def test_non_finite_values_propagate_like_ieee(mpw_lib):
+    """A NaN in live data spreads through the stencil exactly as in the oracle's
+    FP64 arithmetic (the fixed-point kernel falls back per CTA)."""
+    n, lo, hi = (40, 24, 20), (-0.5, -0.3, -0.2), (0.5, 0.4, 0.3)
+    ps, pi = wl.random_fields((n[2], n[1], n[0]), 4)
+    ps[7, 11, 13] = np.nan
+    o = po.Oracle(6, 0.005)
+    o.add_patch(po.GLOBAL, n, lo, hi, po.BC_PERIODIC)
+    g = mpw_lib.Multipatch(6, 0.005)
+    g.create_patch(mpw_lib.PATCH_GLOBAL, n, lo, hi, mpw_lib.BC_PERIODIC)
+    o.set_fields(0, ps, pi)
+    g.set_fields(0, ps, pi)
+    o.step(0.002, 1)
+    g.step(0.002, 1)
+    a, b = g.get_fields(0), o.get_fields(0)
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(np.isnan(x), np.isnan(y))
+        assert np.isnan(y).any()
+        m = np.isfinite(y)
+        assert np.abs(x[m] - y[m]).max() <= 1e-12 * np.abs(y[m]).max()
 
 
 def test_analytic_fill_matches_oracle(mpw_lib):
@@ -121,11 +155,12 @@ def test_ghost_fill_matches_oracle(mpw_lib, make):
         assert np.abs(a_pi[m] - b_pi[m]).max() <= 1e-13 * max(scale, np.abs(b_pi[m]).max())
 
 
-def test_static_gauss_one_and_hundred_steps(mpw_lib):
+@pytest.mark.parametrize("arith", ARITH)
+def test_static_gauss_one_and_hundred_steps(mpw_lib, arith):
     """48^3 global + 32^3 local, static, 5-point Lagrange, 100 steps."""
     w = wl.static_gauss()
     o = oracle_from(w, THREADS)
-    g = gpu_from(mpw_lib, w)
+    g = gpu_from(mpw_lib, w, arith=arith)
     seed_both(o, g, 2)
     o.step(w.dt, 1)
     g.step(w.dt, 1)
@@ -140,12 +175,13 @@ def test_static_gauss_one_and_hundred_steps(mpw_lib):
     assert abs(g.time - o.time) == 0.0
 
 
-def test_orbiting_downscaled_many_steps(mpw_lib):
+@pytest.mark.parametrize("arith", ARITH)
+def test_orbiting_downscaled_many_steps(mpw_lib, arith):
     """64^3 global + four orbiting 32^3 locals, 6-point Lagrange, 40 steps:
     flags change, cells are revived and poisoned along the way."""
     w = wl.orbiting_gauss(scale=4)
     o = oracle_from(w, THREADS)
-    g = gpu_from(mpw_lib, w)
+    g = gpu_from(mpw_lib, w, arith=arith)
     seed_both(o, g, 5)
     o.step(w.dt, 1)
     g.step(w.dt, 1)
