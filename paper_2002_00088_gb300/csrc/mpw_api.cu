@@ -62,7 +62,10 @@ struct mpw_ctx {
   std::vector<PatchState> p;
   int akind = -1, acount = 0;
   std::vector<double> aparams;
+  std::vector<float4> screen;
   double* d_aparams = nullptr;
+  float4* d_ascreen = nullptr;  // FP32 screening data of Gaussian pulses
+  bool screen_ok = false;
   uint8_t* d_flags = nullptr;
   bool flags_valid = false;
   std::vector<Box> boxes;  // covered boxes at the last flag computation
@@ -302,6 +305,83 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   return MPW_OK;
 }
 
+// Tile extent for one slab of an interpolation segment: the thin axis takes
+// the slab thickness, the two wide axes the first candidate whose donor block
+// (span of the windows of the tile's targets, at the target/donor spacing
+// ratio) fits the separable kernel's shared-memory budget.
+void choose_tile(const double ratio[3], int P, int thin, const int extent[3], int td[3]) {
+  static const int cand[][2] = {{32, 8}, {16, 16}, {16, 8}, {8, 8}, {8, 4}, {4, 4}, {2, 2}, {1, 1}};
+  const int wa = thin == 0 ? 1 : 0, wb = thin == 2 ? 1 : 2;
+  for (const auto& cd : cand) {
+    int T[3];
+    T[thin] = extent[thin];
+    T[wa] = std::min(cd[0], extent[wa]);
+    T[wb] = std::min(cd[1], extent[wb]);
+    int Dn[3];
+    for (int a = 0; a < 3; ++a) Dn[a] = (int)std::floor((T[a] - 1) * ratio[a]) + 1 + P;
+    const bool ok = T[0] <= fill_max_tile() && T[1] <= fill_max_tile() && T[2] <= fill_max_tile() &&
+                    Dn[0] * Dn[1] * Dn[2] <= fill_cap_d() && Dn[2] * Dn[1] * T[0] <= fill_cap_r1() &&
+                    Dn[2] * T[1] * T[0] <= fill_cap_r2();
+    if (ok || (cd[0] == 1 && cd[1] == 1)) {
+      for (int a = 0; a < 3; ++a) td[a] = std::max(T[a], 1);
+      return;
+    }
+  }
+}
+
+// Cut the hollow box (origin O0, extent O, walls NG thick) into six slabs and
+// tile them; returns the number of CTAs.
+int build_segment(InterpSeg& S, const int O0[3], const int O[3], int P) {
+  int lo[3], hi[3];  // wall thickness at the low / high end of each axis
+  for (int a = 0; a < 3; ++a) {
+    lo[a] = std::min(NG, O[a]);
+    hi[a] = std::min(NG, O[a] - lo[a]);
+  }
+  const int mid0[3] = {lo[0], lo[1], lo[2]};
+  const int midn[3] = {O[0] - lo[0] - hi[0], O[1] - lo[1] - hi[1], O[2] - lo[2] - hi[2]};
+  int sb[6][3], se[6][3];
+  // z-, z+
+  for (int k = 0; k < 2; ++k) {
+    sb[k][0] = 0, se[k][0] = O[0];
+    sb[k][1] = 0, se[k][1] = O[1];
+    sb[k][2] = k ? O[2] - hi[2] : 0, se[k][2] = k ? hi[2] : lo[2];
+  }
+  // y-, y+ (between the z walls)
+  for (int k = 0; k < 2; ++k) {
+    sb[2 + k][0] = 0, se[2 + k][0] = O[0];
+    sb[2 + k][1] = k ? O[1] - hi[1] : 0, se[2 + k][1] = k ? hi[1] : lo[1];
+    sb[2 + k][2] = mid0[2], se[2 + k][2] = midn[2];
+  }
+  // x-, x+ (between the z and y walls)
+  for (int k = 0; k < 2; ++k) {
+    sb[4 + k][0] = k ? O[0] - hi[0] : 0, se[4 + k][0] = k ? hi[0] : lo[0];
+    sb[4 + k][1] = mid0[1], se[4 + k][1] = midn[1];
+    sb[4 + k][2] = mid0[2], se[4 + k][2] = midn[2];
+  }
+  double ratio[3];
+  for (int a = 0; a < 3; ++a) ratio[a] = S.gt.h[a] / S.gd.h[a];
+  int blocks = 0;
+  for (int sl = 0; sl < 6; ++sl) {
+    S.slab_block0[sl] = blocks;
+    for (int a = 0; a < 3; ++a) {
+      S.sb[sl][a] = O0[a] + sb[sl][a];
+      S.se[sl][a] = se[sl][a];
+    }
+    if (se[sl][0] <= 0 || se[sl][1] <= 0 || se[sl][2] <= 0) {
+      S.tn[sl][0] = S.tn[sl][1] = 0;
+      for (int a = 0; a < 3; ++a) S.td[sl][a] = 1;
+      continue;
+    }
+    choose_tile(ratio, P, sl / 2 == 0 ? 2 : (sl / 2 == 1 ? 1 : 0), se[sl], S.td[sl]);
+    int n[3];
+    for (int a = 0; a < 3; ++a) n[a] = (se[sl][a] + S.td[sl][a] - 1) / S.td[sl][a];
+    S.tn[sl][0] = n[0];
+    S.tn[sl][1] = n[1];
+    blocks += n[0] * n[1] * n[2];
+  }
+  return blocks;
+}
+
 // Ghost fill of the stage buffer `b` at time t; clears the exponent slots of
 // buffer reset_buf (the output of the following RHS launch), if >= 0.
 mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
@@ -314,52 +394,63 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   a.akind = c->akind;
   a.acount = c->acount;
   a.aparams = c->d_aparams;
+  a.ascreen = c->screen_ok ? c->d_ascreen : nullptr;
   a.t = t;
   a.outer_count = (long long)(g.d.n[0] + 2 * NG) * (g.d.n[1] + 2 * NG) * (g.d.n[2] + 2 * NG) -
                   (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
-  a.nloc = (int)c->p.size() - 1;
-  long long pos = a.outer_count;
-  for (int q = 0; q < a.nloc; ++q) {
-    FillLocal& L = a.loc[q];
+  a.outer_blocks = (int)((a.outer_count + fill_threads() - 1) / fill_threads());
+  int blocks = a.outer_blocks;
+  a.nseg = 0;
+  const int nloc = (int)c->p.size() - 1;
+  // Local-to-Global: the effective-ghost shell of each covered box
+  for (int q = 0; q < nloc; ++q) {
     const Box& bx = c->boxes[q];
-    L.l2g_begin = pos;
-    L.l2g_count = 0;
-    if (!box_empty(bx)) {
-      long long outer = 1, inner = 1;
-      bool any = true;
-      for (int k = 0; k < 3; ++k) {
-        L.shell_lo[k] = bx.lo[k] + c->buffer;
-        L.shell_dim[k] = bx.hi[k] - bx.lo[k] + 1 - 2 * c->buffer;
-        if (L.shell_dim[k] <= 0) any = false;
-        outer *= std::max(L.shell_dim[k], 0);
-        inner *= std::max(L.shell_dim[k] - 2 * NG, 0);
-      }
-      if (any) L.l2g_count = outer - inner;
+    if (box_empty(bx)) continue;
+    int O0[3], O[3];
+    bool any = true;
+    for (int k = 0; k < 3; ++k) {
+      O0[k] = bx.lo[k] + c->buffer;
+      O[k] = bx.hi[k] - bx.lo[k] + 1 - 2 * c->buffer;
+      any = any && O[k] > 0;
     }
-    pos += L.l2g_count;
+    if (!any) continue;
+    const PatchState& L = c->p[q + 1];
+    InterpSeg& S = a.seg[a.nseg++];
+    S.T = g.buf(b);
+    S.gt = g.g;
+    S.tpatch = 0;
+    S.D = L.buf(b);
+    S.gd = L.g;
+    double X0[3], w[3];
+    motion(L.d, t, X0, w);
+    for (int k = 0; k < 3; ++k) S.shift[k] = -X0[k];
+    S.block0 = blocks;
+    blocks += build_segment(S, O0, O, c->P);
   }
-  for (int q = 0; q < a.nloc; ++q) {
-    FillLocal& L = a.loc[q];
-    const PatchState& P = c->p[q + 1];
-    L.Y = P.buf(b);
-    L.g = P.g;
-    double w[3];
-    motion(P.d, t, L.X0, w);
-    L.g2l_begin = pos;
-    L.g2l_count = (long long)(P.d.n[0] + 2 * NG) * (P.d.n[1] + 2 * NG) * (P.d.n[2] + 2 * NG) -
-                  (long long)P.d.n[0] * P.d.n[1] * P.d.n[2];
-    pos += L.g2l_count;
+  // Global-to-Local: the ghost shell of each local patch
+  for (int q = 0; q < nloc; ++q) {
+    const PatchState& L = c->p[q + 1];
+    InterpSeg& S = a.seg[a.nseg++];
+    S.T = L.buf(b);
+    S.gt = L.g;
+    S.tpatch = q + 1;
+    S.D = g.buf(b);
+    S.gd = g.g;
+    double X0[3], w[3];
+    motion(L.d, t, X0, w);
+    for (int k = 0; k < 3; ++k) S.shift[k] = X0[k];
+    const int O0[3] = {-NG, -NG, -NG};
+    const int O[3] = {L.d.n[0] + 2 * NG, L.d.n[1] + 2 * NG, L.d.n[2] + 2 * NG};
+    S.block0 = blocks;
+    blocks += build_segment(S, O0, O, c->P);
   }
-  a.total = pos;
-  a.flags = c->d_flags;
+  a.total_blocks = blocks;
   a.P = c->P;
-  a.buffer = c->buffer;
   a.err = c->d_err;
   a.expo = c->d_expo;
   a.y_buf = b;
   a.reset_buf = reset_buf;
   a.np = (int)c->p.size();
-  if (a.total <= 0) return set_err(MPW_ERR_STATE, "empty ghost fill");
   c->launch_begin(MPW_KERNEL_FILL);
   launch_fill(a, c->stream);
   c->launch_end(MPW_KERNEL_FILL);
@@ -435,6 +526,31 @@ mpw_status ensure_u_exponents(mpw_ctx* c) {
   return MPW_OK;
 }
 
+// FP32 screening data of Gaussian pulses (centre, radius): sqrt(50) widths
+// plus a slack that covers FP32 rounding of coordinates of magnitude up to
+// the largest patch or centre coordinate.
+mpw_status upload_screen(mpw_ctx* c) {
+  c->screen_ok = false;
+  if (c->akind != MPW_ANALYTIC_GAUSS_SUM || c->acount <= 0) return MPW_OK;
+  const double* params = c->aparams.data();
+  double extent = 1.0;
+  for (const auto& P : c->p)
+    for (int a = 0; a < 3; ++a) extent = std::max(extent, std::max(std::fabs(P.d.lo[a]), std::fabs(P.d.hi[a])));
+  for (int q = 0; q < c->acount; ++q)
+    for (int a = 0; a < 3; ++a) extent = std::max(extent, std::fabs(params[5 * q + 2 + a]));
+  c->screen.resize(c->acount);
+  for (int q = 0; q < c->acount; ++q) {
+    const double* g = params + 5 * q;
+    const double R = std::sqrt(50.0) * std::fabs(g[1]) * (1.0 + 1e-5) + 1e-5 * (4.0 * extent);
+    c->screen[q] = make_float4((float)g[2], (float)g[3], (float)g[4], (float)R);
+  }
+  CUDA_TRY(cudaMemcpyAsync(c->d_ascreen, c->screen.data(), sizeof(float4) * c->acount, cudaMemcpyHostToDevice,
+                           c->stream));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  c->screen_ok = true;
+  return MPW_OK;
+}
+
 mpw_status read_error_word(mpw_ctx* c) {
   CUDA_TRY(cudaMemcpyAsync(c->h_err, c->d_err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -477,8 +593,9 @@ mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out) {
   }
   c->d_err = (int*)c->dalloc(256);
   c->d_aparams = (double*)c->dalloc(sizeof(double) * MAX_APARAMS);
+  c->d_ascreen = (float4*)c->dalloc(sizeof(float4) * (MAX_APARAMS / 5 + 1));
   c->d_expo = (int*)c->dalloc(sizeof(int) * MAX_PATCHES * EXP_SLOTS_PER_PATCH);
-  if (!c->d_err || !c->d_aparams || !c->d_expo || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+  if (!c->d_err || !c->d_aparams || !c->d_ascreen || !c->d_expo || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
     mpw_destroy(c);
     return set_err(MPW_ERR_CUDA, "context allocation failed");
   }
@@ -499,6 +616,7 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_flags);
   c->dfree(c->d_err);
   c->dfree(c->d_aparams);
+  c->dfree(c->d_ascreen);
   c->dfree(c->d_expo);
   c->dfree(c->d_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -550,6 +668,7 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
   }
   c->p.push_back(P);
   c->flags_valid = false;
+  if (mpw_status st2 = upload_screen(c)) return st2;
   *patch_id = (int)c->p.size() - 1;
   return MPW_OK;
 }
@@ -574,6 +693,7 @@ mpw_status mpw_set_analytic(mpw_ctx* c, int kind, const double* params, int coun
   c->aparams.assign(params, params + need);
   if (need) CUDA_TRY(cudaMemcpyAsync(c->d_aparams, c->aparams.data(), sizeof(double) * need, cudaMemcpyHostToDevice,
                                      c->stream));
+  if ((st = upload_screen(c))) return st;
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   return MPW_OK;
 }
@@ -586,7 +706,8 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
   for (auto& P : c->p) {
     double X0[3], w[3];
     motion(P.d, t, X0, w);
-    launch_analytic(P.buf(BUF_U), P.g, X0[0], X0[1], X0[2], c->akind, c->acount, c->d_aparams, t, c->stream);
+    launch_analytic(P.buf(BUF_U), P.g, X0[0], X0[1], X0[2], c->akind, c->acount, c->d_aparams,
+                    c->screen_ok ? c->d_ascreen : nullptr, t, c->stream);
     CUDA_TRY(cudaGetLastError());
     P.u_expo_valid = false;
   }

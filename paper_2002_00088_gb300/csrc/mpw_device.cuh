@@ -1,0 +1,197 @@
+// mpw_device.cuh -- device helpers shared by the libmpw kernels: closed-form
+// solutions, 1-D Lagrange weights, the direct tensor-product interpolation and
+// the enumeration of hollow-box shells.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "mpw_internal.cuh"
+
+namespace mpw {
+
+// ---------------------------------------------------------------------------
+// Closed forms (Sec. 3): spherical Gaussian pulse pairs, plane-wave sums and
+// the static harmonic basis.  psi = [g(t+r) - g(t-r)] / (2r) with
+// g(s) = A s exp(-s^2/w^2) solves the wave equation with psi(0) = A
+// exp(-r^2/w^2), Pi(0) = 0; Pi is its time derivative.  Near r = 0 the
+// quotient is replaced by its Taylor expansion g'(t) + r^2 g'''(t)/6.
+__device__ __forceinline__ void gauss_pulse(double A, double w, double r, double t, double& ps, double& pv) {
+  const double a = 1.0 / (w * w);
+  if (r < 1e-5) {
+    const double e = A * exp(-a * t * t), t2 = t * t;
+    const double g1 = e * (1.0 - 2.0 * a * t2);
+    const double g2 = e * (4.0 * a * a * t2 * t - 6.0 * a * t);
+    const double g3 = e * (-6.0 * a + 24.0 * a * a * t2 - 8.0 * a * a * a * t2 * t2);
+    const double g4 = e * (60.0 * a * a * t - 80.0 * a * a * a * t2 * t + 16.0 * a * a * a * a * t2 * t2 * t);
+    ps += g1 + r * r * g3 / 6.0;
+    pv += g2 + r * r * g4 / 6.0;
+  } else {
+    const double sp = t + r, sm = t - r;
+    const double ep = A * exp(-a * sp * sp), em = A * exp(-a * sm * sm);
+    const double inv = 1.0 / (2.0 * r);
+    ps += (ep * sp - em * sm) * inv;
+    pv += (ep * (1.0 - 2.0 * a * sp * sp) - em * (1.0 - 2.0 * a * sm * sm)) * inv;
+  }
+}
+
+// screen (Gaussian sums only, may be null): per pulse (cx, cy, cz, R) in
+// FP32 with R >= sqrt(50) width plus rounding slack.  When the distance r from
+// the centre exceeds |t| + R, both arguments t +- r are beyond sqrt(50) widths
+// and the pulse adds less than 2e-20 |A| to psi and Pi; such pulses are
+// skipped after a cheap FP32 test instead of two FP64 exponentials.
+__device__ __forceinline__ void closed_form(int kind, const double* __restrict__ P, const float4* __restrict__ screen, int count,
+                            double t, double x, double y, double z, double& ps, double& pv) {
+  ps = 0.0;
+  pv = 0.0;
+  if (kind == 0) {
+    const float xf = (float)x, yf = (float)y, zf = (float)z, tf = fabsf((float)t) * 1.000001f;
+    for (int q = 0; q < count; ++q) {
+      if (screen) {
+        const float4 s = screen[q];
+        const float ex = xf - s.x, ey = yf - s.y, ez = zf - s.z, lim = tf + s.w;
+        if (ex * ex + ey * ey + ez * ez > lim * lim) continue;
+      }
+      const double* g = P + 5 * q;
+      const double dx = x - g[2], dy = y - g[3], dz = z - g[4];
+      gauss_pulse(g[0], g[1], sqrt(dx * dx + dy * dy + dz * dz), t, ps, pv);
+    }
+  } else if (kind == 1) {
+    ps = P[0];
+    for (int q = 0; q < count; ++q) {
+      const double* wv = P + 1 + 5 * q;
+      const double kk = sqrt(wv[1] * wv[1] + wv[2] * wv[2] + wv[3] * wv[3]);
+      double sn, cs;
+      sincos(wv[1] * x + wv[2] * y + wv[3] * z - kk * t + wv[4], &sn, &cs);
+      ps += wv[0] * sn;
+      pv -= wv[0] * kk * cs;
+    }
+  } else {
+    const double basis[14] = {1.0,
+                              x,
+                              y,
+                              z,
+                              x * y,
+                              y * z,
+                              z * x,
+                              x * x - y * y,
+                              y * y - z * z,
+                              x * y * z,
+                              x * (x * x - 3.0 * y * y),
+                              y * (y * y - 3.0 * z * z),
+                              z * (z * z - 3.0 * x * x),
+                              (x * x - y * y) * (x * x - y * y) - 4.0 * x * x * y * y};
+    for (int q = 0; q < count && q < 14; ++q) ps += P[q] * basis[q];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 1-D Lagrange weights of the window that starts two nodes below
+// i_c = floor(s) (Sec. 2.4, Eq. Pijk).  With u = s - i_c and node offsets
+// o_m = m - 2, w_m = prod_{q != m} (u - o_q) / prod_{q != m} (o_m - o_q); the
+// numerators come from prefix and suffix products.
+template <int P>
+__device__ __forceinline__ int lagrange_weights(double s, double* w) {
+  const double fl = floor(s);
+  const double u = s - fl;
+  double d[P], pre[P + 1], suf[P + 1];
+#pragma unroll
+  for (int m = 0; m < P; ++m) d[m] = u - (double)(m - 2);
+  pre[0] = 1.0;
+  suf[P] = 1.0;
+#pragma unroll
+  for (int m = 0; m < P; ++m) pre[m + 1] = pre[m] * d[m];
+#pragma unroll
+  for (int m = P - 1; m >= 0; --m) suf[m] = suf[m + 1] * d[m];
+  if (P == 6) {
+    const double inv[6] = {-1.0 / 120.0, 1.0 / 24.0, -1.0 / 12.0, 1.0 / 12.0, -1.0 / 24.0, 1.0 / 120.0};
+#pragma unroll
+    for (int m = 0; m < P; ++m) w[m] = pre[m] * suf[m + 1] * inv[m];
+  } else {
+    const double inv[5] = {1.0 / 24.0, -1.0 / 6.0, 1.0 / 4.0, -1.0 / 6.0, 1.0 / 24.0};
+#pragma unroll
+    for (int m = 0; m < P; ++m) w[m] = pre[m] * suf[m + 1] * inv[m];
+  }
+  return (int)fl - 2;
+}
+
+// Tensor-product interpolation of both fields of a donor box at the numeric
+// position (x, y, z).  The window must lie inside the donor interior; returns
+// false (point skipped) otherwise.
+template <int P>
+__device__ __forceinline__ bool interp_point(const double* __restrict__ src, const Geom& g, double x, double y, double z,
+                             double& o0, double& o1) {
+  double wx[P], wy[P], wz[P];
+  const int sx = lagrange_weights<P>((x - g.lo[0]) / g.h[0] - 0.5, wx);
+  const int sy = lagrange_weights<P>((y - g.lo[1]) / g.h[1] - 0.5, wy);
+  const int sz = lagrange_weights<P>((z - g.lo[2]) / g.h[2] - 0.5, wz);
+  if (sx < 0 || sy < 0 || sz < 0 || sx + P > g.n[0] || sy + P > g.n[1] || sz + P > g.n[2]) return false;
+  const double* s0 = src;
+  const double* s1 = src + g.vol;
+  double a0 = 0.0, a1 = 0.0;
+#pragma unroll
+  for (int c = 0; c < P; ++c) {
+    double b0 = 0.0, b1 = 0.0;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      const long long row = g.at(sx, sy + b, sz + c);
+      double r0 = 0.0, r1 = 0.0;
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        r0 = fma(wx[a], s0[row + a], r0);
+        r1 = fma(wx[a], s1[row + a], r1);
+      }
+      b0 = fma(wy[b], r0, b0);
+      b1 = fma(wy[b], r1, b1);
+    }
+    a0 = fma(wz[c], b0, a0);
+    a1 = fma(wz[c], b1, a1);
+  }
+  o0 = a0;
+  o1 = a1;
+  return true;
+}
+
+
+// Maps idx in [0, Ox*Oy*Oz - Ix*Iy*Iz) onto the points of the hollow box of
+// outer extent O whose walls are th thick (I = max(O - 2 th, 0)).
+__device__ __forceinline__ void shell_point(long long idx, const int O[3], int th, int& x, int& y, int& z) {
+  const int Ix = max(O[0] - 2 * th, 0), Iy = max(O[1] - 2 * th, 0), Iz = max(O[2] - 2 * th, 0);
+  const long long pxy = (long long)O[0] * O[1];
+  const long long nz = pxy * (O[2] - Iz);
+  if (idx < nz) {
+    const int zs = (int)(idx / pxy);
+    const long long r = idx - (long long)zs * pxy;
+    z = zs < th ? zs : zs + Iz;
+    y = (int)(r / O[0]);
+    x = (int)(r - (long long)y * O[0]);
+    return;
+  }
+  idx -= nz;
+  const long long rowsy = (long long)O[0] * (O[1] - Iy);
+  const long long ny = rowsy * Iz;
+  if (idx < ny) {
+    const int zz = (int)(idx / rowsy);
+    const long long r = idx - (long long)zz * rowsy;
+    z = th + zz;
+    const int ys = (int)(r / O[0]);
+    x = (int)(r - (long long)ys * O[0]);
+    y = ys < th ? ys : ys + Iy;
+    return;
+  }
+  idx -= ny;
+  const int wx = O[0] - Ix;
+  const long long per_z = (long long)wx * Iy;
+  const int zz = (int)(idx / per_z);
+  const long long r = idx - (long long)zz * per_z;
+  z = th + zz;
+  const int yy = (int)(r / wx);
+  const int xs = (int)(r - (long long)yy * wx);
+  y = th + yy;
+  x = xs < th ? xs : xs + Ix;
+}
+
+__device__ __forceinline__ int wrap_index(int i, int n) { return ((i % n) + n) % n; }
+
+}  // namespace mpw

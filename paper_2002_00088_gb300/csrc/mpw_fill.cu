@@ -1,0 +1,237 @@
+// mpw_fill.cu -- ghost-zone fill of one RK4 substage (Sec. 2.4), one launch:
+//   * the global outer ghost shell: analytic closed form at the substage time
+//     (Sec. 3) or periodic wrap -- one thread per point;
+//   * Local-to-Global (Sec. 2.4.2): the global effective-ghost shell under each
+//     local patch, interpolated from that patch;
+//   * Global-to-Local (Sec. 2.4.1): every local ghost shell, interpolated from
+//     the global patch.
+// The three target sets are disjoint and each reads only data the others do
+// not write (the buffer makes every interpolation donor a live cell).
+//
+// Interpolation is the tensor-product Lagrange sum of Eq. (Pijk).  Under
+// rigid translation the three 1-D weight sets of a target depend only on its
+// index along the respective axis, so the sum factors: a CTA takes a tile of
+// targets that is a box, stages the donor block that the tile's windows cover
+// in shared memory and contracts x, then y, then z (separable passes).  A
+// tile whose donor block exceeds the shared-memory budget or the donor
+// interior is evaluated point by point with the direct sum instead.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+
+#include "mpw_device.cuh"
+#include "mpw_fixed.cuh"
+#include "mpw_internal.cuh"
+
+namespace mpw {
+
+// shared-memory budget of one CTA of the separable path, in doubles (one
+// field at a time): donor block, x-contracted block, xy-contracted block
+constexpr int CAP_D = 4096;
+constexpr int CAP_R1 = 2560;
+constexpr int CAP_R2 = 2048;
+constexpr int MAXT = 32;  // largest tile extent along an axis
+constexpr int FILL_THREADS = 256;
+constexpr size_t FILL_SMEM = sizeof(double) * (CAP_D + CAP_R1 + CAP_R2 + 3 * MAXT * 6) + sizeof(int) * 3 * MAXT;
+
+namespace {
+
+
+// Warp- then CTA-level maximum of two exponents, reported with one atomicMax
+// per field by the first thread.
+__device__ void report_block_max(int* slot2, int e0, int e1) {
+  __shared__ int red[2];
+  if (threadIdx.x == 0) red[0] = red[1] = 0;
+  __syncthreads();
+  e0 = __reduce_max_sync(0xffffffffu, e0);
+  e1 = __reduce_max_sync(0xffffffffu, e1);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&red[0], e0);
+    atomicMax(&red[1], e1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (red[0]) atomicMax(&slot2[0], red[0]);
+    if (red[1]) atomicMax(&slot2[1], red[1]);
+  }
+}
+
+// Position of target index i along axis a in the donor's index units.
+__device__ __forceinline__ double donor_index(const InterpSeg& S, int a, int i) {
+  return ((S.gt.lo[a] + (i + 0.5) * S.gt.h[a] + S.shift[a]) - S.gd.lo[a]) / S.gd.h[a] - 0.5;
+}
+
+template <int P>
+__device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], double* sm) {
+  double* D = sm;
+  double* R1 = D + CAP_D;
+  double* R2 = R1 + CAP_R1;
+  double* W = R2 + CAP_R2;                 // [3][MAXT][6]
+  int* WS = reinterpret_cast<int*>(W + 3 * MAXT * 6);  // [3][MAXT] window starts
+  const int tid = threadIdx.x;
+  // 1-D weights of every target index of the tile, per axis
+  for (int e = tid; e < T[0] + T[1] + T[2]; e += FILL_THREADS) {
+    const int a = e < T[0] ? 0 : (e < T[0] + T[1] ? 1 : 2);
+    const int k = e - (a == 0 ? 0 : (a == 1 ? T[0] : T[0] + T[1]));
+    double w[P];
+    WS[a * MAXT + k] = lagrange_weights<P>(donor_index(S, a, org[a] + k), w);
+#pragma unroll
+    for (int m = 0; m < P; ++m) W[(a * MAXT + k) * 6 + m] = w[m];
+  }
+  __syncthreads();
+  int D0[3], Dn[3];
+  bool inside = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    D0[a] = WS[a * MAXT];
+    Dn[a] = WS[a * MAXT + T[a] - 1] - D0[a] + P;
+    inside = inside && D0[a] >= 0 && D0[a] + Dn[a] <= S.gd.n[a];
+  }
+  const bool fits = Dn[0] * Dn[1] * Dn[2] <= CAP_D && Dn[2] * Dn[1] * T[0] <= CAP_R1 && Dn[2] * T[1] * T[0] <= CAP_R2;
+  int emax[2] = {0, 0};
+  const int ntar = T[0] * T[1] * T[2];
+  if (!(inside && fits)) {
+    // direct tensor sum, point by point (reports uninterpolable points)
+    for (int e = tid; e < ntar; e += FILL_THREADS) {
+      const int x = e % T[0], y = (e / T[0]) % T[1], z = e / (T[0] * T[1]);
+      const int i = org[0] + x, j = org[1] + y, k = org[2] + z;
+      double v0, v1;
+      const double px = S.gt.lo[0] + (i + 0.5) * S.gt.h[0] + S.shift[0];
+      const double py = S.gt.lo[1] + (j + 0.5) * S.gt.h[1] + S.shift[1];
+      const double pz = S.gt.lo[2] + (k + 0.5) * S.gt.h[2] + S.shift[2];
+      if (!interp_point<P>(S.D, S.gd, px, py, pz, v0, v1)) {
+        atomicOr(A.err, ERR_UNFILLED);
+        continue;
+      }
+      const long long c = S.gt.at(i, j, k);
+      S.T[c] = v0;
+      S.T[c + S.gt.vol] = v1;
+      emax[0] = max(emax[0], biased_exponent(v0));
+      emax[1] = max(emax[1], biased_exponent(v1));
+    }
+  } else {
+    const int nD = Dn[0] * Dn[1] * Dn[2];
+    const int n1 = Dn[2] * Dn[1] * T[0];
+    const int n2 = Dn[2] * T[1] * T[0];
+    for (int f = 0; f < 2; ++f) {
+      const double* src = S.D + f * S.gd.vol;
+      // donor block, x fastest (coalesced rows)
+      for (int e = tid; e < nD; e += FILL_THREADS) {
+        const int x = e % Dn[0], y = (e / Dn[0]) % Dn[1], z = e / (Dn[0] * Dn[1]);
+        D[e] = src[S.gd.at(D0[0] + x, D0[1] + y, D0[2] + z)];
+      }
+      __syncthreads();
+      // contract x: R1[dz][dy][tx]
+      for (int e = tid; e < n1; e += FILL_THREADS) {
+        const int tx = e % T[0], r = e / T[0];  // r = dz * Dn[1] + dy
+        const double* row = D + r * Dn[0] + (WS[tx] - D0[0]);
+        const double* w = W + tx * 6;
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < P; ++m) acc = fma(w[m], row[m], acc);
+        R1[e] = acc;
+      }
+      __syncthreads();
+      // contract y: R2[dz][ty][tx]
+      for (int e = tid; e < n2; e += FILL_THREADS) {
+        const int tx = e % T[0], ty = (e / T[0]) % T[1], dz = e / (T[0] * T[1]);
+        const double* col = R1 + (dz * Dn[1] + (WS[MAXT + ty] - D0[1])) * T[0] + tx;
+        const double* w = W + (MAXT + ty) * 6;
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < P; ++m) acc = fma(w[m], col[m * T[0]], acc);
+        R2[e] = acc;
+      }
+      __syncthreads();
+      // contract z and store
+      for (int e = tid; e < ntar; e += FILL_THREADS) {
+        const int tx = e % T[0], ty = (e / T[0]) % T[1], tz = e / (T[0] * T[1]);
+        const double* col = R2 + ((WS[2 * MAXT + tz] - D0[2]) * T[1] + ty) * T[0] + tx;
+        const double* w = W + (2 * MAXT + tz) * 6;
+        double acc = 0.0;
+#pragma unroll
+        for (int m = 0; m < P; ++m) acc = fma(w[m], col[m * T[1] * T[0]], acc);
+        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = acc;
+        emax[f] = max(emax[f], biased_exponent(acc));
+      }
+      __syncthreads();
+    }
+  }
+  report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2, emax[0], emax[1]);
+}
+
+}  // namespace
+
+template <int P>
+__global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ FillArgs A) {
+  extern __shared__ double fill_smem[];
+  if (A.reset_buf >= 0 && blockIdx.x == 0 && threadIdx.x < 2 * A.np)
+    A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
+  const int b = blockIdx.x;
+  if (b < A.outer_blocks) {
+    // global outer ghost shell, one point per thread
+    const long long idx = (long long)b * FILL_THREADS + threadIdx.x;
+    int e0 = 0, e1 = 0;
+    if (idx < A.outer_count) {
+      const int O[3] = {A.gg.n[0] + 2 * NG, A.gg.n[1] + 2 * NG, A.gg.n[2] + 2 * NG};
+      int x, y, z;
+      shell_point(idx, O, NG, x, y, z);
+      const int i = x - NG, j = y - NG, k = z - NG;
+      const long long c = A.gg.at(i, j, k);
+      double w0, w1;
+      if (A.outer_bc == 1) {
+        const long long s =
+            A.gg.at(wrap_index(i, A.gg.n[0]), wrap_index(j, A.gg.n[1]), wrap_index(k, A.gg.n[2]));
+        w0 = A.Yg[s];
+        w1 = A.Yg[s + A.gg.vol];
+      } else {
+        closed_form(A.akind, A.aparams, A.ascreen, A.acount, A.t, A.gg.lo[0] + (i + 0.5) * A.gg.h[0],
+                    A.gg.lo[1] + (j + 0.5) * A.gg.h[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2], w0, w1);
+      }
+      A.Yg[c] = w0;
+      A.Yg[c + A.gg.vol] = w1;
+      e0 = biased_exponent(w0);
+      e1 = biased_exponent(w1);
+    }
+    report_block_max(A.expo + A.y_buf * 2, e0, e1);
+    return;
+  }
+  // interpolation tile: find its segment, slab and position
+  int s = 0;
+  while (s + 1 < A.nseg && b >= A.seg[s + 1].block0) ++s;
+  const InterpSeg& S = A.seg[s];
+  int r = b - S.block0;
+  int sl = 0;
+  while (sl < 5 && r >= S.slab_block0[sl + 1]) ++sl;
+  r -= S.slab_block0[sl];
+  const int nx = S.tn[sl][0], ny = S.tn[sl][1];
+  const int tx = r % nx, ty = (r / nx) % ny, tz = r / (nx * ny);
+  int org[3], T[3];
+  const int tt[3] = {tx, ty, tz};
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    org[a] = S.sb[sl][a] + tt[a] * S.td[sl][a];
+    T[a] = min(S.td[sl][a], S.sb[sl][a] + S.se[sl][a] - org[a]);
+  }
+  interp_tile<P>(A, S, org, T, fill_smem);
+}
+
+void launch_fill(const FillArgs& a, void* stream) {
+  if (a.total_blocks <= 0) return;
+  if (a.P == 6) {
+    cudaFuncSetAttribute(k_fill<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM);
+    k_fill<6><<<a.total_blocks, FILL_THREADS, FILL_SMEM, (cudaStream_t)stream>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_fill<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM);
+    k_fill<5><<<a.total_blocks, FILL_THREADS, FILL_SMEM, (cudaStream_t)stream>>>(a);
+  }
+}
+
+int fill_cap_d() { return CAP_D; }
+int fill_cap_r1() { return CAP_R1; }
+int fill_cap_r2() { return CAP_R2; }
+int fill_max_tile() { return MAXT; }
+int fill_threads() { return FILL_THREADS; }
+
+}  // namespace mpw

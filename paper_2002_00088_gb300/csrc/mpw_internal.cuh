@@ -6,6 +6,8 @@
 // is a multiple of 16 doubles (128 B); the interior cell i = 0 sits at column
 // XOFF = 4 (32 B aligned), the ghost cells i = -3..-1 at columns 1..3.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace mpw {
@@ -65,14 +67,25 @@ struct RhsArgs {
 };
 
 // ---------------------------------------------------------------- fill
-struct FillLocal {
-  double* Y;          // this patch's stage buffer (psi; Pi at +vol)
-  Geom g;
-  double X0[3];       // map at the substage time
-  long long g2l_begin, g2l_count;   // its ghost shell
-  long long l2g_begin, l2g_count;   // global effective-ghost shell under it
-  int shell_lo[3], shell_dim[3];    // outer box of that shell (global indices) and extents
+// One interpolation target set: the hollow box shell (walls NG thick) of a
+// target patch, filled from a donor patch.  The shell is cut into six slabs
+// (z-, z+, y-, y+, x-, x+), each tiled by boxes of td targets.
+struct InterpSeg {
+  double* T;           // target buffer (psi; Pi at +vol)
+  Geom gt;
+  int tpatch;          // target patch id (exponent slots)
+  const double* D;     // donor buffer (psi; Pi at +vol)
+  Geom gd;
+  double shift[3];     // X0_target - X0_donor at the substage time
+  int sb[6][3];        // slab origin (target indices)
+  int se[6][3];        // slab extent
+  int td[6][3];        // tile extent
+  int tn[6][2];        // tiles along x and y of each slab (z follows)
+  int slab_block0[6];  // first CTA of each slab, relative to block0
+  int block0;          // first CTA of the segment
 };
+
+constexpr int MAX_SEGS = 2 * (MAX_PATCHES - 1);
 
 struct FillArgs {
   double* Yg;          // global stage buffer
@@ -80,19 +93,19 @@ struct FillArgs {
   int outer_bc;        // 0 analytic, 1 periodic
   int akind, acount;
   const double* aparams;
+  const float4* ascreen;  // FP32 screening data of Gaussian pulses (or null)
   double t;
   long long outer_count;
-  int nloc;
-  FillLocal loc[MAX_PATCHES];
-  const uint8_t* flags;
+  int outer_blocks;
+  int nseg;
+  InterpSeg seg[MAX_SEGS];
   int P;
-  int buffer;
-  long long total;
   int* err;
   int* expo;
   int y_buf;           // buffer being filled (its exponent slots receive the ghost values)
   int reset_buf;       // buffer whose exponent slots are cleared (the next stage's output), or -1
   int np;
+  int total_blocks;
 };
 
 // ---------------------------------------------------------------- flags
@@ -117,9 +130,14 @@ struct FlagArgs {
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
 void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);
 void launch_fill(const FillArgs& a, void* stream);
+int fill_cap_d();
+int fill_cap_r1();
+int fill_cap_r2();
+int fill_max_tile();
+int fill_threads();
 void launch_flags(const FlagArgs& a, void* stream);
 void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
-                     const double* aparams, double t, void* stream);
+                     const double* aparams, const float4* screen, double t, void* stream);
 void launch_pack(const double* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags,
                  void* stream);
 void launch_unpack(double* buf, const Geom& g, const double* d0, const double* d1, void* stream);

@@ -83,7 +83,7 @@ __device__ __forceinline__ int slot(int patch, int buf, int field) {
 }  // namespace
 
 template <int TX, int TY, bool FIXED>
-__global__ void __launch_bounds__(TX* TY) k_rhs(const __grid_constant__ RhsArgs A) {
+__global__ void __launch_bounds__(TX* TY, 2) k_rhs(const __grid_constant__ RhsArgs A) {
   __shared__ long long sm[2][TY + 6][TX + 6];
   __shared__ Terms T;
   const int b = blockIdx.x;
@@ -152,26 +152,63 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const __grid_constant__ RhsArgs 
   const bool h_ok = hi_ >= -NG && hi_ < g.n[0] + NG && hj >= -NG && hj < g.n[1] + NG;
   constexpr int SY = TX + 6;
   int emax_s = 0, emax_p = 0;
+  // software pipeline: the raw values of plane z+3 (own column) and of the
+  // halo of plane z are loaded one iteration ahead
+  double nx_s = 0.0, nx_p = 0.0, nh_s = 0.0, nh_p = 0.0;
+  if (in_box && z0 < z1) {
+    const long long c = g.at(i, j, z0 + NG);
+    nx_s = Ys[c];
+    nx_p = Yp[c];
+  }
+  if (h_ok && z0 < z1) {
+    const long long c = g.at(hi_, hj, z0);
+    nh_s = Ys[c];
+    nh_p = Yp[c];
+  }
   for (int z = z0; z < z1; ++z) {
-    if (in_box) {
-      const long long c = g.at(i, j, z + NG);
-      qs[6] = load(Ys, c, Es);
-      qp[6] = load(Yp, c, Ep);
+    const long long cz = g.at(i, j, z);
+    // operands of the stage combination and the cover flag, issued early
+    double ua_s = 0.0, ua_p = 0.0, ub_s = 0.0, ub_p = 0.0;
+    int fl = FLAG_LIVE;
+    if (in_xy) {
+      if (A.stage == 0) {
+        ua_s = Ys[cz];
+        ua_p = Yp[cz];
+      } else {
+        ub_s = Pt.ACC[cz];
+        ub_p = Pt.ACC[cz + g.vol];
+        if (A.stage != 3) {
+          ua_s = Pt.U[cz];
+          ua_p = Pt.U[cz + g.vol];
+        }
+      }
+      if (check_flags) fl = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
+    }
+    const long long hs_v = fx ? to_fixed(nh_s, Es) : __double_as_longlong(nh_s);
+    const long long hp_v = fx ? to_fixed(nh_p, Ep) : __double_as_longlong(nh_p);
+    qs[6] = fx ? to_fixed(nx_s, Es) : __double_as_longlong(nx_s);
+    qp[6] = fx ? to_fixed(nx_p, Ep) : __double_as_longlong(nx_p);
+    if (z + 1 < z1) {
+      if (in_box) {
+        const long long c = g.at(i, j, z + 1 + NG);
+        nx_s = Ys[c];
+        nx_p = Yp[c];
+      }
+      if (h_ok) {
+        const long long c = g.at(hi_, hj, z + 1);
+        nh_s = Ys[c];
+        nh_p = Yp[c];
+      }
     }
     __syncthreads();
     sm[0][lj + 3][li + 3] = qs[3];
     sm[1][lj + 3][li + 3] = qp[3];
     if (h_ok) {
-      const long long c = g.at(hi_, hj, z);
-      sm[0][hsj][hsi] = load(Ys, c, Es);
-      sm[1][hsj][hsi] = load(Yp, c, Ep);
+      sm[0][hsj][hsi] = hs_v;
+      sm[1][hsj][hsi] = hp_v;
     }
     __syncthreads();
-    bool live = in_xy;
-    if (live && check_flags) {
-      const int f = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
-      live = (f == FLAG_LIVE) || (f == FLAG_REVIVED);
-    }
+    const bool live = in_xy && (fl == FLAG_LIVE || fl == FLAG_REVIVED);
     if (live) {
       const long long* rs = &sm[0][lj + 3][li + 3];
       const long long* rp = &sm[1][lj + 3][li + 3];
@@ -245,18 +282,16 @@ __global__ void __launch_bounds__(TX* TY) k_rhs(const __grid_constant__ RhsArgs 
         }
       }
       // ---- RK4 stage combination (FP64)
-      const long long c = g.at(i, j, z);
+      const long long c = cz;
       double os, op;
       if (A.stage == 3) {
-        os = fma(A.alpha, Ks, Pt.ACC[c]);
-        op = fma(A.alpha, Kp, Pt.ACC[c + g.vol]);
+        os = fma(A.alpha, Ks, ub_s);
+        op = fma(A.alpha, Kp, ub_p);
       } else {
-        const double us = A.stage == 0 ? Ys[c] : Pt.U[c];
-        const double up = A.stage == 0 ? Yp[c] : Pt.U[c + g.vol];
-        const double as = A.stage == 0 ? us : Pt.ACC[c];
-        const double ap = A.stage == 0 ? up : Pt.ACC[c + g.vol];
-        os = fma(A.alpha, Ks, us);
-        op = fma(A.alpha, Kp, up);
+        const double as = A.stage == 0 ? ua_s : ub_s;
+        const double ap = A.stage == 0 ? ua_p : ub_p;
+        os = fma(A.alpha, Ks, ua_s);
+        op = fma(A.alpha, Kp, ua_p);
         Pt.ACC[c] = fma(A.beta, Ks, as);
         Pt.ACC[c + g.vol] = fma(A.beta, Kp, ap);
       }
