@@ -280,6 +280,8 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   a.flags = c->d_flags;
   for (int k = 0; k < 3; ++k) a.n[k] = g.d.n[k];
   a.nloc = (int)c->p.size() - 1;
+  const std::vector<Box> old_boxes = c->boxes;
+  const bool restrict_cells = c->flags_valid && (int)old_boxes.size() == a.nloc;
   c->boxes.assign(a.nloc, Box{});
   for (int q = 0; q < a.nloc; ++q) {
     const PatchState& L = c->p[q + 1];
@@ -289,6 +291,55 @@ mpw_status run_flags(mpw_ctx* c, double t) {
     a.gl[q] = L.g;
     double w[3];
     motion(L.d, t, a.X0[q], w);
+  }
+  // With valid flags only cells inside an old or a new covered box can change:
+  // visit the bounding box of each pair, merging regions until disjoint.
+  a.nreg = 0;
+  if (restrict_cells) {
+    std::vector<Box> reg;
+    for (int q = 0; q < a.nloc; ++q) {
+      const Box& o = old_boxes[q];
+      const Box& nw = c->boxes[q];
+      Box r{};
+      bool any = false;
+      for (const Box* bx : {&o, &nw}) {
+        if (box_empty(*bx)) continue;
+        for (int k = 0; k < 3; ++k) {
+          r.lo[k] = any ? std::min(r.lo[k], bx->lo[k]) : bx->lo[k];
+          r.hi[k] = any ? std::max(r.hi[k], bx->hi[k]) : bx->hi[k];
+        }
+        any = true;
+      }
+      if (any) reg.push_back(r);
+    }
+    for (bool merged = true; merged;) {
+      merged = false;
+      for (size_t x = 0; x < reg.size() && !merged; ++x)
+        for (size_t y = x + 1; y < reg.size() && !merged; ++y) {
+          bool overlap = true;
+          for (int k = 0; k < 3; ++k) overlap = overlap && reg[x].lo[k] <= reg[y].hi[k] && reg[y].lo[k] <= reg[x].hi[k];
+          if (!overlap) continue;
+          for (int k = 0; k < 3; ++k) {
+            reg[x].lo[k] = std::min(reg[x].lo[k], reg[y].lo[k]);
+            reg[x].hi[k] = std::max(reg[x].hi[k], reg[y].hi[k]);
+          }
+          reg.erase(reg.begin() + y);
+          merged = true;
+        }
+    }
+    long long pos = 0;
+    for (size_t q = 0; q < reg.size(); ++q) {
+      a.reg[q] = reg[q];
+      a.reg_begin[q] = pos;
+      pos += (long long)(reg[q].hi[0] - reg[q].lo[0] + 1) * (reg[q].hi[1] - reg[q].lo[1] + 1) *
+             (reg[q].hi[2] - reg[q].lo[2] + 1);
+    }
+    a.reg_begin[reg.size()] = pos;
+    a.nreg = (int)reg.size();
+    if (a.nreg == 0) {  // nothing covered before or now: no flag can change
+      c->flags_valid = true;
+      return MPW_OK;
+    }
   }
   a.buffer = c->buffer;
   a.old_valid = c->flags_valid ? 1 : 0;

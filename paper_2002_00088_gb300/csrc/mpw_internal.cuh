@@ -124,6 +124,11 @@ struct FlagArgs {
   int P;
   int* err;
   int* expo;
+  // cells to visit: disjoint boxes (global indices) covering every cell whose
+  // flag can change (the old and new covered boxes); nreg = 0 means all cells
+  int nreg;
+  Box reg[MAX_PATCHES];
+  long long reg_begin[MAX_PATCHES + 1];
 };
 
 // ---------------------------------------------------------------- host entry points of the kernels
@@ -142,7 +147,14 @@ void launch_pack(const double* buf, const Geom& g, double* d0, double* d1, int p
                  void* stream);
 void launch_unpack(double* buf, const Geom& g, const double* d0, const double* d1, void* stream);
 
+#ifndef MPW_RHS_TY
+#define MPW_RHS_TY 8
+#endif
+#ifndef MPW_RHS_MINB
+#define MPW_RHS_MINB 2
+#endif
 constexpr int RHS_TX = 32;
-constexpr int RHS_TY = 8;
+constexpr int RHS_TY = MPW_RHS_TY;      // tile rows (threads per CTA = 32 x RHS_TY)
+constexpr int RHS_MIN_BLOCKS = MPW_RHS_MINB;  // CTAs per SM the register budget is sized for
 
 }  // namespace mpw

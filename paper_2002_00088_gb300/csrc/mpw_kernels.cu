@@ -21,13 +21,28 @@ namespace mpw {
 // REVIVED: u_n there is interpolated from the owning local patch at t_n.
 template <int P>
 __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs A) {
-  const long long N = (long long)A.n[0] * A.n[1] * A.n[2];
-  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (idx >= N) return;
-  const int i = (int)(idx % A.n[0]);
-  const long long r = idx / A.n[0];
-  const int j = (int)(r % A.n[1]);
-  const int k = (int)(r / A.n[1]);
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  int i, j, k;
+  if (A.nreg == 0) {
+    const long long N = (long long)A.n[0] * A.n[1] * A.n[2];
+    if (idx >= N) return;
+    i = (int)(idx % A.n[0]);
+    const long long r = idx / A.n[0];
+    j = (int)(r % A.n[1]);
+    k = (int)(r / A.n[1]);
+  } else {
+    if (idx >= A.reg_begin[A.nreg]) return;
+    int g = 0;
+    while (idx >= A.reg_begin[g + 1]) ++g;
+    idx -= A.reg_begin[g];
+    const Box& R = A.reg[g];
+    const int w0 = R.hi[0] - R.lo[0] + 1, w1 = R.hi[1] - R.lo[1] + 1;
+    i = R.lo[0] + (int)(idx % w0);
+    const long long r = idx / w0;
+    j = R.lo[1] + (int)(r % w1);
+    k = R.lo[2] + (int)(r / w1);
+    idx = ((long long)k * A.n[1] + j) * A.n[0] + i;
+  }
   int owner = 0, d = 0;
   for (int q = 0; q < A.nloc; ++q) {
     const Box& b = A.box[q];
@@ -65,7 +80,8 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
 }
 
 void launch_flags(const FlagArgs& a, void* stream) {
-  const long long N = (long long)a.n[0] * a.n[1] * a.n[2];
+  const long long N = a.nreg ? a.reg_begin[a.nreg] : (long long)a.n[0] * a.n[1] * a.n[2];
+  if (N <= 0) return;
   const unsigned blocks = (unsigned)((N + 255) / 256);
   if (a.P == 6)
     k_flags<6><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);

@@ -83,7 +83,7 @@ __device__ __forceinline__ int slot(int patch, int buf, int field) {
 }  // namespace
 
 template <int TX, int TY, bool FIXED>
-__global__ void __launch_bounds__(TX* TY, 2) k_rhs(const __grid_constant__ RhsArgs A) {
+__global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_constant__ RhsArgs A) {
   __shared__ long long sm[2][TY + 6][TX + 6];
   __shared__ Terms T;
   const int b = blockIdx.x;
