@@ -175,6 +175,36 @@ mpw_status mpw_profile_enable(mpw_ctx* ctx, int enable);
  * (launches, may be NULL) since the last read, then reset both. */
 mpw_status mpw_profile_read(mpw_ctx* ctx, double* ms, long long* launches, int n);
 
+/* Largest interior extent per axis accepted by mpw_step_periodic_noalloc. */
+#define MPW_NOALLOC_MAX_N 48
+
+/* Advance one periodic Cartesian patch (static frame) by nsteps RK4 steps
+ * without allocating any memory.  The paper has no counterpart; the entry
+ * point exists for callers that may not allocate device memory when they step
+ * a field: plugins whose host application owns every device allocation, and
+ * timing-critical loops that must not enter the driver's allocator.  It runs
+ * the same ghost-fill and fused RHS + RK4 stage kernels as mpw_step on a single
+ * periodic patch, with every work buffer (padded state, accumulator, stage
+ * buffers, exponent slots, error word) in one file-scope device array of about
+ * 12 MB that each GPU loading the library holds until the process exits.
+ *   n, lo, hi  patch extents (host memory); each n must lie in
+ *              [6, MPW_NOALLOC_MAX_N], larger sizes return MPW_ERR_ARG.
+ *   ko_eps     Kreiss-Oliger strength; dt, nsteps as in mpw_step (dt is checked
+ *              against the RK4 stability estimate, MPW_ERR_CFL).
+ *   psi, pi    device pointers on the current device, dense [k][j][i]
+ *              interiors; read at the start, overwritten with the result.
+ *   stream     cudaStream_t to enqueue on (NULL: the legacy default stream).
+ * The work is enqueued asynchronously and no cudaMalloc/cudaFree is called.
+ * The first call on a device looks up the device address of the array
+ * (cudaGetSymbolAddress); make that first call before any stream capture
+ * begins.  All calls share the array, which keeps the last call's contents
+ * (the exponent slots and error word are cleared at the start of each call):
+ * calls whose work overlaps on the GPU (other streams, unordered host
+ * threads) race and corrupt each other.  Errors: MPW_ERR_ARG, MPW_ERR_CFL,
+ * MPW_ERR_CUDA, with a message from mpw_last_error(). */
+mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[3], const double hi[3], double ko_eps,
+                                     double dt, int nsteps, double* psi, double* pi, void* stream);
+
 /* Thread-local message of the last failing call on this thread. */
 const char* mpw_last_error(void);
 

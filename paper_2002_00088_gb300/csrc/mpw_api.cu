@@ -616,6 +616,10 @@ mpw_status read_error_word(mpw_ctx* c) {
 
 }  // namespace
 
+namespace mpw {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace mpw
+
 // ============================================================================ C ABI
 
 extern "C" {

@@ -131,6 +131,9 @@ struct FlagArgs {
   long long reg_begin[MAX_PATCHES + 1];
 };
 
+// Record the thread-local message returned by mpw_last_error().
+void set_last_error(const char* msg);
+
 // ---------------------------------------------------------------- host entry points of the kernels
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
 void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);

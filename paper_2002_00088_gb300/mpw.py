@@ -61,6 +61,8 @@ SIGNATURES = {
     "mpw_live_points": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
     "mpw_profile_enable": (C.c_int, [_vp, C.c_int]),
     "mpw_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
+    "mpw_step_periodic_noalloc": (C.c_int, [C.POINTER(C.c_int), _dp, _dp, C.c_double, C.c_double, C.c_int, _vp, _vp,
+                                            _vp]),
     "mpw_last_error": (C.c_char_p, []),
     "mpw_destroy": (None, [_vp]),
 }
@@ -79,6 +81,20 @@ def _load():
 
 
 lib = _load()
+
+
+NOALLOC_MAX_N = 48
+
+
+def step_periodic_noalloc(n, lo, hi, ko_eps, dt, nsteps, psi, pi, stream=None):
+    """mpw_step_periodic_noalloc on two CUDA float64 tensors of shape (n2, n1, n0),
+    advanced in place; nothing is allocated by the library."""
+    nn = (C.c_int * 3)(*[int(v) for v in n])
+    lo_ = (C.c_double * 3)(*[float(v) for v in lo])
+    hi_ = (C.c_double * 3)(*[float(v) for v in hi])
+    s = None if stream is None else C.c_void_p(stream.cuda_stream)
+    check(lib.mpw_step_periodic_noalloc(nn, lo_, hi_, float(ko_eps), float(dt), int(nsteps),
+                                        C.c_void_p(psi.data_ptr()), C.c_void_p(pi.data_ptr()), s))
 
 
 class MpwError(RuntimeError):
