@@ -63,8 +63,10 @@ struct mpw_ctx {
   int akind = -1, acount = 0;
   std::vector<double> aparams;
   std::vector<float4> screen;
+  std::vector<double> apre;
   double* d_aparams = nullptr;
   float4* d_ascreen = nullptr;  // FP32 screening data of Gaussian pulses
+  double* d_apre = nullptr;     // 1/width^2 of every Gaussian pulse
   bool screen_ok = false;
   uint8_t* d_flags = nullptr;
   bool flags_valid = false;
@@ -446,6 +448,7 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   a.acount = c->acount;
   a.aparams = c->d_aparams;
   a.ascreen = c->screen_ok ? c->d_ascreen : nullptr;
+  a.apre = c->screen_ok ? c->d_apre : nullptr;
   a.t = t;
   a.outer_count = (long long)(g.d.n[0] + 2 * NG) * (g.d.n[1] + 2 * NG) * (g.d.n[2] + 2 * NG) -
                   (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
@@ -590,12 +593,16 @@ mpw_status upload_screen(mpw_ctx* c) {
   for (int q = 0; q < c->acount; ++q)
     for (int a = 0; a < 3; ++a) extent = std::max(extent, std::fabs(params[5 * q + 2 + a]));
   c->screen.resize(c->acount);
+  c->apre.resize(c->acount);
   for (int q = 0; q < c->acount; ++q) {
     const double* g = params + 5 * q;
     const double R = std::sqrt(50.0) * std::fabs(g[1]) * (1.0 + 1e-5) + 1e-5 * (4.0 * extent);
     c->screen[q] = make_float4((float)g[2], (float)g[3], (float)g[4], (float)R);
+    c->apre[q] = 1.0 / (g[1] * g[1]);
   }
   CUDA_TRY(cudaMemcpyAsync(c->d_ascreen, c->screen.data(), sizeof(float4) * c->acount, cudaMemcpyHostToDevice,
+                           c->stream));
+  CUDA_TRY(cudaMemcpyAsync(c->d_apre, c->apre.data(), sizeof(double) * c->acount, cudaMemcpyHostToDevice,
                            c->stream));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   c->screen_ok = true;
@@ -649,8 +656,9 @@ mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out) {
   c->d_err = (int*)c->dalloc(256);
   c->d_aparams = (double*)c->dalloc(sizeof(double) * MAX_APARAMS);
   c->d_ascreen = (float4*)c->dalloc(sizeof(float4) * (MAX_APARAMS / 5 + 1));
+  c->d_apre = (double*)c->dalloc(sizeof(double) * (MAX_APARAMS / 5 + 1));
   c->d_expo = (int*)c->dalloc(sizeof(int) * MAX_PATCHES * EXP_SLOTS_PER_PATCH);
-  if (!c->d_err || !c->d_aparams || !c->d_ascreen || !c->d_expo || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+  if (!c->d_err || !c->d_aparams || !c->d_ascreen || !c->d_apre || !c->d_expo || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
     mpw_destroy(c);
     return set_err(MPW_ERR_CUDA, "context allocation failed");
   }
@@ -672,6 +680,7 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_err);
   c->dfree(c->d_aparams);
   c->dfree(c->d_ascreen);
+  c->dfree(c->d_apre);
   c->dfree(c->d_expo);
   c->dfree(c->d_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
@@ -762,7 +771,7 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
     double X0[3], w[3];
     motion(P.d, t, X0, w);
     launch_analytic(P.buf(BUF_U), P.g, X0[0], X0[1], X0[2], c->akind, c->acount, c->d_aparams,
-                    c->screen_ok ? c->d_ascreen : nullptr, t, c->stream);
+                    c->screen_ok ? c->d_ascreen : nullptr, c->screen_ok ? c->d_apre : nullptr, t, c->stream);
     CUDA_TRY(cudaGetLastError());
     P.u_expo_valid = false;
   }

@@ -186,7 +186,7 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
         w0 = A.Yg[s];
         w1 = A.Yg[s + A.gg.vol];
       } else {
-        closed_form(A.akind, A.aparams, A.ascreen, A.acount, A.t, A.gg.lo[0] + (i + 0.5) * A.gg.h[0],
+        closed_form(A.akind, A.aparams, A.ascreen, A.apre, A.acount, A.t, A.gg.lo[0] + (i + 0.5) * A.gg.h[0],
                     A.gg.lo[1] + (j + 0.5) * A.gg.h[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2], w0, w1);
       }
       A.Yg[c] = w0;

@@ -94,6 +94,7 @@ struct FillArgs {
   int akind, acount;
   const double* aparams;
   const float4* ascreen;  // FP32 screening data of Gaussian pulses (or null)
+  const double* apre;     // 1/width^2 of every Gaussian pulse (or null)
   double t;
   long long outer_count;
   int outer_blocks;
@@ -145,7 +146,7 @@ int fill_max_tile();
 int fill_threads();
 void launch_flags(const FlagArgs& a, void* stream);
 void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
-                     const double* aparams, const float4* screen, double t, void* stream);
+                     const double* aparams, const float4* screen, const double* apre, double t, void* stream);
 void launch_pack(const double* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags,
                  void* stream);
 void launch_unpack(double* buf, const Geom& g, const double* d0, const double* d1, void* stream);

@@ -92,7 +92,8 @@ void launch_flags(const FlagArgs& a, void* stream) {
 // ---------------------------------------------------------------------------
 // Interior <- closed form at time t (positions X_B = numeric + X0).
 __global__ void k_analytic(double* buf, const Geom g, double X0x, double X0y, double X0z, int akind, int acount,
-                           const double* __restrict__ P, const float4* __restrict__ screen, double t) {
+                           const double* __restrict__ P, const float4* __restrict__ screen,
+                           const double* __restrict__ apre, double t) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= N) return;
@@ -101,7 +102,7 @@ __global__ void k_analytic(double* buf, const Geom g, double X0x, double X0y, do
   const int j = (int)(r % g.n[1]);
   const int k = (int)(r / g.n[1]);
   double ps, pv;
-  closed_form(akind, P, screen, acount, t, g.lo[0] + (i + 0.5) * g.h[0] + X0x, g.lo[1] + (j + 0.5) * g.h[1] + X0y,
+  closed_form(akind, P, screen, apre, acount, t, g.lo[0] + (i + 0.5) * g.h[0] + X0x, g.lo[1] + (j + 0.5) * g.h[1] + X0y,
               g.lo[2] + (k + 0.5) * g.h[2] + X0z, ps, pv);
   const long long c = g.at(i, j, k);
   buf[c] = ps;
@@ -109,10 +110,10 @@ __global__ void k_analytic(double* buf, const Geom g, double X0x, double X0y, do
 }
 
 void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
-                     const double* aparams, const float4* screen, double t, void* stream) {
+                     const double* aparams, const float4* screen, const double* apre, double t, void* stream) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   k_analytic<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)stream>>>(buf, g, X0x, X0y, X0z, akind, acount,
-                                                                            aparams, screen, t);
+                                                                            aparams, screen, apre, t);
 }
 
 // Padded buffer -> dense array (interior, or the whole padded box).  With
