@@ -50,6 +50,8 @@ struct PatchState {
   Geom g;
   bool u_expo_valid = false;  // exponent slots of u track its live values
   double* base = nullptr;     // 4 buffers x 2 fields x vol doubles
+  CUtensorMap tile_map[4];    // RHS input tiles of each buffer (TMA)
+  CUtensorMap point_map[2];   // RHS stage operands: u, ACC (TMA)
   double* buf(int b) const { return base + (size_t)b * 2 * (size_t)g.vol; }
 };
 
@@ -528,10 +530,14 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
   a.nbox = (int)c->boxes.size();
   for (int q = 0; q < a.nbox; ++q) a.box[q] = c->boxes[q];
   a.expo = c->d_expo;
+  a.err = c->d_err;
   int blocks = 0;
   for (int q = 0; q < a.np; ++q) {
     const PatchState& P = c->p[q];
     RhsPatch& R = a.p[q];
+    R.ymap = P.tile_map[in_buf[l]];
+    R.umap = P.point_map[0];
+    R.amap = P.point_map[1];
     R.Y = P.buf(in_buf[l]);
     R.U = P.buf(BUF_U);
     R.ACC = P.buf(BUF_ACC);
@@ -615,6 +621,7 @@ mpw_status read_error_word(mpw_ctx* c) {
   const int e = *c->h_err;
   if (e) {
     CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
+    if (e & ERR_TIMEOUT) return set_err(MPW_ERR_TIMEOUT, "a bounded device wait ran out (error word 0x%x)", e);
     if (e & ERR_UNFILLED) return set_err(MPW_ERR_GHOST_UNFILLED, "a ghost point could not be interpolated");
     return set_err(MPW_ERR_BOUNDS, "device index check failed (error word 0x%x)", e);
   }
@@ -724,6 +731,16 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
   P.base = (double*)c->dalloc(bytes);
   if (!P.base) return set_err(MPW_ERR_CUDA, "allocation of %zu bytes failed", bytes);
   CUDA_TRY(cudaMemsetAsync(P.base, 0, bytes, c->stream));
+  for (int b = 0; b < 4; ++b)
+    if (!encode_rhs_map(&P.tile_map[b], P.buf(b), P.g, true)) {
+      c->dfree(P.base);
+      return set_err(MPW_ERR_CUDA, "tensor map encoding failed");
+    }
+  if (!encode_rhs_map(&P.point_map[0], P.buf(BUF_U), P.g, false) ||
+      !encode_rhs_map(&P.point_map[1], P.buf(BUF_ACC), P.g, false)) {
+    c->dfree(P.base);
+    return set_err(MPW_ERR_CUDA, "tensor map encoding failed");
+  }
   if (d->kind == MPW_PATCH_GLOBAL) {
     const size_t nb = (size_t)d->n[0] * d->n[1] * d->n[2];
     c->d_flags = (uint8_t*)c->dalloc(nb);

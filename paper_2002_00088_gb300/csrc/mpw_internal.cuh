@@ -6,6 +6,7 @@
 // is a multiple of 16 doubles (128 B); the interior cell i = 0 sits at column
 // XOFF = 4 (32 B aligned), the ghost cells i = -3..-1 at columns 1..3.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -19,7 +20,7 @@ constexpr int MAX_APARAMS = 1024;
 
 enum { BUF_U = 0, BUF_ACC = 1, BUF_YA = 2, BUF_YB = 3 };
 enum { FLAG_LIVE = 0, FLAG_GHOST = 1, FLAG_DEAD = 2, FLAG_REVIVED = 3 };
-enum { ERR_UNFILLED = 1, ERR_BOUNDS = 2, ERR_NONFINITE = 4 };
+enum { ERR_UNFILLED = 1, ERR_BOUNDS = 2, ERR_NONFINITE = 4, ERR_TIMEOUT = 8 };
 
 struct Geom {
   int n[3];
@@ -38,7 +39,13 @@ struct Box {
 };
 
 // ---------------------------------------------------------------- K1
+// Tensor maps of one patch buffer for the RHS kernel's TMA loads: `tile`
+// covers a (32+8) x (8+6) x 1 x 2-field box (a column tile with its x/y halo,
+// x start rounded down to a 16-byte boundary), `point` a 32 x 8 x 1 x 2 box.
 struct RhsPatch {
+  CUtensorMap ymap;  // tile map of the stencil input buffer
+  CUtensorMap umap;  // point map of u
+  CUtensorMap amap;  // point map of the accumulator
   const double* Y;   // stencil input (psi; Pi at +vol)
   const double* U;   // u_n
   double* ACC;       // accumulator
@@ -64,6 +71,7 @@ struct RhsArgs {
   int nbox;
   Box box[MAX_PATCHES];
   int* expo;            // tracked maximum biased exponents, [patch][buffer][field]
+  int* err;             // device error word
 };
 
 // ---------------------------------------------------------------- fill
@@ -134,6 +142,12 @@ struct FlagArgs {
 
 // Record the thread-local message returned by mpw_last_error().
 void set_last_error(const char* msg);
+
+// ---------------------------------------------------------------- tensor maps
+// Encode the TMA maps of the RHS kernel for one field buffer (psi at base, Pi
+// at base + vol) of geometry g: box (RHS_TX + 8) x (RHS_TY + 6) ("tile") or
+// RHS_TX x RHS_TY ("point").  Returns false if the driver rejects the map.
+bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool tile);
 
 // ---------------------------------------------------------------- host entry points of the kernels
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);

@@ -91,6 +91,12 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
   if (dt * std::sqrt(lap) > 2.8) return fail(MPW_ERR_CFL, "dt exceeds the RK4 stability estimate");
   double* buf[4];
   for (int b = 0; b < 4; ++b) buf[b] = base + (long long)b * 2 * g.vol;
+  // TMA maps of the scratch buffers (host-side encoding, no allocation)
+  CUtensorMap tile_map[4], point_map[2];
+  for (int b = 0; b < 4; ++b)
+    if (!encode_rhs_map(&tile_map[b], buf[b], g, true)) return fail(MPW_ERR_CUDA, "tensor map encoding failed");
+  if (!encode_rhs_map(&point_map[0], buf[BUF_U], g, false) || !encode_rhs_map(&point_map[1], buf[BUF_ACC], g, false))
+    return fail(MPW_ERR_CUDA, "tensor map encoding failed");
   int* expo = reinterpret_cast<int*>(base + 8 * NOALLOC_MAX_VOL);
   int* err = expo + 32;
   cudaStream_t s = (cudaStream_t)stream;
@@ -128,7 +134,11 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
       r.alpha = alpha[l];
       r.beta = beta[l];
       r.expo = expo;
+      r.err = err;
       RhsPatch& R = r.p[0];
+      R.ymap = tile_map[in_buf[l]];
+      R.umap = point_map[0];
+      R.amap = point_map[1];
       R.Y = buf[in_buf[l]];
       R.U = buf[BUF_U];
       R.ACC = buf[BUF_ACC];

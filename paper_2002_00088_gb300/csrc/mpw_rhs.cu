@@ -11,9 +11,12 @@
 //   stage 2: ACC += dt/3 K,     OUT = U + dt K
 //   stage 3:                    OUT(=U) = ACC + dt/6 K
 //
-// Traversal: a CTA owns a TX x TY column tile and marches zc planes; the z
-// neighbours of its own column live in a 7-deep register queue, the x/y
-// neighbours of the current plane in shared memory (halo 3, star stencil).
+// Traversal: a CTA owns a 32 x 8 column tile and marches zc planes.  The raw
+// input tile of each plane (with its x/y halo) and the stage operands arrive
+// by TMA (cp.async.bulk.tensor) several planes ahead; each value is converted
+// once, the z neighbours of a thread's own column then live in a 7-deep
+// register queue and the x/y neighbours in a small ring of converted planes in
+// shared memory (halo 3, star stencil).
 //
 // Arithmetic (template FIXED):
 //   true  -- stencil inputs are converted once, on load, to exact int64 fixed
@@ -25,6 +28,8 @@
 //            non-finite live value falls back to the FP64 formulas, so NaN and
 //            Inf propagate as in IEEE arithmetic.
 //   false -- native FP64 throughout (the reference GPU path).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -82,17 +87,89 @@ __device__ __forceinline__ int slot(int patch, int buf, int field) {
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// TMA pipeline.  Iteration z of a CTA consumes one ring slot holding the raw
+// tile (with halo) of input plane z+3 and the stage operands u and ACC of
+// plane z; slots are refilled RHS_DEPTH iterations ahead by one elected
+// thread with cp.async.bulk.tensor, completion tracked by one mbarrier per
+// slot.  Every wait is bounded: a wait that runs out sets ERR_TIMEOUT in the
+// error word, the CTA drains its own copies (again bounded) and returns.
+constexpr int RHS_DEPTH = 4;
+constexpr int BOX_X = RHS_TX + 8, BOX_Y = RHS_TY + 6;
+constexpr int TILE_DOUBLES = BOX_X * BOX_Y * 2;
+constexpr int PT_DOUBLES = RHS_TX * RHS_TY * 2;
+constexpr int SLOT_DOUBLES = TILE_DOUBLES + 2 * PT_DOUBLES;  // tile | u | ACC
+constexpr int CONV_PLANE = (RHS_TY + 6) * (RHS_TX + 6);      // one field of a converted plane
+constexpr int CONV_SLOTS = 4;
+constexpr size_t RHS_SMEM = 1024 + sizeof(double) * RHS_DEPTH * SLOT_DOUBLES +
+                            sizeof(long long) * CONV_SLOTS * 2 * CONV_PLANE + 8 * RHS_DEPTH;
+constexpr unsigned WAIT_LIMIT = 1u << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void bar_init(unsigned bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(unsigned bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false if the limit ran out.
+__device__ __forceinline__ bool bar_wait(unsigned bar, unsigned parity) {
+  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (ok) return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int x, int y, int z, int f,
+                                            unsigned bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(bar)
+      : "memory");
+}
+
+// Issue the loads of iteration zz (tile of input plane zz+3, u and ACC of
+// plane zz) into slot s.
+__device__ __forceinline__ void issue_slot(const RhsPatch& Pt, int stage, double* slot, unsigned bar, int i0, int j0,
+                                           int zz) {
+  const unsigned bytes = sizeof(double) * (TILE_DOUBLES + (stage < 3 ? PT_DOUBLES : 0) + (stage > 0 ? PT_DOUBLES : 0));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  bar_expect_tx(bar, bytes);
+  // tile: columns from interior i0 - 4 (padded column i0), rows from interior j0 - 3 (padded row j0)
+  tma_load_4d(smem_u32(slot), &Pt.ymap, i0, j0, zz + 3 + NG, 0, bar);
+  if (stage < 3) tma_load_4d(smem_u32(slot + TILE_DOUBLES), &Pt.umap, i0 + XOFF, j0 + NG, zz + NG, 0, bar);
+  if (stage > 0) tma_load_4d(smem_u32(slot + TILE_DOUBLES + PT_DOUBLES), &Pt.amap, i0 + XOFF, j0 + NG, zz + NG, 0, bar);
+}
+
 template <int TX, int TY, bool FIXED>
 __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_constant__ RhsArgs A) {
-  __shared__ long long sm[2][TY + 6][TX + 6];
+  static_assert(TX == RHS_TX && TY == RHS_TY, "TMA boxes are sized for RHS_TX x RHS_TY tiles");
+  extern __shared__ unsigned char smem_dyn[];
   __shared__ Terms T;
+  __shared__ int s_abort;
+  constexpr int SY = TX + 6;
+  // 1 KB-aligned carve-up of the dynamic shared memory
+  const unsigned long long base = (reinterpret_cast<unsigned long long>(smem_dyn) + 1023ull) & ~1023ull;
+  double* slots = reinterpret_cast<double*>(base);
+  long long* conv = reinterpret_cast<long long*>(slots + RHS_DEPTH * SLOT_DOUBLES);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(conv + CONV_SLOTS * 2 * CONV_PLANE);
   const int b = blockIdx.x;
   int p = 0;
   while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
   const RhsPatch& Pt = A.p[p];
   const Geom& g = Pt.g;
-  if (threadIdx.x == 0)
-    setup_terms(T, Pt, A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 1)], FIXED);
   int lb = b - Pt.block0;
   const int tx = lb % Pt.tiles_x;
   lb /= Pt.tiles_x;
@@ -102,6 +179,17 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   const int i0 = tx * TX, j0 = ty * TY;
   const int i = i0 + li, j = j0 + lj;
   const int z0 = tz * Pt.zc, z1 = min(z0 + Pt.zc, g.n[2]);
+  if (threadIdx.x == 0) {
+    setup_terms(T, Pt, A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 1)], FIXED);
+    s_abort = 0;
+    for (int s = 0; s < RHS_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < RHS_DEPTH && z0 + s < z1; ++s)
+      issue_slot(Pt, A.stage, slots + s * SLOT_DOUBLES, smem_u32(&bars[s]), i0, j0, z0 + s);
   const bool in_box = (i < g.n[0] + NG) && (j < g.n[1] + NG);
   const bool in_xy = (i < g.n[0]) && (j < g.n[1]);
   bool check_flags = false;
@@ -113,105 +201,108 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
         check_flags = true;
     }
   }
-  __syncthreads();
-  const bool fx = FIXED && T.fixed;
-  const int Es = T.Es, Ep = T.Ep;
-  auto load = [&](const double* base, long long c, int E) -> long long {
-    const double v = base[c];
-    return fx ? to_fixed(v, E) : __double_as_longlong(v);
-  };
-  const double* Ys = Pt.Y;
-  const double* Yp = Pt.Y + g.vol;
-  long long qs[7], qp[7];
-#pragma unroll
-  for (int o = 0; o < 6; ++o) {
-    qs[o] = 0;
-    qp[o] = 0;
-    if (in_box) {
-      const long long c = g.at(i, j, z0 - NG + o);
-      qs[o] = load(Ys, c, Es);
-      qp[o] = load(Yp, c, Ep);
-    }
-  }
-  // halo assignment: threads [0, 6 TX) load the y halo, [6 TX, 6 TX + 6 TY) the x halo
+  // halo assignment: threads [0, 6 TX) carry the y halo, [6 TX, 6 TX + 6 TY) the x halo
   const int t = threadIdx.x;
-  int hi_ = -100, hj = -100, hsi = 0, hsj = 0;
+  int hi_ = -100, hj = -100, hoff = 0;
   if (t < 6 * TX) {
     const int rr = t / TX, cc = t % TX;
-    hsj = rr < 3 ? rr : TY + rr;
-    hsi = cc + 3;
+    hoff = (rr < 3 ? rr : TY + rr) * SY + cc + 3;
     hi_ = i0 + cc;
     hj = j0 + (rr < 3 ? rr - 3 : TY + rr - 3);
   } else if (t < 6 * TX + 6 * TY) {
     const int u = t - 6 * TX, rr = u / 6, cc = u % 6;
-    hsj = rr + 3;
-    hsi = cc < 3 ? cc : TX + cc;
+    hoff = (rr + 3) * SY + (cc < 3 ? cc : TX + cc);
     hj = j0 + rr;
     hi_ = i0 + (cc < 3 ? cc - 3 : TX + cc - 3);
   }
   const bool h_ok = hi_ >= -NG && hi_ < g.n[0] + NG && hj >= -NG && hj < g.n[1] + NG;
-  constexpr int SY = TX + 6;
-  int emax_s = 0, emax_p = 0;
-  // software pipeline: the raw values of plane z+3 (own column) and of the
-  // halo of plane z are loaded one iteration ahead
-  double nx_s = 0.0, nx_p = 0.0, nh_s = 0.0, nh_p = 0.0;
-  if (in_box && z0 < z1) {
-    const long long c = g.at(i, j, z0 + NG);
-    nx_s = Ys[c];
-    nx_p = Yp[c];
-  }
-  if (h_ok && z0 < z1) {
-    const long long c = g.at(hi_, hj, z0);
-    nh_s = Ys[c];
-    nh_p = Yp[c];
-  }
-  for (int z = z0; z < z1; ++z) {
-    const long long cz = g.at(i, j, z);
-    // operands of the stage combination and the cover flag, issued early
-    double ua_s = 0.0, ua_p = 0.0, ub_s = 0.0, ub_p = 0.0;
-    int fl = FLAG_LIVE;
-    if (in_xy) {
-      if (A.stage == 0) {
-        ua_s = Ys[cz];
-        ua_p = Yp[cz];
-      } else {
-        ub_s = Pt.ACC[cz];
-        ub_p = Pt.ACC[cz + g.vol];
-        if (A.stage != 3) {
-          ua_s = Pt.U[cz];
-          ua_p = Pt.U[cz + g.vol];
-        }
-      }
-      if (check_flags) fl = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
+  const int own = (lj + 3) * SY + li + 3;
+  // positions in a raw tile slot (x from interior i0 - 4, y from interior j0 - 3)
+  const int own_raw = (lj + 3) * BOX_X + li + 4;
+  const int halo_raw = (hj - j0 + 3) * BOX_X + (hi_ - i0 + 4);
+  const bool fx = FIXED && T.fixed;
+  const int Es = T.Es, Ep = T.Ep;
+  const double* Ys = Pt.Y;
+  const double* Yp = Pt.Y + g.vol;
+  auto cvt = [&](double v, int E) -> long long { return fx ? to_fixed(v, E) : __double_as_longlong(v); };
+  auto conv_of = [&](int zz) -> long long* { return conv + ((zz - z0) & (CONV_SLOTS - 1)) * 2 * CONV_PLANE; };
+  // prologue: planes z0-3 .. z0+2 by plain loads (queue), z0 .. z0+2 also into the converted ring
+  long long qs[7], qp[7];
+#pragma unroll
+  for (int o = 0; o < 6; ++o) {
+    const int zz = z0 - NG + o;
+    qs[o] = 0;
+    qp[o] = 0;
+    if (in_box) {
+      const long long c = g.at(i, j, zz);
+      qs[o] = cvt(Ys[c], Es);
+      qp[o] = cvt(Yp[c], Ep);
     }
-    const long long hs_v = fx ? to_fixed(nh_s, Es) : __double_as_longlong(nh_s);
-    const long long hp_v = fx ? to_fixed(nh_p, Ep) : __double_as_longlong(nh_p);
-    qs[6] = fx ? to_fixed(nx_s, Es) : __double_as_longlong(nx_s);
-    qp[6] = fx ? to_fixed(nx_p, Ep) : __double_as_longlong(nx_p);
-    if (z + 1 < z1) {
-      if (in_box) {
-        const long long c = g.at(i, j, z + 1 + NG);
-        nx_s = Ys[c];
-        nx_p = Yp[c];
-      }
+    if (o >= NG && zz < z1) {
+      long long* cv = conv_of(zz);
+      cv[own] = qs[o];
+      cv[CONV_PLANE + own] = qp[o];
       if (h_ok) {
-        const long long c = g.at(hi_, hj, z + 1);
-        nh_s = Ys[c];
-        nh_p = Yp[c];
+        const long long c = g.at(hi_, hj, zz);
+        cv[hoff] = cvt(Ys[c], Es);
+        cv[CONV_PLANE + hoff] = cvt(Yp[c], Ep);
       }
     }
-    __syncthreads();
-    sm[0][lj + 3][li + 3] = qs[3];
-    sm[1][lj + 3][li + 3] = qp[3];
+  }
+  int emax_s = 0, emax_p = 0;
+  for (int z = z0; z < z1; ++z) {
+    const int it = z - z0;
+    const int s = it % RHS_DEPTH;
+    const double* sl = slots + s * SLOT_DOUBLES;
+    const unsigned bar = smem_u32(&bars[s]);
+    int fl = FLAG_LIVE;
+    if (in_xy && check_flags) fl = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
+    if (!bar_wait(bar, (unsigned)(it / RHS_DEPTH) & 1u)) s_abort = 1;
+    // raw values of this iteration
+    const double rs_own = sl[own_raw], rp_own = sl[BOX_X * BOX_Y + own_raw];
+    double rs_h = 0.0, rp_h = 0.0;
     if (h_ok) {
-      sm[0][hsj][hsi] = hs_v;
-      sm[1][hsj][hsi] = hp_v;
+      rs_h = sl[halo_raw];
+      rp_h = sl[BOX_X * BOX_Y + halo_raw];
+    }
+    const int pt = lj * TX + li;
+    double ua_s = 0.0, ua_p = 0.0, ub_s = 0.0, ub_p = 0.0;
+    if (A.stage < 3) {
+      ua_s = sl[TILE_DOUBLES + pt];
+      ua_p = sl[TILE_DOUBLES + TX * TY + pt];
+    }
+    if (A.stage > 0) {
+      ub_s = sl[TILE_DOUBLES + PT_DOUBLES + pt];
+      ub_p = sl[TILE_DOUBLES + PT_DOUBLES + TX * TY + pt];
     }
     __syncthreads();
+    if (s_abort) {
+      // drain this CTA's copies still in flight (bounded), report, leave
+      if (threadIdx.x == 0) {
+        atomicOr(A.err, ERR_TIMEOUT);
+        for (int k = it; k < it + RHS_DEPTH && z0 + k < z1; ++k)
+          bar_wait(smem_u32(&bars[k % RHS_DEPTH]), (unsigned)(k / RHS_DEPTH) & 1u);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && z + RHS_DEPTH < z1)
+      issue_slot(Pt, A.stage, slots + s * SLOT_DOUBLES, bar, i0, j0, z + RHS_DEPTH);
+    // plane z+3 enters the queue and the converted ring
+    qs[6] = cvt(rs_own, Es);
+    qp[6] = cvt(rp_own, Ep);
+    {
+      long long* cv = conv_of(z + NG);
+      cv[own] = qs[6];
+      cv[CONV_PLANE + own] = qp[6];
+      if (h_ok) {
+        cv[hoff] = cvt(rs_h, Es);
+        cv[CONV_PLANE + hoff] = cvt(rp_h, Ep);
+      }
+    }
     const bool live = in_xy && (fl == FLAG_LIVE || fl == FLAG_REVIVED);
     if (live) {
-      const long long* rs = &sm[0][lj + 3][li + 3];
-      const long long* rp = &sm[1][lj + 3][li + 3];
+      const long long* rs = conv_of(z) + own;
+      const long long* rp = rs + CONV_PLANE;
       double Ks, Kp;
       if (fx) {
         // ---- exact integer stencil sums
@@ -282,7 +373,7 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
         }
       }
       // ---- RK4 stage combination (FP64)
-      const long long c = cz;
+      const long long cz = g.at(i, j, z);
       double os, op;
       if (A.stage == 3) {
         os = fma(A.alpha, Ks, ub_s);
@@ -292,11 +383,11 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
         const double ap = A.stage == 0 ? ua_p : ub_p;
         os = fma(A.alpha, Ks, ua_s);
         op = fma(A.alpha, Kp, ua_p);
-        Pt.ACC[c] = fma(A.beta, Ks, as);
-        Pt.ACC[c + g.vol] = fma(A.beta, Kp, ap);
+        Pt.ACC[cz] = fma(A.beta, Ks, as);
+        Pt.ACC[cz + g.vol] = fma(A.beta, Kp, ap);
       }
-      Pt.OUT[c] = os;
-      Pt.OUT[c + g.vol] = op;
+      Pt.OUT[cz] = os;
+      Pt.OUT[cz + g.vol] = op;
       emax_s = max(emax_s, biased_exponent(os));
       emax_p = max(emax_p, biased_exponent(op));
     }
@@ -315,11 +406,35 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   }
 }
 
+// Host: TMA maps of one field buffer (4-D: x, y, plane, field).
+bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool tile) {
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  if (!encode) {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return false;
+    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[4] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.n[2] + 2 * NG), 2};
+  const cuuint64_t strides[3] = {(cuuint64_t)g.px * 8, (cuuint64_t)g.plane * 8, (cuuint64_t)g.vol * 8};
+  const cuuint32_t box[4] = {(cuuint32_t)(tile ? BOX_X : RHS_TX), (cuuint32_t)(tile ? BOX_Y : RHS_TY), 1, 2};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<double*>(base), dims, strides, box,
+                            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream) {
-  if (fixed)
-    k_rhs<RHS_TX, RHS_TY, true><<<blocks, RHS_TX * RHS_TY, 0, (cudaStream_t)stream>>>(a);
-  else
-    k_rhs<RHS_TX, RHS_TY, false><<<blocks, RHS_TX * RHS_TY, 0, (cudaStream_t)stream>>>(a);
+  if (fixed) {
+    cudaFuncSetAttribute(k_rhs<RHS_TX, RHS_TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS_SMEM);
+    k_rhs<RHS_TX, RHS_TY, true><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_rhs<RHS_TX, RHS_TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS_SMEM);
+    k_rhs<RHS_TX, RHS_TY, false><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(a);
+  }
 }
 
 }  // namespace mpw
