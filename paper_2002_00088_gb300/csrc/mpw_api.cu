@@ -76,6 +76,10 @@ struct mpw_ctx {
   int* d_err = nullptr;
   int* h_err = nullptr;
   int* d_expo = nullptr;  // [patch][buffer][field] maximum biased exponent
+  // Time whose closed form each global buffer's outer shell holds (NaN: none).
+  // The RK4 substage times repeat (c = 0, 1/2, 1/2, 1, and t_n + dt starts the
+  // next step), so half of the analytic shell evaluations become copies.
+  double shell_time[4] = {NAN, NAN, NAN, NAN};
   double* d_stage = nullptr;
   size_t stage_bytes = 0;
   double t = 0.0;
@@ -451,6 +455,12 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   a.aparams = c->d_aparams;
   a.ascreen = c->screen_ok ? c->d_ascreen : nullptr;
   a.apre = c->screen_ok ? c->d_apre : nullptr;
+  a.shell_src = nullptr;
+  if (a.outer_bc == 0) {
+    for (int k = 0; k < 4; ++k)
+      if (k != b && c->shell_time[k] == t) a.shell_src = g.buf(k);
+    c->shell_time[b] = t;
+  }
   a.t = t;
   a.outer_count = (long long)(g.d.n[0] + 2 * NG) * (g.d.n[1] + 2 * NG) * (g.d.n[2] + 2 * NG) -
                   (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
@@ -771,6 +781,7 @@ mpw_status mpw_set_analytic(mpw_ctx* c, int kind, const double* params, int coun
   if (use_device(c)) return MPW_ERR_CUDA;
   c->akind = kind;
   c->acount = count;
+  for (double& st2 : c->shell_time) st2 = NAN;
   c->aparams.assign(params, params + need);
   if (need) CUDA_TRY(cudaMemcpyAsync(c->d_aparams, c->aparams.data(), sizeof(double) * need, cudaMemcpyHostToDevice,
                                      c->stream));

@@ -185,6 +185,10 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
             A.gg.at(wrap_index(i, A.gg.n[0]), wrap_index(j, A.gg.n[1]), wrap_index(k, A.gg.n[2]));
         w0 = A.Yg[s];
         w1 = A.Yg[s + A.gg.vol];
+      } else if (A.shell_src) {
+        // the closed form at this very time already sits in another buffer's shell
+        w0 = A.shell_src[c];
+        w1 = A.shell_src[c + A.gg.vol];
       } else {
         closed_form(A.akind, A.aparams, A.ascreen, A.apre, A.acount, A.t, A.gg.lo[0] + (i + 0.5) * A.gg.h[0],
                     A.gg.lo[1] + (j + 0.5) * A.gg.h[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2], w0, w1);

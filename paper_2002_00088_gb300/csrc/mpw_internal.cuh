@@ -103,6 +103,7 @@ struct FillArgs {
   const double* aparams;
   const float4* ascreen;  // FP32 screening data of Gaussian pulses (or null)
   const double* apre;     // 1/width^2 of every Gaussian pulse (or null)
+  const double* shell_src;  // global buffer whose outer shell holds the closed form at t (or null)
   double t;
   long long outer_count;
   int outer_blocks;

@@ -94,7 +94,10 @@ __device__ __forceinline__ int slot(int patch, int buf, int field) {
 // thread with cp.async.bulk.tensor, completion tracked by one mbarrier per
 // slot.  Every wait is bounded: a wait that runs out sets ERR_TIMEOUT in the
 // error word, the CTA drains its own copies (again bounded) and returns.
-constexpr int RHS_DEPTH = 4;
+#ifndef MPW_RHS_DEPTH
+#define MPW_RHS_DEPTH 4
+#endif
+constexpr int RHS_DEPTH = MPW_RHS_DEPTH;  // planes in flight per CTA
 constexpr int BOX_X = RHS_TX + 8, BOX_Y = RHS_TY + 6;
 constexpr int TILE_DOUBLES = BOX_X * BOX_Y * 2;
 constexpr int PT_DOUBLES = RHS_TX * RHS_TY * 2;
