@@ -48,9 +48,13 @@ struct Terms {
   int Ss, Sp;       // output scales of K_psi and K_Pi
   int Es, Ep;       // input scales (biased exponents) of psi and Pi
   int fixed;        // 0: FP64 fallback for this CTA
+  double fa[2], fb[2];  // stage coefficients alpha, beta applied to K (psi, Pi), scaled by 2^S
 };
 
-__device__ void setup_terms(Terms& T, const RhsPatch& P, int Es_raw, int Ep_raw, bool want_fixed) {
+__device__ void setup_terms(Terms& T, const RhsPatch& P, int Es_raw, int Ep_raw, bool want_fixed, double alpha,
+                            double beta) {
+  T.fa[0] = T.fa[1] = alpha;
+  T.fb[0] = T.fb[1] = beta;
   T.fixed = want_fixed && Es_raw < EXP_NONFINITE && Ep_raw < EXP_NONFINITE;
   if (!T.fixed) return;
   const int Es = max(Es_raw, 64), Ep = max(Ep_raw, 64);
@@ -79,6 +83,17 @@ __device__ void setup_terms(Terms& T, const RhsPatch& P, int Es_raw, int Ep_raw,
   T.Sp = Sp;
   for (int t = 0; t < 7; ++t) T.ms[t] = term_multiplier(cs[t], es[t], Ss);
   for (int t = 0; t < 9; ++t) T.mp[t] = term_multiplier(cp[t], ep[t], Sp);
+  // K = k 2^S with k the exact int64 sum: the stage updates use alpha 2^S and
+  // beta 2^S (exact scalings), or the FP64 path when they would leave the
+  // normal range
+  if (Ss < -960 || Sp < -960 || Ss > 960 || Sp > 960) {
+    T.fixed = 0;
+    return;
+  }
+  T.fa[0] = scalbn(alpha, Ss);
+  T.fb[0] = scalbn(beta, Ss);
+  T.fa[1] = scalbn(alpha, Sp);
+  T.fb[1] = scalbn(beta, Sp);
 }
 
 __device__ __forceinline__ int slot(int patch, int buf, int field) {
@@ -183,7 +198,7 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   const int i = i0 + li, j = j0 + lj;
   const int z0 = tz * Pt.zc, z1 = min(z0 + Pt.zc, g.n[2]);
   if (threadIdx.x == 0) {
-    setup_terms(T, Pt, A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 1)], FIXED);
+    setup_terms(T, Pt, A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 1)], FIXED, A.alpha, A.beta);
     s_abort = 0;
     for (int s = 0; s < RHS_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -290,20 +305,13 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
     }
     if (threadIdx.x == 0 && z + RHS_DEPTH < z1)
       issue_slot(Pt, A.stage, slots + s * SLOT_DOUBLES, bar, i0, j0, z + RHS_DEPTH);
-    // plane z+3 enters the queue and the converted ring
+    // plane z+3 enters the queue (its converted plane is stored after the compute)
     qs[6] = cvt(rs_own, Es);
     qp[6] = cvt(rp_own, Ep);
-    {
-      long long* cv = conv_of(z + NG);
-      cv[own] = qs[6];
-      cv[CONV_PLANE + own] = qp[6];
-      if (h_ok) {
-        cv[hoff] = cvt(rs_h, Es);
-        cv[CONV_PLANE + hoff] = cvt(rp_h, Ep);
-      }
-    }
+    // every thread computes (points outside the patch or not live read valid
+    // shared memory and store nothing), so the block has no divergent branch
     const bool live = in_xy && (fl == FLAG_LIVE || fl == FLAG_REVIVED);
-    if (live) {
+    {
       const long long* rs = conv_of(z) + own;
       const long long* rp = rs + CONV_PLANE;
       double Ks, Kp;
@@ -342,8 +350,8 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
                 mulhi(8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]), T.mp[7]) +
                 mulhi(8 * (qp[4] - qp[2]) - (qp[5] - qp[1]), T.mp[8]);
         }
-        Ks = fixed_to_double(ks, T.Ss);
-        Kp = fixed_to_double(kp, T.Sp);
+        Ks = (double)ks;  // K_psi / 2^Ss, rounded once
+        Kp = (double)kp;
       } else {
         // ---- native FP64
         auto D = [](long long v) { return __longlong_as_double(v); };
@@ -377,22 +385,38 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
       }
       // ---- RK4 stage combination (FP64)
       const long long cz = g.at(i, j, z);
+      const double fa_s = fx ? T.fa[0] : A.alpha, fa_p = fx ? T.fa[1] : A.alpha;
+      const double fb_s = fx ? T.fb[0] : A.beta, fb_p = fx ? T.fb[1] : A.beta;
       double os, op;
       if (A.stage == 3) {
-        os = fma(A.alpha, Ks, ub_s);
-        op = fma(A.alpha, Kp, ub_p);
+        os = fma(fa_s, Ks, ub_s);
+        op = fma(fa_p, Kp, ub_p);
       } else {
         const double as = A.stage == 0 ? ua_s : ub_s;
         const double ap = A.stage == 0 ? ua_p : ub_p;
-        os = fma(A.alpha, Ks, ua_s);
-        op = fma(A.alpha, Kp, ua_p);
-        Pt.ACC[cz] = fma(A.beta, Ks, as);
-        Pt.ACC[cz + g.vol] = fma(A.beta, Kp, ap);
+        os = fma(fa_s, Ks, ua_s);
+        op = fma(fa_p, Kp, ua_p);
+        if (live) {
+          Pt.ACC[cz] = fma(fb_s, Ks, as);
+          Pt.ACC[cz + g.vol] = fma(fb_p, Kp, ap);
+        }
       }
-      Pt.OUT[cz] = os;
-      Pt.OUT[cz + g.vol] = op;
-      emax_s = max(emax_s, biased_exponent(os));
-      emax_p = max(emax_p, biased_exponent(op));
+      if (live) {
+        Pt.OUT[cz] = os;
+        Pt.OUT[cz + g.vol] = op;
+        emax_s = max(emax_s, biased_exponent(os));
+        emax_p = max(emax_p, biased_exponent(op));
+      }
+    }
+    // plane z+3 into the converted ring (read from iteration z+3 on)
+    {
+      long long* cv = conv_of(z + NG);
+      cv[own] = qs[6];
+      cv[CONV_PLANE + own] = qp[6];
+      if (h_ok) {
+        cv[hoff] = cvt(rs_h, Es);
+        cv[CONV_PLANE + hoff] = cvt(rp_h, Ep);
+      }
     }
 #pragma unroll
     for (int o = 0; o < 6; ++o) {
