@@ -62,6 +62,45 @@ __device__ __forceinline__ double donor_index(const InterpSeg& S, int a, int i) 
   return ((S.gt.lo[a] + (i + 0.5) * S.gt.h[a] + S.shift[a]) - S.gd.lo[a]) / S.gd.h[a] - 0.5;
 }
 
+// One separable pass: contract axis AX of the block `in` (extents din, x
+// fastest) against the 1-D weights of the tile's targets along AX, giving the
+// block `out` whose extent along AX is the number of targets T.  ws holds the
+// absolute window starts, off the block origin along AX, w the P weights per
+// target.
+template <int P, int AX>
+__device__ __forceinline__ void contract_axis(const double* __restrict__ in, double* __restrict__ out, const int din[3],
+                                              int T, const double* __restrict__ w, const int* __restrict__ ws, int off) {
+  const int d0 = AX == 0 ? T : din[0], d1 = AX == 1 ? T : din[1], d2 = AX == 2 ? T : din[2];
+  const int s1 = din[0], s2 = din[0] * din[1];
+  const int st = AX == 0 ? 1 : (AX == 1 ? s1 : s2);
+  const int n = d0 * d1 * d2;
+  for (int e = threadIdx.x; e < n; e += FILL_THREADS) {
+    int o0 = e % d0, o1 = (e / d0) % d1, o2 = e / (d0 * d1);
+    const int t = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
+    const int c = ws[t] - off;
+    if (AX == 0) o0 = c;
+    if (AX == 1) o1 = c;
+    if (AX == 2) o2 = c;
+    const double* src = in + o0 + o1 * s1 + o2 * s2;
+    const double* wt = w + t * 6;
+    double acc = 0.0;
+#pragma unroll
+    for (int m = 0; m < P; ++m) acc = fma(wt[m], src[m * st], acc);
+    out[e] = acc;
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void contract(const double* in, double* out, const int din[3], int ax, int T,
+                                         const double* w, const int* ws, int off) {
+  if (ax == 0)
+    contract_axis<P, 0>(in, out, din, T, w, ws, off);
+  else if (ax == 1)
+    contract_axis<P, 1>(in, out, din, T, w, ws, off);
+  else
+    contract_axis<P, 2>(in, out, din, T, w, ws, off);
+}
+
 template <int P>
 __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], double* sm) {
   double* D = sm;
@@ -88,7 +127,30 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
     Dn[a] = WS[a * MAXT + T[a] - 1] - D0[a] + P;
     inside = inside && D0[a] >= 0 && D0[a] + Dn[a] <= S.gd.n[a];
   }
-  const bool fits = Dn[0] * Dn[1] * Dn[2] <= CAP_D && Dn[2] * Dn[1] * T[0] <= CAP_R1 && Dn[2] * T[1] * T[0] <= CAP_R2;
+  // order of the three passes: the one with the fewest multiply-adds whose
+  // intermediate blocks fit the shared-memory budget
+  int ord[3] = {0, 1, 2};
+  bool fits = Dn[0] * Dn[1] * Dn[2] <= CAP_D;
+  if (fits) {
+    long long best = -1;
+    for (int pm = 0; pm < 6; ++pm) {
+      const int a0 = pm >> 1, a1 = (a0 + 1 + (pm & 1)) % 3, a2 = 3 - a0 - a1;
+      const int Ta0 = a0 == 0 ? T[0] : (a0 == 1 ? T[1] : T[2]);
+      const int Ta1 = a1 == 0 ? T[0] : (a1 == 1 ? T[1] : T[2]);
+      const int Da1 = a1 == 0 ? Dn[0] : (a1 == 1 ? Dn[1] : Dn[2]);
+      const int Da2 = a2 == 0 ? Dn[0] : (a2 == 1 ? Dn[1] : Dn[2]);
+      const long long s1 = (long long)Ta0 * Da1 * Da2;
+      const long long s2 = (long long)Ta0 * Ta1 * Da2;
+      const long long s3 = (long long)T[0] * T[1] * T[2];
+      if (s1 > CAP_R1 || s2 > CAP_R2) continue;
+      const long long cost = s1 + s2 + s3;
+      if (best < 0 || cost < best) {
+        best = cost;
+        ord[0] = a0, ord[1] = a1, ord[2] = a2;
+      }
+    }
+    fits = best >= 0;
+  }
   int emax[2] = {0, 0};
   const int ntar = T[0] * T[1] * T[2];
   if (!(inside && fits)) {
@@ -112,8 +174,10 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
     }
   } else {
     const int nD = Dn[0] * Dn[1] * Dn[2];
-    const int n1 = Dn[2] * Dn[1] * T[0];
-    const int n2 = Dn[2] * T[1] * T[0];
+    int d1[3] = {Dn[0], Dn[1], Dn[2]};
+    d1[ord[0]] = T[ord[0]];
+    int d2[3] = {d1[0], d1[1], d1[2]};
+    d2[ord[1]] = T[ord[1]];
     for (int f = 0; f < 2; ++f) {
       const double* src = S.D + f * S.gd.vol;
       // donor block, x fastest (coalesced rows)
@@ -122,38 +186,17 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
         D[e] = src[S.gd.at(D0[0] + x, D0[1] + y, D0[2] + z)];
       }
       __syncthreads();
-      // contract x: R1[dz][dy][tx]
-      for (int e = tid; e < n1; e += FILL_THREADS) {
-        const int tx = e % T[0], r = e / T[0];  // r = dz * Dn[1] + dy
-        const double* row = D + r * Dn[0] + (WS[tx] - D0[0]);
-        const double* w = W + tx * 6;
-        double acc = 0.0;
-#pragma unroll
-        for (int m = 0; m < P; ++m) acc = fma(w[m], row[m], acc);
-        R1[e] = acc;
-      }
+      contract<P>(D, R1, Dn, ord[0], T[ord[0]], W + ord[0] * MAXT * 6, WS + ord[0] * MAXT, D0[ord[0]]);
       __syncthreads();
-      // contract y: R2[dz][ty][tx]
-      for (int e = tid; e < n2; e += FILL_THREADS) {
-        const int tx = e % T[0], ty = (e / T[0]) % T[1], dz = e / (T[0] * T[1]);
-        const double* col = R1 + (dz * Dn[1] + (WS[MAXT + ty] - D0[1])) * T[0] + tx;
-        const double* w = W + (MAXT + ty) * 6;
-        double acc = 0.0;
-#pragma unroll
-        for (int m = 0; m < P; ++m) acc = fma(w[m], col[m * T[0]], acc);
-        R2[e] = acc;
-      }
+      contract<P>(R1, R2, d1, ord[1], T[ord[1]], W + ord[1] * MAXT * 6, WS + ord[1] * MAXT, D0[ord[1]]);
       __syncthreads();
-      // contract z and store
+      contract<P>(R2, D, d2, ord[2], T[ord[2]], W + ord[2] * MAXT * 6, WS + ord[2] * MAXT, D0[ord[2]]);
+      __syncthreads();
       for (int e = tid; e < ntar; e += FILL_THREADS) {
         const int tx = e % T[0], ty = (e / T[0]) % T[1], tz = e / (T[0] * T[1]);
-        const double* col = R2 + ((WS[2 * MAXT + tz] - D0[2]) * T[1] + ty) * T[0] + tx;
-        const double* w = W + (2 * MAXT + tz) * 6;
-        double acc = 0.0;
-#pragma unroll
-        for (int m = 0; m < P; ++m) acc = fma(w[m], col[m * T[1] * T[0]], acc);
-        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = acc;
-        emax[f] = max(emax[f], biased_exponent(acc));
+        const double v = D[e];
+        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
+        emax[f] = max(emax[f], biased_exponent(v));
       }
       __syncthreads();
     }
