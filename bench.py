@@ -115,12 +115,15 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
+RHS_SOURCES = ("mpw_rhs.cu", "mpw_fixed.cuh", "mpw_internal.cuh")
+
+
 def kernel_source_hash():
+    """Hash of the sources that define the fused RHS + stage kernel."""
     h = hashlib.sha256()
-    for name in sorted(os.listdir(os.path.join(ROOT, "paper_2002_00088_gb300", "csrc"))):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(ROOT, "paper_2002_00088_gb300", "csrc", name), "rb") as f:
-                h.update(f.read())
+    for name in RHS_SOURCES:
+        with open(os.path.join(ROOT, "paper_2002_00088_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 

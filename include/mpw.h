@@ -14,8 +14,12 @@
  *  - Field arrays exchanged with the library are dense interior boxes
  *    [k][j][i], i fastest, n[0]*n[1]*n[2] doubles.  A pointer flagged
  *    on_device = 1 is a CUDA device pointer on the context's device; 0 means
- *    host memory (pinned or pageable).  The library never keeps or frees a
- *    caller pointer.
+ *    host memory (pinned or pageable).  Page-locked host arrays that are
+ *    mapped into the device address space are read or written in place by
+ *    the library's kernels; pageable arrays go through a device staging
+ *    buffer.  Either way a host-pointer call returns once the host array may
+ *    be reused (set) or holds the result (get).  The library never keeps or
+ *    frees a caller pointer.
  *  - Patch geometry: patch j has numeric coordinates X'_j; the live box is
  *    [lo, hi] per axis holding n cells of width h = (hi - lo)/n, nodes
  *    cell-centred at lo + (i + 1/2) h.  The background Cartesian frame of

@@ -815,6 +815,19 @@ static mpw_status get_patch(mpw_ctx* c, int patch, PatchState** out) {
   return use_device(c);
 }
 
+// Device alias of a page-locked host array (cudaHostAlloc, cudaMallocHost or
+// cudaHostRegister'ed memory mapped into the device address space), or null
+// for pageable memory.  The pack and unpack kernels read and write such an
+// array in place, so the host copy needs no staging buffer and no copy engine.
+static void* pinned_alias(const void* p) {
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();  // pageable memory on older drivers reports an error
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double* pi, int on_device) {
   PatchState* P;
   mpw_status st = get_patch(c, patch, &P);
@@ -822,7 +835,12 @@ mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double
   if (!psi || !pi) return set_err(MPW_ERR_ARG, "null field pointer");
   const size_t n = (size_t)P->d.n[0] * P->d.n[1] * P->d.n[2];
   const double *s0 = psi, *s1 = pi;
-  if (!on_device) {
+  const double* a0 = on_device ? nullptr : (const double*)pinned_alias(psi);
+  const double* a1 = on_device ? nullptr : (const double*)pinned_alias(pi);
+  if (a0 && a1) {
+    s0 = a0;
+    s1 = a1;
+  } else if (!on_device) {
     if ((st = ensure_stage(c, 2 * n * sizeof(double)))) return st;
     CUDA_TRY(cudaMemcpyAsync(c->d_stage, psi, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
     CUDA_TRY(cudaMemcpyAsync(c->d_stage + n, pi, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
@@ -844,8 +862,10 @@ static mpw_status get_impl(mpw_ctx* c, int patch, double* psi, double* pi, int o
   const int e = padded ? 2 * NG : 0;
   const size_t n = (size_t)(P->d.n[0] + e) * (P->d.n[1] + e) * (P->d.n[2] + e);
   const uint8_t* flags = (patch == 0 && c->flags_valid) ? c->d_flags : nullptr;
-  if (on_device) {
-    launch_pack(P->buf(BUF_U), P->g, psi, pi, padded, flags, c->stream);
+  double* a0 = on_device ? nullptr : (double*)pinned_alias(psi);
+  double* a1 = on_device ? nullptr : (double*)pinned_alias(pi);
+  if (on_device || (a0 && a1)) {
+    launch_pack(P->buf(BUF_U), P->g, on_device ? psi : a0, on_device ? pi : a1, padded, flags, c->stream);
     CUDA_TRY(cudaGetLastError());
   } else {
     if ((st = ensure_stage(c, 2 * n * sizeof(double)))) return st;

@@ -194,10 +194,18 @@ class Multipatch:
             check(lib.mpw_set_fields(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp), 0))
 
     def get_fields(self, pid, out=None):
-        """Returns host numpy arrays, or fills the given pair of CUDA tensors."""
+        """Returns host numpy arrays, or fills the given pair of CUDA tensors or
+        C-contiguous float64 host arrays (page-locked ones are written in place
+        by the pack kernel)."""
         if out is not None:
             psi, pi = out
-            check(lib.mpw_get_fields(self.h, pid, C.c_void_p(psi.data_ptr()), C.c_void_p(pi.data_ptr()), 1))
+            if isinstance(psi, self._torch.Tensor) and psi.is_cuda:
+                check(lib.mpw_get_fields(self.h, pid, C.c_void_p(psi.data_ptr()), C.c_void_p(pi.data_ptr()), 1))
+                return psi, pi
+            for a in (psi, pi):
+                if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != tuple(self.shapes[pid]):
+                    raise ValueError("host output arrays must be C-contiguous float64 of the patch shape")
+            check(lib.mpw_get_fields(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp), 0))
             return psi, pi
         psi = np.empty(self.shapes[pid])
         pi = np.empty(self.shapes[pid])
