@@ -80,8 +80,9 @@ typedef struct {
   mpw_alloc_fn alloc; /* optional device allocator hook */
   mpw_free_fn free;
   void* alloc_user;
-  int arith;          /* RHS arithmetic: 0 = exact int64 fixed-point stencil sums with FP64
-                         stage updates (default), 1 = native FP64 throughout */
+  int arith;          /* 0 (default): exact int64 fixed-point stencil sums in the RHS with
+                         FP64 stage updates, and int64 fixed-point separable contractions
+                         in the ghost-zone interpolation; 1: native FP64 throughout */
 } mpw_config;
 
 typedef struct {

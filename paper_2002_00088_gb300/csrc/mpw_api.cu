@@ -517,6 +517,7 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   a.y_buf = b;
   a.reset_buf = reset_buf;
   a.np = (int)c->p.size();
+  a.fixed = c->cfg.arith != 1;
   c->launch_begin(MPW_KERNEL_FILL);
   launch_fill(a, c->stream);
   c->launch_end(MPW_KERNEL_FILL);

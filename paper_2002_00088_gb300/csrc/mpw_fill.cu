@@ -12,9 +12,23 @@
 // rigid translation the three 1-D weight sets of a target depend only on its
 // index along the respective axis, so the sum factors: a CTA takes a tile of
 // targets that is a box, stages the donor block that the tile's windows cover
-// in shared memory and contracts x, then y, then z (separable passes).  A
-// tile whose donor block exceeds the shared-memory budget or the donor
-// interior is evaluated point by point with the direct sum instead.
+// in shared memory and contracts one axis after the other (separable passes,
+// cheapest order first).  A tile whose donor block exceeds the shared-memory
+// budget or the donor interior is evaluated point by point with the direct
+// sum instead.
+//
+// Fixed-point passes (FillArgs::fixed).  GB300 issues FP64 FMAs at a small
+// fraction of its integer rate, so by default the passes run on integers:
+// the donor block is put on the scale of its own largest exponent E
+// (q = round(x 2^(1075-E)), |q| < 2^53, then a = 64 q), the weights on
+// 2^59 (every weight of these windows has |w| <= 1), and each product is
+// formed from three 32 x 32 -> 64 partial products of the values split at
+// bit 31 (the low x low product is dropped).  One pass maps values below
+// 2^60 to values below Lambda 2^60 with Lambda = 1.39, the largest Lebesgue
+// constant of the P = 5 and 6 windows, so the three passes stay inside int64;
+// each pass adds an error below one unit of q, so the result is within a few
+// units in the last place of the block's largest value.  A block holding a
+// non-finite value takes the FP64 passes, which propagate it.
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -33,7 +47,8 @@ constexpr int CAP_R1 = 2560;
 constexpr int CAP_R2 = 2048;
 constexpr int MAXT = 32;  // largest tile extent along an axis
 constexpr int FILL_THREADS = 256;
-constexpr size_t FILL_SMEM = sizeof(double) * (CAP_D + CAP_R1 + CAP_R2 + 3 * MAXT * 6) + sizeof(int) * 3 * MAXT;
+constexpr size_t FILL_SMEM = sizeof(double) * (2 * CAP_D + CAP_R1 + CAP_R2 + 3 * MAXT * 6) + sizeof(int) * 3 * MAXT +
+                             sizeof(int2) * 3 * MAXT * 6;
 
 namespace {
 
@@ -90,6 +105,71 @@ __device__ __forceinline__ void contract_axis(const double* __restrict__ in, dou
   }
 }
 
+// 8-byte asynchronous global -> shared copy (no register round trip) and the
+// wait for all of this thread's copies.
+__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all() {
+  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
+}
+
+// v = hi 2^31 + lo with 0 <= lo < 2^31 (|v| < 2^62).
+__device__ __forceinline__ int2 split31(long long v) {
+  return make_int2((int)(v & 0x7FFFFFFFll), (int)(v >> 31));
+}
+
+// Fixed-point version of contract_axis: inputs and weights split at bit 31
+// (x = low 31 bits, y = the rest), output = sum_m a_m w_m / 2^59 from the
+// high x high, high x low and low x high partial products, split again for
+// the next pass or kept whole after the last one (FINAL).
+template <int P, int AX, bool FINAL>
+__device__ __forceinline__ void contract_axis_fx(const int2* __restrict__ in, void* __restrict__ out, const int din[3],
+                                                 int T, const int2* __restrict__ w, const int* __restrict__ ws,
+                                                 int off) {
+  const int d0 = AX == 0 ? T : din[0], d1 = AX == 1 ? T : din[1], d2 = AX == 2 ? T : din[2];
+  const int s1 = din[0], s2 = din[0] * din[1];
+  const int st = AX == 0 ? 1 : (AX == 1 ? s1 : s2);
+  const int n = d0 * d1 * d2;
+  for (int e = threadIdx.x; e < n; e += FILL_THREADS) {
+    int o0 = e % d0, o1 = (e / d0) % d1, o2 = e / (d0 * d1);
+    const int t = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
+    const int c = ws[t] - off;
+    if (AX == 0) o0 = c;
+    if (AX == 1) o1 = c;
+    if (AX == 2) o2 = c;
+    const int2* src = in + o0 + o1 * s1 + o2 * s2;
+    const int2* wt = w + t * 6;
+    long long hh = 0, hl = 0, lh = 0;
+#pragma unroll
+    for (int m = 0; m < P; ++m) {
+      const int2 a = src[m * st];
+      const int2 b = wt[m];
+      hh += (long long)a.y * b.y;
+      hl += (long long)a.y * b.x;
+      lh += (long long)a.x * b.y;
+    }
+    const long long v = hh * 8 + (hl >> 28) + (lh >> 28);
+    if (FINAL)
+      static_cast<long long*>(out)[e] = v;
+    else
+      static_cast<int2*>(out)[e] = split31(v);
+  }
+}
+
+template <int P, bool FINAL>
+__device__ __forceinline__ void contract_fx(const int2* in, void* out, const int din[3], int ax, int T, const int2* w,
+                                            const int* ws, int off) {
+  if (ax == 0)
+    contract_axis_fx<P, 0, FINAL>(in, out, din, T, w, ws, off);
+  else if (ax == 1)
+    contract_axis_fx<P, 1, FINAL>(in, out, din, T, w, ws, off);
+  else
+    contract_axis_fx<P, 2, FINAL>(in, out, din, T, w, ws, off);
+}
+
 template <int P>
 __device__ __forceinline__ void contract(const double* in, double* out, const int din[3], int ax, int T,
                                          const double* w, const int* ws, int off) {
@@ -103,12 +183,15 @@ __device__ __forceinline__ void contract(const double* in, double* out, const in
 
 template <int P>
 __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], double* sm) {
-  double* D = sm;
-  double* R1 = D + CAP_D;
+  double* D = sm;                          // [2][CAP_D] donor blocks of psi and Pi
+  double* R1 = D + 2 * CAP_D;
   double* R2 = R1 + CAP_R1;
   double* W = R2 + CAP_R2;                 // [3][MAXT][6]
   int* WS = reinterpret_cast<int*>(W + 3 * MAXT * 6);  // [3][MAXT] window starts
+  int2* WQ = reinterpret_cast<int2*>(WS + 3 * MAXT);   // [3][MAXT][6] weights on 2^59, split
+  __shared__ int s_E[2];                   // largest biased exponent of each field's donor block
   const int tid = threadIdx.x;
+  if (tid < 2) s_E[tid] = 0;
   // 1-D weights of every target index of the tile, per axis
   for (int e = tid; e < T[0] + T[1] + T[2]; e += FILL_THREADS) {
     const int a = e < T[0] ? 0 : (e < T[0] + T[1] ? 1 : 2);
@@ -116,7 +199,10 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
     double w[P];
     WS[a * MAXT + k] = lagrange_weights<P>(donor_index(S, a, org[a] + k), w);
 #pragma unroll
-    for (int m = 0; m < P; ++m) W[(a * MAXT + k) * 6 + m] = w[m];
+    for (int m = 0; m < P; ++m) {
+      W[(a * MAXT + k) * 6 + m] = w[m];
+      WQ[(a * MAXT + k) * 6 + m] = split31(__double2ll_rn(w[m] * 0x1p59));
+    }
   }
   __syncthreads();
   int D0[3], Dn[3];
@@ -178,26 +264,73 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
     d1[ord[0]] = T[ord[0]];
     int d2[3] = {d1[0], d1[1], d1[2]};
     d2[ord[1]] = T[ord[1]];
-    for (int f = 0; f < 2; ++f) {
-      const double* src = S.D + f * S.gd.vol;
-      // donor block, x fastest (coalesced rows)
+    // donor blocks of both fields, x fastest, copied asynchronously so that
+    // every element of the block is in flight at once
+    for (int e = tid; e < nD; e += FILL_THREADS) {
+      const int x = e % Dn[0], y = (e / Dn[0]) % Dn[1], z = e / (Dn[0] * Dn[1]);
+      const double* src = S.D + S.gd.at(D0[0] + x, D0[1] + y, D0[2] + z);
+      cp_async8(D + e, src);
+      cp_async8(D + CAP_D + e, src + S.gd.vol);
+    }
+    cp_async_wait_all();
+    if (A.fixed) {
+      // largest exponent of each block, on the entries this thread copied
+      int e0 = 0, e1 = 0;
       for (int e = tid; e < nD; e += FILL_THREADS) {
-        const int x = e % Dn[0], y = (e / Dn[0]) % Dn[1], z = e / (Dn[0] * Dn[1]);
-        D[e] = src[S.gd.at(D0[0] + x, D0[1] + y, D0[2] + z)];
+        e0 = max(e0, biased_exponent(D[e]));
+        e1 = max(e1, biased_exponent(D[CAP_D + e]));
       }
-      __syncthreads();
-      contract<P>(D, R1, Dn, ord[0], T[ord[0]], W + ord[0] * MAXT * 6, WS + ord[0] * MAXT, D0[ord[0]]);
-      __syncthreads();
-      contract<P>(R1, R2, d1, ord[1], T[ord[1]], W + ord[1] * MAXT * 6, WS + ord[1] * MAXT, D0[ord[1]]);
-      __syncthreads();
-      contract<P>(R2, D, d2, ord[2], T[ord[2]], W + ord[2] * MAXT * 6, WS + ord[2] * MAXT, D0[ord[2]]);
-      __syncthreads();
-      for (int e = tid; e < ntar; e += FILL_THREADS) {
-        const int tx = e % T[0], ty = (e / T[0]) % T[1], tz = e / (T[0] * T[1]);
-        const double v = D[e];
-        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
-        emax[f] = max(emax[f], biased_exponent(v));
+      e0 = __reduce_max_sync(0xffffffffu, e0);
+      e1 = __reduce_max_sync(0xffffffffu, e1);
+      if ((tid & 31) == 0) {
+        atomicMax(&s_E[0], e0);
+        atomicMax(&s_E[1], e1);
       }
+    }
+    __syncthreads();
+    for (int f = 0; f < 2; ++f) {
+      double* Df = D + f * CAP_D;
+      const int E = s_E[f];
+      if (A.fixed && E < EXP_NONFINITE) {
+        const int Eu = max(E, 64);
+        int2* DQ = reinterpret_cast<int2*>(Df);
+        // in place: every entry is read and rewritten by the same thread
+        for (int e = tid; e < nD; e += FILL_THREADS) DQ[e] = split31(to_fixed(Df[e], Eu) * 64);
+        __syncthreads();
+        int2* R1Q = reinterpret_cast<int2*>(R1);
+        int2* R2Q = reinterpret_cast<int2*>(R2);
+        contract_fx<P, false>(DQ, R1Q, Dn, ord[0], T[ord[0]], WQ + ord[0] * MAXT * 6, WS + ord[0] * MAXT, D0[ord[0]]);
+        __syncthreads();
+        contract_fx<P, false>(R1Q, R2Q, d1, ord[1], T[ord[1]], WQ + ord[1] * MAXT * 6, WS + ord[1] * MAXT,
+                              D0[ord[1]]);
+        __syncthreads();
+        contract_fx<P, true>(R2Q, Df, d2, ord[2], T[ord[2]], WQ + ord[2] * MAXT * 6, WS + ord[2] * MAXT,
+                             D0[ord[2]]);
+        __syncthreads();
+        // results are on 2^(Eu - 1075 - 6): an exact power-of-two scaling
+        const double p2 = __longlong_as_double((long long)(Eu - 58) << 52);
+        const long long* DR = reinterpret_cast<const long long*>(Df);
+        for (int e = tid; e < ntar; e += FILL_THREADS) {
+          const int tx = e % T[0], ty = (e / T[0]) % T[1], tz = e / (T[0] * T[1]);
+          const double v = (double)DR[e] * p2;
+          S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
+          emax[f] = max(emax[f], biased_exponent(v));
+        }
+      } else {
+        contract<P>(Df, R1, Dn, ord[0], T[ord[0]], W + ord[0] * MAXT * 6, WS + ord[0] * MAXT, D0[ord[0]]);
+        __syncthreads();
+        contract<P>(R1, R2, d1, ord[1], T[ord[1]], W + ord[1] * MAXT * 6, WS + ord[1] * MAXT, D0[ord[1]]);
+        __syncthreads();
+        contract<P>(R2, Df, d2, ord[2], T[ord[2]], W + ord[2] * MAXT * 6, WS + ord[2] * MAXT, D0[ord[2]]);
+        __syncthreads();
+        for (int e = tid; e < ntar; e += FILL_THREADS) {
+          const int tx = e % T[0], ty = (e / T[0]) % T[1], tz = e / (T[0] * T[1]);
+          const double v = Df[e];
+          S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
+          emax[f] = max(emax[f], biased_exponent(v));
+        }
+      }
+      // R1 and R2 are reused by the next field
       __syncthreads();
     }
   }

@@ -116,6 +116,7 @@ struct FillArgs {
   int reset_buf;       // buffer whose exponent slots are cleared (the next stage's output), or -1
   int np;
   int total_blocks;
+  int fixed;           // 1: separable contractions in int64 fixed point, 0: native FP64
 };
 
 // ---------------------------------------------------------------- flags

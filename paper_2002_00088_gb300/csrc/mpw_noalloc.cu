@@ -125,6 +125,7 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
       f.reset_buf = out_buf[l];
       f.np = 1;
       f.total_blocks = f.outer_blocks;
+      f.fixed = 1;
       launch_fill(f, s);
       RhsArgs r{};
       r.np = 1;

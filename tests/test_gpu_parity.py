@@ -133,13 +133,23 @@ def test_static_flags_counts(mpw_lib):
     assert g.live_points() == 48 ** 3 - 512 + 32 ** 3
 
 
+@pytest.mark.parametrize("arith", ARITH)
+@pytest.mark.parametrize("data", ["closed_form", "random"])
 @pytest.mark.parametrize("make", [lambda: wl.static_gauss(), lambda: wl.orbiting_gauss(scale=4)])
-def test_ghost_fill_matches_oracle(mpw_lib, make):
-    """Outer BC + Local-to-Global + Global-to-Local on identical data."""
+def test_ghost_fill_matches_oracle(mpw_lib, make, data, arith):
+    """Outer BC + Local-to-Global + Global-to-Local on identical data: the
+    closed form, or random fields whose magnitude varies over six decades."""
     w = make()
     o = oracle_from(w, THREADS)
-    g = gpu_from(mpw_lib, w)
+    g = gpu_from(mpw_lib, w, arith=arith)
     seed_both(o, g, len(w.patches))
+    if data == "random":
+        for q, p in enumerate(w.patches):
+            shape = (p.n[2], p.n[1], p.n[0])
+            ps, pi = wl.random_fields(shape, 40 + q)
+            mag = 10.0 ** np.random.default_rng(60 + q).uniform(-3.0, 3.0, shape)
+            o.set_fields(q, ps * mag, pi * mag)
+            g.set_fields(q, ps * mag, pi * mag)
     o.compute_flags()
     g.compute_flags()
     t = 0.013
