@@ -76,6 +76,7 @@ struct mpw_ctx {
   int* d_err = nullptr;
   int* h_err = nullptr;
   int* d_expo = nullptr;  // [patch][buffer][field] maximum biased exponent
+  long long* d_rev = nullptr;  // queue of revived cells (REVIVE_CAP entries); its length lives in d_err[32]
   // Time whose closed form each global buffer's outer shell holds (NaN: none).
   // The RK4 substage times repeat (c = 0, 1/2, 1/2, 1, and t_n + dt starts the
   // next step), so half of the analytic shell evaluations become copies.
@@ -356,8 +357,12 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   a.P = c->P;
   a.err = c->d_err;
   a.expo = c->d_expo;
+  a.rev_list = c->d_rev;
+  a.rev_count = c->d_err + 32;
+  a.rev_cap = REVIVE_CAP;
   c->launch_begin(MPW_KERNEL_FLAGS);
-  launch_flags(a, c->stream);
+  const int kernels = launch_flags(a, c->stream);  // flags kernel, plus the revival kernel when old flags exist
+  c->launches[MPW_KERNEL_FLAGS] += kernels - 1;
   c->launch_end(MPW_KERNEL_FLAGS);
   CUDA_TRY(cudaGetLastError());
   c->flags_valid = true;
@@ -676,7 +681,9 @@ mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out) {
   c->d_ascreen = (float4*)c->dalloc(sizeof(float4) * (MAX_APARAMS / 5 + 1));
   c->d_apre = (double*)c->dalloc(sizeof(double) * (MAX_APARAMS / 5 + 1));
   c->d_expo = (int*)c->dalloc(sizeof(int) * MAX_PATCHES * EXP_SLOTS_PER_PATCH);
-  if (!c->d_err || !c->d_aparams || !c->d_ascreen || !c->d_apre || !c->d_expo || cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
+  c->d_rev = (long long*)c->dalloc(sizeof(long long) * REVIVE_CAP);
+  if (!c->d_err || !c->d_aparams || !c->d_ascreen || !c->d_apre || !c->d_expo || !c->d_rev ||
+      cudaMallocHost(&c->h_err, sizeof(int)) != cudaSuccess) {
     mpw_destroy(c);
     return set_err(MPW_ERR_CUDA, "context allocation failed");
   }
@@ -700,6 +707,7 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_ascreen);
   c->dfree(c->d_apre);
   c->dfree(c->d_expo);
+  c->dfree(c->d_rev);
   c->dfree(c->d_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& v : c->ev)

@@ -140,7 +140,14 @@ struct FlagArgs {
   int nreg;
   Box reg[MAX_PATCHES];
   long long reg_begin[MAX_PATCHES + 1];
+  // revived cells, interpolated by a second kernel with full warps: entry =
+  // global cell index | (local patch << 40); cells past rev_cap are
+  // interpolated in place by the flags kernel
+  long long* rev_list;
+  int* rev_count;
+  int rev_cap;
 };
+constexpr int REVIVE_CAP = 1 << 16;  // queue entries (one box crossing revives a few thousand cells)
 
 // Record the thread-local message returned by mpw_last_error().
 void set_last_error(const char* msg);
@@ -160,7 +167,7 @@ int fill_cap_r1();
 int fill_cap_r2();
 int fill_max_tile();
 int fill_threads();
-void launch_flags(const FlagArgs& a, void* stream);
+int launch_flags(const FlagArgs& a, void* stream);  // returns the number of kernels launched
 void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
                      const double* aparams, const float4* screen, const double* apre, double t, void* stream);
 void launch_pack(const double* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags,

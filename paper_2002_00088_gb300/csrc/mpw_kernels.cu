@@ -3,6 +3,7 @@
 // exponent scan, and the closed-form / pack / unpack helpers of the C ABI.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
 
@@ -64,6 +65,13 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
     A.Ug[c + A.gg.vol] = __longlong_as_double(0x7ff8000000000000LL);
   } else if (st == FLAG_REVIVED) {
     const int q = owner - 1;
+    // queue the cell: a warp holds about one revived cell, and a warp-wide
+    // FP64 instruction costs the same with one active lane as with 32
+    const int slot = atomicAdd(A.rev_count, 1);
+    if (slot < A.rev_cap) {
+      A.rev_list[slot] = idx | ((long long)q << 40);
+      return;
+    }
     double v0, v1;
     const bool ok = interp_point<P>(A.Uloc[q], A.gl[q], A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
                               A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - A.X0[q][1],
@@ -79,14 +87,63 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
   }
 }
 
-void launch_flags(const FlagArgs& a, void* stream) {
+constexpr int REVIVE_BLOCKS = 4 * 152;  // four CTAs per SM of a GB300
+
+// Revival (reading of Sec. 2.4.2): the queued cells take the Lagrange
+// interpolant of their local patch at the current time, densely packed.
+template <int P>
+__global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs A) {
+  const int count = min(*A.rev_count, A.rev_cap);
+  int e0 = 0, e1 = 0;
+  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+    const int r = base + threadIdx.x;
+    if (r < count) {
+      const long long ent = A.rev_list[r];
+      const long long idx = ent & ((1ll << 40) - 1);
+      const int q = (int)(ent >> 40);
+      const int i = (int)(idx % A.n[0]);
+      const long long rr = idx / A.n[0];
+      const int j = (int)(rr % A.n[1]);
+      const int k = (int)(rr / A.n[1]);
+      double v0, v1;
+      if (interp_point<P>(A.Uloc[q], A.gl[q], A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
+                          A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - A.X0[q][1],
+                          A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - A.X0[q][2], v0, v1)) {
+        const long long c = A.gg.at(i, j, k);
+        A.Ug[c] = v0;
+        A.Ug[c + A.gg.vol] = v1;
+        e0 = max(e0, biased_exponent(v0));
+        e1 = max(e1, biased_exponent(v1));
+      } else {
+        atomicOr(A.err, ERR_UNFILLED);
+      }
+    }
+  }
+  e0 = __reduce_max_sync(0xffffffffu, e0);
+  e1 = __reduce_max_sync(0xffffffffu, e1);
+  if ((threadIdx.x & 31) == 0) {
+    if (e0) atomicMax(&A.expo[BUF_U * 2], e0);
+    if (e1) atomicMax(&A.expo[BUF_U * 2 + 1], e1);
+  }
+}
+
+int launch_flags(const FlagArgs& a, void* stream) {
   const long long N = a.nreg ? a.reg_begin[a.nreg] : (long long)a.n[0] * a.n[1] * a.n[2];
-  if (N <= 0) return;
+  if (N <= 0) return 0;
+  const cudaStream_t s = (cudaStream_t)stream;
+  cudaMemsetAsync(a.rev_count, 0, sizeof(int), s);
   const unsigned blocks = (unsigned)((N + 255) / 256);
-  if (a.P == 6)
-    k_flags<6><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
-  else
-    k_flags<5><<<blocks, 256, 0, (cudaStream_t)stream>>>(a);
+  // the revival kernel walks the queue with a fixed grid (its length is
+  // known on the device only); empty queues cost one short launch
+  const unsigned rblocks = (unsigned)std::min<long long>((N + 255) / 256, REVIVE_BLOCKS);
+  if (a.P == 6) {
+    k_flags<6><<<blocks, 256, 0, s>>>(a);
+    if (a.old_valid) k_revive<6><<<rblocks, 256, 0, s>>>(a);
+  } else {
+    k_flags<5><<<blocks, 256, 0, s>>>(a);
+    if (a.old_valid) k_revive<5><<<rblocks, 256, 0, s>>>(a);
+  }
+  return a.old_valid ? 2 : 1;
 }
 
 // ---------------------------------------------------------------------------
