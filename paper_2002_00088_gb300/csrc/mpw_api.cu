@@ -370,22 +370,25 @@ mpw_status run_flags(mpw_ctx* c, double t) {
 }
 
 // Tile extent for one slab of an interpolation segment: the thin axis takes
-// the slab thickness, the two wide axes the first candidate whose donor block
-// (span of the windows of the tile's targets, at the target/donor spacing
-// ratio) fits the separable kernel's shared-memory budget.
+// the slab thickness, the two wide axes the largest candidate whose blocks
+// fit the separable kernel's budget.  Donor extents are bounded as the
+// kernel computes them: (T - 1) * ratio spans at most floor of that plus one
+// donor, plus the P nodes of the last window.
 void choose_tile(const double ratio[3], int P, int thin, const int extent[3], int td[3]) {
-  static const int cand[][2] = {{32, 8}, {16, 16}, {16, 8}, {8, 8}, {8, 4}, {4, 4}, {2, 2}, {1, 1}};
+  static const int cand[][2] = {{32, 32}, {32, 16}, {16, 32}, {16, 16}, {32, 8}, {8, 32}, {16, 8}, {8, 16},
+                                {8, 8},   {8, 4},   {4, 8},   {4, 4},   {2, 2}, {1, 1}};
   const int wa = thin == 0 ? 1 : 0, wb = thin == 2 ? 1 : 2;
   for (const auto& cd : cand) {
     int T[3];
     T[thin] = extent[thin];
     T[wa] = std::min(cd[0], extent[wa]);
     T[wb] = std::min(cd[1], extent[wb]);
-    int Dn[3];
-    for (int a = 0; a < 3; ++a) Dn[a] = (int)std::floor((T[a] - 1) * ratio[a]) + 1 + P;
-    const bool ok = T[0] <= fill_max_tile() && T[1] <= fill_max_tile() && T[2] <= fill_max_tile() &&
-                    Dn[0] * Dn[1] * Dn[2] <= fill_cap_d() && Dn[2] * Dn[1] * T[0] <= fill_cap_r1() &&
-                    Dn[2] * T[1] * T[0] <= fill_cap_r2();
+    long long Dn[3];
+    for (int a = 0; a < 3; ++a) Dn[a] = (long long)std::floor((T[a] - 1) * ratio[a]) + 1 + P;
+    const long long r1 = T[thin] * Dn[wa] * Dn[wb];
+    const long long r2 = std::min(T[thin] * T[wa] * Dn[wb], T[thin] * Dn[wa] * T[wb]);
+    const bool ok = T[wa] <= fill_max_tile() && T[wb] <= fill_max_tile() && T[thin] <= NG &&
+                    Dn[thin] <= fill_max_thin_donors() && r1 <= fill_cap_r1() && r2 <= fill_cap_r2();
     if (ok || (cd[0] == 1 && cd[1] == 1)) {
       for (int a = 0; a < 3; ++a) td[a] = std::max(T[a], 1);
       return;
@@ -490,6 +493,7 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
     S.T = g.buf(b);
     S.gt = g.g;
     S.tpatch = 0;
+    S.dpatch = q + 1;
     S.D = L.buf(b);
     S.gd = L.g;
     double X0[3], w[3];
@@ -505,6 +509,7 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
     S.T = L.buf(b);
     S.gt = L.g;
     S.tpatch = q + 1;
+    S.dpatch = 0;
     S.D = g.buf(b);
     S.gd = g.g;
     double X0[3], w[3];

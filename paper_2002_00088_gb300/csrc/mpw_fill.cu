@@ -40,18 +40,19 @@
 
 namespace mpw {
 
-// shared-memory budget of one CTA of the separable path, in doubles (one
-// field at a time): donor block, x-contracted block, xy-contracted block
-constexpr int CAP_D = 4096;
-constexpr int CAP_R1 = 2560;
-constexpr int CAP_R2 = 2048;
-constexpr int MAXT = 32;  // largest tile extent along an axis
+// Shared-memory budget of one CTA of the separable path, per field (both
+// fields are contracted together): the block after the thin-axis pass and
+// the block after the second pass.  The final values reuse the first.
+constexpr int CAP_R1 = 4608;
+constexpr int CAP_R2 = 1792;
+constexpr int MAXT = 32;      // largest tile extent along a wide axis
+constexpr int MAXT0 = NG;     // targets along the thin axis (slab walls are NG thick)
+constexpr int MAXD = 16;      // largest donor extent along the thin axis
 constexpr int FILL_THREADS = 256;
-constexpr size_t FILL_SMEM = sizeof(double) * (2 * CAP_D + CAP_R1 + CAP_R2 + 3 * MAXT * 6) + sizeof(int) * 3 * MAXT +
-                             sizeof(int2) * 3 * MAXT * 6;
+constexpr size_t FILL_SMEM = sizeof(double) * 2 * (CAP_R1 + CAP_R2) +
+                             (sizeof(double) + sizeof(int2)) * (3 * MAXT * 6 + MAXT0 * MAXD) + sizeof(int) * 3 * MAXT;
 
 namespace {
-
 
 // Warp- then CTA-level maximum of two exponents, reported with one atomicMax
 // per field by the first thread.
@@ -77,131 +78,178 @@ __device__ __forceinline__ double donor_index(const InterpSeg& S, int a, int i) 
   return ((S.gt.lo[a] + (i + 0.5) * S.gt.h[a] + S.shift[a]) - S.gd.lo[a]) / S.gd.h[a] - 0.5;
 }
 
-// One separable pass: contract axis AX of the block `in` (extents din, x
-// fastest) against the 1-D weights of the tile's targets along AX, giving the
-// block `out` whose extent along AX is the number of targets T.  ws holds the
-// absolute window starts, off the block origin along AX, w the P weights per
-// target.
-template <int P, int AX>
-__device__ __forceinline__ void contract_axis(const double* __restrict__ in, double* __restrict__ out, const int din[3],
-                                              int T, const double* __restrict__ w, const int* __restrict__ ws, int off) {
-  const int d0 = AX == 0 ? T : din[0], d1 = AX == 1 ? T : din[1], d2 = AX == 2 ? T : din[2];
-  const int s1 = din[0], s2 = din[0] * din[1];
-  const int st = AX == 0 ? 1 : (AX == 1 ? s1 : s2);
-  const int n = d0 * d1 * d2;
-  for (int e = threadIdx.x; e < n; e += FILL_THREADS) {
-    int o0 = e % d0, o1 = (e / d0) % d1, o2 = e / (d0 * d1);
-    const int t = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
-    const int c = ws[t] - off;
-    if (AX == 0) o0 = c;
-    if (AX == 1) o1 = c;
-    if (AX == 2) o2 = c;
-    const double* src = in + o0 + o1 * s1 + o2 * s2;
-    const double* wt = w + t * 6;
-    double acc = 0.0;
-#pragma unroll
-    for (int m = 0; m < P; ++m) acc = fma(wt[m], src[m * st], acc);
-    out[e] = acc;
-  }
-}
-
-// 8-byte asynchronous global -> shared copy (no register round trip) and the
-// wait for all of this thread's copies.
-__device__ __forceinline__ void cp_async8(double* dst, const double* src) {
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(dst)), "l"(src)
-               : "memory");
-}
-
-__device__ __forceinline__ void cp_async_wait_all() {
-  asm volatile("cp.async.commit_group;\n cp.async.wait_group 0;" ::: "memory");
-}
-
 // v = hi 2^31 + lo with 0 <= lo < 2^31 (|v| < 2^62).
 __device__ __forceinline__ int2 split31(long long v) {
   return make_int2((int)(v & 0x7FFFFFFFll), (int)(v >> 31));
 }
 
-// Fixed-point version of contract_axis: inputs and weights split at bit 31
-// (x = low 31 bits, y = the rest), output = sum_m a_m w_m / 2^59 from the
-// high x high, high x low and low x high partial products, split again for
-// the next pass or kept whole after the last one (FINAL).
-template <int P, int AX, bool FINAL>
-__device__ __forceinline__ void contract_axis_fx(const int2* __restrict__ in, void* __restrict__ out, const int din[3],
-                                                 int T, const int2* __restrict__ w, const int* __restrict__ ws,
-                                                 int off) {
+// Fixed-point multiply-add of a split value and a split weight on 2^59:
+// accumulates the high x high, high x low and low x high partial products.
+struct Acc3 {
+  long long hh = 0, hl = 0, lh = 0;
+  __device__ __forceinline__ void mac(int2 a, int2 b) {
+    hh += (long long)a.y * b.y;
+    hl += (long long)a.y * b.x;
+    lh += (long long)a.x * b.y;
+  }
+  // sum of a w over the accumulated terms (the low x low products, each
+  // below 2^62 / 2^59 = 8 units, are dropped)
+  __device__ __forceinline__ long long value() const { return hh * 8 + (hl >> 28) + (lh >> 28); }
+};
+
+// One separable pass over both fields: contract axis AX of the blocks `in`
+// (extents din, x fastest, field f at in + f * in_stride) against the 1-D
+// weights of the tile's targets along AX.  ws holds the absolute window
+// starts, off the block origin along AX, w the P weights per target.  FX
+// selects the fixed-point form (int2 entries, split output; FINAL keeps the
+// last output whole as long long).
+template <int P, int AX, bool FX, bool FINAL>
+__device__ __forceinline__ void contract_axis(const void* __restrict__ in, int in_stride, void* __restrict__ out,
+                                              int out_stride, const int din[3], int T, const void* __restrict__ w,
+                                              const int* __restrict__ ws, int off) {
   const int d0 = AX == 0 ? T : din[0], d1 = AX == 1 ? T : din[1], d2 = AX == 2 ? T : din[2];
   const int s1 = din[0], s2 = din[0] * din[1];
   const int st = AX == 0 ? 1 : (AX == 1 ? s1 : s2);
   const int n = d0 * d1 * d2;
-  for (int e = threadIdx.x; e < n; e += FILL_THREADS) {
-    int o0 = e % d0, o1 = (e / d0) % d1, o2 = e / (d0 * d1);
+  for (int e = threadIdx.x; e < 2 * n; e += FILL_THREADS) {
+    const int f = e >= n;
+    const int r = e - f * n;
+    int o0 = r % d0, o1 = (r / d0) % d1, o2 = r / (d0 * d1);
     const int t = AX == 0 ? o0 : (AX == 1 ? o1 : o2);
     const int c = ws[t] - off;
     if (AX == 0) o0 = c;
     if (AX == 1) o1 = c;
     if (AX == 2) o2 = c;
-    const int2* src = in + o0 + o1 * s1 + o2 * s2;
-    const int2* wt = w + t * 6;
-    long long hh = 0, hl = 0, lh = 0;
+    const int src = f * in_stride + o0 + o1 * s1 + o2 * s2;
+    if (FX) {
+      const int2* a = static_cast<const int2*>(in) + src;
+      const int2* wt = static_cast<const int2*>(w) + t * 6;
+      Acc3 acc;
 #pragma unroll
-    for (int m = 0; m < P; ++m) {
-      const int2 a = src[m * st];
-      const int2 b = wt[m];
-      hh += (long long)a.y * b.y;
-      hl += (long long)a.y * b.x;
-      lh += (long long)a.x * b.y;
+      for (int m = 0; m < P; ++m) acc.mac(a[m * st], wt[m]);
+      if (FINAL)
+        static_cast<long long*>(out)[f * out_stride + r] = acc.value();
+      else
+        static_cast<int2*>(out)[f * out_stride + r] = split31(acc.value());
+    } else {
+      const double* a = static_cast<const double*>(in) + src;
+      const double* wt = static_cast<const double*>(w) + t * 6;
+      double acc = 0.0;
+#pragma unroll
+      for (int m = 0; m < P; ++m) acc = fma(wt[m], a[m * st], acc);
+      static_cast<double*>(out)[f * out_stride + r] = acc;
     }
-    const long long v = hh * 8 + (hl >> 28) + (lh >> 28);
-    if (FINAL)
-      static_cast<long long*>(out)[e] = v;
-    else
-      static_cast<int2*>(out)[e] = split31(v);
   }
 }
 
-template <int P, bool FINAL>
-__device__ __forceinline__ void contract_fx(const int2* in, void* out, const int din[3], int ax, int T, const int2* w,
-                                            const int* ws, int off) {
+template <int P, bool FX, bool FINAL>
+__device__ __forceinline__ void contract(const void* in, int in_stride, void* out, int out_stride, const int din[3],
+                                         int ax, int T, const void* w, const int* ws, int off) {
   if (ax == 0)
-    contract_axis_fx<P, 0, FINAL>(in, out, din, T, w, ws, off);
+    contract_axis<P, 0, FX, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
   else if (ax == 1)
-    contract_axis_fx<P, 1, FINAL>(in, out, din, T, w, ws, off);
+    contract_axis<P, 1, FX, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
   else
-    contract_axis_fx<P, 2, FINAL>(in, out, din, T, w, ws, off);
+    contract_axis<P, 2, FX, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
+}
+
+// Thin-axis pass fused with the donor load: one thread per donor pencil
+// along the thin axis a0 (both fields), holding its nk values in registers
+// and contracting them against the band matrix of the tile's targets along
+// a0 (row t: the P weights of target t at its window offset, zeros
+// elsewhere).  Output: the block with extent T0 along a0 and the donor
+// extents along the other axes, x fastest.
+template <int P, bool FX>
+__device__ __forceinline__ void thin_pass(const InterpSeg& S, int a0, const int D0[3], const int Dn[3], int T0,
+                                          const void* __restrict__ band, int Es, int Ep, void* __restrict__ out) {
+  const int a1 = a0 == 0 ? 1 : 0, a2 = a0 == 2 ? 1 : 2;
+  const int n1 = Dn[a1], n2 = Dn[a2], nk = Dn[a0];
+  const long long st0 = a0 == 0 ? 1 : (a0 == 1 ? (long long)S.gd.px : S.gd.plane);
+  // strides of the output block (extent T0 along a0)
+  int ext[3] = {Dn[0], Dn[1], Dn[2]};
+  ext[a0] = T0;
+  const int ostr[3] = {1, ext[0], ext[0] * ext[1]};
+  const int npen = n1 * n2;
+  for (int e = threadIdx.x; e < 2 * npen; e += FILL_THREADS) {
+    const int f = e >= npen;
+    const int p = e - f * npen;
+    const int c1 = p % n1, c2 = p / n1;
+    int o[3];
+    o[a0] = D0[a0];
+    o[a1] = D0[a1] + c1;
+    o[a2] = D0[a2] + c2;
+    const double* src = S.D + f * S.gd.vol + S.gd.at(o[0], o[1], o[2]);
+    const int obase = c1 * ostr[a1] + c2 * ostr[a2] + f * CAP_R1;
+    if (FX) {
+      const int E = f ? Ep : Es;
+      int2 v[MAXD];
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) v[k] = split31(k < nk ? to_fixed(src[k * st0], E) * 64 : 0);
+      const int2* bq = static_cast<const int2*>(band);
+#pragma unroll
+      for (int t = 0; t < MAXT0; ++t) {
+        if (t >= T0) break;
+        Acc3 acc;
+#pragma unroll
+        for (int k = 0; k < MAXD; ++k)
+          if (k < nk) acc.mac(v[k], bq[t * MAXD + k]);
+        static_cast<int2*>(out)[obase + t * ostr[a0]] = split31(acc.value());
+      }
+    } else {
+      double v[MAXD];
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) v[k] = k < nk ? src[k * st0] : 0.0;
+      const double* bd = static_cast<const double*>(band);
+#pragma unroll
+      for (int t = 0; t < MAXT0; ++t) {
+        if (t >= T0) break;
+        double acc = 0.0;
+#pragma unroll
+        for (int k = 0; k < MAXD; ++k)
+          if (k < nk) acc = fma(bd[t * MAXD + k], v[k], acc);
+        static_cast<double*>(out)[obase + t * ostr[a0]] = acc;
+      }
+    }
+  }
 }
 
 template <int P>
-__device__ __forceinline__ void contract(const double* in, double* out, const int din[3], int ax, int T,
-                                         const double* w, const int* ws, int off) {
-  if (ax == 0)
-    contract_axis<P, 0>(in, out, din, T, w, ws, off);
-  else if (ax == 1)
-    contract_axis<P, 1>(in, out, din, T, w, ws, off);
-  else
-    contract_axis<P, 2>(in, out, din, T, w, ws, off);
-}
-
-template <int P>
-__device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], double* sm) {
-  double* D = sm;                          // [2][CAP_D] donor blocks of psi and Pi
-  double* R1 = D + 2 * CAP_D;
-  double* R2 = R1 + CAP_R1;
-  double* W = R2 + CAP_R2;                 // [3][MAXT][6]
-  int* WS = reinterpret_cast<int*>(W + 3 * MAXT * 6);  // [3][MAXT] window starts
-  int2* WQ = reinterpret_cast<int2*>(WS + 3 * MAXT);   // [3][MAXT][6] weights on 2^59, split
-  __shared__ int s_E[2];                   // largest biased exponent of each field's donor block
+__device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], int a0,
+                            double* sm) {
+  double* R1 = sm;                          // [2][CAP_R1]
+  double* R2 = R1 + 2 * CAP_R1;             // [2][CAP_R2]
+  double* W = R2 + 2 * CAP_R2;              // [3][MAXT][6]
+  int2* WQ = reinterpret_cast<int2*>(W + 3 * MAXT * 6);  // [3][MAXT][6] weights on 2^59, split
+  double* BW = reinterpret_cast<double*>(WQ + 3 * MAXT * 6);  // [MAXT0][MAXD] band matrix of the thin axis
+  int2* BQ = reinterpret_cast<int2*>(BW + MAXT0 * MAXD);
+  int* WS = reinterpret_cast<int*>(BQ + MAXT0 * MAXD);   // [3][MAXT] window starts
   const int tid = threadIdx.x;
-  if (tid < 2) s_E[tid] = 0;
-  // 1-D weights of every target index of the tile, per axis
+  // 1-D weights of every target index of the tile, per axis; the threads of
+  // the thin axis also write their row of the band matrix
   for (int e = tid; e < T[0] + T[1] + T[2]; e += FILL_THREADS) {
     const int a = e < T[0] ? 0 : (e < T[0] + T[1] ? 1 : 2);
     const int k = e - (a == 0 ? 0 : (a == 1 ? T[0] : T[0] + T[1]));
     double w[P];
-    WS[a * MAXT + k] = lagrange_weights<P>(donor_index(S, a, org[a] + k), w);
+    const int start = lagrange_weights<P>(donor_index(S, a, org[a] + k), w);
+    WS[a * MAXT + k] = start;
 #pragma unroll
     for (int m = 0; m < P; ++m) {
       W[(a * MAXT + k) * 6 + m] = w[m];
       WQ[(a * MAXT + k) * 6 + m] = split31(__double2ll_rn(w[m] * 0x1p59));
+    }
+    if (a == a0 && k < MAXT0) {
+      double w0[P];
+      const int off = start - lagrange_weights<P>(donor_index(S, a, org[a]), w0);  // window offset in the block
+      for (int q = 0; q < MAXD; ++q) {
+        const int m = q - off;
+        const bool in = m >= 0 && m < P;
+        double wm = 0.0;
+#pragma unroll
+        for (int mm = 0; mm < P; ++mm)
+          if (mm == m) wm = w[mm];
+        BW[k * MAXD + q] = in ? wm : 0.0;
+        BQ[k * MAXD + q] = in ? split31(__double2ll_rn(wm * 0x1p59)) : make_int2(0, 0);
+      }
     }
   }
   __syncthreads();
@@ -213,33 +261,16 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
     Dn[a] = WS[a * MAXT + T[a] - 1] - D0[a] + P;
     inside = inside && D0[a] >= 0 && D0[a] + Dn[a] <= S.gd.n[a];
   }
-  // order of the three passes: the one with the fewest multiply-adds whose
-  // intermediate blocks fit the shared-memory budget
-  int ord[3] = {0, 1, 2};
-  bool fits = Dn[0] * Dn[1] * Dn[2] <= CAP_D;
-  if (fits) {
-    long long best = -1;
-    for (int pm = 0; pm < 6; ++pm) {
-      const int a0 = pm >> 1, a1 = (a0 + 1 + (pm & 1)) % 3, a2 = 3 - a0 - a1;
-      const int Ta0 = a0 == 0 ? T[0] : (a0 == 1 ? T[1] : T[2]);
-      const int Ta1 = a1 == 0 ? T[0] : (a1 == 1 ? T[1] : T[2]);
-      const int Da1 = a1 == 0 ? Dn[0] : (a1 == 1 ? Dn[1] : Dn[2]);
-      const int Da2 = a2 == 0 ? Dn[0] : (a2 == 1 ? Dn[1] : Dn[2]);
-      const long long s1 = (long long)Ta0 * Da1 * Da2;
-      const long long s2 = (long long)Ta0 * Ta1 * Da2;
-      const long long s3 = (long long)T[0] * T[1] * T[2];
-      if (s1 > CAP_R1 || s2 > CAP_R2) continue;
-      const long long cost = s1 + s2 + s3;
-      if (best < 0 || cost < best) {
-        best = cost;
-        ord[0] = a0, ord[1] = a1, ord[2] = a2;
-      }
-    }
-    fits = best >= 0;
-  }
+  // after the thin pass: contract the wide axis whose pass leaves the
+  // smaller block first
+  const int b1 = a0 == 0 ? 1 : 0, b2 = a0 == 2 ? 1 : 2;
+  const long long s1 = (long long)T[a0] * Dn[b1] * Dn[b2];
+  const long long s2a = (long long)T[a0] * T[b1] * Dn[b2], s2b = (long long)T[a0] * Dn[b1] * T[b2];
+  const int x1 = s2a <= s2b ? b1 : b2, x2 = s2a <= s2b ? b2 : b1;
+  const bool fits = inside && T[a0] <= MAXT0 && Dn[a0] <= MAXD && s1 <= CAP_R1 && (s2a <= s2b ? s2a : s2b) <= CAP_R2;
   int emax[2] = {0, 0};
   const int ntar = T[0] * T[1] * T[2];
-  if (!(inside && fits)) {
+  if (!fits) {
     // direct tensor sum, point by point (reports uninterpolable points)
     for (int e = tid; e < ntar; e += FILL_THREADS) {
       const int x = e % T[0], y = (e / T[0]) % T[1], z = e / (T[0] * T[1]);
@@ -259,82 +290,54 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
       emax[1] = max(emax[1], biased_exponent(v1));
     }
   } else {
-    const int nD = Dn[0] * Dn[1] * Dn[2];
     int d1[3] = {Dn[0], Dn[1], Dn[2]};
-    d1[ord[0]] = T[ord[0]];
+    d1[a0] = T[a0];
     int d2[3] = {d1[0], d1[1], d1[2]};
-    d2[ord[1]] = T[ord[1]];
-    // donor blocks of both fields, x fastest, copied asynchronously so that
-    // every element of the block is in flight at once
-    for (int e = tid; e < nD; e += FILL_THREADS) {
-      const int x = e % Dn[0], y = (e / Dn[0]) % Dn[1], z = e / (Dn[0] * Dn[1]);
-      const double* src = S.D + S.gd.at(D0[0] + x, D0[1] + y, D0[2] + z);
-      cp_async8(D + e, src);
-      cp_async8(D + CAP_D + e, src + S.gd.vol);
-    }
-    cp_async_wait_all();
-    if (A.fixed) {
-      // largest exponent of each block, on the entries this thread copied
-      int e0 = 0, e1 = 0;
-      for (int e = tid; e < nD; e += FILL_THREADS) {
-        e0 = max(e0, biased_exponent(D[e]));
-        e1 = max(e1, biased_exponent(D[CAP_D + e]));
-      }
-      e0 = __reduce_max_sync(0xffffffffu, e0);
-      e1 = __reduce_max_sync(0xffffffffu, e1);
-      if ((tid & 31) == 0) {
-        atomicMax(&s_E[0], e0);
-        atomicMax(&s_E[1], e1);
-      }
-    }
-    __syncthreads();
-    for (int f = 0; f < 2; ++f) {
-      double* Df = D + f * CAP_D;
-      const int E = s_E[f];
-      if (A.fixed && E < EXP_NONFINITE) {
-        const int Eu = max(E, 64);
-        int2* DQ = reinterpret_cast<int2*>(Df);
-        // in place: every entry is read and rewritten by the same thread
-        for (int e = tid; e < nD; e += FILL_THREADS) DQ[e] = split31(to_fixed(Df[e], Eu) * 64);
-        __syncthreads();
-        int2* R1Q = reinterpret_cast<int2*>(R1);
-        int2* R2Q = reinterpret_cast<int2*>(R2);
-        contract_fx<P, false>(DQ, R1Q, Dn, ord[0], T[ord[0]], WQ + ord[0] * MAXT * 6, WS + ord[0] * MAXT, D0[ord[0]]);
-        __syncthreads();
-        contract_fx<P, false>(R1Q, R2Q, d1, ord[1], T[ord[1]], WQ + ord[1] * MAXT * 6, WS + ord[1] * MAXT,
-                              D0[ord[1]]);
-        __syncthreads();
-        contract_fx<P, true>(R2Q, Df, d2, ord[2], T[ord[2]], WQ + ord[2] * MAXT * 6, WS + ord[2] * MAXT,
-                             D0[ord[2]]);
-        __syncthreads();
-        // results are on 2^(Eu - 1075 - 6): an exact power-of-two scaling
-        const double p2 = __longlong_as_double((long long)(Eu - 58) << 52);
-        const long long* DR = reinterpret_cast<const long long*>(Df);
-        for (int e = tid; e < ntar; e += FILL_THREADS) {
-          const int tx = e % T[0], ty = (e / T[0]) % T[1], tz = e / (T[0] * T[1]);
-          const double v = (double)DR[e] * p2;
-          S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
-          emax[f] = max(emax[f], biased_exponent(v));
-        }
-      } else {
-        contract<P>(Df, R1, Dn, ord[0], T[ord[0]], W + ord[0] * MAXT * 6, WS + ord[0] * MAXT, D0[ord[0]]);
-        __syncthreads();
-        contract<P>(R1, R2, d1, ord[1], T[ord[1]], W + ord[1] * MAXT * 6, WS + ord[1] * MAXT, D0[ord[1]]);
-        __syncthreads();
-        contract<P>(R2, Df, d2, ord[2], T[ord[2]], W + ord[2] * MAXT * 6, WS + ord[2] * MAXT, D0[ord[2]]);
-        __syncthreads();
-        for (int e = tid; e < ntar; e += FILL_THREADS) {
-          const int tx = e % T[0], ty = (e / T[0]) % T[1], tz = e / (T[0] * T[1]);
-          const double v = Df[e];
-          S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
-          emax[f] = max(emax[f], biased_exponent(v));
-        }
-      }
-      // R1 and R2 are reused by the next field
+    d2[x1] = T[x1];
+    // donor scale: the largest exponent of the donor buffer's live values
+    // (complete before this launch; the fill itself only raises the ghost
+    // slots), so the scale is known before the donors are read
+    const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+    const int Es = dslot[0], Ep = dslot[1];
+    if (A.fixed && Es < EXP_NONFINITE && Ep < EXP_NONFINITE) {
+      const int Esu = max(Es, 64), Epu = max(Ep, 64);
+      thin_pass<P, true>(S, a0, D0, Dn, T[a0], BQ, Esu, Epu, R1);
       __syncthreads();
+      contract<P, true, false>(R1, CAP_R1, R2, CAP_R2, d1, x1, T[x1], WQ + x1 * MAXT * 6, WS + x1 * MAXT, D0[x1]);
+      __syncthreads();
+      contract<P, true, true>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], WQ + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
+      __syncthreads();
+      // results are on 2^(E - 1075 - 6): exact power-of-two scalings
+      const double p2[2] = {__longlong_as_double((long long)(Esu - 58) << 52),
+                            __longlong_as_double((long long)(Epu - 58) << 52)};
+      const long long* out = reinterpret_cast<const long long*>(R1);
+      for (int e = tid; e < 2 * ntar; e += FILL_THREADS) {
+        const int f = e >= ntar;
+        const int r = e - f * ntar;
+        const int tx = r % T[0], ty = (r / T[0]) % T[1], tz = r / (T[0] * T[1]);
+        const double v = (double)out[f * CAP_R1 + r] * p2[f];
+        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
+        emax[f] = max(emax[f], biased_exponent(v));
+      }
+    } else {
+      thin_pass<P, false>(S, a0, D0, Dn, T[a0], BW, 0, 0, R1);
+      __syncthreads();
+      contract<P, false, false>(R1, CAP_R1, R2, CAP_R2, d1, x1, T[x1], W + x1 * MAXT * 6, WS + x1 * MAXT, D0[x1]);
+      __syncthreads();
+      contract<P, false, false>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], W + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
+      __syncthreads();
+      for (int e = tid; e < 2 * ntar; e += FILL_THREADS) {
+        const int f = e >= ntar;
+        const int r = e - f * ntar;
+        const int tx = r % T[0], ty = (r / T[0]) % T[1], tz = r / (T[0] * T[1]);
+        const double v = R1[f * CAP_R1 + r];
+        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
+        emax[f] = max(emax[f], biased_exponent(v));
+      }
     }
+    // each thread's emax[f] covers only entries of field f, the other stays 0
   }
-  report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2, emax[0], emax[1]);
+  report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, emax[0], emax[1]);
 }
 
 }  // namespace
@@ -344,6 +347,8 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
   extern __shared__ double fill_smem[];
   if (A.reset_buf >= 0 && blockIdx.x == 0 && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
+  if (A.reset_buf >= 0 && blockIdx.x == 0 && threadIdx.x < 2 * A.np)
+    A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
   const int b = blockIdx.x;
   if (b < A.outer_blocks) {
     // global outer ghost shell, one point per thread
@@ -374,7 +379,7 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
       e0 = biased_exponent(w0);
       e1 = biased_exponent(w1);
     }
-    report_block_max(A.expo + A.y_buf * 2, e0, e1);
+    report_block_max(A.expo + EXP_GHOST + A.y_buf * 2, e0, e1);
     return;
   }
   // interpolation tile: find its segment, slab and position
@@ -394,7 +399,7 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
     org[a] = S.sb[sl][a] + tt[a] * S.td[sl][a];
     T[a] = min(S.td[sl][a], S.sb[sl][a] + S.se[sl][a] - org[a]);
   }
-  interp_tile<P>(A, S, org, T, fill_smem);
+  interp_tile<P>(A, S, org, T, 2 - sl / 2, fill_smem);  // slabs come in z, y, x pairs: the wall axis is thin
 }
 
 void launch_fill(const FillArgs& a, void* stream) {
@@ -408,10 +413,10 @@ void launch_fill(const FillArgs& a, void* stream) {
   }
 }
 
-int fill_cap_d() { return CAP_D; }
 int fill_cap_r1() { return CAP_R1; }
 int fill_cap_r2() { return CAP_R2; }
 int fill_max_tile() { return MAXT; }
+int fill_max_thin_donors() { return MAXD; }
 int fill_threads() { return FILL_THREADS; }
 
 }  // namespace mpw

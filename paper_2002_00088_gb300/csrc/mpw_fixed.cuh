@@ -15,7 +15,12 @@
 
 namespace mpw {
 
-constexpr int EXP_SLOTS_PER_PATCH = 8;  // 4 buffers x 2 fields
+// Exponent slots per patch: [buffer][field] of the live values (written by
+// the RHS, the exponent scan and revival), then the same for the ghost
+// values written by the ghost fill (EXP_GHOST on).  A buffer's scale is the
+// larger of its two slots.
+constexpr int EXP_SLOTS_PER_PATCH = 16;
+constexpr int EXP_GHOST = 8;
 constexpr int EXP_NONFINITE = 2047;
 
 // Biased exponent field of a binary64 value (0 for zero/subnormal, 2047 for

@@ -82,6 +82,7 @@ struct InterpSeg {
   double* T;           // target buffer (psi; Pi at +vol)
   Geom gt;
   int tpatch;          // target patch id (exponent slots)
+  int dpatch;          // donor patch id (exponent slots)
   const double* D;     // donor buffer (psi; Pi at +vol)
   Geom gd;
   double shift[3];     // X0_target - X0_donor at the substage time
@@ -162,7 +163,7 @@ bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool ti
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
 void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);
 void launch_fill(const FillArgs& a, void* stream);
-int fill_cap_d();
+int fill_max_thin_donors();
 int fill_cap_r1();
 int fill_cap_r2();
 int fill_max_tile();

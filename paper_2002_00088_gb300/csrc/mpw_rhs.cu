@@ -198,7 +198,10 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   const int i = i0 + li, j = j0 + lj;
   const int z0 = tz * Pt.zc, z1 = min(z0 + Pt.zc, g.n[2]);
   if (threadIdx.x == 0) {
-    setup_terms(T, Pt, A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 1)], FIXED, A.alpha, A.beta);
+    // input scale: live values and the ghost values the fill wrote
+    const int Es = max(A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 0) + EXP_GHOST]);
+    const int Ep = max(A.expo[slot(p, Pt.in_buf, 1)], A.expo[slot(p, Pt.in_buf, 1) + EXP_GHOST]);
+    setup_terms(T, Pt, Es, Ep, FIXED, A.alpha, A.beta);
     s_abort = 0;
     for (int s = 0; s < RHS_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");

@@ -155,14 +155,19 @@ def test_ghost_fill_matches_oracle(mpw_lib, make, data, arith):
     t = 0.013
     o.fill_ghosts(t)
     g.fill_ghosts(t)
-    for q in range(len(w.patches)):
-        a_ps, a_pi = g.get_padded(q)
-        b_ps, b_pi = o.get_padded(q, which=1)
-        m = np.isfinite(b_ps)
-        assert m.sum() > 0
-        scale = np.abs(b_ps[m]).max()
-        assert np.abs(a_ps[m] - b_ps[m]).max() <= 1e-13 * scale
-        assert np.abs(a_pi[m] - b_pi[m]).max() <= 1e-13 * max(scale, np.abs(b_pi[m]).max())
+    got = [g.get_padded(q) for q in range(len(w.patches))]
+    want = [o.get_padded(q, which=1) for q in range(len(w.patches))]
+    # max |difference| over every patch relative to the largest |value| of the
+    # state over the whole domain (both fields: at t = 0.013 the closed-form
+    # Pi is near zero and cancels, so its own maximum is rounding noise)
+    scale = max(np.nanmax(np.abs(b[f])) for b in want for f in range(2))
+    for f in range(2):
+        for q in range(len(w.patches)):
+            a, b = got[q][f], want[q][f]
+            m = np.isfinite(b)
+            assert m.sum() > 0
+            err = np.abs(a[m] - b[m]).max() / scale
+            assert err <= 1e-13, f"patch {q} field {f}: {err:.3e}"
 
 
 @pytest.mark.parametrize("arith", ARITH)
