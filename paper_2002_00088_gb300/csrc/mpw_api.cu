@@ -552,7 +552,7 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
   for (int q = 0; q < a.nbox; ++q) a.box[q] = c->boxes[q];
   a.expo = c->d_expo;
   a.err = c->d_err;
-  long long work = 0;
+  int blocks = 0;
   for (int q = 0; q < a.np; ++q) {
     const PatchState& P = c->p[q];
     RhsPatch& R = a.p[q];
@@ -580,12 +580,13 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
     R.out_buf = out_buf[l];
     R.tiles_x = (P.d.n[0] + RHS_TX - 1) / RHS_TX;
     R.tiles_y = (P.d.n[1] + RHS_TY - 1) / RHS_TY;
-    R.work0 = work;
-    work += (long long)R.tiles_x * R.tiles_y * P.d.n[2];
+    R.zc = P.d.n[2] >= 128 ? 32 : 8;
+    R.zchunks = (P.d.n[2] + R.zc - 1) / R.zc;
+    R.block0 = blocks;
+    blocks += R.tiles_x * R.tiles_y * R.zchunks;
   }
-  a.work = work;
   c->launch_begin(MPW_KERNEL_RHS);
-  launch_rhs(a, rhs_grid(work), c->cfg.arith != 1, c->stream);
+  launch_rhs(a, blocks, c->cfg.arith != 1, c->stream);
   c->launch_end(MPW_KERNEL_RHS);
   CUDA_TRY(cudaGetLastError());
   return MPW_OK;

@@ -54,8 +54,8 @@ struct RhsPatch {
   double c1[3];      // w_a / (12 h_a)
   double c2[3];      // 1 / (12 h_a^2)
   double cko[3];     // eps / (64 h_a)
-  int tiles_x, tiles_y;
-  long long work0;   // first plane-tile of this patch in the launch's linear order
+  int tiles_x, tiles_y, zchunks, zc;
+  int block0;
   int moving;        // any w_a != 0
   int is_global;
   int iso;           // equal spacing on all axes (D2 and KO sums aggregated)
@@ -72,7 +72,6 @@ struct RhsArgs {
   Box box[MAX_PATCHES];
   int* expo;            // tracked maximum biased exponents, [patch][buffer][field]
   int* err;             // device error word
-  long long work;       // plane-tiles of all patches (tiles_x tiles_y n[2] each)
 };
 
 // ---------------------------------------------------------------- fill
@@ -161,9 +160,6 @@ void set_last_error(const char* msg);
 bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool tile);
 
 // ---------------------------------------------------------------- host entry points of the kernels
-// Grid of the balanced RHS launch: RHS_MIN_BLOCKS CTAs per SM of the
-// current device, at most one per plane-tile.
-int rhs_grid(long long work);
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
 void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);
 void launch_fill(const FillArgs& a, void* stream);

@@ -157,9 +157,10 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
       R.out_buf = out_buf[l];
       R.tiles_x = (n[0] + RHS_TX - 1) / RHS_TX;
       R.tiles_y = (n[1] + RHS_TY - 1) / RHS_TY;
-      R.work0 = 0;
-      r.work = (long long)R.tiles_x * R.tiles_y * n[2];
-      launch_rhs(r, rhs_grid(r.work), true, s);
+      R.zc = 8;
+      R.zchunks = (n[2] + R.zc - 1) / R.zc;
+      R.block0 = 0;
+      launch_rhs(r, R.tiles_x * R.tiles_y * R.zchunks, true, s);
     }
     t += dt;
   }

@@ -32,7 +32,6 @@
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
-#include <algorithm>
 #include <cstdint>
 
 #include "mpw_fixed.cuh"
@@ -184,46 +183,34 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   double* slots = reinterpret_cast<double*>(base);
   long long* conv = reinterpret_cast<long long*>(slots + RHS_DEPTH * SLOT_DOUBLES);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(conv + CONV_SLOTS * 2 * CONV_PLANE);
-  if (threadIdx.x == 0) {
-    s_abort = 0;
-    for (int s = 0; s < RHS_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  }
-  // Balanced split: the plane-tiles of every patch (columns of 32 x 8 points,
-  // one plane deep) in one linear order, z fastest; CTA b takes the range
-  // [W b / G, W (b + 1) / G), i.e. a few column segments.  The mbarrier
-  // phases run on across segments (itg counts this CTA's iterations).
-  const long long W = A.work;
-  long long pos = W * blockIdx.x / gridDim.x;
-  const long long end = W * (blockIdx.x + 1) / gridDim.x;
-  unsigned itg = 0;
-  while (pos < end) {
+  const int b = blockIdx.x;
   int p = 0;
-  while (p + 1 < A.np && pos >= A.p[p + 1].work0) ++p;
+  while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
   const RhsPatch& Pt = A.p[p];
   const Geom& g = Pt.g;
-  const long long lpos = pos - Pt.work0;
-  const int col = (int)(lpos / g.n[2]);
-  const int z0 = (int)(lpos - (long long)col * g.n[2]);
-  const int z1 = (int)min((long long)g.n[2], z0 + (end - pos));
-  const int tx = col % Pt.tiles_x, ty = col / Pt.tiles_x;
+  int lb = b - Pt.block0;
+  const int tx = lb % Pt.tiles_x;
+  lb /= Pt.tiles_x;
+  const int ty = lb % Pt.tiles_y;
+  const int tz = lb / Pt.tiles_y;
   const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
   const int i0 = tx * TX, j0 = ty * TY;
   const int i = i0 + li, j = j0 + lj;
-  // the previous segment's readers of T, the ring and the slots are done
-  __syncthreads();
+  const int z0 = tz * Pt.zc, z1 = min(z0 + Pt.zc, g.n[2]);
   if (threadIdx.x == 0) {
     // input scale: live values and the ghost values the fill wrote
     const int Es = max(A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 0) + EXP_GHOST]);
     const int Ep = max(A.expo[slot(p, Pt.in_buf, 1)], A.expo[slot(p, Pt.in_buf, 1) + EXP_GHOST]);
     setup_terms(T, Pt, Es, Ep, FIXED, A.alpha, A.beta);
-    for (int s = 0; s < RHS_DEPTH && z0 + s < z1; ++s) {
-      const unsigned q = (itg + s) % RHS_DEPTH;
-      issue_slot(Pt, A.stage, slots + q * SLOT_DOUBLES, smem_u32(&bars[q]), i0, j0, z0 + s);
-    }
+    s_abort = 0;
+    for (int s = 0; s < RHS_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
+  if (threadIdx.x == 0)
+    for (int s = 0; s < RHS_DEPTH && z0 + s < z1; ++s)
+      issue_slot(Pt, A.stage, slots + s * SLOT_DOUBLES, smem_u32(&bars[s]), i0, j0, z0 + s);
   const bool in_box = (i < g.n[0] + NG) && (j < g.n[1] + NG);
   const bool in_xy = (i < g.n[0]) && (j < g.n[1]);
   bool check_flags = false;
@@ -285,13 +272,13 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   }
   int emax_s = 0, emax_p = 0;
   for (int z = z0; z < z1; ++z) {
-    const unsigned it = itg + (unsigned)(z - z0);
-    const int s = (int)(it % RHS_DEPTH);
+    const int it = z - z0;
+    const int s = it % RHS_DEPTH;
     const double* sl = slots + s * SLOT_DOUBLES;
     const unsigned bar = smem_u32(&bars[s]);
     int fl = FLAG_LIVE;
     if (in_xy && check_flags) fl = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
-    if (!bar_wait(bar, (it / RHS_DEPTH) & 1u)) s_abort = 1;
+    if (!bar_wait(bar, (unsigned)(it / RHS_DEPTH) & 1u)) s_abort = 1;
     // raw values of this iteration
     const double rs_own = sl[own_raw], rp_own = sl[BOX_X * BOX_Y + own_raw];
     double rs_h = 0.0, rp_h = 0.0;
@@ -314,10 +301,8 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
       // drain this CTA's copies still in flight (bounded), report, leave
       if (threadIdx.x == 0) {
         atomicOr(A.err, ERR_TIMEOUT);
-        for (int k = z - z0; k < z - z0 + RHS_DEPTH && z0 + k < z1; ++k) {
-          const unsigned kk = itg + (unsigned)k;
-          bar_wait(smem_u32(&bars[kk % RHS_DEPTH]), (kk / RHS_DEPTH) & 1u);
-        }
+        for (int k = it; k < it + RHS_DEPTH && z0 + k < z1; ++k)
+          bar_wait(smem_u32(&bars[k % RHS_DEPTH]), (unsigned)(k / RHS_DEPTH) & 1u);
       }
       return;
     }
@@ -449,9 +434,6 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
     if (emax_s) atomicMax(&A.expo[slot(p, Pt.out_buf, 0)], emax_s);
     if (emax_p) atomicMax(&A.expo[slot(p, Pt.out_buf, 1)], emax_p);
   }
-  itg += (unsigned)(z1 - z0);
-  pos += z1 - z0;
-  }
 }
 
 // Host: TMA maps of one field buffer (4-D: x, y, plane, field).
@@ -473,14 +455,6 @@ bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool ti
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
-}
-
-int rhs_grid(long long work) {
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
-      sms <= 0)
-    sms = 152;
-  return (int)std::min<long long>((long long)RHS_MIN_BLOCKS * sms, std::max<long long>(work, 1));
 }
 
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream) {
