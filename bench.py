@@ -40,13 +40,16 @@ BYTES_PER_POINT_STAGE = 64.0
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=1, help="divide the workload resolution (testing only)")
     ap.add_argument("--e2e-steps", type=int, default=3)
-    ap.add_argument("--cpu-sample-scale", type=int, default=2)
-    ap.add_argument("--cpu-sample-steps", type=int, default=1)
+    ap.add_argument("--cpu-sample-scale", type=int, default=1,
+                    help="cpu_baseline: the workload at this resolution divisor")
+    ap.add_argument("--cpu-sample-steps", type=int, default=10, help="cpu_baseline: timed oracle steps")
+    ap.add_argument("--ref-sample-scale", type=int, default=2,
+                    help="--impl reference: resolution divisor of the oracle sample taken per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -144,7 +147,7 @@ def cpu_baseline(args, threads):
     """The oracle as it stands, on the host cores, on a bounded sample."""
     from oracle import pyoracle as po
     from paper_2002_00088_gb300 import workloads as wl
-    w = wl.orbiting_gauss(scale=args.cpu_sample_scale)
+    w = wl.orbiting_gauss(scale=max(args.scale, args.cpu_sample_scale))
     o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
     for p in w.patches:
         o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
@@ -156,8 +159,8 @@ def cpu_baseline(args, threads):
     o.step(w.dt, args.cpu_sample_steps)
     el = time.perf_counter() - t0
     return {"value": live * 4 * args.cpu_sample_steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
-            "sample": f"{args.cpu_sample_steps} step(s) of {w.name} (the workload at 1/{args.cpu_sample_scale} "
-                      f"resolution per axis), {live} live points, {el:.2f} s"}
+            "sample": f"{args.cpu_sample_steps} step(s) of {w.name} after one untimed step, {live} live points, "
+                      f"{el:.2f} s"}
 
 
 def run_reference(args):
@@ -168,7 +171,7 @@ def run_reference(args):
     from paper_2002_00088_gb300 import workloads as wl
     threads = os.cpu_count() or 1
     full = wl.orbiting_gauss(scale=args.scale)
-    w = wl.orbiting_gauss(scale=max(args.scale, args.cpu_sample_scale))
+    w = wl.orbiting_gauss(scale=max(args.scale, args.ref_sample_scale))
     o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
     for p in w.patches:
         o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
@@ -180,7 +183,7 @@ def run_reference(args):
     o.step(w.dt, args.steps)
     el = time.perf_counter() - t0
     value = live * 4 * args.steps / el
-    sample = (f"each step: one oracle step of {w.name} (the workload at 1/{max(args.scale, args.cpu_sample_scale)}"
+    sample = (f"each step: one oracle step of {w.name} (the workload at 1/{max(args.scale, args.ref_sample_scale)}"
               f" resolution per axis), {live} live points")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
