@@ -59,7 +59,12 @@ typedef enum {
 enum { MPW_PATCH_GLOBAL = 0, MPW_PATCH_LOCAL = 1 };
 enum { MPW_BC_ANALYTIC = 0, MPW_BC_PERIODIC = 1, MPW_BC_INTERPATCH = 2 };
 enum { MPW_MOTION_STATIC = 0, MPW_MOTION_LINEAR = 1, MPW_MOTION_CIRCULAR = 2 };
-enum { MPW_ANALYTIC_GAUSS_SUM = 0, MPW_ANALYTIC_PLANE_SUM = 1, MPW_ANALYTIC_HARMONIC_POLY = 2 };
+enum {
+  MPW_ANALYTIC_GAUSS_SUM = 0,
+  MPW_ANALYTIC_PLANE_SUM = 1,
+  MPW_ANALYTIC_HARMONIC_POLY = 2,
+  MPW_ANALYTIC_PLANE_GAUSS = 3
+};
 /* Cover-flag byte of a global interior cell: state | (owning local patch id << 2). */
 enum { MPW_FLAG_LIVE = 0, MPW_FLAG_GHOST = 1, MPW_FLAG_DEAD = 2, MPW_FLAG_REVIVED = 3 };
 
@@ -70,7 +75,12 @@ typedef void* (*mpw_alloc_fn)(size_t bytes, void* user);
 typedef void (*mpw_free_fn)(void* ptr, void* user);
 
 typedef struct {
-  int precision;      /* 64 (IEEE binary64); no other value is accepted */
+  int precision;      /* 64: fields stored in IEEE binary64 (the paper's precision);
+                         32: fields stored in binary32 and the stencil, stage and
+                         interpolation arithmetic done in binary32, with the maps, the
+                         Lagrange weights (rounded once), the closed forms and time in
+                         binary64.  Field arrays exchanged through the ABI stay binary64
+                         either way (converted on the device). */
   int ghost;          /* NG, must be 3 (the reach of the KO stencil, Sec. 2.4.2) */
   int interp_points;  /* Lagrange window P: 6 (the paper's i_c-2..i_c+3) or 5 (i_c-2..i_c+2) */
   double ko_eps;      /* Kreiss-Oliger strength epsilon (Sec. 2.3; the paper uses 0.005) */
@@ -116,6 +126,8 @@ mpw_status mpw_create_patch(mpw_ctx* ctx, const mpw_patch_desc* desc, int* patch
  *   HARMONIC_POLY count <= 14 coefficients of the static harmonic basis
  *                 1, x, y, z, xy, yz, zx, x^2-y^2, y^2-z^2, xyz, x^3-3xy^2,
  *                 y^3-3yz^2, z^3-3zx^2, x^4-6x^2y^2+y^4 (Pi = 0).
+ *   PLANE_GAUSS   params (C, A, kx, ky, kz, phase) of one plane wave, then count
+ *                 pulses of 5 params as in GAUSS_SUM: the sum of the two solutions.
  * params is host memory and is copied.  Errors: MPW_ERR_ARG. */
 mpw_status mpw_set_analytic(mpw_ctx* ctx, int kind, const double* params, int count);
 

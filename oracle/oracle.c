@@ -149,7 +149,9 @@ int orc_lagrange(int P, double s, double* w) {
  *             wave_solution and the superposition of Sec. 3.4.2).
  * HARMONIC_POLY params: coefficients of the static harmonic basis
  *             1, x, y, z, xy, yz, zx, x^2-y^2, y^2-z^2, xyz, x^3-3xy^2,
- *             y^3-3yz^2, z^3-3zx^2, x^4-6x^2y^2+y^4;  Pi = 0.            */
+ *             y^3-3yz^2, z^3-3zx^2, x^4-6x^2y^2+y^4;  Pi = 0.
+ * PLANE_GAUSS params (C, A, kx, ky, kz, phase) of one plane wave, then
+ *             count Gaussian pulses as in GAUSS_SUM: their sum.             */
 static void gauss_derivs(double A, double a, double s, double g[5]) {
   double e = A * exp(-a * s * s), s2 = s * s;
   g[0] = e * s;
@@ -190,6 +192,14 @@ void orc_closed_form(int kind, const double* prm, int count, double t, double x,
       ps += wv[0] * sin(th);
       pv -= wv[0] * kk * cos(th);
     }
+  } else if (kind == ORC_PLANE_GAUSS) {
+    /* one plane wave (C, A, kx, ky, kz, phase) plus count Gaussian pulses:
+       the wave equation is linear, so the sum of the two solutions is one */
+    double p1, v1, p2, v2;
+    orc_closed_form(ORC_PLANE_SUM, prm, 1, t, x, y, z, &p1, &v1);
+    orc_closed_form(ORC_GAUSS_SUM, prm + 6, count, t, x, y, z, &p2, &v2);
+    ps = p1 + p2;
+    pv = v1 + v2;
   } else if (kind == ORC_HARMONIC_POLY) {
     double b[14] = {1.0,
                     x,
@@ -286,7 +296,10 @@ int orc_add_patch(orc_sim* s, const orc_patch_desc* d) {
 }
 
 int orc_set_analytic(orc_sim* s, int kind, const double* params, int count) {
-  int need = kind == ORC_GAUSS_SUM ? 5 * count : kind == ORC_PLANE_SUM ? 1 + 5 * count : count;
+  int need = kind == ORC_GAUSS_SUM     ? 5 * count
+             : kind == ORC_PLANE_SUM   ? 1 + 5 * count
+             : kind == ORC_PLANE_GAUSS ? 6 + 5 * count
+                                       : count;
   if (need > ORC_MAX_APARAMS || count < 0) return fail(s, ORC_ERR_ARG, "too many analytic params");
   s->akind = kind;
   s->acount = count;

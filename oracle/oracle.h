@@ -46,7 +46,7 @@ extern "C" {
 enum { ORC_GLOBAL = 0, ORC_LOCAL = 1 };
 enum { ORC_BC_ANALYTIC = 0, ORC_BC_PERIODIC = 1, ORC_BC_INTERPATCH = 2 };
 enum { ORC_STATIC = 0, ORC_LINEAR = 1, ORC_CIRCULAR = 2 };
-enum { ORC_GAUSS_SUM = 0, ORC_PLANE_SUM = 1, ORC_HARMONIC_POLY = 2 };
+enum { ORC_GAUSS_SUM = 0, ORC_PLANE_SUM = 1, ORC_HARMONIC_POLY = 2, ORC_PLANE_GAUSS = 3 };
 /* flag byte of a global interior cell: state | (owning local patch << 2) */
 enum { ORC_LIVE = 0, ORC_GHOST = 1, ORC_DEAD = 2, ORC_REVIVED = 3 };
 

@@ -8,7 +8,7 @@ from . import LIB_PATH, build_oracle
 GLOBAL, LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
 STATIC, LINEAR, CIRCULAR = 0, 1, 2
-GAUSS_SUM, PLANE_SUM, HARMONIC_POLY = 0, 1, 2
+GAUSS_SUM, PLANE_SUM, HARMONIC_POLY, PLANE_GAUSS = 0, 1, 2, 3
 LIVE, GHOST, DEAD, REVIVED = 0, 1, 2, 3
 NG = 3
 

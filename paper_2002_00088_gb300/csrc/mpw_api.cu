@@ -49,10 +49,14 @@ struct PatchState {
   mpw_patch_desc d;
   Geom g;
   bool u_expo_valid = false;  // exponent slots of u track its live values
-  double* base = nullptr;     // 4 buffers x 2 fields x vol doubles
+  double* base = nullptr;     // 4 buffers x 2 fields x vol elements (binary64, or binary32 when esize = 4)
+  size_t esize = 8;           // bytes per element
   CUtensorMap tile_map[4];    // RHS input tiles of each buffer (TMA)
   CUtensorMap point_map[2];   // RHS stage operands: u, ACC (TMA)
-  double* buf(int b) const { return base + (size_t)b * 2 * (size_t)g.vol; }
+  // device address of buffer b (its element type follows esize)
+  double* buf(int b) const {
+    return reinterpret_cast<double*>(reinterpret_cast<char*>(base) + (size_t)b * 2 * (size_t)g.vol * esize);
+  }
 };
 
 }  // namespace
@@ -360,6 +364,7 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   a.rev_list = c->d_rev;
   a.rev_count = c->d_err + 32;
   a.rev_cap = REVIVE_CAP;
+  a.f32 = c->cfg.precision == 32;
   c->launch_begin(MPW_KERNEL_FLAGS);
   const int kernels = launch_flags(a, c->stream);  // flags kernel, plus the revival kernel when old flags exist
   c->launches[MPW_KERNEL_FLAGS] += kernels - 1;
@@ -528,6 +533,7 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   a.reset_buf = reset_buf;
   a.np = (int)c->p.size();
   a.fixed = c->cfg.arith != 1;
+  a.f32 = c->cfg.precision == 32;
   c->launch_begin(MPW_KERNEL_FILL);
   launch_fill(a, c->stream);
   c->launch_end(MPW_KERNEL_FILL);
@@ -586,7 +592,10 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
     blocks += R.tiles_x * R.tiles_y * R.zchunks;
   }
   c->launch_begin(MPW_KERNEL_RHS);
-  launch_rhs(a, blocks, c->cfg.arith != 1, c->stream);
+  if (c->cfg.precision == 32)
+    launch_rhs32(a, blocks, c->stream);
+  else
+    launch_rhs(a, blocks, c->cfg.arith != 1, c->stream);
   c->launch_end(MPW_KERNEL_RHS);
   CUDA_TRY(cudaGetLastError());
   return MPW_OK;
@@ -595,6 +604,7 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
 // Recompute the exponent slots of u for patches whose u was written from
 // outside a step (creation, set_fields, fill_analytic).
 mpw_status ensure_u_exponents(mpw_ctx* c) {
+  if (c->cfg.precision == 32) return MPW_OK;  // the slots scale binary64 fixed-point arithmetic only
   for (size_t q = 0; q < c->p.size(); ++q) {
     PatchState& P = c->p[q];
     if (P.u_expo_valid) continue;
@@ -612,8 +622,9 @@ mpw_status ensure_u_exponents(mpw_ctx* c) {
 // the largest patch or centre coordinate.
 mpw_status upload_screen(mpw_ctx* c) {
   c->screen_ok = false;
-  if (c->akind != MPW_ANALYTIC_GAUSS_SUM || c->acount <= 0) return MPW_OK;
-  const double* params = c->aparams.data();
+  if ((c->akind != MPW_ANALYTIC_GAUSS_SUM && c->akind != MPW_ANALYTIC_PLANE_GAUSS) || c->acount <= 0) return MPW_OK;
+  // the pulses' parameters (after the plane wave for PLANE_GAUSS)
+  const double* params = c->aparams.data() + (c->akind == MPW_ANALYTIC_PLANE_GAUSS ? 6 : 0);
   double extent = 1.0;
   for (const auto& P : c->p)
     for (int a = 0; a < 3; ++a) extent = std::max(extent, std::max(std::fabs(P.d.lo[a]), std::fabs(P.d.hi[a])));
@@ -664,7 +675,7 @@ const char* mpw_last_error(void) { return g_last_error.c_str(); }
 mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out) {
   if (!cfg || !out) return set_err(MPW_ERR_ARG, "null argument");
   *out = nullptr;
-  if (cfg->precision != 64) return set_err(MPW_ERR_ARG, "precision must be 64");
+  if (cfg->precision != 64 && cfg->precision != 32) return set_err(MPW_ERR_ARG, "precision must be 64 or 32");
   if (cfg->ghost != NG) return set_err(MPW_ERR_ARG, "ghost must be %d", NG);
   if (cfg->interp_points != 5 && cfg->interp_points != 6) return set_err(MPW_ERR_ARG, "interp_points must be 5 or 6");
   if (!(cfg->ko_eps >= 0.0)) return set_err(MPW_ERR_ARG, "ko_eps must be >= 0");
@@ -751,17 +762,19 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
   PatchState P;
   P.d = *d;
   P.g = make_geom(*d);
-  const size_t bytes = sizeof(double) * 8 * (size_t)P.g.vol;
+  const bool f32 = c->cfg.precision == 32;
+  P.esize = f32 ? 4 : 8;
+  const size_t bytes = P.esize * 8 * (size_t)P.g.vol;
   P.base = (double*)c->dalloc(bytes);
   if (!P.base) return set_err(MPW_ERR_CUDA, "allocation of %zu bytes failed", bytes);
   CUDA_TRY(cudaMemsetAsync(P.base, 0, bytes, c->stream));
   for (int b = 0; b < 4; ++b)
-    if (!encode_rhs_map(&P.tile_map[b], P.buf(b), P.g, true)) {
+    if (!encode_rhs_map(&P.tile_map[b], P.buf(b), P.g, true, f32)) {
       c->dfree(P.base);
       return set_err(MPW_ERR_CUDA, "tensor map encoding failed");
     }
-  if (!encode_rhs_map(&P.point_map[0], P.buf(BUF_U), P.g, false) ||
-      !encode_rhs_map(&P.point_map[1], P.buf(BUF_ACC), P.g, false)) {
+  if (!encode_rhs_map(&P.point_map[0], P.buf(BUF_U), P.g, false, f32) ||
+      !encode_rhs_map(&P.point_map[1], P.buf(BUF_ACC), P.g, false, f32)) {
     c->dfree(P.base);
     return set_err(MPW_ERR_CUDA, "tensor map encoding failed");
   }
@@ -788,6 +801,8 @@ mpw_status mpw_set_analytic(mpw_ctx* c, int kind, const double* params, int coun
     need = 1 + 5 * count;
   else if (kind == MPW_ANALYTIC_HARMONIC_POLY)
     need = count;
+  else if (kind == MPW_ANALYTIC_PLANE_GAUSS)
+    need = 6 + 5 * count;
   else
     return set_err(MPW_ERR_ARG, "unknown analytic kind %d", kind);
   if (count < 0 || need > MAX_APARAMS || (kind == MPW_ANALYTIC_HARMONIC_POLY && count > 14) || (need && !params))
@@ -813,7 +828,8 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
     double X0[3], w[3];
     motion(P.d, t, X0, w);
     launch_analytic(P.buf(BUF_U), P.g, X0[0], X0[1], X0[2], c->akind, c->acount, c->d_aparams,
-                    c->screen_ok ? c->d_ascreen : nullptr, c->screen_ok ? c->d_apre : nullptr, t, c->stream);
+                    c->screen_ok ? c->d_ascreen : nullptr, c->screen_ok ? c->d_apre : nullptr, t,
+                    c->cfg.precision == 32, c->stream);
     CUDA_TRY(cudaGetLastError());
     P.u_expo_valid = false;
   }
@@ -861,7 +877,7 @@ mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double
     s0 = c->d_stage;
     s1 = c->d_stage + n;
   }
-  launch_unpack(P->buf(BUF_U), P->g, s0, s1, c->stream);
+  launch_unpack(P->buf(BUF_U), P->g, s0, s1, c->cfg.precision == 32, c->stream);
   CUDA_TRY(cudaGetLastError());
   P->u_expo_valid = false;
   if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -879,11 +895,12 @@ static mpw_status get_impl(mpw_ctx* c, int patch, double* psi, double* pi, int o
   double* a0 = on_device ? nullptr : (double*)pinned_alias(psi);
   double* a1 = on_device ? nullptr : (double*)pinned_alias(pi);
   if (on_device || (a0 && a1)) {
-    launch_pack(P->buf(BUF_U), P->g, on_device ? psi : a0, on_device ? pi : a1, padded, flags, c->stream);
+    launch_pack(P->buf(BUF_U), P->g, on_device ? psi : a0, on_device ? pi : a1, padded, flags,
+                c->cfg.precision == 32, c->stream);
     CUDA_TRY(cudaGetLastError());
   } else {
     if ((st = ensure_stage(c, 2 * n * sizeof(double)))) return st;
-    launch_pack(P->buf(BUF_U), P->g, c->d_stage, c->d_stage + n, padded, flags, c->stream);
+    launch_pack(P->buf(BUF_U), P->g, c->d_stage, c->d_stage + n, padded, flags, c->cfg.precision == 32, c->stream);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(psi, c->d_stage, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaMemcpyAsync(pi, c->d_stage + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));

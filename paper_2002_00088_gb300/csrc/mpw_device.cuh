@@ -81,35 +81,54 @@ __device__ __forceinline__ void gauss_pulse(double A, double a, double r2, doubl
   pv += (ep * (1.0 + 2.0 * qp) - em * (1.0 + 2.0 * qm)) * inv;
 }
 
-// apre (may be null): 1/width^2 of every Gaussian pulse, precomputed.
+// Sum of Gaussian pulses (params 5 per pulse), accumulated into ps, pv.
+// apre (may be null): 1/width^2 of every pulse, precomputed.
+__device__ __forceinline__ void gauss_sum(const double* __restrict__ P, const float4* __restrict__ screen,
+                                          const double* __restrict__ apre, int count, double t, double x, double y,
+                                          double z, double& ps, double& pv) {
+  const float xf = (float)x, yf = (float)y, zf = (float)z, tf = fabsf((float)t) * 1.000001f;
+  for (int q = 0; q < count; ++q) {
+    if (screen) {
+      const float4 s = screen[q];
+      const float ex = xf - s.x, ey = yf - s.y, ez = zf - s.z, lim = tf + s.w;
+      if (ex * ex + ey * ey + ez * ez > lim * lim) continue;
+    }
+    const double* g = P + 5 * q;
+    const double dx = x - g[2], dy = y - g[3], dz = z - g[4];
+    const double a = apre ? apre[q] : 1.0 / (g[1] * g[1]);
+    gauss_pulse(g[0], a, dx * dx + dy * dy + dz * dz, t, ps, pv);
+  }
+}
+
+// Constant plus plane waves (params C, then 5 per wave), accumulated.
+__device__ __forceinline__ void plane_sum(const double* __restrict__ P, int count, double t, double x, double y,
+                                          double z, double& ps, double& pv) {
+  ps += P[0];
+  for (int q = 0; q < count; ++q) {
+    const double* wv = P + 1 + 5 * q;
+    const double kk = sqrt(wv[1] * wv[1] + wv[2] * wv[2] + wv[3] * wv[3]);
+    double sn, cs;
+    sincos(wv[1] * x + wv[2] * y + wv[3] * z - kk * t + wv[4], &sn, &cs);
+    ps += wv[0] * sn;
+    pv -= wv[0] * kk * cs;
+  }
+}
+
+// The closed forms of mpw_set_analytic (kinds GAUSS_SUM 0, PLANE_SUM 1,
+// HARMONIC_POLY 2, PLANE_GAUSS 3) at time t and point (x, y, z).
 __device__ __forceinline__ void closed_form(int kind, const double* __restrict__ P, const float4* __restrict__ screen,
                                             const double* __restrict__ apre, int count, double t, double x, double y,
                                             double z, double& ps, double& pv) {
   ps = 0.0;
   pv = 0.0;
   if (kind == 0) {
-    const float xf = (float)x, yf = (float)y, zf = (float)z, tf = fabsf((float)t) * 1.000001f;
-    for (int q = 0; q < count; ++q) {
-      if (screen) {
-        const float4 s = screen[q];
-        const float ex = xf - s.x, ey = yf - s.y, ez = zf - s.z, lim = tf + s.w;
-        if (ex * ex + ey * ey + ez * ez > lim * lim) continue;
-      }
-      const double* g = P + 5 * q;
-      const double dx = x - g[2], dy = y - g[3], dz = z - g[4];
-      const double a = apre ? apre[q] : 1.0 / (g[1] * g[1]);
-      gauss_pulse(g[0], a, dx * dx + dy * dy + dz * dz, t, ps, pv);
-    }
+    gauss_sum(P, screen, apre, count, t, x, y, z, ps, pv);
   } else if (kind == 1) {
-    ps = P[0];
-    for (int q = 0; q < count; ++q) {
-      const double* wv = P + 1 + 5 * q;
-      const double kk = sqrt(wv[1] * wv[1] + wv[2] * wv[2] + wv[3] * wv[3]);
-      double sn, cs;
-      sincos(wv[1] * x + wv[2] * y + wv[3] * z - kk * t + wv[4], &sn, &cs);
-      ps += wv[0] * sn;
-      pv -= wv[0] * kk * cs;
-    }
+    plane_sum(P, count, t, x, y, z, ps, pv);
+  } else if (kind == 3) {
+    // one plane wave plus the pulses: the wave equation is linear
+    plane_sum(P, 1, t, x, y, z, ps, pv);
+    gauss_sum(P + 6, screen, apre, count, t, x, y, z, ps, pv);
   } else {
     const double basis[14] = {1.0,
                               x,
@@ -162,16 +181,16 @@ __device__ __forceinline__ int lagrange_weights(double s, double* w) {
 // Tensor-product interpolation of both fields of a donor box at the numeric
 // position (x, y, z).  The window must lie inside the donor interior; returns
 // false (point skipped) otherwise.
-template <int P>
-__device__ __forceinline__ bool interp_point(const double* __restrict__ src, const Geom& g, double x, double y, double z,
+template <int P, typename ST>
+__device__ __forceinline__ bool interp_point(const ST* __restrict__ src, const Geom& g, double x, double y, double z,
                              double& o0, double& o1) {
   double wx[P], wy[P], wz[P];
   const int sx = lagrange_weights<P>((x - g.lo[0]) / g.h[0] - 0.5, wx);
   const int sy = lagrange_weights<P>((y - g.lo[1]) / g.h[1] - 0.5, wy);
   const int sz = lagrange_weights<P>((z - g.lo[2]) / g.h[2] - 0.5, wz);
   if (sx < 0 || sy < 0 || sz < 0 || sx + P > g.n[0] || sy + P > g.n[1] || sz + P > g.n[2]) return false;
-  const double* s0 = src;
-  const double* s1 = src + g.vol;
+  const ST* s0 = src;
+  const ST* s1 = src + g.vol;
   double a0 = 0.0, a1 = 0.0;
 #pragma unroll
   for (int c = 0; c < P; ++c) {
@@ -182,8 +201,8 @@ __device__ __forceinline__ bool interp_point(const double* __restrict__ src, con
       double r0 = 0.0, r1 = 0.0;
 #pragma unroll
       for (int a = 0; a < P; ++a) {
-        r0 = fma(wx[a], s0[row + a], r0);
-        r1 = fma(wx[a], s1[row + a], r1);
+        r0 = fma(wx[a], (double)s0[row + a], r0);
+        r1 = fma(wx[a], (double)s1[row + a], r1);
       }
       b0 = fma(wy[b], r0, b0);
       b1 = fma(wy[b], r1, b1);

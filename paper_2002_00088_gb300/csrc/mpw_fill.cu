@@ -101,9 +101,12 @@ struct Acc3 {
 // (extents din, x fastest, field f at in + f * in_stride) against the 1-D
 // weights of the tile's targets along AX.  ws holds the absolute window
 // starts, off the block origin along AX, w the P weights per target.  FX
-// selects the fixed-point form (int2 entries, split output; FINAL keeps the
-// last output whole as long long).
-template <int P, int AX, bool FX, bool FINAL>
+// is the arithmetic: M_FP64 (double entries), M_FIXED (int2 entries, split
+// output; FINAL keeps the last output whole as long long) or M_FP32 (float
+// entries and weights).
+enum { M_FP64 = 0, M_FIXED = 1, M_FP32 = 2 };
+
+template <int P, int AX, int MODE, bool FINAL>
 __device__ __forceinline__ void contract_axis(const void* __restrict__ in, int in_stride, void* __restrict__ out,
                                               int out_stride, const int din[3], int T, const void* __restrict__ w,
                                               const int* __restrict__ ws, int off) {
@@ -121,7 +124,7 @@ __device__ __forceinline__ void contract_axis(const void* __restrict__ in, int i
     if (AX == 1) o1 = c;
     if (AX == 2) o2 = c;
     const int src = f * in_stride + o0 + o1 * s1 + o2 * s2;
-    if (FX) {
+    if (MODE == M_FIXED) {
       const int2* a = static_cast<const int2*>(in) + src;
       const int2* wt = static_cast<const int2*>(w) + t * 6;
       Acc3 acc;
@@ -131,6 +134,13 @@ __device__ __forceinline__ void contract_axis(const void* __restrict__ in, int i
         static_cast<long long*>(out)[f * out_stride + r] = acc.value();
       else
         static_cast<int2*>(out)[f * out_stride + r] = split31(acc.value());
+    } else if (MODE == M_FP32) {
+      const float* a = static_cast<const float*>(in) + src;
+      const float* wt = static_cast<const float*>(w) + t * 6;
+      float acc = 0.0f;
+#pragma unroll
+      for (int m = 0; m < P; ++m) acc = fmaf(wt[m], a[m * st], acc);
+      static_cast<float*>(out)[f * out_stride + r] = acc;
     } else {
       const double* a = static_cast<const double*>(in) + src;
       const double* wt = static_cast<const double*>(w) + t * 6;
@@ -142,15 +152,15 @@ __device__ __forceinline__ void contract_axis(const void* __restrict__ in, int i
   }
 }
 
-template <int P, bool FX, bool FINAL>
+template <int P, int MODE, bool FINAL>
 __device__ __forceinline__ void contract(const void* in, int in_stride, void* out, int out_stride, const int din[3],
                                          int ax, int T, const void* w, const int* ws, int off) {
   if (ax == 0)
-    contract_axis<P, 0, FX, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
+    contract_axis<P, 0, MODE, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
   else if (ax == 1)
-    contract_axis<P, 1, FX, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
+    contract_axis<P, 1, MODE, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
   else
-    contract_axis<P, 2, FX, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
+    contract_axis<P, 2, MODE, FINAL>(in, in_stride, out, out_stride, din, T, w, ws, off);
 }
 
 // Thin-axis pass fused with the donor load: one thread per donor pencil
@@ -159,7 +169,7 @@ __device__ __forceinline__ void contract(const void* in, int in_stride, void* ou
 // a0 (row t: the P weights of target t at its window offset, zeros
 // elsewhere).  Output: the block with extent T0 along a0 and the donor
 // extents along the other axes, x fastest.
-template <int P, bool FX>
+template <int P, int MODE, typename ST>
 __device__ __forceinline__ void thin_pass(const InterpSeg& S, int a0, const int D0[3], const int Dn[3], int T0,
                                           const void* __restrict__ band, int Es, int Ep, void* __restrict__ out) {
   const int a1 = a0 == 0 ? 1 : 0, a2 = a0 == 2 ? 1 : 2;
@@ -178,13 +188,27 @@ __device__ __forceinline__ void thin_pass(const InterpSeg& S, int a0, const int 
     o[a0] = D0[a0];
     o[a1] = D0[a1] + c1;
     o[a2] = D0[a2] + c2;
-    const double* src = S.D + f * S.gd.vol + S.gd.at(o[0], o[1], o[2]);
+    const ST* src = reinterpret_cast<const ST*>(S.D) + f * S.gd.vol + S.gd.at(o[0], o[1], o[2]);
     const int obase = c1 * ostr[a1] + c2 * ostr[a2] + f * CAP_R1;
-    if (FX) {
+    if (MODE == M_FP32) {
+      float v[MAXD];
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) v[k] = k < nk ? (float)src[k * st0] : 0.0f;
+      const float* bf = static_cast<const float*>(band);
+#pragma unroll
+      for (int t = 0; t < MAXT0; ++t) {
+        if (t >= T0) break;
+        float acc = 0.0f;
+#pragma unroll
+        for (int k = 0; k < MAXD; ++k)
+          if (k < nk) acc = fmaf(bf[t * MAXD + k], v[k], acc);
+        static_cast<float*>(out)[obase + t * ostr[a0]] = acc;
+      }
+    } else if (MODE == M_FIXED) {
       const int E = f ? Ep : Es;
       int2 v[MAXD];
 #pragma unroll
-      for (int k = 0; k < MAXD; ++k) v[k] = split31(k < nk ? to_fixed(src[k * st0], E) * 64 : 0);
+      for (int k = 0; k < MAXD; ++k) v[k] = split31(k < nk ? to_fixed((double)src[k * st0], E) * 64 : 0);
       const int2* bq = static_cast<const int2*>(band);
 #pragma unroll
       for (int t = 0; t < MAXT0; ++t) {
@@ -198,7 +222,7 @@ __device__ __forceinline__ void thin_pass(const InterpSeg& S, int a0, const int 
     } else {
       double v[MAXD];
 #pragma unroll
-      for (int k = 0; k < MAXD; ++k) v[k] = k < nk ? src[k * st0] : 0.0;
+      for (int k = 0; k < MAXD; ++k) v[k] = k < nk ? (double)src[k * st0] : 0.0;
       const double* bd = static_cast<const double*>(band);
 #pragma unroll
       for (int t = 0; t < MAXT0; ++t) {
@@ -213,16 +237,23 @@ __device__ __forceinline__ void thin_pass(const InterpSeg& S, int a0, const int 
   }
 }
 
-template <int P>
+// One interpolation tile.  ST is the storage type of the field buffers:
+// double (arithmetic FP64 or fixed point, FillArgs::fixed) or float (FP32
+// arithmetic, with the weights computed in FP64 and rounded once).
+template <int P, typename ST>
 __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], int a0,
                             double* sm) {
+  constexpr bool F32 = sizeof(ST) == 4;
   double* R1 = sm;                          // [2][CAP_R1]
   double* R2 = R1 + 2 * CAP_R1;             // [2][CAP_R2]
   double* W = R2 + 2 * CAP_R2;              // [3][MAXT][6]
-  int2* WQ = reinterpret_cast<int2*>(W + 3 * MAXT * 6);  // [3][MAXT][6] weights on 2^59, split
+  int2* WQ = reinterpret_cast<int2*>(W + 3 * MAXT * 6);  // [3][MAXT][6] weights on 2^59 split, or binary32
   double* BW = reinterpret_cast<double*>(WQ + 3 * MAXT * 6);  // [MAXT0][MAXD] band matrix of the thin axis
-  int2* BQ = reinterpret_cast<int2*>(BW + MAXT0 * MAXD);
+  int2* BQ = reinterpret_cast<int2*>(BW + MAXT0 * MAXD);      // the same on 2^59 split, or binary32
   int* WS = reinterpret_cast<int*>(BQ + MAXT0 * MAXD);   // [3][MAXT] window starts
+  float* WF = reinterpret_cast<float*>(WQ);
+  float* BF = reinterpret_cast<float*>(BQ);
+  ST* Tt = reinterpret_cast<ST*>(S.T);
   const int tid = threadIdx.x;
   // 1-D weights of every target index of the tile, per axis; the threads of
   // the thin axis also write their row of the band matrix
@@ -235,7 +266,10 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
 #pragma unroll
     for (int m = 0; m < P; ++m) {
       W[(a * MAXT + k) * 6 + m] = w[m];
-      WQ[(a * MAXT + k) * 6 + m] = split31(__double2ll_rn(w[m] * 0x1p59));
+      if (F32)
+        WF[(a * MAXT + k) * 6 + m] = (float)w[m];
+      else
+        WQ[(a * MAXT + k) * 6 + m] = split31(__double2ll_rn(w[m] * 0x1p59));
     }
     if (a == a0 && k < MAXT0) {
       double w0[P];
@@ -248,7 +282,10 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
         for (int mm = 0; mm < P; ++mm)
           if (mm == m) wm = w[mm];
         BW[k * MAXD + q] = in ? wm : 0.0;
-        BQ[k * MAXD + q] = in ? split31(__double2ll_rn(wm * 0x1p59)) : make_int2(0, 0);
+        if (F32)
+          BF[k * MAXD + q] = in ? (float)wm : 0.0f;
+        else
+          BQ[k * MAXD + q] = in ? split31(__double2ll_rn(wm * 0x1p59)) : make_int2(0, 0);
       }
     }
   }
@@ -279,13 +316,13 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
       const double px = S.gt.lo[0] + (i + 0.5) * S.gt.h[0] + S.shift[0];
       const double py = S.gt.lo[1] + (j + 0.5) * S.gt.h[1] + S.shift[1];
       const double pz = S.gt.lo[2] + (k + 0.5) * S.gt.h[2] + S.shift[2];
-      if (!interp_point<P>(S.D, S.gd, px, py, pz, v0, v1)) {
+      if (!interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, px, py, pz, v0, v1)) {
         atomicOr(A.err, ERR_UNFILLED);
         continue;
       }
       const long long c = S.gt.at(i, j, k);
-      S.T[c] = v0;
-      S.T[c + S.gt.vol] = v1;
+      Tt[c] = (ST)v0;
+      Tt[c + S.gt.vol] = (ST)v1;
       emax[0] = max(emax[0], biased_exponent(v0));
       emax[1] = max(emax[1], biased_exponent(v1));
     }
@@ -299,13 +336,27 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
     // slots), so the scale is known before the donors are read
     const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
     const int Es = dslot[0], Ep = dslot[1];
-    if (A.fixed && Es < EXP_NONFINITE && Ep < EXP_NONFINITE) {
+    if (F32) {
+      thin_pass<P, M_FP32, ST>(S, a0, D0, Dn, T[a0], BF, 0, 0, R1);
+      __syncthreads();
+      contract<P, M_FP32, false>(R1, CAP_R1, R2, CAP_R2, d1, x1, T[x1], WF + x1 * MAXT * 6, WS + x1 * MAXT, D0[x1]);
+      __syncthreads();
+      contract<P, M_FP32, false>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], WF + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
+      __syncthreads();
+      const float* out = reinterpret_cast<const float*>(R1);
+      for (int e = tid; e < 2 * ntar; e += FILL_THREADS) {
+        const int f = e >= ntar;
+        const int r = e - f * ntar;
+        const int tx = r % T[0], ty = (r / T[0]) % T[1], tz = r / (T[0] * T[1]);
+        Tt[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = (ST)out[f * CAP_R1 + r];
+      }
+    } else if (A.fixed && Es < EXP_NONFINITE && Ep < EXP_NONFINITE) {
       const int Esu = max(Es, 64), Epu = max(Ep, 64);
-      thin_pass<P, true>(S, a0, D0, Dn, T[a0], BQ, Esu, Epu, R1);
+      thin_pass<P, M_FIXED, ST>(S, a0, D0, Dn, T[a0], BQ, Esu, Epu, R1);
       __syncthreads();
-      contract<P, true, false>(R1, CAP_R1, R2, CAP_R2, d1, x1, T[x1], WQ + x1 * MAXT * 6, WS + x1 * MAXT, D0[x1]);
+      contract<P, M_FIXED, false>(R1, CAP_R1, R2, CAP_R2, d1, x1, T[x1], WQ + x1 * MAXT * 6, WS + x1 * MAXT, D0[x1]);
       __syncthreads();
-      contract<P, true, true>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], WQ + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
+      contract<P, M_FIXED, true>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], WQ + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
       __syncthreads();
       // results are on 2^(E - 1075 - 6): exact power-of-two scalings
       const double p2[2] = {__longlong_as_double((long long)(Esu - 58) << 52),
@@ -316,34 +367,36 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
         const int r = e - f * ntar;
         const int tx = r % T[0], ty = (r / T[0]) % T[1], tz = r / (T[0] * T[1]);
         const double v = (double)out[f * CAP_R1 + r] * p2[f];
-        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
+        Tt[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = (ST)v;
         emax[f] = max(emax[f], biased_exponent(v));
       }
     } else {
-      thin_pass<P, false>(S, a0, D0, Dn, T[a0], BW, 0, 0, R1);
+      thin_pass<P, M_FP64, ST>(S, a0, D0, Dn, T[a0], BW, 0, 0, R1);
       __syncthreads();
-      contract<P, false, false>(R1, CAP_R1, R2, CAP_R2, d1, x1, T[x1], W + x1 * MAXT * 6, WS + x1 * MAXT, D0[x1]);
+      contract<P, M_FP64, false>(R1, CAP_R1, R2, CAP_R2, d1, x1, T[x1], W + x1 * MAXT * 6, WS + x1 * MAXT, D0[x1]);
       __syncthreads();
-      contract<P, false, false>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], W + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
+      contract<P, M_FP64, false>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], W + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
       __syncthreads();
       for (int e = tid; e < 2 * ntar; e += FILL_THREADS) {
         const int f = e >= ntar;
         const int r = e - f * ntar;
         const int tx = r % T[0], ty = (r / T[0]) % T[1], tz = r / (T[0] * T[1]);
         const double v = R1[f * CAP_R1 + r];
-        S.T[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = v;
+        Tt[S.gt.at(org[0] + tx, org[1] + ty, org[2] + tz) + f * S.gt.vol] = (ST)v;
         emax[f] = max(emax[f], biased_exponent(v));
       }
     }
     // each thread's emax[f] covers only entries of field f, the other stays 0
   }
-  report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, emax[0], emax[1]);
+  // exponent slots are kept for binary64 buffers only (the fixed-point scale)
+  if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, emax[0], emax[1]);
 }
 
 }  // namespace
 
-template <int P>
+template <int P, typename ST>
 __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ FillArgs A) {
+  constexpr bool F32 = sizeof(ST) == 4;
   extern __shared__ double fill_smem[];
   if (A.reset_buf >= 0 && blockIdx.x == 0 && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
@@ -360,26 +413,31 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
       shell_point(idx, O, NG, x, y, z);
       const int i = x - NG, j = y - NG, k = z - NG;
       const long long c = A.gg.at(i, j, k);
-      double w0, w1;
+      ST* Yg = reinterpret_cast<ST*>(A.Yg);
+      const ST* shell = reinterpret_cast<const ST*>(A.shell_src);
+      ST w0, w1;
       if (A.outer_bc == 1) {
         const long long s =
             A.gg.at(wrap_index(i, A.gg.n[0]), wrap_index(j, A.gg.n[1]), wrap_index(k, A.gg.n[2]));
-        w0 = A.Yg[s];
-        w1 = A.Yg[s + A.gg.vol];
-      } else if (A.shell_src) {
+        w0 = Yg[s];
+        w1 = Yg[s + A.gg.vol];
+      } else if (shell) {
         // the closed form at this very time already sits in another buffer's shell
-        w0 = A.shell_src[c];
-        w1 = A.shell_src[c + A.gg.vol];
+        w0 = shell[c];
+        w1 = shell[c + A.gg.vol];
       } else {
+        double v0, v1;
         closed_form(A.akind, A.aparams, A.ascreen, A.apre, A.acount, A.t, A.gg.lo[0] + (i + 0.5) * A.gg.h[0],
-                    A.gg.lo[1] + (j + 0.5) * A.gg.h[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2], w0, w1);
+                    A.gg.lo[1] + (j + 0.5) * A.gg.h[1], A.gg.lo[2] + (k + 0.5) * A.gg.h[2], v0, v1);
+        w0 = (ST)v0;
+        w1 = (ST)v1;
       }
-      A.Yg[c] = w0;
-      A.Yg[c + A.gg.vol] = w1;
-      e0 = biased_exponent(w0);
-      e1 = biased_exponent(w1);
+      Yg[c] = w0;
+      Yg[c + A.gg.vol] = w1;
+      e0 = biased_exponent((double)w0);
+      e1 = biased_exponent((double)w1);
     }
-    report_block_max(A.expo + EXP_GHOST + A.y_buf * 2, e0, e1);
+    if (!F32) report_block_max(A.expo + EXP_GHOST + A.y_buf * 2, e0, e1);
     return;
   }
   // interpolation tile: find its segment, slab and position
@@ -399,18 +457,22 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
     org[a] = S.sb[sl][a] + tt[a] * S.td[sl][a];
     T[a] = min(S.td[sl][a], S.sb[sl][a] + S.se[sl][a] - org[a]);
   }
-  interp_tile<P>(A, S, org, T, 2 - sl / 2, fill_smem);  // slabs come in z, y, x pairs: the wall axis is thin
+  interp_tile<P, ST>(A, S, org, T, 2 - sl / 2, fill_smem);  // slabs come in z, y, x pairs: the wall axis is thin
+}
+
+template <int P, typename ST>
+static void launch_fill_t(const FillArgs& a, cudaStream_t s) {
+  cudaFuncSetAttribute(k_fill<P, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM);
+  k_fill<P, ST><<<a.total_blocks, FILL_THREADS, FILL_SMEM, s>>>(a);
 }
 
 void launch_fill(const FillArgs& a, void* stream) {
   if (a.total_blocks <= 0) return;
-  if (a.P == 6) {
-    cudaFuncSetAttribute(k_fill<6>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM);
-    k_fill<6><<<a.total_blocks, FILL_THREADS, FILL_SMEM, (cudaStream_t)stream>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_fill<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM);
-    k_fill<5><<<a.total_blocks, FILL_THREADS, FILL_SMEM, (cudaStream_t)stream>>>(a);
-  }
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (a.f32)
+    a.P == 6 ? launch_fill_t<6, float>(a, s) : launch_fill_t<5, float>(a, s);
+  else
+    a.P == 6 ? launch_fill_t<6, double>(a, s) : launch_fill_t<5, double>(a, s);
 }
 
 int fill_cap_r1() { return CAP_R1; }

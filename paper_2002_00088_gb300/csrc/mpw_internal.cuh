@@ -118,6 +118,7 @@ struct FillArgs {
   int np;
   int total_blocks;
   int fixed;           // 1: separable contractions in int64 fixed point, 0: native FP64
+  int f32;             // field buffers hold binary32 (FP32 arithmetic; fixed is ignored)
 };
 
 // ---------------------------------------------------------------- flags
@@ -147,6 +148,7 @@ struct FlagArgs {
   long long* rev_list;
   int* rev_count;
   int rev_cap;
+  int f32;             // field buffers hold binary32
 };
 constexpr int REVIVE_CAP = 1 << 16;  // queue entries (one box crossing revives a few thousand cells)
 
@@ -156,11 +158,13 @@ void set_last_error(const char* msg);
 // ---------------------------------------------------------------- tensor maps
 // Encode the TMA maps of the RHS kernel for one field buffer (psi at base, Pi
 // at base + vol) of geometry g: box (RHS_TX + 8) x (RHS_TY + 6) ("tile") or
-// RHS_TX x RHS_TY ("point").  Returns false if the driver rejects the map.
-bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool tile);
+// RHS_TX x RHS_TY ("point"), elements binary64 or (f32) binary32.  Returns
+// false if the driver rejects the map.
+bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile, bool f32 = false);
 
 // ---------------------------------------------------------------- host entry points of the kernels
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
+void launch_rhs32(const RhsArgs& a, int blocks, void* stream);  // binary32 storage and arithmetic
 void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);
 void launch_fill(const FillArgs& a, void* stream);
 int fill_max_thin_donors();
@@ -169,11 +173,14 @@ int fill_cap_r2();
 int fill_max_tile();
 int fill_threads();
 int launch_flags(const FlagArgs& a, void* stream);  // returns the number of kernels launched
-void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
-                     const double* aparams, const float4* screen, const double* apre, double t, void* stream);
-void launch_pack(const double* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags,
+// buf: a field buffer of binary64, or of binary32 when f32; the dense arrays
+// d0, d1 are binary64 in every case.
+void launch_analytic(void* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
+                     const double* aparams, const float4* screen, const double* apre, double t, bool f32,
+                     void* stream);
+void launch_pack(const void* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags, bool f32,
                  void* stream);
-void launch_unpack(double* buf, const Geom& g, const double* d0, const double* d1, void* stream);
+void launch_unpack(void* buf, const Geom& g, const double* d0, const double* d1, bool f32, void* stream);
 
 #ifndef MPW_RHS_TY
 #define MPW_RHS_TY 8

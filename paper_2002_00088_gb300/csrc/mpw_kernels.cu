@@ -20,7 +20,7 @@ namespace mpw {
 // d <= buffer, GHOST if d <= buffer + NG, DEAD beyond.  DEAD cells of u are
 // poisoned with NaN; cells that turn LIVE after having been GHOST or DEAD are
 // REVIVED: u_n there is interpolated from the owning local patch at t_n.
-template <int P>
+template <int P, typename ST>
 __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs A) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   int i, j, k;
@@ -60,9 +60,10 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
   }
   A.flags[idx] = (uint8_t)(st | (owner << 2));
   const long long c = A.gg.at(i, j, k);
+  ST* Ug = reinterpret_cast<ST*>(A.Ug);
   if (st == FLAG_DEAD) {
-    A.Ug[c] = __longlong_as_double(0x7ff8000000000000LL);
-    A.Ug[c + A.gg.vol] = __longlong_as_double(0x7ff8000000000000LL);
+    Ug[c] = (ST)__longlong_as_double(0x7ff8000000000000LL);
+    Ug[c + A.gg.vol] = (ST)__longlong_as_double(0x7ff8000000000000LL);
   } else if (st == FLAG_REVIVED) {
     const int q = owner - 1;
     // queue the cell: a warp holds about one revived cell, and a warp-wide
@@ -73,17 +74,20 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
       return;
     }
     double v0, v1;
-    const bool ok = interp_point<P>(A.Uloc[q], A.gl[q], A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
-                              A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - A.X0[q][1],
-                              A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - A.X0[q][2], v0, v1);
+    const bool ok = interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q],
+                                    A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
+                                    A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - A.X0[q][1],
+                                    A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - A.X0[q][2], v0, v1);
     if (!ok) {
       atomicOr(A.err, ERR_UNFILLED);
       return;
     }
-    A.Ug[c] = v0;
-    A.Ug[c + A.gg.vol] = v1;
-    atomicMax(&A.expo[BUF_U * 2], biased_exponent(v0));
-    atomicMax(&A.expo[BUF_U * 2 + 1], biased_exponent(v1));
+    Ug[c] = (ST)v0;
+    Ug[c + A.gg.vol] = (ST)v1;
+    if (sizeof(ST) == 8) {
+      atomicMax(&A.expo[BUF_U * 2], biased_exponent(v0));
+      atomicMax(&A.expo[BUF_U * 2 + 1], biased_exponent(v1));
+    }
   }
 }
 
@@ -91,7 +95,7 @@ constexpr int REVIVE_BLOCKS = 4 * 152;  // four CTAs per SM of a GB300
 
 // Revival (reading of Sec. 2.4.2): the queued cells take the Lagrange
 // interpolant of their local patch at the current time, densely packed.
-template <int P>
+template <int P, typename ST>
 __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs A) {
   const int count = min(*A.rev_count, A.rev_cap);
   int e0 = 0, e1 = 0;
@@ -106,12 +110,14 @@ __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs
       const int j = (int)(rr % A.n[1]);
       const int k = (int)(rr / A.n[1]);
       double v0, v1;
-      if (interp_point<P>(A.Uloc[q], A.gl[q], A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
+      if (interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q],
+                          A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
                           A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - A.X0[q][1],
                           A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - A.X0[q][2], v0, v1)) {
         const long long c = A.gg.at(i, j, k);
-        A.Ug[c] = v0;
-        A.Ug[c + A.gg.vol] = v1;
+        ST* Ug = reinterpret_cast<ST*>(A.Ug);
+        Ug[c] = (ST)v0;
+        Ug[c + A.gg.vol] = (ST)v1;
         e0 = max(e0, biased_exponent(v0));
         e1 = max(e1, biased_exponent(v1));
       } else {
@@ -121,10 +127,16 @@ __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs
   }
   e0 = __reduce_max_sync(0xffffffffu, e0);
   e1 = __reduce_max_sync(0xffffffffu, e1);
-  if ((threadIdx.x & 31) == 0) {
+  if (sizeof(ST) == 8 && (threadIdx.x & 31) == 0) {
     if (e0) atomicMax(&A.expo[BUF_U * 2], e0);
     if (e1) atomicMax(&A.expo[BUF_U * 2 + 1], e1);
   }
+}
+
+template <int P, typename ST>
+static void launch_flags_t(const FlagArgs& a, unsigned blocks, unsigned rblocks, cudaStream_t s) {
+  k_flags<P, ST><<<blocks, 256, 0, s>>>(a);
+  if (a.old_valid) k_revive<P, ST><<<rblocks, 256, 0, s>>>(a);
 }
 
 int launch_flags(const FlagArgs& a, void* stream) {
@@ -136,19 +148,17 @@ int launch_flags(const FlagArgs& a, void* stream) {
   // the revival kernel walks the queue with a fixed grid (its length is
   // known on the device only); empty queues cost one short launch
   const unsigned rblocks = (unsigned)std::min<long long>((N + 255) / 256, REVIVE_BLOCKS);
-  if (a.P == 6) {
-    k_flags<6><<<blocks, 256, 0, s>>>(a);
-    if (a.old_valid) k_revive<6><<<rblocks, 256, 0, s>>>(a);
-  } else {
-    k_flags<5><<<blocks, 256, 0, s>>>(a);
-    if (a.old_valid) k_revive<5><<<rblocks, 256, 0, s>>>(a);
-  }
+  if (a.f32)
+    a.P == 6 ? launch_flags_t<6, float>(a, blocks, rblocks, s) : launch_flags_t<5, float>(a, blocks, rblocks, s);
+  else
+    a.P == 6 ? launch_flags_t<6, double>(a, blocks, rblocks, s) : launch_flags_t<5, double>(a, blocks, rblocks, s);
   return a.old_valid ? 2 : 1;
 }
 
 // ---------------------------------------------------------------------------
 // Interior <- closed form at time t (positions X_B = numeric + X0).
-__global__ void k_analytic(double* buf, const Geom g, double X0x, double X0y, double X0z, int akind, int acount,
+template <typename ST>
+__global__ void k_analytic(ST* buf, const Geom g, double X0x, double X0y, double X0z, int akind, int acount,
                            const double* __restrict__ P, const float4* __restrict__ screen,
                            const double* __restrict__ apre, double t) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -162,20 +172,27 @@ __global__ void k_analytic(double* buf, const Geom g, double X0x, double X0y, do
   closed_form(akind, P, screen, apre, acount, t, g.lo[0] + (i + 0.5) * g.h[0] + X0x, g.lo[1] + (j + 0.5) * g.h[1] + X0y,
               g.lo[2] + (k + 0.5) * g.h[2] + X0z, ps, pv);
   const long long c = g.at(i, j, k);
-  buf[c] = ps;
-  buf[c + g.vol] = pv;
+  buf[c] = (ST)ps;
+  buf[c + g.vol] = (ST)pv;
 }
 
-void launch_analytic(double* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
-                     const double* aparams, const float4* screen, const double* apre, double t, void* stream) {
+void launch_analytic(void* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
+                     const double* aparams, const float4* screen, const double* apre, double t, bool f32,
+                     void* stream) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_analytic<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)stream>>>(buf, g, X0x, X0y, X0z, akind, acount,
-                                                                            aparams, screen, apre, t);
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  if (f32)
+    k_analytic<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<float*>(buf), g, X0x, X0y, X0z, akind,
+                                                                acount, aparams, screen, apre, t);
+  else
+    k_analytic<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<double*>(buf), g, X0x, X0y, X0z, akind,
+                                                                 acount, aparams, screen, apre, t);
 }
 
 // Padded buffer -> dense array (interior, or the whole padded box).  With
 // flags, global cells that are not live read as NaN.
-__global__ void k_pack(const double* __restrict__ buf, const Geom g, double* __restrict__ d0,
+template <typename ST>
+__global__ void k_pack(const ST* __restrict__ buf, const Geom g, double* __restrict__ d0,
                        double* __restrict__ d1, int padded, const uint8_t* __restrict__ flags) {
   const int e = padded ? 2 * NG : 0, o = padded ? NG : 0;
   const int m0 = g.n[0] + e, m1 = g.n[1] + e, m2 = g.n[2] + e;
@@ -187,7 +204,7 @@ __global__ void k_pack(const double* __restrict__ buf, const Geom g, double* __r
   const int j = (int)(r % m1) - o;
   const int k = (int)(r / m1) - o;
   const long long c = g.at(i, j, k);
-  double v0 = buf[c], v1 = buf[c + g.vol];
+  double v0 = (double)buf[c], v1 = (double)buf[c + g.vol];
   if (flags) {
     const int f = flags[((long long)k * g.n[1] + j) * g.n[0] + i] & 3;
     if (f == FLAG_GHOST || f == FLAG_DEAD) v0 = v1 = __longlong_as_double(0x7ff8000000000000LL);
@@ -196,15 +213,21 @@ __global__ void k_pack(const double* __restrict__ buf, const Geom g, double* __r
   d1[idx] = v1;
 }
 
-void launch_pack(const double* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags,
+void launch_pack(const void* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags, bool f32,
                  void* stream) {
   const int e = padded ? 2 * NG : 0;
   const long long N = (long long)(g.n[0] + e) * (g.n[1] + e) * (g.n[2] + e);
-  k_pack<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)stream>>>(buf, g, d0, d1, padded,
-                                                                        padded ? nullptr : flags);
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  if (f32)
+    k_pack<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<const float*>(buf), g, d0, d1, padded,
+                                                            padded ? nullptr : flags);
+  else
+    k_pack<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<const double*>(buf), g, d0, d1, padded,
+                                                             padded ? nullptr : flags);
 }
 
-__global__ void k_unpack(double* buf, const Geom g, const double* __restrict__ d0, const double* __restrict__ d1) {
+template <typename ST>
+__global__ void k_unpack(ST* buf, const Geom g, const double* __restrict__ d0, const double* __restrict__ d1) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (idx >= N) return;
@@ -213,13 +236,17 @@ __global__ void k_unpack(double* buf, const Geom g, const double* __restrict__ d
   const int j = (int)(r % g.n[1]);
   const int k = (int)(r / g.n[1]);
   const long long c = g.at(i, j, k);
-  buf[c] = d0[idx];
-  buf[c + g.vol] = d1[idx];
+  buf[c] = (ST)d0[idx];
+  buf[c + g.vol] = (ST)d1[idx];
 }
 
-void launch_unpack(double* buf, const Geom& g, const double* d0, const double* d1, void* stream) {
+void launch_unpack(void* buf, const Geom& g, const double* d0, const double* d1, bool f32, void* stream) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_unpack<<<(unsigned)((N + 255) / 256), 256, 0, (cudaStream_t)stream>>>(buf, g, d0, d1);
+  const unsigned blocks = (unsigned)((N + 255) / 256);
+  if (f32)
+    k_unpack<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<float*>(buf), g, d0, d1);
+  else
+    k_unpack<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<double*>(buf), g, d0, d1);
 }
 
 }  // namespace mpw

@@ -101,7 +101,7 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
   int* err = expo + 32;
   cudaStream_t s = (cudaStream_t)stream;
   // state in; exponent slots and error word start at zero on every call
-  launch_unpack(buf[BUF_U], g, psi, pi, s);
+  launch_unpack(buf[BUF_U], g, psi, pi, false, s);
   if (cudaMemsetAsync(expo, 0, 64 * sizeof(int), s) != cudaSuccess) return fail(MPW_ERR_CUDA, "memset");
   launch_expo_scan(buf[BUF_U], g, nullptr, expo + BUF_U * 2, s);
   static const double RK_C[4] = {0.0, 0.5, 0.5, 1.0};
@@ -126,6 +126,7 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
       f.np = 1;
       f.total_blocks = f.outer_blocks;
       f.fixed = 1;
+      f.f32 = 0;
       launch_fill(f, s);
       RhsArgs r{};
       r.np = 1;
@@ -164,7 +165,7 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
     }
     t += dt;
   }
-  launch_pack(buf[BUF_U], g, psi, pi, 0, nullptr, s);
+  launch_pack(buf[BUF_U], g, psi, pi, 0, nullptr, false, s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MPW_ERR_CUDA, cudaGetErrorString(e));
   return MPW_OK;

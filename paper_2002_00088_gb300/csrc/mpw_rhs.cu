@@ -36,6 +36,7 @@
 
 #include "mpw_fixed.cuh"
 #include "mpw_internal.cuh"
+#include "mpw_tma.cuh"
 
 namespace mpw {
 
@@ -121,43 +122,6 @@ constexpr int CONV_PLANE = (RHS_TY + 6) * (RHS_TX + 6);      // one field of a c
 constexpr int CONV_SLOTS = 4;
 constexpr size_t RHS_SMEM = 1024 + sizeof(double) * RHS_DEPTH * SLOT_DOUBLES +
                             sizeof(long long) * CONV_SLOTS * 2 * CONV_PLANE + 8 * RHS_DEPTH;
-constexpr unsigned WAIT_LIMIT = 1u << 20;
-
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void bar_init(unsigned bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void bar_expect_tx(unsigned bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
-}
-
-// Bounded wait for phase `parity` of an mbarrier; false if the limit ran out.
-__device__ __forceinline__ bool bar_wait(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
-    unsigned ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tma_load_4d(unsigned dst, const CUtensorMap* map, int x, int y, int z, int f,
-                                            unsigned bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
-      "%5}], [%6];" ::"r"(dst),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(f), "r"(bar)
-      : "memory");
-}
-
 // Issue the loads of iteration zz (tile of input plane zz+3, u and ACC of
 // plane zz) into slot s.
 __device__ __forceinline__ void issue_slot(const RhsPatch& Pt, int stage, double* slot, unsigned bar, int i0, int j0,
@@ -437,7 +401,7 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
 }
 
 // Host: TMA maps of one field buffer (4-D: x, y, plane, field).
-bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool tile) {
+bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile, bool f32) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
   if (!encode) {
     cudaDriverEntryPointQueryResult q;
@@ -448,10 +412,12 @@ bool encode_rhs_map(CUtensorMap* map, const double* base, const Geom& g, bool ti
     encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
   }
   const cuuint64_t dims[4] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.n[2] + 2 * NG), 2};
-  const cuuint64_t strides[3] = {(cuuint64_t)g.px * 8, (cuuint64_t)g.plane * 8, (cuuint64_t)g.vol * 8};
+  const cuuint64_t es = f32 ? 4 : 8;
+  const cuuint64_t strides[3] = {(cuuint64_t)g.px * es, (cuuint64_t)g.plane * es, (cuuint64_t)g.vol * es};
   const cuuint32_t box[4] = {(cuuint32_t)(tile ? BOX_X : RHS_TX), (cuuint32_t)(tile ? BOX_Y : RHS_TY), 1, 2};
   const cuuint32_t estr[4] = {1, 1, 1, 1};
-  const CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4, const_cast<double*>(base), dims, strides, box,
+  const CUresult r = encode(map, f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 4,
+                            const_cast<void*>(base), dims, strides, box,
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;

@@ -21,7 +21,7 @@ STATUS_NAMES = {0: "MPW_OK", 1: "MPW_ERR_ARG", 2: "MPW_ERR_OVERLAP", 3: "MPW_ERR
 PATCH_GLOBAL, PATCH_LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
 MOTION_STATIC, MOTION_LINEAR, MOTION_CIRCULAR = 0, 1, 2
-ANALYTIC_GAUSS_SUM, ANALYTIC_PLANE_SUM, ANALYTIC_HARMONIC_POLY = 0, 1, 2
+ANALYTIC_GAUSS_SUM, ANALYTIC_PLANE_SUM, ANALYTIC_HARMONIC_POLY, ANALYTIC_PLANE_GAUSS = 0, 1, 2, 3
 FLAG_LIVE, FLAG_GHOST, FLAG_DEAD, FLAG_REVIVED = 0, 1, 2, 3
 NG = 3
 
@@ -121,7 +121,7 @@ class Multipatch:
     mpw_config allocator hook; work is enqueued on the current torch stream.
     """
 
-    def __init__(self, interp_points=6, ko_eps=0.005, buffer=0, device=0, stream=None, arith=0):
+    def __init__(self, interp_points=6, ko_eps=0.005, buffer=0, device=0, stream=None, arith=0, precision=64):
         torch = _torch()
         self.device = device
         self._torch = torch
@@ -137,7 +137,8 @@ class Multipatch:
 
         self._alloc_cb = ALLOC_FN(_alloc)
         self._free_cb = FREE_FN(_free)
-        cfg = mpw_config(precision=64, ghost=NG, interp_points=interp_points, ko_eps=ko_eps, buffer=buffer,
+        self.precision = precision
+        cfg = mpw_config(precision=precision, ghost=NG, interp_points=interp_points, ko_eps=ko_eps, buffer=buffer,
                          device=device, stream=C.c_void_p(stream.cuda_stream), alloc=self._alloc_cb,
                          free=self._free_cb, alloc_user=None, arith=arith)
         self.h = C.c_void_p()

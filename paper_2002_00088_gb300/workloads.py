@@ -13,6 +13,9 @@ Gaussian-pulse closed forms:
 * ``static_gauss``   -- global 48^3 on [-1,1]^3 plus one static local 32^3 at
   2x resolution centred on the origin, one Gaussian pulse (A = 1, width 0.1,
   centre uniform in [-0.2,0.2]^3), 5-point Lagrange, CFL 0.25, 100 steps.
+* ``plane_gauss``    -- the precision configuration: global 512^3 (periodic)
+  plus one static local 256^3 at 2x, plane wave k = (2,3,5) pi plus one
+  Gaussian pulse; 200 steps.
 * ``orbiting_gauss`` -- global 256^3 on [-1,1]^3 plus four local 128^3 patches
   (half-width 0.25, 2x resolution) on circular orbits of radius 0.4 and
   angular speed 2 pi in the planes z = +-0.3 (pairs opposite in phase, pair
@@ -29,7 +32,7 @@ SEED_BASE = 20020088
 GLOBAL, LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
 STATIC, LINEAR, CIRCULAR = 0, 1, 2
-GAUSS_SUM, PLANE_SUM, HARMONIC_POLY = 0, 1, 2
+GAUSS_SUM, PLANE_SUM, HARMONIC_POLY, PLANE_GAUSS = 0, 1, 2, 3
 
 
 @dataclass
@@ -100,6 +103,30 @@ def orbiting_gauss(scale=1, steps=200, interp_points=6, seed_index=1, radius=0.4
     h_min = 2.0 * half_width / nl
     return Workload(f"orbiting_gauss_{ng}+4x{nl}", patches, GAUSS_SUM, params, 8, interp_points, 0.005,
                     0.25 * h_min, steps)
+
+
+def plane_gauss(scale=1, steps=200, interp_points=6, seed_index=2):
+    """The precision configuration: the static layout of ``static_gauss`` at global
+    512^3/scale on the periodic box [-1,1]^3 and one local 256^3/scale patch of
+    half-width 0.25 (2x resolution) centred on the origin.  Initial data: the
+    plane wave k = (2, 3, 5) pi (period 2 on every axis, so the periodic box
+    holds it exactly; amplitude 1, phase seeded) plus one Gaussian pulse
+    (A = 1, width 0.1, centre uniform in [-0.2,0.2]^3), whose tail at the box
+    faces is below 1e-40 and which travels 0.1 in 200 steps.  CFL 0.25 on the
+    local spacing."""
+    r = rng(seed_index)
+    phase = r.uniform(0.0, 2.0 * np.pi)
+    centre = r.uniform(-0.2, 0.2, 3)
+    ng, nl = 512 // scale, 256 // scale
+    patches = [
+        PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_PERIODIC),
+        PatchSpec(LOCAL, (nl, nl, nl), (-0.25, -0.25, -0.25), (0.25, 0.25, 0.25), BC_INTERPATCH),
+    ]
+    k = np.pi * np.array([2.0, 3.0, 5.0])
+    params = np.array([0.0, 1.0, k[0], k[1], k[2], phase, 1.0, 0.1, centre[0], centre[1], centre[2]])
+    h_min = 0.5 / nl
+    return Workload(f"plane_gauss_{ng}+{nl}", patches, PLANE_GAUSS, params, 1, interp_points, 0.005,
+                    0.25 * h_min, steps, {"centre": centre, "phase": phase})
 
 
 def translating_plane(scale=1, steps=16, interp_points=6, velocity=(0.4, 0.3, 0.0), start=(-0.05, -0.02, 0.0)):

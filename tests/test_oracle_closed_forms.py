@@ -116,3 +116,61 @@ def test_circular_and_linear_motion():
     X0, w = po.motion(po.LINEAR, [-5, -5, 0, 0.1, 0.1, 0], 20.0)  # Sec. 3.2 translating patch
     np.testing.assert_allclose(X0, [-3.0, -3.0, 0.0], atol=1e-14)
     np.testing.assert_array_equal(w, [0.1, 0.1, 0.0])
+
+
+PLANE_GAUSS_PRM = [0.5, 0.7, 2 * np.pi, 3 * np.pi, 5 * np.pi, 0.3,   # plane wave k = (2, 3, 5) pi
+                   1.1, 0.12, 0.05, -0.02, 0.01]                      # one Gaussian pulse
+
+
+def test_plane_gauss_initial_data():
+    """At t = 0: psi = C + A sin(k.x + phase) + A_g exp(-r^2/w^2); Pi = -A |k| cos(k.x + phase)."""
+    p = PLANE_GAUSS_PRM
+    rng = np.random.default_rng(7)
+    k = np.array(p[2:5])
+    for _ in range(8):
+        x = rng.uniform(-1, 1, 3)
+        ps, pv = cf(po.PLANE_GAUSS, p, 1, 0.0, *x)
+        th = k @ x + p[5]
+        r2 = ((x - np.array(p[8:11])) ** 2).sum()
+        assert abs(ps - (p[0] + p[1] * np.sin(th) + p[6] * np.exp(-r2 / p[7] ** 2))) < 1e-13
+        assert abs(pv - (-p[1] * np.linalg.norm(k) * np.cos(th))) < 1e-12
+
+
+@pytest.mark.parametrize("t", [0.02, 0.07])
+def test_plane_gauss_solves_wave_equation(t):
+    """Pi = d psi/dt and dPi/dt = laplacian(psi), by 4th-order differences."""
+    p = PLANE_GAUSS_PRM
+    x0 = np.array([0.11, -0.07, 0.04])
+    d = 1e-3
+
+    def f(tt, x, which):
+        return float(cf(po.PLANE_GAUSS, p, 1, tt, *x)[which])
+
+    def d1(g, a):
+        return (-g(a + 2 * d) + 8 * g(a + d) - 8 * g(a - d) + g(a - 2 * d)) / (12 * d)
+
+    assert abs(d1(lambda tt: f(tt, x0, 0), t) - f(t, x0, 1)) < 1e-6
+    lap = 0.0
+    for a in range(3):
+        e = np.zeros(3)
+        e[a] = d
+        v = [f(t, x0 + k * e, 0) for k in (-2, -1, 0, 1, 2)]
+        lap += (-v[0] + 16 * v[1] - 30 * v[2] + 16 * v[3] - v[4]) / (12 * d * d)
+    dpi = d1(lambda tt: f(tt, x0, 1), t)
+    assert abs(dpi - lap) < 2e-4 * max(1.0, abs(lap))
+
+
+def test_plane_gauss_plane_part_has_period_two():
+    """k = (2, 3, 5) pi: the plane wave repeats with period 2 on every axis, so a
+    periodic box [-1, 1]^3 holds it exactly (the Gaussian is switched off here)."""
+    p = PLANE_GAUSS_PRM[:6] + [0.0, 0.12, 0.0, 0.0, 0.0]
+    rng = np.random.default_rng(9)
+    for _ in range(5):
+        x = rng.uniform(-1, 1, 3)
+        t = rng.uniform(0, 0.2)
+        a = cf(po.PLANE_GAUSS, p, 1, t, *x)
+        for ax in range(3):
+            y = x.copy()
+            y[ax] += 2.0
+            b = cf(po.PLANE_GAUSS, p, 1, t, *y)
+            assert abs(a[0] - b[0]) < 1e-12 and abs(a[1] - b[1]) < 1e-11
