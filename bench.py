@@ -8,7 +8,13 @@ eight Gaussian pulses, 6-point Lagrange, FP64 (paper_2002_00088_gb300.workloads
 .orbiting_gauss).  The state (~1.8 GB) is far larger than L2, so no flush is
 needed between steps.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision 64|32]
+
+--precision 32 runs the binary32 precision workload instead
+(workloads.plane_gauss: periodic global 512^3 plus a static local 256^3 at 2x,
+plane wave k = (2,3,5) pi plus a Gaussian pulse).  Its line adds "accuracy":
+the binary32 error against the closed form after the run, and the FP64 path's
+time and error on the same workload and steps.
 
 With --gpus N > 1 (under torch.distributed.run) every rank advances an
 independent replica on its own GPU ("replicas only": the method needs no
@@ -34,7 +40,7 @@ UNIT = "stage-updates/s"
 FALLBACK_HBM_GBS = 6800.0
 # algorithmic bytes of one live point in one fused RHS+stage launch, averaged
 # over the four substages: S1 48 B, S2 80 B, S3 80 B, S4 48 B (FP64)
-BYTES_PER_POINT_STAGE = 64.0
+BYTES_PER_POINT_STAGE = 64  # (32 B in binary32)
 
 
 def parse():
@@ -51,6 +57,9 @@ def parse():
     ap.add_argument("--ref-sample-scale", type=int, default=2,
                     help="--impl reference: resolution divisor of the oracle sample taken per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
+                    help="64: the FP64 workload (default); 32: the binary32 precision workload, with its error "
+                         "against the closed form and the FP64 path on the same workload")
     return ap.parse_args()
 
 
@@ -118,36 +127,102 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-RHS_SOURCES = ("mpw_rhs.cu", "mpw_fixed.cuh", "mpw_internal.cuh")
+RHS_SOURCES = ("mpw_rhs.cu", "mpw_fixed.cuh", "mpw_internal.cuh", "mpw_tma.cuh")
+RHS32_SOURCES = ("mpw_rhs32.cu", "mpw_internal.cuh", "mpw_tma.cuh")
 
 
-def kernel_source_hash():
+def kernel_source_hash(f32=False):
     """Hash of the sources that define the fused RHS + stage kernel."""
     h = hashlib.sha256()
-    for name in RHS_SOURCES:
+    for name in (RHS32_SOURCES if f32 else RHS_SOURCES):
         with open(os.path.join(ROOT, "paper_2002_00088_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def recorded_traffic():
+def recorded_traffic(f32=False):
     """DRAM bytes per launch of the RHS kernel from the committed ncu summary,
     if it was taken on the current kernel sources."""
-    path = os.path.join(ROOT, "profiles", "rhs_stage_traffic.json")
+    path = os.path.join(ROOT, "profiles", "rhs32_stage_traffic.json" if f32 else "rhs_stage_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
-    if d.get("kernel_source_hash") != kernel_source_hash():
+    if d.get("kernel_source_hash") != kernel_source_hash(f32):
         return None
     return d.get("traffic_bytes_per_launch")
+
+
+def precision_report(args, w, sim, mpw, stream, device):
+    """Binary32 run: its error against the closed form at the current time and
+    the FP64 path on the same workload and number of steps (time and error).
+    The closed form is evaluated by the library's own FP64 kernel in a third
+    context; errors are max |difference| over the live cells of all patches
+    relative to the largest |exact value| of the field."""
+    import torch
+    steps = args.warmup + args.steps
+    t = sim.time
+
+    def make(precision):
+        s = mpw.Multipatch(w.interp_points, w.ko_eps, device=device, stream=stream, precision=precision)
+        for p in w.patches:
+            s.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+        s.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
+        return s
+
+    def fields(s):
+        out = []
+        for q, p in enumerate(w.patches):
+            a = torch.empty((p.n[2], p.n[1], p.n[0]), dtype=torch.float64, device=device)
+            b = torch.empty_like(a)
+            s.get_fields(q, out=(a, b))
+            out.append((a, b))
+        return out
+
+    exact_sim = make(64)
+    exact_sim.fill_analytic(t)
+    exact = fields(exact_sim)
+    del exact_sim
+
+    def errors(run):
+        res = []
+        for f in range(2):
+            scale = max(float(x[f].abs().max()) for x in exact)
+            e = 0.0
+            for a, b in zip(run, exact):
+                d = (a[f] - b[f]).abs()
+                e = max(e, float(torch.nan_to_num(d, nan=0.0).max()))
+            res.append(e / scale)
+        return res
+
+    e32 = errors(fields(sim))
+    s64 = make(64)
+    s64.fill_analytic(0.0)
+    s64.step(w.dt, args.warmup)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    s64.step(w.dt, args.steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms64 = a.elapsed_time(b)
+    e64 = errors(fields(s64))
+    live = s64.live_points()
+    del s64
+    torch.cuda.empty_cache()
+    return {"time": t, "steps": steps,
+            "f32_error_vs_closed_form": {"psi": e32[0], "pi": e32[1]},
+            "f64_error_vs_closed_form": {"psi": e64[0], "pi": e64[1]},
+            "f64_value": live * 4 * args.steps / (ms64 * 1e-3), "f64_ms_per_step": ms64 / args.steps}
 
 
 def cpu_baseline(args, threads):
     """The oracle as it stands, on the host cores, on a bounded sample."""
     from oracle import pyoracle as po
     from paper_2002_00088_gb300 import workloads as wl
-    w = wl.orbiting_gauss(scale=max(args.scale, args.cpu_sample_scale))
+    # the precision workload is 6x larger: its oracle sample runs at half resolution
+    make = wl.plane_gauss if args.precision == 32 else wl.orbiting_gauss
+    w = make(scale=max(args.scale, args.cpu_sample_scale, 2 if args.precision == 32 else 1))
     o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
     for p in w.patches:
         o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
@@ -160,7 +235,7 @@ def cpu_baseline(args, threads):
     el = time.perf_counter() - t0
     return {"value": live * 4 * args.cpu_sample_steps / el, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": f"{args.cpu_sample_steps} step(s) of {w.name} after one untimed step, {live} live points, "
-                      f"{el:.2f} s"}
+                      f"{el:.2f} s, binary64"}
 
 
 def run_reference(args):
@@ -210,9 +285,10 @@ def run_ours(args):
     from paper_2002_00088_gb300 import mpw
     from paper_2002_00088_gb300 import workloads as wl
 
-    w = wl.orbiting_gauss(scale=args.scale)
+    f32 = args.precision == 32
+    w = wl.plane_gauss(scale=args.scale) if f32 else wl.orbiting_gauss(scale=args.scale)
     stream = torch.cuda.current_stream(local)
-    sim = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream)
+    sim = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream, precision=args.precision)
     for p in w.patches:
         sim.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
     sim.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
@@ -246,6 +322,7 @@ def run_ours(args):
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         ms = float(t.item())
     value = live * 4 * args.steps * world / (ms * 1e-3)
+    accuracy = precision_report(args, w, sim, mpw, stream, local) if f32 else None
 
     # ---- end-to-end through the C ABI with host buffers: every step copies the
     # state in from pinned host memory and the result back out
@@ -287,27 +364,34 @@ def run_ours(args):
     flags_ms, flags_n = prof["flags"]
     rhs_avg_ms = rhs_ms / max(rhs_n, 1)
     peak, peak_kind = measured_peaks()
-    achieved = live * BYTES_PER_POINT_STAGE / (rhs_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic()
+    bytes_pt = BYTES_PER_POINT_STAGE // 2 if f32 else BYTES_PER_POINT_STAGE
+    achieved = live * bytes_pt / (rhs_avg_ms * 1e-3) / 1e9
+    traffic = recorded_traffic(f32)
+    esize = 4 if f32 else 8
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded closed-form Gaussian pulses)",
+        "vs_baseline": None, "dtype": "f32" if f32 else "f64",
+        "data": "synthetic (seeded closed-form plane wave + Gaussian pulse)" if f32 else
+                "synthetic (seeded closed-form Gaussian pulses)",
         "config": {"workload": w.name, "live_points": live, "interp_points": w.interp_points,
                    "dt": w.dt, "parallelism": "replicas" if world > 1 else "single",
                    "l2": "state of %.2f GB, larger than L2; no flush" % (
-                       sum(8 * 8 * (p.n[0] + 6) * (p.n[1] + 6) * (p.n[2] + 6) for p in w.patches) / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": "rhs_stage (fused RHS + RK4 stage)", "achieved": achieved,
+                       sum(8 * esize * (p.n[0] + 6) * (p.n[1] + 6) * (p.n[2] + 6) for p in w.patches) / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "rhs_stage (fused RHS + RK4 stage%s)" % (", binary32" if f32 else ""),
+                     "achieved": achieved,
                      "peak": peak, "peak_source": f"{peak_kind} HBM GB/s", "unit": "GB/s",
                      "frac": achieved / peak, "traffic": traffic,
                      "avg_launch_ms": rhs_avg_ms,
-                     "algorithmic_bytes_per_launch": live * BYTES_PER_POINT_STAGE},
+                     "algorithmic_bytes_per_launch": live * bytes_pt},
         "kernel_time_share": {"rhs_stage": rhs_ms / ms, "ghost_fill": fill_ms / ms, "cover_flags": flags_ms / ms},
         "gpu_launches": int(rhs_n + fill_n + flags_n),
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_in, "d2h_bytes_per_step": bytes_in,
                 "steps": args.e2e_steps},
     }
+    if accuracy is not None:
+        line["accuracy"] = accuracy
     if world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(args, os.cpu_count() or 1)
     print(json.dumps(line), flush=True)
