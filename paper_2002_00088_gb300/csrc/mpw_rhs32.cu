@@ -15,6 +15,12 @@
 // to zero).  Neighbouring values of a smooth field agree to within a factor of
 // two, so the differences are exact in binary32 and the rounding error of a
 // stencil scales with the local variation of u, not with |u| / h^2.
+//
+// Packing.  psi and Pi go through the same stencil sums, so the two fields of a
+// point travel as one pair: the ring of planes holds (psi, Pi) pairs, a
+// neighbour is one 64-bit shared-memory load, and the differences, sums and
+// stage updates are the packed binary32 pair instructions of sm_100 and later
+// (add/sub/fma .rn.f32x2), each lane rounded exactly as the scalar operation.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -36,7 +42,7 @@ constexpr int SLOT_F = TILE_F + 2 * PT_F;          // tile | u | ACC
 constexpr int RING_PLANE = (RHS_TY + 6) * (RHS_TX + 6);
 constexpr int RING_SLOTS = 4;
 constexpr size_t RHS32_SMEM =
-    1024 + sizeof(float) * R32_DEPTH * SLOT_F + sizeof(float) * RING_SLOTS * 2 * RING_PLANE + 8 * R32_DEPTH;
+    1024 + sizeof(float) * R32_DEPTH * SLOT_F + 8 * RING_SLOTS * RING_PLANE + 8 * R32_DEPTH;
 
 // Loads of iteration zz (tile of input plane zz+3, u and ACC of plane zz).
 __device__ __forceinline__ void issue_slot32(const RhsPatch& Pt, int stage, float* slot, unsigned bar, int i0, int j0,
@@ -49,20 +55,56 @@ __device__ __forceinline__ void issue_slot32(const RhsPatch& Pt, int stage, floa
   if (stage > 0) tma_load_4d(smem_u32(slot + TILE_F + PT_F), &Pt.amap, i0 + XOFF, j0 + NG, zz + NG, 0, bar);
 }
 
-// Sums of the differences to the centre along one axis: s1 = d1 + d-1,
-// s2 = d2 + d-2, s3 = d3 + d-3 and the first-derivative combination.
+// A (psi, Pi) pair of binary32 values in one 64-bit register: psi in the low
+// half.
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 pk(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float lo(f2 v) { return __uint_as_float((unsigned)(v & 0xFFFFFFFFull)); }
+__device__ __forceinline__ float hi(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 sub2(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2 fma2(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// Sums of the differences to the centre along one axis, both fields:
+// s1 = d1 + d-1, s2 = d2 + d-2, s3 = d3 + d-3.
 struct AxisSums {
-  float s1, s2, s3, d1;
+  f2 s1, s2, s3;
 };
 
-__device__ __forceinline__ AxisSums axis_sums(float m3, float m2, float m1, float u0, float p1, float p2, float p3) {
-  const float a1 = m1 - u0, b1 = p1 - u0, a2 = m2 - u0, b2 = p2 - u0;
+__device__ __forceinline__ AxisSums axis_sums(f2 m3, f2 m2, f2 m1, f2 u0, f2 p1, f2 p2, f2 p3) {
   AxisSums r;
-  r.s1 = a1 + b1;
-  r.s2 = a2 + b2;
-  r.s3 = (m3 - u0) + (p3 - u0);
-  r.d1 = 8.0f * (b1 - a1) - (b2 - a2);
+  r.s1 = add2(sub2(m1, u0), sub2(p1, u0));
+  r.s2 = add2(sub2(m2, u0), sub2(p2, u0));
+  r.s3 = add2(sub2(m3, u0), sub2(p3, u0));
   return r;
+}
+
+// First-derivative combination 8 (u1 - u-1) - (u2 - u-2), both fields (u0
+// cancels, so no difference form is needed).
+__device__ __forceinline__ f2 d1_pair(f2 m2, f2 m1, f2 p1, f2 p2) {
+  return fma2(pk(8.0f, 8.0f), sub2(p1, m1), sub2(m2, p2));
+}
+
+// KO sixth-difference sum s3 - 6 s2 + 15 s1, both fields.
+__device__ __forceinline__ f2 ko_pair(const AxisSums& a) {
+  return fma2(pk(15.0f, 15.0f), a.s1, fma2(pk(-6.0f, -6.0f), a.s2, a.s3));
 }
 
 }  // namespace
@@ -73,8 +115,8 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid
   __shared__ int s_abort;
   const unsigned long long base = (reinterpret_cast<unsigned long long>(smem32) + 1023ull) & ~1023ull;
   float* slots = reinterpret_cast<float*>(base);
-  float* ring = slots + R32_DEPTH * SLOT_F;
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ring + RING_SLOTS * 2 * RING_PLANE);
+  f2* ring = reinterpret_cast<f2*>(slots + R32_DEPTH * SLOT_F);  // [RING_SLOTS][RING_PLANE] (psi, Pi) pairs
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(ring + RING_SLOTS * RING_PLANE);
   const int b = blockIdx.x;
   int p = 0;
   while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
@@ -141,30 +183,27 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid
     ck[a] = (float)Pt.cko[a];
   }
   const float alpha = (float)A.alpha, beta = (float)A.beta;
-  auto ring_of = [&](int zz) -> float* { return ring + ((zz - z0) & (RING_SLOTS - 1)) * 2 * RING_PLANE; };
+  auto ring_of = [&](int zz) -> f2* { return ring + ((zz - z0) & (RING_SLOTS - 1)) * RING_PLANE; };
   // prologue: planes z0-3 .. z0+2 by plain loads (queue), z0 .. z0+2 also into the ring
-  float qs[7], qp[7];
+  f2 q[7];
 #pragma unroll
   for (int o = 0; o < 6; ++o) {
     const int zz = z0 - NG + o;
-    qs[o] = 0.0f;
-    qp[o] = 0.0f;
+    q[o] = 0ull;
     if (in_box) {
       const long long c = g.at(i, j, zz);
-      qs[o] = Ys[c];
-      qp[o] = Yp[c];
+      q[o] = pk(Ys[c], Yp[c]);
     }
     if (o >= NG && zz < z1) {
-      float* rv = ring_of(zz);
-      rv[own] = qs[o];
-      rv[RING_PLANE + own] = qp[o];
+      f2* rv = ring_of(zz);
+      rv[own] = q[o];
       if (h_ok) {
         const long long c = g.at(hi_, hj, zz);
-        rv[hoff] = Ys[c];
-        rv[RING_PLANE + hoff] = Yp[c];
+        rv[hoff] = pk(Ys[c], Yp[c]);
       }
     }
   }
+  const f2 alpha2 = pk(alpha, alpha), beta2 = pk(beta, beta);
   for (int z = z0; z < z1; ++z) {
     const int it = z - z0;
     const int s = it % R32_DEPTH;
@@ -180,15 +219,9 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid
       rp_h = sl[BX * BY + halo_raw];
     }
     const int pt = lj * TX + li;
-    float ua_s = 0.0f, ua_p = 0.0f, ub_s = 0.0f, ub_p = 0.0f;
-    if (A.stage < 3) {
-      ua_s = sl[TILE_F + pt];
-      ua_p = sl[TILE_F + TX * TY + pt];
-    }
-    if (A.stage > 0) {
-      ub_s = sl[TILE_F + PT_F + pt];
-      ub_p = sl[TILE_F + PT_F + TX * TY + pt];
-    }
+    f2 ua = 0ull, ub = 0ull;
+    if (A.stage < 3) ua = pk(sl[TILE_F + pt], sl[TILE_F + TX * TY + pt]);
+    if (A.stage > 0) ub = pk(sl[TILE_F + PT_F + pt], sl[TILE_F + PT_F + TX * TY + pt]);
     __syncthreads();
     if (s_abort) {
       if (threadIdx.x == 0) {
@@ -200,68 +233,62 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid
     }
     if (threadIdx.x == 0 && z + R32_DEPTH < z1)
       issue_slot32(Pt, A.stage, slots + s * SLOT_F, bar, i0, j0, z + R32_DEPTH);
-    qs[6] = rs_own;
-    qp[6] = rp_own;
+    q[6] = pk(rs_own, rp_own);
     const bool live = in_xy && (fl == FLAG_LIVE || fl == FLAG_REVIVED);
     {
-      const float* rs = ring_of(z) + own;
-      const float* rp = rs + RING_PLANE;
-      const float u0 = qs[3], v0 = qp[3];
-      const AxisSums sx = axis_sums(rs[-3], rs[-2], rs[-1], u0, rs[1], rs[2], rs[3]);
-      const AxisSums sy = axis_sums(rs[-3 * SY], rs[-2 * SY], rs[-SY], u0, rs[SY], rs[2 * SY], rs[3 * SY]);
-      const AxisSums sz = axis_sums(qs[0], qs[1], qs[2], u0, qs[4], qs[5], qs[6]);
-      const AxisSums px = axis_sums(rp[-3], rp[-2], rp[-1], v0, rp[1], rp[2], rp[3]);
-      const AxisSums py = axis_sums(rp[-3 * SY], rp[-2 * SY], rp[-SY], v0, rp[SY], rp[2 * SY], rp[3 * SY]);
-      const AxisSums pz = axis_sums(qp[0], qp[1], qp[2], v0, qp[4], qp[5], qp[6]);
-      float Ks, Kp;
+      const f2* r = ring_of(z) + own;
+      const f2 u0 = q[3];
+      const AxisSums sx = axis_sums(r[-3], r[-2], r[-1], u0, r[1], r[2], r[3]);
+      const AxisSums sy = axis_sums(r[-3 * SY], r[-2 * SY], r[-SY], u0, r[SY], r[2 * SY], r[3 * SY]);
+      const AxisSums sz = axis_sums(q[0], q[1], q[2], u0, q[4], q[5], q[6]);
+      // KO of both fields (KO_psi, KO_Pi) and D2 of psi
+      f2 ko;
+      float d2;
       if (Pt.iso) {
-        const float S1 = sx.s1 + sy.s1 + sz.s1, S2 = sx.s2 + sy.s2 + sz.s2, S3 = sx.s3 + sy.s3 + sz.s3;
-        const float P1 = px.s1 + py.s1 + pz.s1, P2 = px.s2 + py.s2 + pz.s2, P3 = px.s3 + py.s3 + pz.s3;
-        Ks = v0 + ck[0] * (S3 - 6.0f * S2 + 15.0f * S1);
-        Kp = c2[0] * (16.0f * S1 - S2) + ck[0] * (P3 - 6.0f * P2 + 15.0f * P1);
+        AxisSums S;
+        S.s1 = add2(add2(sx.s1, sy.s1), sz.s1);
+        S.s2 = add2(add2(sx.s2, sy.s2), sz.s2);
+        S.s3 = add2(add2(sx.s3, sy.s3), sz.s3);
+        ko = fma2(pk(ck[0], ck[0]), ko_pair(S), 0ull);
+        d2 = c2[0] * fmaf(16.0f, lo(S.s1), -lo(S.s2));
       } else {
-        Ks = v0 + ck[0] * (sx.s3 - 6.0f * sx.s2 + 15.0f * sx.s1) + ck[1] * (sy.s3 - 6.0f * sy.s2 + 15.0f * sy.s1) +
-             ck[2] * (sz.s3 - 6.0f * sz.s2 + 15.0f * sz.s1);
-        Kp = c2[0] * (16.0f * sx.s1 - sx.s2) + c2[1] * (16.0f * sy.s1 - sy.s2) + c2[2] * (16.0f * sz.s1 - sz.s2) +
-             ck[0] * (px.s3 - 6.0f * px.s2 + 15.0f * px.s1) + ck[1] * (py.s3 - 6.0f * py.s2 + 15.0f * py.s1) +
-             ck[2] * (pz.s3 - 6.0f * pz.s2 + 15.0f * pz.s1);
+        ko = fma2(pk(ck[2], ck[2]), ko_pair(sz),
+                  fma2(pk(ck[1], ck[1]), ko_pair(sy), fma2(pk(ck[0], ck[0]), ko_pair(sx), 0ull)));
+        d2 = c2[0] * fmaf(16.0f, lo(sx.s1), -lo(sx.s2)) + c2[1] * fmaf(16.0f, lo(sy.s1), -lo(sy.s2)) +
+             c2[2] * fmaf(16.0f, lo(sz.s1), -lo(sz.s2));
       }
+      // K = (Pi + KO_psi, D2 psi + KO_Pi) (+ w . D1 of both fields on a moving patch)
+      f2 K = add2(ko, pk(hi(u0), d2));
       if (Pt.moving) {
-        Ks += c1[0] * sx.d1 + c1[1] * sy.d1 + c1[2] * sz.d1;
-        Kp += c1[0] * px.d1 + c1[1] * py.d1 + c1[2] * pz.d1;
+        const f2 dx = d1_pair(r[-2], r[-1], r[1], r[2]);
+        const f2 dy = d1_pair(r[-2 * SY], r[-SY], r[SY], r[2 * SY]);
+        const f2 dz = d1_pair(q[1], q[2], q[4], q[5]);
+        K = fma2(pk(c1[2], c1[2]), dz, fma2(pk(c1[1], c1[1]), dy, fma2(pk(c1[0], c1[0]), dx, K)));
       }
       const long long cz = g.at(i, j, z);
-      if (A.stage == 3) {
-        if (live) {
-          OUT[cz] = fmaf(alpha, Ks, ub_s);
-          OUT[cz + g.vol] = fmaf(alpha, Kp, ub_p);
-        }
-      } else {
-        const float as = A.stage == 0 ? ua_s : ub_s;
-        const float ap = A.stage == 0 ? ua_p : ub_p;
-        if (live) {
-          ACC[cz] = fmaf(beta, Ks, as);
-          ACC[cz + g.vol] = fmaf(beta, Kp, ap);
-          OUT[cz] = fmaf(alpha, Ks, ua_s);
-          OUT[cz + g.vol] = fmaf(alpha, Kp, ua_p);
+      if (live) {
+        if (A.stage == 3) {
+          const f2 o = fma2(alpha2, K, ub);
+          OUT[cz] = lo(o);
+          OUT[cz + g.vol] = hi(o);
+        } else {
+          const f2 o = fma2(alpha2, K, ua);
+          const f2 acc = fma2(beta2, K, A.stage == 0 ? ua : ub);
+          ACC[cz] = lo(acc);
+          ACC[cz + g.vol] = hi(acc);
+          OUT[cz] = lo(o);
+          OUT[cz + g.vol] = hi(o);
         }
       }
     }
     // plane z+3 into the ring (read from iteration z+3 on)
     {
-      float* rv = ring_of(z + NG);
-      rv[own] = qs[6];
-      rv[RING_PLANE + own] = qp[6];
-      if (h_ok) {
-        rv[hoff] = rs_h;
-        rv[RING_PLANE + hoff] = rp_h;
-      }
+      f2* rv = ring_of(z + NG);
+      rv[own] = q[6];
+      if (h_ok) rv[hoff] = pk(rs_h, rp_h);
     }
 #pragma unroll
-    for (int o = 0; o < 6; ++o) {
-      qs[o] = qs[o + 1];
-      qp[o] = qp[o + 1];
-    }
+    for (int o = 0; o < 6; ++o) q[o] = q[o + 1];
   }
 }
 
