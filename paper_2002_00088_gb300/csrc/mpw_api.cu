@@ -171,18 +171,10 @@ bool is_moving(const mpw_patch_desc& d) {
   return v[0] != 0.0 || v[1] != 0.0 || v[2] != 0.0;
 }
 
-Geom make_geom(const mpw_patch_desc& d) {
-  Geom g{};
-  for (int a = 0; a < 3; ++a) {
-    g.n[a] = d.n[a];
-    g.lo[a] = d.lo[a];
-    g.h[a] = (d.hi[a] - d.lo[a]) / d.n[a];
-  }
-  g.px = ((d.n[0] + XOFF + NG + 1) + 15) / 16 * 16;
-  g.py = d.n[1] + 2 * NG;
-  g.plane = (long long)g.px * g.py;
-  g.vol = g.plane * (d.n[2] + 2 * NG);
-  return g;
+Geom make_geom(const mpw_patch_desc& d, int esize = 8) {
+  double h[3];
+  for (int a = 0; a < 3; ++a) h[a] = (d.hi[a] - d.lo[a]) / d.n[a];
+  return padded_geom(d.n, d.lo, h, esize);
 }
 
 // Covered box of local patch l on the global grid at time t (Sec. 2.4.2,
@@ -761,9 +753,9 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
   if (use_device(c)) return MPW_ERR_CUDA;
   PatchState P;
   P.d = *d;
-  P.g = make_geom(*d);
   const bool f32 = c->cfg.precision == 32;
   P.esize = f32 ? 4 : 8;
+  P.g = make_geom(*d, (int)P.esize);
   const size_t bytes = P.esize * 8 * (size_t)P.g.vol;
   P.base = (double*)c->dalloc(bytes);
   if (!P.base) return set_err(MPW_ERR_CUDA, "allocation of %zu bytes failed", bytes);

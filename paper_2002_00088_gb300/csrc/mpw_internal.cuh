@@ -3,8 +3,10 @@
 // Layout in HBM.  Every patch owns one allocation of 8 field arrays
 // (state u, accumulator, two stage buffers; x 2 fields psi, Pi).  A field
 // array is a padded box of (n+6) planes x (n+6) rows with a row pitch px that
-// is a multiple of 16 doubles (128 B); the interior cell i = 0 sits at column
-// XOFF = 4 (32 B aligned), the ghost cells i = -3..-1 at columns 1..3.
+// is a multiple of 128 B; the interior cell i = 0 sits at column xoff, 32 B
+// into the row (xoff = 4 binary64 or 8 binary32 elements), so that the 32
+// points of a warp write whole 32-byte sectors; the ghost cells
+// i = -3..-1 sit just left of it.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
@@ -14,7 +16,7 @@
 namespace mpw {
 
 constexpr int NG = 3;
-constexpr int XOFF = 4;
+constexpr int XOFF_BYTES = 32;  // byte offset of interior column 0 in a row
 constexpr int MAX_PATCHES = 16;
 constexpr int MAX_APARAMS = 1024;
 
@@ -25,12 +27,31 @@ enum { ERR_UNFILLED = 1, ERR_BOUNDS = 2, ERR_NONFINITE = 4, ERR_TIMEOUT = 8 };
 struct Geom {
   int n[3];
   int px, py;
+  int xoff;           // column of interior cell i = 0 (XOFF_BYTES / element size)
   long long plane, vol;
   double lo[3], h[3];
   __host__ __device__ __forceinline__ long long at(int i, int j, int k) const {
-    return (long long)(k + NG) * plane + (long long)(j + NG) * px + (i + XOFF);
+    return (long long)(k + NG) * plane + (long long)(j + NG) * px + (i + xoff);
   }
 };
+
+// Padded geometry of an n[0] x n[1] x n[2] patch on [lo, lo + n h] with
+// elements of esize bytes.
+inline Geom padded_geom(const int n[3], const double lo[3], const double h[3], int esize) {
+  Geom g{};
+  for (int a = 0; a < 3; ++a) {
+    g.n[a] = n[a];
+    g.lo[a] = lo[a];
+    g.h[a] = h[a];
+  }
+  g.xoff = XOFF_BYTES / esize;
+  const int row = 128 / esize;  // elements per 128 B
+  g.px = ((n[0] + g.xoff + NG + 1) + row - 1) / row * row;
+  g.py = n[1] + 2 * NG;
+  g.plane = (long long)g.px * g.py;
+  g.vol = g.plane * (n[2] + 2 * NG);
+  return g;
+}
 
 // Covered box of one local patch in global index space (inclusive bounds);
 // empty when lo > hi on any axis.

@@ -76,16 +76,9 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
     base = g_scratch_ptr[dev];
   }
   // padded geometry (same layout as the context path)
-  Geom g{};
-  for (int a = 0; a < 3; ++a) {
-    g.n[a] = n[a];
-    g.lo[a] = lo[a];
-    g.h[a] = (hi[a] - lo[a]) / n[a];
-  }
-  g.px = ((n[0] + XOFF + NG + 1) + 15) / 16 * 16;
-  g.py = n[1] + 2 * NG;
-  g.plane = (long long)g.px * g.py;
-  g.vol = g.plane * (n[2] + 2 * NG);
+  double h[3];
+  for (int a = 0; a < 3; ++a) h[a] = (hi[a] - lo[a]) / n[a];
+  const Geom g = padded_geom(n, lo, h, 8);
   double lap = 0.0;
   for (int a = 0; a < 3; ++a) lap += 16.0 / (3.0 * g.h[a] * g.h[a]);
   if (dt * std::sqrt(lap) > 2.8) return fail(MPW_ERR_CFL, "dt exceeds the RK4 stability estimate");

@@ -129,10 +129,10 @@ __device__ __forceinline__ void issue_slot(const RhsPatch& Pt, int stage, double
   const unsigned bytes = sizeof(double) * (TILE_DOUBLES + (stage < 3 ? PT_DOUBLES : 0) + (stage > 0 ? PT_DOUBLES : 0));
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   bar_expect_tx(bar, bytes);
-  // tile: columns from interior i0 - 4 (padded column i0), rows from interior j0 - 3 (padded row j0)
-  tma_load_4d(smem_u32(slot), &Pt.ymap, i0, j0, zz + 3 + NG, 0, bar);
-  if (stage < 3) tma_load_4d(smem_u32(slot + TILE_DOUBLES), &Pt.umap, i0 + XOFF, j0 + NG, zz + NG, 0, bar);
-  if (stage > 0) tma_load_4d(smem_u32(slot + TILE_DOUBLES + PT_DOUBLES), &Pt.amap, i0 + XOFF, j0 + NG, zz + NG, 0, bar);
+  // tile: columns from interior i0 - 4 (padded column i0 + xoff - 4), rows from interior j0 - 3 (padded row j0)
+  tma_load_4d(smem_u32(slot), &Pt.ymap, i0 + Pt.g.xoff - 4, j0, zz + 3 + NG, 0, bar);
+  if (stage < 3) tma_load_4d(smem_u32(slot + TILE_DOUBLES), &Pt.umap, i0 + Pt.g.xoff, j0 + NG, zz + NG, 0, bar);
+  if (stage > 0) tma_load_4d(smem_u32(slot + TILE_DOUBLES + PT_DOUBLES), &Pt.amap, i0 + Pt.g.xoff, j0 + NG, zz + NG, 0, bar);
 }
 
 template <int TX, int TY, bool FIXED>

@@ -33,8 +33,14 @@ namespace mpw {
 
 namespace {
 
-constexpr int R32_DEPTH = 4;                       // planes in flight per CTA
-constexpr int R32_MINB = 4;                        // CTAs per SM the register budget is sized for
+#ifndef MPW_R32_DEPTH
+#define MPW_R32_DEPTH 4
+#endif
+#ifndef MPW_R32_MINB
+#define MPW_R32_MINB 4
+#endif
+constexpr int R32_DEPTH = MPW_R32_DEPTH;           // planes in flight per CTA
+constexpr int R32_MINB = MPW_R32_MINB;             // CTAs per SM the register budget is sized for
 constexpr int BX = RHS_TX + 8, BY = RHS_TY + 6;    // TMA tile box (x start rounded down 16 bytes)
 constexpr int TILE_F = BX * BY * 2;
 constexpr int PT_F = RHS_TX * RHS_TY * 2;
@@ -50,9 +56,9 @@ __device__ __forceinline__ void issue_slot32(const RhsPatch& Pt, int stage, floa
   const unsigned bytes = sizeof(float) * (TILE_F + (stage < 3 ? PT_F : 0) + (stage > 0 ? PT_F : 0));
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   bar_expect_tx(bar, bytes);
-  tma_load_4d(smem_u32(slot), &Pt.ymap, i0, j0, zz + 3 + NG, 0, bar);
-  if (stage < 3) tma_load_4d(smem_u32(slot + TILE_F), &Pt.umap, i0 + XOFF, j0 + NG, zz + NG, 0, bar);
-  if (stage > 0) tma_load_4d(smem_u32(slot + TILE_F + PT_F), &Pt.amap, i0 + XOFF, j0 + NG, zz + NG, 0, bar);
+  tma_load_4d(smem_u32(slot), &Pt.ymap, i0 + Pt.g.xoff - 4, j0, zz + 3 + NG, 0, bar);
+  if (stage < 3) tma_load_4d(smem_u32(slot + TILE_F), &Pt.umap, i0 + Pt.g.xoff, j0 + NG, zz + NG, 0, bar);
+  if (stage > 0) tma_load_4d(smem_u32(slot + TILE_F + PT_F), &Pt.amap, i0 + Pt.g.xoff, j0 + NG, zz + NG, 0, bar);
 }
 
 // A (psi, Pi) pair of binary32 values in one 64-bit register: psi in the low
