@@ -174,6 +174,34 @@ mpw_status mpw_fill_ghosts(mpw_ctx* ctx, double t);
  * MPW_ERR_GHOST_UNFILLED or MPW_ERR_BOUNDS. */
 mpw_status mpw_step(mpw_ctx* ctx, double dt, int nsteps);
 
+/* ---- Batches: many independent multipatch instances advanced together.
+ * The paper has no counterpart (it runs one instance per set of MPI ranks);
+ * this is the batching pattern of serving many small simulations on one GPU.
+ * Each instance is an ordinary context.  A batched step does per instance
+ * what mpw_step does (validation, cover flags, exponent slots), but every
+ * ghost fill and every RHS + stage substage is ONE kernel launch over all
+ * instances, so small instances share the GPU instead of running one after
+ * the other.  Results are bit for bit those of mpw_step on each context.
+ *
+ * mpw_batch_create: ctxs[0..n) must be distinct, live, hold a global patch,
+ *   and share device, stream, precision, interp_points and arith; the array
+ *   is copied, the contexts stay owned by the caller and must outlive the
+ *   batch.  Allocates the argument tables (device and page-locked host).
+ *   Errors: MPW_ERR_ARG, MPW_ERR_STATE, MPW_ERR_CUDA.
+ * mpw_batch_step: advance every instance i by nsteps steps of dt[i] (host
+ *   array of n doubles).  The first steps of a batch also tune the RHS
+ *   chunk depth (planes marched per CTA): each candidate (8, 16, 32, 64)
+ *   runs one step, timed with CUDA events, and the fastest is kept.
+ *   Errors as mpw_step, for the first instance that fails.
+ * mpw_batch_tuning: the chosen chunk depth (0 while tuning), its measured
+ *   RHS time per step in ms, and the number of batched launches so far.
+ * mpw_batch_destroy: frees the tables (not the contexts). */
+typedef struct mpw_batch mpw_batch;
+mpw_status mpw_batch_create(mpw_ctx* const* ctxs, int n, mpw_batch** out);
+mpw_status mpw_batch_step(mpw_batch* batch, const double* dt, int nsteps);
+mpw_status mpw_batch_tuning(const mpw_batch* batch, int* chunk, double* rhs_ms, long long* launches);
+void mpw_batch_destroy(mpw_batch* batch);
+
 /* Number of live points summed over patches (the unit of the throughput
  * metric: one live point advanced through one RK4 substage). */
 mpw_status mpw_live_points(mpw_ctx* ctx, long long* count);

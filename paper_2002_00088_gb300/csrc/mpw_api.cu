@@ -448,9 +448,9 @@ int build_segment(InterpSeg& S, const int O0[3], const int O[3], int P) {
 
 // Ghost fill of the stage buffer `b` at time t; clears the exponent slots of
 // buffer reset_buf (the output of the following RHS launch), if >= 0.
-mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
+mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
   const PatchState& g = c->p[0];
-  FillArgs a{};
+  a = FillArgs{};
   a.Yg = g.buf(b);
   a.gg = g.g;
   a.outer_bc = g.d.outer_bc == MPW_BC_PERIODIC ? 1 : 0;
@@ -526,6 +526,12 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   a.np = (int)c->p.size();
   a.fixed = c->cfg.arith != 1;
   a.f32 = c->cfg.precision == 32;
+  return MPW_OK;
+}
+
+mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
+  FillArgs a;
+  if (mpw_status st = prep_fill(c, b, t, reset_buf, a)) return st;
   c->launch_begin(MPW_KERNEL_FILL);
   launch_fill(a, c->stream);
   c->launch_end(MPW_KERNEL_FILL);
@@ -534,10 +540,12 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
 }
 
 // One fused RHS + RK4 stage launch over every patch (substage l at t).
-mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
+// RHS + stage arguments of substage l for every patch of c; returns the
+// number of CTAs.  zc: planes per CTA chunk (0: the default).
+int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
   static const int in_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
   static const int out_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
-  RhsArgs a{};
+  a = RhsArgs{};
   a.np = (int)c->p.size();
   a.stage = l;
   // OUT = U + alpha K (l < 3) or ACC + alpha K (l = 3); ACC = base + beta K
@@ -578,11 +586,17 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
     R.out_buf = out_buf[l];
     R.tiles_x = (P.d.n[0] + RHS_TX - 1) / RHS_TX;
     R.tiles_y = (P.d.n[1] + RHS_TY - 1) / RHS_TY;
-    R.zc = P.d.n[2] >= 128 ? 32 : 8;
+    R.zc = zc > 0 ? zc : (P.d.n[2] >= 128 ? 32 : 8);
     R.zchunks = (P.d.n[2] + R.zc - 1) / R.zc;
     R.block0 = blocks;
     blocks += R.tiles_x * R.tiles_y * R.zchunks;
   }
+  return blocks;
+}
+
+mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
+  RhsArgs a;
+  const int blocks = prep_rhs(c, l, t, dt, a);
   c->launch_begin(MPW_KERNEL_RHS);
   if (c->cfg.precision == 32)
     launch_rhs32(a, blocks, c->stream);
@@ -964,22 +978,43 @@ mpw_status mpw_fill_ghosts(mpw_ctx* c, double t) {
   return read_error_word(c);
 }
 
+}  // extern "C"
+
+namespace {
+const int FILL_BUF[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
+const int NEXT_BUF[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
+
+bool any_moving(const mpw_ctx* c) {
+  for (size_t q = 1; q < c->p.size(); ++q)
+    if (is_moving(c->p[q].d)) return true;
+  return false;
+}
+
+// What a step does before its substages: validation at t_n, the cover flags
+// (every step when a patch moves, once otherwise) and the exponent slots of u.
+mpw_status step_prologue(mpw_ctx* c, double dt) {
+  mpw_status st;
+  const double tn = c->t;
+  if ((st = validate_step(c, dt, tn))) return st;
+  if (any_moving(c) || !c->flags_valid)
+    if ((st = run_flags(c, tn))) return st;
+  return ensure_u_exponents(c);
+}
+}  // namespace
+
+extern "C" {
+
 mpw_status mpw_step(mpw_ctx* c, double dt, int nsteps) {
   mpw_status st = check_ctx(c);
   if (st) return st;
   if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
   if (nsteps < 0) return set_err(MPW_ERR_ARG, "nsteps must be >= 0");
   if (use_device(c)) return MPW_ERR_CUDA;
-  bool moving = false;
-  for (size_t q = 1; q < c->p.size(); ++q) moving = moving || is_moving(c->p[q].d);
   for (int s = 0; s < nsteps; ++s) {
     const double tn = c->t;
-    if ((st = validate_step(c, dt, tn))) return st;
-    if (moving || !c->flags_valid)
-      if ((st = run_flags(c, tn))) return st;
-    if ((st = ensure_u_exponents(c))) return st;
-    static const int fill_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
-    static const int next_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
+    if ((st = step_prologue(c, dt))) return st;
+    const int* fill_buf = FILL_BUF;
+    const int* next_buf = NEXT_BUF;
     for (int l = 0; l < 4; ++l) {
       const double tl = tn + RK_C[l] * dt;
       if ((st = run_fill(c, fill_buf[l], tl, next_buf[l]))) return st;
@@ -1034,6 +1069,189 @@ mpw_status mpw_profile_read(mpw_ctx* c, double* ms, long long* launches, int n) 
     c->ev_used[f] = 0;
     c->launches[f] = 0;
   }
+  return MPW_OK;
+}
+
+
+// ============================================================================ batches
+}  // extern "C"
+
+struct mpw_batch {
+  std::vector<mpw_ctx*> ctx;
+  cudaStream_t stream = nullptr;
+  int P = 6;
+  bool f32 = false, fixed = true;
+  // argument tables of the 8 launches of one step (4 fills, 4 RHS): device
+  // copies, reused every step in stream order, and two pinned host halves,
+  // alternated by step, each released by the event after its last copy
+  size_t region = 0;            // bytes per launch region
+  char* d_args = nullptr;
+  char* h_args[2] = {nullptr, nullptr};
+  cudaEvent_t copied[2] = {nullptr, nullptr};
+  long long steps_done = 0;
+  // chunk-depth tuning of the RHS launches
+  std::vector<int> cand;
+  std::vector<cudaEvent_t> tev;  // start/stop per candidate
+  int zc = 0;                    // chosen chunk depth (0 until tuned)
+  double zc_ms = 0.0;            // its measured RHS time per step
+  long long launches = 0;
+};
+
+namespace {
+const int ZC_CANDIDATES[] = {8, 16, 32, 64};
+}
+
+extern "C" {
+
+mpw_status mpw_batch_create(mpw_ctx* const* ctxs, int n, mpw_batch** out) {
+  if (!ctxs || !out || n < 1) return set_err(MPW_ERR_ARG, "need at least one context");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (mpw_status st = check_ctx(ctxs[i])) return st;
+    const mpw_ctx* c = ctxs[i];
+    if (c->p.empty()) return set_err(MPW_ERR_STATE, "context %d has no global patch", i);
+    if (c->cfg.device != ctxs[0]->cfg.device || c->stream != ctxs[0]->stream)
+      return set_err(MPW_ERR_ARG, "batched contexts must share the device and the stream");
+    if (c->cfg.precision != ctxs[0]->cfg.precision || c->P != ctxs[0]->P ||
+        (c->cfg.arith != 1) != (ctxs[0]->cfg.arith != 1))
+      return set_err(MPW_ERR_ARG, "batched contexts must share precision, interp_points and arith");
+    for (int j = 0; j < i; ++j)
+      if (ctxs[j] == c) return set_err(MPW_ERR_ARG, "a context appears twice in the batch");
+  }
+  mpw_batch* b = new mpw_batch();
+  b->ctx.assign(ctxs, ctxs + n);
+  b->stream = ctxs[0]->stream;
+  b->P = ctxs[0]->P;
+  b->f32 = ctxs[0]->cfg.precision == 32;
+  b->fixed = ctxs[0]->cfg.arith != 1;
+  const size_t table = std::max(sizeof(FillArgs), sizeof(RhsArgs)) * (size_t)n;
+  b->region = (table + sizeof(int) * (size_t)(n + 1) + 255) / 256 * 256;
+  if (use_device(ctxs[0])) {
+    delete b;
+    return MPW_ERR_CUDA;
+  }
+  bool ok = cudaMalloc(&b->d_args, 8 * b->region) == cudaSuccess;
+  for (int h = 0; h < 2 && ok; ++h)
+    ok = cudaMallocHost(&b->h_args[h], 8 * b->region) == cudaSuccess &&
+         cudaEventCreateWithFlags(&b->copied[h], cudaEventDisableTiming) == cudaSuccess;
+  for (int z : ZC_CANDIDATES) b->cand.push_back(z);
+  b->tev.resize(2 * b->cand.size());
+  for (auto& e : b->tev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+  if (!ok) {
+    mpw_batch_destroy(b);
+    return set_err(MPW_ERR_CUDA, "batch allocation failed");
+  }
+  *out = b;
+  return MPW_OK;
+}
+
+void mpw_batch_destroy(mpw_batch* b) {
+  if (!b) return;
+  if (b->stream || !b->ctx.empty()) cudaStreamSynchronize(b->stream);
+  cudaFree(b->d_args);
+  for (int h = 0; h < 2; ++h) {
+    if (b->h_args[h]) cudaFreeHost(b->h_args[h]);
+    if (b->copied[h]) cudaEventDestroy(b->copied[h]);
+  }
+  for (auto& e : b->tev)
+    if (e) cudaEventDestroy(e);
+  delete b;
+}
+
+mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
+  if (!b || !dt) return set_err(MPW_ERR_ARG, "null argument");
+  if (nsteps < 0) return set_err(MPW_ERR_ARG, "nsteps must be >= 0");
+  const int n = (int)b->ctx.size();
+  for (mpw_ctx* c : b->ctx)
+    if (mpw_status st = check_ctx(c)) return st;
+  if (use_device(b->ctx[0])) return MPW_ERR_CUDA;
+  mpw_status st;
+  const size_t nc = b->cand.size();
+  for (int s = 0; s < nsteps; ++s) {
+    // chunk depth: the first steps try every candidate, timing the RHS
+    // launches; results do not depend on it (each point's arithmetic is the
+    // same whatever chunk its CTA marches)
+    const long long k = b->steps_done;
+    const bool trial = b->zc == 0 && k < (long long)nc;
+    const int zc = b->zc ? b->zc : (trial ? b->cand[k] : 0);
+    double tn[64];
+    std::vector<double> tnv;
+    double* tnp = n <= 64 ? tn : (tnv.resize(n), tnv.data());
+    for (int i = 0; i < n; ++i) {
+      tnp[i] = b->ctx[i]->t;
+      if ((st = step_prologue(b->ctx[i], dt[i]))) return st;
+    }
+    const int h = (int)(k & 1);
+    CUDA_TRY(cudaEventSynchronize(b->copied[h]));  // the pinned half from two steps ago has been copied
+    for (int l = 0; l < 4; ++l) {
+      for (int pass = 0; pass < 2; ++pass) {  // 0: ghost fill, 1: RHS + stage
+        const int r = 2 * l + pass;
+        char* hreg = b->h_args[h] + (size_t)r * b->region;
+        char* dreg = b->d_args + (size_t)r * b->region;
+        const size_t esz = pass ? sizeof(RhsArgs) : sizeof(FillArgs);
+        int* blk0 = reinterpret_cast<int*>(hreg + esz * n);
+        int total = 0;
+        for (int i = 0; i < n; ++i) {
+          mpw_ctx* c = b->ctx[i];
+          const double tl = tnp[i] + RK_C[l] * dt[i];
+          blk0[i] = total;
+          if (pass == 0) {
+            FillArgs* fa = reinterpret_cast<FillArgs*>(hreg) + i;
+            if ((st = prep_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], *fa))) return st;
+            total += fa->total_blocks;
+          } else {
+            RhsArgs* ra = reinterpret_cast<RhsArgs*>(hreg) + i;
+            total += prep_rhs(c, l, tl, dt[i], *ra, zc);
+          }
+        }
+        blk0[n] = total;
+        CUDA_TRY(cudaMemcpyAsync(dreg, hreg, esz * n + sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->stream));
+        const int* d_blk0 = reinterpret_cast<const int*>(dreg + esz * n);
+        if (pass == 0) {
+          launch_fill_batch(reinterpret_cast<const FillArgs*>(dreg), d_blk0, n, total, b->P, b->f32, b->stream);
+        } else {
+          if (trial && l == 0) CUDA_TRY(cudaEventRecord(b->tev[2 * k], b->stream));
+          if (b->f32)
+            launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, total, b->stream);
+          else
+            launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, total, b->fixed, b->stream);
+          if (trial && l == 3) CUDA_TRY(cudaEventRecord(b->tev[2 * k + 1], b->stream));
+        }
+        CUDA_TRY(cudaGetLastError());
+        ++b->launches;
+      }
+    }
+    CUDA_TRY(cudaEventRecord(b->copied[h], b->stream));
+    for (int i = 0; i < n; ++i) {
+      b->ctx[i]->t = tnp[i] + dt[i];
+      b->ctx[i]->stepped = true;
+    }
+    ++b->steps_done;
+    if (trial && b->steps_done == (long long)nc) {
+      // every candidate ran once (the fills in between are the same for all)
+      double best = 0.0;
+      for (size_t c = 0; c < nc; ++c) {
+        float ms = 0.0f;
+        CUDA_TRY(cudaEventSynchronize(b->tev[2 * c + 1]));
+        CUDA_TRY(cudaEventElapsedTime(&ms, b->tev[2 * c], b->tev[2 * c + 1]));
+        if (b->zc == 0 || ms < best) {
+          best = ms;
+          b->zc = b->cand[c];
+        }
+      }
+      b->zc_ms = best;
+    }
+  }
+  for (mpw_ctx* c : b->ctx)
+    if ((st = read_error_word(c))) return st;
+  return MPW_OK;
+}
+
+mpw_status mpw_batch_tuning(const mpw_batch* b, int* zc, double* rhs_ms, long long* launches) {
+  if (!b) return set_err(MPW_ERR_ARG, "null batch");
+  if (zc) *zc = b->zc;
+  if (rhs_ms) *rhs_ms = b->zc_ms;
+  if (launches) *launches = b->launches;
   return MPW_OK;
 }
 

@@ -394,15 +394,15 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
 
 }  // namespace
 
+// Body of the fill for block b of the launch described by A.
 template <int P, typename ST>
-__global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ FillArgs A) {
+__device__ __forceinline__ void fill_body(const FillArgs& A, const int b) {
   constexpr bool F32 = sizeof(ST) == 4;
   extern __shared__ double fill_smem[];
-  if (A.reset_buf >= 0 && blockIdx.x == 0 && threadIdx.x < 2 * A.np)
+  if (A.reset_buf >= 0 && b == 0 && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
-  if (A.reset_buf >= 0 && blockIdx.x == 0 && threadIdx.x < 2 * A.np)
+  if (A.reset_buf >= 0 && b == 0 && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
-  const int b = blockIdx.x;
   if (b < A.outer_blocks) {
     // global outer ghost shell, one point per thread
     const long long idx = (long long)b * FILL_THREADS + threadIdx.x;
@@ -458,6 +458,41 @@ __global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ F
     T[a] = min(S.td[sl][a], S.sb[sl][a] + S.se[sl][a] - org[a]);
   }
   interp_tile<P, ST>(A, S, org, T, 2 - sl / 2, fill_smem);  // slabs come in z, y, x pairs: the wall axis is thin
+}
+
+template <int P, typename ST>
+__global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ FillArgs A) {
+  fill_body<P, ST>(A, blockIdx.x);
+}
+
+// Batched launch: instance i owns blocks [blk0[i], blk0[i + 1]), arguments As[i].
+template <int P, typename ST>
+__global__ void __launch_bounds__(FILL_THREADS) k_fill_batch(const FillArgs* __restrict__ As,
+                                                             const int* __restrict__ blk0, int ninst) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)blockIdx.x >= blk0[mid]) lo = mid; else hi = mid - 1;
+  }
+  fill_body<P, ST>(As[lo], blockIdx.x - blk0[lo]);
+}
+
+template <int P, typename ST>
+static void launch_fill_batch_t(const FillArgs* d_args, const int* d_blk0, int ninst, int blocks, cudaStream_t s) {
+  cudaFuncSetAttribute(k_fill_batch<P, ST>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FILL_SMEM);
+  k_fill_batch<P, ST><<<blocks, FILL_THREADS, FILL_SMEM, s>>>(d_args, d_blk0, ninst);
+}
+
+void launch_fill_batch(const FillArgs* d_args, const int* d_blk0, int ninst, int blocks, int P, bool f32,
+                       void* stream) {
+  if (blocks <= 0) return;
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (f32)
+    P == 6 ? launch_fill_batch_t<6, float>(d_args, d_blk0, ninst, blocks, s)
+           : launch_fill_batch_t<5, float>(d_args, d_blk0, ninst, blocks, s);
+  else
+    P == 6 ? launch_fill_batch_t<6, double>(d_args, d_blk0, ninst, blocks, s)
+           : launch_fill_batch_t<5, double>(d_args, d_blk0, ninst, blocks, s);
 }
 
 template <int P, typename ST>

@@ -186,6 +186,12 @@ bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile
 // ---------------------------------------------------------------- host entry points of the kernels
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
 void launch_rhs32(const RhsArgs& a, int blocks, void* stream);  // binary32 storage and arithmetic
+// Batched launches over independent instances: d_args[i] (device memory)
+// describes instance i, whose blocks are [d_blk0[i], d_blk0[i + 1]).
+void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool fixed, void* stream);
+void launch_rhs32_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, void* stream);
+void launch_fill_batch(const FillArgs* d_args, const int* d_blk0, int ninst, int blocks, int P, bool f32,
+                       void* stream);
 void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);
 void launch_fill(const FillArgs& a, void* stream);
 int fill_max_thin_donors();

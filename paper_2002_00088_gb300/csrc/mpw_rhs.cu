@@ -135,8 +135,10 @@ __device__ __forceinline__ void issue_slot(const RhsPatch& Pt, int stage, double
   if (stage > 0) tma_load_4d(smem_u32(slot + TILE_DOUBLES + PT_DOUBLES), &Pt.amap, i0 + Pt.g.xoff, j0 + NG, zz + NG, 0, bar);
 }
 
+// Body of the kernel for block b of the launch described by A (A may sit in
+// kernel parameter space or, for a batched launch, in global memory).
 template <int TX, int TY, bool FIXED>
-__global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_constant__ RhsArgs A) {
+__device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
   static_assert(TX == RHS_TX && TY == RHS_TY, "TMA boxes are sized for RHS_TX x RHS_TY tiles");
   extern __shared__ unsigned char smem_dyn[];
   __shared__ Terms T;
@@ -147,7 +149,6 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   double* slots = reinterpret_cast<double*>(base);
   long long* conv = reinterpret_cast<long long*>(slots + RHS_DEPTH * SLOT_DOUBLES);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(conv + CONV_SLOTS * 2 * CONV_PLANE);
-  const int b = blockIdx.x;
   int p = 0;
   while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
   const RhsPatch& Pt = A.p[p];
@@ -400,6 +401,29 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_con
   }
 }
 
+template <int TX, int TY, bool FIXED>
+__global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_constant__ RhsArgs A) {
+  rhs_body<TX, TY, FIXED>(A, blockIdx.x);
+}
+
+// Batched launch over independent instances: instance i owns the blocks
+// [blk0[i], blk0[i + 1]) and its arguments As[i] (in global memory).
+__device__ __forceinline__ int batch_instance(const int* __restrict__ blk0, int ninst) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)blockIdx.x >= blk0[mid]) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+template <int TX, int TY, bool FIXED>
+__global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs_batch(const RhsArgs* __restrict__ As,
+                                                                      const int* __restrict__ blk0, int ninst) {
+  const int i = batch_instance(blk0, ninst);
+  rhs_body<TX, TY, FIXED>(As[i], blockIdx.x - blk0[i]);
+}
+
 // Host: TMA maps of one field buffer (4-D: x, y, plane, field).
 bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile, bool f32) {
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
@@ -421,6 +445,20 @@ bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile
                             estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
+}
+
+void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool fixed, void* stream) {
+  if (fixed) {
+    cudaFuncSetAttribute(k_rhs_batch<RHS_TX, RHS_TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RHS_SMEM);
+    k_rhs_batch<RHS_TX, RHS_TY, true><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(d_args, d_blk0,
+                                                                                                   ninst);
+  } else {
+    cudaFuncSetAttribute(k_rhs_batch<RHS_TX, RHS_TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RHS_SMEM);
+    k_rhs_batch<RHS_TX, RHS_TY, false><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(d_args, d_blk0,
+                                                                                                    ninst);
+  }
 }
 
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream) {

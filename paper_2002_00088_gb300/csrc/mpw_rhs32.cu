@@ -115,7 +115,7 @@ __device__ __forceinline__ f2 ko_pair(const AxisSums& a) {
 
 }  // namespace
 
-__global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid_constant__ RhsArgs A) {
+__device__ __forceinline__ void rhs32_body(const RhsArgs& A, const int b) {
   constexpr int TX = RHS_TX, TY = RHS_TY, SY = TX + 6;
   extern __shared__ unsigned char smem32[];
   __shared__ int s_abort;
@@ -123,7 +123,6 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid
   float* slots = reinterpret_cast<float*>(base);
   f2* ring = reinterpret_cast<f2*>(slots + R32_DEPTH * SLOT_F);  // [RING_SLOTS][RING_PLANE] (psi, Pi) pairs
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(ring + RING_SLOTS * RING_PLANE);
-  const int b = blockIdx.x;
   int p = 0;
   while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
   const RhsPatch& Pt = A.p[p];
@@ -296,6 +295,26 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid
 #pragma unroll
     for (int o = 0; o < 6; ++o) q[o] = q[o + 1];
   }
+}
+
+__global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid_constant__ RhsArgs A) {
+  rhs32_body(A, blockIdx.x);
+}
+
+// Batched launch: instance i owns blocks [blk0[i], blk0[i + 1]), arguments As[i].
+__global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32_batch(const RhsArgs* __restrict__ As,
+                                                                          const int* __restrict__ blk0, int ninst) {
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)blockIdx.x >= blk0[mid]) lo = mid; else hi = mid - 1;
+  }
+  rhs32_body(As[lo], blockIdx.x - blk0[lo]);
+}
+
+void launch_rhs32_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, void* stream) {
+  cudaFuncSetAttribute(k_rhs32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS32_SMEM);
+  k_rhs32_batch<<<blocks, RHS_TX * RHS_TY, RHS32_SMEM, (cudaStream_t)stream>>>(d_args, d_blk0, ninst);
 }
 
 void launch_rhs32(const RhsArgs& a, int blocks, void* stream) {

@@ -63,6 +63,10 @@ SIGNATURES = {
     "mpw_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
     "mpw_step_periodic_noalloc": (C.c_int, [C.POINTER(C.c_int), _dp, _dp, C.c_double, C.c_double, C.c_int, _vp, _vp,
                                             _vp]),
+    "mpw_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
+    "mpw_batch_step": (C.c_int, [_vp, _dp, C.c_int]),
+    "mpw_batch_tuning": (C.c_int, [_vp, C.POINTER(C.c_int), _dp, C.POINTER(C.c_longlong)]),
+    "mpw_batch_destroy": (None, [_vp]),
     "mpw_last_error": (C.c_char_p, []),
     "mpw_destroy": (None, [_vp]),
 }
@@ -261,3 +265,30 @@ class Multipatch:
         n = C.c_longlong()
         check(lib.mpw_live_points(self.h, C.byref(n)))
         return n.value
+
+
+class Batch:
+    """Independent Multipatch instances advanced together: one ghost-fill and
+    one RHS launch per substage over all of them (mpw_batch_*)."""
+
+    def __init__(self, sims):
+        self.sims = list(sims)  # keeps the contexts alive as long as the batch
+        arr = (C.c_void_p * len(self.sims))(*[s.h.value for s in self.sims])
+        self.h = C.c_void_p()
+        check(lib.mpw_batch_create(arr, len(self.sims), C.byref(self.h)))
+
+    def step(self, dt, nsteps=1):
+        """dt: one step size for all instances, or one per instance."""
+        d = np.broadcast_to(np.asarray(dt, dtype=np.float64), (len(self.sims),)).copy()
+        check(lib.mpw_batch_step(self.h, d.ctypes.data_as(_dp), int(nsteps)))
+
+    def tuning(self):
+        """(chosen RHS chunk depth or 0 while tuning, its RHS ms per step, batched launches)."""
+        zc, ms, n = C.c_int(), C.c_double(), C.c_longlong()
+        check(lib.mpw_batch_tuning(self.h, C.byref(zc), C.byref(ms), C.byref(n)))
+        return zc.value, ms.value, n.value
+
+    def __del__(self):
+        if getattr(self, "h", None) and self.h.value:
+            lib.mpw_batch_destroy(self.h)
+            self.h = C.c_void_p()

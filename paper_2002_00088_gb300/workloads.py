@@ -129,6 +129,46 @@ def plane_gauss(scale=1, steps=200, interp_points=6, seed_index=2):
                     0.25 * h_min, steps, {"centre": centre, "phase": phase})
 
 
+def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_global=192):
+    """Independent instances of uneven sizes for a batched run.
+
+    Instance k: a global cube of n_g^3 (n_g from 64 to ``max_global`` in steps
+    of 32) on [-1,1]^3 with the analytic outer BC, and 1 to 8 local cubes of
+    n_l^3 at 2x resolution (n_l from 32 to n_g/2), one per octant of the
+    global box, each centred in its octant and moving with a seeded constant
+    velocity of at most 0.5.  The velocity is capped so that after ``steps``
+    steps of dt = h_local/4 the cube keeps its containment margin and its
+    gap to the neighbouring octants.  Initial data: two Gaussian pulses
+    (amplitudes N(0,1), widths U[0.08,0.2], centres U[-0.8,0.8]^3)."""
+    r = rng(seed_index)
+    out = []
+    sizes = [n for n in range(64, max_global + 1, 32)]
+    for k in range(count):
+        ng = int(r.choice(sizes))
+        nloc = int(r.integers(1, 9))
+        nl = int(r.choice([n for n in range(32, ng // 2 + 1, 16)]))
+        h0, hl = 2.0 / ng, 1.0 / ng
+        dt = 0.25 * hl
+        ext = nl * hl                       # local cube edge
+        margin = 3 * hl + 8 * h0            # to the octant walls (containment, gaps)
+        room = 0.5 * (1.0 - ext) - margin   # free travel inside the octant
+        vmax = max(0.0, min(0.5, room / (steps * dt)))
+        octs = r.permutation(8)[:nloc]
+        patches = [PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC)]
+        for o in octs:
+            c = np.array([0.5 if (o >> a) & 1 else -0.5 for a in range(3)])
+            d = r.normal(size=3)
+            v = d / np.linalg.norm(d) * r.uniform(0.0, vmax)
+            half = 0.5 * ext
+            patches.append(PatchSpec(LOCAL, (nl, nl, nl), (-half,) * 3, (half,) * 3, BC_INTERPATCH, LINEAR,
+                                     (c[0], c[1], c[2], v[0], v[1], v[2])))
+        params = np.column_stack([r.normal(0.0, 1.0, 2), r.uniform(0.08, 0.2, 2),
+                                  r.uniform(-0.8, 0.8, (2, 3))]).ravel()
+        out.append(Workload(f"instance{k}_{ng}+{nloc}x{nl}", patches, GAUSS_SUM, params, 2, interp_points, 0.005,
+                            dt, steps))
+    return out
+
+
 def translating_plane(scale=1, steps=16, interp_points=6, velocity=(0.4, 0.3, 0.0), start=(-0.05, -0.02, 0.0)):
     """Sec. 3.2-style convergence layout at reduced size: global cube [-1,1]^3
     and a 2:1 local cube [-0.5,0.5]^3 translating with constant velocity,

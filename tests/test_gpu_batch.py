@@ -1,0 +1,52 @@
+"""Batched stepping (mpw_batch_*): several independent instances advanced with
+one ghost-fill and one RHS launch per substage over all of them.  The batch
+must reproduce, bit for bit, each instance stepped on its own; the chunk-depth
+tuning that runs during the first steps must not change any value."""
+import numpy as np
+import pytest
+
+from paper_2002_00088_gb300 import workloads as wl
+from tests.helpers import gpu_from
+
+pytestmark = pytest.mark.gpu
+
+
+def make_all(mpw, ws, precision):
+    sims = []
+    for w in ws:
+        g = gpu_from(mpw, w, precision=precision)
+        g.fill_analytic(0.0)
+        sims.append(g)
+    return sims
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_matches_individual_steps(mpw_lib, precision):
+    ws = wl.batch_instances(count=5, steps=12, seed_index=11, max_global=96)
+    assert any(p.motion == wl.LINEAR and any(p.motion_params[3:6]) for w in ws for p in w.patches[1:])
+    alone = make_all(mpw_lib, ws, precision)
+    together = make_all(mpw_lib, ws, precision)
+    steps = 6  # four tuning steps (chunk depths 8, 16, 32, 64), then the chosen depth
+    for g, w in zip(alone, ws):
+        g.step(w.dt, steps)
+    b = mpw_lib.Batch(together)
+    b.step([w.dt for w in ws], steps)
+    zc, ms, launches = b.tuning()
+    assert zc in (8, 16, 32, 64) and ms > 0.0
+    assert launches == 8 * steps
+    for g, h, w in zip(alone, together, ws):
+        assert g.time == h.time
+        np.testing.assert_array_equal(g.get_flags(), h.get_flags())
+        for q in range(len(w.patches)):
+            a, c = g.get_fields(q), h.get_fields(q)
+            np.testing.assert_array_equal(a[0], c[0])
+            np.testing.assert_array_equal(a[1], c[1])
+
+
+def test_batch_rejects_mixed_precision(mpw_lib):
+    ws = wl.batch_instances(count=2, steps=12, seed_index=12, max_global=64)
+    a = gpu_from(mpw_lib, ws[0], precision=64)
+    c = gpu_from(mpw_lib, ws[1], precision=32)
+    with pytest.raises(mpw_lib.MpwError) as e:
+        mpw_lib.Batch([a, c])
+    assert e.value.status == 1
