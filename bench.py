@@ -57,6 +57,9 @@ def parse():
     ap.add_argument("--ref-sample-scale", type=int, default=2,
                     help="--impl reference: resolution divisor of the oracle sample taken per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch", type=int, default=0,
+                    help="time N independent instances of uneven sizes (workloads.batch_instances) advanced with "
+                         "batched launches, beside the same instances stepped one after the other")
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="64: the FP64 workload (default); 32: the binary32 precision workload, with its error "
                          "against the closed form and the FP64 path on the same workload")
@@ -400,10 +403,82 @@ def run_ours(args):
     return 0
 
 
+def run_batch(args):
+    """Batched instances: value = live points of all instances x 4 x steps /
+    device time of the batched steps; "sequential" times the same instances
+    stepped one after the other with mpw_step."""
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    from paper_2002_00088_gb300.build import build_library
+    build_library()
+    from paper_2002_00088_gb300 import mpw
+    from paper_2002_00088_gb300 import workloads as wl
+    ws = wl.batch_instances(count=args.batch, steps=args.warmup + args.steps)
+    stream = torch.cuda.current_stream(local)
+
+    def make():
+        sims = []
+        for w in ws:
+            g = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream, precision=args.precision)
+            for p in w.patches:
+                g.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+            g.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
+            g.fill_analytic(0.0)
+            sims.append(g)
+        return sims
+
+    dts = [w.dt for w in ws]
+    sims = make()
+    live = sum(g.live_points() for g in sims)
+    b = mpw.Batch(sims)
+    b.step(dts, args.warmup + 4)  # warm-up, including the four chunk-depth trials
+    zc, zc_ms, _ = b.tuning()
+    sampler = ClockSampler(local)
+    sampler.start()
+    start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    start.record(stream)
+    b.step(dts, args.steps)
+    end.record(stream)
+    torch.cuda.synchronize()
+    ms = start.elapsed_time(end)
+    clocks = sampler.stop()
+    del b, sims
+    torch.cuda.empty_cache()
+    # the same instances, one mpw_step after the other
+    seq = make()
+    for g, dt in zip(seq, dts):
+        g.step(dt, args.warmup)
+    torch.cuda.synchronize()
+    start.record(stream)
+    for _ in range(args.steps):
+        for g, dt in zip(seq, dts):
+            g.step(dt, 1)
+    end.record(stream)
+    torch.cuda.synchronize()
+    ms_seq = start.elapsed_time(end)
+    line = {
+        "metric": METRIC, "value": live * 4 * args.steps / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
+        "data": "synthetic (seeded closed-form Gaussian pulses)",
+        "config": {"workload": f"batch of {len(ws)} instances (globals 64^3-192^3, 1-8 moving locals each)",
+                   "instances": len(ws), "live_points": live, "parallelism": "single",
+                   "rhs_chunk_depth": zc, "tuning_rhs_ms": zc_ms},
+        "sequential": {"value": live * 4 * args.steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps},
+        "gpu_launches": 8 * args.steps, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.batch:
+        return run_batch(args)
     return run_ours(args)
 
 
