@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--batch", type=int, default=0,
                     help="time N independent instances of uneven sizes (workloads.batch_instances) advanced with "
                          "batched launches, beside the same instances stepped one after the other")
+    ap.add_argument("--max-global", type=int, default=192, help="--batch: largest global patch edge")
+    ap.add_argument("--static", action="store_true", help="--batch: local patches do not move (graph replay)")
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="64: the FP64 workload (default); 32: the binary32 precision workload, with its error "
                          "against the closed form and the FP64 path on the same workload")
@@ -414,7 +416,8 @@ def run_batch(args):
     build_library()
     from paper_2002_00088_gb300 import mpw
     from paper_2002_00088_gb300 import workloads as wl
-    ws = wl.batch_instances(count=args.batch, steps=args.warmup + args.steps)
+    ws = wl.batch_instances(count=args.batch, steps=args.warmup + args.steps + 4, max_global=args.max_global,
+                            moving=not args.static)
     stream = torch.cuda.current_stream(local)
 
     def make():
@@ -433,7 +436,7 @@ def run_batch(args):
     live = sum(g.live_points() for g in sims)
     b = mpw.Batch(sims)
     b.step(dts, args.warmup + 4)  # warm-up, including the four chunk-depth trials
-    zc, zc_ms, _ = b.tuning()
+    zc, zc_ms, _, g0 = b.tuning()
     sampler = ClockSampler(local)
     sampler.start()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -444,6 +447,7 @@ def run_batch(args):
     torch.cuda.synchronize()
     ms = start.elapsed_time(end)
     clocks = sampler.stop()
+    graph_steps = b.tuning()[3] - g0
     del b, sims
     torch.cuda.empty_cache()
     # the same instances, one mpw_step after the other
@@ -463,9 +467,10 @@ def run_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
         "data": "synthetic (seeded closed-form Gaussian pulses)",
-        "config": {"workload": f"batch of {len(ws)} instances (globals 64^3-192^3, 1-8 moving locals each)",
+        "config": {"workload": f"batch of {len(ws)} instances (globals 64^3-{args.max_global}^3, 1-8 "
+                               f"{'static' if args.static else 'moving'} locals each)",
                    "instances": len(ws), "live_points": live, "parallelism": "single",
-                   "rhs_chunk_depth": zc, "tuning_rhs_ms": zc_ms},
+                   "rhs_chunk_depth": zc, "tuning_rhs_ms": zc_ms, "graph_replayed_steps": graph_steps},
         "sequential": {"value": live * 4 * args.steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps},
         "gpu_launches": 8 * args.steps, "clocks": clocks,
     }

@@ -193,13 +193,19 @@ mpw_status mpw_step(mpw_ctx* ctx, double dt, int nsteps);
  *   chunk depth (planes marched per CTA): each candidate (8, 16, 32, 64)
  *   runs one step, timed with CUDA events, and the fastest is kept.
  *   Errors as mpw_step, for the first instance that fails.
+ *   While no instance has a moving patch, the copies and launches of a step
+ *   are captured once in a CUDA graph (one per argument buffer) and replayed:
+ *   the launches and grids are then the same every step, and the replayed
+ *   copies pick up the new substage times from the page-locked buffers.
  * mpw_batch_tuning: the chosen chunk depth (0 while tuning), its measured
- *   RHS time per step in ms, and the number of batched launches so far.
+ *   RHS time per step in ms, the number of batched launches so far and the
+ *   number of steps replayed from a captured graph.
  * mpw_batch_destroy: frees the tables (not the contexts). */
 typedef struct mpw_batch mpw_batch;
 mpw_status mpw_batch_create(mpw_ctx* const* ctxs, int n, mpw_batch** out);
 mpw_status mpw_batch_step(mpw_batch* batch, const double* dt, int nsteps);
-mpw_status mpw_batch_tuning(const mpw_batch* batch, int* chunk, double* rhs_ms, long long* launches);
+mpw_status mpw_batch_tuning(const mpw_batch* batch, int* chunk, double* rhs_ms, long long* launches,
+                            long long* graph_steps);
 void mpw_batch_destroy(mpw_batch* batch);
 
 /* Number of live points summed over patches (the unit of the throughput

@@ -1095,6 +1095,15 @@ struct mpw_batch {
   int zc = 0;                    // chosen chunk depth (0 until tuned)
   double zc_ms = 0.0;            // its measured RHS time per step
   long long launches = 0;
+  // CUDA graphs of one step (one per pinned half), used while no instance
+  // moves: the launches and their grids are then the same every step and
+  // only the argument values (substage times) change, which the captured
+  // copies pick up from the pinned half at replay
+  cudaStream_t cap = nullptr;    // capture stream
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int gtot[2][8] = {};
+  bool graphs = true;
+  long long graph_steps = 0;
 };
 
 namespace {
@@ -1134,6 +1143,7 @@ mpw_status mpw_batch_create(mpw_ctx* const* ctxs, int n, mpw_batch** out) {
   for (int h = 0; h < 2 && ok; ++h)
     ok = cudaMallocHost(&b->h_args[h], 8 * b->region) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->copied[h], cudaEventDisableTiming) == cudaSuccess;
+  ok = ok && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
   for (int z : ZC_CANDIDATES) b->cand.push_back(z);
   b->tev.resize(2 * b->cand.size());
   for (auto& e : b->tev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
@@ -1155,6 +1165,9 @@ void mpw_batch_destroy(mpw_batch* b) {
   }
   for (auto& e : b->tev)
     if (e) cudaEventDestroy(e);
+  for (int h = 0; h < 2; ++h)
+    if (b->gexec[h]) cudaGraphExecDestroy(b->gexec[h]);
+  if (b->cap) cudaStreamDestroy(b->cap);
   delete b;
 }
 
@@ -1183,11 +1196,12 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     }
     const int h = (int)(k & 1);
     CUDA_TRY(cudaEventSynchronize(b->copied[h]));  // the pinned half from two steps ago has been copied
+    // arguments of the 8 launches of this step into pinned half h
+    int totals[8];
     for (int l = 0; l < 4; ++l) {
       for (int pass = 0; pass < 2; ++pass) {  // 0: ghost fill, 1: RHS + stage
         const int r = 2 * l + pass;
         char* hreg = b->h_args[h] + (size_t)r * b->region;
-        char* dreg = b->d_args + (size_t)r * b->region;
         const size_t esz = pass ? sizeof(RhsArgs) : sizeof(FillArgs);
         int* blk0 = reinterpret_cast<int*>(hreg + esz * n);
         int total = 0;
@@ -1205,22 +1219,62 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
           }
         }
         blk0[n] = total;
-        CUDA_TRY(cudaMemcpyAsync(dreg, hreg, esz * n + sizeof(int) * (n + 1), cudaMemcpyHostToDevice, b->stream));
-        const int* d_blk0 = reinterpret_cast<const int*>(dreg + esz * n);
-        if (pass == 0) {
-          launch_fill_batch(reinterpret_cast<const FillArgs*>(dreg), d_blk0, n, total, b->P, b->f32, b->stream);
-        } else {
-          if (trial && l == 0) CUDA_TRY(cudaEventRecord(b->tev[2 * k], b->stream));
-          if (b->f32)
-            launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, total, b->stream);
-          else
-            launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, total, b->fixed, b->stream);
-          if (trial && l == 3) CUDA_TRY(cudaEventRecord(b->tev[2 * k + 1], b->stream));
-        }
-        CUDA_TRY(cudaGetLastError());
-        ++b->launches;
+        totals[r] = total;
       }
     }
+    // copies and launches of the step, on stream sm
+    auto enqueue = [&](cudaStream_t sm) -> cudaError_t {
+      for (int r = 0; r < 8; ++r) {
+        const int l = r / 2, pass = r % 2;
+        char* hreg = b->h_args[h] + (size_t)r * b->region;
+        char* dreg = b->d_args + (size_t)r * b->region;
+        const size_t esz = pass ? sizeof(RhsArgs) : sizeof(FillArgs);
+        cudaError_t e = cudaMemcpyAsync(dreg, hreg, esz * n + sizeof(int) * (n + 1), cudaMemcpyHostToDevice, sm);
+        if (e != cudaSuccess) return e;
+        const int* d_blk0 = reinterpret_cast<const int*>(dreg + esz * n);
+        if (pass == 0) {
+          launch_fill_batch(reinterpret_cast<const FillArgs*>(dreg), d_blk0, n, totals[r], b->P, b->f32, sm);
+        } else {
+          if (trial && l == 0) cudaEventRecord(b->tev[2 * k], sm);
+          if (b->f32)
+            launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], sm);
+          else
+            launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], b->fixed, sm);
+          if (trial && l == 3) cudaEventRecord(b->tev[2 * k + 1], sm);
+        }
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
+      return cudaSuccess;
+    };
+    bool moving = false;
+    for (mpw_ctx* c : b->ctx) moving = moving || any_moving(c);
+    bool replayed = false;
+    if (b->graphs && !trial && !moving) {
+      if (!b->gexec[h] || std::memcmp(b->gtot[h], totals, sizeof(totals)) != 0) {
+        if (b->gexec[h]) cudaGraphExecDestroy(b->gexec[h]);
+        b->gexec[h] = nullptr;
+        cudaGraph_t graph = nullptr;
+        bool ok = cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+        const cudaError_t eq = ok ? enqueue(b->cap) : cudaErrorUnknown;
+        ok = cudaStreamEndCapture(b->cap, &graph) == cudaSuccess && ok && eq == cudaSuccess && graph;
+        ok = ok && cudaGraphInstantiate(&b->gexec[h], graph, 0) == cudaSuccess;
+        if (graph) cudaGraphDestroy(graph);
+        cudaGetLastError();
+        if (ok) {
+          std::memcpy(b->gtot[h], totals, sizeof(totals));
+        } else {
+          b->gexec[h] = nullptr;
+          b->graphs = false;  // this configuration does not capture: launch directly from now on
+        }
+      }
+      if (b->gexec[h]) {
+        CUDA_TRY(cudaGraphLaunch(b->gexec[h], b->stream));
+        ++b->graph_steps;
+        replayed = true;
+      }
+    }
+    if (!replayed) CUDA_TRY(enqueue(b->stream));
+    b->launches += 8;
     CUDA_TRY(cudaEventRecord(b->copied[h], b->stream));
     for (int i = 0; i < n; ++i) {
       b->ctx[i]->t = tnp[i] + dt[i];
@@ -1247,11 +1301,13 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
   return MPW_OK;
 }
 
-mpw_status mpw_batch_tuning(const mpw_batch* b, int* zc, double* rhs_ms, long long* launches) {
+mpw_status mpw_batch_tuning(const mpw_batch* b, int* zc, double* rhs_ms, long long* launches,
+                            long long* graph_steps) {
   if (!b) return set_err(MPW_ERR_ARG, "null batch");
   if (zc) *zc = b->zc;
   if (rhs_ms) *rhs_ms = b->zc_ms;
   if (launches) *launches = b->launches;
+  if (graph_steps) *graph_steps = b->graph_steps;
   return MPW_OK;
 }
 

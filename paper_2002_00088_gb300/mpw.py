@@ -65,7 +65,8 @@ SIGNATURES = {
                                             _vp]),
     "mpw_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
     "mpw_batch_step": (C.c_int, [_vp, _dp, C.c_int]),
-    "mpw_batch_tuning": (C.c_int, [_vp, C.POINTER(C.c_int), _dp, C.POINTER(C.c_longlong)]),
+    "mpw_batch_tuning": (C.c_int, [_vp, C.POINTER(C.c_int), _dp, C.POINTER(C.c_longlong),
+                                   C.POINTER(C.c_longlong)]),
     "mpw_batch_destroy": (None, [_vp]),
     "mpw_last_error": (C.c_char_p, []),
     "mpw_destroy": (None, [_vp]),
@@ -283,10 +284,11 @@ class Batch:
         check(lib.mpw_batch_step(self.h, d.ctypes.data_as(_dp), int(nsteps)))
 
     def tuning(self):
-        """(chosen RHS chunk depth or 0 while tuning, its RHS ms per step, batched launches)."""
-        zc, ms, n = C.c_int(), C.c_double(), C.c_longlong()
-        check(lib.mpw_batch_tuning(self.h, C.byref(zc), C.byref(ms), C.byref(n)))
-        return zc.value, ms.value, n.value
+        """(chosen RHS chunk depth or 0 while tuning, its RHS ms per step,
+        batched launches, steps replayed from a captured CUDA graph)."""
+        zc, ms, n, g = C.c_int(), C.c_double(), C.c_longlong(), C.c_longlong()
+        check(lib.mpw_batch_tuning(self.h, C.byref(zc), C.byref(ms), C.byref(n), C.byref(g)))
+        return zc.value, ms.value, n.value, g.value
 
     def __del__(self):
         if getattr(self, "h", None) and self.h.value:

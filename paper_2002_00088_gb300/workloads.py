@@ -129,7 +129,7 @@ def plane_gauss(scale=1, steps=200, interp_points=6, seed_index=2):
                     0.25 * h_min, steps, {"centre": centre, "phase": phase})
 
 
-def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_global=192):
+def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_global=192, moving=True):
     """Independent instances of uneven sizes for a batched run.
 
     Instance k: a global cube of n_g^3 (n_g from 64 to ``max_global`` in steps
@@ -139,7 +139,8 @@ def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_glob
     velocity of at most 0.5.  The velocity is capped so that after ``steps``
     steps of dt = h_local/4 the cube keeps its containment margin and its
     gap to the neighbouring octants.  Initial data: two Gaussian pulses
-    (amplitudes N(0,1), widths U[0.08,0.2], centres U[-0.8,0.8]^3)."""
+    (amplitudes N(0,1), widths U[0.08,0.2], centres U[-0.8,0.8]^3).  With
+    ``moving=False`` every local cube stays at its octant centre."""
     r = rng(seed_index)
     out = []
     sizes = [n for n in range(64, max_global + 1, 32)]
@@ -152,7 +153,7 @@ def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_glob
         ext = nl * hl                       # local cube edge
         margin = 3 * hl + 8 * h0            # to the octant walls (containment, gaps)
         room = 0.5 * (1.0 - ext) - margin   # free travel inside the octant
-        vmax = max(0.0, min(0.5, room / (steps * dt)))
+        vmax = max(0.0, min(0.5, room / (steps * dt))) if moving else 0.0
         octs = r.permutation(8)[:nloc]
         patches = [PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC)]
         for o in octs:

@@ -31,9 +31,10 @@ def test_batch_matches_individual_steps(mpw_lib, precision):
         g.step(w.dt, steps)
     b = mpw_lib.Batch(together)
     b.step([w.dt for w in ws], steps)
-    zc, ms, launches = b.tuning()
+    zc, ms, launches, graph_steps = b.tuning()
     assert zc in (8, 16, 32, 64) and ms > 0.0
     assert launches == 8 * steps
+    assert graph_steps == 0  # instances with moving patches are launched directly
     for g, h, w in zip(alone, together, ws):
         assert g.time == h.time
         np.testing.assert_array_equal(g.get_flags(), h.get_flags())
@@ -50,3 +51,24 @@ def test_batch_rejects_mixed_precision(mpw_lib):
     with pytest.raises(mpw_lib.MpwError) as e:
         mpw_lib.Batch([a, c])
     assert e.value.status == 1
+
+
+def test_static_batch_replays_a_captured_graph(mpw_lib):
+    """Without moving patches the step is captured in a CUDA graph after the
+    tuning steps; replaying it must give the same bits as stepping alone."""
+    ws = [wl.static_gauss(interp_points=6), wl.plane_gauss(scale=8)]
+    alone = make_all(mpw_lib, ws, 64)
+    together = make_all(mpw_lib, ws, 64)
+    steps = 9
+    for g, w in zip(alone, ws):
+        g.step(w.dt, steps)
+    b = mpw_lib.Batch(together)
+    b.step([w.dt for w in ws], 5)
+    b.step([w.dt for w in ws], steps - 5)
+    _, _, launches, graph_steps = b.tuning()
+    assert launches == 8 * steps and graph_steps == steps - 4
+    for g, h, w in zip(alone, together, ws):
+        for q in range(len(w.patches)):
+            a, c = g.get_fields(q), h.get_fields(q)
+            np.testing.assert_array_equal(a[0], c[0])
+            np.testing.assert_array_equal(a[1], c[1])
