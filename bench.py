@@ -72,6 +72,22 @@ def dist_info():
     return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
 
 
+def whole_job(seconds, units, world, device="cpu"):
+    """Whole-job throughput of independent replicas: the units of every rank
+    divided by the slowest rank's time (a max over ranks; no data-path
+    collective).  Returns (max seconds, summed units, units per second)."""
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([float(seconds), float(units)], dtype=torch.float64, device=device)
+        mx = t.clone()
+        dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+        sm = t.clone()
+        dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+        seconds, units = float(mx[0]), float(sm[1])
+    return seconds, units, units / seconds
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -322,11 +338,8 @@ def run_ours(args):
     prof = sim.profile_read()
     sim.profile(False)
     clocks = sampler.stop()
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms = float(t.item())
-    value = live * 4 * args.steps * world / (ms * 1e-3)
+    sec, _, value = whole_job(ms * 1e-3, live * 4 * args.steps, world, "cuda")
+    ms = sec * 1e3
     accuracy = precision_report(args, w, sim, mpw, stream, local) if f32 else None
 
     # ---- end-to-end through the C ABI with host buffers: every step copies the
@@ -353,11 +366,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_value = live * 4 * args.e2e_steps * world / e2e_s
+    e2e_s, _, e2e_value = whole_job(e2e_s, live * 4 * args.e2e_steps, world, "cuda")
 
     if rank != 0:
         if world > 1:
