@@ -180,6 +180,56 @@ __device__ __forceinline__ void thin_pass(const InterpSeg& S, int a0, const int 
   ext[a0] = T0;
   const int ostr[3] = {1, ext[0], ext[0] * ext[1]};
   const int npen = n1 * n2;
+  auto pencil = [&](int e, int& f, int& obase) -> const ST* {
+    f = e >= npen;
+    const int p = e - f * npen;
+    const int c1 = p % n1, c2 = p / n1;
+    int o[3];
+    o[a0] = D0[a0];
+    o[a1] = D0[a1] + c1;
+    o[a2] = D0[a2] + c2;
+    obase = c1 * ostr[a1] + c2 * ostr[a2] + f * CAP_R1;
+    return reinterpret_cast<const ST*>(S.D) + f * S.gd.vol + S.gd.at(o[0], o[1], o[2]);
+  };
+  if (MODE == M_FIXED) {
+    // software-pipelined: the next pencil's donors are in flight while this
+    // one is converted and contracted
+    ST raw[MAXD];
+    int f, obase;
+    if ((int)threadIdx.x < 2 * npen) {
+      const ST* src = pencil(threadIdx.x, f, obase);
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) raw[k] = k < nk ? src[k * st0] : (ST)0;
+    }
+    const int2* bq = static_cast<const int2*>(band);
+    for (int e = threadIdx.x; e < 2 * npen; e += FILL_THREADS) {
+      pencil(e, f, obase);
+      ST nxt[MAXD];
+      const int en = e + FILL_THREADS;
+      if (en < 2 * npen) {
+        int fn, on;
+        const ST* src = pencil(en, fn, on);
+#pragma unroll
+        for (int k = 0; k < MAXD; ++k) nxt[k] = k < nk ? src[k * st0] : (ST)0;
+      }
+      const int E = f ? Ep : Es;
+      int2 v[MAXD];
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) v[k] = split31(k < nk ? to_fixed((double)raw[k], E) * 64 : 0);
+#pragma unroll
+      for (int t = 0; t < MAXT0; ++t) {
+        if (t >= T0) break;
+        Acc3 acc;
+#pragma unroll
+        for (int k = 0; k < MAXD; ++k)
+          if (k < nk) acc.mac(v[k], bq[t * MAXD + k]);
+        static_cast<int2*>(out)[obase + t * ostr[a0]] = split31(acc.value());
+      }
+#pragma unroll
+      for (int k = 0; k < MAXD; ++k) raw[k] = nxt[k];
+    }
+    return;
+  }
   for (int e = threadIdx.x; e < 2 * npen; e += FILL_THREADS) {
     const int f = e >= npen;
     const int p = e - f * npen;
@@ -394,14 +444,19 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
 
 }  // namespace
 
-// Body of the fill for block b of the launch described by A.
+// Body of the fill for block b0 of the launch described by A.  The launch
+// runs the interpolation tiles first and the outer-shell blocks after them
+// (the tiles take longer; measured 5 % faster than the other order); b is
+// the block in A's numbering (outer shell first, then the segments).
 template <int P, typename ST>
-__device__ __forceinline__ void fill_body(const FillArgs& A, const int b) {
+__device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
   constexpr bool F32 = sizeof(ST) == 4;
   extern __shared__ double fill_smem[];
-  if (A.reset_buf >= 0 && b == 0 && threadIdx.x < 2 * A.np)
+  const int ntile = A.total_blocks - A.outer_blocks;
+  const int b = b0 < ntile ? b0 + A.outer_blocks : b0 - ntile;
+  if (A.reset_buf >= 0 && b0 == 0 && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
-  if (A.reset_buf >= 0 && b == 0 && threadIdx.x < 2 * A.np)
+  if (A.reset_buf >= 0 && b0 == 0 && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
   if (b < A.outer_blocks) {
     // global outer ghost shell, one point per thread
