@@ -144,6 +144,25 @@ mpw_status mpw_set_fields(mpw_ctx* ctx, int patch, const double* psi, const doub
  * (effective ghost or deactivated, Sec. 2.4.2) read as NaN. */
 mpw_status mpw_get_fields(mpw_ctx* ctx, int patch, double* psi, double* pi, int on_device);
 
+/* Asynchronous host transfers for pipelined use (no counterpart in the
+ * paper): the copies run on the GPU's copy engines, on two streams of the
+ * context's own, so that the next step's input travels in and the last
+ * step's result travels out while a step computes.  psi and pi must be
+ * page-locked host arrays (dense interior, binary64); MPW_ERR_ARG otherwise.
+ *   mpw_set_fields_async queues psi, pi as the new interior of `patch`: they
+ *     are copied into a device staging buffer and enter u at the start of
+ *     the next call that reads or writes u (mpw_step, a get, a fill ...).
+ *     The host arrays must stay unchanged until mpw_sync.
+ *   mpw_get_fields_async copies the current interior out (NaN on non-live
+ *     global cells, as mpw_get_fields) through a device staging buffer; the
+ *     host arrays hold it after mpw_sync.  A second get of the same patch
+ *     waits on the device for the first to leave the staging buffer.
+ *   mpw_sync waits for the context's stream and both copy streams.
+ * Staging takes 2 x 2 x n0 n1 n2 doubles per patch, allocated on first use. */
+mpw_status mpw_set_fields_async(mpw_ctx* ctx, int patch, const double* psi, const double* pi);
+mpw_status mpw_get_fields_async(mpw_ctx* ctx, int patch, double* psi, double* pi);
+mpw_status mpw_sync(mpw_ctx* ctx);
+
 /* Copy the whole padded box of the state u (ghost zones included) out, dense
  * [k][j][i] over (n+6)^3, index (i+3) + (n0+6)((j+3) + (n1+6)(k+3)).  Ghost
  * values are those of the last boundary fill of substage 1 (or of

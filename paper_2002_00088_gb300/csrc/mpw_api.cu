@@ -53,6 +53,13 @@ struct PatchState {
   size_t esize = 8;           // bytes per element
   CUtensorMap tile_map[4];    // RHS input tiles of each buffer (TMA)
   CUtensorMap point_map[2];   // RHS stage operands: u, ACC (TMA)
+  // asynchronous host IO (mpw_set_fields_async / mpw_get_fields_async):
+  // device staging of the next input and of the last result (2 n doubles
+  // each), and the events that order them with the copy streams
+  double* io_in = nullptr;
+  double* io_out = nullptr;
+  cudaEvent_t in_copied = nullptr, in_free = nullptr, out_packed = nullptr, out_free = nullptr;
+  bool in_pending = false;
   // device address of buffer b (its element type follows esize)
   double* buf(int b) const {
     return reinterpret_cast<double*>(reinterpret_cast<char*>(base) + (size_t)b * 2 * (size_t)g.vol * esize);
@@ -87,6 +94,8 @@ struct mpw_ctx {
   double shell_time[4] = {NAN, NAN, NAN, NAN};
   double* d_stage = nullptr;
   size_t stage_bytes = 0;
+  // copy streams of the asynchronous host IO: inputs in, results out
+  cudaStream_t io_in = nullptr, io_out = nullptr;
   double t = 0.0;
   bool stepped = false;
   // measurement: per kernel family, a pool of event pairs and a launch count
@@ -676,6 +685,8 @@ void set_last_error(const char* msg) { g_last_error = msg; }
 
 extern "C" {
 
+static mpw_status apply_pending_inputs(mpw_ctx* c);
+
 const char* mpw_last_error(void) { return g_last_error.c_str(); }
 
 mpw_status mpw_create(const mpw_config* cfg, mpw_ctx** out) {
@@ -722,7 +733,17 @@ void mpw_destroy(mpw_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->cfg.device);
   cudaStreamSynchronize(c->stream);
-  for (auto& P : c->p) c->dfree(P.base);
+  if (c->io_in) cudaStreamSynchronize(c->io_in);
+  if (c->io_out) cudaStreamSynchronize(c->io_out);
+  for (auto& P : c->p) {
+    c->dfree(P.base);
+    c->dfree(P.io_in);
+    c->dfree(P.io_out);
+    for (cudaEvent_t e : {P.in_copied, P.in_free, P.out_packed, P.out_free})
+      if (e) cudaEventDestroy(e);
+  }
+  if (c->io_in) cudaStreamDestroy(c->io_in);
+  if (c->io_out) cudaStreamDestroy(c->io_out);
   c->dfree(c->d_flags);
   c->dfree(c->d_err);
   c->dfree(c->d_aparams);
@@ -830,6 +851,7 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
   if (st) return st;
   if (c->akind < 0) return set_err(MPW_ERR_STATE, "no analytic function set");
   if (use_device(c)) return MPW_ERR_CUDA;
+  if ((st = apply_pending_inputs(c))) return st;
   for (auto& P : c->p) {
     double X0[3], w[3];
     motion(P.d, t, X0, w);
@@ -851,6 +873,40 @@ static mpw_status get_patch(mpw_ctx* c, int patch, PatchState** out) {
   return use_device(c);
 }
 
+// Staging buffers, events and copy streams of the asynchronous host IO of
+// patch P (allocated on first use).
+static mpw_status ensure_async_io(mpw_ctx* c, PatchState& P) {
+  if (!c->io_in) {
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->io_in, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&c->io_out, cudaStreamNonBlocking));
+  }
+  if (!P.io_in) {
+    const size_t bytes = 2 * sizeof(double) * (size_t)P.d.n[0] * P.d.n[1] * P.d.n[2];
+    P.io_in = (double*)c->dalloc(bytes);
+    P.io_out = (double*)c->dalloc(bytes);
+    if (!P.io_in || !P.io_out) return set_err(MPW_ERR_CUDA, "IO staging allocation of %zu bytes failed", bytes);
+    for (cudaEvent_t* e : {&P.in_copied, &P.in_free, &P.out_packed, &P.out_free})
+      CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  }
+  return MPW_OK;
+}
+
+// Inputs queued by mpw_set_fields_async enter u, in stream order, before
+// anything reads or writes u.
+static mpw_status apply_pending_inputs(mpw_ctx* c) {
+  for (auto& P : c->p) {
+    if (!P.in_pending) continue;
+    const size_t n = (size_t)P.d.n[0] * P.d.n[1] * P.d.n[2];
+    CUDA_TRY(cudaStreamWaitEvent(c->stream, P.in_copied, 0));
+    launch_unpack(P.buf(BUF_U), P.g, P.io_in, P.io_in + n, c->cfg.precision == 32, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaEventRecord(P.in_free, c->stream));
+    P.in_pending = false;
+    P.u_expo_valid = false;
+  }
+  return MPW_OK;
+}
+
 // Device alias of a page-locked host array (cudaHostAlloc, cudaMallocHost or
 // cudaHostRegister'ed memory mapped into the device address space), or null
 // for pageable memory.  The pack and unpack kernels read and write such an
@@ -869,6 +925,7 @@ mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double
   mpw_status st = get_patch(c, patch, &P);
   if (st) return st;
   if (!psi || !pi) return set_err(MPW_ERR_ARG, "null field pointer");
+  if ((st = apply_pending_inputs(c))) return st;
   const size_t n = (size_t)P->d.n[0] * P->d.n[1] * P->d.n[2];
   const double *s0 = psi, *s1 = pi;
   const double* a0 = on_device ? nullptr : (const double*)pinned_alias(psi);
@@ -895,6 +952,7 @@ static mpw_status get_impl(mpw_ctx* c, int patch, double* psi, double* pi, int o
   mpw_status st = get_patch(c, patch, &P);
   if (st) return st;
   if (!psi || !pi) return set_err(MPW_ERR_ARG, "null field pointer");
+  if ((st = apply_pending_inputs(c))) return st;
   const int e = padded ? 2 * NG : 0;
   const size_t n = (size_t)(P->d.n[0] + e) * (P->d.n[1] + e) * (P->d.n[2] + e);
   const uint8_t* flags = (patch == 0 && c->flags_valid) ? c->d_flags : nullptr;
@@ -919,6 +977,57 @@ mpw_status mpw_get_fields(mpw_ctx* c, int patch, double* psi, double* pi, int on
   return get_impl(c, patch, psi, pi, on_device, 0);
 }
 
+mpw_status mpw_set_fields_async(mpw_ctx* c, int patch, const double* psi, const double* pi) {
+  PatchState* P;
+  mpw_status st = get_patch(c, patch, &P);
+  if (st) return st;
+  if (!psi || !pi) return set_err(MPW_ERR_ARG, "null field pointer");
+  if (!pinned_alias(psi) || !pinned_alias(pi))
+    return set_err(MPW_ERR_ARG, "asynchronous host transfers need page-locked host arrays");
+  if ((st = ensure_async_io(c, *P))) return st;
+  const size_t n = (size_t)P->d.n[0] * P->d.n[1] * P->d.n[2];
+  // the previous input has left the staging buffer (its unpack ran)
+  CUDA_TRY(cudaStreamWaitEvent(c->io_in, P->in_free, 0));
+  CUDA_TRY(cudaMemcpyAsync(P->io_in, psi, n * sizeof(double), cudaMemcpyHostToDevice, c->io_in));
+  CUDA_TRY(cudaMemcpyAsync(P->io_in + n, pi, n * sizeof(double), cudaMemcpyHostToDevice, c->io_in));
+  CUDA_TRY(cudaEventRecord(P->in_copied, c->io_in));
+  P->in_pending = true;
+  return MPW_OK;
+}
+
+mpw_status mpw_get_fields_async(mpw_ctx* c, int patch, double* psi, double* pi) {
+  PatchState* P;
+  mpw_status st = get_patch(c, patch, &P);
+  if (st) return st;
+  if (!psi || !pi) return set_err(MPW_ERR_ARG, "null field pointer");
+  if (!pinned_alias(psi) || !pinned_alias(pi))
+    return set_err(MPW_ERR_ARG, "asynchronous host transfers need page-locked host arrays");
+  if ((st = ensure_async_io(c, *P))) return st;
+  if ((st = apply_pending_inputs(c))) return st;
+  const size_t n = (size_t)P->d.n[0] * P->d.n[1] * P->d.n[2];
+  const uint8_t* flags = (patch == 0 && c->flags_valid) ? c->d_flags : nullptr;
+  // the previous result has left the staging buffer (its copy ran)
+  CUDA_TRY(cudaStreamWaitEvent(c->stream, P->out_free, 0));
+  launch_pack(P->buf(BUF_U), P->g, P->io_out, P->io_out + n, 0, flags, c->cfg.precision == 32, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaEventRecord(P->out_packed, c->stream));
+  CUDA_TRY(cudaStreamWaitEvent(c->io_out, P->out_packed, 0));
+  CUDA_TRY(cudaMemcpyAsync(psi, P->io_out, n * sizeof(double), cudaMemcpyDeviceToHost, c->io_out));
+  CUDA_TRY(cudaMemcpyAsync(pi, P->io_out + n, n * sizeof(double), cudaMemcpyDeviceToHost, c->io_out));
+  CUDA_TRY(cudaEventRecord(P->out_free, c->io_out));
+  return MPW_OK;
+}
+
+mpw_status mpw_sync(mpw_ctx* c) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  if (use_device(c)) return MPW_ERR_CUDA;
+  if (c->io_in) CUDA_TRY(cudaStreamSynchronize(c->io_in));
+  CUDA_TRY(cudaStreamSynchronize(c->stream));
+  if (c->io_out) CUDA_TRY(cudaStreamSynchronize(c->io_out));
+  return MPW_OK;
+}
+
 mpw_status mpw_get_padded(mpw_ctx* c, int patch, double* psi, double* pi, int on_device) {
   return get_impl(c, patch, psi, pi, on_device, 1);
 }
@@ -937,6 +1046,7 @@ mpw_status mpw_compute_flags(mpw_ctx* c) {
   if (st) return st;
   if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
   if (use_device(c)) return MPW_ERR_CUDA;
+  if ((st = apply_pending_inputs(c))) return st;
   if ((st = run_flags(c, c->t))) return st;
   return read_error_word(c);
 }
@@ -972,6 +1082,7 @@ mpw_status mpw_fill_ghosts(mpw_ctx* c, double t) {
   if (st) return st;
   if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
   if (use_device(c)) return MPW_ERR_CUDA;
+  if ((st = apply_pending_inputs(c))) return st;
   if (!c->flags_valid && (st = run_flags(c, c->t))) return st;
   if ((st = ensure_u_exponents(c))) return st;
   if ((st = run_fill(c, BUF_U, t, -1))) return st;
@@ -1010,6 +1121,7 @@ mpw_status mpw_step(mpw_ctx* c, double dt, int nsteps) {
   if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
   if (nsteps < 0) return set_err(MPW_ERR_ARG, "nsteps must be >= 0");
   if (use_device(c)) return MPW_ERR_CUDA;
+  if ((st = apply_pending_inputs(c))) return st;
   for (int s = 0; s < nsteps; ++s) {
     const double tn = c->t;
     if ((st = step_prologue(c, dt))) return st;
@@ -1179,6 +1291,8 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     if (mpw_status st = check_ctx(c)) return st;
   if (use_device(b->ctx[0])) return MPW_ERR_CUDA;
   mpw_status st;
+  for (mpw_ctx* c : b->ctx)
+    if ((st = apply_pending_inputs(c))) return st;
   const size_t nc = b->cand.size();
   for (int s = 0; s < nsteps; ++s) {
     // chunk depth: the first steps try every candidate, timing the RHS

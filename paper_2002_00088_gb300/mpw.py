@@ -63,6 +63,9 @@ SIGNATURES = {
     "mpw_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
     "mpw_step_periodic_noalloc": (C.c_int, [C.POINTER(C.c_int), _dp, _dp, C.c_double, C.c_double, C.c_int, _vp, _vp,
                                             _vp]),
+    "mpw_set_fields_async": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "mpw_get_fields_async": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "mpw_sync": (C.c_int, [_vp]),
     "mpw_batch_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.POINTER(C.c_void_p)]),
     "mpw_batch_step": (C.c_int, [_vp, _dp, C.c_int]),
     "mpw_batch_tuning": (C.c_int, [_vp, C.POINTER(C.c_int), _dp, C.POINTER(C.c_longlong),
@@ -217,6 +220,26 @@ class Multipatch:
         pi = np.empty(self.shapes[pid])
         check(lib.mpw_get_fields(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp), 0))
         return psi, pi
+
+    def set_fields_async(self, pid, psi, pi):
+        """Queue page-locked host arrays (C-contiguous float64, patch shape) as the
+        new interior; they enter u at the next call that uses u.  Keep them
+        unchanged until sync()."""
+        self._check_host(pid, psi, pi)
+        check(lib.mpw_set_fields_async(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp)))
+
+    def get_fields_async(self, pid, psi, pi):
+        """Copy the interior into page-locked host arrays; valid after sync()."""
+        self._check_host(pid, psi, pi)
+        check(lib.mpw_get_fields_async(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp)))
+
+    def sync(self):
+        check(lib.mpw_sync(self.h))
+
+    def _check_host(self, pid, *arrays):
+        for a in arrays:
+            if a.dtype != np.float64 or not a.flags.c_contiguous or a.shape != tuple(self.shapes[pid]):
+                raise ValueError("host arrays must be C-contiguous float64 of the patch shape")
 
     def get_padded(self, pid):
         s = tuple(v + 2 * NG for v in self.shapes[pid])

@@ -309,6 +309,50 @@ def test_pinned_host_fields_match_pageable(mpw_lib):
         np.testing.assert_array_equal(out[1], ref[1])
 
 
+def test_async_host_io_matches_synchronous(mpw_lib):
+    """Pipelined use of the asynchronous transfers: each step takes a fresh
+    input and returns its result; the bits must equal the synchronous calls."""
+    import torch
+    w = wl.orbiting_gauss(scale=4)
+    rng = np.random.default_rng(5)
+    a = gpu_from(mpw_lib, w)
+    b = gpu_from(mpw_lib, w)
+    a.fill_analytic(0.0)
+    b.fill_analytic(0.0)
+    npatch = len(w.patches)
+    pinned = lambda s: torch.zeros(s, dtype=torch.float64, pin_memory=True).numpy()
+    base = [a.get_fields(q) for q in range(npatch)]
+    inputs = []
+    for k in range(3):
+        step_in = []
+        for q in range(npatch):
+            ps, pi = (np.nan_to_num(x) * (1.0 + 1e-3 * rng.standard_normal(x.shape)) for x in base[q])
+            hp, hq = pinned(ps.shape), pinned(pi.shape)
+            hp[...] = ps
+            hq[...] = pi
+            step_in.append((hp, hq))
+        inputs.append(step_in)
+    outs = [[(pinned(a.shapes[q]), pinned(a.shapes[q])) for q in range(npatch)] for _ in range(3)]
+    for k in range(3):
+        for q in range(npatch):
+            a.set_fields_async(q, *inputs[k][q])
+        a.step(w.dt, 1)
+        for q in range(npatch):
+            a.get_fields_async(q, *outs[k][q])
+    a.sync()
+    for k in range(3):
+        for q in range(npatch):
+            b.set_fields(q, *inputs[k][q])
+        b.step(w.dt, 1)
+        for q in range(npatch):
+            ref = b.get_fields(q)
+            np.testing.assert_array_equal(outs[k][q][0], ref[0])
+            np.testing.assert_array_equal(outs[k][q][1], ref[1])
+    with pytest.raises(mpw_lib.MpwError) as e:
+        a.set_fields_async(0, np.zeros(a.shapes[0]), np.zeros(a.shapes[0]))  # pageable
+    assert e.value.status == 1
+
+
 def test_validation_errors(mpw_lib):
     M = mpw_lib
     w = wl.static_gauss()
