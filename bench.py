@@ -368,7 +368,7 @@ def run_ours(args):
     for k in range(args.e2e_steps):
         for q in range(len(shapes)):
             sim.set_fields_async(q, host[q][0], host[q][1])
-        sim.step(w.dt, 1)
+        sim.step_async(w.dt, 1)
         for q in range(len(shapes)):
             sim.get_fields_async(q, outs[k % 2][q][0], outs[k % 2][q][1])
     sim.sync()

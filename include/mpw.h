@@ -157,7 +157,8 @@ mpw_status mpw_get_fields(mpw_ctx* ctx, int patch, double* psi, double* pi, int 
  *     global cells, as mpw_get_fields) through a device staging buffer; the
  *     host arrays hold it after mpw_sync.  A second get of the same patch
  *     waits on the device for the first to leave the staging buffer.
- *   mpw_sync waits for the context's stream and both copy streams.
+ *   mpw_sync waits for the context's stream and both copy streams, then
+ *     reports device-side errors of earlier mpw_step_async calls.
  * Staging takes 2 x 2 x n0 n1 n2 doubles per patch, allocated on first use. */
 mpw_status mpw_set_fields_async(mpw_ctx* ctx, int patch, const double* psi, const double* pi);
 mpw_status mpw_get_fields_async(mpw_ctx* ctx, int patch, double* psi, double* pi);
@@ -192,6 +193,12 @@ mpw_status mpw_fill_ghosts(mpw_ctx* ctx, double t);
  * error word once at the end.  On a device-side error the call returns
  * MPW_ERR_GHOST_UNFILLED or MPW_ERR_BOUNDS. */
 mpw_status mpw_step(mpw_ctx* ctx, double dt, int nsteps);
+
+/* As mpw_step, but returns once the work is enqueued: the device error word
+ * is read by the next mpw_sync (or mpw_step) instead, so the host can queue
+ * the next step's transfers while this one computes.  Host-side validation
+ * errors are still returned at once. */
+mpw_status mpw_step_async(mpw_ctx* ctx, double dt, int nsteps);
 
 /* ---- Batches: many independent multipatch instances advanced together.
  * The paper has no counterpart (it runs one instance per set of MPI ranks);

@@ -1025,7 +1025,7 @@ mpw_status mpw_sync(mpw_ctx* c) {
   if (c->io_in) CUDA_TRY(cudaStreamSynchronize(c->io_in));
   CUDA_TRY(cudaStreamSynchronize(c->stream));
   if (c->io_out) CUDA_TRY(cudaStreamSynchronize(c->io_out));
-  return MPW_OK;
+  return read_error_word(c);  // device-side errors of mpw_step_async calls
 }
 
 mpw_status mpw_get_padded(mpw_ctx* c, int patch, double* psi, double* pi, int on_device) {
@@ -1115,7 +1115,13 @@ mpw_status step_prologue(mpw_ctx* c, double dt) {
 
 extern "C" {
 
-mpw_status mpw_step(mpw_ctx* c, double dt, int nsteps) {
+static mpw_status step_impl(mpw_ctx* c, double dt, int nsteps, bool check_errors);
+
+mpw_status mpw_step(mpw_ctx* c, double dt, int nsteps) { return step_impl(c, dt, nsteps, true); }
+
+mpw_status mpw_step_async(mpw_ctx* c, double dt, int nsteps) { return step_impl(c, dt, nsteps, false); }
+
+static mpw_status step_impl(mpw_ctx* c, double dt, int nsteps, bool check_errors) {
   mpw_status st = check_ctx(c);
   if (st) return st;
   if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
@@ -1135,7 +1141,7 @@ mpw_status mpw_step(mpw_ctx* c, double dt, int nsteps) {
     c->t = tn + dt;
     c->stepped = true;
   }
-  return read_error_word(c);
+  return check_errors ? read_error_word(c) : MPW_OK;
 }
 
 mpw_status mpw_live_points(mpw_ctx* c, long long* count) {

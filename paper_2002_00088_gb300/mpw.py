@@ -63,6 +63,7 @@ SIGNATURES = {
     "mpw_profile_read": (C.c_int, [_vp, _dp, C.POINTER(C.c_longlong), C.c_int]),
     "mpw_step_periodic_noalloc": (C.c_int, [C.POINTER(C.c_int), _dp, _dp, C.c_double, C.c_double, C.c_int, _vp, _vp,
                                             _vp]),
+    "mpw_step_async": (C.c_int, [_vp, C.c_double, C.c_int]),
     "mpw_set_fields_async": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "mpw_get_fields_async": (C.c_int, [_vp, C.c_int, _vp, _vp]),
     "mpw_sync": (C.c_int, [_vp]),
@@ -232,6 +233,10 @@ class Multipatch:
         """Copy the interior into page-locked host arrays; valid after sync()."""
         self._check_host(pid, psi, pi)
         check(lib.mpw_get_fields_async(self.h, pid, psi.ctypes.data_as(_vp), pi.ctypes.data_as(_vp)))
+
+    def step_async(self, dt, nsteps=1):
+        """Enqueue the steps and return; device errors surface at sync()."""
+        check(lib.mpw_step_async(self.h, float(dt), int(nsteps)))
 
     def sync(self):
         check(lib.mpw_sync(self.h))

@@ -336,7 +336,7 @@ def test_async_host_io_matches_synchronous(mpw_lib):
     for k in range(3):
         for q in range(npatch):
             a.set_fields_async(q, *inputs[k][q])
-        a.step(w.dt, 1)
+        a.step_async(w.dt, 1)
         for q in range(npatch):
             a.get_fields_async(q, *outs[k][q])
     a.sync()
