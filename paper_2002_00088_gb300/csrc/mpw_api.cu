@@ -794,22 +794,26 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
   const size_t bytes = P.esize * 8 * (size_t)P.g.vol;
   P.base = (double*)c->dalloc(bytes);
   if (!P.base) return set_err(MPW_ERR_CUDA, "allocation of %zu bytes failed", bytes);
-  CUDA_TRY(cudaMemsetAsync(P.base, 0, bytes, c->stream));
-  for (int b = 0; b < 4; ++b)
-    if (!encode_rhs_map(&P.tile_map[b], P.buf(b), P.g, true, f32)) {
-      c->dfree(P.base);
-      return set_err(MPW_ERR_CUDA, "tensor map encoding failed");
-    }
-  if (!encode_rhs_map(&P.point_map[0], P.buf(BUF_U), P.g, false, f32) ||
-      !encode_rhs_map(&P.point_map[1], P.buf(BUF_ACC), P.g, false, f32)) {
+  // every failure below frees what this call allocated
+  auto undo = [&](const char* msg) {
     c->dfree(P.base);
-    return set_err(MPW_ERR_CUDA, "tensor map encoding failed");
-  }
+    return set_err(MPW_ERR_CUDA, "%s", msg);
+  };
+  if (cudaMemsetAsync(P.base, 0, bytes, c->stream) != cudaSuccess) return undo("memset of the new patch failed");
+  for (int b = 0; b < 4; ++b)
+    if (!encode_rhs_map(&P.tile_map[b], P.buf(b), P.g, true, f32)) return undo("tensor map encoding failed");
+  if (!encode_rhs_map(&P.point_map[0], P.buf(BUF_U), P.g, false, f32) ||
+      !encode_rhs_map(&P.point_map[1], P.buf(BUF_ACC), P.g, false, f32))
+    return undo("tensor map encoding failed");
   if (d->kind == MPW_PATCH_GLOBAL) {
     const size_t nb = (size_t)d->n[0] * d->n[1] * d->n[2];
     c->d_flags = (uint8_t*)c->dalloc(nb);
-    if (!c->d_flags) return set_err(MPW_ERR_CUDA, "flag allocation failed");
-    CUDA_TRY(cudaMemsetAsync(c->d_flags, 0, nb, c->stream));
+    if (!c->d_flags) return undo("flag allocation failed");
+    if (cudaMemsetAsync(c->d_flags, 0, nb, c->stream) != cudaSuccess) {
+      c->dfree(c->d_flags);
+      c->d_flags = nullptr;
+      return undo("memset of the cover flags failed");
+    }
   }
   c->p.push_back(P);
   c->flags_valid = false;

@@ -426,15 +426,16 @@ __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs_batch(const RhsA
 
 // Host: TMA maps of one field buffer (4-D: x, y, plane, field).
 bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile, bool f32) {
-  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-  if (!encode) {
+  // looked up once (thread-safe initialisation of a function-local static)
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
     cudaDriverEntryPointQueryResult q;
     void* fn = nullptr;
     if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return false;
-    encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-  }
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
   const cuuint64_t dims[4] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)(g.n[2] + 2 * NG), 2};
   const cuuint64_t es = f32 ? 4 : 8;
   const cuuint64_t strides[3] = {(cuuint64_t)g.px * es, (cuuint64_t)g.plane * es, (cuuint64_t)g.vol * es};
