@@ -88,15 +88,24 @@ static int is_live(const orc_sim* s, int pi, int i, int j, int k) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Patch motion.  Local patches are rigidly translated: X_B = X' + X0(t), and
- * w = dX0/dt is the frame velocity entering the RHS.
+/* Patch motion.  Local patches move rigidly: X_B = R(t) X' + X0(t).  Under
+ * translation R = I and w = dX0/dt is the frame velocity entering the RHS.
  *   STATIC   : X0 = (p0, p1, p2)
  *   LINEAR   : X0 = (p0, p1, p2) + t (p3, p4, p5)
  *   CIRCULAR : X0 = (p0, p1, p2) + p3 (cos(p4 t + p5), sin(p4 t + p5), 0)
- * (centre, radius, angular speed, phase; orbit in the z = p2 plane). */
+ *              (centre, radius, angular speed, phase; orbit in the z = p2 plane)
+ *   ROTATING : X0 = (p0, p1, p2) + t (p3, p4, p5), and R(t) the rotation by
+ *              theta = p9 t + p10 about the unit axis n = (p6, p7, p8), see
+ *              orc_frame (the rotating local patch of Sec. 3.2, Test Two);
+ *              orc_motion returns X0 and the frame velocity at X' = 0. */
 void orc_motion(int motion, const double* mp, double t, double X0[3], double w[3]) {
   int a;
-  if (motion == ORC_LINEAR) {
+  if (motion == ORC_ROTATING) {
+    const double zero[3] = {0.0, 0.0, 0.0};
+    double R[9];
+    orc_frame(motion, mp, t, R, X0);
+    orc_frame_velocity(motion, mp, t, zero, w);
+  } else if (motion == ORC_LINEAR) {
     for (a = 0; a < 3; ++a) {
       X0[a] = mp[a] + t * mp[3 + a];
       w[a] = mp[3 + a];
@@ -116,6 +125,71 @@ void orc_motion(int motion, const double* mp, double t, double X0[3], double w[3
       w[a] = 0.0;
     }
   }
+}
+
+/* Rotation about the unit axis n by theta, right-handed (counter-clockwise
+ * seen from the tip of n), by Rodrigues' formula
+ *   R = cos(theta) I + sin(theta) [n]_x + (1 - cos(theta)) n n^T,
+ * [n]_x the cross-product matrix ([n]_x v = n x v).  For n = z this is the
+ * rotation of the x-y plane by theta.  The entries are formed in a fixed
+ * order: the cover flags depend on their last bit. */
+void orc_frame(int motion, const double* mp, double t, double R[9], double X0[3]) {
+  if (motion != ORC_ROTATING) {
+    double w[3];
+    orc_motion(motion, mp, t, X0, w);
+    for (int e = 0; e < 9; ++e) R[e] = (e % 4 == 0) ? 1.0 : 0.0;
+    return;
+  }
+  const double* n = mp + 6;
+  const double th = mp[9] * t + mp[10];
+  const double c = cos(th), sn = sin(th), omc = 1.0 - c;
+  const double K[9] = {0.0, -n[2], n[1], n[2], 0.0, -n[0], -n[1], n[0], 0.0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) R[3 * a + b] = ((a == b ? c : 0.0) + sn * K[3 * a + b]) + (omc * n[a]) * n[b];
+  for (int a = 0; a < 3; ++a) X0[a] = mp[a] + t * mp[3 + a];
+}
+
+/* Frame velocity at the patch point X' in patch components: the background
+ * velocity of the moving node, dX_B/dt = Omega n x (R X') + V, taken back to
+ * the patch frame, w = R^T dX_B/dt = Omega n x X' + R^T V (R^T n = n). */
+void orc_frame_velocity(int motion, const double* mp, double t, const double xl[3], double w[3]) {
+  double R[9], X0[3];
+  if (motion != ORC_ROTATING) {
+    orc_motion(motion, mp, t, X0, w);
+    return;
+  }
+  orc_frame(motion, mp, t, R, X0);
+  const double* n = mp + 6;
+  const double om = mp[9];
+  const double cr[3] = {n[1] * xl[2] - n[2] * xl[1], n[2] * xl[0] - n[0] * xl[2], n[0] * xl[1] - n[1] * xl[0]};
+  for (int a = 0; a < 3; ++a) w[a] = om * cr[a] + (R[a] * mp[3] + R[3 + a] * mp[4] + R[6 + a] * mp[5]);
+}
+
+/* The map of one patch at one time, and the two directions of it. */
+typedef struct {
+  int rot;
+  double R[9], X0[3];
+} oframe;
+
+static oframe frame_at(const opatch* p, double t) {
+  oframe f;
+  f.rot = p->d.motion == ORC_ROTATING;
+  orc_frame(p->d.motion, p->d.motion_params, t, f.R, f.X0);
+  return f;
+}
+
+/* X_B = R X' + X0 (translation: X' + X0) */
+static void to_background(const oframe* f, const double xl[3], double xb[3]) {
+  for (int a = 0; a < 3; ++a)
+    xb[a] = f->rot ? ((f->R[3 * a] * xl[0] + f->R[3 * a + 1] * xl[1]) + f->R[3 * a + 2] * xl[2]) + f->X0[a]
+                   : xl[a] + f->X0[a];
+}
+
+/* X' = R^T (X_B - X0) (translation: X_B - X0) */
+static void to_local(const oframe* f, const double xb[3], double xl[3]) {
+  const double d[3] = {xb[0] - f->X0[0], xb[1] - f->X0[1], xb[2] - f->X0[2]};
+  for (int a = 0; a < 3; ++a)
+    xl[a] = f->rot ? (f->R[a] * d[0] + f->R[3 + a] * d[1]) + f->R[6 + a] * d[2] : d[a];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -272,6 +346,12 @@ int orc_add_patch(orc_sim* s, const orc_patch_desc* d) {
     return fail(s, ORC_ERR_ARG, "patch 0 must be the single global patch");
   for (int a = 0; a < 3; ++a)
     if (d->n[a] < 2 * NG || !(d->hi[a] > d->lo[a])) return fail(s, ORC_ERR_ARG, "bad extent");
+  if (d->motion < ORC_STATIC || d->motion > ORC_ROTATING) return fail(s, ORC_ERR_ARG, "bad motion law");
+  if (d->motion == ORC_ROTATING) {
+    const double* n = d->motion_params + 6;
+    if (fabs(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] - 1.0) > 1e-12)
+      return fail(s, ORC_ERR_ARG, "the rotation axis must be a unit vector");
+  }
   opatch* p = &s->p[s->np];
   memset(p, 0, sizeof *p);
   p->d = *d;
@@ -313,14 +393,14 @@ double orc_time(const orc_sim* s) { return s->t; }
 int orc_fill_analytic(orc_sim* s, double t) {
   for (int q = 0; q < s->np; ++q) {
     opatch* p = &s->p[q];
-    double X0[3], w[3];
-    orc_motion(p->d.motion, p->d.motion_params, t, X0, w);
+    oframe f = frame_at(p, t);
     for (int k = 0; k < p->d.n[2]; ++k)
       for (int j = 0; j < p->d.n[1]; ++j)
         for (int i = 0; i < p->d.n[0]; ++i) {
           long c = at(p, i, j, k);
-          orc_closed_form(s->akind, s->ap, s->acount, t, node(p, 0, i) + X0[0], node(p, 1, j) + X0[1],
-                          node(p, 2, k) + X0[2], &p->U[0][c], &p->U[1][c]);
+          double xl[3] = {node(p, 0, i), node(p, 1, j), node(p, 2, k)}, xb[3];
+          to_background(&f, xl, xb);
+          orc_closed_form(s->akind, s->ap, s->acount, t, xb[0], xb[1], xb[2], &p->U[0][c], &p->U[1][c]);
         }
   }
   s->t = t;
@@ -466,17 +546,14 @@ int orc_compute_flags(orc_sim* s) {
   /* coverage test in each local patch's numeric coordinates */
   for (int q = 1; q < s->np && rc == 0; ++q) {
     opatch* p = &s->p[q];
-    double X0[3], w[3];
-    orc_motion(p->d.motion, p->d.motion_params, s->t, X0, w);
+    oframe f = frame_at(p, s->t);
     for (int k = 0; k < g->d.n[2] && rc == 0; ++k)
       for (int j = 0; j < g->d.n[1] && rc == 0; ++j)
         for (int i = 0; i < g->d.n[0]; ++i) {
-          double xb[3] = {node(g, 0, i), node(g, 1, j), node(g, 2, k)};
+          double xb[3] = {node(g, 0, i), node(g, 1, j), node(g, 2, k)}, xl[3];
           int inside = 1;
-          for (int a = 0; a < 3; ++a) {
-            double xl = xb[a] - X0[a];
-            inside = inside && (p->d.lo[a] <= xl) && (xl <= p->d.hi[a]);
-          }
+          to_local(&f, xb, xl);
+          for (int a = 0; a < 3; ++a) inside = inside && (p->d.lo[a] <= xl[a]) && (xl[a] <= p->d.hi[a]);
           if (!inside) continue;
           long c = gidx(g, i, j, k);
           if (owner[c]) {
@@ -512,13 +589,13 @@ int orc_compute_flags(orc_sim* s) {
           g->U[1][c] = NAN;
         } else if ((f & 3) == ORC_REVIVED) {
           int q = f >> 2;
-          double X0[3], w[3], x[3], v[2];
+          double xb[3] = {node(g, 0, i), node(g, 1, j), node(g, 2, k)}, x[3], v[2];
           if (q < 1 || q >= s->np) {
             rc = fail(s, ORC_ERR_UNFILLED, "revived cell without owner");
             continue;
           }
-          orc_motion(s->p[q].d.motion, s->p[q].d.motion_params, s->t, X0, w);
-          for (int a = 0; a < 3; ++a) x[a] = node(g, a, a == 0 ? i : a == 1 ? j : k) - X0[a];
+          oframe fq = frame_at(&s->p[q], s->t);
+          to_local(&fq, xb, x);
           if (interp_point(s, q, s->p[q].U, x, v) != 0) {
             rc = fail(s, ORC_ERR_UNFILLED, "revived cell (%d,%d,%d) not interpolable", i, j, k);
             continue;
@@ -592,11 +669,9 @@ static void fill_l2g(orc_sim* s, double t, const double Xg[3], long* unfilled_, 
         unsigned char f = s->flags[gidx(g, i, j, k)];
         if ((f & 3) != ORC_GHOST) continue;
         int q = f >> 2;
-        double X0[3], w[3], x[3], v[2];
-        orc_motion(s->p[q].d.motion, s->p[q].d.motion_params, t, X0, w);
-        x[0] = node(g, 0, i) + Xg[0] - X0[0];
-        x[1] = node(g, 1, j) + Xg[1] - X0[1];
-        x[2] = node(g, 2, k) + Xg[2] - X0[2];
+        double xb[3] = {node(g, 0, i) + Xg[0], node(g, 1, j) + Xg[1], node(g, 2, k) + Xg[2]}, x[3], v[2];
+        oframe fq = frame_at(&s->p[q], t);
+        to_local(&fq, xb, x);
         int r = interp_point(s, q, s->p[q].Y, x, v);
         if (r == -1) ++unfilled;
         if (r == -2) ++bad_donor;
@@ -617,17 +692,17 @@ static void fill_g2l(orc_sim* s, double t, const double Xg[3], long* unfilled_, 
   long unfilled = 0, bad_donor = 0;
   for (int q = 1; q < s->np; ++q) {
     opatch* p = &s->p[q];
-    double X0[3], w[3];
-    orc_motion(p->d.motion, p->d.motion_params, t, X0, w);
+    oframe f = frame_at(p, t);
 #pragma omp parallel for schedule(dynamic) reduction(+ : unfilled, bad_donor) num_threads(s->nthreads)
     for (int k = -NG; k < p->d.n[2] + NG; ++k)
       for (int j = -NG; j < p->d.n[1] + NG; ++j)
         for (int i = -NG; i < p->d.n[0] + NG; ++i) {
           if (in_interior(p, i, j, k)) continue;
-          double x[3], v[2];
-          x[0] = node(p, 0, i) + X0[0] - Xg[0];
-          x[1] = node(p, 1, j) + X0[1] - Xg[1];
-          x[2] = node(p, 2, k) + X0[2] - Xg[2];
+          double xl[3] = {node(p, 0, i), node(p, 1, j), node(p, 2, k)}, xb[3], x[3], v[2];
+          to_background(&f, xl, xb);
+          x[0] = xb[0] - Xg[0];
+          x[1] = xb[1] - Xg[1];
+          x[2] = xb[2] - Xg[2];
           int r = interp_point(s, 0, g->Y, x, v);
           if (r == -1) ++unfilled;
           if (r == -2) ++bad_donor;
@@ -686,8 +761,11 @@ int orc_fill_ghosts(orc_sim* s, double t) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Right-hand side (Sec. 2.2, Eqs. eom1-eom3, in a rigidly translating frame
- * of velocity w with Pi the background-frame time derivative of psi):
+/* Right-hand side (Sec. 2.2, Eqs. eom1-eom3, in a rigidly moving frame with
+ * Pi the background-frame time derivative of psi; w is the frame velocity at
+ * the point, constant under translation, w(X') = Omega n x X' + R^T V in a
+ * rotating frame, where the Laplacian keeps its form because R is
+ * orthogonal):
  *   K_psi = Pi + w . D1 psi + KO(psi)
  *   K_Pi  = sum_a D2_a psi + w . D1 Pi + KO(Pi)
  * 4th-order centred differences along each axis with spacing h:
@@ -711,8 +789,9 @@ static double fd_ko(const double* u, long st, double h, double eps) {
 
 static void rhs(orc_sim* s, int q, double t, double* const Y[2], double* Kpsi, double* Kpi) {
   opatch* p = &s->p[q];
-  double X0[3], w[3];
-  orc_motion(p->d.motion, p->d.motion_params, t, X0, w);
+  double X0[3], w0[3];
+  orc_motion(p->d.motion, p->d.motion_params, t, X0, w0);
+  const int rot = p->d.motion == ORC_ROTATING;
   long st[3] = {1, p->m[0], (long)p->m[0] * p->m[1]};
 #pragma omp parallel for schedule(static) num_threads(s->nthreads)
   for (int k = 0; k < p->d.n[2]; ++k)
@@ -726,6 +805,11 @@ static void rhs(orc_sim* s, int q, double t, double* const Y[2], double* Kpsi, d
         }
         const double* ps = Y[0] + c;
         const double* pv = Y[1] + c;
+        double w[3] = {w0[0], w0[1], w0[2]};
+        if (rot) {
+          const double xl[3] = {node(p, 0, i), node(p, 1, j), node(p, 2, k)};
+          orc_frame_velocity(p->d.motion, p->d.motion_params, t, xl, w);
+        }
         double kps = pv[0], kpi = 0.0;
         for (int a = 0; a < 3; ++a) {
           kps += w[a] * fd_d1(ps, st[a], p->h[a]) + fd_ko(ps, st[a], p->h[a], s->eps);

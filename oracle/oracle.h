@@ -45,7 +45,7 @@ extern "C" {
 
 enum { ORC_GLOBAL = 0, ORC_LOCAL = 1 };
 enum { ORC_BC_ANALYTIC = 0, ORC_BC_PERIODIC = 1, ORC_BC_INTERPATCH = 2 };
-enum { ORC_STATIC = 0, ORC_LINEAR = 1, ORC_CIRCULAR = 2 };
+enum { ORC_STATIC = 0, ORC_LINEAR = 1, ORC_CIRCULAR = 2, ORC_ROTATING = 3 };
 enum { ORC_GAUSS_SUM = 0, ORC_PLANE_SUM = 1, ORC_HARMONIC_POLY = 2, ORC_PLANE_GAUSS = 3 };
 /* flag byte of a global interior cell: state | (owning local patch << 2) */
 enum { ORC_LIVE = 0, ORC_GHOST = 1, ORC_DEAD = 2, ORC_REVIVED = 3 };
@@ -63,8 +63,8 @@ typedef struct {
   int n[3];                 /* interior cells per axis */
   double lo[3], hi[3];      /* numeric-coordinate extent of the live box */
   int outer_bc;             /* global: ANALYTIC or PERIODIC; local: INTERPATCH */
-  int motion;               /* ORC_STATIC / ORC_LINEAR / ORC_CIRCULAR */
-  double motion_params[16]; /* see orc_motion() */
+  int motion;               /* ORC_STATIC / ORC_LINEAR / ORC_CIRCULAR / ORC_ROTATING */
+  double motion_params[16]; /* see orc_motion() and orc_frame() */
 } orc_patch_desc;
 
 typedef struct orc_sim orc_sim;
@@ -99,6 +99,11 @@ double orc_energy(const orc_sim* s, int patch);
 
 /* building blocks, exposed for the pins */
 void orc_motion(int motion, const double* mp, double t, double X0[3], double w[3]);
+/* map of a patch at time t: X_B = R X' + X0, R row-major (identity unless
+ * ORC_ROTATING) */
+void orc_frame(int motion, const double* mp, double t, double R[9], double X0[3]);
+/* frame velocity w (patch components) at the patch point X' */
+void orc_frame_velocity(int motion, const double* mp, double t, const double xl[3], double w[3]);
 int orc_lagrange(int P, double s, double* w);      /* returns the window start index */
 void orc_closed_form(int kind, const double* params, int count, double t,
                      double x, double y, double z, double* psi, double* pi);

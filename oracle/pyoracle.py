@@ -7,7 +7,7 @@ from . import LIB_PATH, build_oracle
 
 GLOBAL, LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
-STATIC, LINEAR, CIRCULAR = 0, 1, 2
+STATIC, LINEAR, CIRCULAR, ROTATING = 0, 1, 2, 3
 GAUSS_SUM, PLANE_SUM, HARMONIC_POLY, PLANE_GAUSS = 0, 1, 2, 3
 LIVE, GHOST, DEAD, REVIVED = 0, 1, 2, 3
 NG = 3
@@ -56,6 +56,8 @@ def lib():
         L.orc_energy.restype = C.c_double
         L.orc_energy.argtypes = [vp, C.c_int]
         L.orc_motion.argtypes = [C.c_int, dp, C.c_double, dp, dp]
+        L.orc_frame.argtypes = [C.c_int, dp, C.c_double, dp, dp]
+        L.orc_frame_velocity.argtypes = [C.c_int, dp, C.c_double, dp, dp]
         L.orc_lagrange.restype = C.c_int
         L.orc_lagrange.argtypes = [C.c_int, C.c_double, dp]
         L.orc_closed_form.argtypes = [C.c_int, dp, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double, dp, dp]
@@ -88,6 +90,26 @@ def motion(kind, params, t):
     w = np.zeros(3)
     lib().orc_motion(kind, _dp(p), float(t), _dp(X0), _dp(w))
     return X0, w
+
+
+def frame(kind, params, t):
+    """(R, X0) of the patch map X_B = R X' + X0 at time t."""
+    p = np.zeros(16)
+    p[:len(params)] = params
+    R = np.zeros(9)
+    X0 = np.zeros(3)
+    lib().orc_frame(kind, _dp(p), float(t), _dp(R), _dp(X0))
+    return R.reshape(3, 3), X0
+
+
+def frame_velocity(kind, params, t, xl):
+    """Frame velocity (patch components) at the patch point xl."""
+    p = np.zeros(16)
+    p[:len(params)] = params
+    x = np.ascontiguousarray(xl, dtype=np.float64)
+    w = np.zeros(3)
+    lib().orc_frame_velocity(kind, _dp(p), float(t), _dp(x), _dp(w))
+    return w
 
 
 def lagrange(P, s):

@@ -21,6 +21,13 @@ Gaussian-pulse closed forms:
   angular speed 2 pi in the planes z = +-0.3 (pairs opposite in phase, pair
   phases seeded), eight Gaussians (amplitudes N(0,1), widths U[0.05,0.2],
   centres U[-1,1]^3), 6-point Lagrange, CFL 0.25, 200 steps.
+* ``spinning_gauss`` -- the rotating-patch configuration: global 256^3 plus
+  four local 96^3 cubes (half-width 3/16, 2x resolution) centred at
+  (+-0.45, +-0.45, 0), each spinning about its centre around a seeded unit
+  axis at angular speed pi (seeded sign and phase); eight Gaussians as in
+  ``orbiting_gauss``; 200 steps.
+* ``rotating_plane`` -- the rotating local patch of Sec. 3.2 (Test Two) at
+  reduced size, for the convergence pin and the small parity cases.
 """
 from dataclasses import dataclass, field
 from typing import List, Tuple
@@ -31,7 +38,7 @@ SEED_BASE = 20020088
 
 GLOBAL, LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
-STATIC, LINEAR, CIRCULAR = 0, 1, 2
+STATIC, LINEAR, CIRCULAR, ROTATING = 0, 1, 2, 3
 GAUSS_SUM, PLANE_SUM, HARMONIC_POLY, PLANE_GAUSS = 0, 1, 2, 3
 
 
@@ -103,6 +110,56 @@ def orbiting_gauss(scale=1, steps=200, interp_points=6, seed_index=1, radius=0.4
     h_min = 2.0 * half_width / nl
     return Workload(f"orbiting_gauss_{ng}+4x{nl}", patches, GAUSS_SUM, params, 8, interp_points, 0.005,
                     0.25 * h_min, steps)
+
+
+def spinning_gauss(scale=1, steps=200, interp_points=6, seed_index=4, centre=0.45, omega=np.pi,
+                   half_width=0.1875):
+    """Global 256^3/scale + four local 96^3/scale cubes spinning in place
+    (ROTATING motion: centre fixed, seeded unit axis, angular speed +-omega,
+    seeded phase).  The rotated cubes keep an L-infinity gap of >= 0.1 between
+    their bounding boxes and stay >= 0.05 inside the global box at every
+    angle for scale 1 and 2."""
+    r = rng(seed_index)
+    axes = r.normal(0.0, 1.0, (4, 3))
+    axes /= np.linalg.norm(axes, axis=1, keepdims=True)
+    signs = np.where(r.uniform(0.0, 1.0, 4) < 0.5, -1.0, 1.0)
+    phases = r.uniform(0.0, 2.0 * np.pi, 4)
+    amps = r.normal(0.0, 1.0, 8)
+    widths = r.uniform(0.05, 0.2, 8)
+    centres = r.uniform(-1.0, 1.0, (8, 3))
+    ng, nl = 256 // scale, 96 // scale
+    patches = [PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC)]
+    for q, (cx, cy) in enumerate(((centre, centre), (-centre, centre), (-centre, -centre), (centre, -centre))):
+        patches.append(PatchSpec(LOCAL, (nl, nl, nl), (-half_width,) * 3, (half_width,) * 3, BC_INTERPATCH,
+                                 ROTATING, (cx, cy, 0.0, 0.0, 0.0, 0.0, axes[q, 0], axes[q, 1], axes[q, 2],
+                                            signs[q] * omega, phases[q])))
+    params = np.column_stack([amps, widths, centres]).ravel()
+    h_min = 2.0 * half_width / nl
+    return Workload(f"spinning_gauss_{ng}+4x{nl}", patches, GAUSS_SUM, params, 8, interp_points, 0.005,
+                    0.25 * h_min, steps)
+
+
+def rotating_plane(scale=1, steps=16, interp_points=6, omega=2.0 * np.pi, axis=(0.0, 0.0, 1.0), half_width=0.3,
+                   nl=20, phase=0.0, velocity=(0.0, 0.0, 0.0)):
+    """Sec. 3.2's rotating local patch (Test Two) at reduced size: global
+    cube [-1,1]^3 at 32 scale cells per axis and a local cube of the given
+    half-width (nl scale cells) whose centre sits at the global origin (or
+    moves with the given velocity) and which turns counter-clockwise about
+    the unit axis at angular speed omega; the two-wave superposition of
+    ``translating_plane`` with analytic outer BCs."""
+    ng, nl = 32 * scale, nl * scale
+    ax = np.asarray(axis, dtype=np.float64)
+    ax = ax / np.linalg.norm(ax)
+    patches = [
+        PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC),
+        PatchSpec(LOCAL, (nl, nl, nl), (-half_width,) * 3, (half_width,) * 3, BC_INTERPATCH, ROTATING,
+                  (0.0, 0.0, 0.0) + tuple(velocity) + tuple(ax) + (omega, phase)),
+    ]
+    k = 2.0 * np.pi / 2.0
+    params = np.array([3.0, 1.0, k, 0.0, 0.0, 0.0, 1.0, k, -k, k, 0.5 * np.pi])
+    h_min = 2.0 * half_width / nl
+    return Workload(f"rotating_plane_{ng}+{nl}", patches, PLANE_SUM, params, 2, interp_points, 0.005,
+                    0.25 * h_min, steps * scale)
 
 
 def plane_gauss(scale=1, steps=200, interp_points=6, seed_index=2):
