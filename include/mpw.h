@@ -58,7 +58,7 @@ typedef enum {
 
 enum { MPW_PATCH_GLOBAL = 0, MPW_PATCH_LOCAL = 1 };
 enum { MPW_BC_ANALYTIC = 0, MPW_BC_PERIODIC = 1, MPW_BC_INTERPATCH = 2 };
-enum { MPW_MOTION_STATIC = 0, MPW_MOTION_LINEAR = 1, MPW_MOTION_CIRCULAR = 2 };
+enum { MPW_MOTION_STATIC = 0, MPW_MOTION_LINEAR = 1, MPW_MOTION_CIRCULAR = 2, MPW_MOTION_ROTATING = 3 };
 enum {
   MPW_ANALYTIC_GAUSS_SUM = 0,
   MPW_ANALYTIC_PLANE_SUM = 1,
@@ -102,9 +102,20 @@ typedef struct {
   int outer_bc;             /* global: ANALYTIC or PERIODIC; local: INTERPATCH */
   int motion;               /* MPW_MOTION_*; the global patch must be STATIC at the origin
                                when local patches exist */
-  double motion_params[16]; /* STATIC   : X0 = (p0,p1,p2)
+  double motion_params[16]; /* The map to the background frame is X_B = R(t) X' + X0(t) with
+                               R = I except for ROTATING (Sec. 2.4, numeric -> background):
+                               STATIC   : X0 = (p0,p1,p2)
                                LINEAR   : X0 = (p0,p1,p2) + t (p3,p4,p5)
-                               CIRCULAR : X0 = (p0,p1,p2) + p3 (cos(p4 t + p5), sin(p4 t + p5), 0) */
+                               CIRCULAR : X0 = (p0,p1,p2) + p3 (cos(p4 t + p5), sin(p4 t + p5), 0)
+                               ROTATING : X0 = (p0,p1,p2) + t (p3,p4,p5) and R the rotation by
+                                          theta = p9 t + p10 about the unit axis (p6,p7,p8),
+                                          counter-clockwise seen from the axis tip (Rodrigues'
+                                          formula); the rotating local patch of Sec. 3.2.  The
+                                          axis must have unit length (within 1e-12).  The frame
+                                          velocity entering the RHS is then position dependent,
+                                          w(X') = p9 n x X' + R^T (p3,p4,p5).  Validation of a
+                                          rotating patch (overlap, distance to the global faces)
+                                          uses the bounding box of its rotated box. */
 } mpw_patch_desc;
 
 /* Create a context on cfg->device.  cfg is copied.  Errors: MPW_ERR_ARG for

@@ -88,6 +88,8 @@ struct mpw_ctx {
   int* h_err = nullptr;
   int* d_expo = nullptr;  // [patch][buffer][field] maximum biased exponent
   long long* d_rev = nullptr;  // queue of revived cells (REVIVE_CAP entries); its length lives in d_err[32]
+  uint8_t* d_cov = nullptr;    // covered masks of the rotating patches' bounding boxes
+  size_t cov_bytes = 0;
   // Time whose closed form each global buffer's outer shell holds (NaN: none).
   // The RK4 substage times repeat (c = 0, 1/2, 1/2, 1, and t_n + dt starts the
   // next step), so half of the analytic shell evaluations become copies.
@@ -139,11 +141,19 @@ struct mpw_ctx {
 
 namespace {
 
-// Rigid translation of a patch: X_B = X' + X0(t); w = dX0/dt.  The rounding
-// order is fixed (no contraction) because the cover flags depend on it.
+void rotation(const mpw_patch_desc& d, double t, double R[9]);
+
+// Rigid motion of a patch: X_B = R(t) X' + X0(t), R = I except for ROTATING;
+// w = R^T dX0/dt is the frame velocity at X' = 0.  The rounding order is
+// fixed (no contraction) because the cover flags depend on it.
 void motion(const mpw_patch_desc& d, double t, double X0[3], double w[3]) {
   const double* mp = d.motion_params;
-  if (d.motion == MPW_MOTION_LINEAR) {
+  if (d.motion == MPW_MOTION_ROTATING) {
+    double R[9];
+    rotation(d, t, R);
+    for (int a = 0; a < 3; ++a) X0[a] = mp[a] + t * mp[3 + a];
+    for (int a = 0; a < 3; ++a) w[a] = R[a] * mp[3] + R[3 + a] * mp[4] + R[6 + a] * mp[5];
+  } else if (d.motion == MPW_MOTION_LINEAR) {
     for (int a = 0; a < 3; ++a) {
       X0[a] = mp[a] + t * mp[3 + a];
       w[a] = mp[3 + a];
@@ -165,13 +175,109 @@ void motion(const mpw_patch_desc& d, double t, double X0[3], double w[3]) {
   }
 }
 
-// Largest |w_a| the motion law can reach.
+// Rotation by theta = p9 t + p10 about the unit axis n = (p6, p7, p8)
+// (Rodrigues: R = cos I + sin [n]_x + (1 - cos) n n^T, row-major), the
+// entries formed in a fixed order: the cover flags depend on their last bit.
+void rotation(const mpw_patch_desc& d, double t, double R[9]) {
+  const double* mp = d.motion_params;
+  const double* n = mp + 6;
+  const double th = mp[9] * t + mp[10];
+  const double c = std::cos(th), sn = std::sin(th), omc = 1.0 - c;
+  const double K[9] = {0.0, -n[2], n[1], n[2], 0.0, -n[0], -n[1], n[0], 0.0};
+  for (int a = 0; a < 3; ++a)
+    for (int b = 0; b < 3; ++b) R[3 * a + b] = ((a == b ? c : 0.0) + sn * K[3 * a + b]) + (omc * n[a]) * n[b];
+}
+
+// Map of a patch at time t and its frame velocity as an affine function of
+// the patch point: X_B = R X' + X0, w(X') = w0 + W X' (patch components;
+// W = Omega [n]_x for a rotating patch, 0 otherwise).
+struct Frame {
+  bool rot = false;
+  double R[9], X0[3], w0[3], W[9];
+};
+
+Frame frame(const mpw_patch_desc& d, double t) {
+  Frame f;
+  f.rot = d.motion == MPW_MOTION_ROTATING;
+  motion(d, t, f.X0, f.w0);
+  for (int e = 0; e < 9; ++e) {
+    f.R[e] = (e % 4 == 0) ? 1.0 : 0.0;
+    f.W[e] = 0.0;
+  }
+  if (f.rot) {
+    rotation(d, t, f.R);
+    const double* n = d.motion_params + 6;
+    const double om = d.motion_params[9];
+    const double K[9] = {0.0, -n[2], n[1], n[2], 0.0, -n[0], -n[1], n[0], 0.0};
+    for (int e = 0; e < 9; ++e) f.W[e] = om * K[e];
+  }
+  return f;
+}
+
+// X_B of the patch point xl (interpolation positions; host side).
+void to_background(const Frame& f, const double xl[3], double xb[3]) {
+  for (int a = 0; a < 3; ++a)
+    xb[a] = f.rot ? ((f.R[3 * a] * xl[0] + f.R[3 * a + 1] * xl[1]) + f.R[3 * a + 2] * xl[2]) + f.X0[a] : xl[a] + f.X0[a];
+}
+
+// Background bounding box of the patch box [lo - e h, hi + e h] at time t
+// (exact for translation).
+void background_extent(const mpw_patch_desc& d, double t, double e, double lo[3], double hi[3]) {
+  const Frame f = frame(d, t);
+  double h[3];
+  for (int a = 0; a < 3; ++a) {
+    h[a] = (d.hi[a] - d.lo[a]) / d.n[a];
+    lo[a] = 1e300;
+    hi[a] = -1e300;
+  }
+  for (int c = 0; c < 8; ++c) {
+    double xl[3], xb[3];
+    for (int a = 0; a < 3; ++a) xl[a] = ((c >> a) & 1) ? d.hi[a] + e * h[a] : d.lo[a] - e * h[a];
+    to_background(f, xl, xb);
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = std::min(lo[a], xb[a]);
+      hi[a] = std::max(hi[a], xb[a]);
+    }
+  }
+}
+
+// Largest speed of a point of the live box in the background frame (the
+// Euclidean bound |Omega| r_max + |V| for a rotating patch).
+double max_point_speed(const mpw_patch_desc& d) {
+  const double* mp = d.motion_params;
+  if (d.motion == MPW_MOTION_LINEAR) return std::sqrt(mp[3] * mp[3] + mp[4] * mp[4] + mp[5] * mp[5]);
+  if (d.motion == MPW_MOTION_CIRCULAR) return std::fabs(mp[3] * mp[4]);
+  if (d.motion != MPW_MOTION_ROTATING) return 0.0;
+  double r2 = 0.0;
+  for (int c = 0; c < 8; ++c) {
+    double q = 0.0;
+    for (int a = 0; a < 3; ++a) {
+      const double x = ((c >> a) & 1) ? d.hi[a] : d.lo[a];
+      q += x * x;
+    }
+    r2 = std::max(r2, q);
+  }
+  return std::fabs(mp[9]) * std::sqrt(r2) + std::sqrt(mp[3] * mp[3] + mp[4] * mp[4] + mp[5] * mp[5]);
+}
+
+// Largest |w_a| per axis the motion law can reach (a rotating patch: the
+// bound over the live box, |Omega| |(n x X')_a| + |V| at the corners).
 void max_speed(const mpw_patch_desc& d, double v[3]) {
   const double* mp = d.motion_params;
   for (int a = 0; a < 3; ++a) v[a] = 0.0;
   if (d.motion == MPW_MOTION_LINEAR)
     for (int a = 0; a < 3; ++a) v[a] = std::fabs(mp[3 + a]);
   if (d.motion == MPW_MOTION_CIRCULAR) v[0] = v[1] = std::fabs(mp[3] * mp[4]);
+  if (d.motion == MPW_MOTION_ROTATING) {
+    const double* n = mp + 6;
+    const double vv = std::sqrt(mp[3] * mp[3] + mp[4] * mp[4] + mp[5] * mp[5]);
+    for (int c = 0; c < 8; ++c) {
+      double x[3];
+      for (int a = 0; a < 3; ++a) x[a] = ((c >> a) & 1) ? d.hi[a] : d.lo[a];
+      const double cr[3] = {n[1] * x[2] - n[2] * x[1], n[2] * x[0] - n[0] * x[2], n[0] * x[1] - n[1] * x[0]};
+      for (int a = 0; a < 3; ++a) v[a] = std::max(v[a], std::fabs(mp[9]) * std::fabs(cr[a]) + vv);
+    }
+  }
 }
 
 bool is_moving(const mpw_patch_desc& d) {
@@ -189,11 +295,24 @@ Geom make_geom(const mpw_patch_desc& d, int esize = 8) {
 // Covered box of local patch l on the global grid at time t (Sec. 2.4.2,
 // "Find Covered Zones"): global cell centres inside the closed live box of l,
 // tested in l's numeric coordinates.  Under translation the covered set is a
-// product of one index interval per axis.
+// product of one index interval per axis.  A rotating patch covers a rotated
+// box: the result is then a bounding box of its cells (one cell of margin
+// around the cells whose centres lie in the background extent), and the
+// cover kernel tests every cell in it.
 Box covered_box(const PatchState& g, const PatchState& l, double t) {
   double X0[3], w[3];
   motion(l.d, t, X0, w);
   Box b;
+  if (l.d.motion == MPW_MOTION_ROTATING) {
+    double lo[3], hi[3];
+    background_extent(l.d, t, 0.0, lo, hi);
+    for (int a = 0; a < 3; ++a) {
+      const double h = (g.d.hi[a] - g.d.lo[a]) / g.d.n[a];
+      b.lo[a] = std::max(0, (int)std::ceil((lo[a] - g.d.lo[a]) / h - 0.5) - 1);
+      b.hi[a] = std::min(g.d.n[a] - 1, (int)std::floor((hi[a] - g.d.lo[a]) / h - 0.5) + 1);
+    }
+    return b;
+  }
   for (int a = 0; a < 3; ++a) {
     b.lo[a] = 1 << 30;
     b.hi[a] = -1;
@@ -241,6 +360,7 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
     const PatchState& P = c->p[q];
     double v[3];
     max_speed(P.d, v);
+    const double sp = max_point_speed(P.d);
     // RK4 stays stable on the imaginary axis up to 2 sqrt(2); the 4th-order
     // Laplacian reaches 16/(3 h^2) per axis, the 4th-order first derivative
     // 1.372/h.
@@ -252,9 +372,10 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
     if (dt * (std::sqrt(lap) + adv) > 2.8)
       return set_err(MPW_ERR_CFL, "patch %zu: dt = %g exceeds the RK4 stability estimate", q, dt);
     if (q == 0) continue;
-    // the buffer of B live cells lets a patch cross B - NG global cells per step
+    // the buffer of B live cells lets a patch cross B - NG global cells per
+    // step (a rotating patch: its fastest point, on every axis)
     for (int a = 0; a < 3; ++a)
-      if (v[a] * dt > (c->buffer - NG) * g.g.h[a])
+      if ((P.d.motion == MPW_MOTION_ROTATING ? sp : v[a]) * dt > (c->buffer - NG) * g.g.h[a])
         return set_err(MPW_ERR_TRAVERSAL, "patch %zu crosses more than %d global cell(s) per step", q,
                        c->buffer - NG);
   }
@@ -264,19 +385,33 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
       const PatchState& P = c->p[q];
       double X0[3], w[3];
       motion(P.d, tt, X0, w);
+      if (P.d.motion == MPW_MOTION_ROTATING) {
+        // the ghost-extended box, rotated; the samples are dt/2 apart
+        double lo[3], hi[3];
+        background_extent(P.d, tt, NG, lo, hi);
+        const double slack = max_point_speed(P.d) * 0.5 * dt;
+        for (int a = 0; a < 3; ++a) {
+          const double margin = (NG + 2) * g.g.h[a] + slack;
+          if (lo[a] - margin < g.d.lo[a] || hi[a] + margin > g.d.hi[a])
+            return set_err(MPW_ERR_OUTSIDE, "patch %zu leaves the global interior at t = %g", q, tt);
+        }
+      }
       for (int a = 0; a < 3; ++a) {
         const double margin = NG * P.g.h[a] + (NG + 2) * g.g.h[a];
-        if (P.d.lo[a] + X0[a] - margin < g.d.lo[a] || P.d.hi[a] + X0[a] + margin > g.d.hi[a])
+        if (P.d.motion != MPW_MOTION_ROTATING &&
+            (P.d.lo[a] + X0[a] - margin < g.d.lo[a] || P.d.hi[a] + X0[a] + margin > g.d.hi[a]))
           return set_err(MPW_ERR_OUTSIDE, "patch %zu leaves the global interior at t = %g", q, tt);
       }
+      double plo[3], phi[3];
+      background_extent(P.d, tt, 0.0, plo, phi);
       for (size_t r = q + 1; r < c->p.size(); ++r) {
         const PatchState& R = c->p[r];
-        double Y0[3], w2[3];
-        motion(R.d, tt, Y0, w2);
+        double rlo[3], rhi[3];
+        background_extent(R.d, tt, 0.0, rlo, rhi);
         double gap = -1e300;
         for (int a = 0; a < 3; ++a) {
-          const double g1 = (R.d.lo[a] + Y0[a]) - (P.d.hi[a] + X0[a]);
-          const double g2 = (P.d.lo[a] + X0[a]) - (R.d.hi[a] + Y0[a]);
+          const double g1 = rlo[a] - phi[a];
+          const double g2 = plo[a] - rhi[a];
           gap = std::max(gap, std::max(g1, g2));
         }
         if (gap < 2.0 * h0)
@@ -297,15 +432,34 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   const std::vector<Box> old_boxes = c->boxes;
   const bool restrict_cells = c->flags_valid && (int)old_boxes.size() == a.nloc;
   c->boxes.assign(a.nloc, Box{});
+  long long ncov = 0;
   for (int q = 0; q < a.nloc; ++q) {
     const PatchState& L = c->p[q + 1];
     c->boxes[q] = covered_box(g, L, t);
     a.box[q] = c->boxes[q];
     a.Uloc[q] = L.buf(BUF_U);
     a.gl[q] = L.g;
-    double w[3];
-    motion(L.d, t, a.X0[q], w);
+    const Frame f = frame(L.d, t);
+    a.rot[q] = f.rot ? 1 : 0;
+    for (int e = 0; e < 9; ++e) a.R[q][e] = f.R[e];
+    for (int k = 0; k < 3; ++k) {
+      a.X0[q][k] = f.X0[k];
+      a.lhi[q][k] = L.d.hi[k];
+    }
+    a.cov_off[q] = ncov;
+    if (f.rot && !box_empty(c->boxes[q])) {
+      const Box& b = c->boxes[q];
+      ncov += (long long)(b.hi[0] - b.lo[0] + 1) * (b.hi[1] - b.lo[1] + 1) * (b.hi[2] - b.lo[2] + 1);
+    }
   }
+  a.cov_off[a.nloc] = ncov;
+  if ((size_t)ncov > c->cov_bytes) {
+    c->dfree(c->d_cov);
+    c->d_cov = (uint8_t*)c->dalloc((size_t)ncov);
+    c->cov_bytes = c->d_cov ? (size_t)ncov : 0;
+    if (!c->d_cov) return set_err(MPW_ERR_CUDA, "covered-mask allocation of %lld bytes failed", ncov);
+  }
+  a.cov = c->d_cov;
   // With valid flags only cells inside an old or a new covered box can change:
   // visit the bounding box of each pair, merging regions until disjoint.
   a.nreg = 0;
@@ -502,10 +656,29 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     S.dpatch = q + 1;
     S.D = L.buf(b);
     S.gd = L.g;
-    double X0[3], w[3];
-    motion(L.d, t, X0, w);
-    for (int k = 0; k < 3; ++k) S.shift[k] = -X0[k];
+    const Frame f = frame(L.d, t);
     S.block0 = blocks;
+    if (f.rot) {
+      // the effective ghosts of a rotated box: every cell of the covered
+      // bounding box whose flag says GHOST of this patch, mapped by
+      // X' = R^T X_B - R^T X0
+      S.kind = SEG_MASKED;
+      S.box = bx;
+      S.flags = c->d_flags;
+      S.want = FLAG_GHOST | ((q + 1) << 2);
+      for (int r = 0; r < 3; ++r) {
+        S.shift[r] = 0.0;
+        for (int k = 0; k < 3; ++k) {
+          S.M[3 * r + k] = f.R[3 * k + r];
+          S.shift[r] -= f.R[3 * k + r] * f.X0[k];
+        }
+      }
+      const long long vol = (long long)(bx.hi[0] - bx.lo[0] + 1) * (bx.hi[1] - bx.lo[1] + 1) * (bx.hi[2] - bx.lo[2] + 1);
+      blocks += (int)((vol + fill_threads() - 1) / fill_threads());
+      continue;
+    }
+    S.kind = SEG_SHELL;
+    for (int k = 0; k < 3; ++k) S.shift[k] = -f.X0[k];
     blocks += build_segment(S, O0, O, c->P);
   }
   // Global-to-Local: the ghost shell of each local patch
@@ -518,9 +691,11 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     S.dpatch = 0;
     S.D = g.buf(b);
     S.gd = g.g;
-    double X0[3], w[3];
-    motion(L.d, t, X0, w);
-    for (int k = 0; k < 3; ++k) S.shift[k] = X0[k];
+    const Frame f = frame(L.d, t);
+    // a rotated ghost shell takes the direct sums through X_B = R X' + X0
+    S.kind = f.rot ? SEG_AFFINE : SEG_SHELL;
+    for (int e = 0; e < 9; ++e) S.M[e] = f.R[e];
+    for (int k = 0; k < 3; ++k) S.shift[k] = f.X0[k];
     const int O0[3] = {-NG, -NG, -NG};
     const int O[3] = {L.d.n[0] + 2 * NG, L.d.n[1] + 2 * NG, L.d.n[2] + 2 * NG};
     S.block0 = blocks;
@@ -579,16 +754,21 @@ int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
     R.ACC = P.buf(BUF_ACC);
     R.OUT = P.buf(out_buf[l]);
     R.g = P.g;
-    double X0[3], w[3];
-    motion(P.d, t, X0, w);
+    const Frame f = frame(P.d, t);
     R.moving = 0;
+    R.rot = f.rot && is_moving(P.d) ? 1 : 0;
     for (int k = 0; k < 3; ++k) {
       const double h = P.g.h[k];
-      R.c1[k] = w[k] / (12.0 * h);
+      // c1 at cell (0, 0, 0): w0 + W X'(0, 0, 0); steps W_kb h_b per index
+      double wk = f.w0[k];
+      for (int m = 0; m < 3; ++m) wk += f.W[3 * k + m] * (P.g.lo[m] + 0.5 * P.g.h[m]);
+      R.c1[k] = wk / (12.0 * h);
+      for (int m = 0; m < 3; ++m) R.c1g[k][m] = f.W[3 * k + m] * P.g.h[m] / (12.0 * h);
       R.c2[k] = 1.0 / (12.0 * h * h);
       R.cko[k] = c->cfg.ko_eps / (64.0 * h);
-      if (w[k] != 0.0) R.moving = 1;
+      if (wk != 0.0) R.moving = 1;
     }
+    if (R.rot) R.moving = 1;
     R.is_global = q == 0 && c->flags_valid && !c->boxes.empty();
     R.iso = P.g.h[0] == P.g.h[1] && P.g.h[1] == P.g.h[2];
     R.in_buf = in_buf[l];
@@ -606,11 +786,13 @@ int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
 mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
   RhsArgs a;
   const int blocks = prep_rhs(c, l, t, dt, a);
+  bool rot = false;
+  for (int q = 0; q < a.np; ++q) rot = rot || a.p[q].rot;
   c->launch_begin(MPW_KERNEL_RHS);
   if (c->cfg.precision == 32)
-    launch_rhs32(a, blocks, c->stream);
+    launch_rhs32(a, blocks, rot, c->stream);
   else
-    launch_rhs(a, blocks, c->cfg.arith != 1, c->stream);
+    launch_rhs(a, blocks, c->cfg.arith != 1, rot, c->stream);
   c->launch_end(MPW_KERNEL_RHS);
   CUDA_TRY(cudaGetLastError());
   return MPW_OK;
@@ -751,6 +933,7 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_apre);
   c->dfree(c->d_expo);
   c->dfree(c->d_rev);
+  c->dfree(c->d_cov);
   c->dfree(c->d_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& v : c->ev)
@@ -770,7 +953,13 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
     if (d->n[a] < 2 * NG) return set_err(MPW_ERR_ARG, "n[%d] must be >= %d", a, 2 * NG);
     if (!(d->hi[a] > d->lo[a])) return set_err(MPW_ERR_ARG, "hi must exceed lo");
   }
-  if (d->motion < MPW_MOTION_STATIC || d->motion > MPW_MOTION_CIRCULAR) return set_err(MPW_ERR_ARG, "bad motion law");
+  if (d->motion < MPW_MOTION_STATIC || d->motion > MPW_MOTION_ROTATING) return set_err(MPW_ERR_ARG, "bad motion law");
+  if (d->motion == MPW_MOTION_ROTATING) {
+    const double* n = d->motion_params + 6;
+    if (!(std::fabs(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] - 1.0) <= 1e-12))
+      return set_err(MPW_ERR_ARG, "the rotation axis must be a unit vector");
+    if (d->kind == MPW_PATCH_GLOBAL) return set_err(MPW_ERR_ARG, "the global patch cannot rotate");
+  }
   if (d->kind == MPW_PATCH_GLOBAL) {
     if (d->outer_bc != MPW_BC_ANALYTIC && d->outer_bc != MPW_BC_PERIODIC)
       return set_err(MPW_ERR_ARG, "global outer_bc must be ANALYTIC or PERIODIC");
@@ -857,9 +1046,11 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
   if (use_device(c)) return MPW_ERR_CUDA;
   if ((st = apply_pending_inputs(c))) return st;
   for (auto& P : c->p) {
-    double X0[3], w[3];
-    motion(P.d, t, X0, w);
-    launch_analytic(P.buf(BUF_U), P.g, X0[0], X0[1], X0[2], c->akind, c->acount, c->d_aparams,
+    const Frame f = frame(P.d, t);
+    Affine map;
+    for (int e = 0; e < 9; ++e) map.R[e] = f.R[e];
+    for (int k = 0; k < 3; ++k) map.X0[k] = f.X0[k];
+    launch_analytic(P.buf(BUF_U), P.g, map, c->akind, c->acount, c->d_aparams,
                     c->screen_ok ? c->d_ascreen : nullptr, c->screen_ok ? c->d_apre : nullptr, t,
                     c->cfg.precision == 32, c->stream);
     CUDA_TRY(cudaGetLastError());
@@ -1154,6 +1345,22 @@ mpw_status mpw_live_points(mpw_ctx* c, long long* count) {
   if (c->p.empty() || !count) return set_err(MPW_ERR_ARG, "no global patch or null pointer");
   long long n = 0;
   for (const auto& P : c->p) n += (long long)P.d.n[0] * P.d.n[1] * P.d.n[2];
+  bool rot = false;
+  for (size_t q = 1; q < c->p.size(); ++q) rot = rot || c->p[q].d.motion == MPW_MOTION_ROTATING;
+  if (rot) {
+    // a rotated covered set is no box: count the live global cells
+    if (use_device(c)) return MPW_ERR_CUDA;
+    if ((st = apply_pending_inputs(c))) return st;
+    if (!c->flags_valid && (st = run_flags(c, c->t))) return st;
+    const PatchState& g = c->p[0];
+    std::vector<uint8_t> fl((size_t)g.d.n[0] * g.d.n[1] * g.d.n[2]);
+    CUDA_TRY(cudaMemcpyAsync(fl.data(), c->d_flags, fl.size(), cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    n -= (long long)fl.size();
+    for (uint8_t f : fl) n += ((f & 3) == FLAG_LIVE || (f & 3) == FLAG_REVIVED) ? 1 : 0;
+    *count = n;
+    return MPW_OK;
+  }
   for (size_t q = 1; q < c->p.size(); ++q) {
     const Box b = c->flags_valid && q - 1 < c->boxes.size() ? c->boxes[q - 1] : covered_box(c->p[0], c->p[q], c->t);
     long long inner = 1;
@@ -1346,6 +1553,9 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         totals[r] = total;
       }
     }
+    bool rot = false;  // some patch rotates: the RHS kernels with a position-dependent w
+    for (mpw_ctx* c : b->ctx)
+      for (const auto& P : c->p) rot = rot || P.d.motion == MPW_MOTION_ROTATING;
     // copies and launches of the step, on stream sm
     auto enqueue = [&](cudaStream_t sm) -> cudaError_t {
       for (int r = 0; r < 8; ++r) {
@@ -1361,9 +1571,9 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         } else {
           if (trial && l == 0) cudaEventRecord(b->tev[2 * k], sm);
           if (b->f32)
-            launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], sm);
+            launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], rot, sm);
           else
-            launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], b->fixed, sm);
+            launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], b->fixed, rot, sm);
           if (trial && l == 3) cudaEventRecord(b->tev[2 * k + 1], sm);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

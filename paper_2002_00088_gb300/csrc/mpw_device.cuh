@@ -256,4 +256,42 @@ __device__ __forceinline__ void shell_point(long long idx, const int O[3], int t
 
 __device__ __forceinline__ int wrap_index(int i, int n) { return ((i % n) + n) % n; }
 
+// ---------------------------------------------------------------------------
+// Patch maps X_B = R X' + X0 (Sec. 2.4, numeric -> background).  The cover
+// flags are discrete decisions taken on these positions, so the two helpers
+// below round every operation as written (no contraction): the same
+// operations in the same order on the host give the same bits.
+// Cell-centred node lo + (i + 1/2) h.
+__device__ __forceinline__ double node_rn(double lo, int i, double h) {
+  return __dadd_rn(lo, __dmul_rn((double)i + 0.5, h));
+}
+
+// X' = R^T (X_B - X0), R row-major.
+__device__ __forceinline__ void to_local_rn(const double* __restrict__ R, const double* __restrict__ X0, double xb,
+                                            double yb, double zb, double xl[3]) {
+  const double d0 = __dsub_rn(xb, X0[0]), d1 = __dsub_rn(yb, X0[1]), d2 = __dsub_rn(zb, X0[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    xl[a] = __dadd_rn(__dadd_rn(__dmul_rn(R[a], d0), __dmul_rn(R[3 + a], d1)), __dmul_rn(R[6 + a], d2));
+}
+
+// X_B = R X' + X0, rounded as written (the closed-form initial data of a
+// rotating patch is then sampled at the oracle's very positions).
+__device__ __forceinline__ void to_background_rn(const double* __restrict__ R, const double* __restrict__ X0, double x,
+                                                 double y, double z, double xb[3]) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+    xb[a] = __dadd_rn(__dadd_rn(__dadd_rn(__dmul_rn(R[3 * a], x), __dmul_rn(R[3 * a + 1], y)), __dmul_rn(R[3 * a + 2], z)),
+                      X0[a]);
+}
+
+// General affine position M x + c (interpolation only: rounding here moves a
+// point by ulps, which the interpolant absorbs).
+__device__ __forceinline__ void affine(const double* __restrict__ M, const double* __restrict__ c, double x, double y,
+                                       double z, double& ox, double& oy, double& oz) {
+  ox = fma(M[0], x, fma(M[1], y, fma(M[2], z, c[0])));
+  oy = fma(M[3], x, fma(M[4], y, fma(M[5], z, c[1])));
+  oz = fma(M[6], x, fma(M[7], y, fma(M[8], z, c[2])));
+}
+
 }  // namespace mpw

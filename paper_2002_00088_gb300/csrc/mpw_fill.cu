@@ -287,6 +287,73 @@ __device__ __forceinline__ void thin_pass(const InterpSeg& S, int a0, const int 
   }
 }
 
+// Donor position of the target point with target numeric coordinates
+// (x, y, z): a shift under translation, an affine map under rotation.
+__device__ __forceinline__ void donor_position(const InterpSeg& S, double x, double y, double z, double& px,
+                                               double& py, double& pz) {
+  if (S.kind == SEG_SHELL) {
+    px = x + S.shift[0], py = y + S.shift[1], pz = z + S.shift[2];
+  } else {
+    affine(S.M, S.shift, x, y, z, px, py, pz);
+  }
+}
+
+// Direct tensor sums (Eq. Pijk) point by point for the targets of a tile;
+// reports uninterpolable points.
+template <int P, typename ST>
+__device__ __noinline__ void direct_points(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], int emax[2]) {
+  ST* Tt = reinterpret_cast<ST*>(S.T);
+  const int ntar = T[0] * T[1] * T[2];
+  for (int e = threadIdx.x; e < ntar; e += FILL_THREADS) {
+    const int x = e % T[0], y = (e / T[0]) % T[1], z = e / (T[0] * T[1]);
+    const int i = org[0] + x, j = org[1] + y, k = org[2] + z;
+    double v0, v1, px, py, pz;
+    donor_position(S, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
+                   S.gt.lo[2] + (k + 0.5) * S.gt.h[2], px, py, pz);
+    if (!interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, px, py, pz, v0, v1)) {
+      atomicOr(A.err, ERR_UNFILLED);
+      continue;
+    }
+    const long long c = S.gt.at(i, j, k);
+    Tt[c] = (ST)v0;
+    Tt[c + S.gt.vol] = (ST)v1;
+    emax[0] = max(emax[0], biased_exponent(v0));
+    emax[1] = max(emax[1], biased_exponent(v1));
+  }
+}
+
+// Local-to-Global under a rotating map: one thread per cell of the covered
+// bounding box; the cells whose flag byte is S.want (effective ghosts of
+// this patch) take the direct sum from the local patch.
+template <int P, typename ST>
+__device__ __noinline__ void masked_block(const FillArgs& A, const InterpSeg& S, int r) {
+  constexpr bool F32 = sizeof(ST) == 4;
+  const Box& b = S.box;
+  const int w0 = b.hi[0] - b.lo[0] + 1, w1 = b.hi[1] - b.lo[1] + 1, w2 = b.hi[2] - b.lo[2] + 1;
+  const long long idx = (long long)r * FILL_THREADS + threadIdx.x;
+  int e0 = 0, e1 = 0;
+  if (idx < (long long)w0 * w1 * w2) {
+    const int i = b.lo[0] + (int)(idx % w0), j = b.lo[1] + (int)((idx / w0) % w1),
+              k = b.lo[2] + (int)(idx / ((long long)w0 * w1));
+    if (S.flags[((long long)k * S.gt.n[1] + j) * S.gt.n[0] + i] == S.want) {
+      double v0, v1, px, py, pz;
+      donor_position(S, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
+                     S.gt.lo[2] + (k + 0.5) * S.gt.h[2], px, py, pz);
+      if (interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, px, py, pz, v0, v1)) {
+        ST* Tt = reinterpret_cast<ST*>(S.T);
+        const long long c = S.gt.at(i, j, k);
+        Tt[c] = (ST)v0;
+        Tt[c + S.gt.vol] = (ST)v1;
+        e0 = biased_exponent(v0);
+        e1 = biased_exponent(v1);
+      } else {
+        atomicOr(A.err, ERR_UNFILLED);
+      }
+    }
+  }
+  if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, e0, e1);
+}
+
 // One interpolation tile.  ST is the storage type of the field buffers:
 // double (arithmetic FP64 or fixed point, FillArgs::fixed) or float (FP32
 // arithmetic, with the weights computed in FP64 and rounded once).
@@ -305,6 +372,13 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
   float* BF = reinterpret_cast<float*>(BQ);
   ST* Tt = reinterpret_cast<ST*>(S.T);
   const int tid = threadIdx.x;
+  if (S.kind == SEG_AFFINE) {
+    // rotated target grid: the 1-D weights differ from point to point
+    int emax[2] = {0, 0};
+    direct_points<P, ST>(A, S, org, T, emax);
+    if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, emax[0], emax[1]);
+    return;
+  }
   // 1-D weights of every target index of the tile, per axis; the threads of
   // the thin axis also write their row of the band matrix
   for (int e = tid; e < T[0] + T[1] + T[2]; e += FILL_THREADS) {
@@ -358,24 +432,7 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
   int emax[2] = {0, 0};
   const int ntar = T[0] * T[1] * T[2];
   if (!fits) {
-    // direct tensor sum, point by point (reports uninterpolable points)
-    for (int e = tid; e < ntar; e += FILL_THREADS) {
-      const int x = e % T[0], y = (e / T[0]) % T[1], z = e / (T[0] * T[1]);
-      const int i = org[0] + x, j = org[1] + y, k = org[2] + z;
-      double v0, v1;
-      const double px = S.gt.lo[0] + (i + 0.5) * S.gt.h[0] + S.shift[0];
-      const double py = S.gt.lo[1] + (j + 0.5) * S.gt.h[1] + S.shift[1];
-      const double pz = S.gt.lo[2] + (k + 0.5) * S.gt.h[2] + S.shift[2];
-      if (!interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, px, py, pz, v0, v1)) {
-        atomicOr(A.err, ERR_UNFILLED);
-        continue;
-      }
-      const long long c = S.gt.at(i, j, k);
-      Tt[c] = (ST)v0;
-      Tt[c + S.gt.vol] = (ST)v1;
-      emax[0] = max(emax[0], biased_exponent(v0));
-      emax[1] = max(emax[1], biased_exponent(v1));
-    }
+    direct_points<P, ST>(A, S, org, T, emax);
   } else {
     int d1[3] = {Dn[0], Dn[1], Dn[2]};
     d1[a0] = T[a0];
@@ -500,6 +557,10 @@ __device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
   while (s + 1 < A.nseg && b >= A.seg[s + 1].block0) ++s;
   const InterpSeg& S = A.seg[s];
   int r = b - S.block0;
+  if (S.kind == SEG_MASKED) {
+    masked_block<P, ST>(A, S, r);
+    return;
+  }
   int sl = 0;
   while (sl < 5 && r >= S.slab_block0[sl + 1]) ++sl;
   r -= S.slab_block0[sl];

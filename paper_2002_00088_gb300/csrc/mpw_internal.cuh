@@ -78,6 +78,8 @@ struct RhsPatch {
   int tiles_x, tiles_y, zchunks, zc;
   int block0;
   int moving;        // any w_a != 0
+  int rot;           // rotating frame: c1 varies with the point,
+  double c1g[3][3];  //   c1_a(i, j, k) = c1[a] + c1g[a][0] i + c1g[a][1] j + c1g[a][2] k
   int is_global;
   int iso;           // equal spacing on all axes (D2 and KO sums aggregated)
   int in_buf, out_buf;
@@ -99,14 +101,24 @@ struct RhsArgs {
 // One interpolation target set: the hollow box shell (walls NG thick) of a
 // target patch, filled from a donor patch.  The shell is cut into six slabs
 // (z-, z+, y-, y+, x-, x+), each tiled by boxes of td targets.
+enum { SEG_SHELL = 0, SEG_AFFINE = 1, SEG_MASKED = 2 };
+
 struct InterpSeg {
+  int kind;            // SEG_SHELL: hollow box under translation (separable passes);
+                       // SEG_AFFINE: hollow box under a rotating map (direct sums);
+                       // SEG_MASKED: the global cells of flag `want` inside `box`
+  double M[9];         // SEG_AFFINE / SEG_MASKED: donor position = M target position + shift
+  Box box;             // SEG_MASKED: target cells to test (global indices)
+  const uint8_t* flags;
+  int want;            // flag byte of the cells to fill (state | owner << 2)
   double* T;           // target buffer (psi; Pi at +vol)
   Geom gt;
   int tpatch;          // target patch id (exponent slots)
   int dpatch;          // donor patch id (exponent slots)
   const double* D;     // donor buffer (psi; Pi at +vol)
   Geom gd;
-  double shift[3];     // X0_target - X0_donor at the substage time
+  double shift[3];     // X0_target - X0_donor at the substage time (translation), or the
+                       // affine offset
   int sb[6][3];        // slab origin (target indices)
   int se[6][3];        // slab extent
   int td[6][3];        // tile extent
@@ -155,6 +167,13 @@ struct FlagArgs {
   const double* Uloc[MAX_PATCHES];
   Geom gl[MAX_PATCHES];
   double X0[MAX_PATCHES][3];
+  // rotating patches: box[q] bounds the covered cells, whose mask the cover
+  // kernel writes to cov (cov_off[q] onwards, box-local x fastest)
+  int rot[MAX_PATCHES];
+  double R[MAX_PATCHES][9];
+  double lhi[MAX_PATCHES][3];  // upper corner of the live box (the descriptor's hi)
+  uint8_t* cov;
+  long long cov_off[MAX_PATCHES + 1];
   int P;
   int* err;
   int* expo;
@@ -184,12 +203,15 @@ void set_last_error(const char* msg);
 bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile, bool f32 = false);
 
 // ---------------------------------------------------------------- host entry points of the kernels
-void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream);
-void launch_rhs32(const RhsArgs& a, int blocks, void* stream);  // binary32 storage and arithmetic
+// rot: some patch of the launch rotates (selects the kernels with a
+// position-dependent frame velocity)
+void launch_rhs(const RhsArgs& a, int blocks, bool fixed, bool rot, void* stream);
+void launch_rhs32(const RhsArgs& a, int blocks, bool rot, void* stream);  // binary32 storage and arithmetic
 // Batched launches over independent instances: d_args[i] (device memory)
 // describes instance i, whose blocks are [d_blk0[i], d_blk0[i + 1]).
-void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool fixed, void* stream);
-void launch_rhs32_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, void* stream);
+void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool fixed, bool rot,
+                      void* stream);
+void launch_rhs32_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool rot, void* stream);
 void launch_fill_batch(const FillArgs* d_args, const int* d_blk0, int ninst, int blocks, int P, bool f32,
                        void* stream);
 void launch_expo_scan(const double* buf, const Geom& g, const uint8_t* flags, int* slot2, void* stream);
@@ -202,9 +224,13 @@ int fill_threads();
 int launch_flags(const FlagArgs& a, void* stream);  // returns the number of kernels launched
 // buf: a field buffer of binary64, or of binary32 when f32; the dense arrays
 // d0, d1 are binary64 in every case.
-void launch_analytic(void* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
-                     const double* aparams, const float4* screen, const double* apre, double t, bool f32,
-                     void* stream);
+struct Affine {
+  double R[9];  // row-major
+  double X0[3];
+};
+// X_B = R X' + X0 for every interior point (the patch map at t).
+void launch_analytic(void* buf, const Geom& g, const Affine& map, int akind, int acount, const double* aparams,
+                     const float4* screen, const double* apre, double t, bool f32, void* stream);
 void launch_pack(const void* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags, bool f32,
                  void* stream);
 void launch_unpack(void* buf, const Geom& g, const double* d0, const double* d1, bool f32, void* stream);

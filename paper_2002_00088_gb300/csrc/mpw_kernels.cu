@@ -14,11 +14,62 @@
 namespace mpw {
 
 // ---------------------------------------------------------------------------
-// Cover flags with buffer (Sec. 2.4.2), from the covered box of every local
-// patch at t_n.  A covered cell's L-infinity distance to the nearest
-// uncovered cell is min over axes of its distance to the box faces; LIVE if
-// d <= buffer, GHOST if d <= buffer + NG, DEAD beyond.  DEAD cells of u are
-// poisoned with NaN; cells that turn LIVE after having been GHOST or DEAD are
+// Covered mask of the rotating local patches (Sec. 2.4.2, "Find Covered
+// Zones"): a global cell is covered when its centre, taken to the patch's
+// numeric coordinates, lies in the closed live box.  One thread per cell of
+// each patch's bounding box; the mask is box-local, x fastest.
+__global__ void __launch_bounds__(256) k_cover(const __grid_constant__ FlagArgs A) {
+  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= A.cov_off[A.nloc]) return;
+  int q = 0;
+  while (idx >= A.cov_off[q + 1]) ++q;
+  const Box& b = A.box[q];
+  const long long r = idx - A.cov_off[q];
+  const int w0 = b.hi[0] - b.lo[0] + 1, w1 = b.hi[1] - b.lo[1] + 1;
+  const int i = b.lo[0] + (int)(r % w0), j = b.lo[1] + (int)((r / w0) % w1), k = b.lo[2] + (int)(r / ((long long)w0 * w1));
+  double xl[3];
+  to_local_rn(A.R[q], A.X0[q], node_rn(A.gg.lo[0], i, A.gg.h[0]), node_rn(A.gg.lo[1], j, A.gg.h[1]),
+              node_rn(A.gg.lo[2], k, A.gg.h[2]), xl);
+  const Geom& gl = A.gl[q];
+  bool in = true;
+#pragma unroll
+  for (int a = 0; a < 3; ++a) in = in && gl.lo[a] <= xl[a] && xl[a] <= A.lhi[q][a];
+  A.cov[idx] = in ? 1 : 0;
+}
+
+// Covered state of global cell (i, j, k) for rotating patch q (cells outside
+// its bounding box are uncovered).
+__device__ __forceinline__ bool covered_rot(const FlagArgs& A, int q, int i, int j, int k) {
+  const Box& b = A.box[q];
+  if (i < b.lo[0] || i > b.hi[0] || j < b.lo[1] || j > b.hi[1] || k < b.lo[2] || k > b.hi[2]) return false;
+  const long long w0 = b.hi[0] - b.lo[0] + 1, w1 = b.hi[1] - b.lo[1] + 1;
+  return A.cov[A.cov_off[q] + ((long long)(k - b.lo[2]) * w1 + (j - b.lo[1])) * w0 + (i - b.lo[0])] != 0;
+}
+
+// Numeric coordinates in local patch q of the centre of global cell (i, j, k).
+__device__ __forceinline__ void cell_in_local(const FlagArgs& A, int q, int i, int j, int k, double& x, double& y,
+                                              double& z) {
+  const double xb = A.gg.lo[0] + (i + 0.5) * A.gg.h[0], yb = A.gg.lo[1] + (j + 0.5) * A.gg.h[1],
+               zb = A.gg.lo[2] + (k + 0.5) * A.gg.h[2];
+  if (A.rot[q]) {
+    double xl[3];
+    to_local_rn(A.R[q], A.X0[q], xb, yb, zb, xl);
+    x = xl[0], y = xl[1], z = xl[2];
+  } else {
+    x = xb - A.X0[q][0], y = yb - A.X0[q][1], z = zb - A.X0[q][2];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cover flags with buffer (Sec. 2.4.2), from the covered set of every local
+// patch at t_n; d is a covered cell's L-infinity index distance to the
+// nearest uncovered cell: LIVE if d <= buffer, GHOST if d <= buffer + NG,
+// DEAD beyond.  Under translation the covered set is a box and d the
+// distance to its faces plus one.  A rotating patch covers the cells of a
+// rotated box, a convex set: the cube of half-width r around a cell holds
+// only covered cells exactly when its eight corners are covered, so d is the
+// first r whose corners are not all covered.  DEAD cells of u are poisoned
+// with NaN; cells that turn LIVE after having been GHOST or DEAD are
 // REVIVED: u_n there is interpolated from the owning local patch at t_n.
 template <int P, typename ST>
 __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs A) {
@@ -48,6 +99,23 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
   for (int q = 0; q < A.nloc; ++q) {
     const Box& b = A.box[q];
     if (i >= b.lo[0] && i <= b.hi[0] && j >= b.lo[1] && j <= b.hi[1] && k >= b.lo[2] && k <= b.hi[2]) {
+      if (A.rot[q]) {
+        if (!covered_rot(A, q, i, j, k)) continue;
+        owner = q + 1;
+        const int rmax = A.buffer + NG;
+        d = rmax + 1;
+        for (int r = 1; r <= rmax; ++r) {
+          bool all = true;
+#pragma unroll
+          for (int c = 0; c < 8; ++c)
+            all = all && covered_rot(A, q, i + ((c & 1) ? r : -r), j + ((c & 2) ? r : -r), k + ((c & 4) ? r : -r));
+          if (!all) {
+            d = r;
+            break;
+          }
+        }
+        break;
+      }
       owner = q + 1;
       d = min(min(min(i - b.lo[0], b.hi[0] - i), min(j - b.lo[1], b.hi[1] - j)), min(k - b.lo[2], b.hi[2] - k)) + 1;
       break;
@@ -73,11 +141,9 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
       A.rev_list[slot] = idx | ((long long)q << 40);
       return;
     }
-    double v0, v1;
-    const bool ok = interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q],
-                                    A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
-                                    A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - A.X0[q][1],
-                                    A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - A.X0[q][2], v0, v1);
+    double v0, v1, x, y, z;
+    cell_in_local(A, q, i, j, k, x, y, z);
+    const bool ok = interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1);
     if (!ok) {
       atomicOr(A.err, ERR_UNFILLED);
       return;
@@ -109,11 +175,9 @@ __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs
       const long long rr = idx / A.n[0];
       const int j = (int)(rr % A.n[1]);
       const int k = (int)(rr / A.n[1]);
-      double v0, v1;
-      if (interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q],
-                          A.gg.lo[0] + (i + 0.5) * A.gg.h[0] - A.X0[q][0],
-                          A.gg.lo[1] + (j + 0.5) * A.gg.h[1] - A.X0[q][1],
-                          A.gg.lo[2] + (k + 0.5) * A.gg.h[2] - A.X0[q][2], v0, v1)) {
+      double v0, v1, x, y, z;
+      cell_in_local(A, q, i, j, k, x, y, z);
+      if (interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1)) {
         const long long c = A.gg.at(i, j, k);
         ST* Ug = reinterpret_cast<ST*>(A.Ug);
         Ug[c] = (ST)v0;
@@ -135,6 +199,8 @@ __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs
 
 template <int P, typename ST>
 static void launch_flags_t(const FlagArgs& a, unsigned blocks, unsigned rblocks, cudaStream_t s) {
+  const long long ncov = a.cov_off[a.nloc];
+  if (ncov > 0) k_cover<<<(unsigned)((ncov + 255) / 256), 256, 0, s>>>(a);
   k_flags<P, ST><<<blocks, 256, 0, s>>>(a);
   if (a.old_valid) k_revive<P, ST><<<rblocks, 256, 0, s>>>(a);
 }
@@ -152,13 +218,13 @@ int launch_flags(const FlagArgs& a, void* stream) {
     a.P == 6 ? launch_flags_t<6, float>(a, blocks, rblocks, s) : launch_flags_t<5, float>(a, blocks, rblocks, s);
   else
     a.P == 6 ? launch_flags_t<6, double>(a, blocks, rblocks, s) : launch_flags_t<5, double>(a, blocks, rblocks, s);
-  return a.old_valid ? 2 : 1;
+  return (a.old_valid ? 2 : 1) + (a.cov_off[a.nloc] > 0 ? 1 : 0);
 }
 
 // ---------------------------------------------------------------------------
 // Interior <- closed form at time t (positions X_B = numeric + X0).
 template <typename ST>
-__global__ void k_analytic(ST* buf, const Geom g, double X0x, double X0y, double X0z, int akind, int acount,
+__global__ void k_analytic(ST* buf, const Geom g, const Affine map, int rot, int akind, int acount,
                            const double* __restrict__ P, const float4* __restrict__ screen,
                            const double* __restrict__ apre, double t) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -168,24 +234,34 @@ __global__ void k_analytic(ST* buf, const Geom g, double X0x, double X0y, double
   const long long r = idx / g.n[0];
   const int j = (int)(r % g.n[1]);
   const int k = (int)(r / g.n[1]);
+  const double x = g.lo[0] + (i + 0.5) * g.h[0], y = g.lo[1] + (j + 0.5) * g.h[1], z = g.lo[2] + (k + 0.5) * g.h[2];
+  double xb, yb, zb;
+  if (rot) {
+    double b[3];
+    to_background_rn(map.R, map.X0, node_rn(g.lo[0], i, g.h[0]), node_rn(g.lo[1], j, g.h[1]),
+                     node_rn(g.lo[2], k, g.h[2]), b);
+    xb = b[0], yb = b[1], zb = b[2];
+  } else {
+    xb = x + map.X0[0], yb = y + map.X0[1], zb = z + map.X0[2];
+  }
   double ps, pv;
-  closed_form(akind, P, screen, apre, acount, t, g.lo[0] + (i + 0.5) * g.h[0] + X0x, g.lo[1] + (j + 0.5) * g.h[1] + X0y,
-              g.lo[2] + (k + 0.5) * g.h[2] + X0z, ps, pv);
+  closed_form(akind, P, screen, apre, acount, t, xb, yb, zb, ps, pv);
   const long long c = g.at(i, j, k);
   buf[c] = (ST)ps;
   buf[c + g.vol] = (ST)pv;
 }
 
-void launch_analytic(void* buf, const Geom& g, double X0x, double X0y, double X0z, int akind, int acount,
-                     const double* aparams, const float4* screen, const double* apre, double t, bool f32,
-                     void* stream) {
+void launch_analytic(void* buf, const Geom& g, const Affine& map, int akind, int acount, const double* aparams,
+                     const float4* screen, const double* apre, double t, bool f32, void* stream) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   const unsigned blocks = (unsigned)((N + 255) / 256);
+  int rot = 0;
+  for (int e = 0; e < 9; ++e) rot |= map.R[e] != ((e % 4 == 0) ? 1.0 : 0.0);
   if (f32)
-    k_analytic<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<float*>(buf), g, X0x, X0y, X0z, akind,
-                                                                acount, aparams, screen, apre, t);
+    k_analytic<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<float*>(buf), g, map, rot, akind, acount,
+                                                                aparams, screen, apre, t);
   else
-    k_analytic<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<double*>(buf), g, X0x, X0y, X0z, akind,
+    k_analytic<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<double*>(buf), g, map, rot, akind,
                                                                  acount, aparams, screen, apre, t);
 }
 

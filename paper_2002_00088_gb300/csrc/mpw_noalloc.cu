@@ -154,7 +154,7 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
       R.zc = 8;
       R.zchunks = (n[2] + R.zc - 1) / R.zc;
       R.block0 = 0;
-      launch_rhs(r, R.tiles_x * R.tiles_y * R.zchunks, true, s);
+      launch_rhs(r, R.tiles_x * R.tiles_y * R.zchunks, true, false, s);
     }
     t += dt;
   }

@@ -2,7 +2,8 @@
 // of one substage, in one launch.
 //
 // Per live point (4th-order centred differences, KO with n = 5, frame
-// velocity w of a translating patch):
+// velocity w: constant on a translating patch, w(X') = Omega n x X' + R^T V
+// on a rotating one):
 //   K_psi = Pi + w . D1 psi + KO(psi)
 //   K_Pi  = sum_a D2_a psi + w . D1 Pi + KO(Pi)
 // then the RK4 stage combination (Table 1, Eqs. k1-k4):
@@ -46,6 +47,7 @@ namespace {
 struct Terms {
   long long ms[7];  // K_psi: Pi_0, KO_x..z(psi) (or aggregated in [1]), D1_x..z(psi)
   long long mp[9];  // K_Pi : D2_x..z(psi) (or aggregated in [0]), KO_x..z(Pi) (or [3]), D1_x..z(Pi)
+  long long gs[3][3], gp[3][3];  // rotating frame: D1 multipliers per unit of i, j, k (psi, Pi)
   int Ss, Sp;       // output scales of K_psi and K_Pi
   int Es, Ep;       // input scales (biased exponents) of psi and Pi
   int fixed;        // 0: FP64 fallback for this CTA
@@ -63,18 +65,30 @@ __device__ void setup_terms(Terms& T, const RhsPatch& P, int Es_raw, int Ep_raw,
   T.Ep = Ep;
   double cs[7], cp[9];
   int es[7], ep[9];
+  // largest |c1_a| over the patch (a rotating frame's c1 is affine in the
+  // indices, so its extremes sit at the corners)
+  double c1m[3];
+  for (int a = 0; a < 3; ++a) {
+    c1m[a] = fabs(P.c1[a]);
+    if (P.rot)
+      for (int c = 0; c < 8; ++c) {
+        double v = P.c1[a];
+        for (int b = 0; b < 3; ++b) v += P.c1g[a][b] * (((c >> b) & 1) ? P.g.n[b] - 1 : 0);
+        c1m[a] = fmax(c1m[a], fabs(v));
+      }
+  }
   cs[0] = 1.0;
   es[0] = Ep;
   for (int a = 0; a < 3; ++a) {
     cs[1 + a] = P.iso ? (a == 0 ? P.cko[0] : 0.0) : P.cko[a];
     es[1 + a] = Es;
-    cs[4 + a] = P.c1[a];
+    cs[4 + a] = c1m[a];
     es[4 + a] = Es;
     cp[a] = P.iso ? (a == 0 ? P.c2[0] : 0.0) : P.c2[a];
     ep[a] = Es;
     cp[3 + a] = P.iso ? (a == 0 ? P.cko[0] : 0.0) : P.cko[a];
     ep[3 + a] = Ep;
-    cp[6 + a] = P.c1[a];
+    cp[6 + a] = c1m[a];
     ep[6 + a] = Ep;
   }
   int Ss = -100000, Sp = -100000;
@@ -84,6 +98,15 @@ __device__ void setup_terms(Terms& T, const RhsPatch& P, int Es_raw, int Ep_raw,
   T.Sp = Sp;
   for (int t = 0; t < 7; ++t) T.ms[t] = term_multiplier(cs[t], es[t], Ss);
   for (int t = 0; t < 9; ++t) T.mp[t] = term_multiplier(cp[t], ep[t], Sp);
+  // D1 multipliers: c1 at cell (0, 0, 0), and its steps per index
+  for (int a = 0; a < 3; ++a) {
+    T.ms[4 + a] = term_multiplier(P.c1[a], Es, Ss);
+    T.mp[6 + a] = term_multiplier(P.c1[a], Ep, Sp);
+    for (int b = 0; b < 3; ++b) {
+      T.gs[a][b] = P.rot ? term_multiplier(P.c1g[a][b], Es, Ss) : 0;
+      T.gp[a][b] = P.rot ? term_multiplier(P.c1g[a][b], Ep, Sp) : 0;
+    }
+  }
   // K = k 2^S with k the exact int64 sum: the stage updates use alpha 2^S and
   // beta 2^S (exact scalings), or the FP64 path when they would leave the
   // normal range
@@ -137,7 +160,7 @@ __device__ __forceinline__ void issue_slot(const RhsPatch& Pt, int stage, double
 
 // Body of the kernel for block b of the launch described by A (A may sit in
 // kernel parameter space or, for a batched launch, in global memory).
-template <int TX, int TY, bool FIXED>
+template <int TX, int TY, bool FIXED, bool ROT>
 __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
   static_assert(TX == RHS_TX && TY == RHS_TY, "TMA boxes are sized for RHS_TX x RHS_TY tiles");
   extern __shared__ unsigned char smem_dyn[];
@@ -311,12 +334,21 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
                mulhi(zp3 - 6 * zp2 + 15 * zp1 - 20 * v0, T.mp[5]);
         }
         if (Pt.moving) {
-          ks += mulhi(8 * (rs[1] - rs[-1]) - (rs[2] - rs[-2]), T.ms[4]) +
-                mulhi(8 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY]), T.ms[5]) +
-                mulhi(8 * (qs[4] - qs[2]) - (qs[5] - qs[1]), T.ms[6]);
-          kp += mulhi(8 * (rp[1] - rp[-1]) - (rp[2] - rp[-2]), T.mp[6]) +
-                mulhi(8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]), T.mp[7]) +
-                mulhi(8 * (qp[4] - qp[2]) - (qp[5] - qp[1]), T.mp[8]);
+          long long m[6] = {T.ms[4], T.ms[5], T.ms[6], T.mp[6], T.mp[7], T.mp[8]};
+          if (ROT && Pt.rot) {
+            // multipliers of c1_a(i, j, z), affine in the indices
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              m[a] += T.gs[a][0] * i + T.gs[a][1] * j + T.gs[a][2] * z;
+              m[3 + a] += T.gp[a][0] * i + T.gp[a][1] * j + T.gp[a][2] * z;
+            }
+          }
+          ks += mulhi(8 * (rs[1] - rs[-1]) - (rs[2] - rs[-2]), m[0]) +
+                mulhi(8 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY]), m[1]) +
+                mulhi(8 * (qs[4] - qs[2]) - (qs[5] - qs[1]), m[2]);
+          kp += mulhi(8 * (rp[1] - rp[-1]) - (rp[2] - rp[-2]), m[3]) +
+                mulhi(8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]), m[4]) +
+                mulhi(8 * (qp[4] - qp[2]) - (qp[5] - qp[1]), m[5]);
         }
         Ks = (double)ks;  // K_psi / 2^Ss, rounded once
         Kp = (double)kp;
@@ -343,12 +375,16 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
         Ks = v0 + kos;
         Kp = d2 + kop;
         if (Pt.moving) {
-          Ks += Pt.c1[0] * (8.0 * (D(rs[1]) - D(rs[-1])) - (D(rs[2]) - D(rs[-2]))) +
-                Pt.c1[1] * (8.0 * (D(rs[SY]) - D(rs[-SY])) - (D(rs[2 * SY]) - D(rs[-2 * SY]))) +
-                Pt.c1[2] * (8.0 * (D(qs[4]) - D(qs[2])) - (D(qs[5]) - D(qs[1])));
-          Kp += Pt.c1[0] * (8.0 * (D(rp[1]) - D(rp[-1])) - (D(rp[2]) - D(rp[-2]))) +
-                Pt.c1[1] * (8.0 * (D(rp[SY]) - D(rp[-SY])) - (D(rp[2 * SY]) - D(rp[-2 * SY]))) +
-                Pt.c1[2] * (8.0 * (D(qp[4]) - D(qp[2])) - (D(qp[5]) - D(qp[1])));
+          double c1[3] = {Pt.c1[0], Pt.c1[1], Pt.c1[2]};
+          if (ROT && Pt.rot)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) c1[a] += Pt.c1g[a][0] * i + Pt.c1g[a][1] * j + Pt.c1g[a][2] * z;
+          Ks += c1[0] * (8.0 * (D(rs[1]) - D(rs[-1])) - (D(rs[2]) - D(rs[-2]))) +
+                c1[1] * (8.0 * (D(rs[SY]) - D(rs[-SY])) - (D(rs[2 * SY]) - D(rs[-2 * SY]))) +
+                c1[2] * (8.0 * (D(qs[4]) - D(qs[2])) - (D(qs[5]) - D(qs[1])));
+          Kp += c1[0] * (8.0 * (D(rp[1]) - D(rp[-1])) - (D(rp[2]) - D(rp[-2]))) +
+                c1[1] * (8.0 * (D(rp[SY]) - D(rp[-SY])) - (D(rp[2 * SY]) - D(rp[-2 * SY]))) +
+                c1[2] * (8.0 * (D(qp[4]) - D(qp[2])) - (D(qp[5]) - D(qp[1])));
         }
       }
       // ---- RK4 stage combination (FP64)
@@ -401,9 +437,9 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
   }
 }
 
-template <int TX, int TY, bool FIXED>
+template <int TX, int TY, bool FIXED, bool ROT>
 __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_constant__ RhsArgs A) {
-  rhs_body<TX, TY, FIXED>(A, blockIdx.x);
+  rhs_body<TX, TY, FIXED, ROT>(A, blockIdx.x);
 }
 
 // Batched launch over independent instances: instance i owns the blocks
@@ -417,11 +453,11 @@ __device__ __forceinline__ int batch_instance(const int* __restrict__ blk0, int 
   return lo;
 }
 
-template <int TX, int TY, bool FIXED>
+template <int TX, int TY, bool FIXED, bool ROT>
 __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs_batch(const RhsArgs* __restrict__ As,
                                                                       const int* __restrict__ blk0, int ninst) {
   const int i = batch_instance(blk0, ninst);
-  rhs_body<TX, TY, FIXED>(As[i], blockIdx.x - blk0[i]);
+  rhs_body<TX, TY, FIXED, ROT>(As[i], blockIdx.x - blk0[i]);
 }
 
 // Host: TMA maps of one field buffer (4-D: x, y, plane, field).
@@ -448,28 +484,37 @@ bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile
   return r == CUDA_SUCCESS;
 }
 
-void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool fixed, void* stream) {
-  if (fixed) {
-    cudaFuncSetAttribute(k_rhs_batch<RHS_TX, RHS_TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RHS_SMEM);
-    k_rhs_batch<RHS_TX, RHS_TY, true><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(d_args, d_blk0,
-                                                                                                   ninst);
-  } else {
-    cudaFuncSetAttribute(k_rhs_batch<RHS_TX, RHS_TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RHS_SMEM);
-    k_rhs_batch<RHS_TX, RHS_TY, false><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(d_args, d_blk0,
-                                                                                                    ninst);
-  }
+template <bool FIXED, bool ROT>
+static void launch_rhs_batch_t(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, cudaStream_t s) {
+  cudaFuncSetAttribute(k_rhs_batch<RHS_TX, RHS_TY, FIXED, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)RHS_SMEM);
+  k_rhs_batch<RHS_TX, RHS_TY, FIXED, ROT><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, s>>>(d_args, d_blk0, ninst);
 }
 
-void launch_rhs(const RhsArgs& a, int blocks, bool fixed, void* stream) {
-  if (fixed) {
-    cudaFuncSetAttribute(k_rhs<RHS_TX, RHS_TY, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS_SMEM);
-    k_rhs<RHS_TX, RHS_TY, true><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_rhs<RHS_TX, RHS_TY, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS_SMEM);
-    k_rhs<RHS_TX, RHS_TY, false><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, (cudaStream_t)stream>>>(a);
-  }
+void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool fixed, bool rot,
+                      void* stream) {
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (fixed)
+    rot ? launch_rhs_batch_t<true, true>(d_args, d_blk0, ninst, blocks, s)
+        : launch_rhs_batch_t<true, false>(d_args, d_blk0, ninst, blocks, s);
+  else
+    rot ? launch_rhs_batch_t<false, true>(d_args, d_blk0, ninst, blocks, s)
+        : launch_rhs_batch_t<false, false>(d_args, d_blk0, ninst, blocks, s);
+}
+
+template <bool FIXED, bool ROT>
+static void launch_rhs_t(const RhsArgs& a, int blocks, cudaStream_t s) {
+  cudaFuncSetAttribute(k_rhs<RHS_TX, RHS_TY, FIXED, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)RHS_SMEM);
+  k_rhs<RHS_TX, RHS_TY, FIXED, ROT><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, s>>>(a);
+}
+
+void launch_rhs(const RhsArgs& a, int blocks, bool fixed, bool rot, void* stream) {
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (fixed)
+    rot ? launch_rhs_t<true, true>(a, blocks, s) : launch_rhs_t<true, false>(a, blocks, s);
+  else
+    rot ? launch_rhs_t<false, true>(a, blocks, s) : launch_rhs_t<false, false>(a, blocks, s);
 }
 
 }  // namespace mpw

@@ -115,6 +115,7 @@ __device__ __forceinline__ f2 ko_pair(const AxisSums& a) {
 
 }  // namespace
 
+template <bool ROT>
 __device__ __forceinline__ void rhs32_body(const RhsArgs& A, const int b) {
   constexpr int TX = RHS_TX, TY = RHS_TY, SY = TX + 6;
   extern __shared__ unsigned char smem32[];
@@ -180,10 +181,13 @@ __device__ __forceinline__ void rhs32_body(const RhsArgs& A, const int b) {
   float* OUT = reinterpret_cast<float*>(Pt.OUT);
   float* ACC = reinterpret_cast<float*>(Pt.ACC);
   // coefficients, rounded once to binary32
-  float c1[3], c2[3], ck[3];
+  float c1[3], c2[3], ck[3], c1z[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
-    c1[a] = (float)Pt.c1[a];
+    // a rotating frame's c1 is affine in the indices: this thread's column
+    // value, and its step per plane
+    c1[a] = (float)((ROT && Pt.rot) ? Pt.c1[a] + Pt.c1g[a][0] * i + Pt.c1g[a][1] * j : Pt.c1[a]);
+    c1z[a] = (ROT && Pt.rot) ? (float)Pt.c1g[a][2] : 0.0f;
     c2[a] = (float)Pt.c2[a];
     ck[a] = (float)Pt.cko[a];
   }
@@ -268,7 +272,11 @@ __device__ __forceinline__ void rhs32_body(const RhsArgs& A, const int b) {
         const f2 dx = d1_pair(r[-2], r[-1], r[1], r[2]);
         const f2 dy = d1_pair(r[-2 * SY], r[-SY], r[SY], r[2 * SY]);
         const f2 dz = d1_pair(q[1], q[2], q[4], q[5]);
-        K = fma2(pk(c1[2], c1[2]), dz, fma2(pk(c1[1], c1[1]), dy, fma2(pk(c1[0], c1[0]), dx, K)));
+        float w[3] = {c1[0], c1[1], c1[2]};
+        if (ROT)
+#pragma unroll
+          for (int a = 0; a < 3; ++a) w[a] = fmaf(c1z[a], (float)z, w[a]);
+        K = fma2(pk(w[2], w[2]), dz, fma2(pk(w[1], w[1]), dy, fma2(pk(w[0], w[0]), dx, K)));
       }
       const long long cz = g.at(i, j, z);
       if (live) {
@@ -297,11 +305,13 @@ __device__ __forceinline__ void rhs32_body(const RhsArgs& A, const int b) {
   }
 }
 
+template <bool ROT>
 __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid_constant__ RhsArgs A) {
-  rhs32_body(A, blockIdx.x);
+  rhs32_body<ROT>(A, blockIdx.x);
 }
 
 // Batched launch: instance i owns blocks [blk0[i], blk0[i + 1]), arguments As[i].
+template <bool ROT>
 __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32_batch(const RhsArgs* __restrict__ As,
                                                                           const int* __restrict__ blk0, int ninst) {
   int lo = 0, hi = ninst - 1;
@@ -309,17 +319,28 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32_batch(const 
     const int mid = (lo + hi + 1) >> 1;
     if ((int)blockIdx.x >= blk0[mid]) lo = mid; else hi = mid - 1;
   }
-  rhs32_body(As[lo], blockIdx.x - blk0[lo]);
+  rhs32_body<ROT>(As[lo], blockIdx.x - blk0[lo]);
 }
 
-void launch_rhs32_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, void* stream) {
-  cudaFuncSetAttribute(k_rhs32_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS32_SMEM);
-  k_rhs32_batch<<<blocks, RHS_TX * RHS_TY, RHS32_SMEM, (cudaStream_t)stream>>>(d_args, d_blk0, ninst);
+template <bool ROT>
+static void launch_rhs32_batch_t(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, cudaStream_t s) {
+  cudaFuncSetAttribute(k_rhs32_batch<ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS32_SMEM);
+  k_rhs32_batch<ROT><<<blocks, RHS_TX * RHS_TY, RHS32_SMEM, s>>>(d_args, d_blk0, ninst);
 }
 
-void launch_rhs32(const RhsArgs& a, int blocks, void* stream) {
-  cudaFuncSetAttribute(k_rhs32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS32_SMEM);
-  k_rhs32<<<blocks, RHS_TX * RHS_TY, RHS32_SMEM, (cudaStream_t)stream>>>(a);
+void launch_rhs32_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool rot, void* stream) {
+  rot ? launch_rhs32_batch_t<true>(d_args, d_blk0, ninst, blocks, (cudaStream_t)stream)
+      : launch_rhs32_batch_t<false>(d_args, d_blk0, ninst, blocks, (cudaStream_t)stream);
+}
+
+template <bool ROT>
+static void launch_rhs32_t(const RhsArgs& a, int blocks, cudaStream_t s) {
+  cudaFuncSetAttribute(k_rhs32<ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RHS32_SMEM);
+  k_rhs32<ROT><<<blocks, RHS_TX * RHS_TY, RHS32_SMEM, s>>>(a);
+}
+
+void launch_rhs32(const RhsArgs& a, int blocks, bool rot, void* stream) {
+  rot ? launch_rhs32_t<true>(a, blocks, (cudaStream_t)stream) : launch_rhs32_t<false>(a, blocks, (cudaStream_t)stream);
 }
 
 }  // namespace mpw

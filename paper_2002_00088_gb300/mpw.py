@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "MPW_OK", 1: "MPW_ERR_ARG", 2: "MPW_ERR_OVERLAP", 3: "MPW_ERR
                 9: "MPW_ERR_CUDA", 10: "MPW_ERR_STATE"}
 PATCH_GLOBAL, PATCH_LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
-MOTION_STATIC, MOTION_LINEAR, MOTION_CIRCULAR = 0, 1, 2
+MOTION_STATIC, MOTION_LINEAR, MOTION_CIRCULAR, MOTION_ROTATING = 0, 1, 2, 3
 ANALYTIC_GAUSS_SUM, ANALYTIC_PLANE_SUM, ANALYTIC_HARMONIC_POLY, ANALYTIC_PLANE_GAUSS = 0, 1, 2, 3
 FLAG_LIVE, FLAG_GHOST, FLAG_DEAD, FLAG_REVIVED = 0, 1, 2, 3
 NG = 3
