@@ -10,6 +10,10 @@ needed between steps.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--precision 64|32]
 
+--motion spinning runs the rotating-patch workload instead
+(workloads.spinning_gauss: global 256^3 plus four local 96^3 cubes at 2x
+spinning in place about seeded axes, the rotating local patch of Sec. 3.2).
+
 --precision 32 runs the binary32 precision workload instead
 (workloads.plane_gauss: periodic global 512^3 plus a static local 256^3 at 2x,
 plane wave k = (2,3,5) pi plus a Gaussian pulse).  Its line adds "accuracy":
@@ -62,6 +66,9 @@ def parse():
                          "batched launches, beside the same instances stepped one after the other")
     ap.add_argument("--max-global", type=int, default=192, help="--batch: largest global patch edge")
     ap.add_argument("--static", action="store_true", help="--batch: local patches do not move (graph replay)")
+    ap.add_argument("--motion", default="orbiting", choices=["orbiting", "spinning"],
+                    help="orbiting: translating local patches on circular orbits (default); spinning: the "
+                         "rotating-patch workload")
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="64: the FP64 workload (default); 32: the binary32 precision workload, with its error "
                          "against the closed form and the FP64 path on the same workload")
@@ -237,12 +244,17 @@ def precision_report(args, w, sim, mpw, stream, device):
             "f64_value": live * 4 * args.steps / (ms64 * 1e-3), "f64_ms_per_step": ms64 / args.steps}
 
 
+def fp64_workload(args):
+    from paper_2002_00088_gb300 import workloads as wl
+    return wl.spinning_gauss if args.motion == "spinning" else wl.orbiting_gauss
+
+
 def cpu_baseline(args, threads):
     """The oracle as it stands, on the host cores, on a bounded sample."""
     from oracle import pyoracle as po
     from paper_2002_00088_gb300 import workloads as wl
     # the precision workload is 6x larger: its oracle sample runs at half resolution
-    make = wl.plane_gauss if args.precision == 32 else wl.orbiting_gauss
+    make = wl.plane_gauss if args.precision == 32 else fp64_workload(args)
     w = make(scale=max(args.scale, args.cpu_sample_scale, 2 if args.precision == 32 else 1))
     o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
     for p in w.patches:
@@ -266,8 +278,8 @@ def run_reference(args):
     from oracle import pyoracle as po
     from paper_2002_00088_gb300 import workloads as wl
     threads = os.cpu_count() or 1
-    full = wl.orbiting_gauss(scale=args.scale)
-    w = wl.orbiting_gauss(scale=max(args.scale, args.ref_sample_scale))
+    full = fp64_workload(args)(scale=args.scale)
+    w = fp64_workload(args)(scale=max(args.scale, args.ref_sample_scale))
     o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
     for p in w.patches:
         o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
@@ -307,7 +319,7 @@ def run_ours(args):
     from paper_2002_00088_gb300 import workloads as wl
 
     f32 = args.precision == 32
-    w = wl.plane_gauss(scale=args.scale) if f32 else wl.orbiting_gauss(scale=args.scale)
+    w = wl.plane_gauss(scale=args.scale) if f32 else fp64_workload(args)(scale=args.scale)
     stream = torch.cuda.current_stream(local)
     sim = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream, precision=args.precision)
     for p in w.patches:

@@ -90,6 +90,10 @@ struct mpw_ctx {
   long long* d_rev = nullptr;  // queue of revived cells (REVIVE_CAP entries); its length lives in d_err[32]
   uint8_t* d_cov = nullptr;    // covered masks of the rotating patches' bounding boxes
   size_t cov_bytes = 0;
+  long long* d_glist = nullptr;  // effective ghosts of the rotating patches (same offsets as d_cov)
+  int* d_gcount = nullptr;       // their counts, MAX_PATCHES entries
+  std::vector<long long> glist_off;  // per local patch, from the last flag computation
+  bool glist_valid = false;          // lists match the current flags
   // Time whose closed form each global buffer's outer shell holds (NaN: none).
   // The RK4 substage times repeat (c = 0, 1/2, 1/2, 1, and t_n + dt starts the
   // next step), so half of the analytic shell evaluations become copies.
@@ -453,13 +457,23 @@ mpw_status run_flags(mpw_ctx* c, double t) {
     }
   }
   a.cov_off[a.nloc] = ncov;
+  c->glist_valid = false;
   if ((size_t)ncov > c->cov_bytes) {
     c->dfree(c->d_cov);
+    c->dfree(c->d_glist);
     c->d_cov = (uint8_t*)c->dalloc((size_t)ncov);
-    c->cov_bytes = c->d_cov ? (size_t)ncov : 0;
-    if (!c->d_cov) return set_err(MPW_ERR_CUDA, "covered-mask allocation of %lld bytes failed", ncov);
+    c->d_glist = (long long*)c->dalloc(sizeof(long long) * (size_t)ncov);
+    c->cov_bytes = c->d_cov && c->d_glist ? (size_t)ncov : 0;
+    if (!c->cov_bytes) return set_err(MPW_ERR_CUDA, "covered-mask allocation for %lld cells failed", ncov);
+  }
+  if (ncov > 0 && !c->d_gcount) {
+    c->d_gcount = (int*)c->dalloc(sizeof(int) * MAX_PATCHES);
+    if (!c->d_gcount) return set_err(MPW_ERR_CUDA, "ghost-list counter allocation failed");
   }
   a.cov = c->d_cov;
+  a.glist = ncov > 0 ? c->d_glist : nullptr;
+  a.gcount = ncov > 0 ? c->d_gcount : nullptr;
+  c->glist_off.assign(a.cov_off, a.cov_off + a.nloc);
   // With valid flags only cells inside an old or a new covered box can change:
   // visit the bounding box of each pair, merging regions until disjoint.
   a.nreg = 0;
@@ -526,6 +540,7 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   c->launch_end(MPW_KERNEL_FLAGS);
   CUDA_TRY(cudaGetLastError());
   c->flags_valid = true;
+  c->glist_valid = a.glist != nullptr;
   return MPW_OK;
 }
 
@@ -550,6 +565,33 @@ void choose_tile(const double ratio[3], int P, int thin, const int extent[3], in
     const bool ok = T[wa] <= fill_max_tile() && T[wb] <= fill_max_tile() && T[thin] <= NG &&
                     Dn[thin] <= fill_max_thin_donors() && r1 <= fill_cap_r1() && r2 <= fill_cap_r2();
     if (ok || (cd[0] == 1 && cd[1] == 1)) {
+      for (int a = 0; a < 3; ++a) td[a] = std::max(T[a], 1);
+      return;
+    }
+  }
+}
+
+// Tile extent for one slab of a rotated ghost shell: the largest candidate
+// whose donor box fits the shared-memory block of the fixed-point tile path.
+// The donor index is affine in the target index with slopes M_ab h_t[b] /
+// h_d[a]; the kernel widens the covered range by the window (P) and three
+// cells of margin.
+void choose_tile_affine(const InterpSeg& S, int P, int thin, const int extent[3], int td[3]) {
+  static const int cand[][2] = {{16, 16}, {16, 8}, {8, 16}, {8, 8}, {8, 4}, {4, 8}, {4, 4}, {2, 2}, {1, 1}};
+  const int wa = thin == 0 ? 1 : 0, wb = thin == 2 ? 1 : 2;
+  const long long cap = fill_cap_r1() + fill_cap_r2();
+  for (const auto& cd : cand) {
+    int T[3];
+    T[thin] = extent[thin];
+    T[wa] = std::min(cd[0], extent[wa]);
+    T[wb] = std::min(cd[1], extent[wb]);
+    long long vol = 1;
+    for (int a = 0; a < 3; ++a) {
+      double span = 0.0;
+      for (int b = 0; b < 3; ++b) span += std::fabs(S.M[3 * a + b]) * (T[b] - 1) * S.gt.h[b] / S.gd.h[a];
+      vol *= (long long)std::floor(span * (1.0 + 1e-12)) + 1 + P + 3;
+    }
+    if (vol <= cap || (cd[0] == 1 && cd[1] == 1)) {
       for (int a = 0; a < 3; ++a) td[a] = std::max(T[a], 1);
       return;
     }
@@ -599,7 +641,10 @@ int build_segment(InterpSeg& S, const int O0[3], const int O[3], int P) {
       for (int a = 0; a < 3; ++a) S.td[sl][a] = 1;
       continue;
     }
-    choose_tile(ratio, P, sl / 2 == 0 ? 2 : (sl / 2 == 1 ? 1 : 0), se[sl], S.td[sl]);
+    if (S.kind == SEG_AFFINE)
+      choose_tile_affine(S, P, sl / 2 == 0 ? 2 : (sl / 2 == 1 ? 1 : 0), se[sl], S.td[sl]);
+    else
+      choose_tile(ratio, P, sl / 2 == 0 ? 2 : (sl / 2 == 1 ? 1 : 0), se[sl], S.td[sl]);
     int n[3];
     for (int a = 0; a < 3; ++a) n[a] = (se[sl][a] + S.td[sl][a] - 1) / S.td[sl][a];
     S.tn[sl][0] = n[0];
@@ -608,6 +653,9 @@ int build_segment(InterpSeg& S, const int O0[3], const int O[3], int P) {
   }
   return blocks;
 }
+
+// CTAs that stride over one rotating patch's list of effective ghosts.
+constexpr int L2G_LIST_BLOCKS = 152;
 
 // Ghost fill of the stage buffer `b` at time t; clears the exponent slots of
 // buffer reset_buf (the output of the following RHS launch), if >= 0.
@@ -659,13 +707,10 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     const Frame f = frame(L.d, t);
     S.block0 = blocks;
     if (f.rot) {
-      // the effective ghosts of a rotated box: every cell of the covered
-      // bounding box whose flag says GHOST of this patch, mapped by
-      // X' = R^T X_B - R^T X0
-      S.kind = SEG_MASKED;
-      S.box = bx;
-      S.flags = c->d_flags;
-      S.want = FLAG_GHOST | ((q + 1) << 2);
+      // the effective ghosts of a rotated box, mapped by X' = R^T X_B - R^T X0:
+      // the list the cover-flag kernel wrote, or (flags set through the ABI)
+      // every cell of the covered bounding box whose flag says GHOST of this
+      // patch
       for (int r = 0; r < 3; ++r) {
         S.shift[r] = 0.0;
         for (int k = 0; k < 3; ++k) {
@@ -673,6 +718,18 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
           S.shift[r] -= f.R[3 * k + r] * f.X0[k];
         }
       }
+      if (c->glist_valid && q < (int)c->glist_off.size()) {
+        S.kind = SEG_LIST;
+        S.list = c->d_glist + c->glist_off[q];
+        S.count = c->d_gcount + q;
+        S.list_blocks = L2G_LIST_BLOCKS;
+        blocks += L2G_LIST_BLOCKS;
+        continue;
+      }
+      S.kind = SEG_MASKED;
+      S.box = bx;
+      S.flags = c->d_flags;
+      S.want = FLAG_GHOST | ((q + 1) << 2);
       const long long vol = (long long)(bx.hi[0] - bx.lo[0] + 1) * (bx.hi[1] - bx.lo[1] + 1) * (bx.hi[2] - bx.lo[2] + 1);
       blocks += (int)((vol + fill_threads() - 1) / fill_threads());
       continue;
@@ -692,7 +749,8 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     S.D = g.buf(b);
     S.gd = g.g;
     const Frame f = frame(L.d, t);
-    // a rotated ghost shell takes the direct sums through X_B = R X' + X0
+    // a rotated ghost shell: per-point sums through X_B = R X' + X0 (fixed-point
+    // tiles with the donor box in shared memory, or direct FP64 sums)
     S.kind = f.rot ? SEG_AFFINE : SEG_SHELL;
     for (int e = 0; e < 9; ++e) S.M[e] = f.R[e];
     for (int k = 0; k < 3; ++k) S.shift[k] = f.X0[k];
@@ -934,6 +992,8 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_expo);
   c->dfree(c->d_rev);
   c->dfree(c->d_cov);
+  c->dfree(c->d_glist);
+  c->dfree(c->d_gcount);
   c->dfree(c->d_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& v : c->ev)
@@ -1269,6 +1329,7 @@ mpw_status mpw_set_flags(mpw_ctx* c, const uint8_t* flags) {
   c->boxes.assign(c->p.size() - 1, Box{});
   for (size_t q = 1; q < c->p.size(); ++q) c->boxes[q - 1] = covered_box(g, c->p[q], c->t);
   c->flags_valid = true;
+  c->glist_valid = false;  // the ghost lists come from the flags kernel only
   return MPW_OK;
 }
 

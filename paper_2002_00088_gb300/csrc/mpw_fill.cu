@@ -298,6 +298,58 @@ __device__ __forceinline__ void donor_position(const InterpSeg& S, double x, dou
   }
 }
 
+// Position of the point in the donor's index units, per axis.
+__device__ __forceinline__ void donor_indices(const InterpSeg& S, int i, int j, int k, double sidx[3]) {
+  double p[3];
+  donor_position(S, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
+                 S.gt.lo[2] + (k + 0.5) * S.gt.h[2], p[0], p[1], p[2]);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) sidx[a] = (p[a] - S.gd.lo[a]) / S.gd.h[a] - 0.5;
+}
+
+// Fixed-point tensor sum of one point under a rotated map (Eq. Pijk with
+// the separable passes' arithmetic: x rows, then y, then z, each an Acc3
+// contraction against weights on 2^59).  fetch(f, x, y, z) returns the
+// donor at window-relative offsets as a split fixed-point value; out[f] is
+// on the scale of the donor values.
+template <int P, typename Fetch>
+__device__ __forceinline__ void contract_point_fixed(const int2 (&wx)[P], const int2 (&wy)[P], const int2 (&wz)[P],
+                                                     Fetch fetch, long long out[2]) {
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    Acc3 az;
+#pragma unroll
+    for (int c = 0; c < P; ++c) {
+      Acc3 ay;
+#pragma unroll
+      for (int b = 0; b < P; ++b) {
+        Acc3 ax;
+#pragma unroll
+        for (int a = 0; a < P; ++a) ax.mac(fetch(f, a, b, c), wx[a]);
+        ay.mac(split31(ax.value()), wy[b]);
+      }
+      az.mac(split31(ay.value()), wz[c]);
+    }
+    out[f] = az.value();
+  }
+}
+
+// 1-D weights of the three axes on 2^59 (split), and the window starts.
+template <int P>
+__device__ __forceinline__ void fixed_weights(const double sidx[3], int2 (&wx)[P], int2 (&wy)[P], int2 (&wz)[P],
+                                              int st[3]) {
+  double w[P];
+  st[0] = lagrange_weights<P>(sidx[0], w);
+#pragma unroll
+  for (int m = 0; m < P; ++m) wx[m] = split31(__double2ll_rn(w[m] * 0x1p59));
+  st[1] = lagrange_weights<P>(sidx[1], w);
+#pragma unroll
+  for (int m = 0; m < P; ++m) wy[m] = split31(__double2ll_rn(w[m] * 0x1p59));
+  st[2] = lagrange_weights<P>(sidx[2], w);
+#pragma unroll
+  for (int m = 0; m < P; ++m) wz[m] = split31(__double2ll_rn(w[m] * 0x1p59));
+}
+
 // Direct tensor sums (Eq. Pijk) point by point for the targets of a tile;
 // reports uninterpolable points.
 template <int P, typename ST>
@@ -322,9 +374,61 @@ __device__ __noinline__ void direct_points(const FillArgs& A, const InterpSeg& S
   }
 }
 
-// Local-to-Global under a rotating map: one thread per cell of the covered
-// bounding box; the cells whose flag byte is S.want (effective ghosts of
-// this patch) take the direct sum from the local patch.
+// Local-to-Global of one global cell (i, j, k) under a rotating map:
+// fixed point with the donors gathered and converted on the fly, or the
+// direct FP64 sum (binary32 storage, native FP64, non-finite donors).
+template <int P, typename ST>
+__device__ __forceinline__ void l2g_point(const FillArgs& A, const InterpSeg& S, int i, int j, int k, int& e0,
+                                          int& e1) {
+  constexpr bool F32 = sizeof(ST) == 4;
+  const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+  const bool fx = !F32 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
+  if (fx) {
+    double sidx[3];
+    donor_indices(S, i, j, k, sidx);
+    int2 wx[P], wy[P], wz[P];
+    int st[3];
+    fixed_weights<P>(sidx, wx, wy, wz, st);
+    if (st[0] < 0 || st[1] < 0 || st[2] < 0 || st[0] + P > S.gd.n[0] || st[1] + P > S.gd.n[1] ||
+        st[2] + P > S.gd.n[2]) {
+      atomicOr(A.err, ERR_UNFILLED);
+      return;
+    }
+    const int E[2] = {max(dslot[0], 64), max(dslot[1], 64)};
+    const double* D = reinterpret_cast<const double*>(S.D);
+    const long long base = S.gd.at(st[0], st[1], st[2]);
+    long long out[2];
+    contract_point_fixed<P>(wx, wy, wz, [&](int f, int a, int b, int c) {
+      return split31(to_fixed(D[f * S.gd.vol + base + c * S.gd.plane + b * S.gd.px + a], E[f]) * 64);
+    }, out);
+    const double v0 = (double)out[0] * __longlong_as_double((long long)(E[0] - 58) << 52);
+    const double v1 = (double)out[1] * __longlong_as_double((long long)(E[1] - 58) << 52);
+    double* Tt = reinterpret_cast<double*>(S.T);
+    const long long c = S.gt.at(i, j, k);
+    Tt[c] = v0;
+    Tt[c + S.gt.vol] = v1;
+    e0 = max(e0, biased_exponent(v0));
+    e1 = max(e1, biased_exponent(v1));
+    return;
+  }
+  double v0, v1, px, py, pz;
+  donor_position(S, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
+                 S.gt.lo[2] + (k + 0.5) * S.gt.h[2], px, py, pz);
+  if (!interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, px, py, pz, v0, v1)) {
+    atomicOr(A.err, ERR_UNFILLED);
+    return;
+  }
+  ST* Tt = reinterpret_cast<ST*>(S.T);
+  const long long c = S.gt.at(i, j, k);
+  Tt[c] = (ST)v0;
+  Tt[c + S.gt.vol] = (ST)v1;
+  e0 = max(e0, biased_exponent(v0));
+  e1 = max(e1, biased_exponent(v1));
+}
+
+// Local-to-Global under a rotating map, from the cover flags: one thread per
+// cell of the covered bounding box; the cells whose flag byte is S.want
+// (effective ghosts of this patch) are filled.
 template <int P, typename ST>
 __device__ __noinline__ void masked_block(const FillArgs& A, const InterpSeg& S, int r) {
   constexpr bool F32 = sizeof(ST) == 4;
@@ -335,23 +439,109 @@ __device__ __noinline__ void masked_block(const FillArgs& A, const InterpSeg& S,
   if (idx < (long long)w0 * w1 * w2) {
     const int i = b.lo[0] + (int)(idx % w0), j = b.lo[1] + (int)((idx / w0) % w1),
               k = b.lo[2] + (int)(idx / ((long long)w0 * w1));
-    if (S.flags[((long long)k * S.gt.n[1] + j) * S.gt.n[0] + i] == S.want) {
-      double v0, v1, px, py, pz;
-      donor_position(S, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
-                     S.gt.lo[2] + (k + 0.5) * S.gt.h[2], px, py, pz);
-      if (interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, px, py, pz, v0, v1)) {
-        ST* Tt = reinterpret_cast<ST*>(S.T);
-        const long long c = S.gt.at(i, j, k);
-        Tt[c] = (ST)v0;
-        Tt[c + S.gt.vol] = (ST)v1;
-        e0 = biased_exponent(v0);
-        e1 = biased_exponent(v1);
-      } else {
-        atomicOr(A.err, ERR_UNFILLED);
-      }
+    if (S.flags[((long long)k * S.gt.n[1] + j) * S.gt.n[0] + i] == S.want) l2g_point<P, ST>(A, S, i, j, k, e0, e1);
+  }
+  if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, e0, e1);
+}
+
+// Local-to-Global under a rotating map, from the list of the patch's
+// effective ghosts written by the cover-flag kernel (dense warps).
+template <int P, typename ST>
+__device__ __noinline__ void list_block(const FillArgs& A, const InterpSeg& S, int r) {
+  constexpr bool F32 = sizeof(ST) == 4;
+  const int count = *S.count;
+  int e0 = 0, e1 = 0;
+  for (int base = r * FILL_THREADS; base < count; base += S.list_blocks * FILL_THREADS) {
+    const int e = base + threadIdx.x;
+    if (e < count) {
+      const long long idx = S.list[e];
+      const int i = (int)(idx % S.gt.n[0]);
+      const long long rr = idx / S.gt.n[0];
+      l2g_point<P, ST>(A, S, i, (int)(rr % S.gt.n[1]), (int)(rr / S.gt.n[1]), e0, e1);
     }
   }
   if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, e0, e1);
+}
+
+// A tile of a rotated ghost shell in fixed point: the donor box that the
+// tile's windows cover (the donor index is affine in the target indices, so
+// its range follows from the tile's corners, widened by one cell against
+// rounding) is converted once into shared memory; every target then takes
+// its own weights and the fixed-point sum from there.  Returns false, with
+// nothing written, when the box does not fit or leaves the donor interior.
+template <int P>
+__device__ __noinline__ bool affine_tile_fixed(const FillArgs& A, const InterpSeg& S, const int org[3], const int T[3], int Es,
+                                  int Ep, double* sm, int emax[2]) {
+  __shared__ int s_box[7];
+  constexpr int CAPB = CAP_R1 + CAP_R2;  // donors per field
+  if (threadIdx.x == 0) {
+    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+    for (int c = 0; c < 8; ++c) {
+      double sidx[3];
+      donor_indices(S, org[0] + ((c & 1) ? T[0] - 1 : 0), org[1] + ((c & 2) ? T[1] - 1 : 0),
+                    org[2] + ((c & 4) ? T[2] - 1 : 0), sidx);
+      for (int a = 0; a < 3; ++a) {
+        lo[a] = fmin(lo[a], sidx[a]);
+        hi[a] = fmax(hi[a], sidx[a]);
+      }
+    }
+    bool ok = true;
+    long long vol = 1;
+    for (int a = 0; a < 3; ++a) {
+      const int d0 = (int)floor(lo[a]) - 3, d1 = (int)floor(hi[a]) + P - 1;  // window starts floor(s) - 2, +-1
+      s_box[a] = max(d0, 0);
+      s_box[3 + a] = min(d1, S.gd.n[a] - 1) - s_box[a] + 1;
+      ok = ok && s_box[3 + a] > 0;
+      vol *= max(s_box[3 + a], 1);
+    }
+    s_box[6] = ok && vol <= CAPB;
+  }
+  __syncthreads();
+  if (!s_box[6]) return false;
+  const int D0[3] = {s_box[0], s_box[1], s_box[2]}, Dn[3] = {s_box[3], s_box[4], s_box[5]};
+  const int nb = Dn[0] * Dn[1] * Dn[2], bxy = Dn[0] * Dn[1];
+  int2* blk = reinterpret_cast<int2*>(sm);
+  const double* D = reinterpret_cast<const double*>(S.D);
+  const int E[2] = {max(Es, 64), max(Ep, 64)};
+  for (int e = threadIdx.x; e < 2 * nb; e += FILL_THREADS) {
+    const int f = e >= nb;
+    const int r = e - f * nb;
+    const int x = r % Dn[0], y = (r / Dn[0]) % Dn[1], z = r / bxy;
+    blk[f * CAPB + r] =
+        split31(to_fixed(D[f * S.gd.vol + S.gd.at(D0[0] + x, D0[1] + y, D0[2] + z)], E[f]) * 64);
+  }
+  __syncthreads();
+  double* Tt = reinterpret_cast<double*>(S.T);
+  const int ntar = T[0] * T[1] * T[2];
+  const double p2[2] = {__longlong_as_double((long long)(E[0] - 58) << 52),
+                        __longlong_as_double((long long)(E[1] - 58) << 52)};
+  for (int e = threadIdx.x; e < ntar; e += FILL_THREADS) {
+    const int i = org[0] + e % T[0], j = org[1] + (e / T[0]) % T[1], k = org[2] + e / (T[0] * T[1]);
+    double sidx[3];
+    donor_indices(S, i, j, k, sidx);
+    int2 wx[P], wy[P], wz[P];
+    int st[3];
+    fixed_weights<P>(sidx, wx, wy, wz, st);
+    const int rx = st[0] - D0[0], ry = st[1] - D0[1], rz = st[2] - D0[2];
+    if (rx < 0 || ry < 0 || rz < 0 || rx + P > Dn[0] || ry + P > Dn[1] || rz + P > Dn[2]) {
+      // outside the staged box (only possible at the donor's faces): unfilled
+      atomicOr(A.err, ERR_UNFILLED);
+      continue;
+    }
+    const int2* b0 = blk + rz * bxy + ry * Dn[0] + rx;
+    long long out[2];
+    contract_point_fixed<P>(wx, wy, wz, [&](int f, int a, int b, int c) {
+      return b0[f * CAPB + c * bxy + b * Dn[0] + a];
+    }, out);
+    const long long cc = S.gt.at(i, j, k);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const double v = (double)out[f] * p2[f];
+      Tt[cc + f * S.gt.vol] = v;
+      emax[f] = max(emax[f], biased_exponent(v));
+    }
+  }
+  return true;
 }
 
 // One interpolation tile.  ST is the storage type of the field buffers:
@@ -375,7 +565,10 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
   if (S.kind == SEG_AFFINE) {
     // rotated target grid: the 1-D weights differ from point to point
     int emax[2] = {0, 0};
-    direct_points<P, ST>(A, S, org, T, emax);
+    const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+    const bool fx = !F32 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
+    if (!fx || !affine_tile_fixed<P>(A, S, org, T, dslot[0], dslot[1], sm, emax))
+      direct_points<P, ST>(A, S, org, T, emax);
     if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, emax[0], emax[1]);
     return;
   }
@@ -561,6 +754,10 @@ __device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
     masked_block<P, ST>(A, S, r);
     return;
   }
+  if (S.kind == SEG_LIST) {
+    list_block<P, ST>(A, S, r);
+    return;
+  }
   int sl = 0;
   while (sl < 5 && r >= S.slab_block0[sl + 1]) ++sl;
   r -= S.slab_block0[sl];
@@ -577,13 +774,13 @@ __device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
 }
 
 template <int P, typename ST>
-__global__ void __launch_bounds__(FILL_THREADS) k_fill(const __grid_constant__ FillArgs A) {
+__global__ void __launch_bounds__(FILL_THREADS, 2) k_fill(const __grid_constant__ FillArgs A) {
   fill_body<P, ST>(A, blockIdx.x);
 }
 
 // Batched launch: instance i owns blocks [blk0[i], blk0[i + 1]), arguments As[i].
 template <int P, typename ST>
-__global__ void __launch_bounds__(FILL_THREADS) k_fill_batch(const FillArgs* __restrict__ As,
+__global__ void __launch_bounds__(FILL_THREADS, 2) k_fill_batch(const FillArgs* __restrict__ As,
                                                              const int* __restrict__ blk0, int ninst) {
   int lo = 0, hi = ninst - 1;
   while (lo < hi) {

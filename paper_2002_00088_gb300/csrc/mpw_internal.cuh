@@ -101,13 +101,17 @@ struct RhsArgs {
 // One interpolation target set: the hollow box shell (walls NG thick) of a
 // target patch, filled from a donor patch.  The shell is cut into six slabs
 // (z-, z+, y-, y+, x-, x+), each tiled by boxes of td targets.
-enum { SEG_SHELL = 0, SEG_AFFINE = 1, SEG_MASKED = 2 };
+enum { SEG_SHELL = 0, SEG_AFFINE = 1, SEG_MASKED = 2, SEG_LIST = 3 };
 
 struct InterpSeg {
   int kind;            // SEG_SHELL: hollow box under translation (separable passes);
                        // SEG_AFFINE: hollow box under a rotating map (direct sums);
-                       // SEG_MASKED: the global cells of flag `want` inside `box`
-  double M[9];         // SEG_AFFINE / SEG_MASKED: donor position = M target position + shift
+                       // SEG_MASKED: the global cells of flag `want` inside `box`;
+                       // SEG_LIST: the global cells listed by the cover-flag kernel
+  double M[9];         // SEG_AFFINE / SEG_MASKED / SEG_LIST: donor position = M target position + shift
+  const long long* list;  // SEG_LIST: linear global cell indices, *count of them
+  const int* count;
+  int list_blocks;     // SEG_LIST: CTAs striding over the list
   Box box;             // SEG_MASKED: target cells to test (global indices)
   const uint8_t* flags;
   int want;            // flag byte of the cells to fill (state | owner << 2)
@@ -174,6 +178,10 @@ struct FlagArgs {
   double lhi[MAX_PATCHES][3];  // upper corner of the live box (the descriptor's hi)
   uint8_t* cov;
   long long cov_off[MAX_PATCHES + 1];
+  // effective ghosts of each rotating patch, listed for Local-to-Global:
+  // glist[cov_off[q] ...], gcount[q] entries (null: no lists)
+  long long* glist;
+  int* gcount;
   int P;
   int* err;
   int* expo;

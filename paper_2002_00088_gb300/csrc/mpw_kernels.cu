@@ -74,29 +74,34 @@ __device__ __forceinline__ void cell_in_local(const FlagArgs& A, int q, int i, i
 template <int P, typename ST>
 __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs A) {
   long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  int i, j, k;
+  int i = 0, j = 0, k = 0;
+  bool valid;
   if (A.nreg == 0) {
     const long long N = (long long)A.n[0] * A.n[1] * A.n[2];
-    if (idx >= N) return;
-    i = (int)(idx % A.n[0]);
-    const long long r = idx / A.n[0];
-    j = (int)(r % A.n[1]);
-    k = (int)(r / A.n[1]);
+    valid = idx < N;
+    if (valid) {
+      i = (int)(idx % A.n[0]);
+      const long long r = idx / A.n[0];
+      j = (int)(r % A.n[1]);
+      k = (int)(r / A.n[1]);
+    }
   } else {
-    if (idx >= A.reg_begin[A.nreg]) return;
-    int g = 0;
-    while (idx >= A.reg_begin[g + 1]) ++g;
-    idx -= A.reg_begin[g];
-    const Box& R = A.reg[g];
-    const int w0 = R.hi[0] - R.lo[0] + 1, w1 = R.hi[1] - R.lo[1] + 1;
-    i = R.lo[0] + (int)(idx % w0);
-    const long long r = idx / w0;
-    j = R.lo[1] + (int)(r % w1);
-    k = R.lo[2] + (int)(r / w1);
-    idx = ((long long)k * A.n[1] + j) * A.n[0] + i;
+    valid = idx < A.reg_begin[A.nreg];
+    if (valid) {
+      int g = 0;
+      while (idx >= A.reg_begin[g + 1]) ++g;
+      idx -= A.reg_begin[g];
+      const Box& R = A.reg[g];
+      const int w0 = R.hi[0] - R.lo[0] + 1, w1 = R.hi[1] - R.lo[1] + 1;
+      i = R.lo[0] + (int)(idx % w0);
+      const long long r = idx / w0;
+      j = R.lo[1] + (int)(r % w1);
+      k = R.lo[2] + (int)(r / w1);
+      idx = ((long long)k * A.n[1] + j) * A.n[0] + i;
+    }
   }
   int owner = 0, d = 0;
-  for (int q = 0; q < A.nloc; ++q) {
+  for (int q = 0; valid && q < A.nloc; ++q) {
     const Box& b = A.box[q];
     if (i >= b.lo[0] && i <= b.hi[0] && j >= b.lo[1] && j <= b.hi[1] && k >= b.lo[2] && k <= b.hi[2]) {
       if (A.rot[q]) {
@@ -121,6 +126,19 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
       break;
     }
   }
+  // effective ghosts of a rotating patch join that patch's list, one atomic
+  // per warp and patch (every lane of the warp takes part)
+  const bool ghost_rot = valid && A.glist && owner > 0 && A.rot[owner - 1] && d > A.buffer && d <= A.buffer + NG;
+  const int gq = ghost_rot ? owner - 1 : -1;
+  const unsigned peers = __match_any_sync(0xffffffffu, gq);
+  if (gq >= 0) {
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader) base = atomicAdd(&A.gcount[gq], __popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    A.glist[A.cov_off[gq] + base + __popc(peers & ((1u << lane) - 1u))] = idx;
+  }
+  if (!valid) return;
   int st = (owner == 0 || d <= A.buffer) ? FLAG_LIVE : (d <= A.buffer + NG ? FLAG_GHOST : FLAG_DEAD);
   if (A.old_valid && st == FLAG_LIVE) {
     const int os = A.flags[idx] & 3;
@@ -210,6 +228,7 @@ int launch_flags(const FlagArgs& a, void* stream) {
   if (N <= 0) return 0;
   const cudaStream_t s = (cudaStream_t)stream;
   cudaMemsetAsync(a.rev_count, 0, sizeof(int), s);
+  if (a.gcount) cudaMemsetAsync(a.gcount, 0, sizeof(int) * MAX_PATCHES, s);
   const unsigned blocks = (unsigned)((N + 255) / 256);
   // the revival kernel walks the queue with a fixed grid (its length is
   // known on the device only); empty queues cost one short launch

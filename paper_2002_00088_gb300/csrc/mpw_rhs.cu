@@ -65,18 +65,19 @@ __device__ void setup_terms(Terms& T, const RhsPatch& P, int Es_raw, int Ep_raw,
   T.Ep = Ep;
   double cs[7], cp[9];
   int es[7], ep[9];
-  // largest |c1_a| over the patch (a rotating frame's c1 is affine in the
-  // indices, so its extremes sit at the corners)
-  double c1m[3];
-  for (int a = 0; a < 3; ++a) {
-    c1m[a] = fabs(P.c1[a]);
-    if (P.rot)
+  // D1 coefficients for the scales: c1 itself, or on a rotating patch the
+  // largest |c1_a| over the patch (c1 is then affine in the indices, so its
+  // extremes sit at the corners)
+  double c1m[3] = {P.c1[0], P.c1[1], P.c1[2]};
+  if (P.rot)
+    for (int a = 0; a < 3; ++a) {
+      c1m[a] = fabs(P.c1[a]);
       for (int c = 0; c < 8; ++c) {
         double v = P.c1[a];
         for (int b = 0; b < 3; ++b) v += P.c1g[a][b] * (((c >> b) & 1) ? P.g.n[b] - 1 : 0);
         c1m[a] = fmax(c1m[a], fabs(v));
       }
-  }
+    }
   cs[0] = 1.0;
   es[0] = Ep;
   for (int a = 0; a < 3; ++a) {
@@ -98,15 +99,18 @@ __device__ void setup_terms(Terms& T, const RhsPatch& P, int Es_raw, int Ep_raw,
   T.Sp = Sp;
   for (int t = 0; t < 7; ++t) T.ms[t] = term_multiplier(cs[t], es[t], Ss);
   for (int t = 0; t < 9; ++t) T.mp[t] = term_multiplier(cp[t], ep[t], Sp);
-  // D1 multipliers: c1 at cell (0, 0, 0), and its steps per index
-  for (int a = 0; a < 3; ++a) {
-    T.ms[4 + a] = term_multiplier(P.c1[a], Es, Ss);
-    T.mp[6 + a] = term_multiplier(P.c1[a], Ep, Sp);
-    for (int b = 0; b < 3; ++b) {
-      T.gs[a][b] = P.rot ? term_multiplier(P.c1g[a][b], Es, Ss) : 0;
-      T.gp[a][b] = P.rot ? term_multiplier(P.c1g[a][b], Ep, Sp) : 0;
+  // rotating frame: D1 multipliers of c1 at cell (0, 0, 0), and their steps
+  // per index (thread 0 of every CTA runs this: the FP64 work stays off the
+  // translating patches)
+  if (P.rot)
+    for (int a = 0; a < 3; ++a) {
+      T.ms[4 + a] = term_multiplier(P.c1[a], Es, Ss);
+      T.mp[6 + a] = term_multiplier(P.c1[a], Ep, Sp);
+      for (int b = 0; b < 3; ++b) {
+        T.gs[a][b] = term_multiplier(P.c1g[a][b], Es, Ss);
+        T.gp[a][b] = term_multiplier(P.c1g[a][b], Ep, Sp);
+      }
     }
-  }
   // K = k 2^S with k the exact int64 sum: the stage updates use alpha 2^S and
   // beta 2^S (exact scalings), or the FP64 path when they would leave the
   // normal range
@@ -333,15 +337,13 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
                mulhi(yp3 - 6 * yp2 + 15 * yp1 - 20 * v0, T.mp[4]) +
                mulhi(zp3 - 6 * zp2 + 15 * zp1 - 20 * v0, T.mp[5]);
         }
-        if (Pt.moving) {
-          long long m[6] = {T.ms[4], T.ms[5], T.ms[6], T.mp[6], T.mp[7], T.mp[8]};
-          if (ROT && Pt.rot) {
-            // multipliers of c1_a(i, j, z), affine in the indices
+        if (ROT && Pt.rot) {
+          // multipliers of c1_a(i, j, z), affine in the indices
+          long long m[6];
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              m[a] += T.gs[a][0] * i + T.gs[a][1] * j + T.gs[a][2] * z;
-              m[3 + a] += T.gp[a][0] * i + T.gp[a][1] * j + T.gp[a][2] * z;
-            }
+          for (int a = 0; a < 3; ++a) {
+            m[a] = T.ms[4 + a] + T.gs[a][0] * i + T.gs[a][1] * j + T.gs[a][2] * z;
+            m[3 + a] = T.mp[6 + a] + T.gp[a][0] * i + T.gp[a][1] * j + T.gp[a][2] * z;
           }
           ks += mulhi(8 * (rs[1] - rs[-1]) - (rs[2] - rs[-2]), m[0]) +
                 mulhi(8 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY]), m[1]) +
@@ -349,6 +351,13 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
           kp += mulhi(8 * (rp[1] - rp[-1]) - (rp[2] - rp[-2]), m[3]) +
                 mulhi(8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]), m[4]) +
                 mulhi(8 * (qp[4] - qp[2]) - (qp[5] - qp[1]), m[5]);
+        } else if (Pt.moving) {
+          ks += mulhi(8 * (rs[1] - rs[-1]) - (rs[2] - rs[-2]), T.ms[4]) +
+                mulhi(8 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY]), T.ms[5]) +
+                mulhi(8 * (qs[4] - qs[2]) - (qs[5] - qs[1]), T.ms[6]);
+          kp += mulhi(8 * (rp[1] - rp[-1]) - (rp[2] - rp[-2]), T.mp[6]) +
+                mulhi(8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]), T.mp[7]) +
+                mulhi(8 * (qp[4] - qp[2]) - (qp[5] - qp[1]), T.mp[8]);
         }
         Ks = (double)ks;  // K_psi / 2^Ss, rounded once
         Kp = (double)kp;

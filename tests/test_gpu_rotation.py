@@ -177,3 +177,27 @@ def test_rotating_validation(mpw_lib):
     g2.fill_analytic(0.0)
     with pytest.raises(mpw_lib.MpwError):
         g2.step(w2.dt, 1)
+
+
+@pytest.mark.parametrize("arith", ARITH)
+def test_rotating_fill_with_flags_set_through_the_abi(mpw_lib, arith):
+    """Flags handed in through mpw_set_flags (no ghost lists from the flags
+    kernel): Local-to-Global scans the covered bounding box instead."""
+    w = wl.spinning_gauss(scale=2)
+    o = oracle_from(w, THREADS)
+    g = gpu_from(mpw_lib, w, arith=arith)
+    seed_both(o, g, len(w.patches))
+    o.compute_flags()
+    g.set_flags(o.get_flags())
+    t = 0.021
+    o.fill_ghosts(t)
+    g.fill_ghosts(t)
+    got = [g.get_padded(q) for q in range(len(w.patches))]
+    want = [o.get_padded(q, which=1) for q in range(len(w.patches))]
+    scale = max(np.nanmax(np.abs(b[f])) for b in want for f in range(2))
+    for f in range(2):
+        for q in range(len(w.patches)):
+            a, b = got[q][f], want[q][f]
+            m = np.isfinite(b)
+            err = np.abs(a[m] - b[m]).max() / scale
+            assert err <= 1e-13, f"patch {q} field {f}: {err:.3e}"
