@@ -598,6 +598,20 @@ void choose_tile_affine(const InterpSeg& S, int P, int thin, const int extent[3]
   }
 }
 
+// Affine map of a rotated segment from target cell indices to donor index
+// coordinates: s_a = sum_b (M_ab h_t[b] / h_d[a]) idx_b
+//                    + (sum_b M_ab (lo_t[b] + h_t[b] / 2) + shift_a - lo_d[a]) / h_d[a] - 1/2.
+void set_index_map(InterpSeg& S) {
+  for (int a = 0; a < 3; ++a) {
+    double c = S.shift[a];
+    for (int b = 0; b < 3; ++b) {
+      S.sidx[a][b] = S.M[3 * a + b] * S.gt.h[b] / S.gd.h[a];
+      c += S.M[3 * a + b] * (S.gt.lo[b] + 0.5 * S.gt.h[b]);
+    }
+    S.sidx[a][3] = (c - S.gd.lo[a]) / S.gd.h[a] - 0.5;
+  }
+}
+
 // Cut the hollow box (origin O0, extent O, walls NG thick) into six slabs and
 // tile them; returns the number of CTAs.
 int build_segment(InterpSeg& S, const int O0[3], const int O[3], int P) {
@@ -718,6 +732,7 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
           S.shift[r] -= f.R[3 * k + r] * f.X0[k];
         }
       }
+      set_index_map(S);
       if (c->glist_valid && q < (int)c->glist_off.size()) {
         S.kind = SEG_LIST;
         S.list = c->d_glist + c->glist_off[q];
@@ -754,6 +769,7 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     S.kind = f.rot ? SEG_AFFINE : SEG_SHELL;
     for (int e = 0; e < 9; ++e) S.M[e] = f.R[e];
     for (int k = 0; k < 3; ++k) S.shift[k] = f.X0[k];
+    if (f.rot) set_index_map(S);
     const int O0[3] = {-NG, -NG, -NG};
     const int O[3] = {L.d.n[0] + 2 * NG, L.d.n[1] + 2 * NG, L.d.n[2] + 2 * NG};
     S.block0 = blocks;

@@ -298,13 +298,52 @@ __device__ __forceinline__ void donor_position(const InterpSeg& S, double x, dou
   }
 }
 
-// Position of the point in the donor's index units, per axis.
+// Position of target cell (i, j, k) in the donor's index units, per axis,
+// from the segment's affine index map (rotated segments).
 __device__ __forceinline__ void donor_indices(const InterpSeg& S, int i, int j, int k, double sidx[3]) {
-  double p[3];
-  donor_position(S, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
-                 S.gt.lo[2] + (k + 0.5) * S.gt.h[2], p[0], p[1], p[2]);
 #pragma unroll
-  for (int a = 0; a < 3; ++a) sidx[a] = (p[a] - S.gd.lo[a]) / S.gd.h[a] - 0.5;
+  for (int a = 0; a < 3; ++a)
+    sidx[a] = fma(S.sidx[a][0], (double)i, fma(S.sidx[a][1], (double)j, fma(S.sidx[a][2], (double)k, S.sidx[a][3])));
+}
+
+// (a b) / 2^56 and (a b) / 2^61, rounded toward minus infinity, from the
+// 128-bit product (the quotients must fit in int64).
+__device__ __forceinline__ long long mul56(long long a, long long b) {
+  return (long long)(((unsigned long long)__mul64hi(a, b) << 8) | ((unsigned long long)(a * b) >> 56));
+}
+__device__ __forceinline__ long long mul61(long long a, long long b) {
+  return (long long)(((unsigned long long)__mul64hi(a, b) << 3) | ((unsigned long long)(a * b) >> 61));
+}
+
+// 1-D Lagrange weights of Eq. (Pijk) on 2^59 (split) for the window that
+// starts two nodes below floor(s), in int64 arithmetic (the FP64 pipe of
+// GB300 issues at a small fraction of the integer rate): u = s - floor(s) on
+// 2^56, the numerators prod_{q != m} (u - o_q) from prefix and suffix
+// products, and the division by the integer D_m = prod_{q != m} (o_m - o_q)
+// as a product with round(2^64 / D_m).  Every factor is at most 3 in
+// magnitude and every product at most 36, so all values fit; the
+// truncations leave each weight within about 2^-52 of its exact value.
+template <int P>
+__device__ __forceinline__ int lagrange_fixed(double s, int2 (&w)[P]) {
+  constexpr long long K6[6] = {-153722867280912930ll, 768614336404564651ll, -1537228672809129301ll,
+                               1537228672809129301ll, -768614336404564651ll, 153722867280912930ll};
+  constexpr long long K5[5] = {768614336404564651ll, -3074457345618258603ll, 4611686018427387904ll,
+                               -3074457345618258603ll, 768614336404564651ll};
+  const double fl = floor(s);
+  constexpr long long one = 1ll << 56;
+  const long long U = __double2ll_rz((s - fl) * 0x1p56);
+  long long d[P], pre[P + 1], suf[P + 1];
+#pragma unroll
+  for (int m = 0; m < P; ++m) d[m] = U - (long long)(m - 2) * one;
+  pre[0] = one;
+  suf[P] = one;
+#pragma unroll
+  for (int m = 0; m < P; ++m) pre[m + 1] = mul56(pre[m], d[m]);
+#pragma unroll
+  for (int m = P - 1; m >= 0; --m) suf[m] = mul56(suf[m + 1], d[m]);
+#pragma unroll
+  for (int m = 0; m < P; ++m) w[m] = split31(mul61(mul56(pre[m], suf[m + 1]), P == 6 ? K6[m] : K5[m]));
+  return (int)fl - 2;
 }
 
 // Fixed-point tensor sum of one point under a rotated map (Eq. Pijk with
@@ -338,16 +377,9 @@ __device__ __forceinline__ void contract_point_fixed(const int2 (&wx)[P], const 
 template <int P>
 __device__ __forceinline__ void fixed_weights(const double sidx[3], int2 (&wx)[P], int2 (&wy)[P], int2 (&wz)[P],
                                               int st[3]) {
-  double w[P];
-  st[0] = lagrange_weights<P>(sidx[0], w);
-#pragma unroll
-  for (int m = 0; m < P; ++m) wx[m] = split31(__double2ll_rn(w[m] * 0x1p59));
-  st[1] = lagrange_weights<P>(sidx[1], w);
-#pragma unroll
-  for (int m = 0; m < P; ++m) wy[m] = split31(__double2ll_rn(w[m] * 0x1p59));
-  st[2] = lagrange_weights<P>(sidx[2], w);
-#pragma unroll
-  for (int m = 0; m < P; ++m) wz[m] = split31(__double2ll_rn(w[m] * 0x1p59));
+  st[0] = lagrange_fixed<P>(sidx[0], wx);
+  st[1] = lagrange_fixed<P>(sidx[1], wy);
+  st[2] = lagrange_fixed<P>(sidx[2], wz);
 }
 
 // Direct tensor sums (Eq. Pijk) point by point for the targets of a tile;

@@ -109,6 +109,8 @@ struct InterpSeg {
                        // SEG_MASKED: the global cells of flag `want` inside `box`;
                        // SEG_LIST: the global cells listed by the cover-flag kernel
   double M[9];         // SEG_AFFINE / SEG_MASKED / SEG_LIST: donor position = M target position + shift
+  double sidx[3][4];   // the same as donor index coordinates of target cell (i, j, k):
+                       // s_a = sidx[a][0] i + sidx[a][1] j + sidx[a][2] k + sidx[a][3]
   const long long* list;  // SEG_LIST: linear global cell indices, *count of them
   const int* count;
   int list_blocks;     // SEG_LIST: CTAs striding over the list
