@@ -351,13 +351,16 @@ __device__ __forceinline__ int lagrange_fixed(double s, int2 (&w)[P]) {
 // contraction against weights on 2^59).  fetch(f, x, y, z) returns the
 // donor at window-relative offsets as a split fixed-point value; out[f] is
 // on the scale of the donor values.
+// The field and plane loops stay rolled: the unrolled 6 x 6 x 6 sum of both
+// fields is large enough to thrash the instruction cache next to the other
+// fill paths.
 template <int P, typename Fetch>
 __device__ __forceinline__ void contract_point_fixed(const int2 (&wx)[P], const int2 (&wy)[P], const int2 (&wz)[P],
                                                      Fetch fetch, long long out[2]) {
-#pragma unroll
+#pragma unroll 1
   for (int f = 0; f < 2; ++f) {
     Acc3 az;
-#pragma unroll
+#pragma unroll 1
     for (int c = 0; c < P; ++c) {
       Acc3 ay;
 #pragma unroll
