@@ -450,6 +450,22 @@ mpw_status run_flags(mpw_ctx* c, double t) {
       a.X0[q][k] = f.X0[k];
       a.lhi[q][k] = L.d.hi[k];
     }
+    // X'_a = sum_b R_ba (lo_b + (idx_b + 1/2) h_b - X0_b), affine in the
+    // global cell indices, rounded to binary32 for the screen.  Its error is
+    // at most about 6 units of 2^-24 of the largest |term| sum, E; the
+    // margin is 1e-5 E, above 25 times that.
+    double E = 0.0;
+    for (int r = 0; r < 3; ++r) {
+      double c = 0.0, e = 0.0;
+      for (int m = 0; m < 3; ++m) {
+        a.scr[q][r][m] = (float)(f.R[3 * m + r] * g.g.h[m]);
+        c += f.R[3 * m + r] * (g.g.lo[m] + 0.5 * g.g.h[m] - f.X0[m]);
+        e += std::fabs(f.R[3 * m + r] * g.g.h[m]) * g.d.n[m];
+      }
+      a.scr[q][r][3] = (float)c;
+      E = std::max(E, e + std::fabs(c) + std::fabs(L.d.lo[r]) + std::fabs(L.d.hi[r]));
+    }
+    a.scrm[q] = (float)(1e-5 * E);
     a.cov_off[q] = ncov;
     if (f.rot && !box_empty(c->boxes[q])) {
       const Box& b = c->boxes[q];

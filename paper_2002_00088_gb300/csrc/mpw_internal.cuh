@@ -178,6 +178,9 @@ struct FlagArgs {
   int rot[MAX_PATCHES];
   double R[MAX_PATCHES][9];
   double lhi[MAX_PATCHES][3];  // upper corner of the live box (the descriptor's hi)
+  // binary32 screen of the coverage test: X'_a ~ scr[q][a][3] + sum_b scr[q][a][b] idx_b
+  float scr[MAX_PATCHES][3][4];
+  float scrm[MAX_PATCHES];     // decision margin of the screen (above 25 x its rounding error)
   uint8_t* cov;
   long long cov_off[MAX_PATCHES + 1];
   // effective ghosts of each rotating patch, listed for Local-to-Global:

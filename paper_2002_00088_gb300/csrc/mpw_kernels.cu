@@ -27,13 +27,29 @@ __global__ void __launch_bounds__(256) k_cover(const __grid_constant__ FlagArgs 
   const long long r = idx - A.cov_off[q];
   const int w0 = b.hi[0] - b.lo[0] + 1, w1 = b.hi[1] - b.lo[1] + 1;
   const int i = b.lo[0] + (int)(r % w0), j = b.lo[1] + (int)((r / w0) % w1), k = b.lo[2] + (int)(r / ((long long)w0 * w1));
-  double xl[3];
-  to_local_rn(A.R[q], A.X0[q], node_rn(A.gg.lo[0], i, A.gg.h[0]), node_rn(A.gg.lo[1], j, A.gg.h[1]),
-              node_rn(A.gg.lo[2], k, A.gg.h[2]), xl);
   const Geom& gl = A.gl[q];
-  bool in = true;
+  // binary32 screen: a cell whose screened position is at least the margin
+  // from every face is decided by it (the margin exceeds 25 times the
+  // screen's rounding error); the others take the exact test
+  const float MARGIN = A.scrm[q];
+  bool sure_in = true, sure_out = false;
 #pragma unroll
-  for (int a = 0; a < 3; ++a) in = in && gl.lo[a] <= xl[a] && xl[a] <= A.lhi[q][a];
+  for (int a = 0; a < 3; ++a) {
+    const float* c = A.scr[q][a];
+    const float v = fmaf(c[0], (float)i, fmaf(c[1], (float)j, fmaf(c[2], (float)k, c[3])));
+    const float lo = (float)gl.lo[a], hi = (float)A.lhi[q][a];
+    sure_in = sure_in && v > lo + MARGIN && v < hi - MARGIN;
+    sure_out = sure_out || v < lo - MARGIN || v > hi + MARGIN;
+  }
+  bool in = sure_in;
+  if (!sure_in && !sure_out) {
+    double xl[3];
+    to_local_rn(A.R[q], A.X0[q], node_rn(A.gg.lo[0], i, A.gg.h[0]), node_rn(A.gg.lo[1], j, A.gg.h[1]),
+                node_rn(A.gg.lo[2], k, A.gg.h[2]), xl);
+    in = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) in = in && gl.lo[a] <= xl[a] && xl[a] <= A.lhi[q][a];
+  }
   A.cov[idx] = in ? 1 : 0;
 }
 

@@ -72,3 +72,28 @@ def test_static_batch_replays_a_captured_graph(mpw_lib):
             a, c = g.get_fields(q), h.get_fields(q)
             np.testing.assert_array_equal(a[0], c[0])
             np.testing.assert_array_equal(a[1], c[1])
+
+
+@pytest.mark.parametrize("precision", [64, 32])
+def test_batch_with_rotating_instances_matches_individual_steps(mpw_lib, precision):
+    """Rotating patches select the rotating-frame RHS kernels for the whole
+    batch; the translating instances in it must still match their own steps
+    bit for bit, and so must the rotating ones."""
+    ws = wl.batch_instances(count=2, steps=12, seed_index=13, max_global=96)
+    ws += [wl.rotating_plane(scale=2),
+           wl.rotating_plane(scale=2, axis=(1.0, 2.0, 2.0), half_width=0.25, nl=16, omega=np.pi, phase=0.7,
+                             velocity=(0.2, -0.1, 0.1))]
+    alone = make_all(mpw_lib, ws, precision)
+    together = make_all(mpw_lib, ws, precision)
+    steps = 6
+    for g, w in zip(alone, ws):
+        g.step(w.dt, steps)
+    b = mpw_lib.Batch(together)
+    b.step([w.dt for w in ws], steps)
+    for g, h, w in zip(alone, together, ws):
+        assert g.time == h.time
+        np.testing.assert_array_equal(g.get_flags(), h.get_flags())
+        for q in range(len(w.patches)):
+            a, c = g.get_fields(q), h.get_fields(q)
+            np.testing.assert_array_equal(a[0], c[0])
+            np.testing.assert_array_equal(a[1], c[1])
