@@ -25,6 +25,7 @@
 #endif
 
 #define NG ORC_NG
+#define ORC_PI 3.14159265358979323846
 
 typedef struct {
   orc_patch_desc d;
@@ -165,31 +166,63 @@ void orc_frame_velocity(int motion, const double* mp, double t, const double xl[
   for (int a = 0; a < 3; ++a) w[a] = om * cr[a] + (R[a] * mp[3] + R[3 + a] * mp[4] + R[6 + a] * mp[5]);
 }
 
-/* The map of one patch at one time, and the two directions of it. */
+/* The map of one patch at one time, and the two directions of it.  A
+ * spherical shell's numeric coordinates (r, theta, phi) first go to the
+ * Cartesian patch frame, X' = r (sin theta cos phi, sin theta sin phi,
+ * cos theta); the rigid motion then acts on X'. */
 typedef struct {
-  int rot;
+  int rot, sph;
   double R[9], X0[3];
 } oframe;
 
 static oframe frame_at(const opatch* p, double t) {
   oframe f;
   f.rot = p->d.motion == ORC_ROTATING;
+  f.sph = p->d.topology == ORC_SPHERICAL;
   orc_frame(p->d.motion, p->d.motion_params, t, f.R, f.X0);
   return f;
 }
 
-/* X_B = R X' + X0 (translation: X' + X0) */
-static void to_background(const oframe* f, const double xl[3], double xb[3]) {
-  for (int a = 0; a < 3; ++a)
-    xb[a] = f->rot ? ((f->R[3 * a] * xl[0] + f->R[3 * a + 1] * xl[1]) + f->R[3 * a + 2] * xl[2]) + f->X0[a]
-                   : xl[a] + f->X0[a];
+static void sph_to_cart(const double q[3], double x[3]) {
+  const double st = sin(q[1]);
+  x[0] = q[0] * st * cos(q[2]);
+  x[1] = q[0] * st * sin(q[2]);
+  x[2] = q[0] * cos(q[1]);
 }
 
-/* X' = R^T (X_B - X0) (translation: X_B - X0) */
-static void to_local(const oframe* f, const double xb[3], double xl[3]) {
-  const double d[3] = {xb[0] - f->X0[0], xb[1] - f->X0[1], xb[2] - f->X0[2]};
+/* X_B = R X' + X0 (translation: X' + X0) of the patch point with numeric
+ * coordinates xl */
+static void to_background(const oframe* f, const double xl[3], double xb[3]) {
+  double x[3] = {xl[0], xl[1], xl[2]};
+  if (f->sph) sph_to_cart(xl, x);
   for (int a = 0; a < 3; ++a)
-    xl[a] = f->rot ? (f->R[a] * d[0] + f->R[3 + a] * d[1]) + f->R[6 + a] * d[2] : d[a];
+    xb[a] = f->rot ? ((f->R[3 * a] * x[0] + f->R[3 * a + 1] * x[1]) + f->R[3 * a + 2] * x[2]) + f->X0[a]
+                   : x[a] + f->X0[a];
+}
+
+/* X' = R^T (X_B - X0) (translation: X_B - X0), the Cartesian patch frame */
+static void to_frame(const oframe* f, const double xb[3], double x[3]) {
+  const double d[3] = {xb[0] - f->X0[0], xb[1] - f->X0[1], xb[2] - f->X0[2]};
+  for (int a = 0; a < 3; ++a) x[a] = f->rot ? (f->R[a] * d[0] + f->R[3 + a] * d[1]) + f->R[6 + a] * d[2] : d[a];
+}
+
+/* numeric coordinates of the background point xb in the patch (a shell:
+ * r = |X'|, theta = acos(z'/r), phi = atan2(y', x') in [0, 2 pi)) */
+static void to_local(const oframe* f, const double xb[3], double xl[3]) {
+  double x[3];
+  to_frame(f, xb, x);
+  if (!f->sph) {
+    for (int a = 0; a < 3; ++a) xl[a] = x[a];
+    return;
+  }
+  const double r = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+  double c = r > 0.0 ? x[2] / r : 1.0;
+  c = c > 1.0 ? 1.0 : (c < -1.0 ? -1.0 : c);
+  double ph = atan2(x[1], x[0]);
+  if (ph < 0.0) ph += 2.0 * ORC_PI;
+  xl[0] = r;
+  xl[1] = acos(c);
+  xl[2] = ph;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -347,6 +380,18 @@ int orc_add_patch(orc_sim* s, const orc_patch_desc* d) {
   for (int a = 0; a < 3; ++a)
     if (d->n[a] < 2 * NG || !(d->hi[a] > d->lo[a])) return fail(s, ORC_ERR_ARG, "bad extent");
   if (d->motion < ORC_STATIC || d->motion > ORC_ROTATING) return fail(s, ORC_ERR_ARG, "bad motion law");
+  if (d->topology == ORC_SPHERICAL) {
+    /* a shell of full azimuth, its ghost nodes away from the origin and
+     * from the poles */
+    const double hr = (d->hi[0] - d->lo[0]) / d->n[0], ht = (d->hi[1] - d->lo[1]) / d->n[1];
+    if (d->kind != ORC_LOCAL) return fail(s, ORC_ERR_ARG, "only local patches can be spherical shells");
+    if (d->lo[0] - NG * hr <= 0.0 || d->lo[1] - NG * ht <= 0.0 || d->hi[1] + NG * ht >= ORC_PI)
+      return fail(s, ORC_ERR_ARG, "shell ghost nodes must stay off the origin and the poles");
+    if (d->lo[2] != 0.0 || fabs(d->hi[2] - 2.0 * ORC_PI) > 1e-12)
+      return fail(s, ORC_ERR_ARG, "a shell spans the full azimuth [0, 2 pi)");
+  } else if (d->topology != ORC_CARTESIAN) {
+    return fail(s, ORC_ERR_ARG, "bad topology");
+  }
   if (d->motion == ORC_ROTATING) {
     const double* n = d->motion_params + 6;
     if (fabs(n[0] * n[0] + n[1] * n[1] + n[2] * n[2] - 1.0) > 1e-12)
@@ -468,20 +513,25 @@ long orc_live_points(const orc_sim* s) {
  * donor patch q at numeric position x.  The whole window must lie in the
  * donor's interior and every donor cell must be live (the buffer guarantees
  * this: Sec. 2.4.2); otherwise the point is skipped and -1 is returned. */
+static long wrap(int i, int n);
+
 static int interp_point(const orc_sim* s, int q, double* const src[2], const double x[3], double out[2]) {
   const opatch* p = &s->p[q];
+  const int sph = p->d.topology == ORC_SPHERICAL;
   double w[3][6];
   int st[3];
   for (int a = 0; a < 3; ++a) {
     double sidx = (x[a] - p->d.lo[a]) / p->h[a] - 0.5;
     st[a] = orc_lagrange(s->P, sidx, w[a]);
+    /* the azimuth of a shell is periodic: its window wraps around */
+    if (sph && a == 2) continue;
     if (st[a] < 0 || st[a] + s->P > p->d.n[a]) return -1;
   }
   double v0 = 0.0, v1 = 0.0;
   for (int c = 0; c < s->P; ++c)
     for (int b = 0; b < s->P; ++b)
       for (int a = 0; a < s->P; ++a) {
-        int i = st[0] + a, j = st[1] + b, k = st[2] + c;
+        int i = st[0] + a, j = st[1] + b, k = sph ? (int)wrap(st[2] + c, p->d.n[2]) : st[2] + c;
         if (!is_live(s, q, i, j, k)) return -2;
         long idx = at(p, i, j, k);
         double wt = w[0][a] * w[1][b] * w[2][c];
@@ -547,13 +597,22 @@ int orc_compute_flags(orc_sim* s) {
   for (int q = 1; q < s->np && rc == 0; ++q) {
     opatch* p = &s->p[q];
     oframe f = frame_at(p, s->t);
+    /* a shell covers r_lo <= r <= r_hi, theta_lo <= theta <= theta_hi, i.e.
+     * r cos(theta_hi) <= z' <= r cos(theta_lo) (cos decreases on [0, pi]) */
+    const double clo = cos(p->d.lo[1]), chi = cos(p->d.hi[1]);
     for (int k = 0; k < g->d.n[2] && rc == 0; ++k)
       for (int j = 0; j < g->d.n[1] && rc == 0; ++j)
         for (int i = 0; i < g->d.n[0]; ++i) {
           double xb[3] = {node(g, 0, i), node(g, 1, j), node(g, 2, k)}, xl[3];
           int inside = 1;
-          to_local(&f, xb, xl);
-          for (int a = 0; a < 3; ++a) inside = inside && (p->d.lo[a] <= xl[a]) && (xl[a] <= p->d.hi[a]);
+          if (f.sph) {
+            to_frame(&f, xb, xl);
+            const double r = sqrt((xl[0] * xl[0] + xl[1] * xl[1]) + xl[2] * xl[2]);
+            inside = p->d.lo[0] <= r && r <= p->d.hi[0] && r * chi <= xl[2] && xl[2] <= r * clo;
+          } else {
+            to_local(&f, xb, xl);
+            for (int a = 0; a < 3; ++a) inside = inside && (p->d.lo[a] <= xl[a]) && (xl[a] <= p->d.hi[a]);
+          }
           if (!inside) continue;
           long c = gidx(g, i, j, k);
           if (owner[c]) {
@@ -698,6 +757,14 @@ static void fill_g2l(orc_sim* s, double t, const double Xg[3], long* unfilled_, 
       for (int j = -NG; j < p->d.n[1] + NG; ++j)
         for (int i = -NG; i < p->d.n[0] + NG; ++i) {
           if (in_interior(p, i, j, k)) continue;
+          if (f.sph && i >= 0 && i < p->d.n[0] && j >= 0 && j < p->d.n[1]) {
+            /* azimuthal ghosts of a shell: the periodic image (an intrapatch
+             * boundary, the same physical point) */
+            long c = at(p, i, j, k), src = at(p, i, j, (int)wrap(k, p->d.n[2]));
+            p->Y[0][c] = p->Y[0][src];
+            p->Y[1][c] = p->Y[1][src];
+            continue;
+          }
           double xl[3] = {node(p, 0, i), node(p, 1, j), node(p, 2, k)}, xb[3], x[3], v[2];
           to_background(&f, xl, xb);
           x[0] = xb[0] - Xg[0];
@@ -787,8 +854,57 @@ static double fd_ko(const double* u, long st, double h, double eps) {
          h;
 }
 
+/* Right-hand side on a spherical shell (the paper's spherical local patch,
+ * Sec. 3.3; the flat metric in spherical coordinates of the appendix, with
+ * g_phiphi = r^2 sin^2 theta): the same two-field system with
+ *   lap u   = u_rr + (2/r) u_r + (u_thth + cot(theta) u_th) / r^2
+ *             + u_phph / (r^2 sin^2 theta),
+ *   w . D u = w_r u_r + (w_th / r) u_th + (w_ph / (r sin theta)) u_ph,
+ * w_r, w_th, w_ph the components of the frame velocity on the unit vectors
+ * r^, theta^, phi^, each derivative the 4th-order centred difference along
+ * its index axis, and KO per axis over the physical spacing of that axis
+ * (h_r, r h_theta, r sin(theta) h_phi). */
+static void rhs_shell(orc_sim* s, int q, double t, double* const Y[2], double* Kpsi, double* Kpi) {
+  opatch* p = &s->p[q];
+  long st[3] = {1, p->m[0], (long)p->m[0] * p->m[1]};
+#pragma omp parallel for schedule(static) num_threads(s->nthreads)
+  for (int k = 0; k < p->d.n[2]; ++k)
+    for (int j = 0; j < p->d.n[1]; ++j)
+      for (int i = 0; i < p->d.n[0]; ++i) {
+        long c = at(p, i, j, k);
+        const double r = node(p, 0, i), th = node(p, 1, j), ph = node(p, 2, k);
+        const double sn = sin(th), cs = cos(th), sp = sin(ph), cp = cos(ph);
+        const double q3[3] = {r, th, ph};
+        double x[3], w[3];
+        sph_to_cart(q3, x);
+        orc_frame_velocity(p->d.motion, p->d.motion_params, t, x, w);
+        const double wr = w[0] * sn * cp + w[1] * sn * sp + w[2] * cs;
+        const double wt = w[0] * cs * cp + w[1] * cs * sp - w[2] * sn;
+        const double wp = -w[0] * sp + w[1] * cp;
+        double K[2];
+        for (int f = 0; f < 2; ++f) {
+          const double* u = Y[f] + c;
+          const double ur = fd_d1(u, st[0], p->h[0]), ut = fd_d1(u, st[1], p->h[1]), up = fd_d1(u, st[2], p->h[2]);
+          const double adv = wr * ur + (wt / r) * ut + (wp / (r * sn)) * up;
+          const double ko = fd_ko(u, st[0], p->h[0], s->eps) + fd_ko(u, st[1], r * p->h[1], s->eps) +
+                            fd_ko(u, st[2], r * sn * p->h[2], s->eps);
+          K[f] = adv + ko;
+        }
+        const double* ps = Y[0] + c;
+        const double lap = fd_d2(ps, st[0], p->h[0]) + (2.0 / r) * fd_d1(ps, st[0], p->h[0]) +
+                           (fd_d2(ps, st[1], p->h[1]) + (cs / sn) * fd_d1(ps, st[1], p->h[1])) / (r * r) +
+                           fd_d2(ps, st[2], p->h[2]) / (r * r * sn * sn);
+        Kpsi[c] = Y[1][c] + K[0];
+        Kpi[c] = lap + K[1];
+      }
+}
+
 static void rhs(orc_sim* s, int q, double t, double* const Y[2], double* Kpsi, double* Kpi) {
   opatch* p = &s->p[q];
+  if (p->d.topology == ORC_SPHERICAL) {
+    rhs_shell(s, q, t, Y, Kpsi, Kpi);
+    return;
+  }
   double X0[3], w0[3];
   orc_motion(p->d.motion, p->d.motion_params, t, X0, w0);
   const int rot = p->d.motion == ORC_ROTATING;

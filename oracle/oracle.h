@@ -44,6 +44,10 @@ extern "C" {
 #define ORC_MAX_APARAMS 1024
 
 enum { ORC_GLOBAL = 0, ORC_LOCAL = 1 };
+/* patch topology: CARTESIAN (numeric x, y, z) or SPHERICAL (a local shell with
+ * numeric (r, theta, phi), theta in (0, pi) away from the poles, phi periodic
+ * over [0, 2 pi)) */
+enum { ORC_CARTESIAN = 0, ORC_SPHERICAL = 1 };
 enum { ORC_BC_ANALYTIC = 0, ORC_BC_PERIODIC = 1, ORC_BC_INTERPATCH = 2 };
 enum { ORC_STATIC = 0, ORC_LINEAR = 1, ORC_CIRCULAR = 2, ORC_ROTATING = 3 };
 enum { ORC_GAUSS_SUM = 0, ORC_PLANE_SUM = 1, ORC_HARMONIC_POLY = 2, ORC_PLANE_GAUSS = 3 };
@@ -65,6 +69,7 @@ typedef struct {
   int outer_bc;             /* global: ANALYTIC or PERIODIC; local: INTERPATCH */
   int motion;               /* ORC_STATIC / ORC_LINEAR / ORC_CIRCULAR / ORC_ROTATING */
   double motion_params[16]; /* see orc_motion() and orc_frame() */
+  int topology;             /* ORC_CARTESIAN or ORC_SPHERICAL (local patches only) */
 } orc_patch_desc;
 
 typedef struct orc_sim orc_sim;

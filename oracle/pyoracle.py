@@ -6,6 +6,7 @@ import numpy as np
 from . import LIB_PATH, build_oracle
 
 GLOBAL, LOCAL = 0, 1
+CARTESIAN, SPHERICAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
 STATIC, LINEAR, CIRCULAR, ROTATING = 0, 1, 2, 3
 GAUSS_SUM, PLANE_SUM, HARMONIC_POLY, PLANE_GAUSS = 0, 1, 2, 3
@@ -15,7 +16,8 @@ NG = 3
 
 class PatchDesc(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("outer_bc", C.c_int), ("motion", C.c_int), ("motion_params", C.c_double * 16)]
+                ("outer_bc", C.c_int), ("motion", C.c_int), ("motion_params", C.c_double * 16),
+                ("topology", C.c_int)]
 
 
 _lib = None
@@ -69,8 +71,9 @@ def _dp(a):
     return a.ctypes.data_as(C.POINTER(C.c_double))
 
 
-def make_desc(kind, n, lo, hi, outer_bc, motion=STATIC, motion_params=()):
+def make_desc(kind, n, lo, hi, outer_bc, motion=STATIC, motion_params=(), topology=CARTESIAN):
     d = PatchDesc()
+    d.topology = topology
     d.kind = kind
     for a in range(3):
         d.n[a] = int(n[a])
@@ -162,8 +165,8 @@ class Oracle:
             raise OracleError(f"oracle error {rc}: {self.L.orc_error(self.h).decode()}")
         return rc
 
-    def add_patch(self, kind, n, lo, hi, outer_bc, motion=STATIC, motion_params=()):
-        d = make_desc(kind, n, lo, hi, outer_bc, motion, motion_params)
+    def add_patch(self, kind, n, lo, hi, outer_bc, motion=STATIC, motion_params=(), topology=CARTESIAN):
+        d = make_desc(kind, n, lo, hi, outer_bc, motion, motion_params, topology)
         pid = self._check(self.L.orc_add_patch(self.h, C.byref(d)))
         self.patches.append(tuple(int(v) for v in n))
         return pid

@@ -39,6 +39,7 @@ SEED_BASE = 20020088
 GLOBAL, LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
 STATIC, LINEAR, CIRCULAR, ROTATING = 0, 1, 2, 3
+CARTESIAN, SPHERICAL = 0, 1
 GAUSS_SUM, PLANE_SUM, HARMONIC_POLY, PLANE_GAUSS = 0, 1, 2, 3
 
 
@@ -51,6 +52,7 @@ class PatchSpec:
     outer_bc: int
     motion: int = STATIC
     motion_params: Tuple[float, ...] = ()
+    topology: int = 0  # CARTESIAN, or SPHERICAL for a local shell (numeric r, theta, phi)
 
 
 @dataclass
@@ -160,6 +162,31 @@ def rotating_plane(scale=1, steps=16, interp_points=6, omega=2.0 * np.pi, axis=(
     h_min = 2.0 * half_width / nl
     return Workload(f"rotating_plane_{ng}+{nl}", patches, PLANE_SUM, params, 2, interp_points, 0.005,
                     0.25 * h_min, steps * scale)
+
+
+def shell_plane(scale=1, steps=16, interp_points=6, r=(0.3, 0.7), theta=(np.pi / 4, 3 * np.pi / 4), n=(12, 24, 96),
+                centre=(0.013, -0.021, 0.017), motion=STATIC, motion_params=None):
+    """A spherical local shell (the paper's spherical local patch, Sec. 3.3:
+    theta in [pi/4, 3 pi/4], full azimuth) inside the global cube [-1,1]^3 at
+    32 scale cells per axis, static at `centre` unless a motion law is
+    given; n = (r, theta, phi) cells at scale 1.  The two-wave superposition
+    of ``translating_plane`` with analytic outer BCs; dt = CFL 0.25 times the
+    smallest physical spacing of the shell (the azimuthal one at r_lo,
+    theta_lo)."""
+    ng = 32 * scale
+    ns = tuple(int(v) * scale for v in n)
+    mp = tuple(centre) if motion_params is None else tuple(motion_params)
+    patches = [
+        PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_ANALYTIC),
+        PatchSpec(LOCAL, ns, (r[0], theta[0], 0.0), (r[1], theta[1], 2.0 * np.pi), BC_INTERPATCH, motion, mp,
+                  SPHERICAL),
+    ]
+    k = 2.0 * np.pi / 2.0
+    params = np.array([3.0, 1.0, k, 0.0, 0.0, 0.0, 1.0, k, -k, k, 0.5 * np.pi])
+    h = [(r[1] - r[0]) / ns[0], r[0] * (theta[1] - theta[0]) / ns[1],
+         r[0] * np.sin(theta[0]) * 2.0 * np.pi / ns[2]]
+    return Workload(f"shell_plane_{ng}+{ns[0]}x{ns[1]}x{ns[2]}", patches, PLANE_SUM, params, 2, interp_points, 0.005,
+                    0.25 * min(h), steps * scale)
 
 
 def plane_gauss(scale=1, steps=200, interp_points=6, seed_index=2):

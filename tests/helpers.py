@@ -9,7 +9,7 @@ from oracle import pyoracle as po
 def oracle_from(w, threads=None, buffer=4):
     o = po.Oracle(w.interp_points, w.ko_eps, buffer, threads or min(8, os.cpu_count() or 1))
     for p in w.patches:
-        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
     o.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
     return o
 
