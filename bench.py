@@ -194,7 +194,7 @@ def precision_report(args, w, sim, mpw, stream, device):
     def make(precision):
         s = mpw.Multipatch(w.interp_points, w.ko_eps, device=device, stream=stream, precision=precision)
         for p in w.patches:
-            s.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+            s.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
         s.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
         return s
 
@@ -258,7 +258,7 @@ def cpu_baseline(args, threads):
     w = make(scale=max(args.scale, args.cpu_sample_scale, 2 if args.precision == 32 else 1))
     o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
     for p in w.patches:
-        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
     o.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
     o.fill_analytic(0.0)
     o.step(w.dt, 1)  # first step: flags from scratch, allocation warm-up
@@ -282,7 +282,7 @@ def run_reference(args):
     w = fp64_workload(args)(scale=max(args.scale, args.ref_sample_scale))
     o = po.Oracle(w.interp_points, w.ko_eps, 4, threads=threads)
     for p in w.patches:
-        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+        o.add_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
     o.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
     o.fill_analytic(0.0)
     o.step(w.dt, args.warmup)
@@ -323,7 +323,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(local)
     sim = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream, precision=args.precision)
     for p in w.patches:
-        sim.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+        sim.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
     sim.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
     sim.fill_analytic(0.0)  # inputs generated in HBM
     sim.step(w.dt, args.warmup)
@@ -455,7 +455,7 @@ def run_batch(args):
         for w in ws:
             g = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream, precision=args.precision)
             for p in w.patches:
-                g.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+                g.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
             g.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
             g.fill_analytic(0.0)
             sims.append(g)

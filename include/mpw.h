@@ -57,6 +57,7 @@ typedef enum {
 } mpw_status;
 
 enum { MPW_PATCH_GLOBAL = 0, MPW_PATCH_LOCAL = 1 };
+enum { MPW_TOPOLOGY_CARTESIAN = 0, MPW_TOPOLOGY_SPHERICAL = 1 };
 enum { MPW_BC_ANALYTIC = 0, MPW_BC_PERIODIC = 1, MPW_BC_INTERPATCH = 2 };
 enum { MPW_MOTION_STATIC = 0, MPW_MOTION_LINEAR = 1, MPW_MOTION_CIRCULAR = 2, MPW_MOTION_ROTATING = 3 };
 enum {
@@ -116,6 +117,15 @@ typedef struct {
                                           w(X') = p9 n x X' + R^T (p3,p4,p5).  Validation of a
                                           rotating patch (overlap, distance to the global faces)
                                           uses the bounding box of its rotated box. */
+  int topology;             /* MPW_TOPOLOGY_CARTESIAN (numeric x, y, z), or MPW_TOPOLOGY_SPHERICAL for a
+                               local shell (the paper's spherical local patch, Sec. 3.3) with numeric
+                               coordinates (r, theta, phi): n = cells along r, theta, phi; lo = (r_lo,
+                               theta_lo, 0), hi = (r_hi, theta_hi, 2 pi) (the full azimuth, periodic); the
+                               ghost nodes must stay off the origin and the poles (r_lo - 3 h_r > 0,
+                               theta_lo - 3 h_theta > 0, theta_hi + 3 h_theta < pi), and the physical
+                               spacings h_r, r_hi h_theta and r_hi h_phi must not exceed the global
+                               spacing.  X' = r (sin theta cos phi, sin theta sin phi, cos theta) is the
+                               patch frame the motion law maps.  Precision 64 only.  Errors: MPW_ERR_ARG. */
 } mpw_patch_desc;
 
 /* Create a context on cfg->device.  cfg is copied.  Errors: MPW_ERR_ARG for

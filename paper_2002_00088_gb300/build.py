@@ -15,7 +15,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libmpw.so")
-SOURCES = ["mpw_api.cu", "mpw_kernels.cu", "mpw_rhs.cu", "mpw_rhs32.cu", "mpw_fill.cu", "mpw_noalloc.cu"]
+SOURCES = ["mpw_api.cu", "mpw_kernels.cu", "mpw_rhs.cu", "mpw_rhs32.cu", "mpw_shell.cu", "mpw_fill.cu", "mpw_noalloc.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 

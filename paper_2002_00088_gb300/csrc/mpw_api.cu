@@ -60,6 +60,7 @@ struct PatchState {
   double* io_out = nullptr;
   cudaEvent_t in_copied = nullptr, in_free = nullptr, out_packed = nullptr, out_free = nullptr;
   bool in_pending = false;
+  bool sph() const { return d.topology == MPW_TOPOLOGY_SPHERICAL; }
   // device address of buffer b (its element type follows esize)
   double* buf(int b) const {
     return reinterpret_cast<double*>(reinterpret_cast<char*>(base) + (size_t)b * 2 * (size_t)g.vol * esize);
@@ -228,6 +229,15 @@ void to_background(const Frame& f, const double xl[3], double xb[3]) {
 // (exact for translation).
 void background_extent(const mpw_patch_desc& d, double t, double e, double lo[3], double hi[3]) {
   const Frame f = frame(d, t);
+  if (d.topology == MPW_TOPOLOGY_SPHERICAL) {
+    // a shell lies in the ball of radius r_hi (+ e radial cells) about X0
+    const double R = d.hi[0] + e * (d.hi[0] - d.lo[0]) / d.n[0];
+    for (int a = 0; a < 3; ++a) {
+      lo[a] = f.X0[a] - R;
+      hi[a] = f.X0[a] + R;
+    }
+    return;
+  }
   double h[3];
   for (int a = 0; a < 3; ++a) {
     h[a] = (d.hi[a] - d.lo[a]) / d.n[a];
@@ -249,6 +259,15 @@ void background_extent(const mpw_patch_desc& d, double t, double e, double lo[3]
 // Euclidean bound |Omega| r_max + |V| for a rotating patch).
 double max_point_speed(const mpw_patch_desc& d) {
   const double* mp = d.motion_params;
+  if (d.topology == MPW_TOPOLOGY_SPHERICAL) {
+    // points of the shell lie within r_hi of the patch origin
+    double v = 0.0;
+    if (d.motion == MPW_MOTION_LINEAR) v = std::sqrt(mp[3] * mp[3] + mp[4] * mp[4] + mp[5] * mp[5]);
+    if (d.motion == MPW_MOTION_CIRCULAR) v = std::fabs(mp[3] * mp[4]);
+    if (d.motion == MPW_MOTION_ROTATING)
+      v = std::fabs(mp[9]) * d.hi[0] + std::sqrt(mp[3] * mp[3] + mp[4] * mp[4] + mp[5] * mp[5]);
+    return v;
+  }
   if (d.motion == MPW_MOTION_LINEAR) return std::sqrt(mp[3] * mp[3] + mp[4] * mp[4] + mp[5] * mp[5]);
   if (d.motion == MPW_MOTION_CIRCULAR) return std::fabs(mp[3] * mp[4]);
   if (d.motion != MPW_MOTION_ROTATING) return 0.0;
@@ -307,7 +326,7 @@ Box covered_box(const PatchState& g, const PatchState& l, double t) {
   double X0[3], w[3];
   motion(l.d, t, X0, w);
   Box b;
-  if (l.d.motion == MPW_MOTION_ROTATING) {
+  if (l.d.motion == MPW_MOTION_ROTATING || l.sph()) {
     double lo[3], hi[3];
     background_extent(l.d, t, 0.0, lo, hi);
     for (int a = 0; a < 3; ++a) {
@@ -369,9 +388,19 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
     // Laplacian reaches 16/(3 h^2) per axis, the 4th-order first derivative
     // 1.372/h.
     double lap = 0.0, adv = 0.0;
-    for (int a = 0; a < 3; ++a) {
-      lap += 16.0 / (3.0 * P.g.h[a] * P.g.h[a]);
-      adv += 1.372 * v[a] / P.g.h[a];
+    if (P.sph()) {
+      // physical spacings at the smallest radius and sin(theta)
+      const double smin = std::min(std::sin(P.d.lo[1]), std::sin(P.d.hi[1]));
+      const double L[3] = {P.g.h[0], P.d.lo[0] * P.g.h[1], P.d.lo[0] * smin * P.g.h[2]};
+      for (int a = 0; a < 3; ++a) {
+        lap += 16.0 / (3.0 * L[a] * L[a]);
+        adv += 1.372 * sp / L[a];
+      }
+    } else {
+      for (int a = 0; a < 3; ++a) {
+        lap += 16.0 / (3.0 * P.g.h[a] * P.g.h[a]);
+        adv += 1.372 * v[a] / P.g.h[a];
+      }
     }
     if (dt * (std::sqrt(lap) + adv) > 2.8)
       return set_err(MPW_ERR_CFL, "patch %zu: dt = %g exceeds the RK4 stability estimate", q, dt);
@@ -379,7 +408,7 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
     // the buffer of B live cells lets a patch cross B - NG global cells per
     // step (a rotating patch: its fastest point, on every axis)
     for (int a = 0; a < 3; ++a)
-      if ((P.d.motion == MPW_MOTION_ROTATING ? sp : v[a]) * dt > (c->buffer - NG) * g.g.h[a])
+      if ((P.d.motion == MPW_MOTION_ROTATING || P.sph() ? sp : v[a]) * dt > (c->buffer - NG) * g.g.h[a])
         return set_err(MPW_ERR_TRAVERSAL, "patch %zu crosses more than %d global cell(s) per step", q,
                        c->buffer - NG);
   }
@@ -389,8 +418,8 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
       const PatchState& P = c->p[q];
       double X0[3], w[3];
       motion(P.d, tt, X0, w);
-      if (P.d.motion == MPW_MOTION_ROTATING) {
-        // the ghost-extended box, rotated; the samples are dt/2 apart
+      if (P.d.motion == MPW_MOTION_ROTATING || P.sph()) {
+        // the ghost-extended box, rotated (a shell: its ball); the samples are dt/2 apart
         double lo[3], hi[3];
         background_extent(P.d, tt, NG, lo, hi);
         const double slack = max_point_speed(P.d) * 0.5 * dt;
@@ -402,7 +431,7 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
       }
       for (int a = 0; a < 3; ++a) {
         const double margin = NG * P.g.h[a] + (NG + 2) * g.g.h[a];
-        if (P.d.motion != MPW_MOTION_ROTATING &&
+        if (P.d.motion != MPW_MOTION_ROTATING && !P.sph() &&
             (P.d.lo[a] + X0[a] - margin < g.d.lo[a] || P.d.hi[a] + X0[a] + margin > g.d.hi[a]))
           return set_err(MPW_ERR_OUTSIDE, "patch %zu leaves the global interior at t = %g", q, tt);
       }
@@ -445,6 +474,9 @@ mpw_status run_flags(mpw_ctx* c, double t) {
     a.gl[q] = L.g;
     const Frame f = frame(L.d, t);
     a.rot[q] = f.rot ? 1 : 0;
+    a.sph[q] = L.sph() ? 1 : 0;
+    a.cth[q][0] = std::cos(L.d.lo[1]);
+    a.cth[q][1] = std::cos(L.d.hi[1]);
     for (int e = 0; e < 9; ++e) a.R[q][e] = f.R[e];
     for (int k = 0; k < 3; ++k) {
       a.X0[q][k] = f.X0[k];
@@ -467,7 +499,7 @@ mpw_status run_flags(mpw_ctx* c, double t) {
     }
     a.scrm[q] = (float)(1e-5 * E);
     a.cov_off[q] = ncov;
-    if (f.rot && !box_empty(c->boxes[q])) {
+    if ((f.rot || L.sph()) && !box_empty(c->boxes[q])) {
       const Box& b = c->boxes[q];
       ncov += (long long)(b.hi[0] - b.lo[0] + 1) * (b.hi[1] - b.lo[1] + 1) * (b.hi[2] - b.lo[2] + 1);
     }
@@ -477,7 +509,8 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   if ((size_t)ncov > c->cov_bytes) {
     c->dfree(c->d_cov);
     c->dfree(c->d_glist);
-    c->d_cov = (uint8_t*)c->dalloc((size_t)ncov);
+    // the shells' distance transform uses two more regions of the same size
+    c->d_cov = (uint8_t*)c->dalloc(3 * (size_t)ncov);
     c->d_glist = (long long*)c->dalloc(sizeof(long long) * (size_t)ncov);
     c->cov_bytes = c->d_cov && c->d_glist ? (size_t)ncov : 0;
     if (!c->cov_bytes) return set_err(MPW_ERR_CUDA, "covered-mask allocation for %lld cells failed", ncov);
@@ -736,7 +769,8 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     S.gd = L.g;
     const Frame f = frame(L.d, t);
     S.block0 = blocks;
-    if (f.rot) {
+    S.sph = L.sph() ? 1 : 0;
+    if (f.rot || L.sph()) {
       // the effective ghosts of a rotated box, mapped by X' = R^T X_B - R^T X0:
       // the list the cover-flag kernel wrote, or (flags set through the ABI)
       // every cell of the covered bounding box whose flag says GHOST of this
@@ -785,6 +819,15 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     S.kind = f.rot ? SEG_AFFINE : SEG_SHELL;
     for (int e = 0; e < 9; ++e) S.M[e] = f.R[e];
     for (int k = 0; k < 3; ++k) S.shift[k] = f.X0[k];
+    if (L.sph()) {
+      // every ghost node of a spherical shell, one thread each
+      S.kind = SEG_SPH_GHOSTS;
+      S.block0 = blocks;
+      const long long cnt = (long long)(L.d.n[0] + 2 * NG) * (L.d.n[1] + 2 * NG) * (L.d.n[2] + 2 * NG) -
+                            (long long)L.d.n[0] * L.d.n[1] * L.d.n[2];
+      blocks += (int)((cnt + fill_threads() - 1) / fill_threads());
+      continue;
+    }
     if (f.rot) set_index_map(S);
     const int O0[3] = {-NG, -NG, -NG};
     const int O[3] = {L.d.n[0] + 2 * NG, L.d.n[1] + 2 * NG, L.d.n[2] + 2 * NG};
@@ -868,7 +911,47 @@ int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
     R.zc = zc > 0 ? zc : (P.d.n[2] >= 128 ? 32 : 8);
     R.zchunks = (P.d.n[2] + R.zc - 1) / R.zc;
     R.block0 = blocks;
+    if (P.sph()) continue;  // spherical shells: k_rhs_shell
     blocks += R.tiles_x * R.tiles_y * R.zchunks;
+  }
+  return blocks;
+}
+
+// RHS + stage arguments of substage l for the spherical shells of c; returns
+// the number of CTAs (0 without shells).
+long long prep_rhs_shell(mpw_ctx* c, int l, double t, double dt, ShellArgs& a) {
+  static const int in_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
+  static const int out_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
+  const double alpha[4] = {0.5 * dt, 0.5 * dt, dt, dt / 6.0};
+  const double beta[4] = {dt / 6.0, dt / 3.0, dt / 3.0, 0.0};
+  a = ShellArgs{};
+  a.stage = l;
+  a.alpha = alpha[l];
+  a.beta = beta[l];
+  a.ko_eps = c->cfg.ko_eps;
+  a.in_buf = in_buf[l];
+  a.out_buf = out_buf[l];
+  a.expo = c->d_expo;
+  long long blocks = 0;
+  for (size_t q = 1; q < c->p.size(); ++q) {
+    const PatchState& P = c->p[q];
+    if (!P.sph()) continue;
+    ShellPatch& S = a.p[a.np++];
+    S.Y = P.buf(in_buf[l]);
+    S.U = P.buf(BUF_U);
+    S.ACC = P.buf(BUF_ACC);
+    S.OUT = P.buf(out_buf[l]);
+    S.g = P.g;
+    const Frame f = frame(P.d, t);
+    for (int e = 0; e < 9; ++e) {
+      S.R[e] = f.R[e];
+      S.W[e] = f.W[e];
+    }
+    for (int k = 0; k < 3; ++k) S.w0[k] = f.w0[k];
+    S.moving = is_moving(P.d) ? 1 : 0;
+    S.patch = (int)q;
+    S.block0 = blocks;
+    blocks += ((long long)P.d.n[0] * P.d.n[1] * P.d.n[2] + 255) / 256;
   }
   return blocks;
 }
@@ -878,11 +961,17 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
   const int blocks = prep_rhs(c, l, t, dt, a);
   bool rot = false;
   for (int q = 0; q < a.np; ++q) rot = rot || a.p[q].rot;
+  ShellArgs sa;
+  const long long sblocks = prep_rhs_shell(c, l, t, dt, sa);
   c->launch_begin(MPW_KERNEL_RHS);
   if (c->cfg.precision == 32)
     launch_rhs32(a, blocks, rot, c->stream);
   else
     launch_rhs(a, blocks, c->cfg.arith != 1, rot, c->stream);
+  if (sblocks > 0) {
+    launch_rhs_shell(sa, sblocks, c->stream);
+    c->launches[MPW_KERNEL_RHS] += 1;
+  }
   c->launch_end(MPW_KERNEL_RHS);
   CUDA_TRY(cudaGetLastError());
   return MPW_OK;
@@ -1053,6 +1142,7 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
     if (d->kind == MPW_PATCH_GLOBAL) return set_err(MPW_ERR_ARG, "the global patch cannot rotate");
   }
   if (d->kind == MPW_PATCH_GLOBAL) {
+    if (d->topology != MPW_TOPOLOGY_CARTESIAN) return set_err(MPW_ERR_ARG, "the global patch is Cartesian");
     if (d->outer_bc != MPW_BC_ANALYTIC && d->outer_bc != MPW_BC_PERIODIC)
       return set_err(MPW_ERR_ARG, "global outer_bc must be ANALYTIC or PERIODIC");
   } else {
@@ -1062,9 +1152,24 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
         g.motion_params[2] != 0.0)
       return set_err(MPW_ERR_ARG, "with local patches the global patch must be static at the origin");
     const Geom gg = make_geom(g);
-    for (int a = 0; a < 3; ++a)
-      if ((d->hi[a] - d->lo[a]) / d->n[a] > gg.h[a] * (1.0 + 1e-12))
-        return set_err(MPW_ERR_ARG, "a local patch must not be coarser than the global patch");
+    if (d->topology == MPW_TOPOLOGY_SPHERICAL) {
+      const double hr = (d->hi[0] - d->lo[0]) / d->n[0], ht = (d->hi[1] - d->lo[1]) / d->n[1];
+      const double hp = (d->hi[2] - d->lo[2]) / d->n[2], pi = 3.14159265358979323846;
+      const double hg = std::min(gg.h[0], std::min(gg.h[1], gg.h[2])) * (1.0 + 1e-12);
+      if (c->cfg.precision != 64) return set_err(MPW_ERR_ARG, "spherical shells run in precision 64 only");
+      if (d->lo[0] - NG * hr <= 0.0 || d->lo[1] - NG * ht <= 0.0 || d->hi[1] + NG * ht >= pi)
+        return set_err(MPW_ERR_ARG, "shell ghost nodes must stay off the origin and the poles");
+      if (d->lo[2] != 0.0 || std::fabs(d->hi[2] - 2.0 * pi) > 1e-12)
+        return set_err(MPW_ERR_ARG, "a shell spans the full azimuth [0, 2 pi)");
+      if (hr > hg || d->hi[0] * ht > hg || d->hi[0] * hp > hg)
+        return set_err(MPW_ERR_ARG, "a shell's physical spacings must not exceed the global spacing");
+    } else if (d->topology != MPW_TOPOLOGY_CARTESIAN) {
+      return set_err(MPW_ERR_ARG, "bad topology");
+    } else {
+      for (int a = 0; a < 3; ++a)
+        if ((d->hi[a] - d->lo[a]) / d->n[a] > gg.h[a] * (1.0 + 1e-12))
+          return set_err(MPW_ERR_ARG, "a local patch must not be coarser than the global patch");
+    }
   }
   if (use_device(c)) return MPW_ERR_CUDA;
   PatchState P;
@@ -1144,7 +1249,7 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
     for (int k = 0; k < 3; ++k) map.X0[k] = f.X0[k];
     launch_analytic(P.buf(BUF_U), P.g, map, c->akind, c->acount, c->d_aparams,
                     c->screen_ok ? c->d_ascreen : nullptr, c->screen_ok ? c->d_apre : nullptr, t,
-                    c->cfg.precision == 32, c->stream);
+                    c->cfg.precision == 32, c->stream, P.sph());
     CUDA_TRY(cudaGetLastError());
     P.u_expo_valid = false;
   }
@@ -1439,7 +1544,7 @@ mpw_status mpw_live_points(mpw_ctx* c, long long* count) {
   long long n = 0;
   for (const auto& P : c->p) n += (long long)P.d.n[0] * P.d.n[1] * P.d.n[2];
   bool rot = false;
-  for (size_t q = 1; q < c->p.size(); ++q) rot = rot || c->p[q].d.motion == MPW_MOTION_ROTATING;
+  for (size_t q = 1; q < c->p.size(); ++q) rot = rot || c->p[q].d.motion == MPW_MOTION_ROTATING || c->p[q].sph();
   if (rot) {
     // a rotated covered set is no box: count the live global cells
     if (use_device(c)) return MPW_ERR_CUDA;
@@ -1649,6 +1754,14 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     bool rot = false;  // some patch rotates: the RHS kernels with a position-dependent w
     for (mpw_ctx* c : b->ctx)
       for (const auto& P : c->p) rot = rot || P.d.motion == MPW_MOTION_ROTATING;
+    // spherical shells: their own RHS launch per instance after each batched one
+    std::vector<ShellArgs> sargs;
+    std::vector<long long> sblocks;
+    for (int l = 0; l < 4; ++l)
+      for (int i = 0; i < n; ++i) {
+        sargs.emplace_back();
+        sblocks.push_back(prep_rhs_shell(b->ctx[i], l, tnp[i] + RK_C[l] * dt[i], dt[i], sargs.back()));
+      }
     // copies and launches of the step, on stream sm
     auto enqueue = [&](cudaStream_t sm) -> cudaError_t {
       for (int r = 0; r < 8; ++r) {
@@ -1667,6 +1780,8 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
             launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], rot, sm);
           else
             launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], b->fixed, rot, sm);
+          for (int i = 0; i < n; ++i)
+            if (sblocks[l * n + i] > 0) launch_rhs_shell(sargs[l * n + i], sblocks[l * n + i], sm);
           if (trial && l == 3) cudaEventRecord(b->tev[2 * k + 1], sm);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1702,6 +1817,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     }
     if (!replayed) CUDA_TRY(enqueue(b->stream));
     b->launches += 8;
+    for (long long sb : sblocks) b->launches += sb > 0 ? 1 : 0;
     CUDA_TRY(cudaEventRecord(b->copied[h], b->stream));
     for (int i = 0; i < n; ++i) {
       b->ctx[i]->t = tnp[i] + dt[i];

@@ -148,6 +148,8 @@ __device__ __forceinline__ void closed_form(int kind, const double* __restrict__
   }
 }
 
+__device__ __forceinline__ int wrap_index(int i, int n) { return ((i % n) + n) % n; }
+
 // ---------------------------------------------------------------------------
 // 1-D Lagrange weights of the window that starts two nodes below
 // i_c = floor(s) (Sec. 2.4, Eq. Pijk).  With u = s - i_c and node offsets
@@ -216,6 +218,66 @@ __device__ __forceinline__ bool interp_point(const ST* __restrict__ src, const G
 }
 
 
+// ---------------------------------------------------------------------------
+// Spherical shells (numeric r, theta, phi; phi periodic over [0, 2 pi)).
+// Cartesian patch frame of the shell point (r, theta, phi).
+__device__ __forceinline__ void sph_to_cart(double r, double th, double ph, double x[3]) {
+  double st, ct, sp, cp;
+  sincos(th, &st, &ct);
+  sincos(ph, &sp, &cp);
+  x[0] = r * st * cp;
+  x[1] = r * st * sp;
+  x[2] = r * ct;
+}
+
+// (r, theta, phi) of a point of the Cartesian patch frame.
+__device__ __forceinline__ void cart_to_sph(const double x[3], double q[3]) {
+  const double r = sqrt((x[0] * x[0] + x[1] * x[1]) + x[2] * x[2]);
+  const double c = r > 0.0 ? fmin(fmax(x[2] / r, -1.0), 1.0) : 1.0;
+  double ph = atan2(x[1], x[0]);
+  if (ph < 0.0) ph += 2.0 * 3.14159265358979323846;
+  q[0] = r;
+  q[1] = acos(c);
+  q[2] = ph;
+}
+
+// Tensor-product interpolation on a shell at numeric (r, theta, phi): the r
+// and theta windows must lie in the interior, the phi window wraps.
+template <int P, typename ST>
+__device__ __forceinline__ bool interp_point_shell(const ST* __restrict__ src, const Geom& g, double r, double th,
+                                                   double ph, double& o0, double& o1) {
+  double wx[P], wy[P], wz[P];
+  const int sx = lagrange_weights<P>((r - g.lo[0]) / g.h[0] - 0.5, wx);
+  const int sy = lagrange_weights<P>((th - g.lo[1]) / g.h[1] - 0.5, wy);
+  const int sz = lagrange_weights<P>((ph - g.lo[2]) / g.h[2] - 0.5, wz);
+  if (sx < 0 || sy < 0 || sx + P > g.n[0] || sy + P > g.n[1]) return false;
+  const ST* s0 = src;
+  const ST* s1 = src + g.vol;
+  double a0 = 0.0, a1 = 0.0;
+#pragma unroll 1
+  for (int c = 0; c < P; ++c) {
+    const int kz = wrap_index(sz + c, g.n[2]);
+    double b0 = 0.0, b1 = 0.0;
+#pragma unroll
+    for (int b = 0; b < P; ++b) {
+      const long long row = g.at(sx, sy + b, kz);
+      double r0 = 0.0, r1 = 0.0;
+#pragma unroll
+      for (int a = 0; a < P; ++a) {
+        r0 = fma(wx[a], (double)s0[row + a], r0);
+        r1 = fma(wx[a], (double)s1[row + a], r1);
+      }
+      b0 = fma(wy[b], r0, b0);
+      b1 = fma(wy[b], r1, b1);
+    }
+    a0 = fma(wz[c], b0, a0);
+    a1 = fma(wz[c], b1, a1);
+  }
+  o0 = a0;
+  o1 = a1;
+  return true;
+}
+
 // Maps idx in [0, Ox*Oy*Oz - Ix*Iy*Iz) onto the points of the hollow box of
 // outer extent O whose walls are th thick (I = max(O - 2 th, 0)).
 __device__ __forceinline__ void shell_point(long long idx, const int O[3], int th, int& x, int& y, int& z) {
@@ -253,8 +315,6 @@ __device__ __forceinline__ void shell_point(long long idx, const int O[3], int t
   y = th + yy;
   x = xs < th ? xs : xs + Ix;
 }
-
-__device__ __forceinline__ int wrap_index(int i, int n) { return ((i % n) + n) % n; }
 
 // ---------------------------------------------------------------------------
 // Patch maps X_B = R X' + X0 (Sec. 2.4, numeric -> background).  The cover

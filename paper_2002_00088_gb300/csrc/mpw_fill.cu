@@ -461,6 +461,119 @@ __device__ __forceinline__ void l2g_point(const FillArgs& A, const InterpSeg& S,
   e1 = max(e1, biased_exponent(v1));
 }
 
+// Fixed-point tensor sum at donor index coordinates sidx, the donors gathered
+// and converted on the fly; WRAP: the third axis is periodic (a shell's
+// azimuth).  False when the window leaves the donor interior.
+template <int P, bool WRAP>
+__device__ __forceinline__ bool gather_fixed(const InterpSeg& S, const double sidx[3], const int E[2], double& v0,
+                                             double& v1) {
+  int2 wx[P], wy[P], wz[P];
+  int st[3];
+  fixed_weights<P>(sidx, wx, wy, wz, st);
+  if (st[0] < 0 || st[1] < 0 || st[0] + P > S.gd.n[0] || st[1] + P > S.gd.n[1]) return false;
+  if (!WRAP && (st[2] < 0 || st[2] + P > S.gd.n[2])) return false;
+  const double* D = reinterpret_cast<const double*>(S.D);
+  long long out[2];
+  contract_point_fixed<P>(wx, wy, wz, [&](int f, int a, int b, int c) {
+    const int kz = WRAP ? wrap_index(st[2] + c, S.gd.n[2]) : st[2] + c;
+    return split31(to_fixed(D[f * S.gd.vol + S.gd.at(st[0] + a, st[1] + b, kz)], E[f]) * 64);
+  }, out);
+  v0 = (double)out[0] * __longlong_as_double((long long)(E[0] - 58) << 52);
+  v1 = (double)out[1] * __longlong_as_double((long long)(E[1] - 58) << 52);
+  return true;
+}
+
+// Local-to-Global from a spherical shell: the global cell centre goes to the
+// shell's Cartesian frame (M, shift), then to (r, theta, phi); the azimuthal
+// window wraps.  Fixed point, or direct FP64 sums (native FP64, non-finite
+// donors).
+template <int P, typename ST>
+__device__ __forceinline__ void l2g_point_sph(const FillArgs& A, const InterpSeg& S, int i, int j, int k, int& e0,
+                                              int& e1) {
+  const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+  const bool fx = sizeof(ST) == 8 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
+  double xf[3], q[3];
+  affine(S.M, S.shift, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
+         S.gt.lo[2] + (k + 0.5) * S.gt.h[2], xf[0], xf[1], xf[2]);
+  cart_to_sph(xf, q);
+  double v0, v1;
+  bool ok;
+  if (fx) {
+    const double sidx[3] = {(q[0] - S.gd.lo[0]) / S.gd.h[0] - 0.5, (q[1] - S.gd.lo[1]) / S.gd.h[1] - 0.5,
+                            (q[2] - S.gd.lo[2]) / S.gd.h[2] - 0.5};
+    const int E[2] = {max(dslot[0], 64), max(dslot[1], 64)};
+    ok = gather_fixed<P, true>(S, sidx, E, v0, v1);
+  } else {
+    ok = interp_point_shell<P>(reinterpret_cast<const ST*>(S.D), S.gd, q[0], q[1], q[2], v0, v1);
+  }
+  if (!ok) {
+    atomicOr(A.err, ERR_UNFILLED);
+    return;
+  }
+  ST* Tt = reinterpret_cast<ST*>(S.T);
+  const long long c = S.gt.at(i, j, k);
+  Tt[c] = (ST)v0;
+  Tt[c + S.gt.vol] = (ST)v1;
+  e0 = max(e0, biased_exponent(v0));
+  e1 = max(e1, biased_exponent(v1));
+}
+
+// The ghost nodes of a spherical shell, one thread per node of its hollow
+// padded box.  Azimuthal ghosts (r and theta inside the live ranges) take
+// their periodic image, the same physical point, from the shell's own
+// interior; the others interpolate the global patch at X_B = M X' + shift
+// (Sec. 2.4: the shell's radial and polar ghosts come from the global patch).
+template <int P, typename ST>
+__device__ __noinline__ void sph_ghost_block(const FillArgs& A, const InterpSeg& S, int r) {
+  constexpr bool F32 = sizeof(ST) == 4;
+  const int O[3] = {S.gt.n[0] + 2 * NG, S.gt.n[1] + 2 * NG, S.gt.n[2] + 2 * NG};
+  const long long count = (long long)O[0] * O[1] * O[2] - (long long)S.gt.n[0] * S.gt.n[1] * S.gt.n[2];
+  const long long idx = (long long)r * FILL_THREADS + threadIdx.x;
+  int e0 = 0, e1 = 0;
+  if (idx < count) {
+    int x, y, z;
+    shell_point(idx, O, NG, x, y, z);
+    const int i = x - NG, j = y - NG, k = z - NG;
+    ST* Tt = reinterpret_cast<ST*>(S.T);
+    const long long c = S.gt.at(i, j, k);
+    if (i >= 0 && i < S.gt.n[0] && j >= 0 && j < S.gt.n[1]) {
+      const long long src = S.gt.at(i, j, wrap_index(k, S.gt.n[2]));
+      const ST v0 = Tt[src], v1 = Tt[src + S.gt.vol];
+      Tt[c] = v0;
+      Tt[c + S.gt.vol] = v1;
+      e0 = biased_exponent((double)v0);
+      e1 = biased_exponent((double)v1);
+    } else {
+      double xl[3], xb[3];
+      sph_to_cart(S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
+                  S.gt.lo[2] + (k + 0.5) * S.gt.h[2], xl);
+      affine(S.M, S.shift, xl[0], xl[1], xl[2], xb[0], xb[1], xb[2]);
+      const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+      const bool fx = !F32 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
+      double v0, v1;
+      bool ok;
+      if (fx) {
+        double sidx[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) sidx[a] = (xb[a] - S.gd.lo[a]) / S.gd.h[a] - 0.5;
+        const int E[2] = {max(dslot[0], 64), max(dslot[1], 64)};
+        ok = gather_fixed<P, false>(S, sidx, E, v0, v1);
+      } else {
+        ok = interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, xb[0], xb[1], xb[2], v0, v1);
+      }
+      if (ok) {
+        Tt[c] = (ST)v0;
+        Tt[c + S.gt.vol] = (ST)v1;
+        e0 = biased_exponent(v0);
+        e1 = biased_exponent(v1);
+      } else {
+        atomicOr(A.err, ERR_UNFILLED);
+      }
+    }
+  }
+  if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, e0, e1);
+}
+
 // Local-to-Global under a rotating map, from the cover flags: one thread per
 // cell of the covered bounding box; the cells whose flag byte is S.want
 // (effective ghosts of this patch) are filled.
@@ -474,7 +587,12 @@ __device__ __noinline__ void masked_block(const FillArgs& A, const InterpSeg& S,
   if (idx < (long long)w0 * w1 * w2) {
     const int i = b.lo[0] + (int)(idx % w0), j = b.lo[1] + (int)((idx / w0) % w1),
               k = b.lo[2] + (int)(idx / ((long long)w0 * w1));
-    if (S.flags[((long long)k * S.gt.n[1] + j) * S.gt.n[0] + i] == S.want) l2g_point<P, ST>(A, S, i, j, k, e0, e1);
+    if (S.flags[((long long)k * S.gt.n[1] + j) * S.gt.n[0] + i] == S.want) {
+      if (S.sph)
+        l2g_point_sph<P, ST>(A, S, i, j, k, e0, e1);
+      else
+        l2g_point<P, ST>(A, S, i, j, k, e0, e1);
+    }
   }
   if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, e0, e1);
 }
@@ -492,7 +610,10 @@ __device__ __noinline__ void list_block(const FillArgs& A, const InterpSeg& S, i
       const long long idx = S.list[e];
       const int i = (int)(idx % S.gt.n[0]);
       const long long rr = idx / S.gt.n[0];
-      l2g_point<P, ST>(A, S, i, (int)(rr % S.gt.n[1]), (int)(rr / S.gt.n[1]), e0, e1);
+      if (S.sph)
+        l2g_point_sph<P, ST>(A, S, i, (int)(rr % S.gt.n[1]), (int)(rr / S.gt.n[1]), e0, e1);
+      else
+        l2g_point<P, ST>(A, S, i, (int)(rr % S.gt.n[1]), (int)(rr / S.gt.n[1]), e0, e1);
     }
   }
   if (!F32) report_block_max(A.expo + S.tpatch * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.y_buf * 2, e0, e1);
@@ -791,6 +912,10 @@ __device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
   }
   if (S.kind == SEG_LIST) {
     list_block<P, ST>(A, S, r);
+    return;
+  }
+  if (S.kind == SEG_SPH_GHOSTS) {
+    sph_ghost_block<P, ST>(A, S, r);
     return;
   }
   int sl = 0;

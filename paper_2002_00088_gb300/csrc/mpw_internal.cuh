@@ -101,19 +101,24 @@ struct RhsArgs {
 // One interpolation target set: the hollow box shell (walls NG thick) of a
 // target patch, filled from a donor patch.  The shell is cut into six slabs
 // (z-, z+, y-, y+, x-, x+), each tiled by boxes of td targets.
-enum { SEG_SHELL = 0, SEG_AFFINE = 1, SEG_MASKED = 2, SEG_LIST = 3 };
+enum { SEG_SHELL = 0, SEG_AFFINE = 1, SEG_MASKED = 2, SEG_LIST = 3, SEG_SPH_GHOSTS = 4 };
 
 struct InterpSeg {
   int kind;            // SEG_SHELL: hollow box under translation (separable passes);
                        // SEG_AFFINE: hollow box under a rotating map (direct sums);
                        // SEG_MASKED: the global cells of flag `want` inside `box`;
-                       // SEG_LIST: the global cells listed by the cover-flag kernel
+                       // SEG_LIST: the global cells listed by the cover-flag kernel;
+                       // SEG_SPH_GHOSTS: every ghost node of a spherical shell (azimuthal
+                       // ghosts copy their periodic image, the others interpolate the
+                       // global patch through X_B = M X'(r, theta, phi) + shift)
   double M[9];         // SEG_AFFINE / SEG_MASKED / SEG_LIST: donor position = M target position + shift
   double sidx[3][4];   // the same as donor index coordinates of target cell (i, j, k):
                        // s_a = sidx[a][0] i + sidx[a][1] j + sidx[a][2] k + sidx[a][3]
   const long long* list;  // SEG_LIST: linear global cell indices, *count of them
   const int* count;
   int list_blocks;     // SEG_LIST: CTAs striding over the list
+  int sph;             // SEG_MASKED / SEG_LIST: the donor is a spherical shell (M, shift map
+                       // the target to the donor's Cartesian frame)
   Box box;             // SEG_MASKED: target cells to test (global indices)
   const uint8_t* flags;
   int want;            // flag byte of the cells to fill (state | owner << 2)
@@ -160,6 +165,32 @@ struct FillArgs {
   int f32;             // field buffers hold binary32 (FP32 arithmetic; fixed is ignored)
 };
 
+// ---------------------------------------------------------------- shell RHS
+// Fused RHS + RK4 stage on spherical shells (plain FP64, one thread per point).
+struct ShellPatch {
+  const double* Y;     // stencil input (psi; Pi at +vol), ghosts filled
+  const double* U;
+  double* ACC;
+  double* OUT;
+  Geom g;              // numeric (r, theta, phi)
+  double R[9];         // frame velocity w(X') = w0 + W X' (patch frame components)
+  double w0[3], W[9];
+  int moving;
+  int patch;           // patch id (exponent slots)
+  long long block0;
+};
+
+struct ShellArgs {
+  ShellPatch p[MAX_PATCHES];
+  int np;
+  int stage;
+  double alpha, beta, ko_eps;
+  int in_buf, out_buf;
+  int* expo;
+};
+
+void launch_rhs_shell(const ShellArgs& a, long long blocks, void* stream);
+
 // ---------------------------------------------------------------- flags
 struct FlagArgs {
   uint8_t* flags;
@@ -183,6 +214,11 @@ struct FlagArgs {
   float scrm[MAX_PATCHES];     // decision margin of the screen (above 25 x its rounding error)
   uint8_t* cov;
   long long cov_off[MAX_PATCHES + 1];
+  // spherical shells: cov holds, per cell of the bounding box, the L-infinity
+  // distance to the nearest uncovered cell capped at DIST_CAP (0: uncovered),
+  // from a separable transform over two more regions of cov_off[nloc] bytes
+  int sph[MAX_PATCHES];
+  double cth[MAX_PATCHES][2];  // cos(theta_lo), cos(theta_hi)
   // effective ghosts of each rotating patch, listed for Local-to-Global:
   // glist[cov_off[q] ...], gcount[q] entries (null: no lists)
   long long* glist;
@@ -204,6 +240,7 @@ struct FlagArgs {
   int f32;             // field buffers hold binary32
 };
 constexpr int REVIVE_CAP = 1 << 16;  // queue entries (one box crossing revives a few thousand cells)
+constexpr int DIST_CAP = 9;          // distances above buffer + NG (<= 8) read as "dead" 
 
 // Record the thread-local message returned by mpw_last_error().
 void set_last_error(const char* msg);
@@ -242,8 +279,9 @@ struct Affine {
   double X0[3];
 };
 // X_B = R X' + X0 for every interior point (the patch map at t).
+// sph: g's numeric coordinates are (r, theta, phi) of a spherical shell.
 void launch_analytic(void* buf, const Geom& g, const Affine& map, int akind, int acount, const double* aparams,
-                     const float4* screen, const double* apre, double t, bool f32, void* stream);
+                     const float4* screen, const double* apre, double t, bool f32, void* stream, bool sph = false);
 void launch_pack(const void* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags, bool f32,
                  void* stream);
 void launch_unpack(void* buf, const Geom& g, const double* d0, const double* d1, bool f32, void* stream);

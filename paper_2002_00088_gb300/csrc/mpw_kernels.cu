@@ -28,6 +28,20 @@ __global__ void __launch_bounds__(256) k_cover(const __grid_constant__ FlagArgs 
   const int w0 = b.hi[0] - b.lo[0] + 1, w1 = b.hi[1] - b.lo[1] + 1;
   const int i = b.lo[0] + (int)(r % w0), j = b.lo[1] + (int)((r / w0) % w1), k = b.lo[2] + (int)(r / ((long long)w0 * w1));
   const Geom& gl = A.gl[q];
+  if (A.sph[q]) {
+    // a shell covers r_lo <= r <= r_hi and r cos(theta_hi) <= z' <= r cos(theta_lo),
+    // rounded as written (the oracle's order); covered cells start at the
+    // distance cap for the transform that follows
+    double xl[3];
+    to_local_rn(A.R[q], A.X0[q], node_rn(A.gg.lo[0], i, A.gg.h[0]), node_rn(A.gg.lo[1], j, A.gg.h[1]),
+                node_rn(A.gg.lo[2], k, A.gg.h[2]), xl);
+    const double rr =
+        __dsqrt_rn(__dadd_rn(__dadd_rn(__dmul_rn(xl[0], xl[0]), __dmul_rn(xl[1], xl[1])), __dmul_rn(xl[2], xl[2])));
+    const bool in = gl.lo[0] <= rr && rr <= A.lhi[q][0] && __dmul_rn(rr, A.cth[q][1]) <= xl[2] &&
+                    xl[2] <= __dmul_rn(rr, A.cth[q][0]);
+    A.cov[idx] = in ? DIST_CAP : 0;
+    return;
+  }
   // binary32 screen: a cell whose screened position is at least the margin
   // from every face is decided by it (the margin exceeds 25 times the
   // screen's rounding error); the others take the exact test
@@ -53,6 +67,35 @@ __global__ void __launch_bounds__(256) k_cover(const __grid_constant__ FlagArgs 
   A.cov[idx] = in ? 1 : 0;
 }
 
+// One pass of the L-infinity distance transform over the bounding box of every
+// spherical shell, along axis ax: out = min over |t| < DIST_CAP of
+// max(|t|, in(cell + t e_ax)), cells outside the box reading 0 (uncovered).
+// Three passes (x, y, z) from the covered mask (DIST_CAP / 0) give, per cell,
+// the distance to the nearest uncovered cell capped at DIST_CAP: max(a,
+// min f) = min max(a, f) makes the cube metric separable.
+__global__ void __launch_bounds__(256) k_cdt(const __grid_constant__ FlagArgs A, int ax, const uint8_t* __restrict__ in,
+                                             uint8_t* __restrict__ out) {
+  const long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (idx >= A.cov_off[A.nloc]) return;
+  int q = 0;
+  while (idx >= A.cov_off[q + 1]) ++q;
+  if (!A.sph[q]) return;
+  const Box& b = A.box[q];
+  const long long r = idx - A.cov_off[q];
+  const int w[3] = {b.hi[0] - b.lo[0] + 1, b.hi[1] - b.lo[1] + 1, b.hi[2] - b.lo[2] + 1};
+  const int pos[3] = {(int)(r % w[0]), (int)((r / w[0]) % w[1]), (int)(r / ((long long)w[0] * w[1]))};
+  const long long stride = ax == 0 ? 1 : (ax == 1 ? (long long)w[0] : (long long)w[0] * w[1]);
+  int best = in[idx];
+#pragma unroll
+  for (int t = 1; t < DIST_CAP; ++t) {
+    const int lo = pos[ax] - t, hi = pos[ax] + t;
+    const int vl = lo >= 0 ? in[idx - t * stride] : 0;
+    const int vh = hi < w[ax] ? in[idx + t * stride] : 0;
+    best = min(best, max(t, min(vl, vh)));
+  }
+  out[idx] = (uint8_t)best;
+}
+
 // Covered state of global cell (i, j, k) for rotating patch q (cells outside
 // its bounding box are uncovered).
 __device__ __forceinline__ bool covered_rot(const FlagArgs& A, int q, int i, int j, int k) {
@@ -67,7 +110,12 @@ __device__ __forceinline__ void cell_in_local(const FlagArgs& A, int q, int i, i
                                               double& z) {
   const double xb = A.gg.lo[0] + (i + 0.5) * A.gg.h[0], yb = A.gg.lo[1] + (j + 0.5) * A.gg.h[1],
                zb = A.gg.lo[2] + (k + 0.5) * A.gg.h[2];
-  if (A.rot[q]) {
+  if (A.sph[q]) {
+    double xl[3], qs[3];
+    to_local_rn(A.R[q], A.X0[q], xb, yb, zb, xl);
+    cart_to_sph(xl, qs);
+    x = qs[0], y = qs[1], z = qs[2];
+  } else if (A.rot[q]) {
     double xl[3];
     to_local_rn(A.R[q], A.X0[q], xb, yb, zb, xl);
     x = xl[0], y = xl[1], z = xl[2];
@@ -120,6 +168,15 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
   for (int q = 0; valid && q < A.nloc; ++q) {
     const Box& b = A.box[q];
     if (i >= b.lo[0] && i <= b.hi[0] && j >= b.lo[1] && j <= b.hi[1] && k >= b.lo[2] && k <= b.hi[2]) {
+      if (A.sph[q]) {
+        // the transform's distance (0: uncovered)
+        const long long w0 = b.hi[0] - b.lo[0] + 1, w1 = b.hi[1] - b.lo[1] + 1;
+        const int dd = A.cov[A.cov_off[q] + ((long long)(k - b.lo[2]) * w1 + (j - b.lo[1])) * w0 + (i - b.lo[0])];
+        if (dd == 0) continue;
+        owner = q + 1;
+        d = dd;
+        break;
+      }
       if (A.rot[q]) {
         if (!covered_rot(A, q, i, j, k)) continue;
         owner = q + 1;
@@ -142,9 +199,10 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
       break;
     }
   }
-  // effective ghosts of a rotating patch join that patch's list, one atomic
+  // effective ghosts of a rotating patch or a shell join that patch's list, one atomic
   // per warp and patch (every lane of the warp takes part)
-  const bool ghost_rot = valid && A.glist && owner > 0 && A.rot[owner - 1] && d > A.buffer && d <= A.buffer + NG;
+  const bool ghost_rot = valid && A.glist && owner > 0 && (A.rot[owner - 1] || A.sph[owner - 1]) &&
+                         d > A.buffer && d <= A.buffer + NG;
   const int gq = ghost_rot ? owner - 1 : -1;
   const unsigned peers = __match_any_sync(0xffffffffu, gq);
   if (gq >= 0) {
@@ -177,7 +235,8 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
     }
     double v0, v1, x, y, z;
     cell_in_local(A, q, i, j, k, x, y, z);
-    const bool ok = interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1);
+    const bool ok = A.sph[q] ? interp_point_shell<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1)
+                             : interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1);
     if (!ok) {
       atomicOr(A.err, ERR_UNFILLED);
       return;
@@ -211,7 +270,8 @@ __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs
       const int k = (int)(rr / A.n[1]);
       double v0, v1, x, y, z;
       cell_in_local(A, q, i, j, k, x, y, z);
-      if (interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1)) {
+      if (A.sph[q] ? interp_point_shell<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1)
+                   : interp_point<P>(reinterpret_cast<const ST*>(A.Uloc[q]), A.gl[q], x, y, z, v0, v1)) {
         const long long c = A.gg.at(i, j, k);
         ST* Ug = reinterpret_cast<ST*>(A.Ug);
         Ug[c] = (ST)v0;
@@ -235,6 +295,15 @@ template <int P, typename ST>
 static void launch_flags_t(const FlagArgs& a, unsigned blocks, unsigned rblocks, cudaStream_t s) {
   const long long ncov = a.cov_off[a.nloc];
   if (ncov > 0) k_cover<<<(unsigned)((ncov + 255) / 256), 256, 0, s>>>(a);
+  bool any_sph = false;
+  for (int q = 0; q < a.nloc; ++q) any_sph = any_sph || a.sph[q];
+  if (any_sph) {
+    // distance transform: mask -> region 1 (x) -> region 2 (y) -> region 0 (z)
+    const unsigned cb = (unsigned)((ncov + 255) / 256);
+    k_cdt<<<cb, 256, 0, s>>>(a, 0, a.cov, a.cov + ncov);
+    k_cdt<<<cb, 256, 0, s>>>(a, 1, a.cov + ncov, a.cov + 2 * ncov);
+    k_cdt<<<cb, 256, 0, s>>>(a, 2, a.cov + 2 * ncov, a.cov);
+  }
   k_flags<P, ST><<<blocks, 256, 0, s>>>(a);
   if (a.old_valid) k_revive<P, ST><<<rblocks, 256, 0, s>>>(a);
 }
@@ -253,13 +322,15 @@ int launch_flags(const FlagArgs& a, void* stream) {
     a.P == 6 ? launch_flags_t<6, float>(a, blocks, rblocks, s) : launch_flags_t<5, float>(a, blocks, rblocks, s);
   else
     a.P == 6 ? launch_flags_t<6, double>(a, blocks, rblocks, s) : launch_flags_t<5, double>(a, blocks, rblocks, s);
-  return (a.old_valid ? 2 : 1) + (a.cov_off[a.nloc] > 0 ? 1 : 0);
+  bool any_sph = false;
+  for (int q = 0; q < a.nloc; ++q) any_sph = any_sph || a.sph[q];
+  return (a.old_valid ? 2 : 1) + (a.cov_off[a.nloc] > 0 ? 1 : 0) + (any_sph ? 3 : 0);
 }
 
 // ---------------------------------------------------------------------------
 // Interior <- closed form at time t (positions X_B = numeric + X0).
 template <typename ST>
-__global__ void k_analytic(ST* buf, const Geom g, const Affine map, int rot, int akind, int acount,
+__global__ void k_analytic(ST* buf, const Geom g, const Affine map, int rot, int sph, int akind, int acount,
                            const double* __restrict__ P, const float4* __restrict__ screen,
                            const double* __restrict__ apre, double t) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
@@ -271,7 +342,11 @@ __global__ void k_analytic(ST* buf, const Geom g, const Affine map, int rot, int
   const int k = (int)(r / g.n[1]);
   const double x = g.lo[0] + (i + 0.5) * g.h[0], y = g.lo[1] + (j + 0.5) * g.h[1], z = g.lo[2] + (k + 0.5) * g.h[2];
   double xb, yb, zb;
-  if (rot) {
+  if (sph) {
+    double xl[3];
+    sph_to_cart(x, y, z, xl);
+    affine(map.R, map.X0, xl[0], xl[1], xl[2], xb, yb, zb);
+  } else if (rot) {
     double b[3];
     to_background_rn(map.R, map.X0, node_rn(g.lo[0], i, g.h[0]), node_rn(g.lo[1], j, g.h[1]),
                      node_rn(g.lo[2], k, g.h[2]), b);
@@ -287,16 +362,16 @@ __global__ void k_analytic(ST* buf, const Geom g, const Affine map, int rot, int
 }
 
 void launch_analytic(void* buf, const Geom& g, const Affine& map, int akind, int acount, const double* aparams,
-                     const float4* screen, const double* apre, double t, bool f32, void* stream) {
+                     const float4* screen, const double* apre, double t, bool f32, void* stream, bool sph) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   const unsigned blocks = (unsigned)((N + 255) / 256);
   int rot = 0;
   for (int e = 0; e < 9; ++e) rot |= map.R[e] != ((e % 4 == 0) ? 1.0 : 0.0);
   if (f32)
-    k_analytic<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<float*>(buf), g, map, rot, akind, acount,
-                                                                aparams, screen, apre, t);
+    k_analytic<float><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<float*>(buf), g, map, rot, sph, akind,
+                                                                acount, aparams, screen, apre, t);
   else
-    k_analytic<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<double*>(buf), g, map, rot, akind,
+    k_analytic<double><<<blocks, 256, 0, (cudaStream_t)stream>>>(static_cast<double*>(buf), g, map, rot, sph, akind,
                                                                  acount, aparams, screen, apre, t);
 }
 

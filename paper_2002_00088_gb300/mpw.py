@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "MPW_OK", 1: "MPW_ERR_ARG", 2: "MPW_ERR_OVERLAP", 3: "MPW_ERR
 PATCH_GLOBAL, PATCH_LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
 MOTION_STATIC, MOTION_LINEAR, MOTION_CIRCULAR, MOTION_ROTATING = 0, 1, 2, 3
+TOPOLOGY_CARTESIAN, TOPOLOGY_SPHERICAL = 0, 1
 ANALYTIC_GAUSS_SUM, ANALYTIC_PLANE_SUM, ANALYTIC_HARMONIC_POLY, ANALYTIC_PLANE_GAUSS = 0, 1, 2, 3
 FLAG_LIVE, FLAG_GHOST, FLAG_DEAD, FLAG_REVIVED = 0, 1, 2, 3
 NG = 3
@@ -37,7 +38,8 @@ class mpw_config(C.Structure):
 
 class mpw_patch_desc(C.Structure):
     _fields_ = [("kind", C.c_int), ("n", C.c_int * 3), ("lo", C.c_double * 3), ("hi", C.c_double * 3),
-                ("outer_bc", C.c_int), ("motion", C.c_int), ("motion_params", C.c_double * 16)]
+                ("outer_bc", C.c_int), ("motion", C.c_int), ("motion_params", C.c_double * 16),
+                ("topology", C.c_int)]
 
 
 # Every symbol that include/mpw.h declares, with its ctypes signature.
@@ -166,9 +168,11 @@ class Multipatch:
             pass
 
     # -- setup --------------------------------------------------------------
-    def create_patch(self, kind, n, lo, hi, outer_bc, motion=MOTION_STATIC, motion_params=()):
+    def create_patch(self, kind, n, lo, hi, outer_bc, motion=MOTION_STATIC, motion_params=(),
+                     topology=TOPOLOGY_CARTESIAN):
         d = mpw_patch_desc()
         d.kind = kind
+        d.topology = topology
         for a in range(3):
             d.n[a] = int(n[a])
             d.lo[a] = float(lo[a])

@@ -18,7 +18,7 @@ def gpu_from(mpw, w, buffer=0, arith=0, precision=64):
     s = mpw.Multipatch(interp_points=w.interp_points, ko_eps=w.ko_eps, buffer=buffer, arith=arith,
                        precision=precision)
     for p in w.patches:
-        s.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params)
+        s.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
     s.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
     return s
 
