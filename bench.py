@@ -66,6 +66,8 @@ def parse():
                          "batched launches, beside the same instances stepped one after the other")
     ap.add_argument("--max-global", type=int, default=192, help="--batch: largest global patch edge")
     ap.add_argument("--static", action="store_true", help="--batch: local patches do not move (graph replay)")
+    ap.add_argument("--shells", action="store_true",
+                    help="--batch: every second instance holds a spherical shell instead of local cubes")
     ap.add_argument("--motion", default="orbiting", choices=["orbiting", "spinning"],
                     help="orbiting: translating local patches on circular orbits (default); spinning: the "
                          "rotating-patch workload")
@@ -447,7 +449,7 @@ def run_batch(args):
     from paper_2002_00088_gb300 import mpw
     from paper_2002_00088_gb300 import workloads as wl
     ws = wl.batch_instances(count=args.batch, steps=args.warmup + args.steps + 4, max_global=args.max_global,
-                            moving=not args.static)
+                            moving=not args.static, shells=args.shells)
     stream = torch.cuda.current_stream(local)
 
     def make():
@@ -498,11 +500,13 @@ def run_batch(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32" if args.precision == 32 else "f64",
         "data": "synthetic (seeded closed-form Gaussian pulses)",
         "config": {"workload": f"batch of {len(ws)} instances (globals 64^3-{args.max_global}^3, 1-8 "
-                               f"{'static' if args.static else 'moving'} locals each)",
+                               f"{'static' if args.static else 'moving'} locals each"
+                               f"{'; every second instance one ' + ('static' if args.static else 'spinning') + ' spherical shell r in [0.1, 0.5]' if args.shells else ''})",
                    "instances": len(ws), "live_points": live, "parallelism": "single",
                    "rhs_chunk_depth": zc, "tuning_rhs_ms": zc_ms, "graph_replayed_steps": graph_steps},
         "sequential": {"value": live * 4 * args.steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps},
-        "gpu_launches": 8 * args.steps, "clocks": clocks,
+        "gpu_launches": (8 + 4 * -(-sum(1 for w in ws for p in w.patches if p.topology) // 64)) * args.steps,
+        "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
     return 0

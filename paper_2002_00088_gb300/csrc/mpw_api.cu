@@ -50,6 +50,7 @@ struct PatchState {
   Geom g;
   bool u_expo_valid = false;  // exponent slots of u track its live values
   double* base = nullptr;     // 4 buffers x 2 fields x vol elements (binary64, or binary32 when esize = 4)
+  double* tab = nullptr;      // spherical shell: node tables of the RHS (see ShellPatch)
   size_t esize = 8;           // bytes per element
   CUtensorMap tile_map[4];    // RHS input tiles of each buffer (TMA)
   CUtensorMap point_map[2];   // RHS stage operands: u, ACC (TMA)
@@ -917,26 +918,34 @@ int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
   return blocks;
 }
 
-// RHS + stage arguments of substage l for the spherical shells of c; returns
-// the number of CTAs (0 without shells).
-long long prep_rhs_shell(mpw_ctx* c, int l, double t, double dt, ShellArgs& a) {
+// RHS + stage arguments of substage l for the spherical shells of c, appended
+// to a (a.np shells so far, `blocks` CTAs so far: one launch may cover the
+// shells of several contexts); returns the new CTA count, or -1 when a
+// would overflow (nothing appended then).
+long long prep_rhs_shell(mpw_ctx* c, int l, double t, double dt, ShellArgs& a, long long blocks = 0) {
   static const int in_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
   static const int out_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
   const double alpha[4] = {0.5 * dt, 0.5 * dt, dt, dt / 6.0};
   const double beta[4] = {dt / 6.0, dt / 3.0, dt / 3.0, 0.0};
-  a = ShellArgs{};
+  int ns = 0;
+  for (size_t q = 1; q < c->p.size(); ++q) ns += c->p[q].sph() ? 1 : 0;
+  if (a.np + ns > MAX_SHELLS) return -1;
   a.stage = l;
-  a.alpha = alpha[l];
-  a.beta = beta[l];
-  a.ko_eps = c->cfg.ko_eps;
   a.in_buf = in_buf[l];
   a.out_buf = out_buf[l];
-  a.expo = c->d_expo;
-  long long blocks = 0;
   for (size_t q = 1; q < c->p.size(); ++q) {
     const PatchState& P = c->p[q];
     if (!P.sph()) continue;
     ShellPatch& S = a.p[a.np++];
+    S.expo = c->d_expo;
+    S.alpha = alpha[l];
+    S.beta = beta[l];
+    S.tab = P.tab;
+    for (int a2 = 0; a2 < 3; ++a2) {
+      S.id1[a2] = 1.0 / (12.0 * P.g.h[a2]);
+      S.id2[a2] = 1.0 / (12.0 * P.g.h[a2] * P.g.h[a2]);
+      S.iko[a2] = c->cfg.ko_eps / (64.0 * P.g.h[a2]);
+    }
     S.Y = P.buf(in_buf[l]);
     S.U = P.buf(BUF_U);
     S.ACC = P.buf(BUF_ACC);
@@ -961,7 +970,7 @@ mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
   const int blocks = prep_rhs(c, l, t, dt, a);
   bool rot = false;
   for (int q = 0; q < a.np; ++q) rot = rot || a.p[q].rot;
-  ShellArgs sa;
+  ShellArgs sa{};
   const long long sblocks = prep_rhs_shell(c, l, t, dt, sa);
   c->launch_begin(MPW_KERNEL_RHS);
   if (c->cfg.precision == 32)
@@ -1098,6 +1107,7 @@ void mpw_destroy(mpw_ctx* c) {
   if (c->io_out) cudaStreamSynchronize(c->io_out);
   for (auto& P : c->p) {
     c->dfree(P.base);
+    c->dfree(P.tab);
     c->dfree(P.io_in);
     c->dfree(P.io_out);
     for (cudaEvent_t e : {P.in_copied, P.in_free, P.out_packed, P.out_free})
@@ -1191,6 +1201,23 @@ mpw_status mpw_create_patch(mpw_ctx* c, const mpw_patch_desc* d, int* patch_id) 
   if (!encode_rhs_map(&P.point_map[0], P.buf(BUF_U), P.g, false, f32) ||
       !encode_rhs_map(&P.point_map[1], P.buf(BUF_ACC), P.g, false, f32))
     return undo("tensor map encoding failed");
+  if (d->topology == MPW_TOPOLOGY_SPHERICAL) {
+    // node tables: r, 1/r; sin, cos, 1/sin of theta; sin, cos of phi
+    std::vector<double> t;
+    for (int i = 0; i < d->n[0]; ++i) t.push_back(P.g.lo[0] + (i + 0.5) * P.g.h[0]);
+    for (int i = 0; i < d->n[0]; ++i) t.push_back(1.0 / (P.g.lo[0] + (i + 0.5) * P.g.h[0]));
+    for (int j = 0; j < d->n[1]; ++j) t.push_back(std::sin(P.g.lo[1] + (j + 0.5) * P.g.h[1]));
+    for (int j = 0; j < d->n[1]; ++j) t.push_back(std::cos(P.g.lo[1] + (j + 0.5) * P.g.h[1]));
+    for (int j = 0; j < d->n[1]; ++j) t.push_back(1.0 / std::sin(P.g.lo[1] + (j + 0.5) * P.g.h[1]));
+    for (int k = 0; k < d->n[2]; ++k) t.push_back(std::sin(P.g.lo[2] + (k + 0.5) * P.g.h[2]));
+    for (int k = 0; k < d->n[2]; ++k) t.push_back(std::cos(P.g.lo[2] + (k + 0.5) * P.g.h[2]));
+    P.tab = (double*)c->dalloc(sizeof(double) * t.size());
+    if (!P.tab) return undo("shell table allocation failed");
+    if (cudaMemcpy(P.tab, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+      c->dfree(P.tab);
+      return undo("shell table upload failed");
+    }
+  }
   if (d->kind == MPW_PATCH_GLOBAL) {
     const size_t nb = (size_t)d->n[0] * d->n[1] * d->n[2];
     c->d_flags = (uint8_t*)c->dalloc(nb);
@@ -1754,14 +1781,27 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     bool rot = false;  // some patch rotates: the RHS kernels with a position-dependent w
     for (mpw_ctx* c : b->ctx)
       for (const auto& P : c->p) rot = rot || P.d.motion == MPW_MOTION_ROTATING;
-    // spherical shells: their own RHS launch per instance after each batched one
+    // spherical shells: after each batched RHS launch, one launch over the
+    // shells of all instances (more launches when they exceed MAX_SHELLS)
     std::vector<ShellArgs> sargs;
     std::vector<long long> sblocks;
-    for (int l = 0; l < 4; ++l)
+    std::vector<int> sfirst(5, 0);
+    for (int l = 0; l < 4; ++l) {
+      sfirst[l] = (int)sargs.size();
+      sargs.emplace_back();
+      sblocks.push_back(0);
       for (int i = 0; i < n; ++i) {
-        sargs.emplace_back();
-        sblocks.push_back(prep_rhs_shell(b->ctx[i], l, tnp[i] + RK_C[l] * dt[i], dt[i], sargs.back()));
+        long long nb = prep_rhs_shell(b->ctx[i], l, tnp[i] + RK_C[l] * dt[i], dt[i], sargs.back(), sblocks.back());
+        if (nb < 0) {  // full: start another launch
+          sargs.emplace_back();
+          sblocks.push_back(0);
+          nb = prep_rhs_shell(b->ctx[i], l, tnp[i] + RK_C[l] * dt[i], dt[i], sargs.back(), 0);
+          if (nb < 0) return set_err(MPW_ERR_ARG, "an instance holds more than %d shells", MAX_SHELLS);
+        }
+        sblocks.back() = nb;
       }
+    }
+    sfirst[4] = (int)sargs.size();
     // copies and launches of the step, on stream sm
     auto enqueue = [&](cudaStream_t sm) -> cudaError_t {
       for (int r = 0; r < 8; ++r) {
@@ -1780,8 +1820,8 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
             launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], rot, sm);
           else
             launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], b->fixed, rot, sm);
-          for (int i = 0; i < n; ++i)
-            if (sblocks[l * n + i] > 0) launch_rhs_shell(sargs[l * n + i], sblocks[l * n + i], sm);
+          for (int k2 = sfirst[l]; k2 < sfirst[l + 1]; ++k2)
+            if (sblocks[k2] > 0) launch_rhs_shell(sargs[k2], sblocks[k2], sm);
           if (trial && l == 3) cudaEventRecord(b->tev[2 * k + 1], sm);
         }
         if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -173,20 +173,27 @@ struct ShellPatch {
   double* ACC;
   double* OUT;
   Geom g;              // numeric (r, theta, phi)
+  // per-axis tables of the nodes: r, 1/r (n_r each), sin, cos, 1/sin of theta
+  // (n_theta each), sin, cos of phi (n_phi each)
+  const double* tab;
   double R[9];         // frame velocity w(X') = w0 + W X' (patch frame components)
   double w0[3], W[9];
   int moving;
   int patch;           // patch id (exponent slots)
+  int* expo;           // the exponent slots of the shell's context
+  double alpha, beta;  // stage coefficients (dt of the shell's context)
+  double id1[3], id2[3];  // 1 / (12 h_a), 1 / (12 h_a^2) per numeric axis
+  double iko[3];       // eps / (64 L_a) with L = h_r, h_theta, h_phi (times 1/r, 1/(r sin theta) per point)
   long long block0;
 };
 
+constexpr int MAX_SHELLS = 64;  // shells of one launch (a batch may span several contexts)
+
 struct ShellArgs {
-  ShellPatch p[MAX_PATCHES];
+  ShellPatch p[MAX_SHELLS];
   int np;
   int stage;
-  double alpha, beta, ko_eps;
   int in_buf, out_buf;
-  int* expo;
 };
 
 void launch_rhs_shell(const ShellArgs& a, long long blocks, void* stream);

@@ -213,7 +213,25 @@ def plane_gauss(scale=1, steps=200, interp_points=6, seed_index=2):
                     0.25 * h_min, steps, {"centre": centre, "phase": phase})
 
 
-def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_global=192, moving=True):
+def shell_instance(ng, rs, moving):
+    """One spherical shell r in [0.1, 0.5], theta in [pi/4, 3 pi/4], full
+    azimuth, for a global n_g^3 on [-1,1]^3: physical spacings at most the
+    global one (n_r, n_theta, n_phi rounded up to multiples of 4, 4, 8), centre
+    U[-0.05,0.05]^3, spinning about its local z axis at a seeded angular speed
+    up to pi when moving."""
+    hg = 2.0 / ng
+    up = lambda x, m: int(np.ceil(x / m) * m)
+    n = (up(0.4 / hg, 4), up(0.5 * (np.pi / 2) / hg, 4), up(0.5 * 2 * np.pi / hg, 8))
+    c = rs.uniform(-0.05, 0.05, 3)
+    omega, phase = rs.uniform(-np.pi, np.pi), rs.uniform(0.0, 2.0 * np.pi)
+    mp = (tuple(c) + (0.0, 0.0, 0.0, 0.0, 0.0, 1.0, omega, phase)) if moving else tuple(c)
+    spec = PatchSpec(LOCAL, n, (0.1, np.pi / 4, 0.0), (0.5, 3 * np.pi / 4, 2 * np.pi), BC_INTERPATCH,
+                     ROTATING if moving else STATIC, mp, SPHERICAL)
+    dmin = min(0.4 / n[0], 0.1 * (np.pi / 2) / n[1], 0.1 * np.sin(np.pi / 4) * 2 * np.pi / n[2])
+    return spec, 0.25 * dmin
+
+
+def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_global=192, moving=True, shells=False):
     """Independent instances of uneven sizes for a batched run.
 
     Instance k: a global cube of n_g^3 (n_g from 64 to ``max_global`` in steps
@@ -224,8 +242,12 @@ def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_glob
     steps of dt = h_local/4 the cube keeps its containment margin and its
     gap to the neighbouring octants.  Initial data: two Gaussian pulses
     (amplitudes N(0,1), widths U[0.08,0.2], centres U[-0.8,0.8]^3).  With
-    ``moving=False`` every local cube stays at its octant centre."""
+    ``moving=False`` every local cube stays at its octant centre.  With
+    ``shells=True`` every second instance holds one spherical shell
+    (``shell_instance``, drawn from a second seeded generator) in place of its
+    local cubes."""
     r = rng(seed_index)
+    rs = rng(50 + seed_index)
     out = []
     sizes = [n for n in range(64, max_global + 1, 32)]
     for k in range(count):
@@ -249,8 +271,12 @@ def batch_instances(count=64, steps=100, seed_index=3, interp_points=6, max_glob
                                      (c[0], c[1], c[2], v[0], v[1], v[2])))
         params = np.column_stack([r.normal(0.0, 1.0, 2), r.uniform(0.08, 0.2, 2),
                                   r.uniform(-0.8, 0.8, (2, 3))]).ravel()
-        out.append(Workload(f"instance{k}_{ng}+{nloc}x{nl}", patches, GAUSS_SUM, params, 2, interp_points, 0.005,
-                            dt, steps))
+        name = f"instance{k}_{ng}+{nloc}x{nl}"
+        if shells and k % 2 == 1:
+            spec, dt = shell_instance(ng, rs, moving)
+            patches = patches[:1] + [spec]
+            name = f"instance{k}_{ng}+shell{spec.n[0]}x{spec.n[1]}x{spec.n[2]}"
+        out.append(Workload(name, patches, GAUSS_SUM, params, 2, interp_points, 0.005, dt, steps))
     return out
 
 
