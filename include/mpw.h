@@ -227,8 +227,11 @@ mpw_status mpw_step_async(mpw_ctx* ctx, double dt, int nsteps);
  * Each instance is an ordinary context.  A batched step does per instance
  * what mpw_step does (validation, cover flags, exponent slots), but every
  * ghost fill and every RHS + stage substage is ONE kernel launch over all
- * instances, so small instances share the GPU instead of running one after
- * the other.  Results are bit for bit those of mpw_step on each context.
+ * instances (plus one RHS launch over the spherical shells of up to 64
+ * instances, when there are shells), so small instances share the GPU
+ * instead of running one after the other.  Instances may hold rotating
+ * patches and spherical shells.  Results are bit for bit those of mpw_step
+ * on each context.
  *
  * mpw_batch_create: ctxs[0..n) must be distinct, live, hold a global patch,
  *   and share device, stream, precision, interp_points and arith; the array
@@ -238,14 +241,16 @@ mpw_status mpw_step_async(mpw_ctx* ctx, double dt, int nsteps);
  * mpw_batch_step: advance every instance i by nsteps steps of dt[i] (host
  *   array of n doubles).  The first steps of a batch also tune the RHS
  *   chunk depth (planes marched per CTA): each candidate (8, 16, 32, 64)
- *   runs one step, timed with CUDA events, and the fastest is kept.
+ *   runs one step, timed with CUDA events from the first RHS launch of the
+ *   step to the end of its last one, and the fastest is kept.
  *   Errors as mpw_step, for the first instance that fails.
  *   While no instance has a moving patch, the copies and launches of a step
  *   are captured once in a CUDA graph (one per argument buffer) and replayed:
  *   the launches and grids are then the same every step, and the replayed
  *   copies pick up the new substage times from the page-locked buffers.
  * mpw_batch_tuning: the chosen chunk depth (0 while tuning), its measured
- *   RHS time per step in ms, the number of batched launches so far and the
+ *   time per step in ms (first RHS launch to the end of the last; three ghost
+ *   fills lie in between), the number of batched launches so far and the
  *   number of steps replayed from a captured graph.
  * mpw_batch_destroy: frees the tables (not the contexts). */
 typedef struct mpw_batch mpw_batch;
