@@ -96,6 +96,8 @@ struct mpw_ctx {
   int* d_gcount = nullptr;       // their counts, MAX_PATCHES entries
   std::vector<long long> glist_off;  // per local patch, from the last flag computation
   bool glist_valid = false;          // lists match the current flags
+  int2* d_mirror = nullptr;          // fixed-point mirrors of the shells' donor regions
+  size_t mirror_cap = 0;             // entries
   // Time whose closed form each global buffer's outer shell holds (NaN: none).
   // The RK4 substage times repeat (c = 0, 1/2, 1/2, 1, and t_n + dt starts the
   // next step), so half of the analytic shell evaluations become copies.
@@ -723,9 +725,91 @@ constexpr int L2G_LIST_BLOCKS = 152;
 
 // Ghost fill of the stage buffer `b` at time t; clears the exponent slots of
 // buffer reset_buf (the output of the following RHS launch), if >= 0.
-mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
+// Fixed-point mirrors for the shells of c at time t (fill of buffer b): per
+// shell, the global cells its ghost nodes' windows can reach (the ball of
+// its ghost-extended radius, widened by the window) and its own padded box.
+// mir_global[q] / mir_shell[q]: region of local patch q, or -1.
+mpw_status prep_mirrors(mpw_ctx* c, int b, double t, MirrorArgs& m, int mir_global[], int mir_shell[]) {
+  m = MirrorArgs{};
+  const PatchState& g = c->p[0];
+  const int nloc = (int)c->p.size() - 1;
+  for (int q = 0; q < nloc; ++q) mir_global[q] = mir_shell[q] = -1;
+  if (c->cfg.arith == 1 || c->cfg.precision != 64) return MPW_OK;
+  // capacity from the shells' radii, the same at every substage (a batch
+  // prepares four substages before it enqueues them)
+  size_t need = 0;
+  for (int q = 0; q < nloc; ++q) {
+    const PatchState& L = c->p[q + 1];
+    if (!L.sph()) continue;
+    const double R = L.d.hi[0] + NG * L.g.h[0];
+    size_t vg = 1, vs = 1;
+    for (int a = 0; a < 3; ++a) {
+      vg *= (size_t)std::ceil(2.0 * R / g.g.h[a]) + 9;
+      vs *= (size_t)(L.d.n[a] + 2 * NG);
+    }
+    need += 2 * (vg + vs);
+  }
+  for (int q = 0; q < nloc; ++q) {
+    const PatchState& L = c->p[q + 1];
+    if (!L.sph()) continue;
+    double lo[3], hi[3];
+    background_extent(L.d, t, NG, lo, hi);
+    MirrorRegion& G = m.r[m.nr];
+    G.src = g.buf(b);
+    G.g = g.g;
+    G.patch = 0;
+    for (int a = 0; a < 3; ++a) {
+      const int l0 = (int)std::floor((lo[a] - g.g.lo[a]) / g.g.h[a] - 0.5) - 3;
+      const int h0 = std::min((int)std::floor((hi[a] - g.g.lo[a]) / g.g.h[a] - 0.5) + 4,
+                              l0 + (int)std::ceil(2.0 * (hi[a] - lo[a]) / 2.0 / g.g.h[a]) + 8);
+      G.box.lo[a] = std::max(-NG, l0);
+      G.box.hi[a] = std::min(g.d.n[a] + NG - 1, h0);
+    }
+    mir_global[q] = m.nr++;
+    MirrorRegion& S = m.r[m.nr];
+    S.src = L.buf(b);
+    S.g = L.g;
+    S.patch = q + 1;
+    for (int a = 0; a < 3; ++a) {
+      S.box.lo[a] = -NG;
+      S.box.hi[a] = L.d.n[a] + NG - 1;
+    }
+    mir_shell[q] = m.nr++;
+  }
+  long long blocks = 0;
+  for (int r = 0; r < m.nr; ++r) {
+    const Box& bx = m.r[r].box;
+    const long long vol = (long long)(bx.hi[0] - bx.lo[0] + 1) * (bx.hi[1] - bx.lo[1] + 1) * (bx.hi[2] - bx.lo[2] + 1);
+    m.r[r].block0 = blocks;
+    blocks += (vol + 255) / 256;
+  }
+  m.blocks = blocks;
+  m.expo = c->d_expo;
+  m.y_buf = b;
+  if (need > c->mirror_cap) {
+    c->dfree(c->d_mirror);
+    c->d_mirror = (int2*)c->dalloc(sizeof(int2) * need);
+    c->mirror_cap = c->d_mirror ? need : 0;
+    if (!c->d_mirror) return set_err(MPW_ERR_CUDA, "mirror allocation of %zu entries failed", need);
+  }
+  size_t off = 0;
+  for (int r = 0; r < m.nr; ++r) {
+    const Box& bx = m.r[r].box;
+    m.r[r].dst = c->d_mirror + off;
+    off += 2 * (size_t)(bx.hi[0] - bx.lo[0] + 1) * (bx.hi[1] - bx.lo[1] + 1) * (bx.hi[2] - bx.lo[2] + 1);
+  }
+  return MPW_OK;
+}
+
+mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, MirrorArgs* mirrors = nullptr) {
   const PatchState& g = c->p[0];
   a = FillArgs{};
+  int mir_global[MAX_PATCHES], mir_shell[MAX_PATCHES];
+  for (int q = 0; q < MAX_PATCHES; ++q) mir_global[q] = mir_shell[q] = -1;
+  MirrorArgs local_m{};
+  MirrorArgs& m = mirrors ? *mirrors : local_m;  // without a launch slot: the per-tap path
+  if (mirrors)
+    if (mpw_status st = prep_mirrors(c, b, t, m, mir_global, mir_shell)) return st;
   a.Yg = g.buf(b);
   a.gg = g.g;
   a.outer_bc = g.d.outer_bc == MPW_BC_PERIODIC ? 1 : 0;
@@ -784,6 +868,11 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
         }
       }
       set_index_map(S);
+      S.mir = nullptr;
+      if (L.sph() && mir_shell[q] >= 0) {
+        S.mir = m.r[mir_shell[q]].dst;
+        S.mbox = m.r[mir_shell[q]].box;
+      }
       if (c->glist_valid && q < (int)c->glist_off.size()) {
         S.kind = SEG_LIST;
         S.list = c->d_glist + c->glist_off[q];
@@ -823,6 +912,11 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
     if (L.sph()) {
       // every ghost node of a spherical shell, one thread each
       S.kind = SEG_SPH_GHOSTS;
+      S.mir = nullptr;
+      if (mir_global[q] >= 0) {
+        S.mir = m.r[mir_global[q]].dst;
+        S.mbox = m.r[mir_global[q]].box;
+      }
       S.block0 = blocks;
       const long long cnt = (long long)(L.d.n[0] + 2 * NG) * (L.d.n[1] + 2 * NG) * (L.d.n[2] + 2 * NG) -
                             (long long)L.d.n[0] * L.d.n[1] * L.d.n[2];
@@ -849,8 +943,13 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a) {
 
 mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
   FillArgs a;
-  if (mpw_status st = prep_fill(c, b, t, reset_buf, a)) return st;
+  MirrorArgs m;
+  if (mpw_status st = prep_fill(c, b, t, reset_buf, a, &m)) return st;
   c->launch_begin(MPW_KERNEL_FILL);
+  if (m.nr > 0) {
+    launch_mirror(m, c->stream);
+    c->launches[MPW_KERNEL_FILL] += 1;
+  }
   launch_fill(a, c->stream);
   c->launch_end(MPW_KERNEL_FILL);
   CUDA_TRY(cudaGetLastError());
@@ -1125,6 +1224,7 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_cov);
   c->dfree(c->d_glist);
   c->dfree(c->d_gcount);
+  c->dfree(c->d_mirror);
   c->dfree(c->d_stage);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& v : c->ev)
@@ -1752,6 +1852,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     }
     const int h = (int)(k & 1);
     CUDA_TRY(cudaEventSynchronize(b->copied[h]));  // the pinned half from two steps ago has been copied
+    std::vector<MirrorArgs> mirs(4 * (size_t)n);    // fixed-point mirrors of each instance's fills
     // arguments of the 8 launches of this step into pinned half h
     int totals[8];
     for (int l = 0; l < 4; ++l) {
@@ -1767,7 +1868,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
           blk0[i] = total;
           if (pass == 0) {
             FillArgs* fa = reinterpret_cast<FillArgs*>(hreg) + i;
-            if ((st = prep_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], *fa))) return st;
+            if ((st = prep_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], *fa, &mirs[l * n + i]))) return st;
             total += fa->total_blocks;
           } else {
             RhsArgs* ra = reinterpret_cast<RhsArgs*>(hreg) + i;
@@ -1813,6 +1914,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         if (e != cudaSuccess) return e;
         const int* d_blk0 = reinterpret_cast<const int*>(dreg + esz * n);
         if (pass == 0) {
+          for (int i = 0; i < n; ++i) launch_mirror(mirs[l * n + i], sm);
           launch_fill_batch(reinterpret_cast<const FillArgs*>(dreg), d_blk0, n, totals[r], b->P, b->f32, sm);
         } else {
           if (trial && l == 0) cudaEventRecord(b->tev[2 * k], sm);
@@ -1858,6 +1960,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     if (!replayed) CUDA_TRY(enqueue(b->stream));
     b->launches += 8;
     for (long long sb : sblocks) b->launches += sb > 0 ? 1 : 0;
+    for (const MirrorArgs& ma : mirs) b->launches += ma.nr > 0 ? 1 : 0;
     CUDA_TRY(cudaEventRecord(b->copied[h], b->stream));
     for (int i = 0; i < n; ++i) {
       b->ctx[i]->t = tnp[i] + dt[i];

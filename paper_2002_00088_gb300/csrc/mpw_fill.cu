@@ -483,6 +483,33 @@ __device__ __forceinline__ bool gather_fixed(const InterpSeg& S, const double si
   return true;
 }
 
+// The same sum from the donor's fixed-point mirror (no conversion per tap);
+// false when the window leaves the mirrored box (or, without WRAP, the donor
+// interior).
+template <int P, bool WRAP>
+__device__ __forceinline__ bool gather_mirror(const InterpSeg& S, const double sidx[3], const int E[2], double& v0,
+                                              double& v1) {
+  int2 wx[P], wy[P], wz[P];
+  int st[3];
+  fixed_weights<P>(sidx, wx, wy, wz, st);
+  if (st[0] < 0 || st[1] < 0 || st[0] + P > S.gd.n[0] || st[1] + P > S.gd.n[1]) return false;
+  if (!WRAP && (st[2] < 0 || st[2] + P > S.gd.n[2])) return false;
+  const Box& b = S.mbox;
+  const int mx = b.hi[0] - b.lo[0] + 1, my = b.hi[1] - b.lo[1] + 1, mz = b.hi[2] - b.lo[2] + 1;
+  if (st[0] < b.lo[0] || st[0] + P - 1 > b.hi[0] || st[1] < b.lo[1] || st[1] + P - 1 > b.hi[1]) return false;
+  if (!WRAP && (st[2] < b.lo[2] || st[2] + P - 1 > b.hi[2])) return false;
+  const long long mvol = (long long)mx * my * mz;
+  const int2* M = S.mir + (long long)(st[1] - b.lo[1]) * mx + (st[0] - b.lo[0]);
+  long long out[2];
+  contract_point_fixed<P>(wx, wy, wz, [&](int f, int a, int bb, int c) {
+    const int kz = WRAP ? wrap_index(st[2] + c, S.gd.n[2]) : st[2] + c;
+    return M[f * mvol + (long long)(kz - b.lo[2]) * mx * my + bb * mx + a];
+  }, out);
+  v0 = (double)out[0] * __longlong_as_double((long long)(E[0] - 58) << 52);
+  v1 = (double)out[1] * __longlong_as_double((long long)(E[1] - 58) << 52);
+  return true;
+}
+
 // Local-to-Global from a spherical shell: the global cell centre goes to the
 // shell's Cartesian frame (M, shift), then to (r, theta, phi); the azimuthal
 // window wraps.  Fixed point, or direct FP64 sums (native FP64, non-finite
@@ -502,7 +529,7 @@ __device__ __forceinline__ void l2g_point_sph(const FillArgs& A, const InterpSeg
     const double sidx[3] = {(q[0] - S.gd.lo[0]) / S.gd.h[0] - 0.5, (q[1] - S.gd.lo[1]) / S.gd.h[1] - 0.5,
                             (q[2] - S.gd.lo[2]) / S.gd.h[2] - 0.5};
     const int E[2] = {max(dslot[0], 64), max(dslot[1], 64)};
-    ok = gather_fixed<P, true>(S, sidx, E, v0, v1);
+    ok = (S.mir && gather_mirror<P, true>(S, sidx, E, v0, v1)) || gather_fixed<P, true>(S, sidx, E, v0, v1);
   } else {
     ok = interp_point_shell<P>(reinterpret_cast<const ST*>(S.D), S.gd, q[0], q[1], q[2], v0, v1);
   }
@@ -557,7 +584,7 @@ __device__ __noinline__ void sph_ghost_block(const FillArgs& A, const InterpSeg&
 #pragma unroll
         for (int a = 0; a < 3; ++a) sidx[a] = (xb[a] - S.gd.lo[a]) / S.gd.h[a] - 0.5;
         const int E[2] = {max(dslot[0], 64), max(dslot[1], 64)};
-        ok = gather_fixed<P, false>(S, sidx, E, v0, v1);
+        ok = (S.mir && gather_mirror<P, false>(S, sidx, E, v0, v1)) || gather_fixed<P, false>(S, sidx, E, v0, v1);
       } else {
         ok = interp_point<P>(reinterpret_cast<const ST*>(S.D), S.gd, xb[0], xb[1], xb[2], v0, v1);
       }
@@ -931,6 +958,32 @@ __device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
     T[a] = min(S.td[sl][a], S.sb[sl][a] + S.se[sl][a] - org[a]);
   }
   interp_tile<P, ST>(A, S, org, T, 2 - sl / 2, fill_smem);  // slabs come in z, y, x pairs: the wall axis is thin
+}
+
+// Fixed-point mirrors of the donor regions of a fill (binary64 buffers): one
+// thread per cell of each region, both fields.
+__global__ void __launch_bounds__(256) k_mirror(const __grid_constant__ MirrorArgs A) {
+  const long long b = blockIdx.x;
+  int q = 0;
+  while (q + 1 < A.nr && b >= A.r[q + 1].block0) ++q;
+  const MirrorRegion& R = A.r[q];
+  const int mx = R.box.hi[0] - R.box.lo[0] + 1, my = R.box.hi[1] - R.box.lo[1] + 1,
+            mz = R.box.hi[2] - R.box.lo[2] + 1;
+  const long long mvol = (long long)mx * my * mz;
+  const long long idx = (b - R.block0) * 256 + threadIdx.x;
+  if (idx >= mvol) return;
+  const int x = (int)(idx % mx), y = (int)((idx / mx) % my), z = (int)(idx / ((long long)mx * my));
+  const long long c = R.g.at(R.box.lo[0] + x, R.box.lo[1] + y, R.box.lo[2] + z);
+  const int* slot = A.expo + R.patch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+#pragma unroll
+  for (int f = 0; f < 2; ++f) {
+    const int E = max(slot[f], 64);  // a non-finite scale sends the fill to its FP64 path
+    R.dst[f * mvol + idx] = split31(to_fixed(R.src[c + f * R.g.vol], E) * 64);
+  }
+}
+
+void launch_mirror(const MirrorArgs& a, void* stream) {
+  if (a.nr > 0 && a.blocks > 0) k_mirror<<<(unsigned)a.blocks, 256, 0, (cudaStream_t)stream>>>(a);
 }
 
 template <int P, typename ST>

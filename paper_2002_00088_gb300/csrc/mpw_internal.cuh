@@ -119,6 +119,8 @@ struct InterpSeg {
   int list_blocks;     // SEG_LIST: CTAs striding over the list
   int sph;             // SEG_MASKED / SEG_LIST: the donor is a spherical shell (M, shift map
                        // the target to the donor's Cartesian frame)
+  const int2* mir;     // fixed-point mirror of the donor over mbox (donor indices, both fields,
+  Box mbox;            // x fastest), or null: the per-point sums gather and convert the donors
   Box box;             // SEG_MASKED: target cells to test (global indices)
   const uint8_t* flags;
   int want;            // flag byte of the cells to fill (state | owner << 2)
@@ -164,6 +166,29 @@ struct FillArgs {
   int fixed;           // 1: separable contractions in int64 fixed point, 0: native FP64
   int f32;             // field buffers hold binary32 (FP32 arithmetic; fixed is ignored)
 };
+
+// ---------------------------------------------------------------- fixed-point mirrors
+// Before a ghost fill whose per-point sums read many donors (spherical
+// shells), the donor cells they can reach are converted once to the split
+// fixed-point form of the fill (a = 64 q on the scale of the donor's live
+// exponent slot for the buffer being filled).
+struct MirrorRegion {
+  const double* src;   // donor buffer (psi; Pi at +vol)
+  Geom g;
+  Box box;             // donor indices, inclusive
+  int2* dst;           // 2 x volume(box) entries, field-major, x fastest
+  int patch;           // donor patch id (exponent slots)
+  long long block0;
+};
+constexpr int MAX_MIRRORS = 2 * MAX_PATCHES;  // per shell: its global donor box and its own box
+struct MirrorArgs {
+  MirrorRegion r[MAX_MIRRORS];
+  int nr;
+  long long blocks;
+  const int* expo;
+  int y_buf;
+};
+void launch_mirror(const MirrorArgs& a, void* stream);
 
 // ---------------------------------------------------------------- shell RHS
 // Fused RHS + RK4 stage on spherical shells (plain FP64, one thread per point).
