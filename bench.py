@@ -157,8 +157,8 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-RHS_SOURCES = ("mpw_rhs.cu", "mpw_fixed.cuh", "mpw_internal.cuh", "mpw_tma.cuh")
-RHS32_SOURCES = ("mpw_rhs32.cu", "mpw_internal.cuh", "mpw_tma.cuh")
+RHS_SOURCES = ("mpw_rhs.cu", "mpw_fixed.cuh", "mpw_rhs_args.cuh", "mpw_tma.cuh")
+RHS32_SOURCES = ("mpw_rhs32.cu", "mpw_rhs_args.cuh", "mpw_tma.cuh")
 
 
 def kernel_source_hash(f32=False):
