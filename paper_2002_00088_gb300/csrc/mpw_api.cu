@@ -1008,7 +1008,7 @@ int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
     R.out_buf = out_buf[l];
     R.tiles_x = (P.d.n[0] + RHS_TX - 1) / RHS_TX;
     R.tiles_y = (P.d.n[1] + RHS_TY - 1) / RHS_TY;
-    R.zc = zc > 0 ? zc : (P.d.n[2] >= 128 ? 32 : 8);
+    R.zc = zc > 0 ? zc : default_rhs_chunk(P.d.n[2], c->cfg.precision == 32);
     R.zchunks = (P.d.n[2] + R.zc - 1) / R.zc;
     R.block0 = blocks;
     if (P.sph()) continue;  // spherical shells: k_rhs_shell
