@@ -15,7 +15,8 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIB_PATH = os.path.join(PKG, "libmpw.so")
-SOURCES = ["mpw_api.cu", "mpw_kernels.cu", "mpw_rhs.cu", "mpw_rhs32.cu", "mpw_shell.cu", "mpw_fill.cu", "mpw_noalloc.cu"]
+SOURCES = ["mpw_api.cu", "mpw_kernels.cu", "mpw_rhs.cu", "mpw_rhs32.cu", "mpw_shell.cu", "mpw_fill.cu", "mpw_noalloc.cu",
+           "mpw_conv.cu", "mpw_surrogate.cu"]
 GENCODE = "arch=compute_103a,code=sm_103a"
 
 
@@ -29,7 +30,8 @@ def nvcc_path() -> str:
 def _inputs():
     files = [os.path.join(CSRC, s) for s in SOURCES]
     files += [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    files.append(os.path.join(ROOT, "include", "mpw.h"))
+    inc = os.path.join(ROOT, "include")
+    files += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     return files
 
 

@@ -1,0 +1,483 @@
+// mpw_conv.cu -- tensor-core layers of the learned surrogate (the C ABI of
+// include/mpw_surrogate.h): periodic 3x3x3 convolution, its input and weight
+// gradients, Adam and the squared-error gradient.
+//
+// Implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32 accumulation).
+// Forward and input gradient: M = points (a warp owns 16 consecutive x
+// points), N = output channels, K = 27 taps x input channels; a CTA stages
+// the periodic halo of a 16 x 8 x 1 point block and the layer's weights in
+// shared memory and loops over blocks.  Weight gradient: M = output channels,
+// N = input channels, K = points; each CTA keeps its partial sums in
+// registers over its blocks and a second kernel adds the partials in a fixed
+// order (deterministic).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+
+#include "../../include/mpw_surrogate.h"
+#include "mpw_internal.cuh"
+
+namespace mpw {
+namespace {
+
+constexpr int BX = 16, BY = 8;                   // output block: BY warp rows of BX x-points
+constexpr int HX = BX + 2, HY = BY + 2, HZ = 3;  // its periodic halo
+constexpr int HPTS = HX * HY * HZ;
+constexpr int FWD_THREADS = 32 * BY;
+constexpr int WG_WARPS = 16;
+constexpr int WG_THREADS = 32 * WG_WARPS;
+
+// BF16 elements per halo point in shared memory: 32 channels padded to 40 make
+// the eight rows of an A fragment fall in distinct banks (20-word stride).
+template <int C>
+__host__ __device__ constexpr int xstride() { return C == 32 ? 40 : C; }
+// K = 27 taps x CIN rounded up to the MMA depth, and the padded weight row
+template <int CIN>
+__host__ __device__ constexpr int kdim() { return (27 * CIN + 15) / 16 * 16; }
+template <int CIN>
+__host__ __device__ constexpr int wstride() { return kdim<CIN>() + 8; }
+
+struct Vol {
+  int n0, n1, n2, batch;
+};
+
+__device__ __forceinline__ int wrap1(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+__device__ __forceinline__ uint32_t pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
+// D = A B + D, A 16x16 row-major, B 16x8 column-major, BF16 in, FP32 out
+__device__ __forceinline__ void mma_bf16(float c[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// block index -> sample b, plane z, first row y0, first column x0
+__device__ __forceinline__ void block_origin(long long blk, const Vol& v, int& b, int& z, int& y0, int& x0) {
+  const int bx = v.n0 / BX, by = v.n1 / BY;
+  x0 = (int)(blk % bx) * BX;
+  blk /= bx;
+  y0 = (int)(blk % by) * BY;
+  blk /= by;
+  z = (int)(blk % v.n2);
+  b = (int)(blk / v.n2);
+}
+
+__device__ __forceinline__ long long point_index(const Vol& v, int b, int z, int y, int x) {
+  return (((long long)b * v.n2 + z) * v.n1 + y) * v.n0 + x;
+}
+
+// the HX x HY x 3 periodic halo of a block, C channels, 16-byte copies
+template <int C>
+__device__ void stage_halo(__nv_bfloat16* Xs, const __nv_bfloat16* x, const Vol& v, int b, int z, int y0, int x0) {
+  constexpr int CH = C / 8;
+  for (int i = threadIdx.x; i < HPTS * CH; i += blockDim.x) {
+    const int hp = i / CH, ch = i - hp * CH;
+    const int hx = hp % HX, hy = (hp / HX) % HY, hz = hp / (HX * HY);
+    const long long p = point_index(v, b, wrap1(z + hz - 1, v.n2), wrap1(y0 + hy - 1, v.n1), wrap1(x0 + hx - 1, v.n0));
+    *reinterpret_cast<int4*>(Xs + hp * xstride<C>() + ch * 8) = *reinterpret_cast<const int4*>(x + p * C + ch * 8);
+  }
+}
+
+struct FwdArgs {
+  const __nv_bfloat16* x;
+  const __nv_bfloat16* w;
+  const float* bias;
+  const __nv_bfloat16* mask;
+  __nv_bfloat16* y;
+  float* y32;
+  Vol v;
+  long long nblocks;
+  int relu;
+  int flip;  // 1: w is the layer W[CIN][27][COUT] and this launch is its input gradient
+};
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(FWD_THREADS) k_conv3(const FwdArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int XS = xstride<CIN>(), KP = kdim<CIN>(), WS = wstride<CIN>(), NT = COUT / 8;
+  __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Xs = Ws + COUT * WS;
+  // B operand, once per CTA: Ws[n][k], k = tap * CIN + c.  The input
+  // gradient correlates with the mirrored taps of the transposed weights.
+  for (int i = threadIdx.x; i < COUT * KP; i += blockDim.x) {
+    const int n = i / KP, k = i - n * KP;
+    __nv_bfloat16 val = __float2bfloat16(0.0f);
+    if (k < 27 * CIN) {
+      const int tap = k / CIN, c = k - tap * CIN;
+      val = A.flip ? A.w[((long long)c * 27 + 26 - tap) * COUT + n] : A.w[((long long)n * 27 + tap) * CIN + c];
+    }
+    Ws[n * WS + k] = val;
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const uint32_t* X32 = reinterpret_cast<const uint32_t*>(Xs);
+  const uint32_t* W32 = reinterpret_cast<const uint32_t*>(Ws);
+  for (long long blk = blockIdx.x; blk < A.nblocks; blk += gridDim.x) {
+    int b, z, y0, x0;
+    block_origin(blk, A.v, b, z, y0, x0);
+    __syncthreads();  // the previous block's fragments are read (and Ws is staged)
+    stage_halo<CIN>(Xs, A.x, A.v, b, z, y0, x0);
+    __syncthreads();
+    float acc[NT][4];
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
+#pragma unroll 2
+    for (int s = 0; s < KP / 16; ++s) {
+      // A fragment: rows g and g + 8 (x points), columns 16 s + 2 t (+ 8)
+      uint32_t a[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 16 * s + 2 * t + 8 * h;
+        if (k < 27 * CIN) {
+          const int tap = k / CIN, c = k - tap * CIN;
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const int hp = (dz * HY + warp + dy) * HX + g + dx;
+          a[2 * h] = X32[(hp * XS + c) >> 1];
+          a[2 * h + 1] = X32[((hp + 8) * XS + c) >> 1];
+        } else {
+          a[2 * h] = a[2 * h + 1] = 0u;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int row = (8 * j + g) * WS + 16 * s + 2 * t;
+        mma_bf16(acc[j], a[0], a[1], a[2], a[3], W32[row >> 1], W32[(row + 8) >> 1]);
+      }
+    }
+    // epilogue: rows g, g + 8; channels 8 j + 2 t, + 1
+    const int y = y0 + warp;
+#pragma unroll
+    for (int j = 0; j < NT; ++j) {
+      const int co = 8 * j + 2 * t;
+      const float bias0 = A.bias ? A.bias[co] : 0.0f, bias1 = A.bias ? A.bias[co + 1] : 0.0f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const long long p = point_index(A.v, b, z, y, x0 + g + 8 * h);
+        float v0 = acc[j][2 * h] + bias0, v1 = acc[j][2 * h + 1] + bias1;
+        if (A.relu) {
+          v0 = fmaxf(v0, 0.0f);
+          v1 = fmaxf(v1, 0.0f);
+        }
+        if (A.mask) {
+          const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(A.mask + p * COUT + co);
+          if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
+          if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
+        }
+        if (A.y32) *reinterpret_cast<float2*>(A.y32 + p * COUT + co) = make_float2(v0, v1);
+        if (A.y) *reinterpret_cast<__nv_bfloat162*>(A.y + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+  }
+}
+
+struct WgArgs {
+  const __nv_bfloat16* x;  // layer input [..][CIN]
+  const __nv_bfloat16* g;  // gradient at the layer output [..][COUT]
+  float* part;             // [gridDim.x][COUT * 27 * CIN + COUT]
+  Vol v;
+  long long nblocks;
+};
+
+// Weight and bias gradient partials of one CTA.  Jobs (tap, 16 output
+// channels) are spread over the warps; a job keeps CIN / 8 accumulator tiles.
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_THREADS) k_conv3_wgrad(const WgArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int XS = xstride<CIN>(), GS = COUT + 8;
+  constexpr int MT = (COUT + 15) / 16, NT = CIN / 8, JOBS = 27 * MT, JPW = (JOBS + WG_WARPS - 1) / WG_WARPS;
+  __nv_bfloat16* Xs = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Gs = Xs + HPTS * XS;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, gq = lane >> 2, t = lane & 3;
+  float acc[JPW][NT][4];
+#pragma unroll
+  for (int i = 0; i < JPW; ++i)
+#pragma unroll
+    for (int j = 0; j < NT; ++j) acc[i][j][0] = acc[i][j][1] = acc[i][j][2] = acc[i][j][3] = 0.0f;
+  float bsum = 0.0f;
+  for (long long blk = blockIdx.x; blk < A.nblocks; blk += gridDim.x) {
+    int b, z, y0, x0;
+    block_origin(blk, A.v, b, z, y0, x0);
+    __syncthreads();
+    stage_halo<CIN>(Xs, A.x, A.v, b, z, y0, x0);
+    constexpr int GCH = COUT / 8;
+    for (int i = threadIdx.x; i < BX * BY * GCH; i += blockDim.x) {
+      const int q = i / GCH, ch = i - q * GCH, r = q / BX, m = q - r * BX;
+      const long long p = point_index(A.v, b, z, y0 + r, x0 + m);
+      *reinterpret_cast<int4*>(Gs + q * GS + ch * 8) = *reinterpret_cast<const int4*>(A.g + p * COUT + ch * 8);
+    }
+    __syncthreads();
+    if (threadIdx.x < COUT)
+      for (int q = 0; q < BX * BY; ++q) bsum += __bfloat162float(Gs[q * GS + threadIdx.x]);
+#pragma unroll
+    for (int i = 0; i < JPW; ++i) {
+      const int job = warp + WG_WARPS * i;
+      if (job >= JOBS) break;  // warp-uniform
+      const int tap = job / MT, mt = job - tap * MT;
+      const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+      const int co = 16 * mt + gq;
+      for (int s = 0; s < BY; ++s) {
+        // A[m = channel][k = point of row s]: rows co, co + 8; points 2t, 2t+1 (+8)
+        uint32_t a[4];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int q = s * BX + 2 * t + 8 * h;
+          a[2 * h] = pack2(Gs[q * GS + co], Gs[(q + 1) * GS + co]);
+          a[2 * h + 1] = co + 8 < COUT ? pack2(Gs[q * GS + co + 8], Gs[(q + 1) * GS + co + 8]) : 0u;
+        }
+        // B[k = point][n = input channel 8 nt + gq], the point shifted by the tap
+        const int hp = (dz * HY + s + dy) * HX + 2 * t + dx;
+#pragma unroll
+        for (int nt = 0; nt < NT; ++nt) {
+          const int ci = 8 * nt + gq;
+          const uint32_t b0 = pack2(Xs[hp * XS + ci], Xs[(hp + 1) * XS + ci]);
+          const uint32_t b1 = pack2(Xs[(hp + 8) * XS + ci], Xs[(hp + 9) * XS + ci]);
+          mma_bf16(acc[i][nt], a[0], a[1], a[2], a[3], b0, b1);
+        }
+      }
+    }
+  }
+  float* P = A.part + (long long)blockIdx.x * (COUT * 27 * CIN + COUT);
+#pragma unroll
+  for (int i = 0; i < JPW; ++i) {
+    const int job = warp + WG_WARPS * i;
+    if (job >= JOBS) break;
+    const int tap = job / MT, mt = job - tap * MT, co = 16 * mt + gq;
+#pragma unroll
+    for (int nt = 0; nt < NT; ++nt) {
+      const int ci = 8 * nt + 2 * t;
+      P[((long long)co * 27 + tap) * CIN + ci] = acc[i][nt][0];
+      P[((long long)co * 27 + tap) * CIN + ci + 1] = acc[i][nt][1];
+      if (co + 8 < COUT) {
+        P[((long long)(co + 8) * 27 + tap) * CIN + ci] = acc[i][nt][2];
+        P[((long long)(co + 8) * 27 + tap) * CIN + ci + 1] = acc[i][nt][3];
+      }
+    }
+  }
+  if (threadIdx.x < COUT) P[COUT * 27 * CIN + threadIdx.x] = bsum;
+}
+
+// out[i] = sum over the partials in index order (gw for i < nw, then gb)
+__global__ void k_sum_parts(const float* part, int nparts, int len, int nw, float* gw, float* gb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= len) return;
+  float s = 0.0f;
+  for (int c = 0; c < nparts; ++c) s += part[(long long)c * len + i];
+  if (i < nw)
+    gw[i] = s;
+  else
+    gb[i - nw] = s;
+}
+
+__global__ void k_adam(float* w, __nv_bfloat16* w16, const float* g, float* m, float* v, long long n, float lr_c1,
+                       float c2, float b1, float b2, float eps) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.0f - b1) * gi;
+    const float vi = b2 * v[i] + (1.0f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float wi = w[i] - lr_c1 * mi / (sqrtf(vi * c2) + eps);
+    w[i] = wi;
+    if (w16) w16[i] = __float2bfloat16_rn(wi);
+  }
+}
+
+__global__ void k_mse(const float* y, int cy, const float* t, int used, long long points, __nv_bfloat16* gy,
+                      double* loss, float gscale, double inv) {
+  double local = 0.0;
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < points;
+       p += (long long)gridDim.x * blockDim.x) {
+    for (int c = 0; c < cy; ++c) {
+      const float d = c < used ? y[p * cy + c] - t[p * used + c] : 0.0f;
+      gy[p * cy + c] = __float2bfloat16_rn(gscale * d);
+      local += (double)d * d;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) local += __shfl_xor_sync(0xffffffffu, local, o);
+  if (loss && (threadIdx.x & 31) == 0) atomicAdd(loss, local * inv);
+}
+
+}  // namespace
+}  // namespace mpw
+
+// ============================================================================ host side
+
+namespace {
+using namespace mpw;
+
+mpw_status fail(mpw_status st, const char* msg) {
+  set_last_error(msg);
+  return st;
+}
+
+mpw_status cuda_fail(cudaError_t e) {
+  static thread_local char buf[160];
+  std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));
+  set_last_error(buf);
+  return MPW_ERR_CUDA;
+}
+
+int sm_count() {
+  int d = 0, n = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, d) != cudaSuccess)
+    return 1;
+  return n > 0 ? n : 1;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// shapes the kernels are instantiated for: (8, 32), (32, 32), (32, 8)
+bool supported(int cin, int cout) {
+  return (cin == 8 || cin == 32) && (cout == 8 || cout == 32) && !(cin == 8 && cout == 8);
+}
+
+mpw_status check_volume(int batch, const int n[3], Vol& v, long long& nblocks) {
+  if (!n || batch < 1 || n[0] < 16 || n[1] < 8 || n[2] < 3 || n[0] % BX || n[1] % BY)
+    return fail(MPW_ERR_ARG, "conv3: volume must have n0 % 16 == 0, n1 % 8 == 0, n2 >= 3 and batch >= 1");
+  v = Vol{n[0], n[1], n[2], batch};
+  nblocks = (long long)batch * n[2] * (n[1] / BY) * (n[0] / BX);
+  return MPW_OK;
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_conv(const FwdArgs& a, cudaStream_t s) {
+  const int smem = (COUT * wstride<CIN>() + HPTS * xstride<CIN>()) * 2;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const long long grid = a.nblocks < 2LL * sm_count() ? a.nblocks : 2LL * sm_count();
+  k_conv3<CIN, COUT><<<(unsigned)grid, FWD_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch_conv(int cin, int cout, const FwdArgs& a, cudaStream_t s) {
+  if (cin == 8) return launch_conv<8, 32>(a, s);
+  if (cout == 8) return launch_conv<32, 8>(a, s);
+  return launch_conv<32, 32>(a, s);
+}
+
+long long wgrad_grid(long long nblocks) { return nblocks < 2LL * sm_count() ? nblocks : 2LL * sm_count(); }
+
+template <int CIN, int COUT>
+cudaError_t launch_wgrad(const WgArgs& a, long long grid, cudaStream_t s) {
+  const int smem = (HPTS * xstride<CIN>() + BX * BY * (COUT + 8)) * 2;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_wgrad<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  k_conv3_wgrad<CIN, COUT><<<(unsigned)grid, WG_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+extern "C" {
+
+mpw_status mpw_conv3_forward(const uint16_t* x, int cin, const uint16_t* w, const float* bias, int cout, int batch,
+                             const int n[3], int relu, const uint16_t* mask, uint16_t* y, float* y32, void* stream) {
+  if (!supported(cin, cout)) return fail(MPW_ERR_ARG, "conv3: (cin, cout) must be (8, 32), (32, 32) or (32, 8)");
+  if (!x || !w || (!y && !y32)) return fail(MPW_ERR_ARG, "conv3: null input, weights or output");
+  if (!aligned16(x) || !aligned16(y) || !aligned16(y32) || !aligned16(mask))
+    return fail(MPW_ERR_ARG, "conv3: tensors must be 16-byte aligned");
+  FwdArgs a{};
+  if (mpw_status st = check_volume(batch, n, a.v, a.nblocks)) return st;
+  a.x = reinterpret_cast<const __nv_bfloat16*>(x);
+  a.w = reinterpret_cast<const __nv_bfloat16*>(w);
+  a.bias = bias;
+  a.mask = reinterpret_cast<const __nv_bfloat16*>(mask);
+  a.y = reinterpret_cast<__nv_bfloat16*>(y);
+  a.y32 = y32;
+  a.relu = relu ? 1 : 0;
+  a.flip = 0;
+  if (cudaError_t e = dispatch_conv(cin, cout, a, (cudaStream_t)stream)) return cuda_fail(e);
+  return MPW_OK;
+}
+
+mpw_status mpw_conv3_backward_data(const uint16_t* gy, int cout, const uint16_t* w, int cin, int batch,
+                                   const int n[3], const uint16_t* mask, uint16_t* gx, float* gx32, void* stream) {
+  if (!supported(cin, cout)) return fail(MPW_ERR_ARG, "conv3: (cin, cout) must be (8, 32), (32, 32) or (32, 8)");
+  if (!gy || !w || (!gx && !gx32)) return fail(MPW_ERR_ARG, "conv3: null gradient, weights or output");
+  if (!aligned16(gy) || !aligned16(gx) || !aligned16(gx32) || !aligned16(mask))
+    return fail(MPW_ERR_ARG, "conv3: tensors must be 16-byte aligned");
+  FwdArgs a{};
+  if (mpw_status st = check_volume(batch, n, a.v, a.nblocks)) return st;
+  a.x = reinterpret_cast<const __nv_bfloat16*>(gy);
+  a.w = reinterpret_cast<const __nv_bfloat16*>(w);
+  a.mask = reinterpret_cast<const __nv_bfloat16*>(mask);
+  a.y = reinterpret_cast<__nv_bfloat16*>(gx);
+  a.y32 = gx32;
+  a.flip = 1;
+  // the transposed layer: its input channels are the layer's outputs
+  if (cudaError_t e = dispatch_conv(cout, cin, a, (cudaStream_t)stream)) return cuda_fail(e);
+  return MPW_OK;
+}
+
+size_t mpw_conv3_wgrad_scratch_bytes(int cin, int cout) {
+  if (!supported(cin, cout)) return 0;
+  return (size_t)2 * sm_count() * (size_t)(cout * 27 * cin + cout) * sizeof(float);
+}
+
+mpw_status mpw_conv3_backward_weights(const uint16_t* x, int cin, const uint16_t* gy, int cout, int batch,
+                                      const int n[3], float* gw, float* gb, void* scratch, size_t scratch_bytes,
+                                      void* stream) {
+  if (!supported(cin, cout)) return fail(MPW_ERR_ARG, "conv3: (cin, cout) must be (8, 32), (32, 32) or (32, 8)");
+  if (!x || !gy || !gw || !gb || !scratch) return fail(MPW_ERR_ARG, "conv3: null tensor or scratch");
+  if (!aligned16(x) || !aligned16(gy)) return fail(MPW_ERR_ARG, "conv3: tensors must be 16-byte aligned");
+  WgArgs a{};
+  if (mpw_status st = check_volume(batch, n, a.v, a.nblocks)) return st;
+  const long long grid = wgrad_grid(a.nblocks);
+  const int len = cout * 27 * cin + cout;
+  if (scratch_bytes < (size_t)grid * len * sizeof(float)) return fail(MPW_ERR_ARG, "conv3: scratch too small");
+  a.x = reinterpret_cast<const __nv_bfloat16*>(x);
+  a.g = reinterpret_cast<const __nv_bfloat16*>(gy);
+  a.part = static_cast<float*>(scratch);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (cin == 8)
+    e = launch_wgrad<8, 32>(a, grid, s);
+  else if (cout == 8)
+    e = launch_wgrad<32, 8>(a, grid, s);
+  else
+    e = launch_wgrad<32, 32>(a, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e);
+  k_sum_parts<<<(len + 255) / 256, 256, 0, s>>>(a.part, (int)grid, len, cout * 27 * cin, gw, gb);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e);
+  return MPW_OK;
+}
+
+mpw_status mpw_adam_step(float* w, uint16_t* w16, const float* g, float* m, float* v, long long count, float lr,
+                         float b1, float b2, float eps, int t, void* stream) {
+  if (!w || !g || !m || !v || count < 0 || t < 1) return fail(MPW_ERR_ARG, "adam: null tensor, count < 0 or t < 1");
+  if (count == 0) return MPW_OK;
+  const double lr_c1 = (double)lr / (1.0 - std::pow((double)b1, t));
+  const double c2 = 1.0 / (1.0 - std::pow((double)b2, t));
+  long long blocks = (count + 255) / 256;
+  if (blocks > 8LL * sm_count()) blocks = 8LL * sm_count();
+  k_adam<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(w, reinterpret_cast<__nv_bfloat16*>(w16), g, m, v, count,
+                                                             (float)lr_c1, (float)c2, b1, b2, eps);
+  if (cudaError_t e = cudaGetLastError()) return cuda_fail(e);
+  return MPW_OK;
+}
+
+mpw_status mpw_mse_grad(const float* y, int cy, const float* t, int used, long long points, uint16_t* gy,
+                        double* loss, void* stream) {
+  if (!y || !t || !gy || cy < 1 || used < 1 || used > cy || points < 1)
+    return fail(MPW_ERR_ARG, "mse: null tensor or bad channel counts");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (loss)
+    if (cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(double), s)) return cuda_fail(e);
+  long long blocks = (points + 255) / 256;
+  if (blocks > 8LL * sm_count()) blocks = 8LL * sm_count();
+  const double inv = 1.0 / ((double)points * used);
+  k_mse<<<(unsigned)blocks, 256, 0, s>>>(y, cy, t, used, points, reinterpret_cast<__nv_bfloat16*>(gy), loss,
+                                         (float)(2.0 * inv), inv);
+  if (cudaError_t e = cudaGetLastError()) return cuda_fail(e);
+  return MPW_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,481 @@
+// mpw_surrogate.cu -- the learned surrogate of include/mpw_surrogate.h: the
+// four-layer network's trainer (forward, squared-error loss, backward, Adam)
+// and inference, and the kernels that turn FP64 wave fields into the
+// network's features, its training targets and, from its output, the state
+// four RK4 steps later.
+//
+// The FP64 arithmetic of the feature, target and update kernels uses
+// explicitly rounded operations (no contraction into fused multiply-adds), in
+// the order the header states, so that every value is defined to the bit.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "../../include/mpw_surrogate.h"
+#include "mpw_internal.cuh"
+
+namespace {
+
+using mpw::set_last_error;
+
+// layer table: padded channel counts, activation, parameter offsets
+struct Layer {
+  int cin, cout, relu;
+  long long w, b;
+};
+constexpr int NLAYER = 4;
+constexpr int CIN[NLAYER] = {8, 32, 32, 32};
+constexpr int COUT[NLAYER] = {32, 32, 32, 8};
+
+long long layer_table(Layer L[NLAYER]) {
+  long long off = 0;
+  for (int l = 0; l < NLAYER; ++l) {
+    L[l].cin = CIN[l];
+    L[l].cout = COUT[l];
+    L[l].relu = l < NLAYER - 1;
+    L[l].w = off;
+    off += (long long)COUT[l] * 27 * CIN[l];
+    L[l].b = off;
+    off += COUT[l];
+  }
+  return off;
+}
+
+mpw_status fail(mpw_status st, const char* msg) {
+  set_last_error(msg);
+  return st;
+}
+
+mpw_status cuda_fail(cudaError_t e) {
+  static thread_local char buf[160];
+  std::snprintf(buf, sizeof(buf), "CUDA error: %s", cudaGetErrorString(e));
+  set_last_error(buf);
+  return MPW_ERR_CUDA;
+}
+
+#define SUR_TRY(x)                                    \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) return cuda_fail(e_);      \
+  } while (0)
+
+#define MPW_TRY(x)                                    \
+  do {                                                \
+    mpw_status s_ = (x);                              \
+    if (s_ != MPW_OK) return s_;                      \
+  } while (0)
+
+struct Dims {
+  int n0, n1, n2, batch;
+  __host__ __device__ long long points() const { return (long long)n0 * n1 * n2; }
+};
+
+// ---------------------------------------------------------------- kernels
+
+__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
+
+// 12 h^2 L u along one axis: (16 (u[-1] + u[1]) - (u[-2] + u[2])) - 30 u
+__device__ __forceinline__ double axis_sum(double um2, double um1, double u0, double up1, double up2) {
+  return __dsub_rn(__dsub_rn(__dmul_rn(16.0, __dadd_rn(um1, up1)), __dadd_rn(um2, up2)), __dmul_rn(30.0, u0));
+}
+
+// L u at (i, j, k) of sample volume u (periodic): ((Sx + Sy) + Sz) / (12 h^2)
+__device__ double lap4(const double* u, const Dims& d, int i, int j, int k, double inv12h2) {
+  const long long row = ((long long)k * d.n1 + j) * d.n0;
+  const double c = u[row + i];
+  const double sx = axis_sum(u[row + wrapi(i - 2, d.n0)], u[row + wrapi(i - 1, d.n0)], c, u[row + wrapi(i + 1, d.n0)],
+                             u[row + wrapi(i + 2, d.n0)]);
+  auto Y = [&](int jj) { return u[((long long)k * d.n1 + wrapi(jj, d.n1)) * d.n0 + i]; };
+  auto Z = [&](int kk) { return u[((long long)wrapi(kk, d.n2) * d.n1 + j) * d.n0 + i]; };
+  const double sy = axis_sum(Y(j - 2), Y(j - 1), c, Y(j + 1), Y(j + 2));
+  const double sz = axis_sum(Z(k - 2), Z(k - 1), c, Z(k + 1), Z(k + 2));
+  return __dmul_rn(__dadd_rn(__dadd_rn(sx, sy), sz), inv12h2);
+}
+
+__global__ void k_absmax(const double* psi, const double* pi, Dims d, double delta, unsigned* maxbits) {
+  const long long P = d.points(), N = P * d.batch;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += (long long)gridDim.x * blockDim.x) {
+    const long long i = base + threadIdx.x;
+    unsigned m = 0;
+    if (i < N) m = __float_as_uint(__double2float_rn(fmax(fabs(psi[i]), __dmul_rn(delta, fabs(pi[i])))));
+    // a warp's 32 indices lie in one sample (P is a multiple of 128)
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && base + (threadIdx.x & ~31) < N) atomicMax(&maxbits[(base + threadIdx.x) / P], m);
+  }
+}
+
+__global__ void k_scale(const unsigned* maxbits, int batch, float* scale) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const float m = __uint_as_float(maxbits[b]);
+  scale[b] = m > 0.0f ? __double2float_rn(__ddiv_rn(1.0, (double)m)) : 1.0f;
+}
+
+struct Coef {
+  double delta, d2, d3, hd2, inv12h2, sigma;  // Delta, Delta^2, Delta^3, Delta^2/2, 1/(12 h^2), sigma
+};
+
+__device__ __forceinline__ void point_ijk(long long q, const Dims& d, int& i, int& j, int& k) {
+  i = (int)(q % d.n0);
+  j = (int)((q / d.n0) % d.n1);
+  k = (int)(q / ((long long)d.n0 * d.n1));
+}
+
+__global__ void k_features(const double* psi, const double* pi, Dims d, Coef c, const float* scale, uint4* x) {
+  const long long P = d.points();
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P * d.batch;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(g / P);
+    int i, j, k;
+    point_ijk(g - (long long)b * P, d, i, j, k);
+    const double* ps = psi + (long long)b * P;
+    const double* pp = pi + (long long)b * P;
+    const double s = (double)scale[b];
+    const double f0 = __dmul_rn(s, ps[g - (long long)b * P]);
+    const double f1 = __dmul_rn(__dmul_rn(s, c.delta), pp[g - (long long)b * P]);
+    const double f2 = __dmul_rn(__dmul_rn(s, c.d2), lap4(ps, d, i, j, k, c.inv12h2));
+    const double f3 = __dmul_rn(__dmul_rn(s, c.d3), lap4(pp, d, i, j, k, c.inv12h2));
+    __nv_bfloat162 a = __floats2bfloat162_rn(__double2float_rn(f0), __double2float_rn(f1));
+    __nv_bfloat162 bb = __floats2bfloat162_rn(__double2float_rn(f2), __double2float_rn(f3));
+    x[g] = make_uint4(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&bb), 0u, 0u);
+  }
+}
+
+__global__ void k_targets(const double* psi0, const double* pi0, const double* psi1, const double* pi1, Dims d,
+                          Coef c, const float* scale, float2* t) {
+  const long long P = d.points();
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P * d.batch;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(g / P);
+    int i, j, k;
+    point_ijk(g - (long long)b * P, d, i, j, k);
+    const double lp = lap4(psi0 + (long long)b * P, d, i, j, k, c.inv12h2);
+    const double lq = lap4(pi0 + (long long)b * P, d, i, j, k, c.inv12h2);
+    const double r0 = __dsub_rn(__dsub_rn(__dsub_rn(psi1[g], psi0[g]), __dmul_rn(c.delta, pi0[g])), __dmul_rn(c.hd2, lp));
+    const double r1 = __dsub_rn(__dsub_rn(__dsub_rn(pi1[g], pi0[g]), __dmul_rn(c.delta, lp)), __dmul_rn(c.hd2, lq));
+    const double cs = __ddiv_rn((double)scale[b], c.sigma);
+    t[g] = make_float2(__double2float_rn(__dmul_rn(cs, r0)), __double2float_rn(__dmul_rn(__dmul_rn(cs, c.delta), r1)));
+  }
+}
+
+// (psi1, Pi1) from (psi0, Pi0) and the network output y ([..][8], channels 0, 1)
+__global__ void k_apply(const double* psi0, const double* pi0, Dims d, Coef c, const float* scale, const float* y,
+                        double* psi1, double* pi1) {
+  const long long P = d.points();
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P * d.batch;
+       g += (long long)gridDim.x * blockDim.x) {
+    const int b = (int)(g / P);
+    int i, j, k;
+    point_ijk(g - (long long)b * P, d, i, j, k);
+    const double lp = lap4(psi0 + (long long)b * P, d, i, j, k, c.inv12h2);
+    const double lq = lap4(pi0 + (long long)b * P, d, i, j, k, c.inv12h2);
+    const double a = __ddiv_rn(c.sigma, (double)scale[b]);
+    const double n0 = (double)y[g * 8], n1 = (double)y[g * 8 + 1];
+    psi1[g] = __dadd_rn(__dadd_rn(__dadd_rn(psi0[g], __dmul_rn(c.delta, pi0[g])), __dmul_rn(c.hd2, lp)), __dmul_rn(a, n0));
+    pi1[g] = __dadd_rn(__dadd_rn(__dadd_rn(pi0[g], __dmul_rn(c.delta, lp)), __dmul_rn(c.hd2, lq)),
+                       __dmul_rn(__ddiv_rn(a, c.delta), n1));
+  }
+}
+
+}  // namespace
+
+namespace {
+
+__global__ void k_to_bf16(const float* w, __nv_bfloat16* w16, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    w16[i] = __float2bfloat16_rn(w[i]);
+}
+
+unsigned grid_for(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+}  // namespace
+
+struct mpw_sur {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  double dt = 0.0, h = 0.0, sigma = 1.0;
+  Coef coef{};
+  Layer L[NLAYER];
+  long long nparam = 0;
+  float* w = nullptr;  // master parameters, their gradient, Adam moments
+  float* g = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  __nv_bfloat16* w16 = nullptr;  // BF16 copy the layers read
+  int t = 0;                     // Adam steps taken
+  long long cap = 0;             // points the activation buffers hold
+  __nv_bfloat16* act[NLAYER - 1] = {};
+  __nv_bfloat16* grad[2] = {};
+  __nv_bfloat16* gy = nullptr;
+  float* y = nullptr;
+  void* scratch = nullptr;
+  size_t scratch_bytes = 0;
+  double* loss = nullptr;
+  // inference workspace
+  long long xcap = 0;
+  uint16_t* x = nullptr;
+  int bcap = 0;
+  float* scale = nullptr;
+  unsigned* maxbits = nullptr;
+};
+
+namespace {
+
+mpw_status use(mpw_sur* s) {
+  if (!s) return fail(MPW_ERR_ARG, "null surrogate handle");
+  SUR_TRY(cudaSetDevice(s->device));
+  return MPW_OK;
+}
+
+mpw_status dims_of(int batch, const int n[3], Dims& d) {
+  if (!n || batch < 1 || n[0] < 16 || n[1] < 8 || n[2] < 5 || n[0] % 16 || n[1] % 8)
+    return fail(MPW_ERR_ARG, "surrogate: volume must have n0 % 16 == 0, n1 % 8 == 0, n2 >= 5, batch >= 1");
+  d = Dims{n[0], n[1], n[2], batch};
+  return MPW_OK;
+}
+
+void free_buffers(mpw_sur* s) {
+  for (auto*& p : s->act) cudaFree(p), p = nullptr;
+  for (auto*& p : s->grad) cudaFree(p), p = nullptr;
+  cudaFree(s->gy);
+  cudaFree(s->y);
+  s->gy = nullptr;
+  s->y = nullptr;
+  s->cap = 0;
+}
+
+mpw_status ensure_train(mpw_sur* s, long long P) {
+  if (P <= s->cap) return MPW_OK;
+  free_buffers(s);
+  for (auto*& p : s->act) SUR_TRY(cudaMalloc(&p, (size_t)P * 32 * 2));
+  for (auto*& p : s->grad) SUR_TRY(cudaMalloc(&p, (size_t)P * 32 * 2));
+  SUR_TRY(cudaMalloc(&s->gy, (size_t)P * 8 * 2));
+  SUR_TRY(cudaMalloc(&s->y, (size_t)P * 8 * 4));
+  s->cap = P;
+  return MPW_OK;
+}
+
+mpw_status ensure_infer(mpw_sur* s, long long P, int batch) {
+  if (P > s->xcap) {
+    cudaFree(s->x);
+    s->x = nullptr;
+    s->xcap = 0;
+    SUR_TRY(cudaMalloc(&s->x, (size_t)P * 8 * 2));
+    s->xcap = P;
+  }
+  if (batch > s->bcap) {
+    cudaFree(s->scale);
+    cudaFree(s->maxbits);
+    s->scale = nullptr;
+    s->maxbits = nullptr;
+    s->bcap = 0;
+    SUR_TRY(cudaMalloc(&s->scale, (size_t)batch * 4));
+    SUR_TRY(cudaMalloc(&s->maxbits, (size_t)batch * 4));
+    s->bcap = batch;
+  }
+  return MPW_OK;
+}
+
+const uint16_t* W16(const mpw_sur* s, int l) { return reinterpret_cast<const uint16_t*>(s->w16 + s->L[l].w); }
+
+// layers 1-3 into s->act, layer 4 into y (FP32)
+mpw_status forward_chain(mpw_sur* s, const uint16_t* x, const Dims& d, float* y) {
+  const int n[3] = {d.n0, d.n1, d.n2};
+  const uint16_t* in = x;
+  for (int l = 0; l < NLAYER - 1; ++l) {
+    uint16_t* out = reinterpret_cast<uint16_t*>(s->act[l]);
+    MPW_TRY(mpw_conv3_forward(in, s->L[l].cin, W16(s, l), s->w + s->L[l].b, s->L[l].cout, d.batch, n, 1, nullptr,
+                              out, nullptr, s->stream));
+    in = out;
+  }
+  const Layer& L = s->L[NLAYER - 1];
+  return mpw_conv3_forward(in, L.cin, W16(s, NLAYER - 1), s->w + L.b, L.cout, d.batch, n, 0, nullptr, nullptr, y,
+                           s->stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+long long mpw_sur_param_count(void) {
+  Layer L[NLAYER];
+  return layer_table(L);
+}
+
+mpw_status mpw_sur_create(int device, void* stream, double dt, double h, double sigma, mpw_sur** out) {
+  if (!out) return fail(MPW_ERR_ARG, "null output handle");
+  *out = nullptr;
+  if (!(dt > 0.0) || !(h > 0.0) || !(sigma > 0.0)) return fail(MPW_ERR_ARG, "surrogate: dt, h and sigma must be > 0");
+  mpw_sur* s = new mpw_sur;
+  s->device = device;
+  s->stream = (cudaStream_t)stream;
+  s->dt = dt;
+  s->h = h;
+  s->sigma = sigma;
+  const double D = 4.0 * dt;
+  s->coef = Coef{D, D * D, D * D * D, D * D / 2.0, 1.0 / (12.0 * h * h), sigma};
+  s->nparam = layer_table(s->L);
+  auto bail = [&](cudaError_t e) {
+    mpw_sur_destroy(s);
+    return cuda_fail(e);
+  };
+  cudaError_t e;
+  if ((e = cudaSetDevice(device))) return bail(e);
+  const size_t pb = (size_t)s->nparam * 4;
+  for (float** p : {&s->w, &s->g, &s->m, &s->v}) {
+    if ((e = cudaMalloc(p, pb))) return bail(e);
+    if ((e = cudaMemsetAsync(*p, 0, pb, s->stream))) return bail(e);
+  }
+  if ((e = cudaMalloc(&s->w16, (size_t)s->nparam * 2))) return bail(e);
+  if ((e = cudaMemsetAsync(s->w16, 0, (size_t)s->nparam * 2, s->stream))) return bail(e);
+  for (int l = 0; l < NLAYER; ++l) {
+    const size_t b = mpw_conv3_wgrad_scratch_bytes(s->L[l].cin, s->L[l].cout);
+    if (b > s->scratch_bytes) s->scratch_bytes = b;
+  }
+  if ((e = cudaMalloc(&s->scratch, s->scratch_bytes))) return bail(e);
+  if ((e = cudaMalloc(&s->loss, sizeof(double)))) return bail(e);
+  if ((e = cudaStreamSynchronize(s->stream))) return bail(e);
+  *out = s;
+  return MPW_OK;
+}
+
+void mpw_sur_destroy(mpw_sur* s) {
+  if (!s) return;
+  cudaSetDevice(s->device);
+  cudaStreamSynchronize(s->stream);
+  free_buffers(s);
+  for (void* p : {(void*)s->w, (void*)s->g, (void*)s->m, (void*)s->v, (void*)s->w16, s->scratch, (void*)s->loss,
+                  (void*)s->x, (void*)s->scale, (void*)s->maxbits})
+    cudaFree(p);
+  delete s;
+}
+
+mpw_status mpw_sur_set_params(mpw_sur* s, const float* params, long long count) {
+  MPW_TRY(use(s));
+  if (!params || count != s->nparam) return fail(MPW_ERR_ARG, "surrogate: params must hold mpw_sur_param_count() values");
+  const size_t pb = (size_t)count * 4;
+  SUR_TRY(cudaMemcpyAsync(s->w, params, pb, cudaMemcpyHostToDevice, s->stream));
+  SUR_TRY(cudaMemsetAsync(s->m, 0, pb, s->stream));
+  SUR_TRY(cudaMemsetAsync(s->v, 0, pb, s->stream));
+  SUR_TRY(cudaMemsetAsync(s->g, 0, pb, s->stream));
+  k_to_bf16<<<grid_for(count), 256, 0, s->stream>>>(s->w, s->w16, count);
+  SUR_TRY(cudaGetLastError());
+  SUR_TRY(cudaStreamSynchronize(s->stream));
+  s->t = 0;
+  return MPW_OK;
+}
+
+static mpw_status copy_out(mpw_sur* s, const float* src, float* dst, long long count) {
+  MPW_TRY(use(s));
+  if (!dst || count != s->nparam) return fail(MPW_ERR_ARG, "surrogate: buffer must hold mpw_sur_param_count() values");
+  SUR_TRY(cudaMemcpyAsync(dst, src, (size_t)count * 4, cudaMemcpyDeviceToHost, s->stream));
+  SUR_TRY(cudaStreamSynchronize(s->stream));
+  return MPW_OK;
+}
+
+mpw_status mpw_sur_get_params(mpw_sur* s, float* params, long long count) {
+  return s ? copy_out(s, s->w, params, count) : fail(MPW_ERR_ARG, "null surrogate handle");
+}
+
+mpw_status mpw_sur_get_grads(mpw_sur* s, float* grads, long long count) {
+  return s ? copy_out(s, s->g, grads, count) : fail(MPW_ERR_ARG, "null surrogate handle");
+}
+
+mpw_status mpw_sur_features(mpw_sur* s, const double* psi0, const double* pi0, int batch, const int n[3],
+                            uint16_t* x, float* scale) {
+  MPW_TRY(use(s));
+  Dims d;
+  MPW_TRY(dims_of(batch, n, d));
+  if (!psi0 || !pi0 || !x || !scale) return fail(MPW_ERR_ARG, "surrogate: null tensor");
+  MPW_TRY(ensure_infer(s, 0, batch));
+  SUR_TRY(cudaMemsetAsync(s->maxbits, 0, (size_t)batch * 4, s->stream));
+  const long long N = d.points() * batch;
+  k_absmax<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef.delta, s->maxbits);
+  k_scale<<<(batch + 127) / 128, 128, 0, s->stream>>>(s->maxbits, batch, scale);
+  k_features<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, scale, reinterpret_cast<uint4*>(x));
+  SUR_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+mpw_status mpw_sur_targets(mpw_sur* s, const double* psi0, const double* pi0, const double* psi1, const double* pi1,
+                           int batch, const int n[3], const float* scale, float* t) {
+  MPW_TRY(use(s));
+  Dims d;
+  MPW_TRY(dims_of(batch, n, d));
+  if (!psi0 || !pi0 || !psi1 || !pi1 || !scale || !t) return fail(MPW_ERR_ARG, "surrogate: null tensor");
+  k_targets<<<grid_for(d.points() * batch), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, scale,
+                                                                  reinterpret_cast<float2*>(t));
+  SUR_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+mpw_status mpw_sur_forward(mpw_sur* s, const uint16_t* x, int batch, const int n[3], float* y) {
+  MPW_TRY(use(s));
+  Dims d;
+  MPW_TRY(dims_of(batch, n, d));
+  if (!x || !y) return fail(MPW_ERR_ARG, "surrogate: null tensor");
+  MPW_TRY(ensure_train(s, d.points() * batch));
+  return forward_chain(s, x, d, y);
+}
+
+mpw_status mpw_sur_train_step(mpw_sur* s, const uint16_t* x, const float* t, int batch, const int n[3], float lr,
+                              double* loss) {
+  MPW_TRY(use(s));
+  Dims d;
+  MPW_TRY(dims_of(batch, n, d));
+  if (!x || !t || !(lr > 0.0f)) return fail(MPW_ERR_ARG, "surrogate: null tensor or lr <= 0");
+  const long long P = d.points() * batch;
+  MPW_TRY(ensure_train(s, P));
+  MPW_TRY(forward_chain(s, x, d, s->y));
+  uint16_t* gy = reinterpret_cast<uint16_t*>(s->gy);
+  MPW_TRY(mpw_mse_grad(s->y, 8, t, 2, P, gy, s->loss, s->stream));
+  // backward, layer 4 down to layer 1; gradients at activations are masked by
+  // the ReLU of the layer that produced them
+  const uint16_t* gout = gy;
+  for (int l = NLAYER - 1; l >= 0; --l) {
+    const Layer& L = s->L[l];
+    const uint16_t* in = l == 0 ? x : reinterpret_cast<const uint16_t*>(s->act[l - 1]);
+    MPW_TRY(mpw_conv3_backward_weights(in, L.cin, gout, L.cout, batch, n, s->g + L.w, s->g + L.b, s->scratch,
+                                       s->scratch_bytes, s->stream));
+    if (l == 0) break;
+    uint16_t* gin = reinterpret_cast<uint16_t*>(s->grad[l & 1]);
+    MPW_TRY(mpw_conv3_backward_data(gout, L.cout, W16(s, l), L.cin, batch, n, in, gin, nullptr, s->stream));
+    gout = gin;
+  }
+  double host_loss = 0.0;
+  if (loss) SUR_TRY(cudaMemcpyAsync(&host_loss, s->loss, sizeof(double), cudaMemcpyDeviceToHost, s->stream));
+  s->t += 1;
+  MPW_TRY(mpw_adam_step(s->w, reinterpret_cast<uint16_t*>(s->w16), s->g, s->m, s->v, s->nparam, lr, 0.9f, 0.999f,
+                        1e-8f, s->t, s->stream));
+  if (loss) {
+    SUR_TRY(cudaStreamSynchronize(s->stream));
+    *loss = host_loss;
+  }
+  return MPW_OK;
+}
+
+mpw_status mpw_sur_predict(mpw_sur* s, const double* psi0, const double* pi0, int batch, const int n[3], double* psi1,
+                           double* pi1) {
+  MPW_TRY(use(s));
+  Dims d;
+  MPW_TRY(dims_of(batch, n, d));
+  if (!psi0 || !pi0 || !psi1 || !pi1) return fail(MPW_ERR_ARG, "surrogate: null tensor");
+  if (psi1 == psi0 || psi1 == pi0 || pi1 == psi0 || pi1 == pi0) return fail(MPW_ERR_ARG, "surrogate: outputs alias inputs");
+  const long long P = d.points() * batch;
+  MPW_TRY(ensure_infer(s, P, batch));
+  MPW_TRY(ensure_train(s, P));
+  MPW_TRY(mpw_sur_features(s, psi0, pi0, batch, n, s->x, s->scale));
+  MPW_TRY(forward_chain(s, s->x, d, s->y));
+  k_apply<<<grid_for(P), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, s->scale, s->y, psi1, pi1);
+  SUR_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+}  // extern "C"

@@ -1,4 +1,4 @@
-"""Thin ctypes binding of libmpw (include/mpw.h).
+"""Thin ctypes binding of libmpw (include/mpw.h, include/mpw_surrogate.h).
 
 Argument marshalling only: every step of the method runs in the CUDA kernels
 of libmpw.so.  PyTorch supplies device memory (through the allocator hook
@@ -75,6 +75,28 @@ SIGNATURES = {
                                    C.POINTER(C.c_longlong)]),
     "mpw_batch_destroy": (None, [_vp]),
     "mpw_last_error": (C.c_char_p, []),
+    # include/mpw_surrogate.h
+    "mpw_conv3_forward": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, _vp, _vp,
+                                    _vp, _vp]),
+    "mpw_conv3_backward_data": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), _vp, _vp, _vp,
+                                          _vp]),
+    "mpw_conv3_wgrad_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "mpw_conv3_backward_weights": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), _vp, _vp, _vp,
+                                             C.c_size_t, _vp]),
+    "mpw_adam_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_longlong, C.c_float, C.c_float, C.c_float, C.c_float,
+                                C.c_int, _vp]),
+    "mpw_mse_grad": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_longlong, _vp, _vp, _vp]),
+    "mpw_sur_param_count": (C.c_longlong, []),
+    "mpw_sur_create": (C.c_int, [C.c_int, _vp, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_void_p)]),
+    "mpw_sur_destroy": (None, [_vp]),
+    "mpw_sur_set_params": (C.c_int, [_vp, _vp, C.c_longlong]),
+    "mpw_sur_get_params": (C.c_int, [_vp, _vp, C.c_longlong]),
+    "mpw_sur_get_grads": (C.c_int, [_vp, _vp, C.c_longlong]),
+    "mpw_sur_features": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), _vp, _vp]),
+    "mpw_sur_targets": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), _vp, _vp]),
+    "mpw_sur_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), C.c_float, _dp]),
+    "mpw_sur_forward": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_int), _vp]),
+    "mpw_sur_predict": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), _vp, _vp]),
     "mpw_destroy": (None, [_vp]),
 }
 

@@ -306,3 +306,55 @@ def random_fields(shape, seed_index, scale=1.0):
 
 def random_offsets(count, seed_index, low, high):
     return rng(200 + seed_index).uniform(low, high, (count, 3))
+
+
+# ---------------------------------------------------------------- learned surrogate inputs
+
+def surrogate_pulses(seed_index, count=8, spread=0.5):
+    """GAUSS_SUM parameters of one training or test state: `count` Gaussians,
+    amplitudes N(0,1), widths U[0.05,0.2], centres U[-spread,spread]^3 (on the
+    periodic box [-1,1]^3 the widest pulse is below 2e-3 at the faces)."""
+    r = rng(seed_index)
+    amps = r.normal(0.0, 1.0, count)
+    widths = r.uniform(0.05, 0.2, count)
+    centres = r.uniform(-spread, spread, (count, 3))
+    return np.column_stack([amps, widths, centres]).ravel()
+
+
+# (cin, cout, relu) of the four layers and their stored channel counts
+SURROGATE_LAYERS = [(4, 32, True), (32, 32, True), (32, 32, True), (32, 2, False)]
+SURROGATE_PADDED = [(8, 32), (32, 32), (32, 32), (32, 8)]
+
+
+def surrogate_init(seed_index):
+    """Initial parameters in the flat padded binary32 layout of
+    include/mpw_surrogate.h: He-scaled normal weights for the ReLU layers, a
+    last layer at 0.1 of that scale, zero biases and zero padding."""
+    r = rng(seed_index)
+    parts = []
+    for (ci, co, relu), (pci, pco) in zip(SURROGATE_LAYERS, SURROGATE_PADDED):
+        std = np.sqrt(2.0 / (27 * ci)) if relu else 0.1 / np.sqrt(27 * ci)
+        W = np.zeros((pco, 27, pci))
+        W[:co, :, :ci] = r.standard_normal((co, 27, ci)) * std
+        parts += [W.ravel(), np.zeros(pco)]
+    return np.concatenate(parts).astype(np.float32)
+
+
+def surrogate_layout(scale=1, steps=400, seed_index=7, interp_points=6):
+    """The learned-surrogate configuration: a periodic global 128^3/scale on
+    [-1,1]^3 (advanced four steps per network call) and two local 64^3/scale
+    patches at 2x resolution (half-width 0.25) on circular orbits of radius
+    0.4, angular speed 2 pi, in the planes z = +0.3 and z = -0.3 (phases
+    seeded), which stay on the plain method; eight Gaussians as in
+    ``surrogate_pulses``; CFL 0.25 on the local spacing; 400 steps."""
+    r = rng(seed_index)
+    phases = r.uniform(0.0, 2.0 * np.pi, 2)
+    ng, nl = 128 // scale, 64 // scale
+    patches = [PatchSpec(GLOBAL, (ng, ng, ng), (-1.0, -1.0, -1.0), (1.0, 1.0, 1.0), BC_PERIODIC)]
+    for z, ph in zip((0.3, -0.3), phases):
+        patches.append(PatchSpec(LOCAL, (nl, nl, nl), (-0.25,) * 3, (0.25,) * 3, BC_INTERPATCH, CIRCULAR,
+                                 (0.0, 0.0, z, 0.4, 2.0 * np.pi, ph)))
+    params = surrogate_pulses(seed_index + 1)
+    h_min = 0.5 / nl
+    return Workload(f"surrogate_{ng}+2x{nl}", patches, GAUSS_SUM, params, 8, interp_points, 0.005, 0.25 * h_min,
+                    steps)

@@ -1,5 +1,5 @@
 """The C-ABI library builds, loads and exports every entry point that
-include/mpw.h declares (no GPU needed: nothing here launches a kernel)."""
+include/*.h declares (no GPU needed: nothing here launches a kernel)."""
 import ctypes
 import os
 import re
@@ -10,7 +10,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "mpw.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^[A-Za-z_][\w \*]*?\b(mpw_\w+)\s*\(", src, flags=re.M)
     return sorted(set(names))
@@ -36,3 +37,18 @@ def test_binding_refuses_to_run_without_the_library(mpw_lib, tmp_path, monkeypat
     monkeypatch.setattr(mpw_lib, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         mpw_lib._load()
+
+
+def test_conv_entry_points_validate_shapes_before_any_launch(mpw_lib):
+    """Unsupported channel counts and volumes are refused on the host."""
+    n_bad = (ctypes.c_int * 3)(24, 8, 4)   # n0 not a multiple of 16
+    n_ok = (ctypes.c_int * 3)(16, 8, 4)
+    fake = ctypes.c_void_p(256)            # never dereferenced: validation comes first
+    L = mpw_lib.lib
+    assert L.mpw_conv3_forward(fake, 32, fake, None, 32, 1, n_bad, 0, None, fake, None, None) == 1
+    assert L.mpw_conv3_forward(fake, 8, fake, None, 8, 1, n_ok, 0, None, fake, None, None) == 1
+    assert L.mpw_conv3_forward(fake, 16, fake, None, 32, 1, n_ok, 0, None, fake, None, None) == 1
+    assert L.mpw_conv3_backward_data(fake, 32, fake, 32, 0, n_ok, None, fake, None, None) == 1
+    assert L.mpw_conv3_wgrad_scratch_bytes(16, 32) == 0
+    assert L.mpw_adam_step(fake, None, fake, fake, fake, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
+    assert L.mpw_mse_grad(fake, 8, fake, 9, 10, fake, None, None) == 1
