@@ -20,6 +20,12 @@ plane wave k = (2,3,5) pi plus a Gaussian pulse).  Its line adds "accuracy":
 the binary32 error against the closed form after the run, and the FP64 path's
 time and error on the same workload and steps.
 
+--surrogate runs the learned-surrogate configuration instead
+(workloads.surrogate_layout: periodic global 128^3, two orbiting local 64^3
+patches at 2x): the network is trained on 2,000 trajectories of the method,
+then 400 steps of the hybrid (one network call advances the global four steps,
+the local patches stay on the method) are timed against the plain method.
+
 With --gpus N > 1 (under torch.distributed.run) every rank advances an
 independent replica on its own GPU ("replicas only": the method needs no
 exchange between instances); value is the sum over ranks.  --impl reference
@@ -71,6 +77,11 @@ def parse():
     ap.add_argument("--motion", default="orbiting", choices=["orbiting", "spinning"],
                     help="orbiting: translating local patches on circular orbits (default); spinning: the "
                          "rotating-patch workload")
+    ap.add_argument("--surrogate", action="store_true",
+                    help="the learned surrogate: train it on the method's trajectories, then time the hybrid "
+                         "(surrogate global, local patches on the method) against the plain method")
+    ap.add_argument("--trajectories", type=int, default=2000, help="--surrogate: training trajectories")
+    ap.add_argument("--tol", type=float, default=1e-4, help="--surrogate: residual tolerance of a call")
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="64: the FP64 workload (default); 32: the binary32 precision workload, with its error "
                          "against the closed form and the FP64 path on the same workload")
@@ -512,12 +523,172 @@ def run_batch(args):
     return 0
 
 
+SUR_SIGMA = 1e-4
+
+
+def surrogate_cpu_baseline(w, params, threads):
+    """The oracle's surrogate call (features, network, update; numpy FP64 with
+    the device's bfloat16 roundings) on a bounded sample volume."""
+    import numpy as np
+    from oracle import surrogate as so
+    n = (32, 16, 16)
+    h = 2.0 / w.patches[0].n[0]
+    r = np.random.default_rng(7)
+    psi = r.standard_normal((1, n[2], n[1], n[0]))
+    pi = r.standard_normal((1, n[2], n[1], n[0])) * 20
+    t0 = time.perf_counter()
+    x, s = so.features(psi, pi, w.dt, h)
+    _, y = so.net_forward(x, params)
+    so.apply(psi, pi, s, y, w.dt, h, SUR_SIGMA)
+    el = time.perf_counter() - t0
+    pts = n[0] * n[1] * n[2]
+    return {"value": pts * 16 / el, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"one surrogate call (4 steps x 4 substages) on a periodic {n[0]}x{n[1]}x{n[2]} volume, "
+                      f"{el:.2f} s, numpy FP64 with bfloat16 roundings"}
+
+
+def run_surrogate(args):
+    """Learned surrogate: train on the method's trajectories (periodic global
+    128^3), then the hybrid (one call advances the global four steps, two
+    moving local 64^3 patches on the method) against the plain method on the
+    same layout, and the plain global-only run the surrogate learned from."""
+    import numpy as np
+    import torch
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    from paper_2002_00088_gb300.build import build_library
+    build_library()
+    from paper_2002_00088_gb300 import mpw
+    from paper_2002_00088_gb300 import surrogate as S
+    from paper_2002_00088_gb300 import workloads as wl
+    stream = torch.cuda.current_stream(local)
+    steps = max(4, args.steps // 4 * 4)
+    calls = steps // 4
+    w = wl.surrogate_layout(scale=args.scale, steps=steps)
+    n = w.patches[0].n[0]
+    h = 2.0 / n
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    # training, every step on the device (trajectories, features, targets, forward, backward, Adam)
+    src = S.Trajectories(n, w.dt, device=local)
+    sur = S.Surrogate(w.dt, h, SUR_SIGMA, device=local, stream=stream, params=wl.surrogate_init(1))
+    t0 = time.perf_counter()
+    losses = S.train(sur, src, trajectories=args.trajectories, batch=2, lr=2e-3, lr_end=1e-4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    # what the network gains: one call against the method's four steps on held-out trajectories
+    off = S.Surrogate(w.dt, h, SUR_SIGMA, device=local, stream=stream, params=np.zeros(sur.count, np.float32))
+    gain = {"trained": 0.0, "network_off": 0.0}
+    for k in range(8):
+        u0 = [torch.empty((n, n, n), dtype=torch.float64, device="cuda") for _ in range(2)]
+        u1 = [torch.empty((n, n, n), dtype=torch.float64, device="cuda") for _ in range(2)]
+        src.pair(80000 + k, u0, u1)
+        sc = max(float(u1[0].abs().max()), 4 * w.dt * float(u1[1].abs().max()))
+        for name, s_ in (("trained", sur), ("network_off", off)):
+            p1, q1 = s_.predict(u0[0], u0[1])
+            e = max(float((p1 - u1[0]).abs().max()), 4 * w.dt * float((q1 - u1[1]).abs().max())) / sc
+            gain[name] = max(gain[name], e)
+
+    def make(npatch):
+        g = mpw.Multipatch(w.interp_points, w.ko_eps, device=local, stream=stream)
+        for p in w.patches[:npatch]:
+            g.create_patch(p.kind, p.n, p.lo, p.hi, p.outer_bc, p.motion, p.motion_params, p.topology)
+        g.set_analytic(w.analytic_kind, w.analytic_params, w.analytic_count)
+        g.fill_analytic(0.0)
+        return g
+
+    # warm-up on a throwaway copy, then the timed hybrid run
+    warm = make(3)
+    S.step_hybrid(warm, sur, w.dt, max(args.warmup, 1), args.tol)
+    del warm
+    hyb = make(3)
+    live = hyb.live_points()
+    sampler = ClockSampler(local)
+    sampler.start()
+    a, b = ev(), ev()
+    torch.cuda.synchronize()
+    a.record(stream)
+    accepted, max_res = S.step_hybrid(hyb, sur, w.dt, calls, args.tol)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_h = a.elapsed_time(b)
+    clocks = sampler.stop()
+    plain = make(3)
+    plain.step(w.dt, args.warmup)
+    plain = make(3)
+    torch.cuda.synchronize()
+    a.record(stream)
+    plain.step(w.dt, steps)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms_p = a.elapsed_time(b)
+    solo = make(1)
+    solo.step(w.dt, steps)
+
+    def errors(x, y, patches):
+        out = []
+        for f in range(2):
+            got = [x.get_fields(q)[f] for q in patches]
+            want = [y.get_fields(q)[f] for q in patches]
+            scale = max(np.nanmax(np.abs(v)) for v in want)
+            out.append(float(max(np.nanmax(np.abs(g - v)) for g, v in zip(got, want)) / scale))
+        return {"psi": out[0], "pi": out[1]}
+
+    err_mp = errors(hyb, plain, range(3))
+    err_solo = errors(hyb, solo, [0])
+    # the network's forward throughput (tensor-core bound), CUDA events
+    x = torch.zeros((1, n, n, n, 8), dtype=torch.bfloat16, device="cuda")
+    for _ in range(3):
+        sur.forward(x)
+    torch.cuda.synchronize()
+    a.record(stream)
+    for _ in range(10):
+        sur.forward(x)
+    b.record(stream)
+    torch.cuda.synchronize()
+    fwd_ms = a.elapsed_time(b) / 10
+    flops = n ** 3 * 2 * 27 * (7 * 32 + 32 * 32 * 2 + 32 * 2)
+    peak = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peak = float(json.load(f)["bf16_tflops"])
+        peak_src = "measured bf16 TFLOP/s (burst)"
+    except Exception:
+        peak, peak_src = 1900.0, "fallback bf16 TFLOP/s"
+    achieved = flops / (fwd_ms * 1e-3) / 1e12
+    line = {
+        "metric": METRIC, "value": live * 4 * steps / (ms_h * 1e-3), "unit": UNIT, "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms_h / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+bf16", "data": "synthetic (seeded Gaussian pulses; trained on the method's "
+                                                           "own trajectories)",
+        "config": {"workload": w.name, "live_points": live, "calls": calls, "tol": args.tol, "sigma": SUR_SIGMA,
+                   "trajectories": args.trajectories, "parallelism": "single",
+                   "l2": "state larger than L2 (global 128^3 x 8 dense FP64 arrays per call); no flush"},
+        "plain": {"value": live * 4 * steps / (ms_p * 1e-3), "ms_per_step": ms_p / steps},
+        "speedup_vs_plain": ms_p / ms_h,
+        "accepted_calls": accepted, "max_residual": max_res,
+        "error_vs_plain_multipatch": err_mp, "error_vs_plain_global_only": err_solo,
+        "one_call_error": gain, "training": {"seconds": train_s, "first_loss": float(np.mean(losses[:20])),
+                                             "last_loss": float(np.mean(losses[-20:]))},
+        "roofline": {"bound": "tensor", "kernel": "k_conv3 (network forward, mma.sync BF16/FP32)",
+                     "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "avg_launch_ms": fwd_ms / 4},
+        "gpu_launches": calls * (6 + 4 + 2 + 16 * 3 + 8),
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = surrogate_cpu_baseline(w, wl.surrogate_init(1), os.cpu_count() or 1)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.surrogate:
+        return run_surrogate(args)
     return run_ours(args)
 
 

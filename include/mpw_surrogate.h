@@ -7,7 +7,7 @@
  * 4th-order centred Laplacian of its stencil, Sec. 2.2), defined here.
  *
  * Network (fixed shape): four 3x3x3 convolutions on a periodic box,
- * channels-last, 4 -> 32 -> 32 -> 32 -> 2, ReLU after layers 1-3, no
+ * channels-last, 7 -> 32 -> 32 -> 32 -> 2, ReLU after layers 1-3, no
  * activation after layer 4.  Tensor-core arithmetic: BF16 operands, FP32
  * accumulation, FP32 bias added after the contraction.
  *
@@ -21,7 +21,7 @@
  *    periodic in x, y and z.  n0 must be a multiple of 16 and n1 of 8;
  *    every n >= 3.
  *  - BF16 tensors are passed as uint16_t (IEEE bfloat16 bit patterns).
- *    Channel counts are 8 or 32: the 4 input features and the 2 outputs are
+ *    Channel counts are 8 or 32: the 7 input features and the 2 outputs are
  *    stored in 8-channel tensors whose extra channels are zero.
  *  - Weights of one layer: W[co][tap][ci], tap = (dz*3 + dy)*3 + dx with
  *    offsets dz-1, dy-1, dx-1 in {-1, 0, 1}:
@@ -89,23 +89,27 @@ mpw_status mpw_mse_grad(const float* y, int cy, const float* t, int used, long l
  * steps of the method) and L the method's 4th-order centred Laplacian
  * (Sec. 2.2: 12 h^2 L u = sum over axes of -u[-2] + 16 u[-1] - 30 u + 16 u[1]
  * - u[2], periodic), the state advances as
- *     psi1 = psi0 + Delta Pi0 + Delta^2/2 L psi0 + (sigma / s) N_0
- *     Pi1  = Pi0 + Delta L psi0 + Delta^2/2 L Pi0 + (sigma / (s Delta)) N_1
- * i.e. a second-order Taylor step of the wave equation plus a learned
- * remainder N = net(x) (channels 0, 1 of the last layer).  Per sample the
- * scale s = 1 / max_p max(|psi0|, Delta |Pi0|) (binary32: the maximum is
- * rounded to binary32, then s = 1/max rounded to binary32; 1 if the state
- * is 0).  Input features (BF16 of the binary32 rounding of the FP64 value):
+ *     psi1 = psi0 + D Pi0 + D^2/2 L psi0 + D^3/6 L Pi0 + D^4/24 L^2 psi0 + (sigma / s) N_0
+ *     Pi1  = Pi0 + D L psi0 + D^2/2 L Pi0 + D^3/6 L^2 psi0 + D^4/24 L^2 Pi0 + (sigma / (s D)) N_1
+ * (D = Delta): the fourth-order Taylor step of d psi/dt = Pi, d Pi/dt = L psi
+ * (for this linear system, one RK4 step of size Delta; stable while Delta
+ * times the largest frequency stays below 2.8) plus a learned remainder
+ * N = net(x) (channels 0, 1 of the last layer).  Every sum is taken left to
+ * right, each operation rounded once.  Per sample the scale
+ * s = 1 / max_p max(|psi0|, Delta |Pi0|) (binary32: the maximum is rounded to
+ * binary32, then s = 1/max rounded to binary32; 1 if the state is 0).  Input
+ * features (BF16 of the binary32 rounding of the FP64 value):
  *     x = (s psi0, s Delta Pi0, s Delta^2 L psi0, s Delta^3 L Pi0, 0, 0, 0, 0)
- * Training targets (binary32): the remainder of the method's own four steps,
- *     t_0 = (s / sigma) (psi1 - psi0 - Delta Pi0 - Delta^2/2 L psi0)
- *     t_1 = (s / sigma) Delta (Pi1 - Pi0 - Delta L psi0 - Delta^2/2 L Pi0).
+ * Training targets (binary32): the remainder of the method's own four steps
+ * over the Taylor step,
+ *     t_0 = (s / sigma) (psi1 - psi0 - D Pi0 - D^2/2 L psi0 - D^3/6 L Pi0 - D^4/24 L^2 psi0)
+ *     t_1 = (s / sigma) D (Pi1 - Pi0 - D L psi0 - D^2/2 L Pi0 - D^3/6 L^2 psi0 - D^4/24 L^2 Pi0).
  * The loss is the mean squared error of (N_0, N_1) against t. */
 typedef struct mpw_sur mpw_sur;
 
 /* Parameters, binary32, in this order for layers l = 1..4 (channel counts
  * padded as above: cin 8,32,32,32; cout 32,32,32,8): W_l[cout][27][cin], then
- * b_l[cout].  The padded entries (W_1 for ci >= 4, W_4 and b_4 for co >= 2)
+ * b_l[cout].  The padded entries (W_1 for ci >= 7, W_4 and b_4 for co >= 2)
  * must be zero; their gradients are zero, so training keeps them zero. */
 long long mpw_sur_param_count(void);
 
@@ -140,6 +144,42 @@ mpw_status mpw_sur_forward(mpw_sur* s, const uint16_t* x, int batch, const int n
  * (outputs may not alias inputs). */
 mpw_status mpw_sur_predict(mpw_sur* s, const double* psi0, const double* pi0, int batch, const int n[3],
                            double* psi1, double* pi1);
+
+/* Residual check of a call (psi0, Pi0) -> (psi1, Pi1) against the method's
+ * RHS: with the two-point quadrature with end corrections,
+ *   R_psi = psi1 - psi0 - Delta/2 (Pi0 + Pi1) + Delta^2/12 (L psi1 - L psi0)
+ *   R_Pi  = Pi1 - Pi0 - Delta/2 (L psi0 + L psi1) + Delta^2/12 (L Pi1 - L Pi0)
+ * which the exact evolution meets to O(Delta^5).  out ([batch][2] binary32,
+ * device) receives max_p max(|R_psi|, Delta |R_Pi|) (rounded up) and
+ * max_p max(|psi0|, Delta |Pi0|) per sample; lap (optional, device,
+ * 4 * batch * points doubles) receives L psi0, L Pi0, L psi1, L Pi1. */
+mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, const double* psi1, const double* pi1,
+                         int batch, const int n[3], double* lap, float* out);
+
+/* Hybrid stepping of a multipatch context: `calls` surrogate calls of four
+ * steps of dt each.  Per call, from the state at t_n (its covered global cells
+ * refilled from the local patches, Sec. 2.4): the surrogate's global state
+ * four steps later and its residual r = max(|R_psi|, Delta |R_Pi|) /
+ * max(|psi0|, Delta |Pi0|) (mpw_sur_check).  r <= tol: the global patch takes
+ * that state, and the local patches take their four RK4 steps of the method,
+ * their ghost zones filled from a global patch that holds, at every substage,
+ * the stage input the method would have formed there: for the linear system,
+ * u, u + dt/2 u', u + dt/2 u' + dt^2/4 u'', u + dt u' + dt^2/2 u'' + dt^3/4 u'''
+ * with u and its time derivatives taken from the quintic Hermite interpolant
+ * in time of (psi, Pi) between the two global states (values, d/dt and
+ * d^2/dt^2 from Pi, L psi and L Pi).
+ * Otherwise (or r not finite) the call is discarded and the four steps are
+ * the method's own (mpw_step).  After an accepted call the global patch
+ * continues from its own state: local-patch data enters it only at a call
+ * that follows a plain step or a change of fields or time, so the data flow
+ * stays one-way from the global patch to the local ones (Sec. 2.4).  Needs a
+ * binary64 context whose global patch is periodic with the surrogate's
+ * spacing, translating Cartesian local patches, and the surrogate's dt; the
+ * surrogate's stream is synchronised with the context's when they differ.
+ * accepted, max_residual (optional): calls taken, largest r.  Errors: those
+ * of mpw_step, MPW_ERR_ARG. */
+mpw_status mpw_step_surrogate(mpw_ctx* ctx, mpw_sur* s, double dt, int calls, double tol, int* accepted,
+                              double* max_residual);
 
 #ifdef __cplusplus
 }

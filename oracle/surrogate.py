@@ -85,13 +85,14 @@ def mse(y, t):
 #
 # One call replaces four RK4 steps of the method (Delta = 4 dt) on a periodic
 # global patch of spacing h.  L is the method's 4th-order centred Laplacian.
-# The state advances by a second-order Taylor step of the wave equation
-# (d psi/dt = Pi, d Pi/dt = L psi) plus the network's learned remainder; the
-# network sees the state and its Laplacians scaled to order one.  The
+# The state advances by the fourth-order Taylor step of the semi-discrete wave
+# equation (d psi/dt = Pi, d Pi/dt = L psi; for this linear system one RK4
+# step of size Delta) plus the network's learned remainder; the network sees
+# the state and its Laplacians scaled to order one.  The
 # operation order below is the order in which every value is defined (the
 # device computes the same FP64 operations, each rounded once).
 
-LAYERS = [(4, 32, True), (32, 32, True), (32, 32, True), (32, 2, False)]  # (cin, cout, relu)
+LAYERS = [(7, 32, True), (32, 32, True), (32, 32, True), (32, 2, False)]  # (cin, cout, relu)
 PADDED = [(8, 32), (32, 32), (32, 32), (32, 8)]                            # stored channel counts
 
 
@@ -123,8 +124,10 @@ def pack_params(layers, dtype=np.float32):
 
 
 def coefficients(dt, h):
+    """Delta, Delta^2/2, Delta^3/6, Delta^4/24, 1/(12 h^2) and the powers Delta^1..6."""
     D = 4.0 * dt
-    return D, D * D, D * D * D, D * D / 2.0, 1.0 / (12.0 * h * h)
+    powers = [D, D * D, D * D * D, D * D * D * D, D * D * D * D * D, D * D * D * D * D * D]
+    return D, D * D / 2.0, D * D * D / 6.0, D * D * D * D / 24.0, 1.0 / (12.0 * h * h), powers
 
 
 def lap4(u, h):
@@ -149,30 +152,38 @@ def scales(psi, pi, dt):
 
 
 def features(psi, pi, dt, h):
-    """x = bf16(s psi, s Delta Pi, s Delta^2 L psi, s Delta^3 L Pi) and s."""
-    D, D2, D3, _, _ = coefficients(dt, h)
+    """x = bf16(s psi, s D Pi, s D^2 L psi, s D^3 L Pi, s D^4 L^2 psi, s D^5 L^2 Pi,
+    s D^6 L^3 psi) (D = Delta: the terms of the Taylor series of the evolution,
+    each scaled to order one) and s."""
+    Dk = coefficients(dt, h)[5]
     s = scales(psi, pi, dt).astype(np.float64)[:, None, None, None]
-    f = [s * psi, (s * D) * pi, (s * D2) * lap4(psi, h), (s * D3) * lap4(pi, h)]
+    lp, lq = lap4(psi, h), lap4(pi, h)
+    llp, llq = lap4(lp, h), lap4(lq, h)
+    lllp = lap4(llp, h)
+    f = [s * psi, (s * Dk[0]) * pi, (s * Dk[1]) * lp, (s * Dk[2]) * lq, (s * Dk[3]) * llp, (s * Dk[4]) * llq,
+         (s * Dk[5]) * lllp]
     return bf16(np.stack(f, axis=-1)), s[:, 0, 0, 0].astype(np.float32)
 
 
 def targets(psi0, pi0, psi1, pi1, s, dt, h, sigma):
     """The remainder of the method's four steps over the Taylor step, scaled."""
-    D, _, _, hD2, _ = coefficients(dt, h)
+    D, hD2, D36, D424, _, _ = coefficients(dt, h)
     lp, lq = lap4(psi0, h), lap4(pi0, h)
-    r0 = ((psi1 - psi0) - D * pi0) - hD2 * lp
-    r1 = ((pi1 - pi0) - D * lp) - hD2 * lq
+    llp, llq = lap4(lp, h), lap4(lq, h)
+    r0 = ((((psi1 - psi0) - D * pi0) - hD2 * lp) - D36 * lq) - D424 * llp
+    r1 = ((((pi1 - pi0) - D * lp) - hD2 * lq) - D36 * llp) - D424 * llq
     cs = np.asarray(s, np.float64)[:, None, None, None] / sigma
     return np.stack([(cs * r0).astype(np.float32), ((cs * D) * r1).astype(np.float32)], axis=-1).astype(np.float64)
 
 
 def apply(psi0, pi0, s, y, dt, h, sigma):
     """(psi1, Pi1) from the Taylor step and the network output y[..., 0:2]."""
-    D, _, _, hD2, _ = coefficients(dt, h)
+    D, hD2, D36, D424, _, _ = coefficients(dt, h)
     lp, lq = lap4(psi0, h), lap4(pi0, h)
+    llp, llq = lap4(lp, h), lap4(lq, h)
     a = sigma / np.asarray(s, np.float64)[:, None, None, None]
-    psi1 = ((psi0 + D * pi0) + hD2 * lp) + a * y[..., 0]
-    pi1 = ((pi0 + D * lp) + hD2 * lq) + (a / D) * y[..., 1]
+    psi1 = ((((psi0 + D * pi0) + hD2 * lp) + D36 * lq) + D424 * llp) + a * y[..., 0]
+    pi1 = ((((pi0 + D * lp) + hD2 * lq) + D36 * llp) + D424 * llq) + (a / D) * y[..., 1]
     return psi1, pi1
 
 
@@ -210,3 +221,27 @@ def net_grads(x, params, t, rounded=True):
         g = conv3_input_grad(g, W, mask=acts[l])
         g = bf16(g) if rounded else g
     return loss, pack_params(grads, np.float64)
+
+
+def residual(psi0, pi0, psi1, pi1, dt, h):
+    """Per sample max(|R_psi|, Delta |R_Pi|) and max(|psi0|, Delta |Pi0|), with the
+    two-point quadrature with end corrections of d psi/dt = Pi, d Pi/dt = L psi:
+    R_psi = psi1 - psi0 - D/2 (Pi0 + Pi1) + D^2/12 (L psi1 - L psi0),
+    R_Pi  = Pi1 - Pi0 - D/2 (L psi0 + L psi1) + D^2/12 (L Pi1 - L Pi0)."""
+    D = 4.0 * dt
+    lp0, lq0, lp1, lq1 = (lap4(u, h) for u in (psi0, pi0, psi1, pi1))
+    rp = (psi1 - psi0) - D / 2 * (pi0 + pi1) + D * D / 12 * (lp1 - lp0)
+    rq = (pi1 - pi0) - D / 2 * (lp0 + lp1) + D * D / 12 * (lq1 - lq0)
+    B = psi0.shape[0]
+    r = np.maximum(np.abs(rp), D * np.abs(rq)).reshape(B, -1).max(axis=1)
+    m = np.maximum(np.abs(psi0), D * np.abs(pi0)).reshape(B, -1).max(axis=1)
+    return r, m
+
+
+def hermite5(tau):
+    """Quintic Hermite basis on [0, 1]: weights of y0, y0', y0'', y1, y1', y1''
+    (derivatives in units of the interval)."""
+    t = tau
+    return np.array([1 - 10 * t**3 + 15 * t**4 - 6 * t**5, t - 6 * t**3 + 8 * t**4 - 3 * t**5,
+                     0.5 * (t**2 - 3 * t**3 + 3 * t**4 - t**5), 10 * t**3 - 15 * t**4 + 6 * t**5,
+                     -4 * t**3 + 7 * t**4 - 3 * t**5, 0.5 * (t**3 - 2 * t**4 + t**5)])

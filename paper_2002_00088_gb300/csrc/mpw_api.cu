@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "../../include/mpw.h"
+#include "../../include/mpw_surrogate.h"
 #include "mpw_fixed.cuh"
 #include "mpw_internal.cuh"
 
@@ -104,6 +105,11 @@ struct mpw_ctx {
   double shell_time[4] = {NAN, NAN, NAN, NAN};
   double* d_stage = nullptr;
   size_t stage_bytes = 0;
+  double* d_sur = nullptr;  // hybrid stepping: dense global states, Laplacians, Hermite coefficients
+  size_t sur_bytes = 0;
+  // the global state the last accepted surrogate call produced is still the
+  // context's (no plain step, field or time change since)
+  bool sur_valid = false;
   // copy streams of the asynchronous host IO: inputs in, results out
   cudaStream_t io_in = nullptr, io_out = nullptr;
   double t = 0.0;
@@ -959,7 +965,7 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
 // One fused RHS + RK4 stage launch over every patch (substage l at t).
 // RHS + stage arguments of substage l for every patch of c; returns the
 // number of CTAs.  zc: planes per CTA chunk (0: the default).
-int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
+int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0, bool skip_global = false) {
   static const int in_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
   static const int out_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
   a = RhsArgs{};
@@ -1012,6 +1018,7 @@ int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0) {
     R.zchunks = (P.d.n[2] + R.zc - 1) / R.zc;
     R.block0 = blocks;
     if (P.sph()) continue;  // spherical shells: k_rhs_shell
+    if (skip_global && q == 0) continue;  // the global patch advanced by other means
     blocks += R.tiles_x * R.tiles_y * R.zchunks;
   }
   return blocks;
@@ -1064,15 +1071,17 @@ long long prep_rhs_shell(mpw_ctx* c, int l, double t, double dt, ShellArgs& a, l
   return blocks;
 }
 
-mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt) {
+mpw_status run_rhs(mpw_ctx* c, int l, double t, double dt, bool skip_global = false) {
   RhsArgs a;
-  const int blocks = prep_rhs(c, l, t, dt, a);
+  const int blocks = prep_rhs(c, l, t, dt, a, 0, skip_global);
   bool rot = false;
   for (int q = 0; q < a.np; ++q) rot = rot || a.p[q].rot;
   ShellArgs sa{};
   const long long sblocks = prep_rhs_shell(c, l, t, dt, sa);
   c->launch_begin(MPW_KERNEL_RHS);
-  if (c->cfg.precision == 32)
+  if (blocks == 0)
+    c->launches[MPW_KERNEL_RHS] -= 1;  // nothing to launch (only shells, or the skipped global patch)
+  else if (c->cfg.precision == 32)
     launch_rhs32(a, blocks, rot, c->stream);
   else
     launch_rhs(a, blocks, c->cfg.arith != 1, rot, c->stream);
@@ -1226,6 +1235,7 @@ void mpw_destroy(mpw_ctx* c) {
   c->dfree(c->d_gcount);
   c->dfree(c->d_mirror);
   c->dfree(c->d_stage);
+  c->dfree(c->d_sur);
   if (c->h_err) cudaFreeHost(c->h_err);
   for (auto& v : c->ev)
     for (cudaEvent_t e : v) cudaEventDestroy(e);
@@ -1381,6 +1391,7 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
     P.u_expo_valid = false;
   }
   c->t = t;
+  c->sur_valid = false;
   return MPW_OK;
 }
 
@@ -1462,6 +1473,7 @@ mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double
   launch_unpack(P->buf(BUF_U), P->g, s0, s1, c->cfg.precision == 32, c->stream);
   CUDA_TRY(cudaGetLastError());
   P->u_expo_valid = false;
+  c->sur_valid = false;
   if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
   return MPW_OK;
 }
@@ -1511,6 +1523,7 @@ mpw_status mpw_set_fields_async(mpw_ctx* c, int patch, const double* psi, const 
   CUDA_TRY(cudaMemcpyAsync(P->io_in + n, pi, n * sizeof(double), cudaMemcpyHostToDevice, c->io_in));
   CUDA_TRY(cudaEventRecord(P->in_copied, c->io_in));
   P->in_pending = true;
+  c->sur_valid = false;
   return MPW_OK;
 }
 
@@ -1555,6 +1568,7 @@ mpw_status mpw_set_time(mpw_ctx* c, double t) {
   mpw_status st = check_ctx(c);
   if (st) return st;
   c->t = t;
+  c->sur_valid = false;
   return MPW_OK;
 }
 
@@ -1660,8 +1674,164 @@ static mpw_status step_impl(mpw_ctx* c, double dt, int nsteps, bool check_errors
     }
     c->t = tn + dt;
     c->stepped = true;
+    c->sur_valid = false;
   }
   return check_errors ? read_error_word(c) : MPW_OK;
+}
+
+// The dead global cells of the U buffer from their local patches (the cover
+// flags and boxes of t_n; translating Cartesian local patches).
+static mpw_status fill_dead_cells(mpw_ctx* c) {
+  const PatchState& g = c->p[0];
+  FlagArgs a{};
+  a.flags = c->d_flags;
+  for (int k = 0; k < 3; ++k) a.n[k] = g.d.n[k];
+  a.nloc = (int)c->p.size() - 1;
+  if (a.nloc == 0 || (int)c->boxes.size() != a.nloc) return MPW_OK;
+  for (int q = 0; q < a.nloc; ++q) {
+    const PatchState& L = c->p[q + 1];
+    a.box[q] = c->boxes[q];
+    a.Uloc[q] = L.buf(BUF_U);
+    a.gl[q] = L.g;
+    const Frame f = frame(L.d, c->t);
+    for (int k = 0; k < 3; ++k) a.X0[q][k] = f.X0[k];
+  }
+  a.Ug = g.buf(BUF_U);
+  a.gg = g.g;
+  a.P = c->P;
+  a.err = c->d_err;
+  launch_fill_dead(a, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+// Quintic Hermite basis on [0, 1] as coefficients of tau^0..tau^5: value,
+// first and second derivative at 0, then at 1.
+static const double HERMITE5[6][6] = {{1, 0, 0, -10, 15, -6}, {0, 1, 0, -6, 8, -3},  {0, 0, 0.5, -1.5, 1.5, -0.5},
+                                      {0, 0, 0, 10, -15, 6},  {0, 0, 0, -4, 7, -3}, {0, 0, 0, 0.5, -1.0, 0.5}};
+
+// k-th derivative in tau of the polynomial c at tau
+static double poly_derivative(const double c[6], int k, double tau) {
+  double s = 0.0;
+  for (int p = 5; p >= k; --p) {
+    double f = 1.0;
+    for (int r = 0; r < k; ++r) f *= p - r;
+    s = s * tau + c[p] * f;
+  }
+  return s;
+}
+
+// Weights of (y0, y0', y0'', y1, y1', y1'') -- the state at both ends of a
+// call and its first two time derivatives -- in the input of RK4 stage l of
+// step m (of the four one call spans).  For the linear system u' = A u the
+// stage inputs of the method are u, u + dt/2 u', u + dt/2 u' + dt^2/4 u'' and
+// u + dt u' + dt^2/2 u'' + dt^3/4 u''' (Table 1 applied to A); u and its
+// derivatives are those of the interpolant at t_n + m dt.
+static void stage_coefficients(int m, int l, double D, double cf[6]) {
+  static const double mult[4][4] = {{1, 0, 0, 0}, {1, 0.5, 0, 0}, {1, 0.5, 0.25, 0}, {1, 1, 0.5, 0.25}};
+  const double tau = m / 4.0, r = 0.25;  // dt / Delta
+  const double unit[6] = {1.0, D, D * D, 1.0, D, D * D};
+  for (int j = 0; j < 6; ++j) {
+    double w = 0.0, rk = 1.0;
+    for (int k = 0; k < 4; ++k, rk *= r) w += mult[l][k] * rk * poly_derivative(HERMITE5[j], k, tau);
+    cf[j] = w * unit[j];
+  }
+}
+
+mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, double tol, int* accepted,
+                              double* max_residual) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  double sdt = 0.0, sh = 0.0;
+  void* sstream = nullptr;
+  if (!sur_geometry(s, &sdt, &sh, &sstream)) return set_err(MPW_ERR_ARG, "null surrogate handle");
+  if (c->p.empty()) return set_err(MPW_ERR_STATE, "no global patch");
+  if (calls < 0) return set_err(MPW_ERR_ARG, "calls must be >= 0");
+  if (c->cfg.precision != 64) return set_err(MPW_ERR_ARG, "the surrogate path runs on binary64 contexts");
+  PatchState& G = c->p[0];
+  if (G.d.outer_bc != MPW_BC_PERIODIC) return set_err(MPW_ERR_ARG, "the surrogate needs a periodic global patch");
+  for (int a = 0; a < 3; ++a)
+    if (std::fabs(G.g.h[a] - sh) > 1e-12 * sh) return set_err(MPW_ERR_ARG, "global spacing differs from the surrogate's");
+  if (std::fabs(dt - sdt) > 1e-12 * sdt) return set_err(MPW_ERR_ARG, "dt differs from the surrogate's");
+  for (size_t q = 1; q < c->p.size(); ++q)
+    if (c->p[q].sph() || c->p[q].d.motion == MPW_MOTION_ROTATING)
+      return set_err(MPW_ERR_ARG, "the surrogate path takes translating Cartesian local patches only");
+  if (use_device(c)) return MPW_ERR_CUDA;
+  if ((st = apply_pending_inputs(c))) return st;
+  const int n[3] = {G.d.n[0], G.d.n[1], G.d.n[2]};
+  const long long P = (long long)n[0] * n[1] * n[2];
+  const size_t need = (size_t)8 * P * sizeof(double) + 16 * 6 * sizeof(double) + 4 * sizeof(float);
+  if (c->sur_bytes < need) {
+    c->dfree(c->d_sur);
+    c->sur_bytes = 0;
+    if (!(c->d_sur = (double*)c->dalloc(need))) return set_err(MPW_ERR_CUDA, "device allocation failed");
+    c->sur_bytes = need;
+  }
+  double* U = c->d_sur;  // psi0, Pi0, psi1, Pi1, then L psi0, L Pi0, L psi1, L Pi1
+  double* coef = U + 8 * P;
+  float* chk = (float*)(coef + 16 * 6);
+  const cudaStream_t ss = (cudaStream_t)sstream;
+  const double D = 4.0 * dt;
+  double hc[16 * 6];
+  for (int m = 0; m < 4; ++m)
+    for (int l = 0; l < 4; ++l) stage_coefficients(m, l, D, hc + (4 * m + l) * 6);
+  CUDA_TRY(cudaMemcpyAsync(coef, hc, sizeof(hc), cudaMemcpyHostToDevice, c->stream));
+  int acc = 0;
+  double rmax = 0.0;
+  for (int call = 0; call < calls; ++call) {
+    if ((st = step_prologue(c, dt))) return st;
+    if (c->sur_valid) {
+      // the global patch continues from its own state: no local data flows
+      // back into it, so nothing the local patches computed returns to them
+      // through the global (the one-way data flow of Sec. 2.4)
+      CUDA_TRY(cudaMemcpyAsync(U, U + 2 * P, 2 * P * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    } else {
+      // the state at t_n, its covered cells filled from the local patches
+      if ((st = run_fill(c, FILL_BUF[0], c->t, NEXT_BUF[0]))) return st;
+      if ((st = fill_dead_cells(c))) return st;
+      launch_pack(G.buf(BUF_U), G.g, U, U + P, 0, nullptr, false, c->stream);
+      CUDA_TRY(cudaGetLastError());
+    }
+    if (ss != c->stream) CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if ((st = mpw_sur_predict(s, U, U + P, 1, n, U + 2 * P, U + 3 * P))) return st;
+    if ((st = mpw_sur_check(s, U, U + P, U + 2 * P, U + 3 * P, 1, n, U + 4 * P, chk))) return st;
+    float h2[2];
+    CUDA_TRY(cudaMemcpyAsync(h2, chk, sizeof(h2), cudaMemcpyDeviceToHost, ss));
+    CUDA_TRY(cudaStreamSynchronize(ss));
+    const double r = h2[1] > 0.0f ? (double)h2[0] / h2[1] : (double)h2[0];
+    rmax = std::isfinite(r) ? std::max(rmax, r) : INFINITY;
+    if (!(r <= tol)) {
+      // fall back: the method's own four steps from the same state
+      if ((st = step_impl(c, dt, 4, false))) return st;
+      continue;  // step_impl cleared sur_valid
+    }
+    ++acc;
+    for (int m = 0; m < 4; ++m) {
+      if (m > 0 && (st = step_prologue(c, dt))) return st;
+      const double tn = c->t;
+      for (int l = 0; l < 4; ++l) {
+        const double tl = tn + RK_C[l] * dt;
+        // the global stage buffer holds the stage input the method would
+        // have formed, from the interpolant; only the local patches take an
+        // RHS + stage update
+        int* slot2 = c->d_expo + FILL_BUF[l] * 2;
+        CUDA_TRY(cudaMemsetAsync(slot2, 0, 2 * sizeof(int), c->stream));
+        launch_hermite(G.buf(FILL_BUF[l]), G.g, U, coef + (4 * m + l) * 6, slot2, c->stream);
+        CUDA_TRY(cudaGetLastError());
+        if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l]))) return st;
+        if ((st = run_rhs(c, l, tl, dt, true))) return st;
+      }
+      c->t = tn + dt;
+      c->stepped = true;
+    }
+    launch_unpack(G.buf(BUF_U), G.g, U + 2 * P, U + 3 * P, false, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    G.u_expo_valid = false;
+    c->sur_valid = true;
+  }
+  if (accepted) *accepted = acc;
+  if (max_residual) *max_residual = rmax;
+  return read_error_word(c);
 }
 
 mpw_status mpw_live_points(mpw_ctx* c, long long* count) {
@@ -1965,6 +2135,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     for (int i = 0; i < n; ++i) {
       b->ctx[i]->t = tnp[i] + dt[i];
       b->ctx[i]->stepped = true;
+      b->ctx[i]->sur_valid = false;
     }
     ++b->steps_done;
     if (trial && b->steps_done == (long long)nc) {

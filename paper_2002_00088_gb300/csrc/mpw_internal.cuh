@@ -8,6 +8,8 @@
 
 #include "mpw_rhs_args.cuh"
 
+struct mpw_sur;
+
 namespace mpw {
 
 // ---------------------------------------------------------------- fill
@@ -190,6 +192,13 @@ constexpr int DIST_CAP = 9;          // distances above buffer + NG (<= 8) read 
 // Record the thread-local message returned by mpw_last_error().
 void set_last_error(const char* msg);
 
+// learned surrogate: the quintic Hermite interpolant in time of the global
+// state between two calls, written into a padded buffer (u: psi0, Pi0, psi1,
+// Pi1, L psi0, L Pi0, L psi1, L Pi1, dense; coef_dev: six device doubles),
+// and the step and spacing a surrogate was made for
+void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, void* stream);
+bool sur_geometry(const mpw_sur* s, double* dt, double* h, void** stream);
+
 // ---------------------------------------------------------------- tensor maps
 // Encode the TMA maps of the RHS kernel for one field buffer (psi at base, Pi
 // at base + vol) of geometry g: box (RHS_TX + 8) x (RHS_TY + 6) ("tile") or
@@ -217,6 +226,7 @@ int fill_cap_r2();
 int fill_max_tile();
 int fill_threads();
 int launch_flags(const FlagArgs& a, void* stream);  // returns the number of kernels launched
+void launch_fill_dead(const FlagArgs& a, void* stream);  // binary64 buffers only
 // buf: a field buffer of binary64, or of binary32 when f32; the dense arrays
 // d0, d1 are binary64 in every case.
 struct Affine {

@@ -291,6 +291,48 @@ __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs
   }
 }
 
+// Every DEAD global cell of buffer A.Ug takes the Lagrange interpolant of the
+// local patch that covers it (A.Uloc: that patch's buffer).  Dead cells take
+// no part in the method; the learned surrogate reads a complete field.
+// Block row q of the grid walks the covered box of local patch q.
+template <int P>
+__global__ void __launch_bounds__(256) k_fill_dead(const __grid_constant__ FlagArgs A) {
+  const int q = blockIdx.y;
+  const Box& b = A.box[q];
+  const int w0 = b.hi[0] - b.lo[0] + 1, w1 = b.hi[1] - b.lo[1] + 1, w2 = b.hi[2] - b.lo[2] + 1;
+  if (w0 <= 0 || w1 <= 0 || w2 <= 0) return;
+  const long long V = (long long)w0 * w1 * w2;
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < V; e += (long long)gridDim.x * blockDim.x) {
+    const int i = b.lo[0] + (int)(e % w0), j = b.lo[1] + (int)((e / w0) % w1), k = b.lo[2] + (int)(e / ((long long)w0 * w1));
+    const uint8_t f = A.flags[((long long)k * A.n[1] + j) * A.n[0] + i];
+    if ((f & 3) != FLAG_DEAD || (f >> 2) != q + 1) continue;
+    double v0, v1, x, y, z;
+    cell_in_local(A, q, i, j, k, x, y, z);
+    if (interp_point<P>(A.Uloc[q], A.gl[q], x, y, z, v0, v1)) {
+      const long long c = A.gg.at(i, j, k);
+      A.Ug[c] = v0;
+      A.Ug[c + A.gg.vol] = v1;
+    } else {
+      atomicOr(A.err, ERR_UNFILLED);
+    }
+  }
+}
+
+void launch_fill_dead(const FlagArgs& a, void* stream) {
+  long long vmax = 0;
+  for (int q = 0; q < a.nloc; ++q) {
+    const Box& b = a.box[q];
+    vmax = std::max(vmax, (long long)std::max(b.hi[0] - b.lo[0] + 1, 0) * std::max(b.hi[1] - b.lo[1] + 1, 0) *
+                              std::max(b.hi[2] - b.lo[2] + 1, 0));
+  }
+  if (vmax == 0 || a.nloc == 0) return;
+  const dim3 grid((unsigned)std::min<long long>((vmax + 255) / 256, 1024), (unsigned)a.nloc);
+  if (a.P == 6)
+    k_fill_dead<6><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+  else
+    k_fill_dead<5><<<grid, 256, 0, (cudaStream_t)stream>>>(a);
+}
+
 template <int P, typename ST>
 static void launch_flags_t(const FlagArgs& a, unsigned blocks, unsigned rblocks, cudaStream_t s) {
   const long long ncov = a.cov_off[a.nloc];

@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "../../include/mpw_surrogate.h"
+#include "mpw_fixed.cuh"
 #include "mpw_internal.cuh"
 
 namespace {
@@ -116,7 +117,8 @@ __global__ void k_scale(const unsigned* maxbits, int batch, float* scale) {
 }
 
 struct Coef {
-  double delta, d2, d3, hd2, inv12h2, sigma;  // Delta, Delta^2, Delta^3, Delta^2/2, 1/(12 h^2), sigma
+  // Delta, Delta^2 .. Delta^6, Delta^2/2, Delta^3/6, Delta^4/24, 1/(12 h^2), sigma
+  double delta, d2, d3, d4, d5, d6, hd2, d36, d424, inv12h2, sigma;
 };
 
 __device__ __forceinline__ void point_ijk(long long q, const Dims& d, int& i, int& j, int& k) {
@@ -125,59 +127,70 @@ __device__ __forceinline__ void point_ijk(long long q, const Dims& d, int& i, in
   k = (int)(q / ((long long)d.n0 * d.n1));
 }
 
-__global__ void k_features(const double* psi, const double* pi, Dims d, Coef c, const float* scale, uint4* x) {
-  const long long P = d.points();
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P * d.batch;
-       g += (long long)gridDim.x * blockDim.x) {
+// lap: the chain L psi, L Pi, L^2 psi, L^2 Pi, L^3 psi, L^3 Pi ([6][batch * points])
+__global__ void k_features(const double* psi, const double* pi, Dims d, Coef c, const float* scale, const double* lap,
+                           uint4* x) {
+  const long long N = d.points() * d.batch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
+    const double s = (double)scale[g / d.points()];
+    const double f[7] = {__dmul_rn(s, psi[g]),
+                         __dmul_rn(__dmul_rn(s, c.delta), pi[g]),
+                         __dmul_rn(__dmul_rn(s, c.d2), lap[g]),
+                         __dmul_rn(__dmul_rn(s, c.d3), lap[N + g]),
+                         __dmul_rn(__dmul_rn(s, c.d4), lap[2 * N + g]),
+                         __dmul_rn(__dmul_rn(s, c.d5), lap[3 * N + g]),
+                         __dmul_rn(__dmul_rn(s, c.d6), lap[4 * N + g])};
+    __nv_bfloat162 h[4];
+    for (int q = 0; q < 3; ++q) h[q] = __floats2bfloat162_rn(__double2float_rn(f[2 * q]), __double2float_rn(f[2 * q + 1]));
+    h[3] = __floats2bfloat162_rn(__double2float_rn(f[6]), 0.0f);
+    x[g] = make_uint4(*reinterpret_cast<unsigned*>(&h[0]), *reinterpret_cast<unsigned*>(&h[1]),
+                      *reinterpret_cast<unsigned*>(&h[2]), *reinterpret_cast<unsigned*>(&h[3]));
+  }
+}
+
+// L psi and L Pi of every sample (lap: [2][batch * points])
+__global__ void k_lap2(const double* psi, const double* pi, Dims d, double inv12h2, double* lap) {
+  const long long P = d.points(), N = P * d.batch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(g / P);
     int i, j, k;
     point_ijk(g - (long long)b * P, d, i, j, k);
-    const double* ps = psi + (long long)b * P;
-    const double* pp = pi + (long long)b * P;
-    const double s = (double)scale[b];
-    const double f0 = __dmul_rn(s, ps[g - (long long)b * P]);
-    const double f1 = __dmul_rn(__dmul_rn(s, c.delta), pp[g - (long long)b * P]);
-    const double f2 = __dmul_rn(__dmul_rn(s, c.d2), lap4(ps, d, i, j, k, c.inv12h2));
-    const double f3 = __dmul_rn(__dmul_rn(s, c.d3), lap4(pp, d, i, j, k, c.inv12h2));
-    __nv_bfloat162 a = __floats2bfloat162_rn(__double2float_rn(f0), __double2float_rn(f1));
-    __nv_bfloat162 bb = __floats2bfloat162_rn(__double2float_rn(f2), __double2float_rn(f3));
-    x[g] = make_uint4(*reinterpret_cast<unsigned*>(&a), *reinterpret_cast<unsigned*>(&bb), 0u, 0u);
+    lap[g] = lap4(psi + (long long)b * P, d, i, j, k, inv12h2);
+    lap[N + g] = lap4(pi + (long long)b * P, d, i, j, k, inv12h2);
   }
 }
 
 __global__ void k_targets(const double* psi0, const double* pi0, const double* psi1, const double* pi1, Dims d,
-                          Coef c, const float* scale, float2* t) {
-  const long long P = d.points();
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P * d.batch;
-       g += (long long)gridDim.x * blockDim.x) {
+                          Coef c, const float* scale, const double* lap, float2* t) {
+  const long long P = d.points(), N = P * d.batch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(g / P);
-    int i, j, k;
-    point_ijk(g - (long long)b * P, d, i, j, k);
-    const double lp = lap4(psi0 + (long long)b * P, d, i, j, k, c.inv12h2);
-    const double lq = lap4(pi0 + (long long)b * P, d, i, j, k, c.inv12h2);
-    const double r0 = __dsub_rn(__dsub_rn(__dsub_rn(psi1[g], psi0[g]), __dmul_rn(c.delta, pi0[g])), __dmul_rn(c.hd2, lp));
-    const double r1 = __dsub_rn(__dsub_rn(__dsub_rn(pi1[g], pi0[g]), __dmul_rn(c.delta, lp)), __dmul_rn(c.hd2, lq));
+    const double lp = lap[g], lq = lap[N + g], llp = lap[2 * N + g], llq = lap[3 * N + g];
+    double r0 = __dsub_rn(__dsub_rn(psi1[g], psi0[g]), __dmul_rn(c.delta, pi0[g]));
+    r0 = __dsub_rn(__dsub_rn(__dsub_rn(r0, __dmul_rn(c.hd2, lp)), __dmul_rn(c.d36, lq)), __dmul_rn(c.d424, llp));
+    double r1 = __dsub_rn(__dsub_rn(pi1[g], pi0[g]), __dmul_rn(c.delta, lp));
+    r1 = __dsub_rn(__dsub_rn(__dsub_rn(r1, __dmul_rn(c.hd2, lq)), __dmul_rn(c.d36, llp)), __dmul_rn(c.d424, llq));
     const double cs = __ddiv_rn((double)scale[b], c.sigma);
     t[g] = make_float2(__double2float_rn(__dmul_rn(cs, r0)), __double2float_rn(__dmul_rn(__dmul_rn(cs, c.delta), r1)));
   }
 }
 
-// (psi1, Pi1) from (psi0, Pi0) and the network output y ([..][8], channels 0, 1)
-__global__ void k_apply(const double* psi0, const double* pi0, Dims d, Coef c, const float* scale, const float* y,
-                        double* psi1, double* pi1) {
-  const long long P = d.points();
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < P * d.batch;
-       g += (long long)gridDim.x * blockDim.x) {
+// (psi1, Pi1) from (psi0, Pi0), their Laplacians and the network output y
+// ([..][8], channels 0, 1)
+__global__ void k_apply(const double* psi0, const double* pi0, Dims d, Coef c, const float* scale, const double* lap,
+                        const float* y, double* psi1, double* pi1) {
+  const long long P = d.points(), N = P * d.batch;
+  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
     const int b = (int)(g / P);
-    int i, j, k;
-    point_ijk(g - (long long)b * P, d, i, j, k);
-    const double lp = lap4(psi0 + (long long)b * P, d, i, j, k, c.inv12h2);
-    const double lq = lap4(pi0 + (long long)b * P, d, i, j, k, c.inv12h2);
+    const double lp = lap[g], lq = lap[N + g], llp = lap[2 * N + g], llq = lap[3 * N + g];
     const double a = __ddiv_rn(c.sigma, (double)scale[b]);
     const double n0 = (double)y[g * 8], n1 = (double)y[g * 8 + 1];
-    psi1[g] = __dadd_rn(__dadd_rn(__dadd_rn(psi0[g], __dmul_rn(c.delta, pi0[g])), __dmul_rn(c.hd2, lp)), __dmul_rn(a, n0));
-    pi1[g] = __dadd_rn(__dadd_rn(__dadd_rn(pi0[g], __dmul_rn(c.delta, lp)), __dmul_rn(c.hd2, lq)),
-                       __dmul_rn(__ddiv_rn(a, c.delta), n1));
+    double u = __dadd_rn(psi0[g], __dmul_rn(c.delta, pi0[g]));
+    u = __dadd_rn(__dadd_rn(__dadd_rn(u, __dmul_rn(c.hd2, lp)), __dmul_rn(c.d36, lq)), __dmul_rn(c.d424, llp));
+    psi1[g] = __dadd_rn(u, __dmul_rn(a, n0));
+    double v = __dadd_rn(pi0[g], __dmul_rn(c.delta, lp));
+    v = __dadd_rn(__dadd_rn(__dadd_rn(v, __dmul_rn(c.hd2, lq)), __dmul_rn(c.d36, llp)), __dmul_rn(c.d424, llq));
+    pi1[g] = __dadd_rn(v, __dmul_rn(__ddiv_rn(a, c.delta), n1));
   }
 }
 
@@ -193,6 +206,78 @@ __global__ void k_to_bf16(const float* w, __nv_bfloat16* w16, long long n) {
 unsigned grid_for(long long n, int threads = 256) {
   long long b = (n + threads - 1) / threads;
   return (unsigned)(b < 4096 ? (b > 0 ? b : 1) : 4096);
+}
+
+
+// Residual of a call against the method's RHS: with f = Pi, f' = L psi for
+// psi and f = L psi, f' = L Pi for Pi, the two-point quadrature with end
+// corrections, int_0^Delta f = Delta/2 (f0 + f1) + Delta^2/12 (f0' - f1'),
+// leaves O(Delta^5) for the exact evolution.  Writes the four Laplacians
+// (optional) and, per sample, max(|R_psi|, Delta |R_Pi|) and max(|psi0|,
+// Delta |Pi0|) as binary32 bit patterns (atomic maximum).
+__global__ void k_check(const double* psi0, const double* pi0, const double* psi1, const double* pi1, Dims d, Coef c,
+                        double* lap, unsigned* out) {
+  const long long P = d.points(), N = P * d.batch;
+  const double hd = 0.5 * c.delta, d12 = c.d2 / 12.0;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += (long long)gridDim.x * blockDim.x) {
+    const long long g = base + threadIdx.x;
+    unsigned r = 0, m = 0;
+    if (g < N) {
+      const int b = (int)(g / P);
+      int i, j, k;
+      point_ijk(g - (long long)b * P, d, i, j, k);
+      const long long o = (long long)b * P;
+      const double lp0 = lap4(psi0 + o, d, i, j, k, c.inv12h2), lq0 = lap4(pi0 + o, d, i, j, k, c.inv12h2);
+      const double lp1 = lap4(psi1 + o, d, i, j, k, c.inv12h2), lq1 = lap4(pi1 + o, d, i, j, k, c.inv12h2);
+      if (lap) {
+        lap[g] = lp0;
+        lap[N + g] = lq0;
+        lap[2 * N + g] = lp1;
+        lap[3 * N + g] = lq1;
+      }
+      const double rp = (psi1[g] - psi0[g]) - hd * (pi0[g] + pi1[g]) + d12 * (lp1 - lp0);
+      const double rq = (pi1[g] - pi0[g]) - hd * (lp0 + lp1) + d12 * (lq1 - lq0);
+      r = __float_as_uint(__double2float_ru(fmax(fabs(rp), c.delta * fabs(rq))));
+      m = __float_as_uint(__double2float_rn(fmax(fabs(psi0[g]), c.delta * fabs(pi0[g]))));
+    }
+    r = __reduce_max_sync(0xffffffffu, r);
+    m = __reduce_max_sync(0xffffffffu, m);
+    if ((threadIdx.x & 31) == 0 && base + (threadIdx.x & ~31) < N) {
+      const long long b = (base + threadIdx.x) / P;
+      atomicMax(&out[2 * b], r);
+      atomicMax(&out[2 * b + 1], m);
+    }
+  }
+}
+
+// Quintic Hermite interpolant in time of the state between two calls, written
+// into the interior of a padded patch buffer: y(tau) = c0 y0 + c1 y0' + c2 y0''
+// + c3 y1 + c4 y1' + c5 y1'' (coefficients: the basis at tau times Delta^k),
+// with y = psi, y' = Pi, y'' = L psi for psi and y = Pi, y' = L psi, y'' = L Pi
+// for Pi.  slot2 receives the largest biased exponent of each field.
+__global__ void k_hermite(double* buf, mpw::Geom g, const double* u, long long P, const double* cf, int* slot2) {
+  const double *psi0 = u, *pi0 = u + P, *psi1 = u + 2 * P, *pi1 = u + 3 * P;
+  const double *lp0 = u + 4 * P, *lq0 = u + 5 * P, *lp1 = u + 6 * P, *lq1 = u + 7 * P;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < P; base += (long long)gridDim.x * blockDim.x) {
+    const long long q = base + threadIdx.x;
+    int e0 = 0, e1 = 0;
+    if (q < P) {
+      const int i = (int)(q % g.n[0]), j = (int)((q / g.n[0]) % g.n[1]), k = (int)(q / ((long long)g.n[0] * g.n[1]));
+      const double ys = cf[0] * psi0[q] + cf[1] * pi0[q] + cf[2] * lp0[q] + cf[3] * psi1[q] + cf[4] * pi1[q] + cf[5] * lp1[q];
+      const double yp = cf[0] * pi0[q] + cf[1] * lp0[q] + cf[2] * lq0[q] + cf[3] * pi1[q] + cf[4] * lp1[q] + cf[5] * lq1[q];
+      const long long a = g.at(i, j, k);
+      buf[a] = ys;
+      buf[g.vol + a] = yp;
+      e0 = mpw::biased_exponent(ys);
+      e1 = mpw::biased_exponent(yp);
+    }
+    e0 = __reduce_max_sync(0xffffffffu, e0);
+    e1 = __reduce_max_sync(0xffffffffu, e1);
+    if ((threadIdx.x & 31) == 0) {
+      if (e0) atomicMax(&slot2[0], e0);
+      if (e1) atomicMax(&slot2[1], e1);
+    }
+  }
 }
 
 }  // namespace
@@ -221,6 +306,7 @@ struct mpw_sur {
   // inference workspace
   long long xcap = 0;
   uint16_t* x = nullptr;
+  double* lap = nullptr;  // the Laplacian chain of the last input (6 * xcap)
   int bcap = 0;
   float* scale = nullptr;
   unsigned* maxbits = nullptr;
@@ -265,9 +351,12 @@ mpw_status ensure_train(mpw_sur* s, long long P) {
 mpw_status ensure_infer(mpw_sur* s, long long P, int batch) {
   if (P > s->xcap) {
     cudaFree(s->x);
+    cudaFree(s->lap);
     s->x = nullptr;
+    s->lap = nullptr;
     s->xcap = 0;
     SUR_TRY(cudaMalloc(&s->x, (size_t)P * 8 * 2));
+    SUR_TRY(cudaMalloc(&s->lap, (size_t)P * 6 * sizeof(double)));
     s->xcap = P;
   }
   if (batch > s->bcap) {
@@ -280,6 +369,16 @@ mpw_status ensure_infer(mpw_sur* s, long long P, int batch) {
     SUR_TRY(cudaMalloc(&s->maxbits, (size_t)batch * 4));
     s->bcap = batch;
   }
+  return MPW_OK;
+}
+
+// The Laplacian chain of (psi, Pi) into s->lap: L, L^2, L^3 of both fields.
+mpw_status lap_chain(mpw_sur* s, const double* psi, const double* pi, const Dims& d) {
+  const long long N = d.points() * d.batch;
+  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(psi, pi, d, s->coef.inv12h2, s->lap);
+  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(s->lap, s->lap + N, d, s->coef.inv12h2, s->lap + 2 * N);
+  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(s->lap + 2 * N, s->lap + 3 * N, d, s->coef.inv12h2, s->lap + 4 * N);
+  SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
 
@@ -320,7 +419,9 @@ mpw_status mpw_sur_create(int device, void* stream, double dt, double h, double 
   s->h = h;
   s->sigma = sigma;
   const double D = 4.0 * dt;
-  s->coef = Coef{D, D * D, D * D * D, D * D / 2.0, 1.0 / (12.0 * h * h), sigma};
+  s->coef = Coef{D,          D * D,          D * D * D,          D * D * D * D,        D * D * D * D * D,
+                  D * D * D * D * D * D, D * D / 2.0, D * D * D / 6.0, D * D * D * D / 24.0, 1.0 / (12.0 * h * h),
+                  sigma};
   s->nparam = layer_table(s->L);
   auto bail = [&](cudaError_t e) {
     mpw_sur_destroy(s);
@@ -352,7 +453,7 @@ void mpw_sur_destroy(mpw_sur* s) {
   cudaStreamSynchronize(s->stream);
   free_buffers(s);
   for (void* p : {(void*)s->w, (void*)s->g, (void*)s->m, (void*)s->v, (void*)s->w16, s->scratch, (void*)s->loss,
-                  (void*)s->x, (void*)s->scale, (void*)s->maxbits})
+                  (void*)s->x, (void*)s->lap, (void*)s->scale, (void*)s->maxbits})
     cudaFree(p);
   delete s;
 }
@@ -394,12 +495,13 @@ mpw_status mpw_sur_features(mpw_sur* s, const double* psi0, const double* pi0, i
   Dims d;
   MPW_TRY(dims_of(batch, n, d));
   if (!psi0 || !pi0 || !x || !scale) return fail(MPW_ERR_ARG, "surrogate: null tensor");
-  MPW_TRY(ensure_infer(s, 0, batch));
-  SUR_TRY(cudaMemsetAsync(s->maxbits, 0, (size_t)batch * 4, s->stream));
   const long long N = d.points() * batch;
+  MPW_TRY(ensure_infer(s, N, batch));
+  SUR_TRY(cudaMemsetAsync(s->maxbits, 0, (size_t)batch * 4, s->stream));
   k_absmax<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef.delta, s->maxbits);
   k_scale<<<(batch + 127) / 128, 128, 0, s->stream>>>(s->maxbits, batch, scale);
-  k_features<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, scale, reinterpret_cast<uint4*>(x));
+  MPW_TRY(lap_chain(s, psi0, pi0, d));
+  k_features<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, scale, s->lap, reinterpret_cast<uint4*>(x));
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
@@ -410,8 +512,11 @@ mpw_status mpw_sur_targets(mpw_sur* s, const double* psi0, const double* pi0, co
   Dims d;
   MPW_TRY(dims_of(batch, n, d));
   if (!psi0 || !pi0 || !psi1 || !pi1 || !scale || !t) return fail(MPW_ERR_ARG, "surrogate: null tensor");
-  k_targets<<<grid_for(d.points() * batch), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, scale,
-                                                                  reinterpret_cast<float2*>(t));
+  const long long P = d.points() * batch;
+  MPW_TRY(ensure_infer(s, P, batch));
+  MPW_TRY(lap_chain(s, psi0, pi0, d));
+  k_targets<<<grid_for(P), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, scale, s->lap,
+                                               reinterpret_cast<float2*>(t));
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
@@ -473,9 +578,40 @@ mpw_status mpw_sur_predict(mpw_sur* s, const double* psi0, const double* pi0, in
   MPW_TRY(ensure_train(s, P));
   MPW_TRY(mpw_sur_features(s, psi0, pi0, batch, n, s->x, s->scale));
   MPW_TRY(forward_chain(s, s->x, d, s->y));
-  k_apply<<<grid_for(P), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, s->scale, s->y, psi1, pi1);
+  // s->lap holds the chain of (psi0, Pi0) from the features
+  k_apply<<<grid_for(P), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, s->scale, s->lap, s->y, psi1, pi1);
+  SUR_TRY(cudaGetLastError());
+  return MPW_OK;
+}
+
+mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, const double* psi1, const double* pi1,
+                         int batch, const int n[3], double* lap, float* out) {
+  MPW_TRY(use(s));
+  Dims d;
+  MPW_TRY(dims_of(batch, n, d));
+  if (!psi0 || !pi0 || !psi1 || !pi1 || !out) return fail(MPW_ERR_ARG, "surrogate: null tensor");
+  SUR_TRY(cudaMemsetAsync(out, 0, (size_t)batch * 2 * sizeof(float), s->stream));
+  k_check<<<grid_for(d.points() * batch), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, lap,
+                                                                reinterpret_cast<unsigned*>(out));
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
 
 }  // extern "C"
+
+namespace mpw {
+
+void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, void* stream) {
+  const long long P = (long long)g.n[0] * g.n[1] * g.n[2];
+  k_hermite<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>(buf, g, u, P, coef_dev, slot2);
+}
+
+bool sur_geometry(const mpw_sur* s, double* dt, double* h, void** stream) {
+  if (!s) return false;
+  *dt = s->dt;
+  *h = s->h;
+  *stream = s->stream;
+  return true;
+}
+
+}  // namespace mpw

@@ -97,6 +97,8 @@ SIGNATURES = {
     "mpw_sur_train_step": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), C.c_float, _dp]),
     "mpw_sur_forward": (C.c_int, [_vp, _vp, C.c_int, C.POINTER(C.c_int), _vp]),
     "mpw_sur_predict": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), _vp, _vp]),
+    "mpw_sur_check": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), _vp, _vp]),
+    "mpw_step_surrogate": (C.c_int, [_vp, _vp, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_int), _dp]),
     "mpw_destroy": (None, [_vp]),
 }
 

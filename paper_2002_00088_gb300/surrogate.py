@@ -162,6 +162,16 @@ class Surrogate:
                                      float(lr), C.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
 
+    def check(self, psi0, pi0, psi1, pi1, want_laplacians=False):
+        """(max residual, max state) per sample (FP32 (B, 2)) and optionally the
+        Laplacians (4, B, n2, n1, n0) of mpw_sur_check."""
+        torch = _torch()
+        psi0_, B, n = self._dims(psi0)
+        out = torch.empty((B, 2), dtype=torch.float32, device=psi0.device)
+        lap = torch.empty((4,) + tuple(psi0_.shape), dtype=torch.float64, device=psi0.device) if want_laplacians else None
+        check(lib.mpw_sur_check(self.handle, _p(psi0_), _p(pi0), _p(psi1), _p(pi1), B, n, _p(lap), _p(out)))
+        return out, lap
+
     def predict(self, psi0, pi0, out=None):
         torch = _torch()
         psi0_, B, n = self._dims(psi0)
@@ -223,3 +233,12 @@ def train(sur, source, trajectories, batch=2, lr=2e-3, lr_end=1e-4, first=0, log
         if log_every and k % log_every == 0:
             print(f"step {k} loss {losses[-1]:.4e} lr {rate:.2e}", flush=True)
     return losses
+
+
+def step_hybrid(sim, sur, dt, calls, tol):
+    """mpw_step_surrogate: `calls` surrogate calls of four steps each on the
+    multipatch simulation `sim`; returns (accepted calls, largest residual)."""
+    acc = C.c_int(0)
+    res = C.c_double(0.0)
+    check(lib.mpw_step_surrogate(sim.h, sur.handle, float(dt), int(calls), float(tol), C.byref(acc), C.byref(res)))
+    return acc.value, res.value

@@ -322,7 +322,7 @@ def surrogate_pulses(seed_index, count=8, spread=0.5):
 
 
 # (cin, cout, relu) of the four layers and their stored channel counts
-SURROGATE_LAYERS = [(4, 32, True), (32, 32, True), (32, 32, True), (32, 2, False)]
+SURROGATE_LAYERS = [(7, 32, True), (32, 32, True), (32, 32, True), (32, 2, False)]
 SURROGATE_PADDED = [(8, 32), (32, 32), (32, 32), (32, 8)]
 
 

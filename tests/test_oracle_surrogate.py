@@ -171,20 +171,30 @@ def test_lap4_of_a_fourier_mode_is_its_symbol():
     np.testing.assert_allclose(so.lap4(u, h), lam * u, rtol=0, atol=1e-10 * abs(lam))
 
 
-def test_taylor_step_with_zero_network_is_the_second_order_map():
-    """With N = 0 one call maps a mode (psi, Pi) by [[1 - D^2 l/2, D], [-D l, 1 - D^2 l/2]]
-    (l = -symbol), the second-order Taylor polynomial of the exact evolution."""
+def test_taylor_step_with_zero_network_is_the_fourth_order_map():
+    """With N = 0 one call maps a mode (psi, Pi) by the fourth-order Taylor
+    polynomial of exp(D A), A = [[0, 1], [-l, 0]] (l = -symbol): since A^2 = -l I,
+    T4 = (1 - D^2 l/2 + D^4 l^2/24) I + (D - D^3 l/6) A, i.e. one RK4 step."""
     n = (16, 8, 8)
     h, dt, sigma = 1.0 / 16, 0.01, 1e-3
     k = [2 * np.pi * m / (n[a] * h) for a, m in enumerate((1, 1, 2))]
     u = mode(n, k, h)[None]
     lam = -sum(symbol(k[a] * h, h) for a in range(3))
     D = 4 * dt
+    c0 = 1 - D * D * lam / 2 + D ** 4 * lam * lam / 24
+    c1 = D - D ** 3 * lam / 6
     psi0, pi0 = 0.7 * u, -1.3 * u
     y = np.zeros(u.shape + (2,))
     psi1, pi1 = so.apply(psi0, pi0, np.float32([2.0]), y, dt, h, sigma)
-    np.testing.assert_allclose(psi1, (1 - D * D * lam / 2) * psi0 + D * pi0, atol=1e-12)
-    np.testing.assert_allclose(pi1, -D * lam * psi0 + (1 - D * D * lam / 2) * pi0, atol=1e-10)
+    np.testing.assert_allclose(psi1, c0 * psi0 + c1 * pi0, atol=1e-12)
+    np.testing.assert_allclose(pi1, c0 * pi0 - lam * c1 * psi0, atol=1e-10)
+    # one RK4 step of size D of the same linear system
+    f = lambda p, q: (q, -lam * p)
+    k1 = f(psi0, pi0)
+    k2 = f(psi0 + D / 2 * k1[0], pi0 + D / 2 * k1[1])
+    k3 = f(psi0 + D / 2 * k2[0], pi0 + D / 2 * k2[1])
+    k4 = f(psi0 + D * k3[0], pi0 + D * k3[1])
+    np.testing.assert_allclose(psi1, psi0 + D / 6 * (k1[0] + 2 * k2[0] + 2 * k3[0] + k4[0]), atol=1e-12)
 
 
 def test_targets_recover_the_network_output():
@@ -207,13 +217,13 @@ def test_features_are_scale_invariant():
     x2, s2 = so.features(psi * 2.0 ** 40, pi * 2.0 ** 40, 1e-3, 1.0 / 32)
     np.testing.assert_array_equal(x1, x2)
     assert s1[0] == s2[0] * 2.0 ** 40
-    assert np.abs(x1[..., :2]).max() == 1.0
+    assert np.abs(x1[..., :2]).max() == 1.0 and x1.shape[-1] == 7
 
 
 def test_network_gradient_matches_finite_differences():
     """Unrounded FP64 network: d loss / d params against central differences."""
     r = np.random.default_rng(11)
-    x = r.standard_normal((1, 4, 4, 4, 4))
+    x = r.standard_normal((1, 4, 4, 4, 7))
     t = r.standard_normal((1, 4, 4, 4, 2)) * 0.1
     p = wl.surrogate_init(12).astype(np.float64)
     loss, g = so.net_grads(x, p, t, rounded=False)
@@ -233,7 +243,7 @@ def test_network_gradient_matches_finite_differences():
     assert len(layers) == 4 and so.param_count() == p.size
     # padded entries carry no gradient
     W1 = np.zeros((32, 27, 8), bool)
-    W1[:, :, 4:] = True
+    W1[:, :, 7:] = True
     assert (g[:W1.size][W1.ravel()] == 0).all()
 
 
@@ -241,3 +251,30 @@ def test_initial_parameters_follow_the_layout():
     p = wl.surrogate_init(3)
     assert p.size == so.param_count() and p.dtype == np.float32
     np.testing.assert_array_equal(so.pack_params(so.unpack_params(p)), p)
+
+
+def test_quintic_hermite_reproduces_quintics():
+    """The basis interpolates every polynomial of degree <= 5 exactly from its
+    value and first two derivatives at both ends."""
+    r = np.random.default_rng(13)
+    c = r.standard_normal(6)
+    p = np.polynomial.Polynomial(c)
+    d1, d2 = p.deriv(1), p.deriv(2)
+    for tau in np.linspace(0, 1, 11):
+        w = so.hermite5(tau)
+        val = w @ np.array([p(0), d1(0), d2(0), p(1), d1(1), d2(1)])
+        assert val == pytest.approx(p(tau), abs=1e-13)
+
+
+def test_residual_vanishes_on_a_discrete_standing_wave():
+    """A standing mode of the semi-discrete system, psi = cos(w t) u(x),
+    Pi = -w sin(w t) u(x) with w^2 = -symbol: the quadrature's error is O(D^5)."""
+    n = (16, 16, 16)
+    h = 1.0 / 16
+    k = [2 * np.pi * 2 / (n[a] * h) for a in range(3)]
+    u = mode(n, k, h)[None]
+    w = np.sqrt(-sum(symbol(k[a] * h, h) for a in range(3)))
+    for dt in (0.004, 0.002):
+        D = 4 * dt
+        r, m = so.residual(u, 0 * u, np.cos(w * D) * u, -w * np.sin(w * D) * u, dt, h)
+        assert r[0] / m[0] <= (w * D) ** 5 / 100
