@@ -1809,6 +1809,20 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
     for (int m = 0; m < 4; ++m) {
       if (m > 0 && (st = step_prologue(c, dt))) return st;
       const double tn = c->t;
+      // Global-to-Local reads the global only around each local patch: its
+      // covered box of this step, widened by the interpolation window, the
+      // ghost depth and the motion within a step (clipped to the patch)
+      std::vector<Box> donors;
+      const int margin = c->P / 2 + NG + 2;
+      for (const Box& bx : c->boxes) {
+        if (box_empty(bx)) continue;
+        Box w{};
+        for (int a = 0; a < 3; ++a) {
+          w.lo[a] = std::max(bx.lo[a] - margin, 0);
+          w.hi[a] = std::min(bx.hi[a] + margin, n[a] - 1);
+        }
+        donors.push_back(w);
+      }
       for (int l = 0; l < 4; ++l) {
         const double tl = tn + RK_C[l] * dt;
         // the global stage buffer holds the stage input the method would
@@ -1816,7 +1830,8 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
         // RHS + stage update
         int* slot2 = c->d_expo + FILL_BUF[l] * 2;
         CUDA_TRY(cudaMemsetAsync(slot2, 0, 2 * sizeof(int), c->stream));
-        launch_hermite(G.buf(FILL_BUF[l]), G.g, U, coef + (4 * m + l) * 6, slot2, c->stream);
+        launch_hermite(G.buf(FILL_BUF[l]), G.g, U, coef + (4 * m + l) * 6, slot2, donors.data(), (int)donors.size(),
+                       c->stream);
         CUDA_TRY(cudaGetLastError());
         if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l]))) return st;
         if ((st = run_rhs(c, l, tl, dt, true))) return st;

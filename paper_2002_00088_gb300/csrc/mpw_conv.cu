@@ -178,6 +178,129 @@ __global__ void __launch_bounds__(FWD_THREADS) k_conv3(const FwdArgs A) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// 32 input channels: two output planes per warp (M = 2 x 16 points), operands
+// loaded with ldmatrix, the 27 taps unrolled with compile-time offsets.  A
+// block is 16 x 8 x 2 points; its periodic halo is 18 x 10 x 4.
+
+constexpr int HZ2 = 4;
+constexpr int HPTS2 = HX * HY * HZ2;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r1) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
+}
+
+template <int COUT>
+__global__ void __launch_bounds__(FWD_THREADS, 2) k_conv3_c32(const FwdArgs A) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  constexpr int CIN = 32, XS = xstride<32>(), KP = kdim<32>(), WS = wstride<32>(), NT = COUT / 8;
+  __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem);
+  __nv_bfloat16* Xs = Ws + COUT * WS;
+  for (int i = threadIdx.x; i < COUT * KP; i += blockDim.x) {
+    const int n = i / KP, k = i - n * KP;
+    const int tap = k / CIN, c = k - tap * CIN;
+    Ws[n * WS + k] = A.flip ? A.w[((long long)c * 27 + 26 - tap) * COUT + n] : A.w[((long long)n * 27 + tap) * CIN + c];
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  // ldmatrix rows: A matrices (points 0-7 | 8-15) x (k 0-7 | 8-15); B matrices
+  // (n-tile, k 0-7 | 8-15)
+  const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, akof = (lane >> 4) * 8;
+  const int bq = lane >> 3, br = lane & 7;
+  const uint32_t xs0 = smem_u32(Xs), ws0 = smem_u32(Ws);
+  uint32_t a_addr[2], b_addr[NT > 1 ? 2 : 1];
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt) a_addr[mt] = xs0 + (((mt * HY + warp) * HX + arow) * XS + akof) * 2;
+  if constexpr (NT > 1) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) b_addr[jj] = ws0 + ((8 * (2 * jj + (bq >> 1)) + br) * WS + 8 * (bq & 1)) * 2;
+  } else {
+    b_addr[0] = ws0 + (br * WS + 8 * (bq & 1)) * 2;
+  }
+  const int bx = A.v.n0 / BX, by = A.v.n1 / BY, bz = (A.v.n2 + 1) / 2;
+  for (long long blk = blockIdx.x; blk < A.nblocks; blk += gridDim.x) {
+    long long r = blk;
+    const int x0 = (int)(r % bx) * BX;
+    r /= bx;
+    const int y0 = (int)(r % by) * BY;
+    r /= by;
+    const int z = (int)(r % bz) * 2;
+    const int b = (int)(r / bz);
+    __syncthreads();
+    constexpr int CH = CIN / 8;
+    for (int i = threadIdx.x; i < HPTS2 * CH; i += blockDim.x) {
+      const int hp = i / CH, ch = i - hp * CH;
+      const int hx = hp % HX, hy = (hp / HX) % HY, hz = hp / (HX * HY);
+      const long long p = point_index(A.v, b, wrap1(z + hz - 1, A.v.n2), wrap1(y0 + hy - 1, A.v.n1),
+                                      wrap1(x0 + hx - 1, A.v.n0));
+      *reinterpret_cast<int4*>(Xs + hp * XS + ch * 8) = *reinterpret_cast<const int4*>(A.x + p * CIN + ch * 8);
+    }
+    __syncthreads();
+    float acc[2][NT][4];
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+      for (int j = 0; j < NT; ++j) acc[mt][j][0] = acc[mt][j][1] = acc[mt][j][2] = acc[mt][j][3] = 0.0f;
+#pragma unroll
+    for (int tap = 0; tap < 27; ++tap) {
+      const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+      const uint32_t toff = (uint32_t)(((dz * HY + dy) * HX + dx) * XS * 2);
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        uint32_t a[2][4], bb[NT][2];
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt) ldsm_x4(a_addr[mt] + toff + c * 32, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+        const uint32_t koff = (uint32_t)((tap * CIN + c * 16) * 2);
+        if constexpr (NT > 1) {
+#pragma unroll
+          for (int jj = 0; jj < NT / 2; ++jj)
+            ldsm_x4(b_addr[jj] + koff, bb[2 * jj][0], bb[2 * jj][1], bb[2 * jj + 1][0], bb[2 * jj + 1][1]);
+        } else {
+          ldsm_x2(b_addr[0] + koff, bb[0][0], bb[0][1]);
+        }
+#pragma unroll
+        for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+          for (int j = 0; j < NT; ++j) mma_bf16(acc[mt][j], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bb[j][0], bb[j][1]);
+      }
+    }
+    const int y = y0 + warp;
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      const int zz = z + mt;
+      if (zz >= A.v.n2) break;
+#pragma unroll
+      for (int j = 0; j < NT; ++j) {
+        const int co = 8 * j + 2 * t;
+        const float bias0 = A.bias ? A.bias[co] : 0.0f, bias1 = A.bias ? A.bias[co + 1] : 0.0f;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const long long p = point_index(A.v, b, zz, y, x0 + g + 8 * h);
+          float v0 = acc[mt][j][2 * h] + bias0, v1 = acc[mt][j][2 * h + 1] + bias1;
+          if (A.relu) {
+            v0 = fmaxf(v0, 0.0f);
+            v1 = fmaxf(v1, 0.0f);
+          }
+          if (A.mask) {
+            const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(A.mask + p * COUT + co);
+            if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
+            if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
+          }
+          if (A.y32) *reinterpret_cast<float2*>(A.y32 + p * COUT + co) = make_float2(v0, v1);
+          if (A.y) *reinterpret_cast<__nv_bfloat162*>(A.y + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
+        }
+      }
+    }
+  }
+}
+
 struct WgArgs {
   const __nv_bfloat16* x;  // layer input [..][CIN]
   const __nv_bfloat16* g;  // gradient at the layer output [..][COUT]
@@ -357,10 +480,22 @@ cudaError_t launch_conv(const FwdArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// 32 input channels: blocks of two planes
+template <int COUT>
+cudaError_t launch_conv_c32(FwdArgs a, cudaStream_t s) {
+  const int smem = (COUT * wstride<32>() + HPTS2 * xstride<32>()) * 2;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_c32<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  a.nblocks = (long long)a.v.batch * ((a.v.n2 + 1) / 2) * (a.v.n1 / BY) * (a.v.n0 / BX);
+  const long long grid = a.nblocks < 2LL * sm_count() ? a.nblocks : 2LL * sm_count();
+  k_conv3_c32<COUT><<<(unsigned)grid, FWD_THREADS, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
 cudaError_t dispatch_conv(int cin, int cout, const FwdArgs& a, cudaStream_t s) {
   if (cin == 8) return launch_conv<8, 32>(a, s);
-  if (cout == 8) return launch_conv<32, 8>(a, s);
-  return launch_conv<32, 32>(a, s);
+  if (cout == 8) return launch_conv_c32<8>(a, s);
+  return launch_conv_c32<32>(a, s);
 }
 
 long long wgrad_grid(long long nblocks) { return nblocks < 2LL * sm_count() ? nblocks : 2LL * sm_count(); }

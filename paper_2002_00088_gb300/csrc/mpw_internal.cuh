@@ -193,10 +193,12 @@ constexpr int DIST_CAP = 9;          // distances above buffer + NG (<= 8) read 
 void set_last_error(const char* msg);
 
 // learned surrogate: the quintic Hermite interpolant in time of the global
-// state between two calls, written into a padded buffer (u: psi0, Pi0, psi1,
-// Pi1, L psi0, L Pi0, L psi1, L Pi1, dense; coef_dev: six device doubles),
-// and the step and spacing a surrogate was made for
-void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, void* stream);
+// state between two calls, written into the cells of `boxes` of a padded
+// buffer (u: psi0, Pi0, psi1, Pi1, L psi0, L Pi0, L psi1, L Pi1, dense;
+// coef_dev: six device doubles), and the step and spacing a surrogate was
+// made for
+void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, const Box* boxes,
+                    int nbox, void* stream);
 bool sur_geometry(const mpw_sur* s, double* dt, double* h, void** stream);
 
 // ---------------------------------------------------------------- tensor maps

@@ -10,6 +10,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -77,23 +78,28 @@ struct Dims {
 
 // ---------------------------------------------------------------- kernels
 
-__device__ __forceinline__ int wrapi(int i, int n) { return i < 0 ? i + n : (i >= n ? i - n : i); }
-
 // 12 h^2 L u along one axis: (16 (u[-1] + u[1]) - (u[-2] + u[2])) - 30 u
 __device__ __forceinline__ double axis_sum(double um2, double um1, double u0, double up1, double up2) {
   return __dsub_rn(__dsub_rn(__dmul_rn(16.0, __dadd_rn(um1, up1)), __dadd_rn(um2, up2)), __dmul_rn(30.0, u0));
 }
 
-// L u at (i, j, k) of sample volume u (periodic): ((Sx + Sy) + Sz) / (12 h^2)
-__device__ double lap4(const double* u, const Dims& d, int i, int j, int k, double inv12h2) {
-  const long long row = ((long long)k * d.n1 + j) * d.n0;
-  const double c = u[row + i];
-  const double sx = axis_sum(u[row + wrapi(i - 2, d.n0)], u[row + wrapi(i - 1, d.n0)], c, u[row + wrapi(i + 1, d.n0)],
-                             u[row + wrapi(i + 2, d.n0)]);
-  auto Y = [&](int jj) { return u[((long long)k * d.n1 + wrapi(jj, d.n1)) * d.n0 + i]; };
-  auto Z = [&](int kk) { return u[((long long)wrapi(kk, d.n2) * d.n1 + j) * d.n0 + i]; };
-  const double sy = axis_sum(Y(j - 2), Y(j - 1), c, Y(j + 1), Y(j + 2));
-  const double sz = axis_sum(Z(k - 2), Z(k - 1), c, Z(k + 1), Z(k + 2));
+// L u at (i, j, k) of sample volume u (periodic): ((Sx + Sy) + Sz) / (12 h^2).
+// Offsets within a sample fit in 32 bits (n0 n1 n2 < 2^31).
+__device__ __forceinline__ double lap4(const double* __restrict__ u, const Dims& d, int i, int j, int k,
+                                       double inv12h2) {
+  const int n0 = d.n0, pl = d.n0 * d.n1;
+  const int c0 = (k * d.n1 + j) * n0 + i;
+  const double c = __ldg(u + c0);
+  const int xm1 = i >= 1 ? -1 : n0 - 1, xm2 = i >= 2 ? -2 : n0 - 2;
+  const int xp1 = i + 1 < n0 ? 1 : 1 - n0, xp2 = i + 2 < n0 ? 2 : 2 - n0;
+  const int ym1 = (j >= 1 ? -1 : d.n1 - 1) * n0, ym2 = (j >= 2 ? -2 : d.n1 - 2) * n0;
+  const int yp1 = (j + 1 < d.n1 ? 1 : 1 - d.n1) * n0, yp2 = (j + 2 < d.n1 ? 2 : 2 - d.n1) * n0;
+  const int zm1 = (k >= 1 ? -1 : d.n2 - 1) * pl, zm2 = (k >= 2 ? -2 : d.n2 - 2) * pl;
+  const int zp1 = (k + 1 < d.n2 ? 1 : 1 - d.n2) * pl, zp2 = (k + 2 < d.n2 ? 2 : 2 - d.n2) * pl;
+  const double* q = u + c0;
+  const double sx = axis_sum(__ldg(q + xm2), __ldg(q + xm1), c, __ldg(q + xp1), __ldg(q + xp2));
+  const double sy = axis_sum(__ldg(q + ym2), __ldg(q + ym1), c, __ldg(q + yp1), __ldg(q + yp2));
+  const double sz = axis_sum(__ldg(q + zm2), __ldg(q + zm1), c, __ldg(q + zp1), __ldg(q + zp2));
   return __dmul_rn(__dadd_rn(__dadd_rn(sx, sy), sz), inv12h2);
 }
 
@@ -212,29 +218,18 @@ unsigned grid_for(long long n, int threads = 256) {
 // Residual of a call against the method's RHS: with f = Pi, f' = L psi for
 // psi and f = L psi, f' = L Pi for Pi, the two-point quadrature with end
 // corrections, int_0^Delta f = Delta/2 (f0 + f1) + Delta^2/12 (f0' - f1'),
-// leaves O(Delta^5) for the exact evolution.  Writes the four Laplacians
-// (optional) and, per sample, max(|R_psi|, Delta |R_Pi|) and max(|psi0|,
+// leaves O(Delta^5) for the exact evolution.  lap: L psi0, L Pi0, L psi1,
+// L Pi1.  Writes, per sample, max(|R_psi|, Delta |R_Pi|) and max(|psi0|,
 // Delta |Pi0|) as binary32 bit patterns (atomic maximum).
 __global__ void k_check(const double* psi0, const double* pi0, const double* psi1, const double* pi1, Dims d, Coef c,
-                        double* lap, unsigned* out) {
+                        const double* lap, unsigned* out) {
   const long long P = d.points(), N = P * d.batch;
   const double hd = 0.5 * c.delta, d12 = c.d2 / 12.0;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += (long long)gridDim.x * blockDim.x) {
     const long long g = base + threadIdx.x;
     unsigned r = 0, m = 0;
     if (g < N) {
-      const int b = (int)(g / P);
-      int i, j, k;
-      point_ijk(g - (long long)b * P, d, i, j, k);
-      const long long o = (long long)b * P;
-      const double lp0 = lap4(psi0 + o, d, i, j, k, c.inv12h2), lq0 = lap4(pi0 + o, d, i, j, k, c.inv12h2);
-      const double lp1 = lap4(psi1 + o, d, i, j, k, c.inv12h2), lq1 = lap4(pi1 + o, d, i, j, k, c.inv12h2);
-      if (lap) {
-        lap[g] = lp0;
-        lap[N + g] = lq0;
-        lap[2 * N + g] = lp1;
-        lap[3 * N + g] = lq1;
-      }
+      const double lp0 = lap[g], lq0 = lap[N + g], lp1 = lap[2 * N + g], lq1 = lap[3 * N + g];
       const double rp = (psi1[g] - psi0[g]) - hd * (pi0[g] + pi1[g]) + d12 * (lp1 - lp0);
       const double rq = (pi1[g] - pi0[g]) - hd * (lp0 + lp1) + d12 * (lq1 - lq0);
       r = __float_as_uint(__double2float_ru(fmax(fabs(rp), c.delta * fabs(rq))));
@@ -250,19 +245,29 @@ __global__ void k_check(const double* psi0, const double* pi0, const double* psi
   }
 }
 
+struct HermiteBoxes {
+  int nb;
+  mpw::Box b[mpw::MAX_PATCHES];
+};
+
 // Quintic Hermite interpolant in time of the state between two calls, written
-// into the interior of a padded patch buffer: y(tau) = c0 y0 + c1 y0' + c2 y0''
+// into the cells of the given boxes of a padded patch buffer: y(tau) = c0 y0 + c1 y0' + c2 y0''
 // + c3 y1 + c4 y1' + c5 y1'' (coefficients: the basis at tau times Delta^k),
 // with y = psi, y' = Pi, y'' = L psi for psi and y = Pi, y' = L psi, y'' = L Pi
 // for Pi.  slot2 receives the largest biased exponent of each field.
-__global__ void k_hermite(double* buf, mpw::Geom g, const double* u, long long P, const double* cf, int* slot2) {
+__global__ void k_hermite(double* buf, mpw::Geom g, const double* u, long long P, const double* cf, int* slot2,
+                          HermiteBoxes hb) {
   const double *psi0 = u, *pi0 = u + P, *psi1 = u + 2 * P, *pi1 = u + 3 * P;
   const double *lp0 = u + 4 * P, *lq0 = u + 5 * P, *lp1 = u + 6 * P, *lq1 = u + 7 * P;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < P; base += (long long)gridDim.x * blockDim.x) {
-    const long long q = base + threadIdx.x;
+  const mpw::Box& bx = hb.b[blockIdx.y];
+  const int w0 = bx.hi[0] - bx.lo[0] + 1, w1 = bx.hi[1] - bx.lo[1] + 1, w2 = bx.hi[2] - bx.lo[2] + 1;
+  const long long V = (long long)w0 * w1 * w2;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < V; base += (long long)gridDim.x * blockDim.x) {
+    const long long e = base + threadIdx.x;
     int e0 = 0, e1 = 0;
-    if (q < P) {
-      const int i = (int)(q % g.n[0]), j = (int)((q / g.n[0]) % g.n[1]), k = (int)(q / ((long long)g.n[0] * g.n[1]));
+    if (e < V) {
+      const int i = bx.lo[0] + (int)(e % w0), j = bx.lo[1] + (int)((e / w0) % w1), k = bx.lo[2] + (int)(e / ((long long)w0 * w1));
+      const long long q = ((long long)k * g.n[1] + j) * g.n[0] + i;
       const double ys = cf[0] * psi0[q] + cf[1] * pi0[q] + cf[2] * lp0[q] + cf[3] * psi1[q] + cf[4] * pi1[q] + cf[5] * lp1[q];
       const double yp = cf[0] * pi0[q] + cf[1] * lp0[q] + cf[2] * lq0[q] + cf[3] * pi1[q] + cf[4] * lp1[q] + cf[5] * lq1[q];
       const long long a = g.at(i, j, k);
@@ -590,9 +595,15 @@ mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, cons
   Dims d;
   MPW_TRY(dims_of(batch, n, d));
   if (!psi0 || !pi0 || !psi1 || !pi1 || !out) return fail(MPW_ERR_ARG, "surrogate: null tensor");
+  const long long N = d.points() * batch;
+  if (!lap) {
+    MPW_TRY(ensure_infer(s, N, batch));
+    lap = s->lap;
+  }
   SUR_TRY(cudaMemsetAsync(out, 0, (size_t)batch * 2 * sizeof(float), s->stream));
-  k_check<<<grid_for(d.points() * batch), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, lap,
-                                                                reinterpret_cast<unsigned*>(out));
+  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef.inv12h2, lap);
+  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(psi1, pi1, d, s->coef.inv12h2, lap + 2 * N);
+  k_check<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, lap, reinterpret_cast<unsigned*>(out));
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
@@ -601,9 +612,22 @@ mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, cons
 
 namespace mpw {
 
-void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, void* stream) {
+void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, const Box* boxes,
+                    int nbox, void* stream) {
+  if (nbox <= 0) return;
+  HermiteBoxes hb{};
+  hb.nb = nbox;
+  long long vmax = 0;
+  for (int q = 0; q < nbox; ++q) {
+    hb.b[q] = boxes[q];
+    long long v = 1;
+    for (int a = 0; a < 3; ++a) v *= std::max(boxes[q].hi[a] - boxes[q].lo[a] + 1, 0);
+    vmax = std::max(vmax, v);
+  }
+  if (vmax == 0) return;
   const long long P = (long long)g.n[0] * g.n[1] * g.n[2];
-  k_hermite<<<grid_for(P), 256, 0, (cudaStream_t)stream>>>(buf, g, u, P, coef_dev, slot2);
+  const dim3 grid(grid_for(vmax), (unsigned)nbox);
+  k_hermite<<<grid, 256, 0, (cudaStream_t)stream>>>(buf, g, u, P, coef_dev, slot2, hb);
 }
 
 bool sur_geometry(const mpw_sur* s, double* dt, double* h, void** stream) {
