@@ -672,7 +672,11 @@ def run_surrogate(args):
         "roofline": {"bound": "tensor", "kernel": "k_conv3 (network forward, mma.sync BF16/FP32)",
                      "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "avg_launch_ms": fwd_ms / 4},
-        "gpu_launches": calls * (6 + 4 + 2 + 16 * 3 + 8),
+        # per accepted call: features 6 (maximum, scale, three Laplacian passes,
+        # features), network 4, update 1, check 3, then per substage Hermite,
+        # fill and RHS (48), cover flags and revival per step (8), the global
+        # unpack (1); the first call adds a fill, the dead-cell fill and a pack
+        "gpu_launches": calls * (6 + 4 + 1 + 3 + 48 + 8 + 1) + 3,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:

@@ -807,7 +807,11 @@ mpw_status prep_mirrors(mpw_ctx* c, int b, double t, MirrorArgs& m, int mir_glob
   return MPW_OK;
 }
 
-mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, MirrorArgs* mirrors = nullptr) {
+// g2l_only: Global-to-Local segments only (the hybrid substages of
+// mpw_step_surrogate, where nothing reads the global's outer ghosts or its
+// Local-to-Global ring).
+mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, MirrorArgs* mirrors = nullptr,
+                     bool g2l_only = false) {
   const PatchState& g = c->p[0];
   a = FillArgs{};
   int mir_global[MAX_PATCHES], mir_shell[MAX_PATCHES];
@@ -826,7 +830,7 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
   a.ascreen = c->screen_ok ? c->d_ascreen : nullptr;
   a.apre = c->screen_ok ? c->d_apre : nullptr;
   a.shell_src = nullptr;
-  if (a.outer_bc == 0) {
+  if (a.outer_bc == 0 && !g2l_only) {
     for (int k = 0; k < 4; ++k)
       if (k != b && c->shell_time[k] == t) a.shell_src = g.buf(k);
     c->shell_time[b] = t;
@@ -834,12 +838,13 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
   a.t = t;
   a.outer_count = (long long)(g.d.n[0] + 2 * NG) * (g.d.n[1] + 2 * NG) * (g.d.n[2] + 2 * NG) -
                   (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
+  if (g2l_only) a.outer_count = 0;
   a.outer_blocks = (int)((a.outer_count + fill_threads() - 1) / fill_threads());
   int blocks = a.outer_blocks;
   a.nseg = 0;
   const int nloc = (int)c->p.size() - 1;
   // Local-to-Global: the effective-ghost shell of each covered box
-  for (int q = 0; q < nloc; ++q) {
+  for (int q = 0; q < (g2l_only ? 0 : nloc); ++q) {
     const Box& bx = c->boxes[q];
     if (box_empty(bx)) continue;
     int O0[3], O[3];
@@ -947,10 +952,10 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
   return MPW_OK;
 }
 
-mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf) {
+mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf, bool g2l_only = false) {
   FillArgs a;
   MirrorArgs m;
-  if (mpw_status st = prep_fill(c, b, t, reset_buf, a, &m)) return st;
+  if (mpw_status st = prep_fill(c, b, t, reset_buf, a, &m, g2l_only)) return st;
   c->launch_begin(MPW_KERNEL_FILL);
   if (m.nr > 0) {
     launch_mirror(m, c->stream);
@@ -1833,7 +1838,7 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
         launch_hermite(G.buf(FILL_BUF[l]), G.g, U, coef + (4 * m + l) * 6, slot2, donors.data(), (int)donors.size(),
                        c->stream);
         CUDA_TRY(cudaGetLastError());
-        if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l]))) return st;
+        if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], true))) return st;
         if ((st = run_rhs(c, l, tl, dt, true))) return st;
       }
       c->t = tn + dt;
