@@ -4,7 +4,9 @@ TEST INFRASTRUCTURE ONLY.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
 CPU-baseline leg of ``bench.py`` may import this package.  It shares no code
 with the CUDA library in ``paper_2002_00088_gb300`` and neither side imports
 the other.  ``pyoracle`` wraps the C oracle (``oracle.c``) with ctypes;
-``build_oracle()`` compiles it with the system C compiler.
+``build_oracle()`` compiles it with the system C compiler.  ``surrogate`` is
+the numpy oracle of the learned surrogate (its layers, gradients, optimizer,
+features, targets, update and residual check).
 """
 import os
 import shutil

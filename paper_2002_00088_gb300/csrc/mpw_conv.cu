@@ -2,14 +2,17 @@
 // include/mpw_surrogate.h): periodic 3x3x3 convolution, its input and weight
 // gradients, Adam and the squared-error gradient.
 //
-// Implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32 accumulation).
-// Forward and input gradient: M = points (a warp owns 16 consecutive x
-// points), N = output channels, K = 27 taps x input channels; a CTA stages
-// the periodic halo of a 16 x 8 x 1 point block and the layer's weights in
-// shared memory and loops over blocks.  Weight gradient: M = output channels,
-// N = input channels, K = points; each CTA keeps its partial sums in
-// registers over its blocks and a second kernel adds the partials in a fixed
-// order (deterministic).
+// Implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32 accumulation):
+//  - k_conv3_t<CIN, COUT>: M = points (a warp owns 16 x-points on two
+//    planes), N = output channels, K = 27 taps x CIN.  A persistent CTA
+//    stages the layer's weights once and the periodic 18 x 10 x 4 halo of
+//    each 16 x 8 x 2 block; both operands come from shared memory through
+//    ldmatrix and the K loop is unrolled.
+//  - The input gradient is the forward kernel reading the weights mirrored
+//    and transposed.
+//  - k_conv3_wgrad: M = output channels, N = input channels, K = points; each
+//    CTA keeps its partial sums in registers over its blocks and k_sum_parts
+//    adds the partials in a fixed order (deterministic).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -100,88 +103,14 @@ struct FwdArgs {
   int flip;  // 1: w is the layer W[CIN][27][COUT] and this launch is its input gradient
 };
 
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(FWD_THREADS) k_conv3(const FwdArgs A) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int XS = xstride<CIN>(), KP = kdim<CIN>(), WS = wstride<CIN>(), NT = COUT / 8;
-  __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem);
-  __nv_bfloat16* Xs = Ws + COUT * WS;
-  // B operand, once per CTA: Ws[n][k], k = tap * CIN + c.  The input
-  // gradient correlates with the mirrored taps of the transposed weights.
-  for (int i = threadIdx.x; i < COUT * KP; i += blockDim.x) {
-    const int n = i / KP, k = i - n * KP;
-    __nv_bfloat16 val = __float2bfloat16(0.0f);
-    if (k < 27 * CIN) {
-      const int tap = k / CIN, c = k - tap * CIN;
-      val = A.flip ? A.w[((long long)c * 27 + 26 - tap) * COUT + n] : A.w[((long long)n * 27 + tap) * CIN + c];
-    }
-    Ws[n * WS + k] = val;
-  }
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const uint32_t* X32 = reinterpret_cast<const uint32_t*>(Xs);
-  const uint32_t* W32 = reinterpret_cast<const uint32_t*>(Ws);
-  for (long long blk = blockIdx.x; blk < A.nblocks; blk += gridDim.x) {
-    int b, z, y0, x0;
-    block_origin(blk, A.v, b, z, y0, x0);
-    __syncthreads();  // the previous block's fragments are read (and Ws is staged)
-    stage_halo<CIN>(Xs, A.x, A.v, b, z, y0, x0);
-    __syncthreads();
-    float acc[NT][4];
-#pragma unroll
-    for (int j = 0; j < NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.0f;
-#pragma unroll 2
-    for (int s = 0; s < KP / 16; ++s) {
-      // A fragment: rows g and g + 8 (x points), columns 16 s + 2 t (+ 8)
-      uint32_t a[4];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int k = 16 * s + 2 * t + 8 * h;
-        if (k < 27 * CIN) {
-          const int tap = k / CIN, c = k - tap * CIN;
-          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-          const int hp = (dz * HY + warp + dy) * HX + g + dx;
-          a[2 * h] = X32[(hp * XS + c) >> 1];
-          a[2 * h + 1] = X32[((hp + 8) * XS + c) >> 1];
-        } else {
-          a[2 * h] = a[2 * h + 1] = 0u;
-        }
-      }
-#pragma unroll
-      for (int j = 0; j < NT; ++j) {
-        const int row = (8 * j + g) * WS + 16 * s + 2 * t;
-        mma_bf16(acc[j], a[0], a[1], a[2], a[3], W32[row >> 1], W32[(row + 8) >> 1]);
-      }
-    }
-    // epilogue: rows g, g + 8; channels 8 j + 2 t, + 1
-    const int y = y0 + warp;
-#pragma unroll
-    for (int j = 0; j < NT; ++j) {
-      const int co = 8 * j + 2 * t;
-      const float bias0 = A.bias ? A.bias[co] : 0.0f, bias1 = A.bias ? A.bias[co + 1] : 0.0f;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const long long p = point_index(A.v, b, z, y, x0 + g + 8 * h);
-        float v0 = acc[j][2 * h] + bias0, v1 = acc[j][2 * h + 1] + bias1;
-        if (A.relu) {
-          v0 = fmaxf(v0, 0.0f);
-          v1 = fmaxf(v1, 0.0f);
-        }
-        if (A.mask) {
-          const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(A.mask + p * COUT + co);
-          if (!(__bfloat162float(m.x) > 0.0f)) v0 = 0.0f;
-          if (!(__bfloat162float(m.y) > 0.0f)) v1 = 0.0f;
-        }
-        if (A.y32) *reinterpret_cast<float2*>(A.y32 + p * COUT + co) = make_float2(v0, v1);
-        if (A.y) *reinterpret_cast<__nv_bfloat162*>(A.y + p * COUT + co) = __floats2bfloat162_rn(v0, v1);
-      }
-    }
-  }
-}
-
 // ---------------------------------------------------------------------------
-// 32 input channels: two output planes per warp (M = 2 x 16 points), operands
-// loaded with ldmatrix, the 27 taps unrolled with compile-time offsets.  A
-// block is 16 x 8 x 2 points; its periodic halo is 18 x 10 x 4.
+// Two output planes per warp (M = 2 x 16 points), operands loaded with
+// ldmatrix, the K loop unrolled with compile-time offsets.  A block is
+// 16 x 8 x 2 points; its periodic halo is 18 x 10 x 4.  With 32 input
+// channels a 16-deep K step is half of one tap; with 8, it is two taps, and
+// the lanes that address the upper half of the A fragment read the second
+// tap (the padding tap past the 27th reads tap 27's neighbour, whose weights
+// are zero).
 
 constexpr int HZ2 = 4;
 constexpr int HPTS2 = HX * HY * HZ2;
@@ -198,21 +127,26 @@ __device__ __forceinline__ void ldsm_x2(uint32_t addr, uint32_t& r0, uint32_t& r
   asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n" : "=r"(r0), "=r"(r1) : "r"(addr));
 }
 
-template <int COUT>
-__global__ void __launch_bounds__(FWD_THREADS, 2) k_conv3_c32(const FwdArgs A) {
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(FWD_THREADS, 2) k_conv3_t(const FwdArgs A) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int CIN = 32, XS = xstride<32>(), KP = kdim<32>(), WS = wstride<32>(), NT = COUT / 8;
+  constexpr int XS = xstride<CIN>(), KP = kdim<CIN>(), WS = wstride<CIN>(), NT = COUT / 8, KSTEPS = KP / 16;
   __nv_bfloat16* Ws = reinterpret_cast<__nv_bfloat16*>(smem);
   __nv_bfloat16* Xs = Ws + COUT * WS;
   for (int i = threadIdx.x; i < COUT * KP; i += blockDim.x) {
     const int n = i / KP, k = i - n * KP;
-    const int tap = k / CIN, c = k - tap * CIN;
-    Ws[n * WS + k] = A.flip ? A.w[((long long)c * 27 + 26 - tap) * COUT + n] : A.w[((long long)n * 27 + tap) * CIN + c];
+    __nv_bfloat16 val = __float2bfloat16(0.0f);
+    if (k < 27 * CIN) {
+      const int tap = k / CIN, c = k - tap * CIN;
+      val = A.flip ? A.w[((long long)c * 27 + 26 - tap) * COUT + n] : A.w[((long long)n * 27 + tap) * CIN + c];
+    }
+    Ws[n * WS + k] = val;
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
   // ldmatrix rows: A matrices (points 0-7 | 8-15) x (k 0-7 | 8-15); B matrices
   // (n-tile, k 0-7 | 8-15)
-  const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, akof = (lane >> 4) * 8;
+  const int arow = (lane & 7) + ((lane >> 3) & 1) * 8, khi = lane >> 4;
+  const int akof = CIN == 32 ? khi * 8 : 0;
   const int bq = lane >> 3, br = lane & 7;
   const uint32_t xs0 = smem_u32(Xs), ws0 = smem_u32(Ws);
   uint32_t a_addr[2], b_addr[NT > 1 ? 2 : 1];
@@ -249,27 +183,33 @@ __global__ void __launch_bounds__(FWD_THREADS, 2) k_conv3_c32(const FwdArgs A) {
 #pragma unroll
       for (int j = 0; j < NT; ++j) acc[mt][j][0] = acc[mt][j][1] = acc[mt][j][2] = acc[mt][j][3] = 0.0f;
 #pragma unroll
-    for (int tap = 0; tap < 27; ++tap) {
-      const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-      const uint32_t toff = (uint32_t)(((dz * HY + dy) * HX + dx) * XS * 2);
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        uint32_t a[2][4], bb[NT][2];
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt) ldsm_x4(a_addr[mt] + toff + c * 32, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
-        const uint32_t koff = (uint32_t)((tap * CIN + c * 16) * 2);
-        if constexpr (NT > 1) {
-#pragma unroll
-          for (int jj = 0; jj < NT / 2; ++jj)
-            ldsm_x4(b_addr[jj] + koff, bb[2 * jj][0], bb[2 * jj][1], bb[2 * jj + 1][0], bb[2 * jj + 1][1]);
-        } else {
-          ldsm_x2(b_addr[0] + koff, bb[0][0], bb[0][1]);
-        }
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-          for (int j = 0; j < NT; ++j) mma_bf16(acc[mt][j], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bb[j][0], bb[j][1]);
+    for (int s = 0; s < KSTEPS; ++s) {
+      // byte offset of this lane's A row for K step s
+      uint32_t aoff;
+      if constexpr (CIN == 32) {
+        const int tap = s / 2, dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        aoff = (uint32_t)((((dz * HY + dy) * HX + dx) * XS + (s % 2) * 16) * 2);
+      } else {
+        const int t0 = 2 * s, t1 = 2 * s + 1 < 27 ? 2 * s + 1 : 26;
+        const uint32_t o0 = (uint32_t)((((t0 / 9) * HY + (t0 / 3) % 3) * HX + t0 % 3) * XS * 2);
+        const uint32_t o1 = (uint32_t)((((t1 / 9) * HY + (t1 / 3) % 3) * HX + t1 % 3) * XS * 2);
+        aoff = khi ? o1 : o0;
       }
+      uint32_t a[2][4], bb[NT][2];
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt) ldsm_x4(a_addr[mt] + aoff, a[mt][0], a[mt][1], a[mt][2], a[mt][3]);
+      const uint32_t koff = (uint32_t)(s * 16 * 2);
+      if constexpr (NT > 1) {
+#pragma unroll
+        for (int jj = 0; jj < NT / 2; ++jj)
+          ldsm_x4(b_addr[jj] + koff, bb[2 * jj][0], bb[2 * jj][1], bb[2 * jj + 1][0], bb[2 * jj + 1][1]);
+      } else {
+        ldsm_x2(b_addr[0] + koff, bb[0][0], bb[0][1]);
+      }
+#pragma unroll
+      for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+        for (int j = 0; j < NT; ++j) mma_bf16(acc[mt][j], a[mt][0], a[mt][1], a[mt][2], a[mt][3], bb[j][0], bb[j][1]);
     }
     const int y = y0 + warp;
 #pragma unroll
@@ -471,31 +411,20 @@ mpw_status check_volume(int batch, const int n[3], Vol& v, long long& nblocks) {
 }
 
 template <int CIN, int COUT>
-cudaError_t launch_conv(const FwdArgs& a, cudaStream_t s) {
-  const int smem = (COUT * wstride<CIN>() + HPTS * xstride<CIN>()) * 2;
-  cudaError_t e = cudaFuncSetAttribute(k_conv3<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  const long long grid = a.nblocks < 2LL * sm_count() ? a.nblocks : 2LL * sm_count();
-  k_conv3<CIN, COUT><<<(unsigned)grid, FWD_THREADS, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-// 32 input channels: blocks of two planes
-template <int COUT>
-cudaError_t launch_conv_c32(FwdArgs a, cudaStream_t s) {
-  const int smem = (COUT * wstride<32>() + HPTS2 * xstride<32>()) * 2;
-  cudaError_t e = cudaFuncSetAttribute(k_conv3_c32<COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+cudaError_t launch_conv(FwdArgs a, cudaStream_t s) {
+  const int smem = (COUT * wstride<CIN>() + HPTS2 * xstride<CIN>()) * 2;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_t<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   a.nblocks = (long long)a.v.batch * ((a.v.n2 + 1) / 2) * (a.v.n1 / BY) * (a.v.n0 / BX);
   const long long grid = a.nblocks < 2LL * sm_count() ? a.nblocks : 2LL * sm_count();
-  k_conv3_c32<COUT><<<(unsigned)grid, FWD_THREADS, smem, s>>>(a);
+  k_conv3_t<CIN, COUT><<<(unsigned)grid, FWD_THREADS, smem, s>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t dispatch_conv(int cin, int cout, const FwdArgs& a, cudaStream_t s) {
   if (cin == 8) return launch_conv<8, 32>(a, s);
-  if (cout == 8) return launch_conv_c32<8>(a, s);
-  return launch_conv_c32<32>(a, s);
+  if (cout == 8) return launch_conv<32, 8>(a, s);
+  return launch_conv<32, 32>(a, s);
 }
 
 long long wgrad_grid(long long nblocks) { return nblocks < 2LL * sm_count() ? nblocks : 2LL * sm_count(); }
