@@ -181,6 +181,13 @@ mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, cons
 mpw_status mpw_step_surrogate(mpw_ctx* ctx, mpw_sur* s, double dt, int calls, double tol, int* accepted,
                               double* max_residual);
 
+/* The weights that mpw_step_surrogate gives (y0, y0', y0'', y1, y1', y1''),
+ * the global state at both ends of a call and its first two time derivatives,
+ * to build the input of RK4 stage l (0..3) of step m (0..3) of the call, for
+ * a call of length delta = 4 dt (host only; no device work).  w6 receives six
+ * doubles.  MPW_ERR_ARG for m or l outside 0..3 or a NULL w6. */
+mpw_status mpw_sur_stage_weights(int m, int l, double delta, double* w6);
+
 #ifdef __cplusplus
 }
 #endif

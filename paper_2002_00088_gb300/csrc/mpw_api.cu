@@ -1743,6 +1743,12 @@ static void stage_coefficients(int m, int l, double D, double cf[6]) {
   }
 }
 
+mpw_status mpw_sur_stage_weights(int m, int l, double delta, double* w6) {
+  if (m < 0 || m > 3 || l < 0 || l > 3 || !w6) return set_err(MPW_ERR_ARG, "stage weights: m, l in 0..3 and w6 non-null");
+  stage_coefficients(m, l, delta, w6);
+  return MPW_OK;
+}
+
 mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, double tol, int* accepted,
                               double* max_residual) {
   mpw_status st = check_ctx(c);

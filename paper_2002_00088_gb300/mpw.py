@@ -99,6 +99,7 @@ SIGNATURES = {
     "mpw_sur_predict": (C.c_int, [_vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), _vp, _vp]),
     "mpw_sur_check": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_int, C.POINTER(C.c_int), _vp, _vp]),
     "mpw_step_surrogate": (C.c_int, [_vp, _vp, C.c_double, C.c_int, C.c_double, C.POINTER(C.c_int), _dp]),
+    "mpw_sur_stage_weights": (C.c_int, [C.c_int, C.c_int, C.c_double, _dp]),
     "mpw_destroy": (None, [_vp]),
 }
 
