@@ -1,8 +1,12 @@
-"""Binding of the learned surrogate's layers (include/mpw_surrogate.h).
+"""Binding of the learned surrogate (include/mpw_surrogate.h): its layer
+primitives, the network handle (features, targets, training step, forward,
+call, residual check), hybrid stepping of a multipatch simulation, and the
+training driver that feeds the network the method's own trajectories.
 
-Argument marshalling only: every layer, gradient and optimizer update runs in
-the CUDA kernels of libmpw.so.  Tensors are torch CUDA tensors, channels-last
-volumes (batch, n2, n1, n0, C); BF16 tensors are torch.bfloat16.
+Argument marshalling only: every layer, gradient, optimizer update and step
+of the method runs in the CUDA kernels of libmpw.so.  Tensors are torch CUDA
+tensors, channels-last volumes (batch, n2, n1, n0, C); BF16 tensors are
+torch.bfloat16.
 """
 import ctypes as C
 
@@ -219,8 +223,9 @@ def train(sur, source, trajectories, batch=2, lr=2e-3, lr_end=1e-4, first=0, log
     torch = _torch()
     n = source.n
     shape = (batch, n, n, n)
-    u0 = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(2)]
-    u1 = [torch.empty(shape, dtype=torch.float64, device="cuda") for _ in range(2)]
+    dev = torch.device("cuda", sur.device)
+    u0 = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(2)]
+    u1 = [torch.empty(shape, dtype=torch.float64, device=dev) for _ in range(2)]
     steps = max(trajectories // batch, 1)
     losses = []
     for k in range(steps):
