@@ -52,3 +52,18 @@ def test_conv_entry_points_validate_shapes_before_any_launch(mpw_lib):
     assert L.mpw_conv3_wgrad_scratch_bytes(16, 32) == 0
     assert L.mpw_adam_step(fake, None, fake, fake, fake, 10, 1e-3, 0.9, 0.999, 1e-8, 0, None) == 1
     assert L.mpw_mse_grad(fake, 8, fake, 9, 10, fake, None, None) == 1
+
+
+def test_surrogate_entry_points_validate_arguments(mpw_lib):
+    """Refused on the host, before any CUDA call."""
+    L = mpw_lib.lib
+    h = ctypes.c_void_p()
+    assert L.mpw_sur_create(0, None, 0.0, 0.1, 1e-4, ctypes.byref(h)) == 1      # dt <= 0
+    assert L.mpw_sur_create(0, None, 1e-3, -0.1, 1e-4, ctypes.byref(h)) == 1    # h <= 0
+    assert L.mpw_sur_create(0, None, 1e-3, 0.1, 0.0, ctypes.byref(h)) == 1      # sigma <= 0
+    assert L.mpw_sur_create(0, None, 1e-3, 0.1, 1e-4, None) == 1                # no output handle
+    assert not h.value
+    n = (ctypes.c_int * 3)(16, 8, 8)
+    assert L.mpw_sur_predict(None, None, None, 1, n, None, None) == 1           # null handle
+    assert L.mpw_step_surrogate(None, None, 1e-3, 1, 1e-4, None, None) == 1     # null context
+    assert L.mpw_sur_param_count() == sum(co * 27 * ci + co for ci, co in [(8, 32), (32, 32), (32, 32), (32, 8)])
