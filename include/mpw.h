@@ -50,8 +50,10 @@ typedef enum {
   MPW_ERR_TRAVERSAL = 4,      /* a patch would cross more than one global cell in a step */
   MPW_ERR_OUTSIDE = 5,        /* a local patch (with ghosts and stencils) leaves the global interior */
   MPW_ERR_GHOST_UNFILLED = 6, /* a ghost point could not be interpolated (Sec. 2.4.1 "skip") */
-  MPW_ERR_BOUNDS = 7,         /* a device-side index check failed */
-  MPW_ERR_TIMEOUT = 8,        /* reserved for bounded device waits */
+                              /* 7 is not used */
+  MPW_ERR_TIMEOUT = 8,        /* a bounded device wait (the RHS kernels' TMA pipeline) ran
+                                 out: the CTA drained its own copies and stopped early, so the
+                                 step's result is incomplete; the context stays usable */
   MPW_ERR_CUDA = 9,           /* a CUDA runtime call failed */
   MPW_ERR_STATE = 10          /* call not valid in the current state */
 } mpw_status;
@@ -204,6 +206,16 @@ mpw_status mpw_compute_flags(mpw_ctx* ctx);
 mpw_status mpw_get_flags(mpw_ctx* ctx, uint8_t* flags);
 mpw_status mpw_set_flags(mpw_ctx* ctx, const uint8_t* flags);
 
+/* Test support for the bounded-wait error path (no counterpart in the
+ * paper).  Every mbarrier wait of the RHS kernels' TMA pipeline gives up
+ * after `limit` try-waits, sets the device error word and lets the CTA drain
+ * its own copies in flight (that drain always uses the default limit) and
+ * return; the step then reports MPW_ERR_TIMEOUT.  The default is 2^20
+ * (about a second and more); 0 makes every such wait give up at once, which
+ * is how the tests drive the error path without a real stall.
+ * Errors: MPW_ERR_ARG for a null context. */
+mpw_status mpw_set_wait_limit(mpw_ctx* ctx, unsigned limit);
+
 /* Fill every ghost zone of the state u at time t (maps at t): physical BC,
  * Local-to-Global, Global-to-Local (Sec. 2.4).  Flags are computed first if
  * invalid. */
@@ -212,7 +224,11 @@ mpw_status mpw_fill_ghosts(mpw_ctx* ctx, double t);
 /* Advance nsteps RK4 steps of size dt (Sec. 2.3, Table 1).  Validates CFL,
  * traversal, separation and containment before launching; reads the device
  * error word once at the end.  On a device-side error the call returns
- * MPW_ERR_GHOST_UNFILLED or MPW_ERR_BOUNDS. */
+ * MPW_ERR_GHOST_UNFILLED (a ghost point was skipped, Sec. 2.4.1) or
+ * MPW_ERR_TIMEOUT (a bounded wait ran out).  The steps run to the end either
+ * way, so the fields then hold an invalid result: restore a checkpoint
+ * (fields, flags, time) before stepping on.  The error word is cleared once
+ * it has been read. */
 mpw_status mpw_step(mpw_ctx* ctx, double dt, int nsteps);
 
 /* As mpw_step, but returns once the work is enqueued: the device error word
@@ -297,14 +313,20 @@ mpw_status mpw_profile_read(mpw_ctx* ctx, double* ms, long long* launches, int n
  *   psi, pi    device pointers on the current device, dense [k][j][i]
  *              interiors; read at the start, overwritten with the result.
  *   stream     cudaStream_t to enqueue on (NULL: the legacy default stream).
- * The work is enqueued asynchronously and no cudaMalloc/cudaFree is called.
+ * No cudaMalloc/cudaFree (or other allocating routine) is called.
  * The first call on a device looks up the device address of the array
  * (cudaGetSymbolAddress); make that first call before any stream capture
  * begins.  All calls share the array, which keeps the last call's contents
  * (the exponent slots and error word are cleared at the start of each call):
  * calls whose work overlaps on the GPU (other streams, unordered host
- * threads) race and corrupt each other.  Errors: MPW_ERR_ARG, MPW_ERR_CFL,
- * MPW_ERR_CUDA, with a message from mpw_last_error(). */
+ * threads) race and corrupt each other.  The call returns once the work has
+ * finished on `stream`: it then reads the device error word into a host
+ * stack variable (no allocation) and synchronises the stream.
+ * Errors: MPW_ERR_ARG, MPW_ERR_CFL (before any work is enqueued),
+ * MPW_ERR_TIMEOUT (a bounded device wait ran out) and
+ * MPW_ERR_GHOST_UNFILLED (a ghost point could not be filled) with psi and
+ * pi then holding an incomplete result, MPW_ERR_CUDA; a message is kept for
+ * mpw_last_error(). */
 mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[3], const double hi[3], double ko_eps,
                                      double dt, int nsteps, double* psi, double* pi, void* stream);
 

@@ -89,6 +89,7 @@ struct mpw_ctx {
   std::vector<Box> boxes;  // covered boxes at the last flag computation
   int* d_err = nullptr;
   int* h_err = nullptr;
+  unsigned wait_limit = WAIT_LIMIT;  // try-waits of the RHS kernels' TMA pipeline waits
   int* d_expo = nullptr;  // [patch][buffer][field] maximum biased exponent
   long long* d_rev = nullptr;  // queue of revived cells (REVIVE_CAP entries); its length lives in d_err[32]
   uint8_t* d_cov = nullptr;    // covered masks of the rotating patches' bounding boxes
@@ -986,6 +987,7 @@ int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0, boo
   for (int q = 0; q < a.nbox; ++q) a.box[q] = c->boxes[q];
   a.expo = c->d_expo;
   a.err = c->d_err;
+  a.wait_limit = c->wait_limit;
   int blocks = 0;
   for (int q = 0; q < a.np; ++q) {
     const PatchState& P = c->p[q];
@@ -1153,7 +1155,7 @@ mpw_status read_error_word(mpw_ctx* c) {
     CUDA_TRY(cudaMemsetAsync(c->d_err, 0, sizeof(int), c->stream));
     if (e & ERR_TIMEOUT) return set_err(MPW_ERR_TIMEOUT, "a bounded device wait ran out (error word 0x%x)", e);
     if (e & ERR_UNFILLED) return set_err(MPW_ERR_GHOST_UNFILLED, "a ghost point could not be interpolated");
-    return set_err(MPW_ERR_BOUNDS, "device index check failed (error word 0x%x)", e);
+    return set_err(MPW_ERR_CUDA, "unexpected device error word 0x%x", e);
   }
   return MPW_OK;
 }
@@ -1613,6 +1615,13 @@ mpw_status mpw_set_flags(mpw_ctx* c, const uint8_t* flags) {
   for (size_t q = 1; q < c->p.size(); ++q) c->boxes[q - 1] = covered_box(g, c->p[q], c->t);
   c->flags_valid = true;
   c->glist_valid = false;  // the ghost lists come from the flags kernel only
+  return MPW_OK;
+}
+
+mpw_status mpw_set_wait_limit(mpw_ctx* c, unsigned limit) {
+  mpw_status st = check_ctx(c);
+  if (st) return st;
+  c->wait_limit = limit;
   return MPW_OK;
 }
 

@@ -130,6 +130,7 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
       r.beta = beta[l];
       r.expo = expo;
       r.err = err;
+      r.wait_limit = WAIT_LIMIT;
       RhsPatch& R = r.p[0];
       R.ymap = tile_map[in_buf[l]];
       R.umap = point_map[0];
@@ -159,7 +160,17 @@ extern "C" mpw_status mpw_step_periodic_noalloc(const int n[3], const double lo[
     t += dt;
   }
   launch_pack(buf[BUF_U], g, psi, pi, 0, nullptr, false, s);
-  const cudaError_t e = cudaGetLastError();
+  cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(MPW_ERR_CUDA, cudaGetErrorString(e));
+  // The device error word, read into a host stack variable once the work has
+  // run: a copy into pageable host memory stages through the driver's own
+  // buffers, so nothing is allocated here either.
+  int word = 0;
+  e = cudaMemcpyAsync(&word, err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(MPW_ERR_CUDA, cudaGetErrorString(e));
+  if (word & ERR_TIMEOUT) return fail(MPW_ERR_TIMEOUT, "a bounded device wait ran out; psi and pi are incomplete");
+  if (word & ERR_UNFILLED) return fail(MPW_ERR_GHOST_UNFILLED, "a ghost point could not be filled");
+  if (word) return fail(MPW_ERR_CUDA, "unexpected device error word");
   return MPW_OK;
 }

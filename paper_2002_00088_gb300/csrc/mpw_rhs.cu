@@ -270,7 +270,7 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
     const unsigned bar = smem_u32(&bars[s]);
     int fl = FLAG_LIVE;
     if (in_xy && check_flags) fl = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
-    if (!bar_wait(bar, (unsigned)(it / RHS_DEPTH) & 1u)) s_abort = 1;
+    if (!bar_wait(bar, (unsigned)(it / RHS_DEPTH) & 1u, A.wait_limit)) s_abort = 1;
     // raw values of this iteration
     const double rs_own = sl[own_raw], rp_own = sl[BOX_X * BOX_Y + own_raw];
     double rs_h = 0.0, rp_h = 0.0;
@@ -446,9 +446,408 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
   }
 }
 
+// ---------------------------------------------------------------------------
+// Fixed-point body for translating frames on isotropic patches (constant w,
+// equal spacing on every axis): the common case.  Same traversal, TMA
+// pipeline and arithmetic model as rhs_body<FIXED>, with the integer work cut
+// down:
+//  - conversion q = round(x 2^(1074-E)) for the buffer's largest biased
+//    exponent E (|q| < 2^52), one variable 64-bit shift (to_fixed52);
+//  - stencil sums formed around the centre, T_m = sum_axes (u_m + u_-m) - 6 u0,
+//    so that D2 = 16 T1 - T2 and KO = T3 - 6 T2 + 15 T1 need no multiple of u0
+//    (the weights of each stencil sum to zero);
+//  - the real coefficients as 64 x 64 high products built from three 32-bit
+//    partial products of a signed-digit split of the per-CTA multiplier
+//    (hi_pos, hi_any), within three units of the output scale 2^S;
+//  - per-CTA constants in registers, pointers advanced per plane.
+// Rotating frames and anisotropic patches keep rhs_body<FIXED, ROT>; a CTA
+// whose input is not finite or whose scales leave the binary64 range takes
+// rhs_body<false>.
+
+// Per-CTA constants of the fixed-point body.  A multiplier M (|M| < 2^61)
+// is held as M = hi 2^32 + lo with lo in [-2^31, 2^31).
+struct FxTerms {
+  int ok;
+  int E1s, E1p;          // conversion exponents of psi and Pi
+  int v0[2];             // K_psi: Pi_0
+  int kos[2];            // K_psi: KO(psi), all axes
+  int d2[2];             // K_Pi : D2(psi), all axes
+  int kop[2];            // K_Pi : KO(Pi), all axes
+  int d1s[3][2];         // K_psi: D1(psi) per axis (moving patch)
+  int d1p[3][2];         // K_Pi : D1(Pi) per axis
+  double fa[2], fb[2];   // alpha 2^S, beta 2^S (psi, Pi)
+};
+
+// q = round-half-away(x 2^(1074-E1)) for a binary64 x whose biased exponent
+// is at most E1 (|q| < 2^52); values of larger exponent (non-live cells only)
+// and values below 2^(E1-1086) give 0.
+__device__ __forceinline__ long long to_fixed52(double x, int E1) {
+  const int hi = __double2hiint(x);
+  const unsigned lo = (unsigned)__double2loint(x);
+  const unsigned mh = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
+  const unsigned sh = (unsigned)(E1 - (int)(((unsigned)hi >> 20) & 0x7FFu));
+  const unsigned long long m = ((unsigned long long)mh << 32) | lo;
+  unsigned long long t;
+  asm("shr.b64 %0, %1, %2;" : "=l"(t) : "l"(m), "r"(sh));  // shift amounts >= 64 give 0
+  const long long sgn = (long long)(hi >> 31);
+  return ((long long)(t ^ (unsigned long long)sgn) + 1) >> 1;
+}
+
+// M = round(coef 2^(E1 - 1074 - S + 64)) as a signed-digit pair.
+__device__ __forceinline__ void fx_multiplier(double coef, int E1, int S, int (&m)[2]) {
+  const long long M = coef == 0.0 ? 0ll : __double2ll_rn(scalbn(coef, E1 - 1074 - S + 64));
+  const long long h = (M + 0x80000000ll) >> 32;
+  m[0] = (int)h;
+  m[1] = (int)(M - (h << 32));
+}
+
+// Smallest S with |coef| 2^(E1-1074-S+64) < 2^61 (so every multiplier is
+// below 2^61); -100000 for coef = 0.
+__device__ __forceinline__ int fx_scale(double coef, int E1) {
+  return coef == 0.0 ? -100000 : ilogb(coef) + E1 - 1074 + 4;
+}
+
+// acc += a M / 2^64 (within 3 units) for |a| < 2^61 and a multiplier M >= 0:
+// the partial products ah mh (exact, 64-bit), ah ml and al mh (their high
+// words); al ml / 2^64 < 1 is dropped.
+__device__ __forceinline__ long long hi_pos(long long a, const int (&m)[2], int& t) {
+  const int ah = (int)(a >> 32);
+  const unsigned al = (unsigned)a;
+  t += __mulhi(ah, m[1]) + (int)__umulhi(al, (unsigned)m[0]);
+  return (long long)ah * m[0];
+}
+// The same for a multiplier of either sign (al is unsigned: its high word
+// against a negative mh needs mh added back when al >= 2^31).
+__device__ __forceinline__ long long hi_any(long long a, const int (&m)[2], int& t) {
+  const int ah = (int)(a >> 32);
+  const int al = (int)(unsigned)a;
+  t += __mulhi(ah, m[1]) + __mulhi(al, m[0]) + ((al >> 31) & m[0]);
+  return (long long)ah * m[0];
+}
+
+__device__ void fx_setup(FxTerms& T, const RhsPatch& P, int Es_raw, int Ep_raw, double alpha, double beta) {
+  T.ok = Es_raw < EXP_NONFINITE && Ep_raw < EXP_NONFINITE;
+  if (!T.ok) return;
+  const int Es = max(Es_raw, 64), Ep = max(Ep_raw, 64);
+  T.E1s = Es;
+  T.E1p = Ep;
+  const double cko = P.cko[0], c2 = P.c2[0];
+  int Ss = max(fx_scale(1.0, Ep), fx_scale(cko, Es));
+  int Sp = max(fx_scale(c2, Es), fx_scale(cko, Ep));
+  if (P.moving)
+    for (int a = 0; a < 3; ++a) {
+      Ss = max(Ss, fx_scale(P.c1[a], Es));
+      Sp = max(Sp, fx_scale(P.c1[a], Ep));
+    }
+  if (Ss < -960 || Sp < -960 || Ss > 960 || Sp > 960) {
+    T.ok = 0;
+    return;
+  }
+  fx_multiplier(1.0, Ep, Ss, T.v0);
+  fx_multiplier(cko, Es, Ss, T.kos);
+  fx_multiplier(c2, Es, Sp, T.d2);
+  fx_multiplier(cko, Ep, Sp, T.kop);
+  for (int a = 0; a < 3; ++a) {
+    fx_multiplier(P.moving ? P.c1[a] : 0.0, Es, Ss, T.d1s[a]);
+    fx_multiplier(P.moving ? P.c1[a] : 0.0, Ep, Sp, T.d1p[a]);
+  }
+  T.fa[0] = scalbn(alpha, Ss);
+  T.fb[0] = scalbn(beta, Ss);
+  T.fa[1] = scalbn(alpha, Sp);
+  T.fb[1] = scalbn(beta, Sp);
+}
+
+template <bool MOVING>
+__device__ __forceinline__ void rhs_fx_body(const RhsArgs& A, const RhsPatch& Pt, const int p, int lb,
+                                            const FxTerms& T, double* slots, long long* conv,
+                                            unsigned long long* bars, int& s_abort) {
+  constexpr int TX = RHS_TX, TY = RHS_TY, SY = TX + 6;
+  const Geom& g = Pt.g;
+  const int tx = lb % Pt.tiles_x;
+  lb /= Pt.tiles_x;
+  const int ty = lb % Pt.tiles_y;
+  const int tz = lb / Pt.tiles_y;
+  const int li = threadIdx.x % TX, lj = threadIdx.x / TX;
+  const int i0 = tx * TX, j0 = ty * TY;
+  const int i = i0 + li, j = j0 + lj;
+  const int z0 = tz * Pt.zc, z1 = min(z0 + Pt.zc, g.n[2]);
+  const int stage = A.stage;
+  if (threadIdx.x == 0)
+    for (int s = 0; s < RHS_DEPTH && z0 + s < z1; ++s)
+      issue_slot(Pt, stage, slots + s * SLOT_DOUBLES, smem_u32(&bars[s]), i0, j0, z0 + s);
+  const bool in_box = (i < g.n[0] + NG) && (j < g.n[1] + NG);
+  const bool in_xy = (i < g.n[0]) && (j < g.n[1]);
+  bool check_flags = false;
+  if (Pt.is_global) {
+    for (int q = 0; q < A.nbox; ++q) {
+      const Box& bx = A.box[q];
+      if (bx.lo[0] <= i0 + TX - 1 && bx.hi[0] >= i0 && bx.lo[1] <= j0 + TY - 1 && bx.hi[1] >= j0 &&
+          bx.lo[2] <= z1 - 1 && bx.hi[2] >= z0)
+        check_flags = true;
+    }
+  }
+  // halo assignment: threads [0, 6 TX) carry the y halo, [6 TX, 6 TX + 6 TY) the x halo
+  const int t = threadIdx.x;
+  int hi_ = -100, hj = -100, hoff = 0;
+  if (t < 6 * TX) {
+    const int rr = t / TX, cc = t % TX;
+    hoff = (rr < 3 ? rr : TY + rr) * SY + cc + 3;
+    hi_ = i0 + cc;
+    hj = j0 + (rr < 3 ? rr - 3 : TY + rr - 3);
+  } else if (t < 6 * TX + 6 * TY) {
+    const int u = t - 6 * TX, rr = u / 6, cc = u % 6;
+    hoff = (rr + 3) * SY + (cc < 3 ? cc : TX + cc);
+    hj = j0 + rr;
+    hi_ = i0 + (cc < 3 ? cc - 3 : TX + cc - 3);
+  }
+  const bool h_ok = hi_ >= -NG && hi_ < g.n[0] + NG && hj >= -NG && hj < g.n[1] + NG;
+  const int own = (lj + 3) * SY + li + 3;
+  const int own_raw = (lj + 3) * BOX_X + li + 4;
+  const int halo_raw = (hj - j0 + 3) * BOX_X + (hi_ - i0 + 4);
+  const int E1s = T.E1s, E1p = T.E1p;
+  const double* Ys = Pt.Y;
+  const long long vol = g.vol, plane = g.plane;
+  auto conv_of = [&](int zz) -> long long* { return conv + ((zz - z0) & (CONV_SLOTS - 1)) * 2 * CONV_PLANE; };
+  // prologue: planes z0-3 .. z0+2 by plain loads (queue), z0 .. z0+2 also into the converted ring
+  long long qs[7], qp[7];
+  {
+    const long long c0 = g.at(min(i, g.n[0] + NG - 1), min(j, g.n[1] + NG - 1), z0 - NG);
+    const long long ch = h_ok ? g.at(hi_, hj, z0) : 0;
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+      const int zz = z0 - NG + o;
+      qs[o] = 0;
+      qp[o] = 0;
+      if (in_box) {
+        const long long c = c0 + o * plane;
+        qs[o] = to_fixed52(Ys[c], E1s);
+        qp[o] = to_fixed52(Ys[c + vol], E1p);
+      }
+      if (o >= NG && zz < z1) {
+        long long* cv = conv_of(zz);
+        cv[own] = qs[o];
+        cv[CONV_PLANE + own] = qp[o];
+        if (h_ok) {
+          const long long c = ch + (o - NG) * plane;
+          cv[hoff] = to_fixed52(Ys[c], E1s);
+          cv[CONV_PLANE + hoff] = to_fixed52(Ys[c + vol], E1p);
+        }
+      }
+    }
+  }
+  // constants in registers
+  const int mv0[2] = {T.v0[0], T.v0[1]}, mkos[2] = {T.kos[0], T.kos[1]}, md2[2] = {T.d2[0], T.d2[1]},
+            mkop[2] = {T.kop[0], T.kop[1]};
+  int md1s[3][2], md1p[3][2];
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      md1s[a][k] = MOVING ? T.d1s[a][k] : 0;
+      md1p[a][k] = MOVING ? T.d1p[a][k] : 0;
+    }
+  const double fa_s = T.fa[0], fa_p = T.fa[1], fb_s = T.fb[0], fb_p = T.fb[1];
+  // output pointers advance one plane per iteration
+  const long long c_own = g.at(min(i, g.n[0] - 1), min(j, g.n[1] - 1), z0);
+  double* outp = Pt.OUT + c_own;
+  double* accp = Pt.ACC + c_own;
+  const uint8_t* flagp = A.flags + ((long long)z0 * g.n[1] + min(j, g.n[1] - 1)) * g.n[0] + min(i, g.n[0] - 1);
+  const long long fplane = (long long)g.n[0] * g.n[1];
+  const int pt = lj * TX + li;
+  unsigned emax_s = 0, emax_p = 0;
+  for (int z = z0; z < z1; ++z) {
+    const int it = z - z0;
+    const int s = it % RHS_DEPTH;
+    const double* sl = slots + s * SLOT_DOUBLES;
+    const unsigned bar = smem_u32(&bars[s]);
+    int fl = FLAG_LIVE;
+    if (in_xy && check_flags) fl = *flagp & 3;
+    if (!bar_wait(bar, (unsigned)(it / RHS_DEPTH) & 1u, A.wait_limit)) s_abort = 1;
+    const double rs_own = sl[own_raw], rp_own = sl[BOX_X * BOX_Y + own_raw];
+    double rs_h = 0.0, rp_h = 0.0;
+    if (h_ok) {
+      rs_h = sl[halo_raw];
+      rp_h = sl[BOX_X * BOX_Y + halo_raw];
+    }
+    double ua_s = 0.0, ua_p = 0.0, ub_s = 0.0, ub_p = 0.0;
+    if (stage < 3) {
+      ua_s = sl[TILE_DOUBLES + pt];
+      ua_p = sl[TILE_DOUBLES + TX * TY + pt];
+    }
+    if (stage > 0) {
+      ub_s = sl[TILE_DOUBLES + PT_DOUBLES + pt];
+      ub_p = sl[TILE_DOUBLES + PT_DOUBLES + TX * TY + pt];
+    }
+    __syncthreads();
+    if (s_abort) {
+      // drain this CTA's copies still in flight (bounded), report, leave
+      if (threadIdx.x == 0) {
+        atomicOr(A.err, ERR_TIMEOUT);
+        for (int k = it; k < it + RHS_DEPTH && z0 + k < z1; ++k)
+          bar_wait(smem_u32(&bars[k % RHS_DEPTH]), (unsigned)(k / RHS_DEPTH) & 1u);
+      }
+      return;
+    }
+    if (threadIdx.x == 0 && z + RHS_DEPTH < z1)
+      issue_slot(Pt, stage, slots + s * SLOT_DOUBLES, bar, i0, j0, z + RHS_DEPTH);
+    qs[6] = to_fixed52(rs_own, E1s);
+    qp[6] = to_fixed52(rp_own, E1p);
+    const bool live = in_xy && (fl == FLAG_LIVE || fl == FLAG_REVIVED);
+    const long long* rs = conv_of(z) + own;
+    const long long* rp = rs + CONV_PLANE;
+    const long long u0 = qs[3], v0 = qp[3];
+    long long ks = 0, kp = 0;
+    int ts = 0, tp = 0;
+    const long long u6 = 6 * u0, v6 = 6 * v0;
+    const long long T1 = (rs[-1] + rs[1] + rs[-SY]) + (rs[SY] + qs[2] + qs[4]) - u6;
+    const long long T2 = (rs[-2] + rs[2] + rs[-2 * SY]) + (rs[2 * SY] + qs[1] + qs[5]) - u6;
+    const long long T3 = (rs[-3] + rs[3] + rs[-3 * SY]) + (rs[3 * SY] + qs[0] + qs[6]) - u6;
+    const long long P1 = (rp[-1] + rp[1] + rp[-SY]) + (rp[SY] + qp[2] + qp[4]) - v6;
+    const long long P2 = (rp[-2] + rp[2] + rp[-2 * SY]) + (rp[2 * SY] + qp[1] + qp[5]) - v6;
+    const long long P3 = (rp[-3] + rp[3] + rp[-3 * SY]) + (rp[3 * SY] + qp[0] + qp[6]) - v6;
+    const long long T16 = T1 * 16;
+    const long long d2 = T16 - T2;
+    const long long kos = T3 - 6 * T2 + (T16 - T1);
+    const long long kop = P3 - 6 * P2 + 15 * P1;
+    ks = hi_pos(v0, mv0, ts) + hi_pos(kos, mkos, ts);
+    kp = hi_pos(d2, md2, tp) + hi_pos(kop, mkop, tp);
+    if (MOVING) {
+      ks += (long long)ts;
+      kp += (long long)tp;
+      ts = 0;
+      tp = 0;
+      const long long dsx = 8 * (rs[1] - rs[-1]) - (rs[2] - rs[-2]);
+      const long long dsy = 8 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY]);
+      const long long dsz = 8 * (qs[4] - qs[2]) - (qs[5] - qs[1]);
+      const long long dpx = 8 * (rp[1] - rp[-1]) - (rp[2] - rp[-2]);
+      const long long dpy = 8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]);
+      const long long dpz = 8 * (qp[4] - qp[2]) - (qp[5] - qp[1]);
+      ks += hi_any(dsx, md1s[0], ts) + hi_any(dsy, md1s[1], ts);
+      ks += (long long)ts;
+      ts = 0;
+      ks += hi_any(dsz, md1s[2], ts);
+      kp += hi_any(dpx, md1p[0], tp) + hi_any(dpy, md1p[1], tp);
+      kp += (long long)tp;
+      tp = 0;
+      kp += hi_any(dpz, md1p[2], tp);
+    }
+    ks += (long long)ts;
+    kp += (long long)tp;
+    // ---- RK4 stage combination (FP64): K = k 2^S, folded into alpha, beta
+    const double Ks = (double)ks, Kp = (double)kp;
+    double os, op;
+    if (stage == 3) {
+      os = fma(fa_s, Ks, ub_s);
+      op = fma(fa_p, Kp, ub_p);
+    } else {
+      const double as = stage == 0 ? ua_s : ub_s;
+      const double ap = stage == 0 ? ua_p : ub_p;
+      os = fma(fa_s, Ks, ua_s);
+      op = fma(fa_p, Kp, ua_p);
+      if (live) {
+        accp[0] = fma(fb_s, Ks, as);
+        accp[vol] = fma(fb_p, Kp, ap);
+      }
+    }
+    if (live) {
+      outp[0] = os;
+      outp[vol] = op;
+      emax_s = max(emax_s, (unsigned)__double2hiint(os) & 0x7FFFFFFFu);
+      emax_p = max(emax_p, (unsigned)__double2hiint(op) & 0x7FFFFFFFu);
+    }
+    // plane z+3 into the converted ring (read from iteration z+3 on)
+    {
+      long long* cv = conv_of(z + NG);
+      cv[own] = qs[6];
+      cv[CONV_PLANE + own] = qp[6];
+      if (h_ok) {
+        cv[hoff] = to_fixed52(rs_h, E1s);
+        cv[CONV_PLANE + hoff] = to_fixed52(rp_h, E1p);
+      }
+    }
+#pragma unroll
+    for (int o = 0; o < 6; ++o) {
+      qs[o] = qs[o + 1];
+      qp[o] = qp[o + 1];
+    }
+    outp += plane;
+    accp += plane;
+    flagp += fplane;
+  }
+  // exponent bookkeeping of the output buffer (consumed by the next substage)
+  int es = (int)(emax_s >> 20), ep = (int)(emax_p >> 20);
+  es = __reduce_max_sync(0xffffffffu, es);
+  ep = __reduce_max_sync(0xffffffffu, ep);
+  if ((threadIdx.x & 31) == 0) {
+    if (es) atomicMax(&A.expo[slot(p, Pt.out_buf, 0)], es);
+    if (ep) atomicMax(&A.expo[slot(p, Pt.out_buf, 1)], ep);
+  }
+}
+
+// The bodies of rhs_body that the fixed-point entry hands CTAs to, kept out
+// of line so that they do not share a register allocation with the
+// isotropic fixed-point bodies: native FP64 (non-finite input, scales out of
+// range), the per-axis fixed-point arithmetic of anisotropic patches and the
+// rotating frames.
+template <int TX, int TY, bool FIXED, bool ROT>
+__device__ __noinline__ void rhs_out_of_line(const RhsArgs& A, const int b) {
+  rhs_body<TX, TY, FIXED, ROT>(A, b);
+}
+
+// Fixed-point launch entry: per-CTA set-up, then the body for the patch: the
+// isotropic fixed-point body of a translating frame (moving or not), or one
+// of the out-of-line bodies.  Every launch (with or without rotating patches,
+// single or batched) takes the same body for the same patch, so results do
+// not depend on what else the launch holds.
+template <int TX, int TY, bool ROT>
+__device__ __forceinline__ void rhs_fx(const RhsArgs& A, const int b) {
+  extern __shared__ unsigned char smem_dyn[];
+  __shared__ FxTerms T;
+  __shared__ int s_abort;
+  const unsigned long long base = (reinterpret_cast<unsigned long long>(smem_dyn) + 1023ull) & ~1023ull;
+  double* slots = reinterpret_cast<double*>(base);
+  long long* conv = reinterpret_cast<long long*>(slots + RHS_DEPTH * SLOT_DOUBLES);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(conv + CONV_SLOTS * 2 * CONV_PLANE);
+  int p = 0;
+  while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
+  const RhsPatch& Pt = A.p[p];
+  if (ROT && Pt.rot) {
+    rhs_out_of_line<TX, TY, true, ROT>(A, b);
+    return;
+  }
+  if (!Pt.iso) {
+    rhs_out_of_line<TX, TY, true, false>(A, b);
+    return;
+  }
+  if (threadIdx.x == 0) {
+    const int Es = max(A.expo[slot(p, Pt.in_buf, 0)], A.expo[slot(p, Pt.in_buf, 0) + EXP_GHOST]);
+    const int Ep = max(A.expo[slot(p, Pt.in_buf, 1)], A.expo[slot(p, Pt.in_buf, 1) + EXP_GHOST]);
+    fx_setup(T, Pt, Es, Ep, A.alpha, A.beta);
+    s_abort = 0;
+    if (T.ok) {
+      for (int s = 0; s < RHS_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+  }
+  __syncthreads();
+  if (!T.ok) {
+    rhs_out_of_line<TX, TY, false, false>(A, b);
+    return;
+  }
+  const int lb = b - Pt.block0;
+  if (Pt.moving)
+    rhs_fx_body<true>(A, Pt, p, lb, T, slots, conv, bars, s_abort);
+  else
+    rhs_fx_body<false>(A, Pt, p, lb, T, slots, conv, bars, s_abort);
+}
+
 template <int TX, int TY, bool FIXED, bool ROT>
 __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs(const __grid_constant__ RhsArgs A) {
-  rhs_body<TX, TY, FIXED, ROT>(A, blockIdx.x);
+  if (FIXED)
+    rhs_fx<TX, TY, ROT>(A, blockIdx.x);
+  else
+    rhs_body<TX, TY, false, ROT>(A, blockIdx.x);
 }
 
 // Batched launch over independent instances: instance i owns the blocks
@@ -466,7 +865,10 @@ template <int TX, int TY, bool FIXED, bool ROT>
 __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs_batch(const RhsArgs* __restrict__ As,
                                                                       const int* __restrict__ blk0, int ninst) {
   const int i = batch_instance(blk0, ninst);
-  rhs_body<TX, TY, FIXED, ROT>(As[i], blockIdx.x - blk0[i]);
+  if (FIXED)
+    rhs_fx<TX, TY, ROT>(As[i], blockIdx.x - blk0[i]);
+  else
+    rhs_body<TX, TY, false, ROT>(As[i], blockIdx.x - blk0[i]);
 }
 
 // Host: TMA maps of one field buffer (4-D: x, y, plane, field).

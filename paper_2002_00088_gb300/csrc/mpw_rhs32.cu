@@ -220,7 +220,7 @@ __device__ __forceinline__ void rhs32_body(const RhsArgs& A, const int b) {
     const unsigned bar = smem_u32(&bars[s]);
     int fl = FLAG_LIVE;
     if (in_xy && check_flags) fl = A.flags[((long long)z * g.n[1] + j) * g.n[0] + i] & 3;
-    if (!bar_wait(bar, (unsigned)(it / R32_DEPTH) & 1u)) s_abort = 1;
+    if (!bar_wait(bar, (unsigned)(it / R32_DEPTH) & 1u, A.wait_limit)) s_abort = 1;
     const float rs_own = sl[own_raw], rp_own = sl[BX * BY + own_raw];
     float rs_h = 0.0f, rp_h = 0.0f;
     if (h_ok) {

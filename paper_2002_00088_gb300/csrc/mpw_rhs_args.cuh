@@ -24,7 +24,13 @@ constexpr int MAX_APARAMS = 1024;
 
 enum { BUF_U = 0, BUF_ACC = 1, BUF_YA = 2, BUF_YB = 3 };
 enum { FLAG_LIVE = 0, FLAG_GHOST = 1, FLAG_DEAD = 2, FLAG_REVIVED = 3 };
-enum { ERR_UNFILLED = 1, ERR_BOUNDS = 2, ERR_NONFINITE = 4, ERR_TIMEOUT = 8 };
+// Bits of the device error word: a ghost point that could not be
+// interpolated (Sec. 2.4.1 "skip"), a bounded mbarrier wait that ran out.
+enum { ERR_UNFILLED = 1, ERR_TIMEOUT = 8 };
+
+// Try-waits a TMA pipeline wait gets by default (about a second and more on
+// GB300); a wait that runs out reports ERR_TIMEOUT instead of hanging.
+constexpr unsigned WAIT_LIMIT = 1u << 20;
 
 struct Geom {
   int n[3];
@@ -97,6 +103,8 @@ struct RhsArgs {
   Box box[MAX_PATCHES];
   int* expo;            // tracked maximum biased exponents, [patch][buffer][field]
   int* err;             // device error word
+  unsigned wait_limit;  // try-waits allowed to the TMA pipeline's waits (the drain after
+                        // an expired wait always gets WAIT_LIMIT)
 };
 
 #ifndef MPW_RHS_TY

@@ -3,9 +3,9 @@
 #pragma once
 #include <cuda.h>
 
-namespace mpw {
+#include "mpw_rhs_args.cuh"
 
-constexpr unsigned WAIT_LIMIT = 1u << 20;
+namespace mpw {
 
 __device__ __forceinline__ unsigned smem_u32(const void* p) {
   return (unsigned)__cvta_generic_to_shared(p);
@@ -19,9 +19,10 @@ __device__ __forceinline__ void bar_expect_tx(unsigned bar, unsigned bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
 
-// Bounded wait for phase `parity` of an mbarrier; false if the limit ran out.
-__device__ __forceinline__ bool bar_wait(unsigned bar, unsigned parity) {
-  for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+// Bounded wait for phase `parity` of an mbarrier: at most `limit` try-waits;
+// false if the limit ran out (a limit of 0 gives up at once).
+__device__ __forceinline__ bool bar_wait(unsigned bar, unsigned parity, unsigned limit = WAIT_LIMIT) {
+  for (unsigned it = 0; it < limit; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"

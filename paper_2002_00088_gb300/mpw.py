@@ -16,8 +16,9 @@ from .build import LIB_PATH
 # enums of include/mpw.h
 MPW_OK = 0
 STATUS_NAMES = {0: "MPW_OK", 1: "MPW_ERR_ARG", 2: "MPW_ERR_OVERLAP", 3: "MPW_ERR_CFL", 4: "MPW_ERR_TRAVERSAL",
-                5: "MPW_ERR_OUTSIDE", 6: "MPW_ERR_GHOST_UNFILLED", 7: "MPW_ERR_BOUNDS", 8: "MPW_ERR_TIMEOUT",
-                9: "MPW_ERR_CUDA", 10: "MPW_ERR_STATE"}
+                5: "MPW_ERR_OUTSIDE", 6: "MPW_ERR_GHOST_UNFILLED", 8: "MPW_ERR_TIMEOUT", 9: "MPW_ERR_CUDA",
+                10: "MPW_ERR_STATE"}
+ERR_ARG, ERR_CFL, ERR_GHOST_UNFILLED, ERR_TIMEOUT, ERR_CUDA = 1, 3, 6, 8, 9
 PATCH_GLOBAL, PATCH_LOCAL = 0, 1
 BC_ANALYTIC, BC_PERIODIC, BC_INTERPATCH = 0, 1, 2
 MOTION_STATIC, MOTION_LINEAR, MOTION_CIRCULAR, MOTION_ROTATING = 0, 1, 2, 3
@@ -59,6 +60,7 @@ SIGNATURES = {
     "mpw_get_flags": (C.c_int, [_vp, _vp]),
     "mpw_set_flags": (C.c_int, [_vp, _vp]),
     "mpw_fill_ghosts": (C.c_int, [_vp, C.c_double]),
+    "mpw_set_wait_limit": (C.c_int, [_vp, C.c_uint]),
     "mpw_step": (C.c_int, [_vp, C.c_double, C.c_int]),
     "mpw_live_points": (C.c_int, [_vp, C.POINTER(C.c_longlong)]),
     "mpw_profile_enable": (C.c_int, [_vp, C.c_int]),
@@ -122,9 +124,31 @@ lib = _load()
 NOALLOC_MAX_N = 48
 
 
+def check_noalloc_fields(n, psi, pi):
+    """Raise ValueError unless psi and pi are C-contiguous float64 CUDA tensors
+    of shape (n2, n1, n0) on the current device: the kernels read and write
+    exactly that many values through the raw pointers."""
+    torch = _torch()
+    want = (int(n[2]), int(n[1]), int(n[0]))
+    for name, a in (("psi", psi), ("pi", pi)):
+        if not isinstance(a, torch.Tensor):
+            raise ValueError(f"{name} must be a torch tensor")
+        if tuple(a.shape) != want:
+            raise ValueError(f"{name} has shape {tuple(a.shape)}, expected (n2, n1, n0) = {want}")
+        if a.dtype != torch.float64:
+            raise ValueError(f"{name} must be float64, not {a.dtype}")
+        if not a.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    for name, a in (("psi", psi), ("pi", pi)):
+        if not a.is_cuda or a.device.index != torch.cuda.current_device():
+            raise ValueError(f"{name} must live on the current CUDA device")
+
+
 def step_periodic_noalloc(n, lo, hi, ko_eps, dt, nsteps, psi, pi, stream=None):
     """mpw_step_periodic_noalloc on two CUDA float64 tensors of shape (n2, n1, n0),
-    advanced in place; nothing is allocated by the library."""
+    advanced in place; nothing is allocated by the library.  Returns once the
+    work has finished on the stream."""
+    check_noalloc_fields(n, psi, pi)
     nn = (C.c_int * 3)(*[int(v) for v in n])
     lo_ = (C.c_double * 3)(*[float(v) for v in lo])
     hi_ = (C.c_double * 3)(*[float(v) for v in hi])
@@ -305,6 +329,10 @@ class Multipatch:
 
     def fill_ghosts(self, t):
         check(lib.mpw_fill_ghosts(self.h, float(t)))
+
+    def set_wait_limit(self, limit):
+        """Try-waits allowed to the RHS kernels' pipeline waits (0: give up at once)."""
+        check(lib.mpw_set_wait_limit(self.h, int(limit)))
 
     def step(self, dt, nsteps=1):
         check(lib.mpw_step(self.h, float(dt), int(nsteps)))

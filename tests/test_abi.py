@@ -67,3 +67,36 @@ def test_surrogate_entry_points_validate_arguments(mpw_lib):
     assert L.mpw_sur_predict(None, None, None, 1, n, None, None) == 1           # null handle
     assert L.mpw_step_surrogate(None, None, 1e-3, 1, 1e-4, None, None) == 1     # null context
     assert L.mpw_sur_param_count() == sum(co * 27 * ci + co for ci, co in [(8, 32), (32, 32), (32, 32), (32, 8)])
+
+
+def test_wait_limit_entry_point_validates_its_context(mpw_lib):
+    assert mpw_lib.lib.mpw_set_wait_limit(None, 0) == 1
+
+
+def test_noalloc_refuses_bad_arguments_before_any_launch(mpw_lib):
+    """Host-side checks of the allocation-free entry point: sizes beyond the
+    fixed work array are refused by the library itself, and the Python
+    binding refuses tensors whose shape, dtype, layout or device would make
+    the kernels read or write outside them."""
+    import torch
+    L = mpw_lib.lib
+    fake = ctypes.c_void_p(256)            # never dereferenced: validation comes first
+    lo = (ctypes.c_double * 3)(0.0, 0.0, 0.0)
+    hi = (ctypes.c_double * 3)(1.0, 1.0, 1.0)
+    big = (ctypes.c_int * 3)(mpw_lib.NOALLOC_MAX_N + 1, 8, 8)
+    small = (ctypes.c_int * 3)(5, 8, 8)
+    assert L.mpw_step_periodic_noalloc(big, lo, hi, 0.005, 1e-3, 1, fake, fake, None) == mpw_lib.ERR_ARG
+    assert L.mpw_step_periodic_noalloc(small, lo, hi, 0.005, 1e-3, 1, fake, fake, None) == mpw_lib.ERR_ARG
+    n = (16, 8, 4)
+    good = torch.zeros((4, 8, 16), dtype=torch.float64)
+    cases = [
+        (torch.zeros((4, 8, 15), dtype=torch.float64), "shape"),
+        (torch.zeros((4, 8, 16), dtype=torch.float32), "float64"),
+        (torch.zeros((4, 16, 8), dtype=torch.float64).transpose(1, 2), "contiguous"),
+        (good, "CUDA device"),                 # a host tensor: no CUDA device here
+    ]
+    for bad, what in cases:
+        with pytest.raises(ValueError, match=what):
+            mpw_lib.check_noalloc_fields(n, bad, good)
+        with pytest.raises(ValueError, match=what):
+            mpw_lib.step_periodic_noalloc(n, (0, 0, 0), (1, 1, 1), 0.005, 1e-3, 1, good, bad)

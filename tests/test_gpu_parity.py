@@ -207,6 +207,25 @@ def test_orbiting_downscaled_many_steps(mpw_lib, arith):
     np.testing.assert_array_equal(g.get_flags(), o.get_flags())
 
 
+def test_orbiting_half_size_hundred_steps(mpw_lib):
+    """128^3 global + four orbiting 64^3 locals (the throughput workload at
+    half resolution), 100 steps: the parity bar of 1e-10 after 100 steps on a
+    moving layout, with the flags recomputed, cells revived and poisoned at
+    every step."""
+    w = wl.orbiting_gauss(scale=2)
+    o = oracle_from(w, THREADS)
+    g = gpu_from(mpw_lib, w)
+    seed_both(o, g, 5)
+    o.step(w.dt, 1)
+    g.step(w.dt, 1)
+    compare_fields(o, g, 5, 1e-12)
+    o.step(w.dt, 99)
+    g.step(w.dt, 99)
+    compare_fields(o, g, 5, 1e-10)
+    np.testing.assert_array_equal(g.get_flags(), o.get_flags())
+    assert g.time == o.time
+
+
 def test_orbiting_full_size_one_step(mpw_lib):
     """256^3 global + four 128^3 locals (the throughput workload), one step."""
     w = wl.orbiting_gauss()

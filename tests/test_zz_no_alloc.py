@@ -17,10 +17,14 @@ from paper_2002_00088_gb300 import workloads as wl
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_step_matches_context_step_twice(mpw_lib):
+@pytest.mark.parametrize("n", [(40, 24, 20), (48, 48, 48), (6, 7, 8)],
+                         ids=["ragged", "largest", "smallest"])
+def test_noalloc_step_matches_context_step_twice(mpw_lib, n):
+    """(48, 48, 48) fills the fixed work array exactly; (6, 7, 8) is the
+    smallest patch the entry point accepts."""
     import torch
     M = mpw_lib
-    n, lo, hi = (40, 24, 20), (-0.5, -0.3, -0.2), (0.5, 0.4, 0.3)
+    lo, hi = (-0.5, -0.3, -0.2), (0.5, 0.4, 0.3)
     ps, pi = wl.random_fields((n[2], n[1], n[0]), 7)
     h = min((hi[a] - lo[a]) / n[a] for a in range(3))
     dt = 0.1 * h
