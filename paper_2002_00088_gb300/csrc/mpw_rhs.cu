@@ -478,19 +478,19 @@ struct FxTerms {
   double fa[2], fb[2];   // alpha 2^S, beta 2^S (psi, Pi)
 };
 
-// q = round-half-away(x 2^(1074-E1)) for a binary64 x whose biased exponent
-// is at most E1 (|q| < 2^52); values of larger exponent (non-live cells only)
-// and values below 2^(E1-1086) give 0.
+// q = x 2^(1074-E1) to within one unit (the magnitude truncated, then the
+// sign applied as a one's complement: -q - 1 for negative x), for a binary64
+// x whose biased exponent is at most E1 (|q| < 2^52); values of larger
+// exponent (non-live cells only) and values below 2^(E1-1086) give 0 or -1.
 __device__ __forceinline__ long long to_fixed52(double x, int E1) {
   const int hi = __double2hiint(x);
   const unsigned lo = (unsigned)__double2loint(x);
   const unsigned mh = ((unsigned)hi & 0xFFFFFu) | 0x100000u;
-  const unsigned sh = (unsigned)(E1 - (int)(((unsigned)hi >> 20) & 0x7FFu));
+  const unsigned sh = (unsigned)(E1 + 1 - (int)(((unsigned)hi >> 20) & 0x7FFu));
   const unsigned long long m = ((unsigned long long)mh << 32) | lo;
   unsigned long long t;
   asm("shr.b64 %0, %1, %2;" : "=l"(t) : "l"(m), "r"(sh));  // shift amounts >= 64 give 0
-  const long long sgn = (long long)(hi >> 31);
-  return ((long long)(t ^ (unsigned long long)sgn) + 1) >> 1;
+  return (long long)(t ^ (unsigned long long)(long long)(hi >> 31));
 }
 
 // M = round(coef 2^(E1 - 1074 - S + 64)) as a signed-digit pair.
@@ -557,7 +557,94 @@ __device__ void fx_setup(FxTerms& T, const RhsPatch& P, int Es_raw, int Ep_raw, 
   T.fb[1] = scalbn(beta, Sp);
 }
 
-template <bool MOVING>
+// Two-plane pipeline of the fixed-point body.  Iteration k of a CTA
+// computes the output planes zb = z0 + 2k and zb + 1; its slot holds, in two
+// halves laid out like one RHS_DEPTH slot each, the raw tiles (with halo) of
+// input planes zb + 3 and zb + 4 and the stage operands u and ACC of planes
+// zb and zb + 1.  FX_DEPTH slots are in flight (four planes ahead).  The
+// z-neighbours live in an 8-deep register queue (planes zb - 3 .. zb + 4),
+// the x/y neighbours in a ring of FX_CONV converted planes: iteration k
+// reads planes zb and zb + 1 and, after its barrier, writes zb + 3 and zb + 4
+// into the slots of zb - 2 and zb - 1 (plane p sits in slot (p - z0) mod 5),
+// which iteration k - 1 read last; so one CTA barrier per iteration orders
+// every write after the last read of its slot, and every read after the
+// write (planes zb + 3, zb + 4 are read from iteration k + 1 on).
+constexpr int FX_DEPTH = 2;
+constexpr int FX_SLOT = 2 * SLOT_DOUBLES;
+constexpr int FX_CONV = 5;
+constexpr size_t FX_SMEM = 128 + sizeof(double) * FX_DEPTH * FX_SLOT +
+                           sizeof(long long) * FX_CONV * 2 * CONV_PLANE + 8 * FX_DEPTH;
+
+// Loads of iteration slot (output planes zb and, when nq = 2, zb + 1): one
+// transaction count for all of them on the slot's barrier.
+__device__ __forceinline__ void issue_pair(const RhsPatch& Pt, int stage, double* slot, unsigned bar, int i0, int j0,
+                                           int zb, int nq) {
+  const unsigned per = sizeof(double) * (TILE_DOUBLES + (stage < 3 ? PT_DOUBLES : 0) + (stage > 0 ? PT_DOUBLES : 0));
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  bar_expect_tx(bar, per * nq);
+  for (int q = 0; q < nq; ++q) {
+    double* sq = slot + q * SLOT_DOUBLES;
+    const int zz = zb + q;
+    tma_load_4d(smem_u32(sq), &Pt.ymap, i0 + Pt.g.xoff - 4, j0, zz + 3 + NG, 0, bar);
+    if (stage < 3) tma_load_4d(smem_u32(sq + TILE_DOUBLES), &Pt.umap, i0 + Pt.g.xoff, j0 + NG, zz + NG, 0, bar);
+    if (stage > 0)
+      tma_load_4d(smem_u32(sq + TILE_DOUBLES + PT_DOUBLES), &Pt.amap, i0 + Pt.g.xoff, j0 + NG, zz + NG, 0, bar);
+  }
+}
+
+// Multipliers of the stencil terms of one CTA, in registers (the D1
+// multipliers of a moving patch are read from shared memory where used).
+struct FxMul {
+  int v0[2], kos[2], d2[2], kop[2];
+};
+
+// K_psi / 2^Ss and K_Pi / 2^Sp of the point whose z column is q[C-3 .. C+3]
+// and whose converted x/y neighbours sit around rs (psi) and rp (Pi).
+template <bool MOVING, int C>
+__device__ __forceinline__ void fx_point(const long long (&qs)[8], const long long (&qp)[8], const long long* rs,
+                                         const long long* rp, const FxMul& M, const FxTerms& T, long long& ks,
+                                         long long& kp) {
+  constexpr int SY = RHS_TX + 6;
+  const long long u0 = qs[C], v0 = qp[C];
+  int ts = 0, tp = 0;
+  const long long u6 = 6 * u0, v6 = 6 * v0;
+  const long long T1 = (rs[-1] + rs[1] + rs[-SY]) + (rs[SY] + qs[C - 1] + qs[C + 1]) - u6;
+  const long long T2 = (rs[-2] + rs[2] + rs[-2 * SY]) + (rs[2 * SY] + qs[C - 2] + qs[C + 2]) - u6;
+  const long long T3 = (rs[-3] + rs[3] + rs[-3 * SY]) + (rs[3 * SY] + qs[C - 3] + qs[C + 3]) - u6;
+  const long long P1 = (rp[-1] + rp[1] + rp[-SY]) + (rp[SY] + qp[C - 1] + qp[C + 1]) - v6;
+  const long long P2 = (rp[-2] + rp[2] + rp[-2 * SY]) + (rp[2 * SY] + qp[C - 2] + qp[C + 2]) - v6;
+  const long long P3 = (rp[-3] + rp[3] + rp[-3 * SY]) + (rp[3 * SY] + qp[C - 3] + qp[C + 3]) - v6;
+  const long long T16 = T1 * 16;
+  const long long d2 = T16 - T2;
+  const long long kos = T3 - 6 * T2 + (T16 - T1);
+  const long long kop = P3 - 6 * P2 + 15 * P1;
+  ks = hi_pos(v0, M.v0, ts) + hi_pos(kos, M.kos, ts);
+  kp = hi_pos(d2, M.d2, tp) + hi_pos(kop, M.kop, tp);
+  if (MOVING) {
+    ks += (long long)ts;
+    kp += (long long)tp;
+    ts = 0;
+    tp = 0;
+    const long long dsx = 8 * (rs[1] - rs[-1]) - (rs[2] - rs[-2]);
+    const long long dsy = 8 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY]);
+    const long long dsz = 8 * (qs[C + 1] - qs[C - 1]) - (qs[C + 2] - qs[C - 2]);
+    const long long dpx = 8 * (rp[1] - rp[-1]) - (rp[2] - rp[-2]);
+    const long long dpy = 8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]);
+    const long long dpz = 8 * (qp[C + 1] - qp[C - 1]) - (qp[C + 2] - qp[C - 2]);
+    ks += hi_any(dsx, T.d1s[0], ts) + hi_any(dsy, T.d1s[1], ts);
+    ks += (long long)ts;
+    ts = 0;
+    ks += hi_any(dsz, T.d1s[2], ts);
+    kp += hi_any(dpx, T.d1p[0], tp) + hi_any(dpy, T.d1p[1], tp);
+    kp += (long long)tp;
+    tp = 0;
+    kp += hi_any(dpz, T.d1p[2], tp);
+  }
+  ks += (long long)ts;
+  kp += (long long)tp;
+}
+
+template <bool MOVING, int STAGE>
 __device__ __forceinline__ void rhs_fx_body(const RhsArgs& A, const RhsPatch& Pt, const int p, int lb,
                                             const FxTerms& T, double* slots, long long* conv,
                                             unsigned long long* bars, int& s_abort) {
@@ -571,10 +658,13 @@ __device__ __forceinline__ void rhs_fx_body(const RhsArgs& A, const RhsPatch& Pt
   const int i0 = tx * TX, j0 = ty * TY;
   const int i = i0 + li, j = j0 + lj;
   const int z0 = tz * Pt.zc, z1 = min(z0 + Pt.zc, g.n[2]);
-  const int stage = A.stage;
+  const int niter = (z1 - z0 + 1) / 2;
+  constexpr int stage = STAGE;
   if (threadIdx.x == 0)
-    for (int s = 0; s < RHS_DEPTH && z0 + s < z1; ++s)
-      issue_slot(Pt, stage, slots + s * SLOT_DOUBLES, smem_u32(&bars[s]), i0, j0, z0 + s);
+    for (int k = 0; k < FX_DEPTH && k < niter; ++k) {
+      const int zb = z0 + 2 * k;
+      issue_pair(Pt, stage, slots + k * FX_SLOT, smem_u32(&bars[k]), i0, j0, zb, zb + 1 < z1 ? 2 : 1);
+    }
   const bool in_box = (i < g.n[0] + NG) && (j < g.n[1] + NG);
   const bool in_xy = (i < g.n[0]) && (j < g.n[1]);
   bool check_flags = false;
@@ -607,9 +697,10 @@ __device__ __forceinline__ void rhs_fx_body(const RhsArgs& A, const RhsPatch& Pt
   const int E1s = T.E1s, E1p = T.E1p;
   const double* Ys = Pt.Y;
   const long long vol = g.vol, plane = g.plane;
-  auto conv_of = [&](int zz) -> long long* { return conv + ((zz - z0) & (CONV_SLOTS - 1)) * 2 * CONV_PLANE; };
-  // prologue: planes z0-3 .. z0+2 by plain loads (queue), z0 .. z0+2 also into the converted ring
-  long long qs[7], qp[7];
+  constexpr int CP2 = 2 * CONV_PLANE;  // one converted plane, both fields
+  // prologue: planes z0-3 .. z0+2 by plain loads (queue), z0 .. z0+2 also
+  // into ring slots 0 .. 2 (plane zz sits in slot (zz - z0) mod FX_CONV)
+  long long qs[8], qp[8];
   {
     const long long c0 = g.at(min(i, g.n[0] + NG - 1), min(j, g.n[1] + NG - 1), z0 - NG);
     const long long ch = h_ok ? g.at(hi_, hj, z0) : 0;
@@ -624,7 +715,7 @@ __device__ __forceinline__ void rhs_fx_body(const RhsArgs& A, const RhsPatch& Pt
         qp[o] = to_fixed52(Ys[c + vol], E1p);
       }
       if (o >= NG && zz < z1) {
-        long long* cv = conv_of(zz);
+        long long* cv = conv + (o - NG) * CP2;
         cv[own] = qs[o];
         cv[CONV_PLANE + own] = qp[o];
         if (h_ok) {
@@ -634,20 +725,18 @@ __device__ __forceinline__ void rhs_fx_body(const RhsArgs& A, const RhsPatch& Pt
         }
       }
     }
+    qs[6] = qs[7] = qp[6] = qp[7] = 0;
   }
-  // constants in registers
-  const int mv0[2] = {T.v0[0], T.v0[1]}, mkos[2] = {T.kos[0], T.kos[1]}, md2[2] = {T.d2[0], T.d2[1]},
-            mkop[2] = {T.kop[0], T.kop[1]};
-  int md1s[3][2], md1p[3][2];
+  FxMul M;
 #pragma unroll
-  for (int a = 0; a < 3; ++a)
-#pragma unroll
-    for (int k = 0; k < 2; ++k) {
-      md1s[a][k] = MOVING ? T.d1s[a][k] : 0;
-      md1p[a][k] = MOVING ? T.d1p[a][k] : 0;
-    }
+  for (int k = 0; k < 2; ++k) {
+    M.v0[k] = T.v0[k];
+    M.kos[k] = T.kos[k];
+    M.d2[k] = T.d2[k];
+    M.kop[k] = T.kop[k];
+  }
   const double fa_s = T.fa[0], fa_p = T.fa[1], fb_s = T.fb[0], fb_p = T.fb[1];
-  // output pointers advance one plane per iteration
+  // output pointers advance two planes per iteration
   const long long c_own = g.at(min(i, g.n[0] - 1), min(j, g.n[1] - 1), z0);
   double* outp = Pt.OUT + c_own;
   double* accp = Pt.ACC + c_own;
@@ -655,124 +744,152 @@ __device__ __forceinline__ void rhs_fx_body(const RhsArgs& A, const RhsPatch& Pt
   const long long fplane = (long long)g.n[0] * g.n[1];
   const int pt = lj * TX + li;
   unsigned emax_s = 0, emax_p = 0;
-  for (int z = z0; z < z1; ++z) {
-    const int it = z - z0;
-    const int s = it % RHS_DEPTH;
-    const double* sl = slots + s * SLOT_DOUBLES;
+  int cs = 0;  // ring slot of plane zb
+  for (int k = 0; k < niter; ++k) {
+    const int zb = z0 + 2 * k;
+    const bool two = zb + 1 < z1;
+    const int s = k % FX_DEPTH;
+    const double* sl = slots + s * FX_SLOT;
     const unsigned bar = smem_u32(&bars[s]);
-    int fl = FLAG_LIVE;
-    if (in_xy && check_flags) fl = *flagp & 3;
-    if (!bar_wait(bar, (unsigned)(it / RHS_DEPTH) & 1u, A.wait_limit)) s_abort = 1;
-    const double rs_own = sl[own_raw], rp_own = sl[BOX_X * BOX_Y + own_raw];
-    double rs_h = 0.0, rp_h = 0.0;
-    if (h_ok) {
-      rs_h = sl[halo_raw];
-      rp_h = sl[BOX_X * BOX_Y + halo_raw];
+    int fl0 = FLAG_LIVE, fl1 = FLAG_LIVE;
+    if (in_xy && check_flags) {
+      fl0 = flagp[0] & 3;
+      if (two) fl1 = flagp[fplane] & 3;
     }
-    double ua_s = 0.0, ua_p = 0.0, ub_s = 0.0, ub_p = 0.0;
+    if (!bar_wait(bar, (unsigned)(k / FX_DEPTH) & 1u, A.wait_limit)) s_abort = 1;
+    // raw values of input planes zb + 3 (half 0) and zb + 4 (half 1)
+    const double* sl1 = sl + SLOT_DOUBLES;
+    const double rs0 = sl[own_raw], rp0 = sl[BOX_X * BOX_Y + own_raw];
+    double rs1 = 0.0, rp1 = 0.0, hs0 = 0.0, hp0 = 0.0, hs1 = 0.0, hp1 = 0.0;
+    if (two) {
+      rs1 = sl1[own_raw];
+      rp1 = sl1[BOX_X * BOX_Y + own_raw];
+    }
+    if (h_ok) {
+      hs0 = sl[halo_raw];
+      hp0 = sl[BOX_X * BOX_Y + halo_raw];
+      if (two) {
+        hs1 = sl1[halo_raw];
+        hp1 = sl1[BOX_X * BOX_Y + halo_raw];
+      }
+    }
+    // stage operands of planes zb (half 0) and zb + 1 (half 1)
+    double ua_s0 = 0.0, ua_p0 = 0.0, ub_s0 = 0.0, ub_p0 = 0.0, ua_s1 = 0.0, ua_p1 = 0.0, ub_s1 = 0.0, ub_p1 = 0.0;
     if (stage < 3) {
-      ua_s = sl[TILE_DOUBLES + pt];
-      ua_p = sl[TILE_DOUBLES + TX * TY + pt];
+      ua_s0 = sl[TILE_DOUBLES + pt];
+      ua_p0 = sl[TILE_DOUBLES + TX * TY + pt];
+      if (two) {
+        ua_s1 = sl1[TILE_DOUBLES + pt];
+        ua_p1 = sl1[TILE_DOUBLES + TX * TY + pt];
+      }
     }
     if (stage > 0) {
-      ub_s = sl[TILE_DOUBLES + PT_DOUBLES + pt];
-      ub_p = sl[TILE_DOUBLES + PT_DOUBLES + TX * TY + pt];
+      ub_s0 = sl[TILE_DOUBLES + PT_DOUBLES + pt];
+      ub_p0 = sl[TILE_DOUBLES + PT_DOUBLES + TX * TY + pt];
+      if (two) {
+        ub_s1 = sl1[TILE_DOUBLES + PT_DOUBLES + pt];
+        ub_p1 = sl1[TILE_DOUBLES + PT_DOUBLES + TX * TY + pt];
+      }
     }
     __syncthreads();
     if (s_abort) {
       // drain this CTA's copies still in flight (bounded), report, leave
       if (threadIdx.x == 0) {
         atomicOr(A.err, ERR_TIMEOUT);
-        for (int k = it; k < it + RHS_DEPTH && z0 + k < z1; ++k)
-          bar_wait(smem_u32(&bars[k % RHS_DEPTH]), (unsigned)(k / RHS_DEPTH) & 1u);
+        for (int m = k; m < k + FX_DEPTH && m < niter; ++m)
+          bar_wait(smem_u32(&bars[m % FX_DEPTH]), (unsigned)(m / FX_DEPTH) & 1u);
       }
       return;
     }
-    if (threadIdx.x == 0 && z + RHS_DEPTH < z1)
-      issue_slot(Pt, stage, slots + s * SLOT_DOUBLES, bar, i0, j0, z + RHS_DEPTH);
-    qs[6] = to_fixed52(rs_own, E1s);
-    qp[6] = to_fixed52(rp_own, E1p);
-    const bool live = in_xy && (fl == FLAG_LIVE || fl == FLAG_REVIVED);
-    const long long* rs = conv_of(z) + own;
-    const long long* rp = rs + CONV_PLANE;
-    const long long u0 = qs[3], v0 = qp[3];
-    long long ks = 0, kp = 0;
-    int ts = 0, tp = 0;
-    const long long u6 = 6 * u0, v6 = 6 * v0;
-    const long long T1 = (rs[-1] + rs[1] + rs[-SY]) + (rs[SY] + qs[2] + qs[4]) - u6;
-    const long long T2 = (rs[-2] + rs[2] + rs[-2 * SY]) + (rs[2 * SY] + qs[1] + qs[5]) - u6;
-    const long long T3 = (rs[-3] + rs[3] + rs[-3 * SY]) + (rs[3 * SY] + qs[0] + qs[6]) - u6;
-    const long long P1 = (rp[-1] + rp[1] + rp[-SY]) + (rp[SY] + qp[2] + qp[4]) - v6;
-    const long long P2 = (rp[-2] + rp[2] + rp[-2 * SY]) + (rp[2 * SY] + qp[1] + qp[5]) - v6;
-    const long long P3 = (rp[-3] + rp[3] + rp[-3 * SY]) + (rp[3 * SY] + qp[0] + qp[6]) - v6;
-    const long long T16 = T1 * 16;
-    const long long d2 = T16 - T2;
-    const long long kos = T3 - 6 * T2 + (T16 - T1);
-    const long long kop = P3 - 6 * P2 + 15 * P1;
-    ks = hi_pos(v0, mv0, ts) + hi_pos(kos, mkos, ts);
-    kp = hi_pos(d2, md2, tp) + hi_pos(kop, mkop, tp);
-    if (MOVING) {
-      ks += (long long)ts;
-      kp += (long long)tp;
-      ts = 0;
-      tp = 0;
-      const long long dsx = 8 * (rs[1] - rs[-1]) - (rs[2] - rs[-2]);
-      const long long dsy = 8 * (rs[SY] - rs[-SY]) - (rs[2 * SY] - rs[-2 * SY]);
-      const long long dsz = 8 * (qs[4] - qs[2]) - (qs[5] - qs[1]);
-      const long long dpx = 8 * (rp[1] - rp[-1]) - (rp[2] - rp[-2]);
-      const long long dpy = 8 * (rp[SY] - rp[-SY]) - (rp[2 * SY] - rp[-2 * SY]);
-      const long long dpz = 8 * (qp[4] - qp[2]) - (qp[5] - qp[1]);
-      ks += hi_any(dsx, md1s[0], ts) + hi_any(dsy, md1s[1], ts);
-      ks += (long long)ts;
-      ts = 0;
-      ks += hi_any(dsz, md1s[2], ts);
-      kp += hi_any(dpx, md1p[0], tp) + hi_any(dpy, md1p[1], tp);
-      kp += (long long)tp;
-      tp = 0;
-      kp += hi_any(dpz, md1p[2], tp);
+    if (threadIdx.x == 0 && k + FX_DEPTH < niter) {
+      const int zn = zb + 2 * FX_DEPTH;
+      issue_pair(Pt, stage, slots + s * FX_SLOT, bar, i0, j0, zn, zn + 1 < z1 ? 2 : 1);
     }
-    ks += (long long)ts;
-    kp += (long long)tp;
-    // ---- RK4 stage combination (FP64): K = k 2^S, folded into alpha, beta
-    const double Ks = (double)ks, Kp = (double)kp;
-    double os, op;
-    if (stage == 3) {
-      os = fma(fa_s, Ks, ub_s);
-      op = fma(fa_p, Kp, ub_p);
-    } else {
-      const double as = stage == 0 ? ua_s : ub_s;
-      const double ap = stage == 0 ? ua_p : ub_p;
-      os = fma(fa_s, Ks, ua_s);
-      op = fma(fa_p, Kp, ua_p);
-      if (live) {
-        accp[0] = fma(fb_s, Ks, as);
-        accp[vol] = fma(fb_p, Kp, ap);
+    qs[6] = to_fixed52(rs0, E1s);
+    qp[6] = to_fixed52(rp0, E1p);
+    qs[7] = to_fixed52(rs1, E1s);
+    qp[7] = to_fixed52(rp1, E1p);
+    // planes zb + 3 and zb + 4 into the ring (read from iterations k + 1 and
+    // k + 2); their slots last held planes zb - 2 and zb - 1, which the
+    // barrier above retired
+    {
+      const int c3 = cs + 3 >= FX_CONV ? cs + 3 - FX_CONV : cs + 3;
+      const int c4 = cs + 4 >= FX_CONV ? cs + 4 - FX_CONV : cs + 4;
+      long long* cv3 = conv + c3 * CP2;
+      long long* cv4 = conv + c4 * CP2;
+      cv3[own] = qs[6];
+      cv3[CONV_PLANE + own] = qp[6];
+      cv4[own] = qs[7];
+      cv4[CONV_PLANE + own] = qp[7];
+      if (h_ok) {
+        cv3[hoff] = to_fixed52(hs0, E1s);
+        cv3[CONV_PLANE + hoff] = to_fixed52(hp0, E1p);
+        cv4[hoff] = to_fixed52(hs1, E1s);
+        cv4[CONV_PLANE + hoff] = to_fixed52(hp1, E1p);
       }
     }
-    if (live) {
-      outp[0] = os;
-      outp[vol] = op;
-      emax_s = max(emax_s, (unsigned)__double2hiint(os) & 0x7FFFFFFFu);
-      emax_p = max(emax_p, (unsigned)__double2hiint(op) & 0x7FFFFFFFu);
-    }
-    // plane z+3 into the converted ring (read from iteration z+3 on)
+    const int cs1 = cs + 1 == FX_CONV ? 0 : cs + 1;
+    // ---- output plane zb
     {
-      long long* cv = conv_of(z + NG);
-      cv[own] = qs[6];
-      cv[CONV_PLANE + own] = qp[6];
-      if (h_ok) {
-        cv[hoff] = to_fixed52(rs_h, E1s);
-        cv[CONV_PLANE + hoff] = to_fixed52(rp_h, E1p);
+      const long long* rs = conv + cs * CP2 + own;
+      long long ks, kp;
+      fx_point<MOVING, 3>(qs, qp, rs, rs + CONV_PLANE, M, T, ks, kp);
+      const double Ks = (double)ks, Kp = (double)kp;
+      const bool live = in_xy && (fl0 == FLAG_LIVE || fl0 == FLAG_REVIVED);
+      double os, op;
+      if (stage == 3) {
+        os = fma(fa_s, Ks, ub_s0);
+        op = fma(fa_p, Kp, ub_p0);
+      } else {
+        os = fma(fa_s, Ks, ua_s0);
+        op = fma(fa_p, Kp, ua_p0);
+        if (live) {
+          accp[0] = fma(fb_s, Ks, stage == 0 ? ua_s0 : ub_s0);
+          accp[vol] = fma(fb_p, Kp, stage == 0 ? ua_p0 : ub_p0);
+        }
+      }
+      if (live) {
+        outp[0] = os;
+        outp[vol] = op;
+        emax_s = max(emax_s, (unsigned)__double2hiint(os) & 0x7FFFFFFFu);
+        emax_p = max(emax_p, (unsigned)__double2hiint(op) & 0x7FFFFFFFu);
+      }
+    }
+    // ---- output plane zb + 1
+    if (two) {
+      const long long* rs = conv + cs1 * CP2 + own;
+      long long ks, kp;
+      fx_point<MOVING, 4>(qs, qp, rs, rs + CONV_PLANE, M, T, ks, kp);
+      const double Ks = (double)ks, Kp = (double)kp;
+      const bool live = in_xy && (fl1 == FLAG_LIVE || fl1 == FLAG_REVIVED);
+      double os, op;
+      if (stage == 3) {
+        os = fma(fa_s, Ks, ub_s1);
+        op = fma(fa_p, Kp, ub_p1);
+      } else {
+        os = fma(fa_s, Ks, ua_s1);
+        op = fma(fa_p, Kp, ua_p1);
+        if (live) {
+          accp[plane] = fma(fb_s, Ks, stage == 0 ? ua_s1 : ub_s1);
+          accp[plane + vol] = fma(fb_p, Kp, stage == 0 ? ua_p1 : ub_p1);
+        }
+      }
+      if (live) {
+        outp[plane] = os;
+        outp[plane + vol] = op;
+        emax_s = max(emax_s, (unsigned)__double2hiint(os) & 0x7FFFFFFFu);
+        emax_p = max(emax_p, (unsigned)__double2hiint(op) & 0x7FFFFFFFu);
       }
     }
 #pragma unroll
     for (int o = 0; o < 6; ++o) {
-      qs[o] = qs[o + 1];
-      qp[o] = qp[o + 1];
+      qs[o] = qs[o + 2];
+      qp[o] = qp[o + 2];
     }
-    outp += plane;
-    accp += plane;
-    flagp += fplane;
+    cs = cs + 2 >= FX_CONV ? cs + 2 - FX_CONV : cs + 2;
+    outp += 2 * plane;
+    accp += 2 * plane;
+    flagp += 2 * fplane;
   }
   // exponent bookkeeping of the output buffer (consumed by the next substage)
   int es = (int)(emax_s >> 20), ep = (int)(emax_p >> 20);
@@ -804,10 +921,10 @@ __device__ __forceinline__ void rhs_fx(const RhsArgs& A, const int b) {
   extern __shared__ unsigned char smem_dyn[];
   __shared__ FxTerms T;
   __shared__ int s_abort;
-  const unsigned long long base = (reinterpret_cast<unsigned long long>(smem_dyn) + 1023ull) & ~1023ull;
+  const unsigned long long base = (reinterpret_cast<unsigned long long>(smem_dyn) + 127ull) & ~127ull;
   double* slots = reinterpret_cast<double*>(base);
-  long long* conv = reinterpret_cast<long long*>(slots + RHS_DEPTH * SLOT_DOUBLES);
-  unsigned long long* bars = reinterpret_cast<unsigned long long*>(conv + CONV_SLOTS * 2 * CONV_PLANE);
+  long long* conv = reinterpret_cast<long long*>(slots + FX_DEPTH * FX_SLOT);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(conv + FX_CONV * 2 * CONV_PLANE);
   int p = 0;
   while (p + 1 < A.np && b >= A.p[p + 1].block0) ++p;
   const RhsPatch& Pt = A.p[p];
@@ -825,7 +942,7 @@ __device__ __forceinline__ void rhs_fx(const RhsArgs& A, const int b) {
     fx_setup(T, Pt, Es, Ep, A.alpha, A.beta);
     s_abort = 0;
     if (T.ok) {
-      for (int s = 0; s < RHS_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
+      for (int s = 0; s < FX_DEPTH; ++s) bar_init(smem_u32(&bars[s]), 1);
       asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     }
@@ -836,10 +953,16 @@ __device__ __forceinline__ void rhs_fx(const RhsArgs& A, const int b) {
     return;
   }
   const int lb = b - Pt.block0;
-  if (Pt.moving)
-    rhs_fx_body<true>(A, Pt, p, lb, T, slots, conv, bars, s_abort);
-  else
-    rhs_fx_body<false>(A, Pt, p, lb, T, slots, conv, bars, s_abort);
+  switch (A.stage * 2 + (Pt.moving ? 1 : 0)) {
+    case 0: rhs_fx_body<false, 0>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+    case 1: rhs_fx_body<true, 0>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+    case 2: rhs_fx_body<false, 1>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+    case 3: rhs_fx_body<true, 1>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+    case 4: rhs_fx_body<false, 2>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+    case 5: rhs_fx_body<true, 2>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+    case 6: rhs_fx_body<false, 3>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+    default: rhs_fx_body<true, 3>(A, Pt, p, lb, T, slots, conv, bars, s_abort); break;
+  }
 }
 
 template <int TX, int TY, bool FIXED, bool ROT>
@@ -895,11 +1018,15 @@ bool encode_rhs_map(CUtensorMap* map, const void* base, const Geom& g, bool tile
   return r == CUDA_SUCCESS;
 }
 
+// Dynamic shared memory of the RHS kernels: the larger of the layouts of
+// rhs_body (RHS_SMEM) and of the two-plane fixed-point body (FX_SMEM).
+constexpr size_t RHS_KERNEL_SMEM = RHS_SMEM > FX_SMEM ? RHS_SMEM : FX_SMEM;
+
 template <bool FIXED, bool ROT>
 static void launch_rhs_batch_t(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, cudaStream_t s) {
   cudaFuncSetAttribute(k_rhs_batch<RHS_TX, RHS_TY, FIXED, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)RHS_SMEM);
-  k_rhs_batch<RHS_TX, RHS_TY, FIXED, ROT><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, s>>>(d_args, d_blk0, ninst);
+                       (int)RHS_KERNEL_SMEM);
+  k_rhs_batch<RHS_TX, RHS_TY, FIXED, ROT><<<blocks, RHS_TX * RHS_TY, RHS_KERNEL_SMEM, s>>>(d_args, d_blk0, ninst);
 }
 
 void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int blocks, bool fixed, bool rot,
@@ -916,8 +1043,8 @@ void launch_rhs_batch(const RhsArgs* d_args, const int* d_blk0, int ninst, int b
 template <bool FIXED, bool ROT>
 static void launch_rhs_t(const RhsArgs& a, int blocks, cudaStream_t s) {
   cudaFuncSetAttribute(k_rhs<RHS_TX, RHS_TY, FIXED, ROT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)RHS_SMEM);
-  k_rhs<RHS_TX, RHS_TY, FIXED, ROT><<<blocks, RHS_TX * RHS_TY, RHS_SMEM, s>>>(a);
+                       (int)RHS_KERNEL_SMEM);
+  k_rhs<RHS_TX, RHS_TY, FIXED, ROT><<<blocks, RHS_TX * RHS_TY, RHS_KERNEL_SMEM, s>>>(a);
 }
 
 void launch_rhs(const RhsArgs& a, int blocks, bool fixed, bool rot, void* stream) {
