@@ -51,6 +51,15 @@ mpw_status mpw_conv3_forward(const uint16_t* x, int cin, const uint16_t* w, cons
                              int batch, const int n[3], int relu, const uint16_t* mask, uint16_t* y, float* y32,
                              void* stream);
 
+/* Forward kernel selection (process-wide; no counterpart in the paper).
+ * kernel = 0 (default): volumes with n0 = 128 run on the tcgen05 tensor-core
+ * kernel (TMEM accumulators, one x-row of 128 points per MMA), every other
+ * volume on the mma.sync kernel; kernel = 1: the mma.sync kernel always (the
+ * parity reference of the tcgen05 one).  Applies to mpw_conv3_forward,
+ * mpw_conv3_backward_data and everything built on them.  Not thread-safe
+ * against concurrent launches.  Errors: MPW_ERR_ARG for another value. */
+mpw_status mpw_conv3_select(int kernel);
+
 /* Gradient with respect to the input of a layer with weights W[cout][27][cin]:
  *     gx[p][ci] = sum_{tap, co} gy[p - off(tap)][co] * W[co][tap][ci]
  * multiplied by 1[mask[p][ci] > 0] when mask (the layer's input activation,

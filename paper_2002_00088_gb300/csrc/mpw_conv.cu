@@ -2,7 +2,11 @@
 // include/mpw_surrogate.h): periodic 3x3x3 convolution, its input and weight
 // gradients, Adam and the squared-error gradient.
 //
-// Implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32 accumulation):
+// Forward and input gradient of volumes 128 points wide run on the
+// 5th-generation tensor cores (k_conv3_tc, tcgen05.mma with TMEM
+// accumulators; described below).  Every other volume, and the weight
+// gradient, use an implicit GEMM on mma.sync m16n8k16 (BF16 operands, FP32
+// accumulation):
 //  - k_conv3_t<CIN, COUT>: M = points (a warp owns 16 x-points on two
 //    planes), N = output channels, K = 27 taps x CIN.  A persistent CTA
 //    stages the layer's weights once and the periodic 18 x 10 x 4 halo of
@@ -13,6 +17,8 @@
 //  - k_conv3_wgrad: M = output channels, N = input channels, K = points; each
 //    CTA keeps its partial sums in registers over its blocks and k_sum_parts
 //    adds the partials in a fixed order (deterministic).
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -22,6 +28,7 @@
 
 #include "../../include/mpw_surrogate.h"
 #include "mpw_internal.cuh"
+#include "mpw_tma.cuh"
 
 namespace mpw {
 namespace {
@@ -114,8 +121,6 @@ struct FwdArgs {
 
 constexpr int HZ2 = 4;
 constexpr int HPTS2 = HX * HY * HZ2;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
@@ -239,6 +244,418 @@ __global__ void __launch_bounds__(FWD_THREADS, 2) k_conv3_t(const FwdArgs A) {
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 path (volumes 128 points wide, n0 = 128): forward and input
+// gradient as an implicit GEMM on the 5th-generation tensor cores.
+//  - One MMA (tcgen05.mma.cta_group::1.kind::f16, BF16 operands, FP32
+//    accumulation in TMEM) multiplies an input x-row, unshifted (A: M = 128
+//    points x K = 16 channels), by the weights of the three x-taps of one
+//    (dz, dy) stacked along N (B: N = 3 x COUT, the last layer's 24 padded
+//    to 32).  Accumulated over the (dz, dy) rows and the channels, column
+//    dx * COUT + c of accumulator lane p holds sum W[c][tap(dz, dy, dx)] .
+//    x[p]; the epilogue forms the output as D_0[p - 1] + D_1[p] + D_2[p + 1]
+//    (periodic in p), by one-lane warp shuffles and, across the four warps,
+//    through shared memory.  18 MMAs per row with 32 input channels (two
+//    K = 16 steps per (dz, dy) row), 6 with 8 (the K halves are two z-rows
+//    of one dy: (dz 0, 1) and (dz 1 with zero weights, dz 2)).  A K = 16
+//    MMA costs about the same time for N = 32 as for N = 96 on GB300, so
+//    stacking the taps along N cuts the MMA time of a row threefold.
+//  - Operands in shared memory, K-major without swizzle.  An input row is
+//    stored channel-group-major, [channel / 8][128 points][8 channels]:
+//    the 8 x 8 core matrices are 8 consecutive 16-byte point rows (128 B),
+//    so the stride along M is 128 B (SBO) and the next channel group, along
+//    K, is 2048 B away (LBO).  Weights: [mma][K half][N][8 channels].
+//  - Input rows arrive by TMA (one box per input x-row, landing
+//    channel-group-major) into a ring of y-slots x 3 z-rows indexed by a running
+//    count of loaded rows, so that consecutive chunks flow through the ring
+//    without draining it.
+//  - Warp roles: warp 8 (one thread) issues the TMA loads, warp 9 (one
+//    thread) the MMAs,
+//    warps 0-7 read the accumulator (thread = point of TMEM lane quadrant
+//    w % 4), combine the taps, add the bias, apply ReLU / mask and store;
+//    warps 0-3 take the even rows and warps 4-7 the odd ones, so that each
+//    group has two rows' time per row.  Four accumulators rotate;
+//    mbarriers hand rows between the roles (an input row landed, an input
+//    row's last MMAs done, a row's MMAs done, an accumulator read).  Every wait is bounded; a wait that runs out makes
+//    the CTA stop issuing work and report through the error word.
+namespace tc {
+constexpr int M = 128;
+constexpr int THREADS = 320;   // warps 0-7: epilogue; warp 8: loads; warp 9: MMAs
+constexpr int EPI = 256;       // epilogue threads
+constexpr int ALIGN = 1024;    // of the smem carve-up (the 64-byte swizzle repeats every 512 B)
+template <int COUT>
+__host__ __device__ constexpr int nt() { return COUT == 32 ? 96 : 32; }
+constexpr int NBUF = 4;        // TMEM accumulators
+template <int COUT>
+__host__ __device__ constexpr int tmem_cols() { return COUT == 32 ? 512 : 128; }
+template <int CIN>
+__host__ __device__ constexpr int nmma() { return CIN == 32 ? 18 : 6; }
+template <int CIN>
+__host__ __device__ constexpr int row_bytes() { return M * CIN * 2; }
+// y-slots of the input ring (three z-rows each): 3 in use, the rest in flight
+template <int CIN>
+__host__ __device__ constexpr int slots() { return CIN == 32 ? 6 : 8; }
+template <int CIN, int COUT>
+__host__ __device__ constexpr int w_bytes() { return nmma<CIN>() * 2 * nt<COUT>() * 16; }
+// weights | ring | boundary exchange (2 groups x 2 parities x 2 sides x 4
+// quadrants x COUT floats) | barriers (full, done, freed)
+template <int CIN, int COUT>
+__host__ __device__ constexpr int smem_bytes() {
+  return ALIGN + w_bytes<CIN, COUT>() + slots<CIN>() * 3 * row_bytes<CIN>() + 2 * 2 * 2 * 4 * COUT * 4 +
+         8 * (2 * slots<CIN>() + 2 * NBUF) + 16;
+}
+
+// Instruction descriptor of kind::f16: D F32, A and B BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+// Shared-memory matrix descriptor (64 bits, K-major): start address >> 4 in
+// bits 0-13, leading-dimension byte offset (between core matrices along K)
+// >> 4 in bits 16-29, stride-dimension byte offset (between groups of eight
+// rows along M or N) >> 4 in bits 32-45, the descriptor version 1 in bit 46,
+// the swizzle mode in bits 61-63.
+//  - sdesc: no swizzle, rows of 16 bytes 128 bytes apart per eight rows;
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo) {
+  return ((uint64_t)((128u >> 4) | (1u << 14)) << 32) | ((addr >> 4) | ((lbo >> 4) << 16));
+}
+//  - sdesc_sw64: 64-byte swizzle (mode 4), rows of 64 bytes (32 channels), the
+//    eight-row groups 512 bytes apart; the leading offset is unused because a
+//    K step of 16 channels stays inside one 64-byte row.  The K half of a
+//    row is selected by adding 32 bytes to the start address: the swizzle is
+//    applied to the final address bits, so the offset composes with it.
+__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
+  return ((uint64_t)((512u >> 4) | (1u << 14) | (4u << 29)) << 32) | ((addr >> 4) | (1u << 16));
+}
+
+__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(id), "r"(acc));
+}
+
+__device__ __forceinline__ void commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void ld8(uint32_t taddr, float (&v)[8]) {
+  uint32_t r[8];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16,%17,%18,%19,"
+      "%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]),
+        "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
+        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// The output rows of a CTA: an even share of the batch x n2 x n1 rows, in
+// (b, z, y) order, cut into chunks at the plane boundaries (a chunk is one
+// (b, z) and consecutive y).  Every role of the CTA walks the same sequence.
+struct Chunks {
+  long long cur, end;
+  int n1, n2;
+  __device__ Chunks(long long total, int n1_, int n2_)
+      : cur(total * blockIdx.x / gridDim.x), end(total * (blockIdx.x + 1) / gridDim.x), n1(n1_), n2(n2_) {}
+  __device__ bool next(int& b, int& z, int& yb, int& R) {
+    if (cur >= end) return false;
+    const long long plane = cur / n1;
+    yb = (int)(cur - plane * n1);
+    R = (int)min(end - cur, (long long)(n1 - yb));
+    z = (int)(plane % n2);
+    b = (int)(plane / n2);
+    cur += R;
+    return true;
+  }
+};
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int r, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+      ::"r"(dst), "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(r), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void bar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+}  // namespace tc
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    k_conv3_tc(const FwdArgs A, const __grid_constant__ CUtensorMap xmap, int* err) {
+  using namespace tc;
+  constexpr int NT = nt<COUT>(), NM = nmma<CIN>(), RB = row_bytes<CIN>(), NG8 = COUT / 8;
+  constexpr int SLOTS = slots<CIN>();
+  constexpr uint32_t ID = idesc(M, NT);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned long long sbase =
+      (reinterpret_cast<unsigned long long>(smem) + (ALIGN - 1)) & ~(unsigned long long)(ALIGN - 1);
+  unsigned char* Ws = reinterpret_cast<unsigned char*>(sbase);
+  unsigned char* Xs = Ws + w_bytes<CIN, COUT>();
+  float* bnd = reinterpret_cast<float*>(Xs + SLOTS * 3 * RB);  // [group][parity][side][quadrant][COUT]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(bnd + 2 * 2 * 2 * 4 * COUT);
+  unsigned long long* empty = full + SLOTS;    // an input row's last MMAs done
+  unsigned long long* done = empty + SLOTS;    // MMAs of an accumulator committed
+  unsigned long long* freed = done + NBUF;     // accumulator read by the epilogue
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(freed + NBUF);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ws_a = smem_u32(Ws), xs_a = smem_u32(Xs);
+  // ---- weights: [mma][K half][n = dx * COUT + c][8 channels], zero outside
+  {
+    __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(Ws);
+    for (int i = tid; i < NM * 2 * NT * 8; i += THREADS) {
+      const int e = i % 8, n = (i / 8) % NT, kh = (i / (8 * NT)) % 2, j = i / (16 * NT);
+      const int dx = n / COUT, co = n % COUT;
+      int dz, dy, ch;
+      if (CIN == 32) {
+        dz = (j / 2) / 3;
+        dy = (j / 2) % 3;
+        ch = 16 * (j % 2) + 8 * kh + e;
+      } else {
+        dy = j / 2;
+        const int pair = j % 2;
+        dz = (pair == 1 && kh == 0) ? -1 : pair + kh;
+        ch = e;
+      }
+      __nv_bfloat16 v = __float2bfloat16(0.0f);
+      if (dx < 3 && dz >= 0) {
+        const int tap = (dz * 3 + dy) * 3 + dx;
+        v = A.flip ? A.w[((long long)ch * 27 + 26 - tap) * COUT + co] : A.w[((long long)co * 27 + tap) * CIN + ch];
+      }
+      W[i] = v;
+    }
+  }
+  __shared__ __align__(16) float sbias[COUT];
+  if (tid < COUT) sbias[tid] = A.bias ? A.bias[tid] : 0.0f;
+  if (tid == 0) {
+    for (int q = 0; q < SLOTS; ++q) {
+      bar_init(smem_u32(&full[q]), 1);
+      bar_init(smem_u32(&empty[q]), 1);
+    }
+    for (int q = 0; q < NBUF; ++q) {
+      bar_init(smem_u32(&done[q]), 1);
+      bar_init(smem_u32(&freed[q]), EPI / 2);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)),
+                 "r"(tmem_cols<COUT>()));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // weights -> tensor core
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int n1 = A.v.n1, n2 = A.v.n2;
+  const long long nrows = (long long)A.v.batch * n2 * n1;
+  if (warp == 8) {
+    // ================= TMA loads (one thread): every input row of every
+    // chunk, in order; load L goes into slot L mod SLOTS once the MMAs that
+    // read the slot's previous row are done
+    if (lane == 0) {
+      long long L = 0;
+      bool stop = false;
+      Chunks ch(nrows, n1, n2);
+      int b, z, yb, R;
+      while (!stop && ch.next(b, z, yb, R)) {
+        for (int u = 0; u < R + 2; ++u, ++L) {
+          const int q = (int)(L % SLOTS);
+          if (L >= SLOTS && !bar_wait(smem_u32(&empty[q]), (unsigned)(((L - SLOTS) / SLOTS) & 1))) {
+            stop = true;
+            break;
+          }
+          const uint32_t bar = smem_u32(&full[q]);
+          bar_expect_tx(bar, 3 * RB);
+          const int yy = wrap1(yb - 1 + u, n1);
+#pragma unroll
+          for (int dz = 0; dz < 3; ++dz) {
+            const int row = ((b * n2) + wrap1(z + dz - 1, n2)) * n1 + yy;
+            tma_load_3d(xs_a + (uint32_t)((q * 3 + dz) * RB), &xmap, 0, 0, row, bar);
+          }
+        }
+      }
+      if (stop) {
+        if (err) atomicOr(err, ERR_TIMEOUT);
+        // the copies still in flight land (bounded) before the CTA exits
+        for (long long l = L - SLOTS; l < L; ++l)
+          if (l >= 0) bar_wait(smem_u32(&full[l % SLOTS]), (unsigned)((l / SLOTS) & 1));
+      }
+    }
+  } else if (warp == 9) {
+    // ================= MMAs (one thread)
+    if (lane == 0) {
+      long long L0 = 0, grow = 0;
+      bool stop = false;
+      Chunks ch(nrows, n1, n2);
+      int b, z, yb, R;
+      while (!stop && ch.next(b, z, yb, R)) {
+        for (int r = 0; r < R && !stop; ++r, ++grow) {
+          // input rows r, r + 1, r + 2 of the chunk (loads L0 + r + dy);
+          // all but the last were waited for by the rows before
+          uint32_t rowa[3];
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy) {
+            const long long l = L0 + r + dy;
+            const int q = (int)(l % SLOTS);
+            if ((dy == 2 || r == 0) && !stop && !bar_wait(smem_u32(&full[q]), (unsigned)((l / SLOTS) & 1)))
+              stop = true;
+            rowa[dy] = xs_a + (uint32_t)(q * 3 * RB);
+          }
+          const int buf = (int)(grow & (NBUF - 1));
+          if (grow >= NBUF && !stop &&
+              !bar_wait(smem_u32(&freed[buf]), (unsigned)(((grow - NBUF) / NBUF) & 1)))
+            stop = true;
+          if (stop) break;
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(buf * NT);
+#pragma unroll
+          for (int j = 0; j < NM; ++j) {
+            const int dy = CIN == 32 ? (j / 2) % 3 : j / 2;
+            const int dz = CIN == 32 ? (j / 2) / 3 : j % 2;       // dz of the first K half
+            const uint32_t a = rowa[dy] + (uint32_t)(dz * RB);
+            const uint32_t bw = ws_a + (uint32_t)(j * 2 * NT * 16);
+            const uint64_t da = CIN == 32 ? sdesc_sw64(a + (uint32_t)(32 * (j % 2))) : sdesc(a, RB);
+            mma(d, da, sdesc(bw, NT * 16), ID, j > 0);
+          }
+          commit(smem_u32(&done[buf]));
+          // input row r is read by no later row of the chunk; the chunk's
+          // last row also retires rows R and R + 1
+          commit(smem_u32(&empty[(L0 + r) % SLOTS]));
+          if (r == R - 1) {
+            commit(smem_u32(&empty[(L0 + R) % SLOTS]));
+            commit(smem_u32(&empty[(L0 + R + 1) % SLOTS]));
+          }
+        }
+        L0 += R + 2;
+      }
+      if (stop && err) atomicOr(err, ERR_TIMEOUT);
+    }
+  } else {
+    // ================= epilogue: thread = point p of the row; group
+    // `grp` takes the rows of its parity
+    const int quad = warp & 3, grp = warp >> 2;
+    const int p = 32 * quad + lane;
+    long long grow = 0;
+    bool stop = false;
+    Chunks ch(nrows, n1, n2);
+    int b, z, yb, R;
+    while (!stop && ch.next(b, z, yb, R)) {
+      for (int r = 0; r < R; ++r, ++grow) {
+        if ((int)(grow & 1) != grp) continue;
+        const int buf = (int)(grow & (NBUF - 1));
+        // the group's threads stop together if any wait ran out, so that
+        // none is left at a named barrier
+        const unsigned ok = bar_wait(smem_u32(&done[buf]), (unsigned)((grow / NBUF) & 1)) ? 1u : 0u;
+        int any_fail;
+        if (grp == 0)
+          asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, 128, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+                       : "=r"(any_fail) : "r"(ok) : "memory");
+        else
+          asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 2, 128, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+                       : "=r"(any_fail) : "r"(ok) : "memory");
+        if (any_fail) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float d0[COUT], d1[COUT], d2[COUT];
+        const uint32_t t0 = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * NT);
+        if constexpr (COUT == 32) {
+          ld32(t0, d0);
+          ld32(t0 + 32u, d1);
+          ld32(t0 + 64u, d2);
+        } else {
+          ld8(t0, d0);
+          ld8(t0 + 8u, d1);
+          ld8(t0 + 16u, d2);
+        }
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        bar_arrive(smem_u32(&freed[buf]));
+        // D_0 of the quadrant's last point and D_2 of its first, for the
+        // neighbouring quadrants (periodic in p)
+        float* bq = bnd + ((grp * 2 + (int)((grow >> 1) & 1)) * 2) * 4 * COUT;
+        if (lane == 31)
+#pragma unroll
+          for (int n = 0; n < COUT; n += 4)
+            *reinterpret_cast<float4*>(bq + quad * COUT + n) = make_float4(d0[n], d0[n + 1], d0[n + 2], d0[n + 3]);
+        if (lane == 0)
+#pragma unroll
+          for (int n = 0; n < COUT; n += 4)
+            *reinterpret_cast<float4*>(bq + 4 * COUT + quad * COUT + n) = make_float4(d2[n], d2[n + 1], d2[n + 2], d2[n + 3]);
+        if (grp == 0)
+          asm volatile("bar.sync 3, 128;" ::: "memory");
+        else
+          asm volatile("bar.sync 4, 128;" ::: "memory");
+        // lane 0 takes D_0 of point p - 1, lane 31 D_2 of point p + 1, from
+        // the neighbouring quadrants
+        const float* edge = lane == 0 ? bq + ((quad + 3) & 3) * COUT : bq + 4 * COUT + ((quad + 1) & 3) * COUT;
+        const long long pi = point_index(A.v, b, z, yb + r, p);
+#pragma unroll
+        for (int g = 0; g < NG8; ++g) {
+          float ed[8], bs[8];
+          if (lane == 0 || lane == 31) {
+            const float4 e0 = *reinterpret_cast<const float4*>(edge + 8 * g);
+            const float4 e1 = *reinterpret_cast<const float4*>(edge + 8 * g + 4);
+            ed[0] = e0.x, ed[1] = e0.y, ed[2] = e0.z, ed[3] = e0.w, ed[4] = e1.x, ed[5] = e1.y, ed[6] = e1.z, ed[7] = e1.w;
+          }
+          {
+            const float4 b0 = *reinterpret_cast<const float4*>(sbias + 8 * g);
+            const float4 b1 = *reinterpret_cast<const float4*>(sbias + 8 * g + 4);
+            bs[0] = b0.x, bs[1] = b0.y, bs[2] = b0.z, bs[3] = b0.w, bs[4] = b1.x, bs[5] = b1.y, bs[6] = b1.z, bs[7] = b1.w;
+          }
+          float v[8];
+#pragma unroll
+          for (int e = 0; e < 8; ++e) {
+            const int n = 8 * g + e;
+            const float up = __shfl_up_sync(0xffffffffu, d0[n], 1);
+            const float dn = __shfl_down_sync(0xffffffffu, d2[n], 1);
+            const float lft = lane == 0 ? ed[e] : up;
+            const float rgt = lane == 31 ? ed[e] : dn;
+            v[e] = (lft + d1[n]) + (rgt + bs[e]);
+            if (A.relu) v[e] = fmaxf(v[e], 0.0f);
+          }
+          if (A.mask) {
+            const int4 mk = *reinterpret_cast<const int4*>(A.mask + pi * COUT + 8 * g);
+            const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              if (!(__bfloat162float(mb[e]) > 0.0f)) v[e] = 0.0f;
+          }
+          if (A.y32) {
+            *reinterpret_cast<float4*>(A.y32 + pi * COUT + 8 * g) = make_float4(v[0], v[1], v[2], v[3]);
+            *reinterpret_cast<float4*>(A.y32 + pi * COUT + 8 * g + 4) = make_float4(v[4], v[5], v[6], v[7]);
+          }
+          if (A.y) {
+            int4 o;
+            __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) ob[e] = __floats2bfloat162_rn(v[2 * e], v[2 * e + 1]);
+            *reinterpret_cast<int4*>(A.y + pi * COUT + 8 * g) = o;
+          }
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols<COUT>()));
 }
 
 struct WgArgs {
@@ -421,7 +838,57 @@ cudaError_t launch_conv(FwdArgs a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// Which forward kernel serves a launch: 0 = tcgen05 wherever the volume is
+// 128 points wide, mma.sync otherwise; 1 = mma.sync always (mpw_conv3_select).
+int g_conv_kernel = 0;
+
+// TMA map of a channels-last BF16 volume of CIN channels and 128-point rows,
+// with the dimensions ordered (8 channels, 128 points, CIN / 8 groups, rows)
+// so that one box, a whole x-row, lands channel-group-major in shared memory
+// ([group][point][8 channels]).
+bool encode_act_map(CUtensorMap* map, const void* x, int cin, const Vol& v) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 encode = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }();
+  if (!encode) return false;
+  // One box is one x-row of 128 points.  With 32 channels a point is one
+  // 64-byte line, swizzled on the way in; with 8 channels the row is a
+  // contiguous 2 KB, fetched as 16 lines of 128 bytes (eight points each).
+  const cuuint64_t rows = (cuuint64_t)v.n1 * v.n2 * v.batch;
+  const bool wide = cin == 32;
+  const cuuint64_t dims[3] = {wide ? 32u : 64u, wide ? (cuuint64_t)v.n0 : (cuuint64_t)v.n0 / 8, rows};
+  const cuuint64_t strides[2] = {wide ? 64u : 128u, (cuuint64_t)v.n0 * cin * 2};
+  const cuuint32_t box[3] = {wide ? 32u : 64u, wide ? (cuuint32_t)tc::M : (cuuint32_t)tc::M / 8, 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  return encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(x), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, wide ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+template <int CIN, int COUT>
+cudaError_t launch_conv_tc(const FwdArgs& a, cudaStream_t s) {
+  constexpr int smem = tc::smem_bytes<CIN, COUT>();
+  CUtensorMap map;
+  if (!encode_act_map(&map, a.x, CIN, a.v)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const long long rows = (long long)a.v.batch * a.v.n2 * a.v.n1;
+  const long long grid = rows < sm_count() ? rows : sm_count();
+  k_conv3_tc<CIN, COUT><<<(unsigned)grid, tc::THREADS, smem, s>>>(a, map, nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t dispatch_conv(int cin, int cout, const FwdArgs& a, cudaStream_t s) {
+  if (g_conv_kernel == 0 && a.v.n0 == tc::M) {
+    if (cin == 8) return launch_conv_tc<8, 32>(a, s);
+    if (cout == 8) return launch_conv_tc<32, 8>(a, s);
+    return launch_conv_tc<32, 32>(a, s);
+  }
   if (cin == 8) return launch_conv<8, 32>(a, s);
   if (cout == 8) return launch_conv<32, 8>(a, s);
   return launch_conv<32, 32>(a, s);
@@ -478,6 +945,12 @@ mpw_status mpw_conv3_backward_data(const uint16_t* gy, int cout, const uint16_t*
   a.flip = 1;
   // the transposed layer: its input channels are the layer's outputs
   if (cudaError_t e = dispatch_conv(cout, cin, a, (cudaStream_t)stream)) return cuda_fail(e);
+  return MPW_OK;
+}
+
+mpw_status mpw_conv3_select(int kernel) {
+  if (kernel != 0 && kernel != 1) return fail(MPW_ERR_ARG, "conv3: kernel must be 0 (tcgen05 where possible) or 1");
+  g_conv_kernel = kernel;
   return MPW_OK;
 }
 

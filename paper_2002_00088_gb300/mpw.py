@@ -83,6 +83,7 @@ SIGNATURES = {
     "mpw_conv3_backward_data": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), _vp, _vp, _vp,
                                           _vp]),
     "mpw_conv3_wgrad_scratch_bytes": (C.c_size_t, [C.c_int, C.c_int]),
+    "mpw_conv3_select": (C.c_int, [C.c_int]),
     "mpw_conv3_backward_weights": (C.c_int, [_vp, C.c_int, _vp, C.c_int, C.c_int, C.POINTER(C.c_int), _vp, _vp, _vp,
                                              C.c_size_t, _vp]),
     "mpw_adam_step": (C.c_int, [_vp, _vp, _vp, _vp, _vp, C.c_longlong, C.c_float, C.c_float, C.c_float, C.c_float,

@@ -100,3 +100,9 @@ def test_noalloc_refuses_bad_arguments_before_any_launch(mpw_lib):
             mpw_lib.check_noalloc_fields(n, bad, good)
         with pytest.raises(ValueError, match=what):
             mpw_lib.step_periodic_noalloc(n, (0, 0, 0), (1, 1, 1), 0.005, 1e-3, 1, good, bad)
+
+
+def test_conv_kernel_selection_is_validated(mpw_lib):
+    L = mpw_lib.lib
+    assert L.mpw_conv3_select(2) == mpw_lib.ERR_ARG
+    assert L.mpw_conv3_select(1) == 0 and L.mpw_conv3_select(0) == 0
