@@ -282,7 +282,7 @@ __global__ void __launch_bounds__(FWD_THREADS, 2) k_conv3_t(const FwdArgs A) {
 //    the CTA stop issuing work and report through the error word.
 namespace tc {
 constexpr int M = 128;
-constexpr int THREADS = 320;   // warps 0-7: epilogue; warp 8: loads; warp 9: MMAs
+constexpr int THREADS = 352;   // warps 0-7: epilogue; 8: loads; 9: MMAs; 10: waits for the MMAs
 constexpr int EPI = 256;       // epilogue threads
 constexpr int ALIGN = 1024;    // of the smem carve-up (the 64-byte swizzle repeats every 512 B)
 template <int COUT>
@@ -317,22 +317,21 @@ __host__ __device__ constexpr uint32_t idesc(int m, int n) {
 // rows along M or N) >> 4 in bits 32-45, the descriptor version 1 in bit 46,
 // the swizzle mode in bits 61-63.
 //  - sdesc: no swizzle, rows of 16 bytes 128 bytes apart per eight rows;
-__device__ __forceinline__ uint64_t sdesc(uint32_t addr, uint32_t lbo) {
-  return ((uint64_t)((128u >> 4) | (1u << 14)) << 32) | ((addr >> 4) | ((lbo >> 4) << 16));
-}
+__host__ __device__ constexpr uint32_t sdesc_hi() { return (128u >> 4) | (1u << 14); }
 //  - sdesc_sw64: 64-byte swizzle (mode 4), rows of 64 bytes (32 channels), the
 //    eight-row groups 512 bytes apart; the leading offset is unused because a
 //    K step of 16 channels stays inside one 64-byte row.  The K half of a
 //    row is selected by adding 32 bytes to the start address: the swizzle is
 //    applied to the final address bits, so the offset composes with it.
-__device__ __forceinline__ uint64_t sdesc_sw64(uint32_t addr) {
-  return ((uint64_t)((512u >> 4) | (1u << 14) | (4u << 29)) << 32) | ((addr >> 4) | (1u << 16));
-}
+__host__ __device__ constexpr uint32_t sdesc_hi_sw64() { return (512u >> 4) | (1u << 14) | (4u << 29); }
 
-__device__ __forceinline__ void mma(uint32_t d, uint64_t a, uint64_t b, uint32_t id, int acc) {
+// One MMA; the descriptors come as (low, high) 32-bit words.
+__device__ __forceinline__ void mma(uint32_t d, uint32_t a_lo, uint32_t a_hi, uint32_t b_lo, uint32_t b_hi, uint32_t id,
+                                    int acc) {
   asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(id), "r"(acc));
+      "{\n .reg .pred p;\n .reg .b64 da, db;\n setp.ne.b32 p, %6, 0;\n mov.b64 da, {%1, %2};\n mov.b64 db, {%3, %4};\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], da, db, %5, p;\n}\n" ::"r"(d),
+      "r"(a_lo), "r"(a_hi), "r"(b_lo), "r"(b_hi), "r"(id), "r"(acc));
 }
 
 __device__ __forceinline__ void commit(uint32_t bar) {
@@ -412,31 +411,49 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   unsigned long long* done = empty + SLOTS;    // MMAs of an accumulator committed
   unsigned long long* freed = done + NBUF;     // accumulator read by the epilogue
   uint32_t* tslot = reinterpret_cast<uint32_t*>(freed + NBUF);
+  uint32_t* ready = tslot + 1;   // rows the MMA thread may start
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t ws_a = smem_u32(Ws), xs_a = smem_u32(Xs);
-  // ---- weights: [mma][K half][n = dx * COUT + c][8 channels], zero outside
+  // ---- weights: [mma][K half][n = dx * COUT + c][8 channels], zero outside.
+  // The raw tensor is first copied with 16-byte loads into the input ring
+  // (not in use yet), then packed from there one 16-byte unit per step.
   {
-    __nv_bfloat16* W = reinterpret_cast<__nv_bfloat16*>(Ws);
-    for (int i = tid; i < NM * 2 * NT * 8; i += THREADS) {
-      const int e = i % 8, n = (i / 8) % NT, kh = (i / (8 * NT)) % 2, j = i / (16 * NT);
+    constexpr int RAW = 27 * CIN * COUT;
+    static_assert(RAW * 2 <= SLOTS * 3 * RB, "raw weights must fit in the ring");
+    __nv_bfloat16* raw = reinterpret_cast<__nv_bfloat16*>(Xs);
+    if ((reinterpret_cast<unsigned long long>(A.w) & 15ull) == 0) {
+      const int4* src = reinterpret_cast<const int4*>(A.w);
+      int4* dst = reinterpret_cast<int4*>(raw);
+      for (int i = tid; i < RAW / 8; i += THREADS) dst[i] = __ldg(src + i);
+    } else {
+      for (int i = tid; i < RAW; i += THREADS) raw[i] = A.w[i];
+    }
+    __syncthreads();
+    int4* W = reinterpret_cast<int4*>(Ws);
+    for (int u = tid; u < NM * 2 * NT; u += THREADS) {
+      const int n = u % NT, kh = (u / NT) % 2, j = u / (2 * NT);
       const int dx = n / COUT, co = n % COUT;
-      int dz, dy, ch;
+      int dz, dy, c0;
       if (CIN == 32) {
         dz = (j / 2) / 3;
         dy = (j / 2) % 3;
-        ch = 16 * (j % 2) + 8 * kh + e;
+        c0 = 16 * (j % 2) + 8 * kh;
       } else {
         dy = j / 2;
         const int pair = j % 2;
         dz = (pair == 1 && kh == 0) ? -1 : pair + kh;
-        ch = e;
+        c0 = 0;
       }
-      __nv_bfloat16 v = __float2bfloat16(0.0f);
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(0.0f);
       if (dx < 3 && dz >= 0) {
         const int tap = (dz * 3 + dy) * 3 + dx;
-        v = A.flip ? A.w[((long long)ch * 27 + 26 - tap) * COUT + co] : A.w[((long long)co * 27 + tap) * CIN + ch];
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          v[e] = A.flip ? raw[((c0 + e) * 27 + 26 - tap) * COUT + co] : raw[(co * 27 + tap) * CIN + c0 + e];
       }
-      W[i] = v;
+      W[u] = *reinterpret_cast<const int4*>(v);
     }
   }
   __shared__ __align__(16) float sbias[COUT];
@@ -448,8 +465,9 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
     for (int q = 0; q < NBUF; ++q) {
       bar_init(smem_u32(&done[q]), 1);
-      bar_init(smem_u32(&freed[q]), EPI / 2);
+      bar_init(smem_u32(&freed[q]), EPI / 2 / 32);   // one arrival per warp of a group
     }
+    *ready = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -469,14 +487,14 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     // chunk, in order; load L goes into slot L mod SLOTS once the MMAs that
     // read the slot's previous row are done
     if (lane == 0) {
-      long long L = 0;
+      int q = 0, L = 0;
+      unsigned ph = 0;   // parity of the slot's previous load, wrapped once the ring has filled
       bool stop = false;
       Chunks ch(nrows, n1, n2);
       int b, z, yb, R;
       while (!stop && ch.next(b, z, yb, R)) {
         for (int u = 0; u < R + 2; ++u, ++L) {
-          const int q = (int)(L % SLOTS);
-          if (L >= SLOTS && !bar_wait(smem_u32(&empty[q]), (unsigned)(((L - SLOTS) / SLOTS) & 1))) {
+          if (L >= SLOTS && !bar_wait(smem_u32(&empty[q]), ph)) {
             stop = true;
             break;
           }
@@ -488,61 +506,114 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
             const int row = ((b * n2) + wrap1(z + dz - 1, n2)) * n1 + yy;
             tma_load_3d(xs_a + (uint32_t)((q * 3 + dz) * RB), &xmap, 0, 0, row, bar);
           }
+          if (++q == SLOTS) {
+            q = 0;
+            if (L >= SLOTS) ph ^= 1u;
+          }
         }
       }
       if (stop) {
         if (err) atomicOr(err, ERR_TIMEOUT);
         // the copies still in flight land (bounded) before the CTA exits
-        for (long long l = L - SLOTS; l < L; ++l)
+        for (int l = L - SLOTS; l < L; ++l)
           if (l >= 0) bar_wait(smem_u32(&full[l % SLOTS]), (unsigned)((l / SLOTS) & 1));
       }
     }
-  } else if (warp == 9) {
-    // ================= MMAs (one thread)
+  } else if (warp == 10) {
+    // ================= waits on behalf of the MMA thread (one thread): a
+    // row may start once its last input row has landed and its accumulator
+    // has been read; the count of such rows goes to `ready`.  The MMA
+    // thread then polls one shared word instead of two mbarriers, which
+    // keeps the tensor core's short queue fed.
     if (lane == 0) {
-      long long L0 = 0, grow = 0;
+      int qf = 0, bf = 0;
+      unsigned pf = 0, pb = 0;
+      unsigned grow = 0;
       bool stop = false;
       Chunks ch(nrows, n1, n2);
       int b, z, yb, R;
       while (!stop && ch.next(b, z, yb, R)) {
         for (int r = 0; r < R && !stop; ++r, ++grow) {
-          // input rows r, r + 1, r + 2 of the chunk (loads L0 + r + dy);
-          // all but the last were waited for by the rows before
-          uint32_t rowa[3];
-#pragma unroll
-          for (int dy = 0; dy < 3; ++dy) {
-            const long long l = L0 + r + dy;
-            const int q = (int)(l % SLOTS);
-            if ((dy == 2 || r == 0) && !stop && !bar_wait(smem_u32(&full[q]), (unsigned)((l / SLOTS) & 1)))
+          // input rows r, r + 1, r + 2 of the chunk: all three for the
+          // chunk's first row, then the one new row (R + 2 loads a chunk)
+          for (int k = (r == 0 ? 3 : 1); k > 0; --k) {
+            if (!bar_wait(smem_u32(&full[qf]), pf)) {
               stop = true;
-            rowa[dy] = xs_a + (uint32_t)(q * 3 * RB);
+              break;
+            }
+            if (++qf == SLOTS) qf = 0, pf ^= 1u;
           }
-          const int buf = (int)(grow & (NBUF - 1));
-          if (grow >= NBUF && !stop &&
-              !bar_wait(smem_u32(&freed[buf]), (unsigned)(((grow - NBUF) / NBUF) & 1)))
+          if (!stop && grow >= (unsigned)NBUF && !bar_wait(smem_u32(&freed[bf]), pb)) stop = true;
+          if (++bf == NBUF) {
+            bf = 0;
+            if (grow >= (unsigned)NBUF) pb ^= 1u;
+          }
+          if (!stop)
+            asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(ready)), "r"(grow + 1) : "memory");
+        }
+      }
+      if (stop) {
+        asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(ready)), "r"(0xffffffffu) : "memory");
+        if (err) atomicOr(err, ERR_TIMEOUT);
+      }
+    }
+  } else if (warp == 9) {
+    // ================= MMAs (one thread)
+    if (lane == 0) {
+      // descriptor words: the high halves are constant, the low halves are
+      // the start address >> 4 plus the leading offset, so an operand at a
+      // byte offset is the base word plus offset >> 4
+      constexpr uint32_t A_HI = CIN == 32 ? sdesc_hi_sw64() : sdesc_hi();
+      constexpr uint32_t A_LBO = CIN == 32 ? (1u << 16) : ((uint32_t)(RB >> 4) << 16);
+      constexpr uint32_t B_HI = sdesc_hi();
+      const uint32_t b_lo0 = (ws_a >> 4) | ((uint32_t)((NT * 16) >> 4) << 16);
+      int q0 = 0;   // slot of the chunk's current first input row
+      unsigned grow = 0;
+      bool stop = false;
+      Chunks ch(nrows, n1, n2);
+      int b, z, yb, R;
+      while (!stop && ch.next(b, z, yb, R)) {
+        for (int r = 0; r < R; ++r, ++grow) {
+          bool ok = false;
+          for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(ready)) : "memory");
+            if (v == 0xffffffffu) break;
+            if (v > grow) {
+              ok = true;
+              break;
+            }
+          }
+          if (!ok) {
             stop = true;
-          if (stop) break;
+            break;
+          }
+          const int q1 = q0 + 1 == SLOTS ? 0 : q0 + 1, q2 = q1 + 1 == SLOTS ? 0 : q1 + 1;
+          const uint32_t a_lo[3] = {((xs_a + (uint32_t)(q0 * 3 * RB)) >> 4) | A_LBO,
+                                    ((xs_a + (uint32_t)(q1 * 3 * RB)) >> 4) | A_LBO,
+                                    ((xs_a + (uint32_t)(q2 * 3 * RB)) >> 4) | A_LBO};
+          const int buf = (int)(grow & (NBUF - 1));
           asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
           const uint32_t d = tmem + (uint32_t)(buf * NT);
 #pragma unroll
           for (int j = 0; j < NM; ++j) {
             const int dy = CIN == 32 ? (j / 2) % 3 : j / 2;
             const int dz = CIN == 32 ? (j / 2) / 3 : j % 2;       // dz of the first K half
-            const uint32_t a = rowa[dy] + (uint32_t)(dz * RB);
-            const uint32_t bw = ws_a + (uint32_t)(j * 2 * NT * 16);
-            const uint64_t da = CIN == 32 ? sdesc_sw64(a + (uint32_t)(32 * (j % 2))) : sdesc(a, RB);
-            mma(d, da, sdesc(bw, NT * 16), ID, j > 0);
+            const uint32_t off = (uint32_t)(dz * RB + (CIN == 32 ? 32 * (j % 2) : 0));
+            mma(d, a_lo[dy] + (off >> 4), A_HI, b_lo0 + (uint32_t)((j * 2 * NT * 16) >> 4), B_HI, ID, j > 0);
           }
           commit(smem_u32(&done[buf]));
           // input row r is read by no later row of the chunk; the chunk's
           // last row also retires rows R and R + 1
-          commit(smem_u32(&empty[(L0 + r) % SLOTS]));
+          commit(smem_u32(&empty[q0]));
           if (r == R - 1) {
-            commit(smem_u32(&empty[(L0 + R) % SLOTS]));
-            commit(smem_u32(&empty[(L0 + R + 1) % SLOTS]));
+            commit(smem_u32(&empty[q1]));
+            commit(smem_u32(&empty[q2]));
           }
+          q0 = q1;
         }
-        L0 += R + 2;
+        // past the chunk's last two input rows
+        q0 = q0 + 2 >= SLOTS ? q0 + 2 - SLOTS : q0 + 2;
       }
       if (stop && err) atomicOr(err, ERR_TIMEOUT);
     }
@@ -587,7 +658,8 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        bar_arrive(smem_u32(&freed[buf]));
+        __syncwarp();
+        if (lane == 0) bar_arrive(smem_u32(&freed[buf]));
         // D_0 of the quadrant's last point and D_2 of its first, for the
         // neighbouring quadrants (periodic in p)
         float* bq = bnd + ((grp * 2 + (int)((grow >> 1) & 1)) * 2) * 4 * COUT;
