@@ -282,8 +282,10 @@ __global__ void __launch_bounds__(FWD_THREADS, 2) k_conv3_t(const FwdArgs A) {
 //    the CTA stop issuing work and report through the error word.
 namespace tc {
 constexpr int M = 128;
-constexpr int THREADS = 352;   // warps 0-7: epilogue; 8: loads; 9: MMAs; 10: waits for the MMAs
-constexpr int EPI = 256;       // epilogue threads
+constexpr int GROUPS = 4;      // epilogue groups of four warps (one per TMEM lane quadrant)
+constexpr int EPI = GROUPS * 128;        // epilogue threads: warps 0 .. 4 GROUPS - 1
+constexpr int W_LOAD = EPI / 32, W_MMA = W_LOAD + 1, W_WAIT = W_LOAD + 2;   // one-thread roles
+constexpr int THREADS = EPI + 96;
 constexpr int ALIGN = 1024;    // of the smem carve-up (the 64-byte swizzle repeats every 512 B)
 template <int COUT>
 __host__ __device__ constexpr int nt() { return COUT == 32 ? 96 : 32; }
@@ -299,11 +301,11 @@ template <int CIN>
 __host__ __device__ constexpr int slots() { return CIN == 32 ? 6 : 8; }
 template <int CIN, int COUT>
 __host__ __device__ constexpr int w_bytes() { return nmma<CIN>() * 2 * nt<COUT>() * 16; }
-// weights | ring | boundary exchange (2 groups x 2 parities x 2 sides x 4
+// weights | ring | boundary exchange (GROUPS x 2 parities x 2 sides x 4
 // quadrants x COUT floats) | barriers (full, done, freed)
 template <int CIN, int COUT>
 __host__ __device__ constexpr int smem_bytes() {
-  return ALIGN + w_bytes<CIN, COUT>() + slots<CIN>() * 3 * row_bytes<CIN>() + 2 * 2 * 2 * 4 * COUT * 4 +
+  return ALIGN + w_bytes<CIN, COUT>() + slots<CIN>() * 3 * row_bytes<CIN>() + GROUPS * 2 * 2 * 4 * COUT * 4 +
          8 * (2 * slots<CIN>() + 2 * NBUF) + 16;
 }
 
@@ -381,6 +383,21 @@ struct Chunks {
   }
 };
 
+typedef unsigned long long f2;   // two binary32 values, low word first
+__device__ __forceinline__ f2 pk2(float a, float b) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float lo2(f2 v) { return __uint_as_float((unsigned)(v & 0xFFFFFFFFull)); }
+__device__ __forceinline__ float hi2(f2 v) { return __uint_as_float((unsigned)(v >> 32)); }
+// Packed addition (add.rn.f32x2): each lane rounded as the scalar addition.
+__device__ __forceinline__ f2 add2(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y, int r, uint32_t bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
@@ -406,7 +423,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   unsigned char* Ws = reinterpret_cast<unsigned char*>(sbase);
   unsigned char* Xs = Ws + w_bytes<CIN, COUT>();
   float* bnd = reinterpret_cast<float*>(Xs + SLOTS * 3 * RB);  // [group][parity][side][quadrant][COUT]
-  unsigned long long* full = reinterpret_cast<unsigned long long*>(bnd + 2 * 2 * 2 * 4 * COUT);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(bnd + GROUPS * 2 * 2 * 4 * COUT);
   unsigned long long* empty = full + SLOTS;    // an input row's last MMAs done
   unsigned long long* done = empty + SLOTS;    // MMAs of an accumulator committed
   unsigned long long* freed = done + NBUF;     // accumulator read by the epilogue
@@ -465,7 +482,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
     for (int q = 0; q < NBUF; ++q) {
       bar_init(smem_u32(&done[q]), 1);
-      bar_init(smem_u32(&freed[q]), EPI / 2 / 32);   // one arrival per warp of a group
+      bar_init(smem_u32(&freed[q]), 4);   // one arrival per warp of a group
     }
     *ready = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -482,7 +499,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   const uint32_t tmem = *tslot;
   const int n1 = A.v.n1, n2 = A.v.n2;
   const long long nrows = (long long)A.v.batch * n2 * n1;
-  if (warp == 8) {
+  if (warp == W_LOAD) {
     // ================= TMA loads (one thread): every input row of every
     // chunk, in order; load L goes into slot L mod SLOTS once the MMAs that
     // read the slot's previous row are done
@@ -519,7 +536,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
           if (l >= 0) bar_wait(smem_u32(&full[l % SLOTS]), (unsigned)((l / SLOTS) & 1));
       }
     }
-  } else if (warp == 10) {
+  } else if (warp == W_WAIT) {
     // ================= waits on behalf of the MMA thread (one thread): a
     // row may start once its last input row has landed and its accumulator
     // has been read; the count of such rows goes to `ready`.  The MMA
@@ -557,7 +574,7 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
         if (err) atomicOr(err, ERR_TIMEOUT);
       }
     }
-  } else if (warp == 9) {
+  } else if (warp == W_MMA) {
     // ================= MMAs (one thread)
     if (lane == 0) {
       // descriptor words: the high halves are constant, the low halves are
@@ -619,50 +636,45 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
     }
   } else {
     // ================= epilogue: thread = point p of the row; group
-    // `grp` takes the rows of its parity
+    // `grp` takes the rows g with g mod GROUPS = grp, always in accumulator
+    // grp.  Registers: D_0 and D_2 first (their sum needs the exchange across
+    // the quadrants), D_1 after, so that at most two of the three are live.
     const int quad = warp & 3, grp = warp >> 2;
     const int p = 32 * quad + lane;
+    const int src_l = (lane + 31) & 31, src_r = (lane + 1) & 31;
     long long grow = 0;
     bool stop = false;
     Chunks ch(nrows, n1, n2);
     int b, z, yb, R;
     while (!stop && ch.next(b, z, yb, R)) {
       for (int r = 0; r < R; ++r, ++grow) {
-        if ((int)(grow & 1) != grp) continue;
+        if ((int)(grow % GROUPS) != grp) continue;
         const int buf = (int)(grow & (NBUF - 1));
         // the group's threads stop together if any wait ran out, so that
         // none is left at a named barrier
         const unsigned ok = bar_wait(smem_u32(&done[buf]), (unsigned)((grow / NBUF) & 1)) ? 1u : 0u;
         int any_fail;
-        if (grp == 0)
-          asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 1, 128, q;\n selp.s32 %0, 1, 0, p;\n}\n"
-                       : "=r"(any_fail) : "r"(ok) : "memory");
-        else
-          asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, 2, 128, q;\n selp.s32 %0, 1, 0, p;\n}\n"
-                       : "=r"(any_fail) : "r"(ok) : "memory");
+        asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, %2, 128, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+                     : "=r"(any_fail) : "r"(ok), "r"(1 + grp) : "memory");
         if (any_fail) {
           stop = true;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        float d0[COUT], d1[COUT], d2[COUT];
+        float d0[COUT], d2[COUT];
         const uint32_t t0 = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(buf * NT);
         if constexpr (COUT == 32) {
           ld32(t0, d0);
-          ld32(t0 + 32u, d1);
           ld32(t0 + 64u, d2);
         } else {
           ld8(t0, d0);
-          ld8(t0 + 8u, d1);
           ld8(t0 + 16u, d2);
         }
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) bar_arrive(smem_u32(&freed[buf]));
         // D_0 of the quadrant's last point and D_2 of its first, for the
-        // neighbouring quadrants (periodic in p)
-        float* bq = bnd + ((grp * 2 + (int)((grow >> 1) & 1)) * 2) * 4 * COUT;
+        // neighbouring quadrants (periodic in p); two buffers alternate
+        // between the group's rows
+        float* bq = bnd + ((grp * 2 + (int)((grow / GROUPS) & 1)) * 2) * 4 * COUT;
         if (lane == 31)
 #pragma unroll
           for (int n = 0; n < COUT; n += 4)
@@ -671,38 +683,65 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
 #pragma unroll
           for (int n = 0; n < COUT; n += 4)
             *reinterpret_cast<float4*>(bq + 4 * COUT + quad * COUT + n) = make_float4(d2[n], d2[n + 1], d2[n + 2], d2[n + 3]);
-        if (grp == 0)
-          asm volatile("bar.sync 3, 128;" ::: "memory");
+        asm volatile("bar.sync %0, 128;" ::"r"(1 + GROUPS + grp) : "memory");
+        // Lane 31's D_0 and lane 0's D_2 feed only the neighbouring
+        // quadrants' outputs, so those registers now take the values coming
+        // in: lane 31 the D_0 of point 32 quad - 1, lane 0 the D_2 of point
+        // 32 quad + 32.  A rotation by one lane then hands every lane its
+        // D_0[p - 1] and D_2[p + 1] with no per-lane selection.
+        if (lane == 31) {
+          const float* e = bq + ((quad + 3) & 3) * COUT;
+#pragma unroll
+          for (int n = 0; n < COUT; n += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(e + n);
+            d0[n] = t.x, d0[n + 1] = t.y, d0[n + 2] = t.z, d0[n + 3] = t.w;
+          }
+        }
+        if (lane == 0) {
+          const float* e = bq + 4 * COUT + ((quad + 1) & 3) * COUT;
+#pragma unroll
+          for (int n = 0; n < COUT; n += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(e + n);
+            d2[n] = t.x, d2[n + 1] = t.y, d2[n + 2] = t.z, d2[n + 3] = t.w;
+          }
+        }
+        // s = D_0[p - 1] + D_2[p + 1], two channels at once (into d0)
+#pragma unroll
+        for (int n = 0; n < COUT; n += 2) {
+          const float l0 = __shfl_sync(0xffffffffu, d0[n], src_l), l1 = __shfl_sync(0xffffffffu, d0[n + 1], src_l);
+          const float r0 = __shfl_sync(0xffffffffu, d2[n], src_r), r1 = __shfl_sync(0xffffffffu, d2[n + 1], src_r);
+          const f2 t = add2(pk2(l0, l1), pk2(r0, r1));
+          d0[n] = lo2(t);
+          d0[n + 1] = hi2(t);
+        }
+        // D_1, then the accumulator is free
+        float d1[COUT];
+        if constexpr (COUT == 32)
+          ld32(t0 + 32u, d1);
         else
-          asm volatile("bar.sync 4, 128;" ::: "memory");
-        // lane 0 takes D_0 of point p - 1, lane 31 D_2 of point p + 1, from
-        // the neighbouring quadrants
-        const float* edge = lane == 0 ? bq + ((quad + 3) & 3) * COUT : bq + 4 * COUT + ((quad + 1) & 3) * COUT;
+          ld8(t0 + 8u, d1);
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) bar_arrive(smem_u32(&freed[buf]));
         const long long pi = point_index(A.v, b, z, yb + r, p);
 #pragma unroll
         for (int g = 0; g < NG8; ++g) {
-          float ed[8], bs[8];
-          if (lane == 0 || lane == 31) {
-            const float4 e0 = *reinterpret_cast<const float4*>(edge + 8 * g);
-            const float4 e1 = *reinterpret_cast<const float4*>(edge + 8 * g + 4);
-            ed[0] = e0.x, ed[1] = e0.y, ed[2] = e0.z, ed[3] = e0.w, ed[4] = e1.x, ed[5] = e1.y, ed[6] = e1.z, ed[7] = e1.w;
-          }
-          {
-            const float4 b0 = *reinterpret_cast<const float4*>(sbias + 8 * g);
-            const float4 b1 = *reinterpret_cast<const float4*>(sbias + 8 * g + 4);
-            bs[0] = b0.x, bs[1] = b0.y, bs[2] = b0.z, bs[3] = b0.w, bs[4] = b1.x, bs[5] = b1.y, bs[6] = b1.z, bs[7] = b1.w;
-          }
+          const float4 b0 = *reinterpret_cast<const float4*>(sbias + 8 * g);
+          const float4 b1 = *reinterpret_cast<const float4*>(sbias + 8 * g + 4);
+          const float bs[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
           float v[8];
 #pragma unroll
-          for (int e = 0; e < 8; ++e) {
+          for (int e = 0; e < 8; e += 2) {
             const int n = 8 * g + e;
-            const float up = __shfl_up_sync(0xffffffffu, d0[n], 1);
-            const float dn = __shfl_down_sync(0xffffffffu, d2[n], 1);
-            const float lft = lane == 0 ? ed[e] : up;
-            const float rgt = lane == 31 ? ed[e] : dn;
-            v[e] = (lft + d1[n]) + (rgt + bs[e]);
-            if (A.relu) v[e] = fmaxf(v[e], 0.0f);
+            // (D_0[p - 1] + D_2[p + 1]) + (D_1[p] + bias)
+            const f2 t = add2(pk2(d0[n], d0[n + 1]), add2(pk2(d1[n], d1[n + 1]), pk2(bs[e], bs[e + 1])));
+            v[e] = lo2(t);
+            v[e + 1] = hi2(t);
           }
+          if (A.relu)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) v[e] = fmaxf(v[e], 0.0f);
           if (A.mask) {
             const int4 mk = *reinterpret_cast<const int4*>(A.mask + pi * COUT + 8 * g);
             const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
