@@ -81,6 +81,9 @@ def parse():
                     help="the learned surrogate: train it on the method's trajectories, then time the hybrid "
                          "(surrogate global, local patches on the method) against the plain method")
     ap.add_argument("--trajectories", type=int, default=2000, help="--surrogate: training trajectories")
+    ap.add_argument("--network", action="store_true",
+                    help="the surrogate network's forward alone (four 3x3x3 conv layers at 128^3, seeded random "
+                         "BF16 input), per layer, against the measured bf16 peak")
     ap.add_argument("--tol", type=float, default=1e-4, help="--surrogate: residual tolerance of a call")
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="64: the FP64 workload (default); 32: the binary32 precision workload, with its error "
@@ -669,7 +672,9 @@ def run_surrogate(args):
         "error_vs_plain_multipatch": err_mp, "error_vs_plain_global_only": err_solo,
         "one_call_error": gain, "training": {"seconds": train_s, "first_loss": float(np.mean(losses[:20])),
                                              "last_loss": float(np.mean(losses[-20:]))},
-        "roofline": {"bound": "tensor", "kernel": "k_conv3 (network forward, mma.sync BF16/FP32)",
+        "roofline": {"bound": "tensor",
+                     "kernel": ("k_conv3_tc (network forward, tcgen05 BF16 with FP32 TMEM accumulators)" if n == 128
+                                else "k_conv3 (network forward, mma.sync BF16/FP32)"),
                      "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "avg_launch_ms": fwd_ms / 4},
         # per accepted call: features 6 (maximum, scale, three Laplacian passes,
@@ -685,10 +690,79 @@ def run_surrogate(args):
     return 0
 
 
+def run_network(args):
+    """The surrogate network's forward (8 -> 32 -> 32 -> 32 -> 8 channels,
+    3x3x3 taps, periodic) on one 128^3 volume: per-layer CUDA-event times
+    over --steps forwards after --warmup ones."""
+    import torch
+    from paper_2002_00088_gb300.build import build_library
+    build_library()
+    from paper_2002_00088_gb300 import surrogate as S
+    n = 128
+    torch.cuda.set_device(0)
+    g = torch.Generator(device="cuda").manual_seed(5)
+    x = torch.randn((1, n, n, n, 8), device="cuda", generator=g).to(torch.bfloat16)
+    layers = [(8, 32), (32, 32), (32, 32), (32, 8)]
+    acts = [x] + [torch.empty((1, n, n, n, co), dtype=torch.bfloat16, device="cuda") for _, co in layers[:-1]]
+    ws = [(torch.randn((co, 27, ci), device="cuda", generator=g) / (27 * ci) ** 0.5).to(torch.bfloat16)
+          for ci, co in layers]
+    bs = [torch.randn(co, device="cuda", generator=g) * 0.1 for _, co in layers]
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    per = [0.0] * len(layers)
+
+    def forward(record):
+        for l, (ci, co) in enumerate(layers):
+            if record:
+                a, b = ev(), ev()
+                a.record()
+            last = l == len(layers) - 1
+            y, _ = S.conv3_forward(acts[l], ws[l], bs[l], relu=not last)
+            if not last:
+                acts[l + 1] = y
+            if record:
+                b.record()
+                events.append((l, a, b))
+
+    events = []
+    for _ in range(max(args.warmup, 1)):
+        forward(False)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    for _ in range(args.steps):
+        forward(True)
+    b.record()
+    torch.cuda.synchronize()
+    for l, e0, e1 in events:
+        per[l] += e0.elapsed_time(e1) / args.steps
+    ms = a.elapsed_time(b) / args.steps
+    flops = [2 * 27 * ci * co * n ** 3 for ci, co in layers]
+    pk = None
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            pk, src = float(json.load(f)["bf16_tflops"]), "measured bf16 TFLOP/s (burst)"
+    except Exception:
+        pk, src = 1900.0, "fallback bf16 TFLOP/s"
+    tf = sum(flops) / (ms * 1e-3) / 1e12
+    line = {"metric": "network forward TFLOP/s", "value": tf, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "bf16 in, f32 accumulate",
+            "data": "synthetic (seeded normal input and weights)",
+            "config": {"workload": "surrogate network 8-32-32-32-8, 3x3x3, periodic 128^3, batch 1",
+                       "kernel": "k_conv3_tc" if n == 128 else "k_conv3_t"},
+            "layers": [{"cin": ci, "cout": co, "ms": per[l], "tflops": flops[l] / (per[l] * 1e-3) / 1e12}
+                       for l, (ci, co) in enumerate(layers)],
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": pk, "peak_source": src, "unit": "TFLOP/s",
+                         "frac": tf / pk}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.network:
+        return run_network(args)
     if args.batch:
         return run_batch(args)
     if args.surrogate:
