@@ -167,7 +167,7 @@ mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, cons
 
 /* Hybrid stepping of a multipatch context: `calls` surrogate calls of four
  * steps of dt each.  Per call, from the state at t_n (its covered global cells
- * refilled from the local patches, Sec. 2.4): the surrogate's global state
+ * refilled from the local patches, Sec. 2.4.2): the surrogate's global state
  * four steps later and its residual r = max(|R_psi|, Delta |R_Pi|) /
  * max(|psi0|, Delta |Pi0|) (mpw_sur_check).  r <= tol: the global patch takes
  * that state, and the local patches take their four RK4 steps of the method,
@@ -178,10 +178,10 @@ mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, cons
  * in time of (psi, Pi) between the two global states (values, d/dt and
  * d^2/dt^2 from Pi, L psi and L Pi).
  * Otherwise (or r not finite) the call is discarded and the four steps are
- * the method's own (mpw_step).  After an accepted call the global patch
- * continues from its own state: local-patch data enters it only at a call
- * that follows a plain step or a change of fields or time, so the data flow
- * stays one-way from the global patch to the local ones (Sec. 2.4).  Needs a
+ * the method's own (mpw_step).  Every call starts from the global state with
+ * its covered cells refilled from the local patches (Local-to-Global,
+ * Sec. 2.4.2), as the method refills them at every substage, so local-patch
+ * data flows back into the global patch once per call.  Needs a
  * binary64 context whose global patch is periodic with the surrogate's
  * spacing, translating Cartesian local patches, and the surrogate's dt; the
  * surrogate's stream is synchronised with the context's when they differ.

@@ -108,9 +108,6 @@ struct mpw_ctx {
   size_t stage_bytes = 0;
   double* d_sur = nullptr;  // hybrid stepping: dense global states, Laplacians, Hermite coefficients
   size_t sur_bytes = 0;
-  // the global state the last accepted surrogate call produced is still the
-  // context's (no plain step, field or time change since)
-  bool sur_valid = false;
   // copy streams of the asynchronous host IO: inputs in, results out
   cudaStream_t io_in = nullptr, io_out = nullptr;
   double t = 0.0;
@@ -1398,7 +1395,6 @@ mpw_status mpw_fill_analytic(mpw_ctx* c, double t) {
     P.u_expo_valid = false;
   }
   c->t = t;
-  c->sur_valid = false;
   return MPW_OK;
 }
 
@@ -1480,7 +1476,6 @@ mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double
   launch_unpack(P->buf(BUF_U), P->g, s0, s1, c->cfg.precision == 32, c->stream);
   CUDA_TRY(cudaGetLastError());
   P->u_expo_valid = false;
-  c->sur_valid = false;
   if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
   return MPW_OK;
 }
@@ -1530,7 +1525,6 @@ mpw_status mpw_set_fields_async(mpw_ctx* c, int patch, const double* psi, const 
   CUDA_TRY(cudaMemcpyAsync(P->io_in + n, pi, n * sizeof(double), cudaMemcpyHostToDevice, c->io_in));
   CUDA_TRY(cudaEventRecord(P->in_copied, c->io_in));
   P->in_pending = true;
-  c->sur_valid = false;
   return MPW_OK;
 }
 
@@ -1575,7 +1569,6 @@ mpw_status mpw_set_time(mpw_ctx* c, double t) {
   mpw_status st = check_ctx(c);
   if (st) return st;
   c->t = t;
-  c->sur_valid = false;
   return MPW_OK;
 }
 
@@ -1688,7 +1681,6 @@ static mpw_status step_impl(mpw_ctx* c, double dt, int nsteps, bool check_errors
     }
     c->t = tn + dt;
     c->stepped = true;
-    c->sur_valid = false;
   }
   return check_errors ? read_error_word(c) : MPW_OK;
 }
@@ -1800,13 +1792,10 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
   double rmax = 0.0;
   for (int call = 0; call < calls; ++call) {
     if ((st = step_prologue(c, dt))) return st;
-    if (c->sur_valid) {
-      // the global patch continues from its own state: no local data flows
-      // back into it, so nothing the local patches computed returns to them
-      // through the global (the one-way data flow of Sec. 2.4)
-      CUDA_TRY(cudaMemcpyAsync(U, U + 2 * P, 2 * P * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-    } else {
-      // the state at t_n, its covered cells filled from the local patches
+    {
+      // the state at t_n, its covered cells refilled from the local patches
+      // (Local-to-Global, Sec. 2.4.2) as the method refills them at every
+      // substage: local-patch data enters the global once per call
       if ((st = run_fill(c, FILL_BUF[0], c->t, NEXT_BUF[0]))) return st;
       if ((st = fill_dead_cells(c))) return st;
       launch_pack(G.buf(BUF_U), G.g, U, U + P, 0, nullptr, false, c->stream);
@@ -1814,7 +1803,7 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
     }
     if (ss != c->stream) CUDA_TRY(cudaStreamSynchronize(c->stream));
     if ((st = mpw_sur_predict(s, U, U + P, 1, n, U + 2 * P, U + 3 * P))) return st;
-    if ((st = mpw_sur_check(s, U, U + P, U + 2 * P, U + 3 * P, 1, n, U + 4 * P, chk))) return st;
+    if ((st = sur_check_after_predict(s, U, U + P, U + 2 * P, U + 3 * P, n, U + 4 * P, chk))) return st;
     float h2[2];
     CUDA_TRY(cudaMemcpyAsync(h2, chk, sizeof(h2), cudaMemcpyDeviceToHost, ss));
     CUDA_TRY(cudaStreamSynchronize(ss));
@@ -1823,7 +1812,7 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
     if (!(r <= tol)) {
       // fall back: the method's own four steps from the same state
       if ((st = step_impl(c, dt, 4, false))) return st;
-      continue;  // step_impl cleared sur_valid
+      continue;
     }
     ++acc;
     for (int m = 0; m < 4; ++m) {
@@ -1862,7 +1851,6 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
     launch_unpack(G.buf(BUF_U), G.g, U + 2 * P, U + 3 * P, false, c->stream);
     CUDA_TRY(cudaGetLastError());
     G.u_expo_valid = false;
-    c->sur_valid = true;
   }
   if (accepted) *accepted = acc;
   if (max_residual) *max_residual = rmax;
@@ -2170,7 +2158,6 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     for (int i = 0; i < n; ++i) {
       b->ctx[i]->t = tnp[i] + dt[i];
       b->ctx[i]->stepped = true;
-      b->ctx[i]->sur_valid = false;
     }
     ++b->steps_done;
     if (trial && b->steps_done == (long long)nc) {

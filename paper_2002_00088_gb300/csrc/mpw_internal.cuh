@@ -6,6 +6,7 @@
 
 #include <cstdint>
 
+#include "../../include/mpw.h"
 #include "mpw_rhs_args.cuh"
 
 struct mpw_sur;
@@ -200,6 +201,11 @@ void set_last_error(const char* msg);
 void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, const Box* boxes,
                     int nbox, void* stream);
 bool sur_geometry(const mpw_sur* s, double* dt, double* h, void** stream);
+// mpw_sur_check for batch 1 right after mpw_sur_predict(s, psi0, pi0, ...):
+// L psi0 and L Pi0 are copied from the prediction's features instead of
+// being computed again (the same kernel, so the same values)
+mpw_status sur_check_after_predict(mpw_sur* s, const double* psi0, const double* pi0, const double* psi1,
+                                   const double* pi1, const int n[3], double* lap, float* out);
 
 // ---------------------------------------------------------------- tensor maps
 // Encode the TMA maps of the RHS kernel for one field buffer (psi at base, Pi

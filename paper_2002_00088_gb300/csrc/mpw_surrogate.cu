@@ -78,9 +78,19 @@ struct Dims {
 
 // ---------------------------------------------------------------- kernels
 
-// 12 h^2 L u along one axis: (16 (u[-1] + u[1]) - (u[-2] + u[2])) - 30 u
-__device__ __forceinline__ double axis_sum(double um2, double um1, double u0, double up1, double up2) {
-  return __dsub_rn(__dsub_rn(__dmul_rn(16.0, __dadd_rn(um1, up1)), __dadd_rn(um2, up2)), __dmul_rn(30.0, u0));
+// 16 x, exactly as __dmul_rn(16.0, x): where x is normal and 16 x stays
+// finite, the biased exponent is raised by 4 (an integer add, not an FP64
+// operation); zeros, subnormals, infinities and NaNs take the multiply.
+__device__ __forceinline__ double times16(double x) {
+  const int hi = __double2hiint(x);
+  const unsigned e = ((unsigned)hi >> 20) & 0x7ffu;
+  return e - 1u < 2042u ? __hiloint2double(hi + (4 << 20), __double2loint(x)) : __dmul_rn(16.0, x);
+}
+
+// 12 h^2 L u along one axis: (16 (u[-1] + u[1]) - (u[-2] + u[2])) - 30 u,
+// with t30 = 30 u (the same for the three axes)
+__device__ __forceinline__ double axis_sum(double um2, double um1, double t30, double up1, double up2) {
+  return __dsub_rn(__dsub_rn(times16(__dadd_rn(um1, up1)), __dadd_rn(um2, up2)), t30);
 }
 
 // L u at (i, j, k) of sample volume u (periodic): ((Sx + Sy) + Sz) / (12 h^2).
@@ -89,7 +99,7 @@ __device__ __forceinline__ double lap4(const double* __restrict__ u, const Dims&
                                        double inv12h2) {
   const int n0 = d.n0, pl = d.n0 * d.n1;
   const int c0 = (k * d.n1 + j) * n0 + i;
-  const double c = __ldg(u + c0);
+  const double t30 = __dmul_rn(30.0, __ldg(u + c0));
   const int xm1 = i >= 1 ? -1 : n0 - 1, xm2 = i >= 2 ? -2 : n0 - 2;
   const int xp1 = i + 1 < n0 ? 1 : 1 - n0, xp2 = i + 2 < n0 ? 2 : 2 - n0;
   const int ym1 = (j >= 1 ? -1 : d.n1 - 1) * n0, ym2 = (j >= 2 ? -2 : d.n1 - 2) * n0;
@@ -97,9 +107,9 @@ __device__ __forceinline__ double lap4(const double* __restrict__ u, const Dims&
   const int zm1 = (k >= 1 ? -1 : d.n2 - 1) * pl, zm2 = (k >= 2 ? -2 : d.n2 - 2) * pl;
   const int zp1 = (k + 1 < d.n2 ? 1 : 1 - d.n2) * pl, zp2 = (k + 2 < d.n2 ? 2 : 2 - d.n2) * pl;
   const double* q = u + c0;
-  const double sx = axis_sum(__ldg(q + xm2), __ldg(q + xm1), c, __ldg(q + xp1), __ldg(q + xp2));
-  const double sy = axis_sum(__ldg(q + ym2), __ldg(q + ym1), c, __ldg(q + yp1), __ldg(q + yp2));
-  const double sz = axis_sum(__ldg(q + zm2), __ldg(q + zm1), c, __ldg(q + zp1), __ldg(q + zp2));
+  const double sx = axis_sum(__ldg(q + xm2), __ldg(q + xm1), t30, __ldg(q + xp1), __ldg(q + xp2));
+  const double sy = axis_sum(__ldg(q + ym2), __ldg(q + ym1), t30, __ldg(q + yp1), __ldg(q + yp2));
+  const double sz = axis_sum(__ldg(q + zm2), __ldg(q + zm1), t30, __ldg(q + zp1), __ldg(q + zp2));
   return __dmul_rn(__dadd_rn(__dadd_rn(sx, sy), sz), inv12h2);
 }
 
@@ -113,6 +123,21 @@ __global__ void k_absmax(const double* psi, const double* pi, Dims d, double del
     m = __reduce_max_sync(0xffffffffu, m);
     if ((threadIdx.x & 31) == 0 && base + (threadIdx.x & ~31) < N) atomicMax(&maxbits[(base + threadIdx.x) / P], m);
   }
+}
+
+// Per-sample products that the feature and update kernels would otherwise
+// form at every point (the same roundings, so the same values): s, s Delta,
+// s Delta^2 .. s Delta^6 (features), a = sigma / s and a / Delta (update),
+// with s = scale[b].  sc: [batch][9].
+__global__ void k_sample_coef(const float* scale, int batch, double delta, double d2, double d3, double d4, double d5,
+                              double d6, double sigma, double* sc) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= batch) return;
+  const double sv = (double)scale[b];
+  const double a = __ddiv_rn(sigma, sv);
+  const double v[9] = {sv, __dmul_rn(sv, delta), __dmul_rn(sv, d2), __dmul_rn(sv, d3), __dmul_rn(sv, d4),
+                       __dmul_rn(sv, d5), __dmul_rn(sv, d6), a, __ddiv_rn(a, delta)};
+  for (int q = 0; q < 9; ++q) sc[b * 9 + q] = v[q];
 }
 
 __global__ void k_scale(const unsigned* maxbits, int batch, float* scale) {
@@ -134,18 +159,14 @@ __device__ __forceinline__ void point_ijk(long long q, const Dims& d, int& i, in
 }
 
 // lap: the chain L psi, L Pi, L^2 psi, L^2 Pi, L^3 psi, L^3 Pi ([6][batch * points])
-__global__ void k_features(const double* psi, const double* pi, Dims d, Coef c, const float* scale, const double* lap,
+__global__ void k_features(const double* psi, const double* pi, Dims d, const double* sc, const double* lap,
                            uint4* x) {
   const long long N = d.points() * d.batch;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
-    const double s = (double)scale[g / d.points()];
-    const double f[7] = {__dmul_rn(s, psi[g]),
-                         __dmul_rn(__dmul_rn(s, c.delta), pi[g]),
-                         __dmul_rn(__dmul_rn(s, c.d2), lap[g]),
-                         __dmul_rn(__dmul_rn(s, c.d3), lap[N + g]),
-                         __dmul_rn(__dmul_rn(s, c.d4), lap[2 * N + g]),
-                         __dmul_rn(__dmul_rn(s, c.d5), lap[3 * N + g]),
-                         __dmul_rn(__dmul_rn(s, c.d6), lap[4 * N + g])};
+    const double* cs = sc + 9 * (g / d.points());
+    const double f[7] = {__dmul_rn(cs[0], psi[g]),        __dmul_rn(cs[1], pi[g]),         __dmul_rn(cs[2], lap[g]),
+                         __dmul_rn(cs[3], lap[N + g]),    __dmul_rn(cs[4], lap[2 * N + g]), __dmul_rn(cs[5], lap[3 * N + g]),
+                         __dmul_rn(cs[6], lap[4 * N + g])};
     __nv_bfloat162 h[4];
     for (int q = 0; q < 3; ++q) h[q] = __floats2bfloat162_rn(__double2float_rn(f[2 * q]), __double2float_rn(f[2 * q + 1]));
     h[3] = __floats2bfloat162_rn(__double2float_rn(f[6]), 0.0f);
@@ -154,16 +175,23 @@ __global__ void k_features(const double* psi, const double* pi, Dims d, Coef c, 
   }
 }
 
-// L psi and L Pi of every sample (lap: [2][batch * points])
-__global__ void k_lap2(const double* psi, const double* pi, Dims d, double inv12h2, double* lap) {
-  const long long P = d.points(), N = P * d.batch;
-  for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(g / P);
-    int i, j, k;
-    point_ijk(g - (long long)b * P, d, i, j, k);
-    lap[g] = lap4(psi + (long long)b * P, d, i, j, k, inv12h2);
-    lap[N + g] = lap4(pi + (long long)b * P, d, i, j, k, inv12h2);
+// L of F fields of every sample (F = 1: a; F = 2: a and b) into out, field f
+// at out + f * batch * points.  Grid (n1, n2, batch); the threads of a block
+// walk the row.
+template <int F>
+__global__ void k_lap(const double* a, const double* b, Dims d, double inv12h2, double* out) {
+  const int j = blockIdx.x, k = blockIdx.y, s = blockIdx.z;
+  const long long P = d.points(), N = P * d.batch, o = (long long)s * P;
+  const long long row = o + ((long long)k * d.n1 + j) * d.n0;
+  for (int i = threadIdx.x; i < d.n0; i += blockDim.x) {
+    out[row + i] = lap4(a + o, d, i, j, k, inv12h2);
+    if (F == 2) out[N + row + i] = lap4(b + o, d, i, j, k, inv12h2);
   }
+}
+
+template <int F>
+void launch_lap(const double* a, const double* b, const Dims& d, double inv12h2, double* out, cudaStream_t st) {
+  k_lap<F><<<dim3((unsigned)d.n1, (unsigned)d.n2, (unsigned)d.batch), 128, 0, st>>>(a, b, d, inv12h2, out);
 }
 
 __global__ void k_targets(const double* psi0, const double* pi0, const double* psi1, const double* pi1, Dims d,
@@ -183,20 +211,21 @@ __global__ void k_targets(const double* psi0, const double* pi0, const double* p
 
 // (psi1, Pi1) from (psi0, Pi0), their Laplacians and the network output y
 // ([..][8], channels 0, 1)
-__global__ void k_apply(const double* psi0, const double* pi0, Dims d, Coef c, const float* scale, const double* lap,
+__global__ void k_apply(const double* psi0, const double* pi0, Dims d, Coef c, const double* sc, const double* lap,
                         const float* y, double* psi1, double* pi1) {
   const long long P = d.points(), N = P * d.batch;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < N; g += (long long)gridDim.x * blockDim.x) {
-    const int b = (int)(g / P);
+    const double* cs = sc + 9 * (g / P);
     const double lp = lap[g], lq = lap[N + g], llp = lap[2 * N + g], llq = lap[3 * N + g];
-    const double a = __ddiv_rn(c.sigma, (double)scale[b]);
-    const double n0 = (double)y[g * 8], n1 = (double)y[g * 8 + 1];
+    const double a = cs[7], ad = cs[8];   // sigma / s and its quotient by Delta
+    const float2 yv = *reinterpret_cast<const float2*>(y + g * 8);
+    const double n0 = (double)yv.x, n1 = (double)yv.y;
     double u = __dadd_rn(psi0[g], __dmul_rn(c.delta, pi0[g]));
     u = __dadd_rn(__dadd_rn(__dadd_rn(u, __dmul_rn(c.hd2, lp)), __dmul_rn(c.d36, lq)), __dmul_rn(c.d424, llp));
     psi1[g] = __dadd_rn(u, __dmul_rn(a, n0));
     double v = __dadd_rn(pi0[g], __dmul_rn(c.delta, lp));
     v = __dadd_rn(__dadd_rn(__dadd_rn(v, __dmul_rn(c.hd2, lq)), __dmul_rn(c.d36, llp)), __dmul_rn(c.d424, llq));
-    pi1[g] = __dadd_rn(v, __dmul_rn(__ddiv_rn(a, c.delta), n1));
+    pi1[g] = __dadd_rn(v, __dmul_rn(ad, n1));
   }
 }
 
@@ -315,6 +344,7 @@ struct mpw_sur {
   int bcap = 0;
   float* scale = nullptr;
   unsigned* maxbits = nullptr;
+  double* sc = nullptr;   // per-sample products of the last features ([bcap][9])
 };
 
 namespace {
@@ -367,22 +397,26 @@ mpw_status ensure_infer(mpw_sur* s, long long P, int batch) {
   if (batch > s->bcap) {
     cudaFree(s->scale);
     cudaFree(s->maxbits);
+    cudaFree(s->sc);
     s->scale = nullptr;
     s->maxbits = nullptr;
+    s->sc = nullptr;
     s->bcap = 0;
     SUR_TRY(cudaMalloc(&s->scale, (size_t)batch * 4));
     SUR_TRY(cudaMalloc(&s->maxbits, (size_t)batch * 4));
+    SUR_TRY(cudaMalloc(&s->sc, (size_t)batch * 9 * sizeof(double)));
     s->bcap = batch;
   }
   return MPW_OK;
 }
 
-// The Laplacian chain of (psi, Pi) into s->lap: L, L^2, L^3 of both fields.
+// The Laplacian chain of (psi, Pi) into s->lap: L psi, L Pi, L^2 psi, L^2 Pi,
+// L^3 psi (the features read no L^3 Pi).
 mpw_status lap_chain(mpw_sur* s, const double* psi, const double* pi, const Dims& d) {
   const long long N = d.points() * d.batch;
-  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(psi, pi, d, s->coef.inv12h2, s->lap);
-  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(s->lap, s->lap + N, d, s->coef.inv12h2, s->lap + 2 * N);
-  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(s->lap + 2 * N, s->lap + 3 * N, d, s->coef.inv12h2, s->lap + 4 * N);
+  launch_lap<2>(psi, pi, d, s->coef.inv12h2, s->lap, s->stream);
+  launch_lap<2>(s->lap, s->lap + N, d, s->coef.inv12h2, s->lap + 2 * N, s->stream);
+  launch_lap<1>(s->lap + 2 * N, nullptr, d, s->coef.inv12h2, s->lap + 4 * N, s->stream);
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
@@ -458,7 +492,7 @@ void mpw_sur_destroy(mpw_sur* s) {
   cudaStreamSynchronize(s->stream);
   free_buffers(s);
   for (void* p : {(void*)s->w, (void*)s->g, (void*)s->m, (void*)s->v, (void*)s->w16, s->scratch, (void*)s->loss,
-                  (void*)s->x, (void*)s->lap, (void*)s->scale, (void*)s->maxbits})
+                  (void*)s->x, (void*)s->lap, (void*)s->scale, (void*)s->maxbits, (void*)s->sc})
     cudaFree(p);
   delete s;
 }
@@ -506,7 +540,10 @@ mpw_status mpw_sur_features(mpw_sur* s, const double* psi0, const double* pi0, i
   k_absmax<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef.delta, s->maxbits);
   k_scale<<<(batch + 127) / 128, 128, 0, s->stream>>>(s->maxbits, batch, scale);
   MPW_TRY(lap_chain(s, psi0, pi0, d));
-  k_features<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, scale, s->lap, reinterpret_cast<uint4*>(x));
+  const Coef& c = s->coef;
+  k_sample_coef<<<(batch + 127) / 128, 128, 0, s->stream>>>(scale, batch, c.delta, c.d2, c.d3, c.d4, c.d5, c.d6, c.sigma,
+                                                          s->sc);
+  k_features<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->sc, s->lap, reinterpret_cast<uint4*>(x));
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
@@ -583,8 +620,9 @@ mpw_status mpw_sur_predict(mpw_sur* s, const double* psi0, const double* pi0, in
   MPW_TRY(ensure_train(s, P));
   MPW_TRY(mpw_sur_features(s, psi0, pi0, batch, n, s->x, s->scale));
   MPW_TRY(forward_chain(s, s->x, d, s->y));
-  // s->lap holds the chain of (psi0, Pi0) from the features
-  k_apply<<<grid_for(P), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, s->scale, s->lap, s->y, psi1, pi1);
+  // s->lap holds the chain of (psi0, Pi0) and s->sc its per-sample products,
+  // both from the features
+  k_apply<<<grid_for(P), 256, 0, s->stream>>>(psi0, pi0, d, s->coef, s->sc, s->lap, s->y, psi1, pi1);
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
 }
@@ -601,8 +639,8 @@ mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, cons
     lap = s->lap;
   }
   SUR_TRY(cudaMemsetAsync(out, 0, (size_t)batch * 2 * sizeof(float), s->stream));
-  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, d, s->coef.inv12h2, lap);
-  k_lap2<<<grid_for(N), 256, 0, s->stream>>>(psi1, pi1, d, s->coef.inv12h2, lap + 2 * N);
+  launch_lap<2>(psi0, pi0, d, s->coef.inv12h2, lap, s->stream);
+  launch_lap<2>(psi1, pi1, d, s->coef.inv12h2, lap + 2 * N, s->stream);
   k_check<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, lap, reinterpret_cast<unsigned*>(out));
   SUR_TRY(cudaGetLastError());
   return MPW_OK;
@@ -611,6 +649,21 @@ mpw_status mpw_sur_check(mpw_sur* s, const double* psi0, const double* pi0, cons
 }  // extern "C"
 
 namespace mpw {
+
+mpw_status sur_check_after_predict(mpw_sur* s, const double* psi0, const double* pi0, const double* psi1,
+                                   const double* pi1, const int n[3], double* lap, float* out) {
+  MPW_TRY(use(s));
+  Dims d;
+  MPW_TRY(dims_of(1, n, d));
+  const long long N = d.points();
+  if (!lap || !out || N > s->xcap) return fail(MPW_ERR_ARG, "surrogate: check without a prediction");
+  SUR_TRY(cudaMemsetAsync(out, 0, 2 * sizeof(float), s->stream));
+  SUR_TRY(cudaMemcpyAsync(lap, s->lap, (size_t)2 * N * sizeof(double), cudaMemcpyDeviceToDevice, s->stream));
+  launch_lap<2>(psi1, pi1, d, s->coef.inv12h2, lap + 2 * N, s->stream);
+  k_check<<<grid_for(N), 256, 0, s->stream>>>(psi0, pi0, psi1, pi1, d, s->coef, lap, reinterpret_cast<unsigned*>(out));
+  SUR_TRY(cudaGetLastError());
+  return MPW_OK;
+}
 
 void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, const Box* boxes,
                     int nbox, void* stream) {
