@@ -638,6 +638,27 @@ def run_surrogate(args):
 
     err_mp = errors(hyb, plain, range(3))
     err_solo = errors(hyb, solo, [0])
+    # each run against the closed form at the final time (the global on the
+    # cells the plain multipatch run keeps live, the local patches whole),
+    # relative to the largest closed-form value on the global
+    exact3, exact1 = make(3), make(1)
+    exact3.fill_analytic(plain.time)
+    exact1.fill_analytic(plain.time)
+    live_cells = (plain.get_flags() & 3) == 0
+
+    def vs_exact(run, ex, patches):
+        out = {}
+        for f, nm in enumerate(("psi", "pi")):
+            scale = np.nanmax(np.abs(ex.get_fields(0)[f]))
+            e = {}
+            for q in patches:
+                d = np.abs(run.get_fields(q)[f] - ex.get_fields(q)[f])
+                e["global" if q == 0 else f"local{q}"] = float(np.nanmax(d[live_cells] if q == 0 else d) / scale)
+            out[nm] = e
+        return out
+
+    err_exact = {"hybrid": vs_exact(hyb, exact3, range(3)), "plain_multipatch": vs_exact(plain, exact3, range(3)),
+                 "plain_global_only": vs_exact(solo, exact1, [0])}
     # the network's forward throughput (tensor-core bound), CUDA events
     x = torch.zeros((1, n, n, n, 8), dtype=torch.bfloat16, device="cuda")
     for _ in range(3):
@@ -670,6 +691,7 @@ def run_surrogate(args):
         "speedup_vs_plain": ms_p / ms_h,
         "accepted_calls": accepted, "max_residual": max_res,
         "error_vs_plain_multipatch": err_mp, "error_vs_plain_global_only": err_solo,
+        "error_vs_closed_form": err_exact,
         "one_call_error": gain, "training": {"seconds": train_s, "first_loss": float(np.mean(losses[:20])),
                                              "last_loss": float(np.mean(losses[-20:]))},
         "roofline": {"bound": "tensor",

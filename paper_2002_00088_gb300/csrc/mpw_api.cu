@@ -805,11 +805,16 @@ mpw_status prep_mirrors(mpw_ctx* c, int b, double t, MirrorArgs& m, int mir_glob
   return MPW_OK;
 }
 
-// g2l_only: Global-to-Local segments only (the hybrid substages of
-// mpw_step_surrogate, where nothing reads the global's outer ghosts or its
-// Local-to-Global ring).
+// Which segments a fill runs: all of them (the method's substages), the
+// Global-to-Local ones only (the hybrid substages of mpw_step_surrogate, where
+// nothing reads the global's outer ghosts or its Local-to-Global ring), or the
+// Local-to-Global ones only (the start of a hybrid call, where only the
+// global's covered cells are read).
+enum FillParts { FILL_ALL = 0, FILL_G2L = 1, FILL_L2G = 2 };
+
 mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, MirrorArgs* mirrors = nullptr,
-                     bool g2l_only = false) {
+                     int parts = FILL_ALL) {
+  const bool g2l_only = parts == FILL_G2L, l2g_only = parts == FILL_L2G;
   const PatchState& g = c->p[0];
   a = FillArgs{};
   int mir_global[MAX_PATCHES], mir_shell[MAX_PATCHES];
@@ -828,7 +833,7 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
   a.ascreen = c->screen_ok ? c->d_ascreen : nullptr;
   a.apre = c->screen_ok ? c->d_apre : nullptr;
   a.shell_src = nullptr;
-  if (a.outer_bc == 0 && !g2l_only) {
+  if (a.outer_bc == 0 && parts == FILL_ALL) {
     for (int k = 0; k < 4; ++k)
       if (k != b && c->shell_time[k] == t) a.shell_src = g.buf(k);
     c->shell_time[b] = t;
@@ -836,7 +841,7 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
   a.t = t;
   a.outer_count = (long long)(g.d.n[0] + 2 * NG) * (g.d.n[1] + 2 * NG) * (g.d.n[2] + 2 * NG) -
                   (long long)g.d.n[0] * g.d.n[1] * g.d.n[2];
-  if (g2l_only) a.outer_count = 0;
+  if (parts != FILL_ALL) a.outer_count = 0;
   a.outer_blocks = (int)((a.outer_count + fill_threads() - 1) / fill_threads());
   int blocks = a.outer_blocks;
   a.nseg = 0;
@@ -903,7 +908,7 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
     blocks += build_segment(S, O0, O, c->P);
   }
   // Global-to-Local: the ghost shell of each local patch
-  for (int q = 0; q < nloc; ++q) {
+  for (int q = 0; q < (l2g_only ? 0 : nloc); ++q) {
     const PatchState& L = c->p[q + 1];
     InterpSeg& S = a.seg[a.nseg++];
     S.T = L.buf(b);
@@ -950,10 +955,10 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
   return MPW_OK;
 }
 
-mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf, bool g2l_only = false) {
+mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf, int parts = FILL_ALL) {
   FillArgs a;
   MirrorArgs m;
-  if (mpw_status st = prep_fill(c, b, t, reset_buf, a, &m, g2l_only)) return st;
+  if (mpw_status st = prep_fill(c, b, t, reset_buf, a, &m, parts)) return st;
   c->launch_begin(MPW_KERNEL_FILL);
   if (m.nr > 0) {
     launch_mirror(m, c->stream);
@@ -1796,7 +1801,7 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
       // the state at t_n, its covered cells refilled from the local patches
       // (Local-to-Global, Sec. 2.4.2) as the method refills them at every
       // substage: local-patch data enters the global once per call
-      if ((st = run_fill(c, FILL_BUF[0], c->t, NEXT_BUF[0]))) return st;
+      if ((st = run_fill(c, FILL_BUF[0], c->t, NEXT_BUF[0], FILL_L2G))) return st;
       if ((st = fill_dead_cells(c))) return st;
       launch_pack(G.buf(BUF_U), G.g, U, U + P, 0, nullptr, false, c->stream);
       CUDA_TRY(cudaGetLastError());
@@ -1842,7 +1847,7 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
         launch_hermite(G.buf(FILL_BUF[l]), G.g, U, coef + (4 * m + l) * 6, slot2, donors.data(), (int)donors.size(),
                        c->stream);
         CUDA_TRY(cudaGetLastError());
-        if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], true))) return st;
+        if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], FILL_G2L))) return st;
         if ((st = run_rhs(c, l, tl, dt, true))) return st;
       }
       c->t = tn + dt;
