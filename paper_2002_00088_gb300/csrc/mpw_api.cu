@@ -1947,13 +1947,17 @@ struct mpw_batch {
   int zc = 0;                    // chosen chunk depth (0 until tuned)
   double zc_ms = 0.0;            // its measured RHS time per step
   long long launches = 0;
-  // CUDA graphs of one step (one per pinned half), used while no instance
-  // moves: the launches and their grids are then the same every step and
-  // only the argument values (substage times) change, which the captured
-  // copies pick up from the pinned half at replay
+  // CUDA graphs of one step (one per pinned half).  The captured copies pick
+  // up each step's arguments from the pinned half at replay, so a graph
+  // serves every step whose launches fit its grids: a static batch has the
+  // same grids every step; a moving one is captured with grids padded to a
+  // capacity (spare blocks exit at once) and captured again only when a
+  // grid outgrows it.  Launches whose arguments travel by value (mirrors and
+  // shells of moving patches) rule the graph out.
   cudaStream_t cap = nullptr;    // capture stream
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int gtot[2][8] = {};
+  int gtot[2][8] = {};           // the grids each graph launches
+  long long captures = 0;
   bool graphs = true;
   long long graph_steps = 0;
 };
@@ -2101,6 +2105,29 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
       }
     }
     sfirst[4] = (int)sargs.size();
+    bool moving = false;
+    for (mpw_ctx* c : b->ctx) moving = moving || any_moving(c);
+    bool by_value = false;  // a launch of this step takes its arguments by value
+    for (long long sb : sblocks) by_value = by_value || sb > 0;
+    for (const MirrorArgs& ma : mirs) by_value = by_value || ma.nr > 0;
+    const bool use_graph = b->graphs && !trial && !(moving && by_value);
+    // the grids: the block totals, or while replaying a moving batch the
+    // graph's padded capacities (a new capture when a total outgrows them)
+    int grid[8];
+    std::memcpy(grid, totals, sizeof(grid));
+    bool recapture = false;
+    if (use_graph) {
+      if (!b->gexec[h]) {
+        recapture = true;
+      } else if (moving) {
+        for (int r = 0; r < 8; ++r) recapture = recapture || totals[r] > b->gtot[h][r];
+      } else {
+        recapture = std::memcmp(b->gtot[h], totals, sizeof(totals)) != 0;
+      }
+      if (moving)
+        for (int r = 0; r < 8; ++r)
+          grid[r] = recapture ? totals[r] + totals[r] / 16 + 64 : std::max(totals[r], b->gtot[h][r]);
+    }
     // copies and launches of the step, on stream sm
     auto enqueue = [&](cudaStream_t sm) -> cudaError_t {
       for (int r = 0; r < 8; ++r) {
@@ -2113,13 +2140,13 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         const int* d_blk0 = reinterpret_cast<const int*>(dreg + esz * n);
         if (pass == 0) {
           for (int i = 0; i < n; ++i) launch_mirror(mirs[l * n + i], sm);
-          launch_fill_batch(reinterpret_cast<const FillArgs*>(dreg), d_blk0, n, totals[r], b->P, b->f32, sm);
+          launch_fill_batch(reinterpret_cast<const FillArgs*>(dreg), d_blk0, n, grid[r], b->P, b->f32, sm);
         } else {
           if (trial && l == 0) cudaEventRecord(b->tev[2 * k], sm);
           if (b->f32)
-            launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], rot, sm);
+            launch_rhs32_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, grid[r], rot, sm);
           else
-            launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, totals[r], b->fixed, rot, sm);
+            launch_rhs_batch(reinterpret_cast<const RhsArgs*>(dreg), d_blk0, n, grid[r], b->fixed, rot, sm);
           for (int k2 = sfirst[l]; k2 < sfirst[l + 1]; ++k2)
             if (sblocks[k2] > 0) launch_rhs_shell(sargs[k2], sblocks[k2], sm);
           if (trial && l == 3) cudaEventRecord(b->tev[2 * k + 1], sm);
@@ -2128,11 +2155,9 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
       }
       return cudaSuccess;
     };
-    bool moving = false;
-    for (mpw_ctx* c : b->ctx) moving = moving || any_moving(c);
     bool replayed = false;
-    if (b->graphs && !trial && !moving) {
-      if (!b->gexec[h] || std::memcmp(b->gtot[h], totals, sizeof(totals)) != 0) {
+    if (use_graph) {
+      if (recapture) {
         if (b->gexec[h]) cudaGraphExecDestroy(b->gexec[h]);
         b->gexec[h] = nullptr;
         cudaGraph_t graph = nullptr;
@@ -2143,7 +2168,8 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         if (graph) cudaGraphDestroy(graph);
         cudaGetLastError();
         if (ok) {
-          std::memcpy(b->gtot[h], totals, sizeof(totals));
+          std::memcpy(b->gtot[h], grid, sizeof(grid));
+          ++b->captures;
         } else {
           b->gexec[h] = nullptr;
           b->graphs = false;  // this configuration does not capture: launch directly from now on

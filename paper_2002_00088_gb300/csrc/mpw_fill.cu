@@ -991,10 +991,13 @@ __global__ void __launch_bounds__(FILL_THREADS, 2) k_fill(const __grid_constant_
   fill_body<P, ST>(A, blockIdx.x);
 }
 
-// Batched launch: instance i owns blocks [blk0[i], blk0[i + 1]), arguments As[i].
+// Batched launch: instance i owns blocks [blk0[i], blk0[i + 1]), arguments
+// As[i]; blocks from blk0[ninst] on (a grid padded to a captured capacity)
+// have no work.
 template <int P, typename ST>
 __global__ void __launch_bounds__(FILL_THREADS, 2) k_fill_batch(const FillArgs* __restrict__ As,
                                                              const int* __restrict__ blk0, int ninst) {
+  if ((int)blockIdx.x >= blk0[ninst]) return;
   int lo = 0, hi = ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;

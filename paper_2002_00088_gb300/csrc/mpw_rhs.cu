@@ -987,6 +987,7 @@ __device__ __forceinline__ int batch_instance(const int* __restrict__ blk0, int 
 template <int TX, int TY, bool FIXED, bool ROT>
 __global__ void __launch_bounds__(TX* TY, RHS_MIN_BLOCKS) k_rhs_batch(const RhsArgs* __restrict__ As,
                                                                       const int* __restrict__ blk0, int ninst) {
+  if ((int)blockIdx.x >= blk0[ninst]) return;  // spare block of a padded grid
   const int i = batch_instance(blk0, ninst);
   if (FIXED)
     rhs_fx<TX, TY, ROT>(As[i], blockIdx.x - blk0[i]);

@@ -604,6 +604,7 @@ __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32(const __grid
 template <bool ROT>
 __global__ void __launch_bounds__(RHS_TX* RHS_TY, R32_MINB) k_rhs32_batch(const RhsArgs* __restrict__ As,
                                                                           const int* __restrict__ blk0, int ninst) {
+  if ((int)blockIdx.x >= blk0[ninst]) return;  // spare block of a padded grid
   int lo = 0, hi = ninst - 1;
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
