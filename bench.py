@@ -703,7 +703,8 @@ def run_surrogate(args):
         "one_call_error": gain, "training": {"seconds": train_s, "first_loss": float(np.mean(losses[:20])),
                                              "last_loss": float(np.mean(losses[-20:]))},
         "roofline": {"bound": "tensor",
-                     "kernel": ("k_conv3_tc (network forward, tcgen05 BF16 with FP32 TMEM accumulators)" if n == 128
+                     "kernel": ("k_conv3_tc, k_conv3_tc_yx (network forward, tcgen05 BF16 with FP32 TMEM "
+                                "accumulators)" if n == 128
                                 else "k_conv3 (network forward, mma.sync BF16/FP32)"),
                      "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "avg_launch_ms": fwd_ms / 4},
@@ -778,7 +779,7 @@ def run_network(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "dtype": "bf16 in, f32 accumulate",
             "data": "synthetic (seeded normal input and weights)",
             "config": {"workload": "surrogate network 8-32-32-32-8, 3x3x3, periodic 128^3, batch 1",
-                       "kernel": "k_conv3_tc" if n == 128 else "k_conv3_t"},
+                       "kernel": "k_conv3_tc (8 -> 32, 32 -> 32), k_conv3_tc_yx (32 -> 8)"},
             "layers": [{"cin": ci, "cout": co, "ms": per[l], "tflops": flops[l] / (per[l] * 1e-3) / 1e12}
                        for l, (ci, co) in enumerate(layers)],
             "roofline": {"bound": "tensor", "achieved": tf, "peak": pk, "peak_source": src, "unit": "TFLOP/s",

@@ -769,6 +769,333 @@ __global__ void __launch_bounds__(tc::THREADS, 1)
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols<COUT>()));
 }
 
+// ---------------------------------------------------------------------------
+// tcgen05 path for 32 input and 8 output channels: the y- and x-taps of one
+// dz stacked along N (9 x 8 = 72 columns, padded to 80), so that an input
+// row takes 6 MMAs (3 dz x 2 K halves) instead of the 18 N = 32 MMAs per
+// output row of k_conv3_tc, whose N is a third used.  The accumulator of an
+// input row yy holds, in column block dy, its contributions to output row
+// yy - dy + 1: output row y sums block 0 of the accumulator of row y - 1,
+// block 1 of row y and block 2 of row y + 1, then the x-taps as in
+// k_conv3_tc.  Accumulators rotate over NA TMEM slots; a slot is freed once
+// the three output rows that read it have (the first reader of a chunk's
+// edge row arrives for the readers it lacks).  Every input row now feeds
+// one MMA group, so its ring slot is released as soon as that group is done.
+namespace tcy {
+constexpr int CIN = 32, COUT = 8, NT = 80, NM = 6, NA = 6, SLOTS = 8;
+constexpr int RB = tc::M * CIN * 2;
+constexpr int W_BYTES = NM * 2 * NT * 16;
+constexpr int SMEM = tc::ALIGN + W_BYTES + SLOTS * 3 * RB + tc::GROUPS * 2 * 2 * 4 * COUT * 4 + 8 * (2 * SLOTS + 2 * NA) +
+                     16;
+}  // namespace tcy
+
+__global__ void __launch_bounds__(tc::THREADS, 1)
+    k_conv3_tc_yx(const FwdArgs A, const __grid_constant__ CUtensorMap xmap, int* err) {
+  using namespace tc;
+  using tcy::CIN;
+  using tcy::COUT;
+  using tcy::NA;
+  using tcy::NM;
+  using tcy::NT;
+  using tcy::RB;
+  using tcy::SLOTS;
+  constexpr uint32_t ID = idesc(M, NT);
+  extern __shared__ __align__(16) unsigned char smem[];
+  const unsigned long long sbase =
+      (reinterpret_cast<unsigned long long>(smem) + (ALIGN - 1)) & ~(unsigned long long)(ALIGN - 1);
+  unsigned char* Ws = reinterpret_cast<unsigned char*>(sbase);
+  unsigned char* Xs = Ws + tcy::W_BYTES;
+  float* bnd = reinterpret_cast<float*>(Xs + SLOTS * 3 * RB);  // [group][parity][side][quadrant][COUT]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(bnd + GROUPS * 2 * 2 * 4 * COUT);
+  unsigned long long* empty = full + SLOTS;  // an input row's MMAs done
+  unsigned long long* done = empty + SLOTS;  // an accumulator's MMAs committed
+  unsigned long long* freed = done + NA;     // an accumulator read by its three output rows
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(freed + NA);
+  uint32_t* ready = tslot + 1;  // input rows the MMA thread may start
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t ws_a = smem_u32(Ws), xs_a = smem_u32(Xs);
+  // ---- weights: [mma j = 2 dz + K half][8-channel group][n = 24 dy + 8 dx + c][8 channels]
+  {
+    constexpr int RAW = 27 * CIN * COUT;
+    static_assert(RAW * 2 <= SLOTS * 3 * RB, "raw weights must fit in the ring");
+    __nv_bfloat16* raw = reinterpret_cast<__nv_bfloat16*>(Xs);
+    if ((reinterpret_cast<unsigned long long>(A.w) & 15ull) == 0) {
+      const int4* src = reinterpret_cast<const int4*>(A.w);
+      int4* dst = reinterpret_cast<int4*>(raw);
+      for (int i = tid; i < RAW / 8; i += THREADS) dst[i] = __ldg(src + i);
+    } else {
+      for (int i = tid; i < RAW; i += THREADS) raw[i] = A.w[i];
+    }
+    __syncthreads();
+    int4* W = reinterpret_cast<int4*>(Ws);
+    for (int u = tid; u < NM * 2 * NT; u += THREADS) {
+      const int n = u % NT, kh = (u / NT) % 2, j = u / (2 * NT);
+      const int dz = j / 2, c0 = 16 * (j % 2) + 8 * kh;
+      __align__(16) __nv_bfloat16 v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = __float2bfloat16(0.0f);
+      if (n < 9 * COUT) {
+        const int dy = n / (3 * COUT), dx = (n / COUT) % 3, co = n % COUT;
+        const int tap = (dz * 3 + dy) * 3 + dx;
+#pragma unroll
+        for (int e = 0; e < 8; ++e)
+          v[e] = A.flip ? raw[((c0 + e) * 27 + 26 - tap) * COUT + co] : raw[(co * 27 + tap) * CIN + c0 + e];
+      }
+      W[u] = *reinterpret_cast<const int4*>(v);
+    }
+  }
+  __shared__ __align__(16) float sbias[COUT];
+  if (tid < COUT) sbias[tid] = A.bias ? A.bias[tid] : 0.0f;
+  if (tid == 0) {
+    for (int q = 0; q < SLOTS; ++q) {
+      bar_init(smem_u32(&full[q]), 1);
+      bar_init(smem_u32(&empty[q]), 1);
+    }
+    for (int q = 0; q < NA; ++q) {
+      bar_init(smem_u32(&done[q]), 1);
+      bar_init(smem_u32(&freed[q]), 3 * 4);   // three output rows, one arrival per warp of a group
+    }
+    *ready = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tslot)), "r"(512));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tslot;
+  const int n1 = A.v.n1, n2 = A.v.n2;
+  const long long nrows = (long long)A.v.batch * n2 * n1;
+  if (warp == W_LOAD) {
+    // ================= TMA loads: every input row of every chunk, in order
+    if (lane == 0) {
+      int q = 0, L = 0;
+      unsigned ph = 0;
+      bool stop = false;
+      Chunks ch(nrows, n1, n2);
+      int b, z, yb, R;
+      while (!stop && ch.next(b, z, yb, R)) {
+        for (int u = 0; u < R + 2; ++u, ++L) {
+          if (L >= SLOTS && !bar_wait(smem_u32(&empty[q]), ph)) {
+            stop = true;
+            break;
+          }
+          const uint32_t bar = smem_u32(&full[q]);
+          bar_expect_tx(bar, 3 * RB);
+          const int yy = wrap1(yb - 1 + u, n1);
+#pragma unroll
+          for (int dz = 0; dz < 3; ++dz) {
+            const int row = ((b * n2) + wrap1(z + dz - 1, n2)) * n1 + yy;
+            tma_load_3d(xs_a + (uint32_t)((q * 3 + dz) * RB), &xmap, 0, 0, row, bar);
+          }
+          if (++q == SLOTS) {
+            q = 0;
+            if (L >= SLOTS) ph ^= 1u;
+          }
+        }
+      }
+      if (stop) {
+        if (err) atomicOr(err, ERR_TIMEOUT);
+        for (int l = L - SLOTS; l < L; ++l)
+          if (l >= 0) bar_wait(smem_u32(&full[l % SLOTS]), (unsigned)((l / SLOTS) & 1));
+      }
+    }
+  } else if (warp == W_WAIT) {
+    // ================= waits for the MMA thread: input row L may start once
+    // it has landed and its accumulator slot's previous row has been read
+    if (lane == 0) {
+      int qf = 0, af = 0;
+      unsigned pf = 0, pa = 0, L = 0;
+      bool stop = false;
+      Chunks ch(nrows, n1, n2);
+      int b, z, yb, R;
+      while (!stop && ch.next(b, z, yb, R)) {
+        for (int u = 0; u < R + 2 && !stop; ++u, ++L) {
+          if (!bar_wait(smem_u32(&full[qf]), pf)) stop = true;
+          if (++qf == SLOTS) qf = 0, pf ^= 1u;
+          if (!stop && L >= (unsigned)NA && !bar_wait(smem_u32(&freed[af]), pa)) stop = true;
+          if (++af == NA) {
+            af = 0;
+            if (L >= (unsigned)NA) pa ^= 1u;
+          }
+          if (!stop)
+            asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(ready)), "r"(L + 1) : "memory");
+        }
+      }
+      if (stop) {
+        asm volatile("st.release.cta.shared::cta.u32 [%0], %1;" ::"r"(smem_u32(ready)), "r"(0xffffffffu) : "memory");
+        if (err) atomicOr(err, ERR_TIMEOUT);
+      }
+    }
+  } else if (warp == W_MMA) {
+    // ================= MMAs (one thread): 6 per input row
+    if (lane == 0) {
+      constexpr uint32_t A_HI = sdesc_hi_sw64(), B_HI = sdesc_hi();
+      const uint32_t b_lo0 = (ws_a >> 4) | ((uint32_t)((NT * 16) >> 4) << 16);
+      int q = 0, a = 0;
+      unsigned L = 0;
+      bool stop = false;
+      Chunks ch(nrows, n1, n2);
+      int b, z, yb, R;
+      while (!stop && ch.next(b, z, yb, R)) {
+        for (int u = 0; u < R + 2; ++u, ++L) {
+          bool ok = false;
+          for (unsigned it = 0; it < WAIT_LIMIT; ++it) {
+            unsigned v;
+            asm volatile("ld.acquire.cta.shared::cta.u32 %0, [%1];" : "=r"(v) : "r"(smem_u32(ready)) : "memory");
+            if (v == 0xffffffffu) break;
+            if (v > L) {
+              ok = true;
+              break;
+            }
+          }
+          if (!ok) {
+            stop = true;
+            break;
+          }
+          const uint32_t a_lo = ((xs_a + (uint32_t)(q * 3 * RB)) >> 4) | (1u << 16);
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t d = tmem + (uint32_t)(a * NT);
+#pragma unroll
+          for (int j = 0; j < NM; ++j) {
+            const uint32_t off = (uint32_t)((j / 2) * RB + 32 * (j % 2));
+            mma(d, a_lo + (off >> 4), A_HI, b_lo0 + (uint32_t)((j * 2 * NT * 16) >> 4), B_HI, ID, j > 0);
+          }
+          commit(smem_u32(&done[a]));
+          commit(smem_u32(&empty[q]));
+          if (++q == SLOTS) q = 0;
+          if (++a == NA) a = 0;
+        }
+      }
+      if (stop && err) atomicOr(err, ERR_TIMEOUT);
+    }
+  } else {
+    // ================= epilogue: group `grp` takes the output rows g with
+    // g mod GROUPS = grp; thread = point p of the row
+    const int quad = warp & 3, grp = warp >> 2;
+    const int p = 32 * quad + lane;
+    const int src_l = (lane + 31) & 31, src_r = (lane + 1) & 31;
+    long long grow = 0;
+    unsigned L0 = 0;   // the chunk's first input row (load index)
+    bool stop = false;
+    Chunks ch(nrows, n1, n2);
+    int b, z, yb, R;
+    while (!stop && ch.next(b, z, yb, R)) {
+      for (int r = 0; r < R; ++r, ++grow) {
+        if ((int)(grow % GROUPS) != grp) continue;
+        const unsigned u2 = L0 + (unsigned)r + 2;   // the last of the three accumulators
+        const unsigned ok = bar_wait(smem_u32(&done[u2 % NA]), (u2 / NA) & 1u) ? 1u : 0u;
+        int any_fail;
+        asm volatile("{\n .reg .pred p, q;\n setp.eq.u32 q, %1, 0;\n bar.red.or.pred p, %2, 128, q;\n selp.s32 %0, 1, 0, p;\n}\n"
+                     : "=r"(any_fail) : "r"(ok), "r"(1 + grp) : "memory");
+        if (any_fail) {
+          stop = true;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        // E[dx][c] = block 0 of row r, block 1 of row r + 1, block 2 of row r + 2
+        float e[3][COUT];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          const uint32_t t0 = tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(((L0 + r + k) % NA) * NT + k * 3 * COUT);
+          float v0[COUT], v1[COUT], v2[COUT];
+          ld8(t0, v0);
+          ld8(t0 + 8u, v1);
+          ld8(t0 + 16u, v2);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+          for (int c = 0; c < COUT; ++c) {
+            e[0][c] = k == 0 ? v0[c] : e[0][c] + v0[c];
+            e[1][c] = k == 0 ? v1[c] : e[1][c] + v1[c];
+            e[2][c] = k == 0 ? v2[c] : e[2][c] + v2[c];
+          }
+        }
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            // readers of chunk row uc: the output rows max(0, uc - 2) .. min(R - 1, uc);
+            // the first of them arrives for the ones the chunk lacks
+            const int uc = r + k, first = uc - 2 > 0 ? uc - 2 : 0, last = uc < R - 1 ? uc : R - 1;
+            const unsigned cnt = r == first ? (unsigned)(1 + 3 - (last - first + 1)) : 1u;
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&freed[(L0 + r + k) % NA])),
+                         "r"(cnt) : "memory");
+          }
+        }
+        float* bq = bnd + ((grp * 2 + (int)((grow / GROUPS) & 1)) * 2) * 4 * COUT;
+        if (lane == 31)
+#pragma unroll
+          for (int c = 0; c < COUT; c += 4)
+            *reinterpret_cast<float4*>(bq + quad * COUT + c) = make_float4(e[0][c], e[0][c + 1], e[0][c + 2], e[0][c + 3]);
+        if (lane == 0)
+#pragma unroll
+          for (int c = 0; c < COUT; c += 4)
+            *reinterpret_cast<float4*>(bq + 4 * COUT + quad * COUT + c) =
+                make_float4(e[2][c], e[2][c + 1], e[2][c + 2], e[2][c + 3]);
+        asm volatile("bar.sync %0, 128;" ::"r"(1 + GROUPS + grp) : "memory");
+        // as in k_conv3_tc: the edge lanes take the neighbouring quadrants'
+        // values, then one-lane rotations combine the x-taps
+        if (lane == 31) {
+          const float* ep = bq + ((quad + 3) & 3) * COUT;
+#pragma unroll
+          for (int c = 0; c < COUT; c += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(ep + c);
+            e[0][c] = t.x, e[0][c + 1] = t.y, e[0][c + 2] = t.z, e[0][c + 3] = t.w;
+          }
+        }
+        if (lane == 0) {
+          const float* ep = bq + 4 * COUT + ((quad + 1) & 3) * COUT;
+#pragma unroll
+          for (int c = 0; c < COUT; c += 4) {
+            const float4 t = *reinterpret_cast<const float4*>(ep + c);
+            e[2][c] = t.x, e[2][c + 1] = t.y, e[2][c + 2] = t.z, e[2][c + 3] = t.w;
+          }
+        }
+        const long long pi = point_index(A.v, b, z, yb + r, p);
+        float v[COUT];
+#pragma unroll
+        for (int c = 0; c < COUT; c += 2) {
+          const float l0 = __shfl_sync(0xffffffffu, e[0][c], src_l), l1 = __shfl_sync(0xffffffffu, e[0][c + 1], src_l);
+          const float r0 = __shfl_sync(0xffffffffu, e[2][c], src_r), r1 = __shfl_sync(0xffffffffu, e[2][c + 1], src_r);
+          // (E_0[p - 1] + E_2[p + 1]) + (E_1[p] + bias)
+          const f2 t = add2(add2(pk2(l0, l1), pk2(r0, r1)), add2(pk2(e[1][c], e[1][c + 1]), pk2(sbias[c], sbias[c + 1])));
+          v[c] = lo2(t);
+          v[c + 1] = hi2(t);
+        }
+        if (A.relu)
+#pragma unroll
+          for (int c = 0; c < COUT; ++c) v[c] = fmaxf(v[c], 0.0f);
+        if (A.mask) {
+          const int4 mk = *reinterpret_cast<const int4*>(A.mask + pi * COUT);
+          const __nv_bfloat16* mb = reinterpret_cast<const __nv_bfloat16*>(&mk);
+#pragma unroll
+          for (int c = 0; c < COUT; ++c)
+            if (!(__bfloat162float(mb[c]) > 0.0f)) v[c] = 0.0f;
+        }
+        if (A.y32) {
+          *reinterpret_cast<float4*>(A.y32 + pi * COUT) = make_float4(v[0], v[1], v[2], v[3]);
+          *reinterpret_cast<float4*>(A.y32 + pi * COUT + 4) = make_float4(v[4], v[5], v[6], v[7]);
+        }
+        if (A.y) {
+          int4 o;
+          __nv_bfloat162* ob = reinterpret_cast<__nv_bfloat162*>(&o);
+#pragma unroll
+          for (int c = 0; c < 4; ++c) ob[c] = __floats2bfloat162_rn(v[2 * c], v[2 * c + 1]);
+          *reinterpret_cast<int4*>(A.y + pi * COUT) = o;
+        }
+      }
+      L0 += (unsigned)R + 2;
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512));
+}
+
 struct WgArgs {
   const __nv_bfloat16* x;  // layer input [..][CIN]
   const __nv_bfloat16* g;  // gradient at the layer output [..][COUT]
@@ -994,10 +1321,21 @@ cudaError_t launch_conv_tc(const FwdArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_conv_tc_yx(const FwdArgs& a, cudaStream_t s) {
+  CUtensorMap map;
+  if (!encode_act_map(&map, a.x, tcy::CIN, a.v)) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_conv3_tc_yx, cudaFuncAttributeMaxDynamicSharedMemorySize, tcy::SMEM);
+  if (e != cudaSuccess) return e;
+  const long long rows = (long long)a.v.batch * a.v.n2 * a.v.n1;
+  const long long grid = rows < sm_count() ? rows : sm_count();
+  k_conv3_tc_yx<<<(unsigned)grid, tc::THREADS, tcy::SMEM, s>>>(a, map, nullptr);
+  return cudaGetLastError();
+}
+
 cudaError_t dispatch_conv(int cin, int cout, const FwdArgs& a, cudaStream_t s) {
   if (g_conv_kernel == 0 && a.v.n0 == tc::M) {
     if (cin == 8) return launch_conv_tc<8, 32>(a, s);
-    if (cout == 8) return launch_conv_tc<32, 8>(a, s);
+    if (cout == 8) return launch_conv_tc_yx(a, s);
     return launch_conv_tc<32, 32>(a, s);
   }
   if (cin == 8) return launch_conv<8, 32>(a, s);
