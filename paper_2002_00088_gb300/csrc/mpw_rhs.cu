@@ -451,8 +451,9 @@ __device__ __forceinline__ void rhs_body(const RhsArgs& A, const int b) {
 // equal spacing on every axis): the common case.  Same traversal, TMA
 // pipeline and arithmetic model as rhs_body<FIXED>, with the integer work cut
 // down:
-//  - conversion q = round(x 2^(1074-E)) for the buffer's largest biased
-//    exponent E (|q| < 2^52), one variable 64-bit shift (to_fixed52);
+//  - conversion of x to q = x 2^(1074-E) within one unit for the buffer's
+//    largest biased exponent E (|q| < 2^52): the significand shifted right
+//    once, the sign applied as a one's complement (to_fixed52);
 //  - stencil sums formed around the centre, T_m = sum_axes (u_m + u_-m) - 6 u0,
 //    so that D2 = 16 T1 - T2 and KO = T3 - 6 T2 + 15 T1 need no multiple of u0
 //    (the weights of each stencil sum to zero);
