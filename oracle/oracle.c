@@ -988,6 +988,101 @@ int orc_step(orc_sim* s, double dt, int nsteps) {
 }
 
 /* ------------------------------------------------------------------------ */
+/* Pieces of a hybrid step, in which the global patch is advanced by other
+ * means (a learned surrogate) and only the local patches take the method's
+ * RK4 step.  Not part of the paper's method: the surrogate is an extension of
+ * it, and these two functions lay out what that extension prescribes, so
+ * that the library's hybrid path has an oracle. */
+
+/* Every DEAD global cell (flags as last computed) of the stage state Y takes
+ * the Lagrange interpolant, Eq. (Pijk), of the u of the local patch that
+ * covers it, mapped at time t: a complete global field for the surrogate
+ * (dead cells take no part in the method itself). */
+int orc_fill_dead(orc_sim* s, double t) {
+  if (s->np < 1 || !s->flags_valid) return fail(s, ORC_ERR_STATE, "no flags");
+  opatch* g = &s->p[0];
+  double Xg[3], wg[3];
+  long unfilled = 0;
+  orc_motion(g->d.motion, g->d.motion_params, t, Xg, wg);
+#pragma omp parallel for schedule(dynamic) reduction(+ : unfilled) num_threads(s->nthreads)
+  for (int k = 0; k < g->d.n[2]; ++k)
+    for (int j = 0; j < g->d.n[1]; ++j)
+      for (int i = 0; i < g->d.n[0]; ++i) {
+        unsigned char f = s->flags[gidx(g, i, j, k)];
+        if ((f & 3) != ORC_DEAD) continue;
+        int q = f >> 2;
+        double xb[3] = {node(g, 0, i) + Xg[0], node(g, 1, j) + Xg[1], node(g, 2, k) + Xg[2]}, x[3], v[2];
+        oframe fq = frame_at(&s->p[q], t);
+        to_local(&fq, xb, x);
+        if (interp_point(s, q, s->p[q].U, x, v)) {
+          ++unfilled;
+          continue;
+        }
+        long c = at(g, i, j, k);
+        g->Y[0][c] = v[0];
+        g->Y[1][c] = v[1];
+      }
+  if (unfilled) return fail(s, ORC_ERR_UNFILLED, "%ld dead cells could not be interpolated", unfilled);
+  return 0;
+}
+
+/* One RK4 step of the local patches only (Sec. 2.3, Table 1) while the global
+ * patch holds, at substage l, the prescribed stage state gstage[2 l + f]
+ * (field f, interior points in (k, j, i) order): flags at t_n, then per
+ * substage the local stage states, the global's prescribed one (its outer
+ * shell by periodic images), Global-to-Local ghost data (Sec. 2.4.1) at t_l
+ * and the local slopes; then the local updates.  The global's u is left as
+ * it was; t advances by dt. */
+int orc_step_locals(orc_sim* s, double dt, const double* const* gstage) {
+  if (s->np < 1) return fail(s, ORC_ERR_STATE, "no global patch");
+  opatch* g = &s->p[0];
+  if (g->d.outer_bc != ORC_BC_PERIODIC) return fail(s, ORC_ERR_ARG, "the global patch must be periodic");
+  double tn = s->t;
+  int rc = orc_compute_flags(s);
+  if (rc) return rc;
+  for (int l = 0; l < 4; ++l) {
+    double tl = tn + RK_C[l] * dt, Xg[3], wg[3];
+    long unfilled = 0, bad_donor = 0;
+    make_stage(s, l, dt);
+    long c = 0;
+    for (int k = 0; k < g->d.n[2]; ++k)
+      for (int j = 0; j < g->d.n[1]; ++j)
+        for (int i = 0; i < g->d.n[0]; ++i, ++c) {
+          g->Y[0][at(g, i, j, k)] = gstage[2 * l][c];
+          g->Y[1][at(g, i, j, k)] = gstage[2 * l + 1][c];
+        }
+    for (int k = -NG; k < g->d.n[2] + NG; ++k)
+      for (int j = -NG; j < g->d.n[1] + NG; ++j)
+        for (int i = -NG; i < g->d.n[0] + NG; ++i) {
+          if (in_interior(g, i, j, k)) continue;
+          long d = at(g, i, j, k), src = at(g, (int)wrap(i, g->d.n[0]), (int)wrap(j, g->d.n[1]), (int)wrap(k, g->d.n[2]));
+          g->Y[0][d] = g->Y[0][src];
+          g->Y[1][d] = g->Y[1][src];
+        }
+    orc_motion(g->d.motion, g->d.motion_params, tl, Xg, wg);
+    fill_g2l(s, tl, Xg, &unfilled, &bad_donor);
+    if (bad_donor) return fail(s, ORC_ERR_DONOR, "%ld interpolation windows touched non-live cells", bad_donor);
+    if (unfilled) return fail(s, ORC_ERR_UNFILLED, "%ld ghost points could not be interpolated", unfilled);
+    for (int q = 1; q < s->np; ++q) rhs(s, q, tl, s->p[q].Y, s->p[q].K[l][0], s->p[q].K[l][1]);
+  }
+  for (int q = 1; q < s->np; ++q) {
+    opatch* p = &s->p[q];
+    for (int k = 0; k < p->d.n[2]; ++k)
+      for (int j = 0; j < p->d.n[1]; ++j)
+        for (int i = 0; i < p->d.n[0]; ++i) {
+          long c = at(p, i, j, k);
+          for (int f = 0; f < 2; ++f) {
+            double half = p->U[f][c] + dt * (RK_B[0] * p->K[0][f][c] + RK_B[1] * p->K[1][f][c] +
+                                             RK_B[2] * p->K[2][f][c]);
+            p->U[f][c] = half + dt * RK_B[3] * p->K[3][f][c];
+          }
+        }
+  }
+  s->t = tn + dt;
+  return 0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Discrete energy of a periodic patch, E_h = 1/2 h^3 sum (Pi^2 - psi D2 psi),
  * with D2 the 3-axis operator above and periodic neighbours. */
 double orc_energy(const orc_sim* s, int q) {

@@ -99,6 +99,12 @@ int orc_set_flags(orc_sim* s, const unsigned char* flags);
 int orc_fill_ghosts(orc_sim* s, double t);          /* Y <- U on live points, then all BCs at t */
 int orc_eval_rhs(orc_sim* s, int patch, double t, double* kpsi, double* kpi);
 int orc_step(orc_sim* s, double dt, int nsteps);
+/* hybrid-step pieces (the learned surrogate, an extension of the method):
+ * dead global cells of Y from their local patch's u at t; one RK4 step of
+ * the local patches with the global's stage states prescribed
+ * (gstage[2 l + f]: substage l, field f, interior in (k, j, i) order) */
+int orc_fill_dead(orc_sim* s, double t);
+int orc_step_locals(orc_sim* s, double dt, const double* const* gstage);
 long orc_live_points(const orc_sim* s);
 double orc_energy(const orc_sim* s, int patch);
 

@@ -53,6 +53,8 @@ def lib():
         L.orc_fill_ghosts.argtypes = [vp, C.c_double]
         L.orc_eval_rhs.argtypes = [vp, C.c_int, C.c_double, dp, dp]
         L.orc_step.argtypes = [vp, C.c_double, C.c_int]
+        L.orc_fill_dead.argtypes = [vp, C.c_double]
+        L.orc_step_locals.argtypes = [vp, C.c_double, C.POINTER(dp)]
         L.orc_live_points.restype = C.c_long
         L.orc_live_points.argtypes = [vp]
         L.orc_energy.restype = C.c_double
@@ -242,6 +244,22 @@ class Oracle:
 
     def step(self, dt, nsteps=1):
         self._check(self.L.orc_step(self.h, float(dt), int(nsteps)))
+
+    def fill_dead(self, t):
+        """Dead global cells of the stage state from their local patch (the
+        complete field a learned surrogate reads)."""
+        self._check(self.L.orc_fill_dead(self.h, float(t)))
+
+    def step_locals(self, dt, gstage):
+        """One RK4 step of the local patches, the global's stage states
+        prescribed: gstage[l] = (psi, pi) interior arrays of substage l."""
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for l in range(4) for a in gstage[l]]
+        n = self.shape(0)
+        for a in arrs:
+            if a.shape != tuple(n):
+                raise ValueError("stage arrays must have the global patch's interior shape")
+        ptrs = (C.POINTER(C.c_double) * 8)(*[_dp(a) for a in arrs])
+        self._check(self.L.orc_step_locals(self.h, float(dt), ptrs))
 
     def live_points(self):
         return self.L.orc_live_points(self.h)

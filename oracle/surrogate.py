@@ -245,3 +245,72 @@ def hermite5(tau):
     return np.array([1 - 10 * t**3 + 15 * t**4 - 6 * t**5, t - 6 * t**3 + 8 * t**4 - 3 * t**5,
                      0.5 * (t**2 - 3 * t**3 + 3 * t**4 - t**5), 10 * t**3 - 15 * t**4 + 6 * t**5,
                      -4 * t**3 + 7 * t**4 - 3 * t**5, 0.5 * (t**3 - 2 * t**4 + t**5)])
+
+
+# ---------------------------------------------------------------------------
+# The hybrid call with local patches (mpw_step_surrogate): the surrogate
+# advances the periodic global patch four steps at once while the local
+# patches take the method's four RK4 steps.  An extension of the paper's
+# method, laid out here from its definition, over the C oracle's pieces.
+
+def hermite_stage_weights(m, l):
+    """Weights of (y0, y0', y0'', y1, y1', y1'') (derivatives in units of the
+    call's interval Delta = 4 dt) that give the RK4 stage state of substage l
+    of step m of a call.  For the linear system y' = A y the RK4 stage states
+    of a step that starts from u are u, u + dt/2 u', u + dt/2 u' + dt^2/4 u'',
+    u + dt u' + dt^2/2 u'' + dt^3/4 u''' (each stage input is u plus dt times
+    the previous stage's slope); u and its time derivatives are those of the
+    quintic Hermite interpolant at tau = m / 4, with d/dt = (1 / Delta) d/dtau
+    and dt / Delta = 1/4."""
+    tau = m / 4.0
+    stage = [(1.0, 0.0, 0.0, 0.0), (1.0, 0.5, 0.0, 0.0), (1.0, 0.5, 0.25, 0.0), (1.0, 1.0, 0.5, 0.25)][l]
+    t = np.polynomial.Polynomial([0.0, 1.0])
+    basis = [1 - 10 * t**3 + 15 * t**4 - 6 * t**5, t - 6 * t**3 + 8 * t**4 - 3 * t**5,
+             0.5 * (t**2 - 3 * t**3 + 3 * t**4 - t**5), 10 * t**3 - 15 * t**4 + 6 * t**5,
+             -4 * t**3 + 7 * t**4 - 3 * t**5, 0.5 * (t**3 - 2 * t**4 + t**5)]
+    w = np.zeros(6)
+    for k, ck in enumerate(stage):
+        if ck == 0.0:
+            continue
+        for j, b in enumerate(basis):
+            # dt^k d^k/dt^k = (1/4)^k d^k/dtau^k
+            w[j] += ck * 0.25**k * b.deriv(k)(tau) if k else ck * b(tau)
+    return w
+
+
+def hybrid_call(o, params, dt, h, sigma, P=6):
+    """One hybrid call on the oracle simulation o (global patch 0 periodic,
+    local patches 1..): from the state at t, with the flags at t (and the
+    revival they bring), the global's covered cells refilled from the local
+    patches (Local-to-Global) and its dead cells interpolated from them, the
+    surrogate's global state four steps later (features, network, update);
+    the local patches then take four RK4 steps of the method whose
+    Global-to-Local data come from the global stage states of the quintic
+    Hermite interpolant between the two global states; the global ends at the
+    surrogate's state.  params: the network's flat parameters (None: the
+    network off, the fourth-order Taylor step alone)."""
+    from oracle import pyoracle as po
+    t = o.time
+    ng = po.NG
+    o.compute_flags()
+    o.fill_ghosts(t)
+    o.fill_dead(t)
+    ps, pq = o.get_padded(0, which=1)
+    inner = (slice(ng, -ng),) * 3
+    psi0, pi0 = ps[inner][None].copy(), pq[inner][None].copy()
+    x, s = features(psi0, pi0, dt, h)
+    y = np.zeros(psi0.shape + (8,)) if params is None else net_forward(x, params)[1]
+    psi1, pi1 = apply(psi0, pi0, s, y, dt, h, sigma)
+    D = 4.0 * dt
+    lp0, lq0, lp1, lq1 = lap4(psi0, h), lap4(pi0, h), lap4(psi1, h), lap4(pi1, h)
+    # interpolant data per field, derivatives in units of the interval
+    data_psi = (psi0, D * pi0, D * D * lp0, psi1, D * pi1, D * D * lp1)
+    data_pi = (pi0, D * lp0, D * D * lq0, pi1, D * lp1, D * D * lq1)
+    for m in range(4):
+        stages = []
+        for l in range(4):
+            w = hermite_stage_weights(m, l)
+            stages.append((sum(wj * v for wj, v in zip(w, data_psi))[0], sum(wj * v for wj, v in zip(w, data_pi))[0]))
+        o.step_locals(dt, stages)
+    o.set_fields(0, psi1[0], pi1[0])
+    return psi1[0], pi1[0]

@@ -1,20 +1,23 @@
 """Hybrid stepping (mpw_step_surrogate): the learned surrogate advances the
 periodic global patch four steps per call while the local patches stay on the
-method, fed from the quintic Hermite interpolant in time of the global state.
+method, fed from the quintic Hermite interpolant in time of the global state,
+and refill the global's covered cells at the start of every call.
 
 What is pinned exactly: a call whose residual is above the tolerance is the
 method's own four steps (bit for bit), and with no local patch an accepted
 call is the surrogate's state (bit for bit).  The residual and the Laplacians
 of the check kernel match the oracle.  With local patches the result is an
 approximation of the method whose error is bounded here against the plain
-run, and a trained network must beat the untrained Taylor step.
+run, and matches the oracle's hybrid call (oracle/surrogate.py hybrid_call,
+pinned piece by piece in tests/test_oracle_hybrid.py); a trained network must
+beat the untrained Taylor step.
 """
 import numpy as np
 import pytest
 
 from oracle import surrogate as so
 from paper_2002_00088_gb300 import workloads as wl
-from tests.helpers import gpu_from
+from tests.helpers import gpu_from, oracle_from
 
 pytestmark = pytest.mark.gpu
 SIGMA = 1e-4
@@ -166,3 +169,42 @@ def test_trained_network_beats_the_taylor_step(sur_mod, trained):
             e = max(float((p1 - u1[0]).abs().max()), 4 * w.dt * float((q1 - u1[1]).abs().max())) / scale
             errs[name] = max(errs[name], e)
     assert errs["trained"] * 2 < errs["off"], errs
+
+
+def test_hybrid_calls_with_local_patches_match_the_oracle(mpw_lib, sur_mod):
+    """Two network-off calls (the fourth-order Taylor step) on the half-size
+    surrogate layout, two orbiting local patches: the device's hybrid against
+    the oracle's hybrid call (flags and revival at the call's start, the
+    Local-to-Global refill and the dead-cell fill, the surrogate's state, the
+    local patches' four RK4 steps on the Hermite stage states, the global at
+    the surrogate's state).  Every patch within 1e-11 of the domain maximum of
+    each field; cover flags equal."""
+    w = wl.surrogate_layout(scale=2)
+    h = 2.0 / w.patches[0].n[0]
+    a = started(mpw_lib, w)
+    sur = surrogate(sur_mod, w, np.zeros(so.param_count(), np.float32))
+    o = oracle_from(w)
+    o.fill_analytic(0.0)
+    for _ in range(2):
+        acc, _ = sur_mod.step_hybrid(a, sur, w.dt, 1, tol=np.inf)
+        assert acc == 1
+        so.hybrid_call(o, None, w.dt, h, SIGMA)
+    npatch = len(w.patches)
+    np.testing.assert_array_equal(a.get_flags(), o.get_flags())
+    # the library reads the global's ghost and dead cells as NaN; compare the
+    # live ones there
+    fl = a.get_flags() & 3
+    live = (fl == 0) | (fl == 3)
+    for f in range(2):
+        want = [o.get_fields(q)[f] for q in range(npatch)]
+        scale = max(np.nanmax(np.abs(x)) for x in want)
+        for q in range(npatch):
+            got = a.get_fields(q)[f]
+            ref = want[q]
+            if q == 0:
+                assert np.isnan(got[~live]).all()
+                got, ref = got[live], ref[live]
+            assert np.isfinite(got).all()
+            err = np.abs(got - ref).max() / scale
+            assert err < 1e-11, (f, q, err)
+    assert a.time == o.time
