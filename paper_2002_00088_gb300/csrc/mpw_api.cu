@@ -463,7 +463,12 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
 }
 
 // Cover flags at time t; revival uses the previous flags when valid.
-mpw_status run_flags(mpw_ctx* c, double t) {
+// revive = false: the cells that turn live keep what u holds there (the NaN
+// of a dead cell).  Only for the steps inside a hybrid call, where u of the
+// global is not read before it is rewritten: every Global-to-Local donor lies
+// in the boxes the Hermite stage states overwrite, and the call ends by
+// writing the surrogate's state over all of u.
+mpw_status run_flags(mpw_ctx* c, double t, bool revive = true) {
   const PatchState& g = c->p[0];
   FlagArgs a{};
   a.flags = c->d_flags;
@@ -581,6 +586,7 @@ mpw_status run_flags(mpw_ctx* c, double t) {
   }
   a.buffer = c->buffer;
   a.old_valid = c->flags_valid ? 1 : 0;
+  a.skip_revive = revive ? 0 : 1;
   a.Ug = g.buf(BUF_U);
   a.gg = g.g;
   a.P = c->P;
@@ -1649,12 +1655,12 @@ bool any_moving(const mpw_ctx* c) {
 
 // What a step does before its substages: validation at t_n, the cover flags
 // (every step when a patch moves, once otherwise) and the exponent slots of u.
-mpw_status step_prologue(mpw_ctx* c, double dt) {
+mpw_status step_prologue(mpw_ctx* c, double dt, bool revive = true) {
   mpw_status st;
   const double tn = c->t;
   if ((st = validate_step(c, dt, tn))) return st;
   if (any_moving(c) || !c->flags_valid)
-    if ((st = run_flags(c, tn))) return st;
+    if ((st = run_flags(c, tn, revive))) return st;
   return ensure_u_exponents(c);
 }
 }  // namespace
@@ -1821,7 +1827,9 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
     }
     ++acc;
     for (int m = 0; m < 4; ++m) {
-      if (m > 0 && (st = step_prologue(c, dt))) return st;
+      // flags of the step; no revival (its values would be overwritten before
+      // any read, see run_flags)
+      if (m > 0 && (st = step_prologue(c, dt, false))) return st;
       const double tn = c->t;
       // Global-to-Local reads the global only around each local patch: its
       // covered box of this step, widened by the interpolation window, the

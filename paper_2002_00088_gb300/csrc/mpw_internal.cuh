@@ -147,6 +147,7 @@ struct FlagArgs {
   Box box[MAX_PATCHES];
   int buffer;
   int old_valid;
+  int skip_revive;     // flags only: the revived cells keep what u holds (see run_flags)
   double* Ug;          // global u (psi; Pi at +vol)
   Geom gg;
   const double* Uloc[MAX_PATCHES];

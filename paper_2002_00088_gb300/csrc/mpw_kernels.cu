@@ -347,7 +347,7 @@ static void launch_flags_t(const FlagArgs& a, unsigned blocks, unsigned rblocks,
     k_cdt<<<cb, 256, 0, s>>>(a, 2, a.cov + 2 * ncov, a.cov);
   }
   k_flags<P, ST><<<blocks, 256, 0, s>>>(a);
-  if (a.old_valid) k_revive<P, ST><<<rblocks, 256, 0, s>>>(a);
+  if (a.old_valid && !a.skip_revive) k_revive<P, ST><<<rblocks, 256, 0, s>>>(a);
 }
 
 int launch_flags(const FlagArgs& a, void* stream) {
@@ -366,7 +366,7 @@ int launch_flags(const FlagArgs& a, void* stream) {
     a.P == 6 ? launch_flags_t<6, double>(a, blocks, rblocks, s) : launch_flags_t<5, double>(a, blocks, rblocks, s);
   bool any_sph = false;
   for (int q = 0; q < a.nloc; ++q) any_sph = any_sph || a.sph[q];
-  return (a.old_valid ? 2 : 1) + (a.cov_off[a.nloc] > 0 ? 1 : 0) + (any_sph ? 3 : 0);
+  return (a.old_valid && !a.skip_revive ? 2 : 1) + (a.cov_off[a.nloc] > 0 ? 1 : 0) + (any_sph ? 3 : 0);
 }
 
 // ---------------------------------------------------------------------------
