@@ -113,16 +113,74 @@ __device__ __forceinline__ double lap4(const double* __restrict__ u, const Dims&
   return __dmul_rn(__dadd_rn(__dadd_rn(sx, sy), sz), inv12h2);
 }
 
-__global__ void k_absmax(const double* psi, const double* pi, Dims d, double delta, unsigned* maxbits) {
-  const long long P = d.points(), N = P * d.batch;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += (long long)gridDim.x * blockDim.x) {
-    const long long i = base + threadIdx.x;
-    unsigned m = 0;
-    if (i < N) m = __float_as_uint(__double2float_rn(fmax(fabs(psi[i]), __dmul_rn(delta, fabs(pi[i])))));
-    // a warp's 32 indices lie in one sample (P is a multiple of 128)
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && base + (threadIdx.x & ~31) < N) atomicMax(&maxbits[(base + threadIdx.x) / P], m);
+// Per-sample maxima of binary32 bit patterns (non-negative values, so the
+// integer order is the float order) over a 256-thread block: each warp keeps
+// the maximum of its current sample (a warp's 32 indices lie in one sample,
+// P being a multiple of 128) and flushes it when the sample changes; at the
+// end the block merges its warps and issues one atomic per sample it saw,
+// instead of one per warp and iteration on the same few addresses.
+struct BlockMax {
+  long long cur = -1;
+  unsigned m[2] = {0u, 0u};
+  __device__ void flush(unsigned* out, int nv) {
+    if (cur < 0) return;
+    for (int v = 0; v < nv; ++v) {
+      const unsigned r = __reduce_max_sync(0xffffffffu, m[v]);
+      if ((threadIdx.x & 31) == 0 && r) atomicMax(&out[nv * cur + v], r);
+    }
   }
+  // warp-uniform: the sample of this warp's indices
+  __device__ void enter(long long b, unsigned* out, int nv) {
+    if (b == cur) return;
+    flush(out, nv);
+    cur = b;
+    m[0] = m[1] = 0u;
+  }
+  __device__ void finish(unsigned* out, int nv) {
+    __shared__ long long wb[8];
+    __shared__ unsigned wm[8][2];
+    const int warp = threadIdx.x >> 5;
+    unsigned r[2] = {0u, 0u};
+    for (int v = 0; v < nv; ++v) r[v] = __reduce_max_sync(0xffffffffu, m[v]);
+    if ((threadIdx.x & 31) == 0) {
+      wb[warp] = cur;
+      wm[warp][0] = r[0];
+      wm[warp][1] = r[1];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long b = -1;
+      unsigned acc[2] = {0u, 0u};
+      for (int w = 0; w <= (int)(blockDim.x >> 5); ++w) {
+        const long long bw = w < (int)(blockDim.x >> 5) ? wb[w] : -2;
+        if (bw != b) {
+          if (b >= 0)
+            for (int v = 0; v < nv; ++v)
+              if (acc[v]) atomicMax(&out[nv * b + v], acc[v]);
+          b = bw;
+          acc[0] = acc[1] = 0u;
+        }
+        if (w < (int)(blockDim.x >> 5) && bw >= 0) {
+          acc[0] = max(acc[0], wm[w][0]);
+          acc[1] = max(acc[1], wm[w][1]);
+        }
+      }
+    }
+  }
+};
+
+__global__ void __launch_bounds__(256) k_absmax(const double* psi, const double* pi, Dims d, double delta,
+                                                unsigned* maxbits) {
+  const long long P = d.points(), N = P * d.batch;
+  BlockMax bm;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += (long long)gridDim.x * blockDim.x) {
+    const long long wfirst = base + (threadIdx.x & ~31);
+    if (wfirst >= N) break;  // warp-uniform
+    bm.enter(wfirst / P, maxbits, 1);
+    const long long i = base + threadIdx.x;
+    if (i < N) bm.m[0] = max(bm.m[0], __float_as_uint(__double2float_rn(fmax(fabs(psi[i]), __dmul_rn(delta, fabs(pi[i]))))));
+  }
+  bm.finish(maxbits, 1);
 }
 
 // Per-sample products that the feature and update kernels would otherwise
@@ -152,11 +210,6 @@ struct Coef {
   double delta, d2, d3, d4, d5, d6, hd2, d36, d424, inv12h2, sigma;
 };
 
-__device__ __forceinline__ void point_ijk(long long q, const Dims& d, int& i, int& j, int& k) {
-  i = (int)(q % d.n0);
-  j = (int)((q / d.n0) % d.n1);
-  k = (int)(q / ((long long)d.n0 * d.n1));
-}
 
 // lap: the chain L psi, L Pi, L^2 psi, L^2 Pi, L^3 psi, L^3 Pi ([6][batch * points])
 __global__ void k_features(const double* psi, const double* pi, Dims d, const double* sc, const double* lap,
@@ -250,28 +303,25 @@ unsigned grid_for(long long n, int threads = 256) {
 // leaves O(Delta^5) for the exact evolution.  lap: L psi0, L Pi0, L psi1,
 // L Pi1.  Writes, per sample, max(|R_psi|, Delta |R_Pi|) and max(|psi0|,
 // Delta |Pi0|) as binary32 bit patterns (atomic maximum).
-__global__ void k_check(const double* psi0, const double* pi0, const double* psi1, const double* pi1, Dims d, Coef c,
-                        const double* lap, unsigned* out) {
+__global__ void __launch_bounds__(256) k_check(const double* psi0, const double* pi0, const double* psi1,
+                                               const double* pi1, Dims d, Coef c, const double* lap, unsigned* out) {
   const long long P = d.points(), N = P * d.batch;
   const double hd = 0.5 * c.delta, d12 = c.d2 / 12.0;
+  BlockMax bm;
   for (long long base = (long long)blockIdx.x * blockDim.x; base < N; base += (long long)gridDim.x * blockDim.x) {
+    const long long wfirst = base + (threadIdx.x & ~31);
+    if (wfirst >= N) break;  // warp-uniform
+    bm.enter(wfirst / P, out, 2);
     const long long g = base + threadIdx.x;
-    unsigned r = 0, m = 0;
     if (g < N) {
       const double lp0 = lap[g], lq0 = lap[N + g], lp1 = lap[2 * N + g], lq1 = lap[3 * N + g];
       const double rp = (psi1[g] - psi0[g]) - hd * (pi0[g] + pi1[g]) + d12 * (lp1 - lp0);
       const double rq = (pi1[g] - pi0[g]) - hd * (lp0 + lp1) + d12 * (lq1 - lq0);
-      r = __float_as_uint(__double2float_ru(fmax(fabs(rp), c.delta * fabs(rq))));
-      m = __float_as_uint(__double2float_rn(fmax(fabs(psi0[g]), c.delta * fabs(pi0[g]))));
-    }
-    r = __reduce_max_sync(0xffffffffu, r);
-    m = __reduce_max_sync(0xffffffffu, m);
-    if ((threadIdx.x & 31) == 0 && base + (threadIdx.x & ~31) < N) {
-      const long long b = (base + threadIdx.x) / P;
-      atomicMax(&out[2 * b], r);
-      atomicMax(&out[2 * b + 1], m);
+      bm.m[0] = max(bm.m[0], __float_as_uint(__double2float_ru(fmax(fabs(rp), c.delta * fabs(rq)))));
+      bm.m[1] = max(bm.m[1], __float_as_uint(__double2float_rn(fmax(fabs(psi0[g]), c.delta * fabs(pi0[g])))));
     }
   }
+  bm.finish(out, 2);
 }
 
 struct HermiteBoxes {
