@@ -818,9 +818,14 @@ mpw_status prep_mirrors(mpw_ctx* c, int b, double t, MirrorArgs& m, int mir_glob
 // global's covered cells are read).
 enum FillParts { FILL_ALL = 0, FILL_G2L = 1, FILL_L2G = 2 };
 
+// gdonor >= 0 (Global-to-Local fills only): the global patch donates from
+// buffer gdonor instead of b, and the fill clears no exponent slot of the
+// global patch (the hybrid step lays the global's stage states out in their
+// own buffers ahead of the substages).
 mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, MirrorArgs* mirrors = nullptr,
-                     int parts = FILL_ALL) {
+                     int parts = FILL_ALL, int gdonor = -1) {
   const bool g2l_only = parts == FILL_G2L, l2g_only = parts == FILL_L2G;
+  if (gdonor >= 0 && !g2l_only) return set_err(MPW_ERR_STATE, "a global donor buffer needs a Global-to-Local fill");
   const PatchState& g = c->p[0];
   a = FillArgs{};
   int mir_global[MAX_PATCHES], mir_shell[MAX_PATCHES];
@@ -921,7 +926,7 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
     S.gt = L.g;
     S.tpatch = q + 1;
     S.dpatch = 0;
-    S.D = g.buf(b);
+    S.D = g.buf(gdonor >= 0 ? gdonor : b);
     S.gd = g.g;
     const Frame f = frame(L.d, t);
     // a rotated ghost shell: per-point sums through X_B = R X' + X0 (fixed-point
@@ -955,16 +960,19 @@ mpw_status prep_fill(mpw_ctx* c, int b, double t, int reset_buf, FillArgs& a, Mi
   a.expo = c->d_expo;
   a.y_buf = b;
   a.reset_buf = reset_buf;
+  a.reset_first = gdonor >= 0 ? 1 : 0;
+  a.gdonor_use = gdonor >= 0 ? 1 : 0;
+  a.gdonor_buf = gdonor >= 0 ? gdonor : 0;
   a.np = (int)c->p.size();
   a.fixed = c->cfg.arith != 1;
   a.f32 = c->cfg.precision == 32;
   return MPW_OK;
 }
 
-mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf, int parts = FILL_ALL) {
+mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf, int parts = FILL_ALL, int gdonor = -1) {
   FillArgs a;
   MirrorArgs m;
-  if (mpw_status st = prep_fill(c, b, t, reset_buf, a, &m, parts)) return st;
+  if (mpw_status st = prep_fill(c, b, t, reset_buf, a, &m, parts, gdonor)) return st;
   c->launch_begin(MPW_KERNEL_FILL);
   if (m.nr > 0) {
     launch_mirror(m, c->stream);
@@ -1845,17 +1853,25 @@ mpw_status mpw_step_surrogate(mpw_ctx* c, mpw_sur* s, double dt, int calls, doub
         }
         donors.push_back(w);
       }
+      // the global's four stage states of the step (the stage inputs the
+      // method would form there, from the interpolant), laid out in its four
+      // buffers at once: substages 0-2 in the buffers the fills read, the
+      // last in ACC (the global's own RHS is skipped, so ACC is free), which
+      // the last fill takes as the global's donor buffer
+      static const int GBUF[4] = {BUF_U, BUF_YA, BUF_YB, BUF_ACC};
+      double* gb[4];
+      int* gs[4];
+      for (int l = 0; l < 4; ++l) {
+        gb[l] = G.buf(GBUF[l]);
+        gs[l] = c->d_expo + GBUF[l] * 2;
+      }
+      CUDA_TRY(cudaMemsetAsync(c->d_expo, 0, 8 * sizeof(int), c->stream));  // live slots of the global's 4 buffers
+      launch_hermite(gb, gs, G.g, U, coef + 4 * m * 6, donors.data(), (int)donors.size(), c->stream);
+      CUDA_TRY(cudaGetLastError());
       for (int l = 0; l < 4; ++l) {
         const double tl = tn + RK_C[l] * dt;
-        // the global stage buffer holds the stage input the method would
-        // have formed, from the interpolant; only the local patches take an
-        // RHS + stage update
-        int* slot2 = c->d_expo + FILL_BUF[l] * 2;
-        CUDA_TRY(cudaMemsetAsync(slot2, 0, 2 * sizeof(int), c->stream));
-        launch_hermite(G.buf(FILL_BUF[l]), G.g, U, coef + (4 * m + l) * 6, slot2, donors.data(), (int)donors.size(),
-                       c->stream);
-        CUDA_TRY(cudaGetLastError());
-        if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], FILL_G2L))) return st;
+        // only the local patches take an RHS + stage update
+        if ((st = run_fill(c, FILL_BUF[l], tl, NEXT_BUF[l], FILL_G2L, GBUF[l]))) return st;
         if ((st = run_rhs(c, l, tl, dt, true))) return st;
       }
       c->t = tn + dt;

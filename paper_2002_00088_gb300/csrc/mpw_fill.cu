@@ -74,6 +74,13 @@ __device__ void report_block_max(int* slot2, int e0, int e1) {
 }
 
 // Position of target index i along axis a in the donor's index units.
+// The buffer whose exponent slots scale a segment's donor values: the one
+// being filled, or for the global patch an override (the hybrid step's
+// prescribed stage states, laid out in other buffers).
+__device__ __forceinline__ int donor_buf(const FillArgs& A, const InterpSeg& S) {
+  return S.dpatch == 0 && A.gdonor_use ? A.gdonor_buf : A.y_buf;
+}
+
 __device__ __forceinline__ double donor_index(const InterpSeg& S, int a, int i) {
   return ((S.gt.lo[a] + (i + 0.5) * S.gt.h[a] + S.shift[a]) - S.gd.lo[a]) / S.gd.h[a] - 0.5;
 }
@@ -416,7 +423,7 @@ template <int P, typename ST>
 __device__ __forceinline__ void l2g_point(const FillArgs& A, const InterpSeg& S, int i, int j, int k, int& e0,
                                           int& e1) {
   constexpr bool F32 = sizeof(ST) == 4;
-  const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+  const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + donor_buf(A, S) * 2;
   const bool fx = !F32 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
   if (fx) {
     double sidx[3];
@@ -517,7 +524,7 @@ __device__ __forceinline__ bool gather_mirror(const InterpSeg& S, const double s
 template <int P, typename ST>
 __device__ __forceinline__ void l2g_point_sph(const FillArgs& A, const InterpSeg& S, int i, int j, int k, int& e0,
                                               int& e1) {
-  const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+  const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + donor_buf(A, S) * 2;
   const bool fx = sizeof(ST) == 8 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
   double xf[3], q[3];
   affine(S.M, S.shift, S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
@@ -575,7 +582,7 @@ __device__ __noinline__ void sph_ghost_block(const FillArgs& A, const InterpSeg&
       sph_to_cart(S.gt.lo[0] + (i + 0.5) * S.gt.h[0], S.gt.lo[1] + (j + 0.5) * S.gt.h[1],
                   S.gt.lo[2] + (k + 0.5) * S.gt.h[2], xl);
       affine(S.M, S.shift, xl[0], xl[1], xl[2], xb[0], xb[1], xb[2]);
-      const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+      const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + donor_buf(A, S) * 2;
       const bool fx = !F32 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
       double v0, v1;
       bool ok;
@@ -748,7 +755,7 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
   if (S.kind == SEG_AFFINE) {
     // rotated target grid: the 1-D weights differ from point to point
     int emax[2] = {0, 0};
-    const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+    const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + donor_buf(A, S) * 2;
     const bool fx = !F32 && A.fixed && dslot[0] < EXP_NONFINITE && dslot[1] < EXP_NONFINITE;
     if (!fx || !affine_tile_fixed<P>(A, S, org, T, dslot[0], dslot[1], sm, emax))
       direct_points<P, ST>(A, S, org, T, emax);
@@ -817,7 +824,7 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
     // donor scale: the largest exponent of the donor buffer's live values
     // (complete before this launch; the fill itself only raises the ghost
     // slots), so the scale is known before the donors are read
-    const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + A.y_buf * 2;
+    const int* dslot = A.expo + S.dpatch * EXP_SLOTS_PER_PATCH + donor_buf(A, S) * 2;
     const int Es = dslot[0], Ep = dslot[1];
     if (F32) {
       thin_pass<P, M_FP32, ST>(S, a0, D0, Dn, T[a0], BF, 0, 0, R1);
@@ -887,9 +894,9 @@ __device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
   extern __shared__ double fill_smem[];
   const int ntile = A.total_blocks - A.outer_blocks;
   const int b = b0 < ntile ? b0 + A.outer_blocks : b0 - ntile;
-  if (A.reset_buf >= 0 && b0 == 0 && threadIdx.x < 2 * A.np)
+  if (A.reset_buf >= 0 && b0 == 0 && threadIdx.x >= 2 * A.reset_first && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
-  if (A.reset_buf >= 0 && b0 == 0 && threadIdx.x < 2 * A.np)
+  if (A.reset_buf >= 0 && b0 == 0 && threadIdx.x >= 2 * A.reset_first && threadIdx.x < 2 * A.np)
     A.expo[(threadIdx.x >> 1) * EXP_SLOTS_PER_PATCH + EXP_GHOST + A.reset_buf * 2 + (threadIdx.x & 1)] = 0;
   if (b < A.outer_blocks) {
     // global outer ghost shell, one point per thread

@@ -77,6 +77,9 @@ struct FillArgs {
   int* expo;
   int y_buf;           // buffer being filled (its exponent slots receive the ghost values)
   int reset_buf;       // buffer whose exponent slots are cleared (the next stage's output), or -1
+  int reset_first;     // first patch whose slots that clears (0: every patch)
+  int gdonor_use;      // 1: the global patch donates from buffer gdonor_buf, not y_buf
+  int gdonor_buf;
   int np;
   int total_blocks;
   int fixed;           // 1: separable contractions in int64 fixed point, 0: native FP64
@@ -194,13 +197,14 @@ constexpr int DIST_CAP = 9;          // distances above buffer + NG (<= 8) read 
 // Record the thread-local message returned by mpw_last_error().
 void set_last_error(const char* msg);
 
-// learned surrogate: the quintic Hermite interpolant in time of the global
-// state between two calls, written into the cells of `boxes` of a padded
-// buffer (u: psi0, Pi0, psi1, Pi1, L psi0, L Pi0, L psi1, L Pi1, dense;
-// coef_dev: six device doubles), and the step and spacing a surrogate was
+// learned surrogate: the four RK4 stage states of one step from the quintic
+// Hermite interpolant in time of the global state between two calls, written
+// into the cells of `boxes` of four padded buffers, their exponent slots
+// raised (u: psi0, Pi0, psi1, Pi1, L psi0, L Pi0, L psi1, L Pi1, dense;
+// coef_dev: 4 x 6 device doubles); and the step and spacing a surrogate was
 // made for
-void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, const Box* boxes,
-                    int nbox, void* stream);
+void launch_hermite(double* const buf[4], int* const slot2[4], const Geom& g, const double* u, const double* coef_dev,
+                    const Box* boxes, int nbox, void* stream);
 bool sur_geometry(const mpw_sur* s, double* dt, double* h, void** stream);
 // mpw_sur_check for batch 1 right after mpw_sur_predict(s, psi0, pi0, ...):
 // L psi0 and L Pi0 are copied from the prediction's features instead of

@@ -329,38 +329,56 @@ struct HermiteBoxes {
   mpw::Box b[mpw::MAX_PATCHES];
 };
 
-// Quintic Hermite interpolant in time of the state between two calls, written
-// into the cells of the given boxes of a padded patch buffer: y(tau) = c0 y0 + c1 y0' + c2 y0''
-// + c3 y1 + c4 y1' + c5 y1'' (coefficients: the basis at tau times Delta^k),
-// with y = psi, y' = Pi, y'' = L psi for psi and y = Pi, y' = L psi, y'' = L Pi
-// for Pi.  slot2 receives the largest biased exponent of each field.
-__global__ void k_hermite(double* buf, mpw::Geom g, const double* u, long long P, const double* cf, int* slot2,
-                          HermiteBoxes hb) {
+// Quintic Hermite interpolant in time of the state between two calls: the
+// four RK4 stage states of one step, written into the cells of the given
+// boxes of four padded patch buffers in one pass.  Stage k is
+// y = c0 y0 + c1 y0' + c2 y0'' + c3 y1 + c4 y1' + c5 y1'' (cf[6 k ..]: the
+// basis and its derivatives at the step's start, times Delta^k, combined as
+// the RK4 stage input of a linear system), with y = psi, y' = Pi, y'' = L psi
+// for psi and y = Pi, y' = L psi, y'' = L Pi for Pi.  slot[k] receives the
+// largest biased exponent of each field of buffer k (one atomic per block).
+struct HermiteOut {
+  double* buf[4];
+  int* slot[4];
+};
+
+__global__ void __launch_bounds__(256) k_hermite(HermiteOut out, mpw::Geom g, const double* u, long long P,
+                                                 const double* cf, HermiteBoxes hb) {
   const double *psi0 = u, *pi0 = u + P, *psi1 = u + 2 * P, *pi1 = u + 3 * P;
   const double *lp0 = u + 4 * P, *lq0 = u + 5 * P, *lp1 = u + 6 * P, *lq1 = u + 7 * P;
   const mpw::Box& bx = hb.b[blockIdx.y];
   const int w0 = bx.hi[0] - bx.lo[0] + 1, w1 = bx.hi[1] - bx.lo[1] + 1, w2 = bx.hi[2] - bx.lo[2] + 1;
   const long long V = (long long)w0 * w1 * w2;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < V; base += (long long)gridDim.x * blockDim.x) {
-    const long long e = base + threadIdx.x;
-    int e0 = 0, e1 = 0;
-    if (e < V) {
-      const int i = bx.lo[0] + (int)(e % w0), j = bx.lo[1] + (int)((e / w0) % w1), k = bx.lo[2] + (int)(e / ((long long)w0 * w1));
-      const long long q = ((long long)k * g.n[1] + j) * g.n[0] + i;
-      const double ys = cf[0] * psi0[q] + cf[1] * pi0[q] + cf[2] * lp0[q] + cf[3] * psi1[q] + cf[4] * pi1[q] + cf[5] * lp1[q];
-      const double yp = cf[0] * pi0[q] + cf[1] * lp0[q] + cf[2] * lq0[q] + cf[3] * pi1[q] + cf[4] * lp1[q] + cf[5] * lq1[q];
-      const long long a = g.at(i, j, k);
-      buf[a] = ys;
-      buf[g.vol + a] = yp;
-      e0 = mpw::biased_exponent(ys);
-      e1 = mpw::biased_exponent(yp);
+  int em[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < V; e += (long long)gridDim.x * blockDim.x) {
+    const int i = bx.lo[0] + (int)(e % w0), j = bx.lo[1] + (int)((e / w0) % w1), k = bx.lo[2] + (int)(e / ((long long)w0 * w1));
+    const long long q = ((long long)k * g.n[1] + j) * g.n[0] + i;
+    const double a0 = psi0[q], a1 = pi0[q], a2 = lp0[q], a3 = psi1[q], a4 = pi1[q], a5 = lp1[q];
+    const double b2 = lq0[q], b5 = lq1[q];
+    const long long at = g.at(i, j, k);
+#pragma unroll
+    for (int st = 0; st < 4; ++st) {
+      const double* c = cf + 6 * st;
+      const double ys = c[0] * a0 + c[1] * a1 + c[2] * a2 + c[3] * a3 + c[4] * a4 + c[5] * a5;
+      const double yp = c[0] * a1 + c[1] * a2 + c[2] * b2 + c[3] * a4 + c[4] * a5 + c[5] * b5;
+      out.buf[st][at] = ys;
+      out.buf[st][g.vol + at] = yp;
+      em[2 * st] = max(em[2 * st], mpw::biased_exponent(ys));
+      em[2 * st + 1] = max(em[2 * st + 1], mpw::biased_exponent(yp));
     }
-    e0 = __reduce_max_sync(0xffffffffu, e0);
-    e1 = __reduce_max_sync(0xffffffffu, e1);
-    if ((threadIdx.x & 31) == 0) {
-      if (e0) atomicMax(&slot2[0], e0);
-      if (e1) atomicMax(&slot2[1], e1);
-    }
+  }
+  __shared__ int bm[8][8];
+  const int warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    const int r = __reduce_max_sync(0xffffffffu, em[v]);
+    if ((threadIdx.x & 31) == 0) bm[warp][v] = r;
+  }
+  __syncthreads();
+  if (threadIdx.x < 8) {
+    int r = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) r = max(r, bm[w][threadIdx.x]);
+    if (r) atomicMax(out.slot[threadIdx.x >> 1] + (threadIdx.x & 1), r);
   }
 }
 
@@ -715,8 +733,8 @@ mpw_status sur_check_after_predict(mpw_sur* s, const double* psi0, const double*
   return MPW_OK;
 }
 
-void launch_hermite(double* buf, const Geom& g, const double* u, const double* coef_dev, int* slot2, const Box* boxes,
-                    int nbox, void* stream) {
+void launch_hermite(double* const buf[4], int* const slot2[4], const Geom& g, const double* u, const double* coef_dev,
+                    const Box* boxes, int nbox, void* stream) {
   if (nbox <= 0) return;
   HermiteBoxes hb{};
   hb.nb = nbox;
@@ -728,9 +746,14 @@ void launch_hermite(double* buf, const Geom& g, const double* u, const double* c
     vmax = std::max(vmax, v);
   }
   if (vmax == 0) return;
+  HermiteOut out{};
+  for (int k = 0; k < 4; ++k) {
+    out.buf[k] = buf[k];
+    out.slot[k] = slot2[k];
+  }
   const long long P = (long long)g.n[0] * g.n[1] * g.n[2];
   const dim3 grid(grid_for(vmax), (unsigned)nbox);
-  k_hermite<<<grid, 256, 0, (cudaStream_t)stream>>>(buf, g, u, P, coef_dev, slot2, hb);
+  k_hermite<<<grid, 256, 0, (cudaStream_t)stream>>>(out, g, u, P, coef_dev, hb);
 }
 
 bool sur_geometry(const mpw_sur* s, double* dt, double* h, void** stream) {
