@@ -708,11 +708,14 @@ def run_surrogate(args):
                                 else "k_conv3 (network forward, mma.sync BF16/FP32)"),
                      "achieved": achieved, "peak": peak, "peak_source": peak_src, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None, "avg_launch_ms": fwd_ms / 4},
-        # per accepted call: features 6 (maximum, scale, three Laplacian passes,
-        # features), network 4, update 1, check 3, then per substage Hermite,
-        # fill and RHS (48), cover flags and revival per step (8), the global
-        # unpack (1); the first call adds a fill, the dead-cell fill and a pack
-        "gpu_launches": calls * (6 + 4 + 1 + 3 + 48 + 8 + 1) + 3,
+        # per accepted call: cover flags and revival 2, the Local-to-Global fill
+        # 1, the dead-cell fill 1, the pack 1, the global's exponent scan 1,
+        # features 7 (maximum, scale, three Laplacians, per-sample products,
+        # features), network 4, update 1, check 2 (Laplacian, residual), per
+        # step the Hermite stage states 1 and 4 x (fill + RHS), cover flags on
+        # steps 2-4 (3), the unpack 1: 60; the first call has no revival and
+        # scans the exponents of all three patches (+1)
+        "gpu_launches": calls * 60 + 1,
         "clocks": clocks,
     }
     if not args.no_cpu_baseline:
