@@ -1445,16 +1445,39 @@ static mpw_status ensure_async_io(mpw_ctx* c, PatchState& P) {
 
 // Inputs queued by mpw_set_fields_async enter u, in stream order, before
 // anything reads or writes u.
+// Unpack new values into u of patch q.  On binary64 contexts the same pass
+// raises u's live exponent slots when it can tell the live cells: every cell
+// of a local patch, and the global's by the current cover flags (a cell those
+// flags exclude and the next flags make live is revived, which raises the
+// slot itself; a cell they count and the next flags drop only raises the
+// bound).  Otherwise the slots are recomputed before the next step.
+static mpw_status unpack_u(mpw_ctx* c, size_t q, const double* s0, const double* s1) {
+  PatchState& P = c->p[q];
+  const bool single = c->p.size() == 1;
+  if (c->cfg.precision == 64 && (q > 0 || single || c->flags_valid)) {
+    int* slot2 = c->d_expo + q * EXP_SLOTS_PER_PATCH + BUF_U * 2;
+    CUDA_TRY(cudaMemsetAsync(slot2, 0, 2 * sizeof(int), c->stream));
+    launch_unpack_scan(static_cast<double*>(P.buf(BUF_U)), P.g, s0, s1, q == 0 && !single ? c->d_flags : nullptr,
+                       slot2, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    P.u_expo_valid = true;
+    return MPW_OK;
+  }
+  launch_unpack(P.buf(BUF_U), P.g, s0, s1, c->cfg.precision == 32, c->stream);
+  CUDA_TRY(cudaGetLastError());
+  P.u_expo_valid = false;
+  return MPW_OK;
+}
+
 static mpw_status apply_pending_inputs(mpw_ctx* c) {
-  for (auto& P : c->p) {
+  for (size_t q = 0; q < c->p.size(); ++q) {
+    PatchState& P = c->p[q];
     if (!P.in_pending) continue;
     const size_t n = (size_t)P.d.n[0] * P.d.n[1] * P.d.n[2];
     CUDA_TRY(cudaStreamWaitEvent(c->stream, P.in_copied, 0));
-    launch_unpack(P.buf(BUF_U), P.g, P.io_in, P.io_in + n, c->cfg.precision == 32, c->stream);
-    CUDA_TRY(cudaGetLastError());
+    if (mpw_status st = unpack_u(c, q, P.io_in, P.io_in + n)) return st;
     CUDA_TRY(cudaEventRecord(P.in_free, c->stream));
     P.in_pending = false;
-    P.u_expo_valid = false;
   }
   return MPW_OK;
 }
@@ -1492,9 +1515,7 @@ mpw_status mpw_set_fields(mpw_ctx* c, int patch, const double* psi, const double
     s0 = c->d_stage;
     s1 = c->d_stage + n;
   }
-  launch_unpack(P->buf(BUF_U), P->g, s0, s1, c->cfg.precision == 32, c->stream);
-  CUDA_TRY(cudaGetLastError());
-  P->u_expo_valid = false;
+  if ((st = unpack_u(c, (size_t)patch, s0, s1))) return st;
   if (!on_device) CUDA_TRY(cudaStreamSynchronize(c->stream));
   return MPW_OK;
 }

@@ -253,5 +253,9 @@ void launch_analytic(void* buf, const Geom& g, const Affine& map, int akind, int
 void launch_pack(const void* buf, const Geom& g, double* d0, double* d1, int padded, const uint8_t* flags, bool f32,
                  void* stream);
 void launch_unpack(void* buf, const Geom& g, const double* d0, const double* d1, bool f32, void* stream);
+// unpack into a binary64 u, raising its live exponent slots (slot2, cleared
+// first by the caller) over the cells flags count as live (flags may be null)
+void launch_unpack_scan(double* buf, const Geom& g, const double* d0, const double* d1, const uint8_t* flags,
+                        int* slot2, void* stream);
 
 }  // namespace mpw

@@ -468,6 +468,57 @@ __global__ void k_unpack(ST* buf, const Geom g, const double* __restrict__ d0, c
   buf[c + g.vol] = (ST)d1[idx];
 }
 
+// k_unpack for binary64 buffers that also raises the buffer's exponent slots
+// (slot2, cleared before the launch) with the largest biased exponent of the
+// live values it writes, as k_expo_scan would, so that u needs no second
+// pass.  flags (global patch, or null): cells flagged GHOST or DEAD are
+// written but not counted.  Rows of the interior are spread over the blocks,
+// the threads of a block along x; one atomic per field and block.
+__global__ void __launch_bounds__(128) k_unpack_scan(double* buf, const Geom g, const double* __restrict__ d0,
+                                                     const double* __restrict__ d1,
+                                                     const uint8_t* __restrict__ flags, int* slot2) {
+  const int n0 = g.n[0], n1 = g.n[1];
+  const int rows = n1 * g.n[2];
+  int e0 = 0, e1 = 0;
+  for (int r = blockIdx.x; r < rows; r += gridDim.x) {
+    const int j = r % n1, k = r / n1;
+    const long long base = (long long)r * n0;
+    const long long c0 = g.at(0, j, k);
+    for (int i = threadIdx.x; i < n0; i += blockDim.x) {
+      const double a = d0[base + i], b = d1[base + i];
+      buf[c0 + i] = a;
+      buf[c0 + i + g.vol] = b;
+      if (flags) {
+        const int f = flags[base + i] & 3;
+        if (f == FLAG_GHOST || f == FLAG_DEAD) continue;
+      }
+      e0 = max(e0, biased_exponent(a));
+      e1 = max(e1, biased_exponent(b));
+    }
+  }
+  __shared__ int red[2];
+  if (threadIdx.x == 0) red[0] = red[1] = 0;
+  __syncthreads();
+  e0 = __reduce_max_sync(0xffffffffu, e0);
+  e1 = __reduce_max_sync(0xffffffffu, e1);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(&red[0], e0);
+    atomicMax(&red[1], e1);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    if (red[0]) atomicMax(&slot2[0], red[0]);
+    if (red[1]) atomicMax(&slot2[1], red[1]);
+  }
+}
+
+void launch_unpack_scan(double* buf, const Geom& g, const double* d0, const double* d1, const uint8_t* flags,
+                        int* slot2, void* stream) {
+  const int rows = g.n[1] * g.n[2];
+  const int blocks = rows < 152 * 16 ? rows : 152 * 16;
+  if (blocks > 0) k_unpack_scan<<<blocks, 128, 0, (cudaStream_t)stream>>>(buf, g, d0, d1, flags, slot2);
+}
+
 void launch_unpack(void* buf, const Geom& g, const double* d0, const double* d1, bool f32, void* stream) {
   const long long N = (long long)g.n[0] * g.n[1] * g.n[2];
   const unsigned blocks = (unsigned)((N + 255) / 256);
