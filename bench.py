@@ -482,7 +482,9 @@ def run_batch(args):
     live = sum(g.live_points() for g in sims)
     b = mpw.Batch(sims)
     b.step(dts, args.warmup + 4)  # warm-up, including the four chunk-depth trials
-    zc, zc_ms, _, g0 = b.tuning()
+    zc, zc_ms, n0, g0 = b.tuning()
+    for g in sims:
+        g.profile_read()  # clears the per-instance launch counters
     sampler = ClockSampler(local)
     sampler.start()
     start, end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -494,6 +496,9 @@ def run_batch(args):
     ms = start.elapsed_time(end)
     clocks = sampler.stop()
     graph_steps = b.tuning()[3] - g0
+    # batched launches (flags included when batched) plus the instances' own
+    # flags launches when they are not
+    launches = b.tuning()[2] - n0 + sum(g.profile_read()["flags"][1] for g in sims)
     del b, sims
     torch.cuda.empty_cache()
     # the same instances, one mpw_step after the other
@@ -519,7 +524,7 @@ def run_batch(args):
                    "instances": len(ws), "live_points": live, "parallelism": "single",
                    "rhs_chunk_depth": zc, "tuning_rhs_ms": zc_ms, "graph_replayed_steps": graph_steps},
         "sequential": {"value": live * 4 * args.steps / (ms_seq * 1e-3), "ms_per_step": ms_seq / args.steps},
-        "gpu_launches": (8 + 4 * -(-sum(1 for w in ws for p in w.patches if p.topology) // 64)) * args.steps,
+        "gpu_launches": launches,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

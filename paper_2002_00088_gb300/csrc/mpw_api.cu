@@ -468,9 +468,14 @@ mpw_status validate_step(mpw_ctx* c, double dt, double t) {
 // global is not read before it is rewritten: every Global-to-Local donor lies
 // in the boxes the Hermite stage states overwrite, and the call ends by
 // writing the surrogate's state over all of u.
-mpw_status run_flags(mpw_ctx* c, double t, bool revive = true) {
+// The arguments of the cover-flag launch at time t (covered boxes, visited
+// regions, revival queue); launch = false when no flag can change (then the
+// flags are already valid).  run_flags launches them; a batched step gathers
+// them for one launch over its instances.
+mpw_status prep_flags(mpw_ctx* c, double t, bool revive, FlagArgs& a, bool& launch) {
   const PatchState& g = c->p[0];
-  FlagArgs a{};
+  launch = false;
+  a = FlagArgs{};
   a.flags = c->d_flags;
   for (int k = 0; k < 3; ++k) a.n[k] = g.d.n[k];
   a.nloc = (int)c->p.size() - 1;
@@ -596,6 +601,15 @@ mpw_status run_flags(mpw_ctx* c, double t, bool revive = true) {
   a.rev_count = c->d_err + 32;
   a.rev_cap = REVIVE_CAP;
   a.f32 = c->cfg.precision == 32;
+  launch = true;
+  return MPW_OK;
+}
+
+mpw_status run_flags(mpw_ctx* c, double t, bool revive = true) {
+  FlagArgs a;
+  bool launch;
+  if (mpw_status st = prep_flags(c, t, revive, a, launch)) return st;
+  if (!launch) return MPW_OK;
   c->launch_begin(MPW_KERNEL_FLAGS);
   const int kernels = launch_flags(a, c->stream);  // flags kernel, plus the revival kernel when old flags exist
   c->launches[MPW_KERNEL_FLAGS] += kernels - 1;
@@ -2001,7 +2015,8 @@ struct mpw_batch {
   // shells of moving patches) rule the graph out.
   cudaStream_t cap = nullptr;    // capture stream
   cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int gtot[2][8] = {};           // the grids each graph launches
+  int gtot[2][9] = {};           // the grids each graph launches (8: batched flags)
+  bool gflags[2] = {false, false};  // whether the graph holds the batched flags launches
   long long captures = 0;
   bool graphs = true;
   long long graph_steps = 0;
@@ -2040,9 +2055,11 @@ mpw_status mpw_batch_create(mpw_ctx* const* ctxs, int n, mpw_batch** out) {
     delete b;
     return MPW_ERR_CUDA;
   }
-  bool ok = cudaMalloc(&b->d_args, 8 * b->region) == cudaSuccess;
+  // regions 0-7: the fill and RHS tables of the 4 substages; 8: the flags
+  static_assert(sizeof(FlagArgs) <= sizeof(FillArgs), "the flags table must fit a region");
+  bool ok = cudaMalloc(&b->d_args, 9 * b->region) == cudaSuccess;
   for (int h = 0; h < 2 && ok; ++h)
-    ok = cudaMallocHost(&b->h_args[h], 8 * b->region) == cudaSuccess &&
+    ok = cudaMallocHost(&b->h_args[h], 9 * b->region) == cudaSuccess &&
          cudaEventCreateWithFlags(&b->copied[h], cudaEventDisableTiming) == cudaSuccess;
   ok = ok && cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) == cudaSuccess;
   for (int z : ZC_CANDIDATES) b->cand.push_back(z);
@@ -2093,15 +2110,55 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     double tn[64];
     std::vector<double> tnv;
     double* tnp = n <= 64 ? tn : (tnv.resize(n), tnv.data());
-    for (int i = 0; i < n; ++i) {
-      tnp[i] = b->ctx[i]->t;
-      if ((st = step_prologue(b->ctx[i], dt[i]))) return st;
-    }
     const int h = (int)(k & 1);
     CUDA_TRY(cudaEventSynchronize(b->copied[h]));  // the pinned half from two steps ago has been copied
+    // cover flags: when every patch of every instance is a translating
+    // Cartesian one and the flags and (binary64) u's exponent slots are in
+    // place, the
+    // moving instances' flags go into the step's launches as one batched
+    // flags launch and one revival launch (argument table in region 8);
+    // otherwise each instance takes its own, here
+    bool fl_batch = true;
+    for (mpw_ctx* c : b->ctx) {
+      fl_batch = fl_batch && c->flags_valid;
+      for (const auto& P : c->p)
+        fl_batch = fl_batch && !P.sph() && P.d.motion != MPW_MOTION_ROTATING &&
+                   (c->cfg.precision == 32 || P.u_expo_valid);
+    }
+    int nflag = 0;
+    {
+      char* freg = b->h_args[h] + (size_t)8 * b->region;
+      FlagArgs* fa = reinterpret_cast<FlagArgs*>(freg);
+      int* fblk0 = reinterpret_cast<int*>(freg + sizeof(FlagArgs) * n);
+      long long ftotal = 0;
+      for (int i = 0; i < n; ++i) {
+        mpw_ctx* c = b->ctx[i];
+        tnp[i] = c->t;
+        fblk0[i] = (int)ftotal;
+        if (!fl_batch) {
+          if ((st = step_prologue(c, dt[i]))) return st;
+          continue;
+        }
+        if ((st = validate_step(c, dt[i], tnp[i]))) return st;
+        bool launch = false;
+        if (any_moving(c) && (st = prep_flags(c, tnp[i], true, fa[i], launch))) return st;
+        if (launch) {
+          ftotal += flags_blocks(fa[i]);
+          c->flags_valid = true;
+          c->glist_valid = false;
+          ++nflag;
+        } else {
+          fa[i] = FlagArgs{};  // no flags this step: the clear and the revival skip it
+        }
+      }
+      fblk0[n] = (int)ftotal;
+      if (ftotal > INT32_MAX / 2) return set_err(MPW_ERR_ARG, "batched flags grid too large");
+    }
+    const bool fl_on = fl_batch && nflag > 0;
     std::vector<MirrorArgs> mirs(4 * (size_t)n);    // fixed-point mirrors of each instance's fills
     // arguments of the 8 launches of this step into pinned half h
-    int totals[8];
+    int totals[9];
+    totals[8] = fl_on ? reinterpret_cast<int*>(b->h_args[h] + (size_t)8 * b->region + sizeof(FlagArgs) * n)[n] : 0;
     for (int l = 0; l < 4; ++l) {
       for (int pass = 0; pass < 2; ++pass) {  // 0: ghost fill, 1: RHS + stage
         const int r = 2 * l + pass;
@@ -2158,23 +2215,33 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
     const bool use_graph = b->graphs && !trial && !(moving && by_value);
     // the grids: the block totals, or while replaying a moving batch the
     // graph's padded capacities (a new capture when a total outgrows them)
-    int grid[8];
+    int grid[9];
     std::memcpy(grid, totals, sizeof(grid));
     bool recapture = false;
     if (use_graph) {
-      if (!b->gexec[h]) {
+      if (!b->gexec[h] || b->gflags[h] != fl_on) {
         recapture = true;
       } else if (moving) {
-        for (int r = 0; r < 8; ++r) recapture = recapture || totals[r] > b->gtot[h][r];
+        for (int r = 0; r < 9; ++r) recapture = recapture || totals[r] > b->gtot[h][r];
       } else {
         recapture = std::memcmp(b->gtot[h], totals, sizeof(totals)) != 0;
       }
       if (moving)
-        for (int r = 0; r < 8; ++r)
+        for (int r = 0; r < 9; ++r)
           grid[r] = recapture ? totals[r] + totals[r] / 16 + 64 : std::max(totals[r], b->gtot[h][r]);
     }
     // copies and launches of the step, on stream sm
     auto enqueue = [&](cudaStream_t sm) -> cudaError_t {
+      if (fl_on) {
+        const char* hreg = b->h_args[h] + (size_t)8 * b->region;
+        char* dreg = b->d_args + (size_t)8 * b->region;
+        cudaError_t e = cudaMemcpyAsync(dreg, hreg, sizeof(FlagArgs) * n + sizeof(int) * (n + 1),
+                                        cudaMemcpyHostToDevice, sm);
+        if (e != cudaSuccess) return e;
+        launch_flags_batch(reinterpret_cast<const FlagArgs*>(dreg),
+                           reinterpret_cast<const int*>(dreg + sizeof(FlagArgs) * n), n, grid[8], b->P, b->f32, sm);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      }
       for (int r = 0; r < 8; ++r) {
         const int l = r / 2, pass = r % 2;
         char* hreg = b->h_args[h] + (size_t)r * b->region;
@@ -2214,6 +2281,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         cudaGetLastError();
         if (ok) {
           std::memcpy(b->gtot[h], grid, sizeof(grid));
+          b->gflags[h] = fl_on;
           ++b->captures;
         } else {
           b->gexec[h] = nullptr;
@@ -2227,7 +2295,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
       }
     }
     if (!replayed) CUDA_TRY(enqueue(b->stream));
-    b->launches += 8;
+    b->launches += 8 + (fl_on ? (grid[8] > 0 ? 3 : 2) : 0);
     for (long long sb : sblocks) b->launches += sb > 0 ? 1 : 0;
     for (const MirrorArgs& ma : mirs) b->launches += ma.nr > 0 ? 1 : 0;
     CUDA_TRY(cudaEventRecord(b->copied[h], b->stream));

@@ -238,6 +238,12 @@ int fill_cap_r1();
 int fill_cap_r2();
 int fill_max_tile();
 int fill_threads();
+// Batched cover flags of translating instances: one clear of the revival
+// counters, one flags launch over `blocks` (prefix table d_blk0, padded grids
+// allowed) and one revival launch, for `ninst` argument sets in device memory.
+void launch_flags_batch(const FlagArgs* d_args, const int* d_blk0, int ninst, int blocks, int P, bool f32,
+                        void* stream);
+long long flags_blocks(const FlagArgs& a);   // blocks of a's flags launch
 int launch_flags(const FlagArgs& a, void* stream);  // returns the number of kernels launched
 void launch_fill_dead(const FlagArgs& a, void* stream);  // binary64 buffers only
 // buf: a field buffer of binary64, or of binary32 when f32; the dense arrays

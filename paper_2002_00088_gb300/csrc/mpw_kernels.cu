@@ -136,8 +136,8 @@ __device__ __forceinline__ void cell_in_local(const FlagArgs& A, int q, int i, i
 // with NaN; cells that turn LIVE after having been GHOST or DEAD are
 // REVIVED: u_n there is interpolated from the owning local patch at t_n.
 template <int P, typename ST>
-__global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs A) {
-  long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void flags_block(const FlagArgs& A, long long bx) {
+  long long idx = bx * (long long)blockDim.x + threadIdx.x;
   int i = 0, j = 0, k = 0;
   bool valid;
   if (A.nreg == 0) {
@@ -250,15 +250,20 @@ __global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs 
   }
 }
 
+template <int P, typename ST>
+__global__ void __launch_bounds__(256) k_flags(const __grid_constant__ FlagArgs A) {
+  flags_block<P, ST>(A, blockIdx.x);
+}
+
 constexpr int REVIVE_BLOCKS = 4 * 152;  // four CTAs per SM of a GB300
 
 // Revival (reading of Sec. 2.4.2): the queued cells take the Lagrange
 // interpolant of their local patch at the current time, densely packed.
 template <int P, typename ST>
-__global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs A) {
+__device__ __forceinline__ void revive_blocks(const FlagArgs& A, int bx, int gx) {
   const int count = min(*A.rev_count, A.rev_cap);
   int e0 = 0, e1 = 0;
-  for (int base = blockIdx.x * blockDim.x; base < count; base += gridDim.x * blockDim.x) {
+  for (int base = bx * blockDim.x; base < count; base += gx * blockDim.x) {
     const int r = base + threadIdx.x;
     if (r < count) {
       const long long ent = A.rev_list[r];
@@ -289,6 +294,64 @@ __global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs
     if (e0) atomicMax(&A.expo[BUF_U * 2], e0);
     if (e1) atomicMax(&A.expo[BUF_U * 2 + 1], e1);
   }
+}
+
+template <int P, typename ST>
+__global__ void __launch_bounds__(256) k_revive(const __grid_constant__ FlagArgs A) {
+  revive_blocks<P, ST>(A, blockIdx.x, gridDim.x);
+}
+
+// Batched cover flags of translating instances (argument tables in device
+// memory): instance i owns flag blocks [blk0[i], blk0[i + 1]) (blocks from
+// blk0[ninst] on pad a captured grid), REVIVE_PER revival blocks each, and
+// its queue counter is cleared first by k_flags_reset.
+constexpr int REVIVE_PER = 16;
+
+__global__ void k_flags_reset(const FlagArgs* __restrict__ As, int ninst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ninst && As[i].rev_count) *As[i].rev_count = 0;
+}
+
+template <int P, typename ST>
+__global__ void __launch_bounds__(256) k_flags_batch(const FlagArgs* __restrict__ As, const int* __restrict__ blk0,
+                                                     int ninst) {
+  if ((int)blockIdx.x >= blk0[ninst]) return;
+  int lo = 0, hi = ninst - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if ((int)blockIdx.x >= blk0[mid]) lo = mid; else hi = mid - 1;
+  }
+  flags_block<P, ST>(As[lo], blockIdx.x - blk0[lo]);
+}
+
+template <int P, typename ST>
+__global__ void __launch_bounds__(256) k_revive_batch(const FlagArgs* __restrict__ As) {
+  const FlagArgs& A = As[blockIdx.x / REVIVE_PER];
+  if (!A.rev_count || !A.old_valid || A.skip_revive) return;
+  revive_blocks<P, ST>(A, blockIdx.x % REVIVE_PER, REVIVE_PER);
+}
+
+template <int P, typename ST>
+static void launch_flags_batch_t(const FlagArgs* d_args, const int* d_blk0, int ninst, int blocks, cudaStream_t s) {
+  k_flags_reset<<<(ninst + 127) / 128, 128, 0, s>>>(d_args, ninst);
+  if (blocks > 0) k_flags_batch<P, ST><<<blocks, 256, 0, s>>>(d_args, d_blk0, ninst);
+  k_revive_batch<P, ST><<<ninst * REVIVE_PER, 256, 0, s>>>(d_args);
+}
+
+void launch_flags_batch(const FlagArgs* d_args, const int* d_blk0, int ninst, int blocks, int P, bool f32,
+                        void* stream) {
+  const cudaStream_t s = (cudaStream_t)stream;
+  if (f32)
+    P == 6 ? launch_flags_batch_t<6, float>(d_args, d_blk0, ninst, blocks, s)
+           : launch_flags_batch_t<5, float>(d_args, d_blk0, ninst, blocks, s);
+  else
+    P == 6 ? launch_flags_batch_t<6, double>(d_args, d_blk0, ninst, blocks, s)
+           : launch_flags_batch_t<5, double>(d_args, d_blk0, ninst, blocks, s);
+}
+
+long long flags_blocks(const FlagArgs& a) {
+  const long long N = a.nreg ? a.reg_begin[a.nreg] : (long long)a.n[0] * a.n[1] * a.n[2];
+  return (N + 255) / 256;
 }
 
 // Every DEAD global cell of buffer A.Ug takes the Lagrange interpolant of the

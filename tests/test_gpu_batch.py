@@ -35,7 +35,10 @@ def test_batch_matches_individual_steps(mpw_lib, precision):
     b.step([w.dt for w in ws], steps)
     zc, ms, launches, graph_steps = b.tuning()
     assert zc in (8, 16, 32, 64) and ms > 0.0
-    assert launches == 8 * steps
+    # from the second step on (flags and exponent slots in place) the moving
+    # instances' cover flags are batched too: a counter clear, the flags and
+    # the revival, 3 launches per step
+    assert launches == 8 * steps + 3 * (steps - 1)
     # after tuning, moving instances replay a captured graph too (grids padded
     # to a capacity; each step's arguments come from the page-locked buffers)
     assert graph_steps == steps - 4
