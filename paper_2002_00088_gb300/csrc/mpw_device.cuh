@@ -7,51 +7,10 @@
 #include <cmath>
 #include <cstdint>
 
+#include "mpw_exp.cuh"
 #include "mpw_internal.cuh"
 
 namespace mpw {
-
-// ---------------------------------------------------------------------------
-// exp(x) for x <= 0 by Tang's table-driven method (ACM TOMS 15(2), 1989):
-// x = (64 k + j) ln2/64 + r with |r| <= ln2/128, exp(x) = 2^k 2^(j/64) (1 + p(r)),
-// p the degree-5 Taylor polynomial of e^r - 1 (truncation below 4e-17).  The
-// 2^(j/64) table holds correctly rounded values; ln2/64 is split so that n times
-// its high part is exact.  Results below 2^-1016 are flushed to zero (the
-// analytic boundary values they would feed are relative to O(1) fields).
-static __constant__ double c_exp2_j64[64] = {
-    0x1.0000000000000p+0, 0x1.02c9a3e778061p+0, 0x1.059b0d3158574p+0, 0x1.0874518759bc8p+0,
-    0x1.0b5586cf9890fp+0, 0x1.0e3ec32d3d1a2p+0, 0x1.11301d0125b51p+0, 0x1.1429aaea92de0p+0,
-    0x1.172b83c7d517bp+0, 0x1.1a35beb6fcb75p+0, 0x1.1d4873168b9aap+0, 0x1.2063b88628cd6p+0,
-    0x1.2387a6e756238p+0, 0x1.26b4565e27cddp+0, 0x1.29e9df51fdee1p+0, 0x1.2d285a6e4030bp+0,
-    0x1.306fe0a31b715p+0, 0x1.33c08b26416ffp+0, 0x1.371a7373aa9cbp+0, 0x1.3a7db34e59ff7p+0,
-    0x1.3dea64c123422p+0, 0x1.4160a21f72e2ap+0, 0x1.44e086061892dp+0, 0x1.486a2b5c13cd0p+0,
-    0x1.4bfdad5362a27p+0, 0x1.4f9b2769d2ca7p+0, 0x1.5342b569d4f82p+0, 0x1.56f4736b527dap+0,
-    0x1.5ab07dd485429p+0, 0x1.5e76f15ad2148p+0, 0x1.6247eb03a5585p+0, 0x1.6623882552225p+0,
-    0x1.6a09e667f3bcdp+0, 0x1.6dfb23c651a2fp+0, 0x1.71f75e8ec5f74p+0, 0x1.75feb564267c9p+0,
-    0x1.7a11473eb0187p+0, 0x1.7e2f336cf4e62p+0, 0x1.82589994cce13p+0, 0x1.868d99b4492edp+0,
-    0x1.8ace5422aa0dbp+0, 0x1.8f1ae99157736p+0, 0x1.93737b0cdc5e5p+0, 0x1.97d829fde4e50p+0,
-    0x1.9c49182a3f090p+0, 0x1.a0c667b5de565p+0, 0x1.a5503b23e255dp+0, 0x1.a9e6b5579fdbfp+0,
-    0x1.ae89f995ad3adp+0, 0x1.b33a2b84f15fbp+0, 0x1.b7f76f2fb5e47p+0, 0x1.bcc1e904bc1d2p+0,
-    0x1.c199bdd85529cp+0, 0x1.c67f12e57d14bp+0, 0x1.cb720dcef9069p+0, 0x1.d072d4a07897cp+0,
-    0x1.d5818dcfba487p+0, 0x1.da9e603db3285p+0, 0x1.dfc97337b9b5fp+0, 0x1.e502ee78b3ff6p+0,
-    0x1.ea4afa2a490dap+0, 0x1.efa1bee615a27p+0, 0x1.f50765b6e4540p+0, 0x1.fa7c1819e90d8p+0,
-};
-
-__device__ __forceinline__ double exp_nonpos(double x) {
-  if (!(x > -704.0)) return x != x ? x : 0.0;
-  const double t = fma(x, 0x1.71547652b82fep+6, 0x1.8p52);  // 1.5 2^52 + round(64 x / ln2)
-  const int n = __double2loint(t);
-  const double nd = t - 0x1.8p52;
-  double r = fma(nd, -0x1.62e42fefa0000p-7, x);
-  r = fma(nd, -0x1.cf79abc9e3b3ap-46, r);
-  double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
-  p = fma(p, r, 1.0 / 6.0);
-  p = fma(p, r, 0.5);
-  p = fma(p * r, r, r);
-  const double T = c_exp2_j64[n & 63];
-  const double m = fma(T, p, T);
-  return __hiloint2double(__double2hiint(m) + ((n >> 6) << 20), __double2loint(m));
-}
 
 // Closed forms (Sec. 3): spherical Gaussian pulse pairs, plane-wave sums and
 // the static harmonic basis.  psi = [g(t+r) - g(t-r)] / (2r) with
@@ -75,7 +34,7 @@ __device__ __forceinline__ void gauss_pulse(double A, double a, double r2, doubl
   const double r = r2 * rs;
   const double sp = t + r, sm = t - r;
   const double qp = -a * sp * sp, qm = -a * sm * sm;
-  const double ep = A * exp_nonpos(qp), em = A * exp_nonpos(qm);
+  const double ep = A * exp_nonpos_fx(qp), em = A * exp_nonpos_fx(qm);
   const double inv = 0.5 * rs;
   ps += (ep * sp - em * sm) * inv;
   pv += (ep * (1.0 + 2.0 * qp) - em * (1.0 + 2.0 * qm)) * inv;
