@@ -184,15 +184,17 @@ def kernel_source_hash(f32=False):
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(f32=False):
+def recorded_traffic(f32=False, workload=None):
     """DRAM bytes per launch of the RHS kernel from the committed ncu summary,
-    if it was taken on the current kernel sources."""
+    if it was taken on the current kernel sources and on this workload."""
     path = os.path.join(ROOT, "profiles", "rhs32_stage_traffic.json" if f32 else "rhs_stage_traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         d = json.load(f)
     if d.get("kernel_source_hash") != kernel_source_hash(f32):
+        return None
+    if workload is not None and d.get("workload") != workload:
         return None
     return d.get("traffic_bytes_per_launch")
 
@@ -417,7 +419,7 @@ def run_ours(args):
     peak, peak_kind = measured_peaks()
     bytes_pt = BYTES_PER_POINT_STAGE // 2 if f32 else BYTES_PER_POINT_STAGE
     achieved = live * bytes_pt / (rhs_avg_ms * 1e-3) / 1e9
-    traffic = recorded_traffic(f32)
+    traffic = recorded_traffic(f32, w.name)
     esize = 4 if f32 else 8
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

@@ -7,7 +7,7 @@
 #include <cmath>
 #include <cstdint>
 
-#include "mpw_exp.cuh"
+#include "mpw_fxmath.cuh"
 #include "mpw_internal.cuh"
 
 namespace mpw {
@@ -30,14 +30,13 @@ __device__ __forceinline__ void gauss_pulse(double A, double a, double r2, doubl
     pv += g2 + r2_6 * g4;
     return;
   }
-  const double rs = rsqrt(r2);  // 1/r
-  const double r = r2 * rs;
+  double r, inv;  // r and 1/(2r)
+  sqrt_pair_fx(r2, r, inv);
   const double sp = t + r, sm = t - r;
   const double qp = -a * sp * sp, qm = -a * sm * sm;
-  const double ep = A * exp_nonpos_fx(qp), em = A * exp_nonpos_fx(qm);
-  const double inv = 0.5 * rs;
-  ps += (ep * sp - em * sm) * inv;
-  pv += (ep * (1.0 + 2.0 * qp) - em * (1.0 + 2.0 * qm)) * inv;
+  const double ep = exp_nonpos_fx(qp), em = exp_nonpos_fx(qm), ia = A * inv;
+  ps += (ep * sp - em * sm) * ia;
+  pv += (ep * (1.0 + 2.0 * qp) - em * (1.0 + 2.0 * qm)) * ia;
 }
 
 // Sum of Gaussian pulses (params 5 per pulse), accumulated into ps, pv.

@@ -1,9 +1,13 @@
-// mpw_exp.cuh -- exp(x) for x <= 0 with the work in 64-bit integers.
+// mpw_fxmath.cuh -- exp(x) for x <= 0, and sqrt(y) with 1/(2 sqrt(y)), with
+// the work in 64-bit integers.
 //
 // GB300 issues FP64 operations at a small fraction of its integer rate, and
 // the Gaussian closed forms of the analytic boundary (Sec. 3) spend most of
-// their FP64 operations in two exponentials per pulse.  This version keeps
-// Tang's table-driven method (ACM TOMS 15(2), 1989): with y = -x >= 0,
+// their FP64 operations in two exponentials and one reciprocal square root
+// per pulse.
+//
+// exp_nonpos_fx keeps Tang's table-driven method (ACM TOMS 15(2), 1989):
+// with y = -x >= 0,
 //   n = round(64 y / ln2),  s = n ln2/64 - y  (|s| <= ln2/128),
 //   exp(x) = 2^(-n/64) e^s = 2^k 2^(j/64) (1 + p(s)),  -n = 64 k + j,
 // p the degree-5 Taylor polynomial of e^s - 1 (truncation below 4e-17), but
@@ -19,6 +23,13 @@
 // fixed-point steps (a few 2^-62).  x <= -704 (and -inf) gives 0, as results
 // below 2^-1015 are flushed; NaN propagates.  The callers pass x = -a s^2
 // with a > 0; x > 0 falls back to the library exp.
+//
+// sqrt_pair_fx writes y = g 4^k with g in [1, 4), refines z = 1/sqrt(g) from
+// the single-precision estimate by two Newton steps z (3 - g z^2) / 2 on 2^62
+// (the estimate's 2^-22 error squares twice), and forms sqrt(y) = g z 2^k and
+// 1/(2 sqrt(y)) = z 2^(-k-1), each rounded once: within 0.53 units in the
+// last place.  Non-finite or non-positive y falls back to the library
+// functions.
 //
 // The file includes nothing: the CUDA intrinsics it names come from the
 // translation units that include it.
@@ -44,6 +55,17 @@ static __device__ const long long g_exp2_q62[64] = {
     8099283532826439817ll, 8187478948029213993ll, 8276634748336579668ll, 8366761391656660532ll,
     8457869449776733335ll, 8549969609603290562ll, 8643072674415606502ll, 8737189565132953757ll,
     8832331321595618838ll, 8928509103859867100ll, 9025734193507008925ll, 9124017994966720698ll};
+
+// The binary64 of M 2^(E - 62) for M in [2^61, 2^63): 53 bits rounded half
+// up.  Adding the mantissa with its leading bit to the exponent field one
+// below also takes a carry out of the rounding into the exponent.
+__device__ __forceinline__ double fx_to_double(long long M, int E) {
+  const bool top = M >= (1ll << 62);
+  const int sh = top ? 10 : 9;
+  const long long r53 = ((M >> (sh - 1)) + 1) >> 1;
+  const long long biased = (top ? 1023 : 1022) + E;
+  return __longlong_as_double(((biased - 1) << 52) + r53);
+}
 
 __device__ __forceinline__ double exp_nonpos_fx(double x) {
   const long long bits = __double_as_longlong(x);
@@ -76,15 +98,35 @@ __device__ __forceinline__ double exp_nonpos_fx(double x) {
   const long long m = -n;
   const long long T = __ldg(&g_exp2_q62[m & 63]);
   const long long M = T + (__mul64hi(T, p) << 2);
-  // binary64 of M 2^(k - 62), k = floor(m / 64): 53 bits, rounded half up;
-  // adding the mantissa with its leading bit to the exponent field one
-  // below also takes a carry out of the rounding into the exponent
-  const int k = (int)(m >> 6);
-  const bool top = M >= (1ll << 62);
-  const int sh = top ? 10 : 9;
-  const long long r53 = ((M >> (sh - 1)) + 1) >> 1;
-  const long long biased = (top ? 1023 : 1022) + k;
-  return __longlong_as_double(((biased - 1) << 52) + r53);
+  return fx_to_double(M, (int)(m >> 6));  // times 2^k, k = floor(m / 64)
+}
+
+__device__ __forceinline__ void sqrt_pair_fx(double y, double& root, double& half_inv) {
+  const long long bits = __double_as_longlong(y);
+  const int e = (int)(bits >> 52);  // y > 0: the sign bit is clear
+  if (bits <= 0 || e == 0 || e == 0x7ff) {  // y <= 0, subnormal, infinite or NaN
+    root = sqrt(y);
+    half_inv = 0.5 / root;
+    return;
+  }
+  const int E = e - 1023, odd = E & 1, k = (E - odd) >> 1;
+  const long long frac = bits & 0xfffffffffffffll;
+  const long long g = (frac | 0x10000000000000ll) << (9 + odd);  // g on 2^61
+  // estimate of 1/sqrt(g) from the binary32 of g, then on 2^62
+  const float zf = rsqrtf(__int_as_float(((127 + odd) << 23) | (int)(frac >> 29)));
+  const int zb = __float_as_int(zf);
+  long long z = (long long)((zb & 0x7fffff) | 0x800000) << (((zb >> 23) & 0xff) - 88);
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const long long z2 = __mul64hi(z, z) << 2;           // z^2 on 2^62
+    const long long gz2 = __mul64hi(g, z2) << 3;         // g z^2 on 2^62
+    const long long h = 3 * (1ll << 61) - (gz2 >> 1);    // (3 - g z^2) / 2 on 2^62
+    z = __mul64hi(z, h) << 2;
+  }
+  half_inv = fx_to_double(z, -k - 1);
+  // g z = sqrt(g) in [1, 2) on 2^59, taken to 2^61 (below 2^62 with room
+  // for the truncation errors), that is M / 2^62 = sqrt(g) / 2
+  root = fx_to_double(__mul64hi(g, z) << 2, k + 1);
 }
 
 }  // namespace mpw
