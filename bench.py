@@ -60,7 +60,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=int, default=1, help="divide the workload resolution (testing only)")
-    ap.add_argument("--e2e-steps", type=int, default=20)
+    ap.add_argument("--e2e-steps", type=int, default=None,
+                    help="end-to-end leg: timed steps (default: --steps; the first input copy and the last "
+                         "result copy are not overlapped, so short legs understate the rate)")
     ap.add_argument("--cpu-sample-scale", type=int, default=1,
                     help="cpu_baseline: the workload at this resolution divisor")
     ap.add_argument("--cpu-sample-steps", type=int, default=10, help="cpu_baseline: timed oracle steps")
@@ -88,7 +90,10 @@ def parse():
     ap.add_argument("--precision", type=int, default=64, choices=[64, 32],
                     help="64: the FP64 workload (default); 32: the binary32 precision workload, with its error "
                          "against the closed form and the FP64 path on the same workload")
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.e2e_steps is None:
+        args.e2e_steps = args.steps
+    return args
 
 
 def dist_info():
