@@ -31,7 +31,7 @@ def _rank(rank, world, port, out):
 
 def test_whole_job_over_two_ranks():
     world = 2
-    with mp.Manager() as m:
+    with mp.get_context("spawn").Manager() as m:  # no fork of a process that may hold a CUDA context
         out = m.dict()
         mp.spawn(_rank, args=(world, _free_port(), out), nprocs=world, join=True)
         for r in range(world):
