@@ -1001,6 +1001,10 @@ mpw_status run_fill(mpw_ctx* c, int b, double t, int reset_buf, int parts = FILL
 // One fused RHS + RK4 stage launch over every patch (substage l at t).
 // RHS + stage arguments of substage l for every patch of c; returns the
 // number of CTAs.  zc: planes per CTA chunk (0: the default).
+// The fixed-point RHS body converts one x/y halo point per thread: the
+// 6 TX + 6 TY halo points of a tile need that many of its TX TY threads.
+static_assert(6 * RHS_TX + 6 * RHS_TY <= RHS_TX * RHS_TY, "RHS tile too small for its halo (MPW_RHS_TY >= 8)");
+
 int prep_rhs(mpw_ctx* c, int l, double t, double dt, RhsArgs& a, int zc = 0, bool skip_global = false) {
   static const int in_buf[4] = {BUF_U, BUF_YA, BUF_YB, BUF_YA};
   static const int out_buf[4] = {BUF_YA, BUF_YB, BUF_YA, BUF_U};
