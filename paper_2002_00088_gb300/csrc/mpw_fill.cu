@@ -603,7 +603,10 @@ __device__ __noinline__ void sph_ghost_block(const FillArgs& A, const InterpSeg&
   int e0 = 0, e1 = 0;
   if (idx < count) {
     int x, y, z;
-    shell_point(idx, O, NG, x, y, z);
+    if (count < (1ll << 31))
+      shell_point_t<unsigned>((unsigned)idx, O, NG, x, y, z);
+    else
+      shell_point(idx, O, NG, x, y, z);
     const int i = x - NG, j = y - NG, k = z - NG;
     ST* Tt = reinterpret_cast<ST*>(S.T);
     const long long c = S.gt.at(i, j, k);
@@ -945,7 +948,10 @@ __device__ __forceinline__ void fill_body(const FillArgs& A, const int b0) {
     if (idx < A.outer_count) {
       const int O[3] = {A.gg.n[0] + 2 * NG, A.gg.n[1] + 2 * NG, A.gg.n[2] + 2 * NG};
       int x, y, z;
-      shell_point(idx, O, NG, x, y, z);
+      if (A.outer_count < (1ll << 31))
+        shell_point_t<unsigned>((unsigned)idx, O, NG, x, y, z);
+      else
+        shell_point(idx, O, NG, x, y, z);
       const int i = x - NG, j = y - NG, k = z - NG;
       const long long c = A.gg.at(i, j, k);
       ST* Yg = reinterpret_cast<ST*>(A.Yg);
