@@ -8,6 +8,7 @@
 #include <cstdint>
 
 #include "mpw_fxmath.cuh"
+#include "mpw_index.cuh"
 #include "mpw_internal.cuh"
 
 namespace mpw {
@@ -234,52 +235,6 @@ __device__ __forceinline__ bool interp_point_shell(const ST* __restrict__ src, c
   o0 = a0;
   o1 = a1;
   return true;
-}
-
-// Maps idx in [0, Ox*Oy*Oz - Ix*Iy*Iz) onto the points of the hollow box of
-// outer extent O whose walls are th thick (I = max(O - 2 th, 0)).
-// IdxT is the index type: unsigned (32-bit divisions, several times cheaper on
-// the GPU) when the shell holds fewer than 2^31 points, whose products
-// below then fit as well; long long otherwise.
-template <typename IdxT>
-__device__ __forceinline__ void shell_point_t(IdxT idx, const int O[3], int th, int& x, int& y, int& z) {
-  const int Ix = max(O[0] - 2 * th, 0), Iy = max(O[1] - 2 * th, 0), Iz = max(O[2] - 2 * th, 0);
-  const IdxT pxy = (IdxT)O[0] * (IdxT)O[1];
-  const IdxT nz = pxy * (IdxT)(O[2] - Iz);
-  if (idx < nz) {
-    const int zs = (int)(idx / pxy);
-    const IdxT r = idx - (IdxT)zs * pxy;
-    z = zs < th ? zs : zs + Iz;
-    y = (int)(r / (IdxT)O[0]);
-    x = (int)(r - (IdxT)y * (IdxT)O[0]);
-    return;
-  }
-  idx -= nz;
-  const IdxT rowsy = (IdxT)O[0] * (IdxT)(O[1] - Iy);
-  const IdxT ny = rowsy * (IdxT)Iz;
-  if (idx < ny) {
-    const int zz = (int)(idx / rowsy);
-    const IdxT r = idx - (IdxT)zz * rowsy;
-    z = th + zz;
-    const int ys = (int)(r / (IdxT)O[0]);
-    x = (int)(r - (IdxT)ys * (IdxT)O[0]);
-    y = ys < th ? ys : ys + Iy;
-    return;
-  }
-  idx -= ny;
-  const int wx = O[0] - Ix;
-  const IdxT per_z = (IdxT)wx * (IdxT)Iy;
-  const int zz = (int)(idx / per_z);
-  const IdxT r = idx - (IdxT)zz * per_z;
-  z = th + zz;
-  const int yy = (int)(r / (IdxT)wx);
-  const int xs = (int)(r - (IdxT)yy * (IdxT)wx);
-  y = th + yy;
-  x = xs < th ? xs : xs + Ix;
-}
-
-__device__ __forceinline__ void shell_point(long long idx, const int O[3], int th, int& x, int& y, int& z) {
-  shell_point_t<long long>(idx, O, th, x, y, z);
 }
 
 // ---------------------------------------------------------------------------

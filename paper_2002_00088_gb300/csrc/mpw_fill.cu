@@ -104,42 +104,6 @@ struct Acc3 {
   __device__ __forceinline__ long long value() const { return hh * 8 + (hl >> 28) + (lh >> 28); }
 };
 
-// Position of element e of a [2][d2][d1][d0] block (x fastest, then y, z,
-// field) and its advance by FILL_THREADS: the divisions are taken once per
-// thread, every later step is a mixed-radix addition with single carries
-// (each digit and its increment are below the radix).
-struct BlockWalk {
-  int o0, o1, o2, f;
-  int a0, a1, a2, a3;
-  int d0, d1, d2;
-  __device__ __forceinline__ BlockWalk(int e, int d0_, int d1_, int d2_) : d0(d0_), d1(d1_), d2(d2_) {
-    int q = e / d0;
-    o0 = e - q * d0;
-    o1 = q % d1;
-    q /= d1;
-    o2 = q % d2;
-    f = q / d2;
-    q = FILL_THREADS / d0;
-    a0 = FILL_THREADS - q * d0;
-    a1 = q % d1;
-    q /= d1;
-    a2 = q % d2;
-    a3 = q / d2;
-  }
-  __device__ __forceinline__ void next() {
-    o0 += a0;
-    int c = o0 >= d0;
-    o0 -= c ? d0 : 0;
-    o1 += a1 + c;
-    c = o1 >= d1;
-    o1 -= c ? d1 : 0;
-    o2 += a2 + c;
-    c = o2 >= d2;
-    o2 -= c ? d2 : 0;
-    f += a3 + c;
-  }
-};
-
 // One separable pass over both fields: contract axis AX of the blocks `in`
 // (extents din, x fastest, field f at in + f * in_stride) against the 1-D
 // weights of the tile's targets along AX.  ws holds the absolute window
@@ -157,7 +121,7 @@ __device__ __forceinline__ void contract_axis(const void* __restrict__ in, int i
   const int s1 = din[0], s2 = din[0] * din[1];
   const int st = AX == 0 ? 1 : (AX == 1 ? s1 : s2);
   const int n = d0 * d1 * d2;
-  BlockWalk wk(threadIdx.x, d0, d1, d2);
+  BlockWalk<FILL_THREADS> wk(threadIdx.x, d0, d1, d2);
   for (int e = threadIdx.x; e < 2 * n; e += FILL_THREADS, wk.next()) {
     const int f = wk.f;
     const int r = e - f * n;
@@ -874,7 +838,7 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
       contract<P, M_FP32, false>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], WF + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
       __syncthreads();
       const float* out = reinterpret_cast<const float*>(R1);
-      BlockWalk wk(tid, T[0], T[1], T[2]);
+      BlockWalk<FILL_THREADS> wk(tid, T[0], T[1], T[2]);
       for (int e = tid; e < 2 * ntar; e += FILL_THREADS, wk.next()) {
         const int f = wk.f;
         const int r = e - f * ntar;
@@ -893,7 +857,7 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
       const double p2[2] = {__longlong_as_double((long long)(Esu - 58) << 52),
                             __longlong_as_double((long long)(Epu - 58) << 52)};
       const long long* out = reinterpret_cast<const long long*>(R1);
-      BlockWalk wk(tid, T[0], T[1], T[2]);
+      BlockWalk<FILL_THREADS> wk(tid, T[0], T[1], T[2]);
       for (int e = tid; e < 2 * ntar; e += FILL_THREADS, wk.next()) {
         const int f = wk.f;
         const int r = e - f * ntar;
@@ -909,7 +873,7 @@ __device__ void interp_tile(const FillArgs& A, const InterpSeg& S, const int org
       __syncthreads();
       contract<P, M_FP64, false>(R2, CAP_R2, R1, CAP_R1, d2, x2, T[x2], W + x2 * MAXT * 6, WS + x2 * MAXT, D0[x2]);
       __syncthreads();
-      BlockWalk wk(tid, T[0], T[1], T[2]);
+      BlockWalk<FILL_THREADS> wk(tid, T[0], T[1], T[2]);
       for (int e = tid; e < 2 * ntar; e += FILL_THREADS, wk.next()) {
         const int f = wk.f;
         const int r = e - f * ntar;
