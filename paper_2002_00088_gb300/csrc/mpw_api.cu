@@ -2129,6 +2129,22 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         fl_batch = fl_batch && !P.sph() && P.d.motion != MPW_MOTION_ROTATING &&
                    (c->cfg.precision == 32 || P.u_expo_valid);
     }
+    // host cover-flag state of the contexts whose flags this step prepares,
+    // put back if the step fails before its launches are queued: the device
+    // flags are then still those of the last completed step, and the next
+    // flag computation must start from that step's covered boxes
+    struct FlagsUndo {
+      std::vector<mpw_ctx*> ctx;
+      std::vector<std::vector<Box>> boxes;
+      std::vector<char> valid, glist;
+      ~FlagsUndo() {
+        for (size_t k = 0; k < ctx.size(); ++k) {
+          ctx[k]->boxes = boxes[k];
+          ctx[k]->flags_valid = valid[k] != 0;
+          ctx[k]->glist_valid = glist[k] != 0;
+        }
+      }
+    } undo;
     int nflag = 0;
     {
       char* freg = b->h_args[h] + (size_t)8 * b->region;
@@ -2145,7 +2161,13 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
         }
         if ((st = validate_step(c, dt[i], tnp[i]))) return st;
         bool launch = false;
-        if (any_moving(c) && (st = prep_flags(c, tnp[i], true, fa[i], launch))) return st;
+        if (any_moving(c)) {
+          undo.ctx.push_back(c);
+          undo.boxes.push_back(c->boxes);
+          undo.valid.push_back(c->flags_valid ? 1 : 0);
+          undo.glist.push_back(c->glist_valid ? 1 : 0);
+          if ((st = prep_flags(c, tnp[i], true, fa[i], launch))) return st;
+        }
         if (launch) {
           ftotal += flags_blocks(fa[i]);
           c->flags_valid = true;
@@ -2299,6 +2321,7 @@ mpw_status mpw_batch_step(mpw_batch* b, const double* dt, int nsteps) {
       }
     }
     if (!replayed) CUDA_TRY(enqueue(b->stream));
+    undo.ctx.clear();  // queued: the prepared flags are the contexts' own now
     b->launches += 8 + (fl_on ? (grid[8] > 0 ? 3 : 2) : 0);
     for (long long sb : sblocks) b->launches += sb > 0 ? 1 : 0;
     for (const MirrorArgs& ma : mirs) b->launches += ma.nr > 0 ? 1 : 0;

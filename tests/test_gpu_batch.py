@@ -104,3 +104,33 @@ def test_batch_with_rotating_instances_matches_individual_steps(mpw_lib, precisi
             a, c = g.get_fields(q), h.get_fields(q)
             np.testing.assert_array_equal(a[0], c[0])
             np.testing.assert_array_equal(a[1], c[1])
+
+
+def test_failed_batch_step_leaves_instances_at_their_last_step(mpw_lib):
+    """A batched step that one instance rejects (dt beyond its CFL bound) after
+    the other instances' cover flags were prepared queues nothing, and leaves
+    every instance as its last completed step left it: further batched steps
+    give the same bits as a twin batch that never saw the failed calls."""
+    # orbiting cubes cross about a third of a global cell per step, so the
+    # covered boxes change between the steps around the failed calls
+    ws = [wl.orbiting_gauss(scale=4, seed_index=k) for k in (1, 2, 3)]
+    dts = [w.dt for w in ws]
+    bad = dts[:-1] + [100.0]
+    a = make_all(mpw_lib, ws, 64)
+    twin = make_all(mpw_lib, ws, 64)
+    ba, bt = mpw_lib.Batch(a), mpw_lib.Batch(twin)
+    ba.step(dts, 2)  # cover flags and exponent slots in place: flags batched from here on
+    bt.step(dts, 2)
+    for _ in range(12):
+        with pytest.raises(mpw_lib.MpwError) as e:
+            ba.step(bad, 1)
+        assert e.value.status in (mpw_lib.ERR_CFL, 4)  # CFL or traversal bound
+        ba.step(dts, 1)
+        bt.step(dts, 1)
+    for g, h, w in zip(a, twin, ws):
+        assert g.time == h.time
+        np.testing.assert_array_equal(g.get_flags(), h.get_flags())
+        for q in range(len(w.patches)):
+            x, y = g.get_fields(q), h.get_fields(q)
+            np.testing.assert_array_equal(x[0], y[0])
+            np.testing.assert_array_equal(x[1], y[1])
