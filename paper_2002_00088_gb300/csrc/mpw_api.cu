@@ -608,7 +608,15 @@ mpw_status prep_flags(mpw_ctx* c, double t, bool revive, FlagArgs& a, bool& laun
 mpw_status run_flags(mpw_ctx* c, double t, bool revive = true) {
   FlagArgs a;
   bool launch;
-  if (mpw_status st = prep_flags(c, t, revive, a, launch)) return st;
+  const std::vector<Box> old_boxes = c->boxes;
+  const bool old_valid = c->flags_valid, old_glist = c->glist_valid;
+  if (mpw_status st = prep_flags(c, t, revive, a, launch)) {
+    // nothing launched: the device flags still belong to the old boxes
+    c->boxes = old_boxes;
+    c->flags_valid = old_valid;
+    c->glist_valid = old_glist;
+    return st;
+  }
   if (!launch) return MPW_OK;
   c->launch_begin(MPW_KERNEL_FLAGS);
   const int kernels = launch_flags(a, c->stream);  // flags kernel, plus the revival kernel when old flags exist
