@@ -241,13 +241,15 @@ mpw_status mpw_step_async(mpw_ctx* ctx, double dt, int nsteps);
  * The paper has no counterpart (it runs one instance per set of MPI ranks);
  * this is the batching pattern of serving many small simulations on one GPU.
  * Each instance is an ordinary context.  A batched step does per instance
- * what mpw_step does (validation, cover flags, exponent slots), but every
- * ghost fill and every RHS + stage substage is ONE kernel launch over all
- * instances (plus one RHS launch over the spherical shells of up to 64
- * instances, when there are shells), so small instances share the GPU
- * instead of running one after the other.  Instances may hold rotating
- * patches and spherical shells.  Results are bit for bit those of mpw_step
- * on each context.
+ * what mpw_step does on the host (validation, the choice of the cells whose
+ * cover flags can change, exponent slots), but every ghost fill and every
+ * RHS + stage substage is ONE kernel launch over all instances (plus one RHS
+ * launch over the spherical shells of up to 64 instances, when there are
+ * shells), and when every patch translates the cover flags of all instances
+ * are one batched launch too, so small instances share the GPU instead of
+ * running one after the other.  Instances may hold rotating patches and
+ * spherical shells (their flags are then launched per instance).  Results
+ * are bit for bit those of mpw_step on each context.
  *
  * mpw_batch_create: ctxs[0..n) must be distinct, live, hold a global patch,
  *   and share device, stream, precision, interp_points and arith; the array
@@ -259,11 +261,15 @@ mpw_status mpw_step_async(mpw_ctx* ctx, double dt, int nsteps);
  *   chunk depth (planes marched per CTA): each candidate (8, 16, 32, 64)
  *   runs one step, timed with CUDA events from the first RHS launch of the
  *   step to the end of its last one, and the fastest is kept.
- *   Errors as mpw_step, for the first instance that fails.
- *   While no instance has a moving patch, the copies and launches of a step
- *   are captured once in a CUDA graph (one per argument buffer) and replayed:
- *   the launches and grids are then the same every step, and the replayed
- *   copies pick up the new substage times from the page-locked buffers.
+ *   Errors as mpw_step, for the first instance that fails.  A step that
+ *   fails before its launches are queued (a host-side check) leaves every
+ *   instance at its last completed step.
+ *   After the tuning steps the copies and launches of a step are captured in
+ *   a CUDA graph (one per argument buffer) and replayed; the replayed copies
+ *   pick up each step's arguments from the page-locked buffers.  With moving
+ *   patches the grids are padded to a capacity (blocks past a step's own
+ *   total exit at once) and a step whose grids outgrow it is captured anew.
+ *   Batches with moving spherical shells launch directly.
  * mpw_batch_tuning: the chosen chunk depth (0 while tuning), its measured
  *   time per step in ms (first RHS launch to the end of the last; three ghost
  *   fills lie in between), the number of batched launches so far and the
